@@ -1,0 +1,872 @@
+/*
+ * kete_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Built with -O2 -ffp-contract=off.  Every function is written for a reader
+ * checking it against the paper by eye; speed is not a goal.  The CUDA path
+ * never includes, links or calls this file.
+ *
+ * Readings of the paper (where it is silent, ambiguous or garbled):
+ *  R1 (Eq. A.1/A.3/A.4 sign convention): r = r_body - r_m, v = v_body - v_m;
+ *     Newton a = -mu r/|r|^3, GR as printed in Eq. A.3 with that r and v,
+ *     J2 = -psi [(1-5z^2/r^2)x, (1-5z^2/r^2)y, (3-5z^2/r^2)z] in the body's
+ *     equatorial frame.
+ *  R2 (App. A.2/A.3): GR for Sun, Jupiter and Earth; J2 for Sun and Jupiter.
+ *  R4 (App. A.6, predictor removed): every step starts its corrector from
+ *     b = 0 and iterates until converged or the cap.
+ *  R5 (App. A.6, "tuned" constants): IAS15 defaults -- step control eps 1e-9,
+ *     safety factor 0.25, corrector threshold 1e-16 on max|db6|/max|a|,
+ *     cap 12 iterations, stop early when the error stops decreasing.
+ *  R6 (Sec. 2, batches): greedy batches over epoch-sorted FoVs, a batch holds
+ *     the epochs t with t - t_first < span; t_ref = (t_first + t_last)/2.
+ *  R7 (Sec. 2, two-body): heliocentric, mu = GM_sun, Sun position re-added at
+ *     the target time.
+ *  R8 (Sec. 2, light delay): tau0 = |r(t)-o|/c, then three fixed iterations
+ *     tau <- |r(t-tau)-o|/c; apparent vector u = r(t-tau)-o.  No aberration.
+ *  R9 (Sec. 3.1): inside iff every n_i.u > 0 (strict).
+ *  R10 (time bookkeeping, not in the paper): epochs are absolute TDB Julian
+ *     dates, so every step is taken as the exact difference of the two
+ *     representable epochs it joins; the last step of a leg lands exactly on
+ *     the target epoch.  Two-body intervals are formed as (t_obs - t_ref) - tau
+ *     before any absolute epoch is rounded.
+ */
+#include "kete_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- constants (App. A.1 units: AU, TDB days) ---------------------------- */
+static const double KM_PER_AU = 149597870.7;
+static double c_au_per_day(void) { return 299792.458 * 86400.0 / KM_PER_AU; }
+static double deg2rad(double d) { return d * (M_PI / 180.0); }
+static double obliquity(void) { return deg2rad(84381.448 / 3600.0); }
+
+void ko_force_model_default(ko_force_model *fm)
+{
+    memset(fm, 0, sizeof(*fm));
+    fm->body_mask = 0x1FF;                          /* Sun + 8 planets */
+    fm->gr_mask = (1u << 0) | (1u << 3) | (1u << 5); /* Sun, Earth, Jupiter */
+    fm->j2_mask = (1u << 0) | (1u << 5);             /* Sun, Jupiter */
+    fm->max_iter = 12;
+    /* Sun */
+    fm->j2[0] = 2.1961e-7;
+    fm->radius[0] = 696000.0 / KM_PER_AU;
+    fm->pole_ra[0] = deg2rad(286.13);
+    fm->pole_dec[0] = deg2rad(63.87);
+    /* Jupiter */
+    fm->j2[5] = 0.014736;
+    fm->radius[5] = 71492.0 / KM_PER_AU;
+    fm->pole_ra[5] = deg2rad(268.056595);
+    fm->pole_dec[5] = deg2rad(64.495303);
+    fm->eps = 1e-9;
+    fm->eps_pc = 1e-16;
+    fm->safety = 0.25;
+    fm->dt_init = 4.0;
+    fm->max_steps = 1000000;
+}
+
+/* ---- ephemeris table (App. A: SPICE-like segment lookup) ----------------- */
+int ko_ephem_load(ko_ephem *e, const void *buf, size_t n)
+{
+    const unsigned char *p = (const unsigned char *)buf;
+    int32_t hdr[4];
+    double td[2];
+    memset(e, 0, sizeof(*e));
+    if (n < 256 || memcmp(p, "KETECHB1", 8) != 0) return -1;
+    memcpy(hdr, p + 8, sizeof(hdr));
+    memcpy(td, p + 24, sizeof(td));
+    if (hdr[0] != 1 || hdr[1] < 1 || hdr[1] > KO_MAX_BODIES || hdr[2] < 1 || hdr[3] < 1)
+        return -1;
+    e->n_bodies = hdr[1];
+    e->n_coef = hdr[2];
+    e->n_seg = hdr[3];
+    e->t_start = td[0];
+    e->seg_len = td[1];
+    memcpy(e->gm, p + 48, sizeof(double) * KO_MAX_BODIES);
+    size_t nc = (size_t)e->n_bodies * e->n_seg * 3 * e->n_coef;
+    if (n < 256 + nc * sizeof(double) || !(e->seg_len > 0)) return -1;
+    e->coef = (double *)malloc(nc * sizeof(double));
+    if (!e->coef) return -1;
+    memcpy(e->coef, p + 256, nc * sizeof(double));
+    return 0;
+}
+
+void ko_ephem_free(ko_ephem *e)
+{
+    free(e->coef);
+    e->coef = NULL;
+}
+
+/* Position (and velocity) of table body `body` at t: sum_k c_k T_k(tau) with
+ * T_k from the textbook three-term recurrence; velocity from dT_k/dtau =
+ * k U_{k-1}(tau) and dtau/dt = 2/L. */
+int ko_ephem_eval(const ko_ephem *e, int body, double t, double pos[3], double vel[3])
+{
+    double t_end = e->t_start + e->n_seg * e->seg_len;
+    if (!(t >= e->t_start && t <= t_end)) return KO_OUT_OF_SPAN;
+    int64_t s = (int64_t)floor((t - e->t_start) / e->seg_len);
+    if (s < 0) s = 0;
+    if (s > e->n_seg - 1) s = e->n_seg - 1;
+    double t_mid = e->t_start + ((double)s + 0.5) * e->seg_len;
+    double tau = 2.0 * (t - t_mid) / e->seg_len;
+    double T[64], U[64];
+    int nc = e->n_coef;
+    T[0] = 1.0;
+    T[1] = tau;
+    U[0] = 1.0;
+    U[1] = 2.0 * tau;
+    for (int k = 2; k < nc; k++) {
+        T[k] = 2.0 * tau * T[k - 1] - T[k - 2];
+        U[k] = 2.0 * tau * U[k - 1] - U[k - 2];
+    }
+    for (int c = 0; c < 3; c++) {
+        const double *cf = e->coef + (((size_t)body * e->n_seg + s) * 3 + c) * nc;
+        double sp = 0.0, sv = 0.0;
+        for (int k = 0; k < nc; k++) sp += cf[k] * T[k];
+        for (int k = 1; k < nc; k++) sv += cf[k] * (double)k * U[k - 1];
+        pos[c] = sp;
+        if (vel) vel[c] = sv * 2.0 / e->seg_len;
+    }
+    return KO_OK;
+}
+
+/* ---- force model: Eq. A.1 = sum over masses of Newton + A.3 + A.4 -------- */
+static void pole_vector(double ra, double dec, double p[3])
+{
+    double eq[3] = {cos(dec) * cos(ra), cos(dec) * sin(ra), sin(dec)};
+    double ce = cos(obliquity()), se = sin(obliquity());
+    p[0] = eq[0];                      /* equatorial -> ecliptic */
+    p[1] = ce * eq[1] + se * eq[2];
+    p[2] = -se * eq[1] + ce * eq[2];
+}
+
+int ko_accel(const ko_ephem *e, const ko_force_model *fm, double t, const double x[3],
+             const double v[3], double a[3])
+{
+    const double c = c_au_per_day();
+    a[0] = a[1] = a[2] = 0.0;
+    for (int m = 0; m < e->n_bodies; m++) {
+        if (!((fm->body_mask >> m) & 1u) || e->gm[m] == 0.0) continue;
+        double pm[3], vm[3];
+        int st = ko_ephem_eval(e, m, t, pm, vm);
+        if (st != KO_OK) return st;
+        double mu = e->gm[m];
+        double r[3] = {x[0] - pm[0], x[1] - pm[1], x[2] - pm[2]};
+        double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        double rn = sqrt(r2);
+        double r3 = r2 * rn;
+        /* Newtonian point mass */
+        for (int i = 0; i < 3; i++) a[i] += -mu * r[i] / r3;
+        /* Eq. A.3: test-particle GR correction */
+        if ((fm->gr_mask >> m) & 1u) {
+            double w[3] = {v[0] - vm[0], v[1] - vm[1], v[2] - vm[2]};
+            double w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+            double rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
+            double k = mu / (c * c * r3);
+            for (int i = 0; i < 3; i++)
+                a[i] += k * ((4.0 * mu / rn - w2) * r[i] + 4.0 * rw * w[i]);
+        }
+        /* Eq. A.4: J2 in the body's equatorial frame, rotated back */
+        if ((fm->j2_mask >> m) & 1u) {
+            double p[3], e1[3], e2[3];
+            pole_vector(fm->pole_ra[m], fm->pole_dec[m], p);
+            /* e1 = normalize(z_ecl x p) (any axis in the equator will do) */
+            e1[0] = -p[1];
+            e1[1] = p[0];
+            e1[2] = 0.0;
+            double n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1]);
+            if (n1 < 1e-12) { e1[0] = 1.0; e1[1] = 0.0; n1 = 1.0; }
+            e1[0] /= n1;
+            e1[1] /= n1;
+            e2[0] = p[1] * e1[2] - p[2] * e1[1];
+            e2[1] = p[2] * e1[0] - p[0] * e1[2];
+            e2[2] = p[0] * e1[1] - p[1] * e1[0];
+            double xb = r[0] * e1[0] + r[1] * e1[1] + r[2] * e1[2];
+            double yb = r[0] * e2[0] + r[1] * e2[1] + r[2] * e2[2];
+            double zb = r[0] * p[0] + r[1] * p[1] + r[2] * p[2];
+            double psi = 1.5 * fm->j2[m] * mu * fm->radius[m] * fm->radius[m] / (r2 * r2 * rn);
+            double q = 5.0 * zb * zb / r2;
+            double ab[3] = {-psi * (1.0 - q) * xb, -psi * (1.0 - q) * yb, -psi * (3.0 - q) * zb};
+            for (int i = 0; i < 3; i++) a[i] += ab[0] * e1[i] + ab[1] * e2[i] + ab[2] * p[i];
+        }
+    }
+    return KO_OK;
+}
+
+/* ---- Gauss-Radau spacings: roots of P7(x)+P8(x) on [-1,1], h=(x+1)/2 ----- */
+static double legendre(int n, double x)
+{
+    double p0 = 1.0, p1 = x;
+    if (n == 0) return p0;
+    for (int k = 1; k < n; k++) {
+        double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+static double radau_poly(double x) { return legendre(7, x) + legendre(8, x); }
+
+void ko_radau_nodes(double h[8])
+{
+    /* x = -1 is a root; the other seven are bracketed on a fine grid and
+     * bisected to the last bit. */
+    int found = 0;
+    h[found++] = 0.0;
+    const int N = 40000;
+    double xa = -1.0 + 1e-9, fa = radau_poly(xa);
+    for (int i = 1; i <= N && found < 8; i++) {
+        double xb = -1.0 + 1e-9 + (2.0 - 2e-9) * i / N, fb = radau_poly(xb);
+        if ((fa < 0) != (fb < 0)) {
+            double lo = xa, hi = xb, flo = fa;
+            for (int it = 0; it < 200; it++) {
+                double mid = 0.5 * (lo + hi);
+                if (mid == lo || mid == hi) break;
+                double fm_ = radau_poly(mid);
+                if ((fm_ < 0) == (flo < 0)) { lo = mid; flo = fm_; } else hi = mid;
+            }
+            h[found++] = 0.5 * (0.5 * (lo + hi) + 1.0);
+        }
+        xa = xb;
+        fa = fb;
+    }
+}
+
+/* ---- IAS15 tables computed from the spacings at first use ---------------- */
+typedef struct {
+    double h[8];
+    double C[8][7];   /* C[j][m]: coefficient of s^(m+1) in s*prod_{i=1}^{j-1}(s-h_i), j=1..7 */
+} ko_radau;
+
+static ko_radau g_radau;
+static pthread_once_t g_radau_once = PTHREAD_ONCE_INIT;
+
+static void radau_init(void)
+{
+    ko_radau_nodes(g_radau.h);
+    memset(g_radau.C, 0, sizeof(g_radau.C));
+    for (int j = 1; j <= 7; j++) {
+        /* poly[p] = coefficient of s^p of prod_{i=1}^{j-1}(s - h_i) */
+        double poly[8] = {0};
+        poly[0] = 1.0;
+        int deg = 0;
+        for (int i = 1; i <= j - 1; i++) {
+            double nxt[8] = {0};
+            for (int p = 0; p <= deg; p++) {
+                nxt[p + 1] += poly[p];
+                nxt[p] -= g_radau.h[i] * poly[p];
+            }
+            deg++;
+            memcpy(poly, nxt, sizeof(poly));
+        }
+        /* multiply by s: coefficient of s^(p+1) is poly[p]; b index m = p */
+        for (int p = 0; p <= deg; p++) g_radau.C[j][p] = poly[p];
+    }
+}
+
+static const ko_radau *radau(void)
+{
+    pthread_once(&g_radau_once, radau_init);
+    return &g_radau;
+}
+
+static int finite3(const double *x)
+{
+    return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
+}
+
+/* One attempt of a Gauss-Radau step of size dt from (t, x0, v0) with a0 given.
+ * Fills x1, v1 and the IAS15 error estimate max|b6|/max|a|. */
+static int radau_attempt(const ko_ephem *e, const ko_force_model *fm, double t,
+                         const double x0[3], const double v0[3], const double a0[3],
+                         double dt, double x1[3], double v1[3], double *err,
+                         ko_stats *stats)
+{
+    const ko_radau *R = radau();
+    double g[8][3], b[7][3], F[8][3];
+    memset(g, 0, sizeof(g));
+    memset(b, 0, sizeof(b));                /* R4: predictor removed, b = 0 */
+    for (int i = 0; i < 3; i++) F[0][i] = a0[i];
+    double pc_prev = 0.0;
+    double amax = 0.0;
+    for (int it = 1; it <= fm->max_iter; it++) {
+        double b6_old[3] = {b[6][0], b[6][1], b[6][2]};
+        for (int n = 1; n <= 7; n++) {
+            double s = R->h[n];
+            double xn[3], vn[3];
+            for (int i = 0; i < 3; i++) {
+                /* x(s) = x0 + v0 dt s + dt^2 (a0 s^2/2 + sum_k b_k s^(k+3)/((k+2)(k+3))) */
+                double acc = a0[i] * s * s / 2.0;
+                double vacc = a0[i] * s;
+                double sp = s * s;  /* s^(k+2) */
+                for (int k = 0; k < 7; k++) {
+                    acc += b[k][i] * sp * s / ((k + 2.0) * (k + 3.0));
+                    vacc += b[k][i] * sp / (k + 2.0);
+                    sp *= s;
+                }
+                xn[i] = x0[i] + v0[i] * dt * s + dt * dt * acc;
+                vn[i] = v0[i] + dt * vacc;
+            }
+            int st = ko_accel(e, fm, t + s * dt, xn, vn, F[n]);
+            if (stats) stats->force_evals++;
+            if (st != KO_OK) return st;
+            /* Newton divided difference g_n from F_0..F_n and g_1..g_{n-1} */
+            for (int i = 0; i < 3; i++) {
+                double d = (F[n][i] - F[0][i]) / (R->h[n] - R->h[0]);
+                for (int k = 1; k < n; k++) d = (d - g[k][i]) / (R->h[n] - R->h[k]);
+                g[n][i] = d;
+            }
+            /* power-basis coefficients b = C g */
+            for (int m = 0; m < 7; m++)
+                for (int i = 0; i < 3; i++) {
+                    double sum = 0.0;
+                    for (int j = m + 1; j <= 7; j++) sum += R->C[j][m] * g[j][i];
+                    b[m][i] = sum;
+                }
+        }
+        if (stats) stats->iterations++;
+        double db = 0.0;
+        amax = 0.0;
+        for (int i = 0; i < 3; i++) {
+            double d = fabs(b[6][i] - b6_old[i]);
+            if (d > db) db = d;
+            if (fabs(F[7][i]) > amax) amax = fabs(F[7][i]);
+        }
+        double pc = db / amax;
+        if (!isfinite(pc)) return KO_NONFINITE;
+        if (pc < fm->eps_pc) break;
+        if (it >= 3 && pc >= pc_prev) break;
+        pc_prev = pc;
+    }
+    double bmax = 0.0;
+    for (int i = 0; i < 3; i++)
+        if (fabs(b[6][i]) > bmax) bmax = fabs(b[6][i]);
+    *err = bmax / amax;
+    for (int i = 0; i < 3; i++) {
+        double acc = a0[i] / 2.0, vacc = a0[i];
+        for (int k = 0; k < 7; k++) {
+            acc += b[k][i] / ((k + 2.0) * (k + 3.0));
+            vacc += b[k][i] / (k + 2.0);
+        }
+        x1[i] = x0[i] + v0[i] * dt + dt * dt * acc;
+        v1[i] = v0[i] + dt * vacc;
+    }
+    if (!finite3(x1) || !finite3(v1)) return KO_NONFINITE;
+    return KO_OK;
+}
+
+/* Integrate (st, *t) to t_target exactly; *dt is the proposed step (carried). */
+int ko_propagate(const ko_ephem *e, const ko_force_model *fm, double st[6], double *t,
+                 double t_target, double *dt, ko_stats *stats)
+{
+    int64_t attempts = 0;
+    double dir = (t_target >= *t) ? 1.0 : -1.0;
+    if (*dt == 0.0 || (*dt > 0) != (dir > 0)) *dt = dir * fabs(*dt == 0.0 ? fm->dt_init : *dt);
+    while (*t != t_target) {
+        double x0[3] = {st[0], st[1], st[2]}, v0[3] = {st[3], st[4], st[5]}, a0[3];
+        int s0 = ko_accel(e, fm, *t, x0, v0, a0);
+        if (stats) stats->force_evals++;
+        if (s0 != KO_OK) return s0;
+        for (;;) {
+            if (++attempts > fm->max_steps) return KO_STEP_CAP;
+            double remaining = t_target - *t;
+            int clamped = fabs(*dt) >= fabs(remaining);
+            /* the step is the exact difference of the two representable epochs
+             * it joins, so that the sum of the steps equals the elapsed time */
+            double t_new = clamped ? t_target : *t + *dt;
+            double h = t_new - *t;
+            double x1[3], v1[3], err;
+            int s1 = radau_attempt(e, fm, *t, x0, v0, a0, h, x1, v1, &err, stats);
+            if (s1 != KO_OK) return s1;
+            /* IAS15 step-size control */
+            double dt_new;
+            if (isnormal(err))
+                dt_new = pow(fm->eps / err, 1.0 / 7.0) * h;
+            else
+                dt_new = h / fm->safety;
+            if (fabs(dt_new / h) < fm->safety) {     /* reject and retry */
+                *dt = dt_new;
+                if (stats) stats->rejected++;
+                continue;
+            }
+            if (fabs(dt_new / h) > 1.0 / fm->safety) dt_new = h / fm->safety;
+            *dt = dt_new;
+            for (int i = 0; i < 3; i++) { st[i] = x1[i]; st[3 + i] = v1[i]; }
+            *t = t_new;
+            if (stats) stats->steps++;
+            break;
+        }
+    }
+    return KO_OK;
+}
+
+/* Chain semantics: stops >= epoch are visited forward in ascending order from
+ * the epoch state, stops < epoch backward in descending order; the proposed
+ * step is carried along each chain, which starts from dt_init. */
+int ko_propagate_stops(const ko_ephem *e, const ko_force_model *fm, const double st0[6],
+                       double epoch, const double *stops, int64_t n_stops, double *out,
+                       ko_stats *stats)
+{
+    int status = KO_OK;
+    int64_t split = 0;
+    while (split < n_stops && stops[split] < epoch) split++;
+    for (int pass = 0; pass < 2; pass++) {
+        double st[6], t = epoch, dt = 0.0;
+        memcpy(st, st0, sizeof(st));
+        int failed = 0;
+        if (pass == 0) {
+            for (int64_t k = split; k < n_stops; k++) {
+                if (!failed) {
+                    int s = ko_propagate(e, fm, st, &t, stops[k], &dt, stats);
+                    if (s != KO_OK) { failed = 1; status = s; }
+                }
+                for (int i = 0; i < 6; i++) out[k * 6 + i] = failed ? NAN : st[i];
+            }
+        } else {
+            for (int64_t k = split - 1; k >= 0; k--) {
+                if (!failed) {
+                    int s = ko_propagate(e, fm, st, &t, stops[k], &dt, stats);
+                    if (s != KO_OK) { failed = 1; status = s; }
+                }
+                for (int i = 0; i < 6; i++) out[k * 6 + i] = failed ? NAN : st[i];
+            }
+        }
+    }
+    return status;
+}
+
+/* ---- threads over bodies ------------------------------------------------- */
+typedef struct {
+    const ko_ephem *e;
+    const ko_force_model *fm;
+    double *states, *epochs;
+    int64_t n;
+    double t_target;
+    int32_t *status;
+    int tid, nt;
+    ko_stats stats;
+} prop_job;
+
+static void *prop_worker(void *arg)
+{
+    prop_job *j = (prop_job *)arg;
+    for (int64_t i = j->tid; i < j->n; i += j->nt) {
+        double st[6], t = j->epochs[i], dt = 0.0;
+        for (int c = 0; c < 6; c++) st[c] = j->states[c * j->n + i];
+        int s = ko_propagate(j->e, j->fm, st, &t, j->t_target, &dt, &j->stats);
+        if (j->status) j->status[i] = s;
+        if (s == KO_OK) {
+            for (int c = 0; c < 6; c++) j->states[c * j->n + i] = st[c];
+            j->epochs[i] = t;
+        }
+    }
+    return NULL;
+}
+
+int ko_propagate_many(const ko_ephem *e, const ko_force_model *fm, double *states,
+                      double *epochs, int64_t n, double t_target, int32_t *status,
+                      int n_threads, ko_stats *stats)
+{
+    if (n_threads < 1) n_threads = 1;
+    prop_job *jobs = (prop_job *)calloc(n_threads, sizeof(prop_job));
+    pthread_t *th = (pthread_t *)calloc(n_threads, sizeof(pthread_t));
+    for (int k = 0; k < n_threads; k++) {
+        prop_job j = {e, fm, states, epochs, n, t_target, status, k, n_threads, {0, 0, 0, 0}};
+        jobs[k] = j;
+        pthread_create(&th[k], NULL, prop_worker, &jobs[k]);
+    }
+    for (int k = 0; k < n_threads; k++) {
+        pthread_join(th[k], NULL);
+        if (stats) {
+            stats->steps += jobs[k].stats.steps;
+            stats->rejected += jobs[k].stats.rejected;
+            stats->force_evals += jobs[k].stats.force_evals;
+            stats->iterations += jobs[k].stats.iterations;
+        }
+    }
+    free(jobs);
+    free(th);
+    return 0;
+}
+
+/* ---- universal-variable two-body propagation (Sec. 2, R7) ---------------- */
+/* Stumpff functions C(z) = c2, S(z) = c3: their power series for |z| < 1,
+ * the closed trigonometric / hyperbolic forms otherwise. */
+void ko_stumpff(double z, double *c2, double *c3)
+{
+    if (fabs(z) < 1.0) {
+        double t2 = 0.5, t3 = 1.0 / 6.0, s2 = 0.0, s3 = 0.0;
+        for (int k = 0; k < 40; k++) {
+            s2 += t2;
+            s3 += t3;
+            t2 *= -z / ((2.0 * k + 3.0) * (2.0 * k + 4.0));
+            t3 *= -z / ((2.0 * k + 4.0) * (2.0 * k + 5.0));
+            if (fabs(t2) < 1e-19 && fabs(t3) < 1e-19) break;
+        }
+        *c2 = s2;
+        *c3 = s3;
+    } else if (z > 0) {
+        double sz = sqrt(z);
+        *c2 = (1.0 - cos(sz)) / z;
+        *c3 = (sz - sin(sz)) / (sz * sz * sz);
+    } else {
+        double sz = sqrt(-z);
+        *c2 = (cosh(sz) - 1.0) / (-z);
+        *c3 = (sinh(sz) - sz) / (sz * sz * sz);
+    }
+}
+
+int ko_kepler(double mu, const double r0v[3], const double v0v[3], double dt, double r[3],
+              double v[3])
+{
+    if (dt == 0.0) {
+        memcpy(r, r0v, 3 * sizeof(double));
+        memcpy(v, v0v, 3 * sizeof(double));
+        return KO_OK;
+    }
+    double smu = sqrt(mu);
+    double r0 = sqrt(r0v[0] * r0v[0] + r0v[1] * r0v[1] + r0v[2] * r0v[2]);
+    double v02 = v0v[0] * v0v[0] + v0v[1] * v0v[1] + v0v[2] * v0v[2];
+    double rv = r0v[0] * v0v[0] + r0v[1] * v0v[1] + r0v[2] * v0v[2];
+    double alpha = 2.0 / r0 - v02 / mu;
+    double A = rv / smu;              /* r0 vr0 / sqrt(mu) */
+    double B = 1.0 - alpha * r0;
+    /* F(chi) = A chi^2 C + B chi^3 S + r0 chi - sqrt(mu) dt, F' = r > 0 */
+    double target = smu * dt;
+    double lo, hi;
+    double chi = smu * dt / r0;
+    /* bracket: F is increasing in chi and F(0) = -target */
+    if (dt > 0) { lo = 0.0; hi = chi; } else { hi = 0.0; lo = chi; }
+    for (int k = 0; k < 200; k++) {
+        double x = (dt > 0) ? hi : lo;
+        double z = alpha * x * x, c2, c3;
+        ko_stumpff(z, &c2, &c3);
+        double F = A * x * x * c2 + B * x * x * x * c3 + r0 * x - target;
+        if ((dt > 0 && F >= 0) || (dt < 0 && F <= 0)) break;
+        if (dt > 0) { lo = hi; hi *= 2.0; } else { hi = lo; lo *= 2.0; }
+        if (k == 199) return KO_KEPLER_FAIL;
+    }
+    int ok = 0;
+    for (int it = 0; it < 200; it++) {
+        double z = alpha * chi * chi, c2, c3;
+        ko_stumpff(z, &c2, &c3);
+        double F = A * chi * chi * c2 + B * chi * chi * chi * c3 + r0 * chi - target;
+        double dF = A * chi * (1.0 - z * c3) + B * chi * chi * c2 + r0;
+        if (F < 0) lo = chi; else hi = chi;
+        double nxt = chi - F / dF;
+        if (!(nxt > lo && nxt < hi)) nxt = 0.5 * (lo + hi);   /* bisection fallback */
+        double d = fabs(nxt - chi);
+        chi = nxt;
+        if (d <= 1e-16 * fabs(chi) || lo == hi) { ok = 1; break; }
+    }
+    if (!ok) return KO_KEPLER_FAIL;
+    double z = alpha * chi * chi, c2, c3;
+    ko_stumpff(z, &c2, &c3);
+    double f = 1.0 - chi * chi / r0 * c2;
+    double g = dt - chi * chi * chi * c3 / smu;
+    for (int i = 0; i < 3; i++) r[i] = f * r0v[i] + g * v0v[i];
+    double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double fdot = smu / (rn * r0) * (z * c3 - 1.0) * chi;
+    double gdot = 1.0 - chi * chi / rn * c2;
+    for (int i = 0; i < 3; i++) v[i] = fdot * r0v[i] + gdot * v0v[i];
+    return KO_OK;
+}
+
+/* Two-body position at t_ref + dt from the heliocentric batch state (R7). */
+static int twobody_pos(const ko_ephem *e, const double helio[6], double t_ref, double dt,
+                       double pos[3])
+{
+    double sun[3], r[3], v[3];
+    int s = ko_ephem_eval(e, 0, t_ref + dt, sun, NULL);
+    if (s != KO_OK) return s;
+    s = ko_kepler(e->gm[0], helio, helio + 3, dt, r, v);
+    if (s != KO_OK) return s;
+    for (int i = 0; i < 3; i++) pos[i] = sun[i] + r[i];
+    return KO_OK;
+}
+
+static double dist3(const double a[3], const double b[3])
+{
+    double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+    return sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+/* Light-delay corrected apparent vector (Sec. 2, R8). */
+int ko_apparent(const ko_ephem *e, const double st_ref[6], double t_ref, double t_obs,
+                const double obs[3], double u[3], double *tau_out)
+{
+    const double c = c_au_per_day();
+    double sp[3], sv[3], helio[6], pos[3];
+    int s = ko_ephem_eval(e, 0, t_ref, sp, sv);
+    if (s != KO_OK) return s;
+    for (int i = 0; i < 3; i++) {
+        helio[i] = st_ref[i] - sp[i];
+        helio[3 + i] = st_ref[3 + i] - sv[i];
+    }
+    /* intervals are formed before absolute epochs (R10) */
+    double dt_obs = t_obs - t_ref;
+    s = twobody_pos(e, helio, t_ref, dt_obs, pos);
+    if (s != KO_OK) return s;
+    double tau = dist3(pos, obs) / c;
+    for (int it = 0; it < 3; it++) {
+        s = twobody_pos(e, helio, t_ref, dt_obs - tau, pos);
+        if (s != KO_OK) return s;
+        tau = dist3(pos, obs) / c;
+    }
+    s = twobody_pos(e, helio, t_ref, dt_obs - tau, pos);
+    if (s != KO_OK) return s;
+    for (int i = 0; i < 3; i++) u[i] = pos[i] - obs[i];
+    if (tau_out) *tau_out = tau;
+    return KO_OK;
+}
+
+/* RA/Dec of an ecliptic vector: rotate by the obliquity to equatorial J2000. */
+void ko_radec(const double u[3], double *ra, double *dec)
+{
+    double ce = cos(obliquity()), se = sin(obliquity());
+    double x = u[0];
+    double y = ce * u[1] - se * u[2];
+    double z = se * u[1] + ce * u[2];
+    double a = atan2(y, x);
+    if (a < 0) a += 2.0 * M_PI;
+    *ra = a;
+    *dec = atan2(z, sqrt(x * x + y * y));
+}
+
+/* Sec. 3.1: inside iff every inward normal has a positive dot product (R9). */
+int ko_in_polygon(const ko_frame *f, const double u[3], double *margin)
+{
+    int inside = 1;
+    double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double mg = INFINITY;
+    for (int k = 0; k < f->n_edges; k++) {
+        const double *nv = f->normals[k];
+        double d = nv[0] * u[0] + nv[1] * u[1] + nv[2] * u[2];
+        if (!(d > 0.0)) inside = 0;
+        double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+        double ang = asin(fmax(-1.0, fmin(1.0, d / (nn * un))));
+        if (ang < mg) mg = ang;
+    }
+    if (margin) *margin = mg;
+    return inside;
+}
+
+/* ---- batching (Sec. 2, R6) ------------------------------------------------ */
+int64_t ko_make_batches(const double *ep, int64_t n, double batch_span, double twobody_max,
+                        int64_t *batch_start, double *t_ref)
+{
+    double span = batch_span;
+    if (2.0 * twobody_max < span) span = 2.0 * twobody_max;
+    int64_t nb = 0, i = 0;
+    while (i < n) {
+        int64_t j = i;
+        while (j + 1 < n && (ep[j + 1] == ep[i] || ep[j + 1] - ep[i] < span)) j++;
+        if (batch_start) batch_start[nb] = i;
+        if (t_ref) t_ref[nb] = 0.5 * (ep[i] + ep[j]);
+        nb++;
+        i = j + 1;
+    }
+    return nb;
+}
+
+/* ---- survey driver (Sec. 2) ------------------------------------------------ */
+typedef struct {
+    ko_hit *h;
+    int64_t n, cap;
+} hitbuf;
+
+static void hit_push(hitbuf *b, const ko_hit *x)
+{
+    if (b->n == b->cap) {
+        b->cap = b->cap ? 2 * b->cap : 256;
+        b->h = (ko_hit *)realloc(b->h, b->cap * sizeof(ko_hit));
+    }
+    b->h[b->n++] = *x;
+}
+
+typedef struct {
+    const ko_ephem *e;
+    const ko_force_model *fm;
+    const double *states, *epochs;
+    int64_t n;
+    const ko_frame *frames;
+    const int64_t *order;        /* frames sorted by epoch */
+    const double *observers;
+    const ko_survey_opts *opt;
+    const int32_t *subset;
+    int64_t n_subset;
+    int64_t nb;
+    const int64_t *bstart;
+    const double *tref;
+    int64_t n_frames;
+    int32_t *status;
+    int tid, nt;
+    hitbuf out;
+    ko_stats stats;
+    double (*centre)[4];         /* frame centre (unit) + circumradius */
+} fov_job;
+
+static void *fov_worker(void *arg)
+{
+    fov_job *j = (fov_job *)arg;
+    const double c = c_au_per_day();
+    double *st_stops = (double *)malloc(sizeof(double) * 6 * (j->nb ? j->nb : 1));
+    for (int64_t q = j->tid; q < j->n_subset; q += j->nt) {
+        int32_t bi = j->subset ? j->subset[q] : (int32_t)q;
+        double st0[6];
+        for (int k = 0; k < 6; k++) st0[k] = j->states[(int64_t)k * j->n + bi];
+        int s = ko_propagate_stops(j->e, j->fm, st0, j->epochs[bi], j->tref, j->nb, st_stops,
+                                   &j->stats);
+        if (j->status) j->status[bi] = s;
+        for (int64_t k = 0; k < j->nb; k++) {
+            const double *sk = st_stops + 6 * k;
+            if (!isfinite(sk[0])) continue;
+            int64_t f0 = j->bstart[k], f1 = (k + 1 < j->nb) ? j->bstart[k + 1] : j->n_frames;
+            for (int64_t fi = f0; fi < f1; fi++) {
+                int64_t fid = j->order[fi];
+                const ko_frame *fr = &j->frames[fid];
+                const double *o = j->observers + 3 * fr->observer_idx;
+                if (j->opt->prefilter_deg > 0) {
+                    /* plain conservative prefilter: angle from the observer to
+                     * the batch-epoch position vs frame centre, padded by a
+                     * bound on the motion over |t - t_ref| + light time. */
+                    double d[3] = {sk[0] - o[0], sk[1] - o[1], sk[2] - o[2]};
+                    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    double vn = sqrt(sk[3] * sk[3] + sk[4] * sk[4] + sk[5] * sk[5]);
+                    double T = fabs(fr->epoch - j->tref[k]) + (dn + 1.0) / c;
+                    double sm = 2.0 * vn * T + 0.01 * T * T + 1e-4;
+                    if (sm < 0.5 * dn) {
+                        const double *cc = j->centre[fid];
+                        double cosang = (d[0] * cc[0] + d[1] * cc[1] + d[2] * cc[2]) / dn;
+                        double lim = cc[3] + deg2rad(j->opt->prefilter_deg) + asin(sm / dn);
+                        if (lim < M_PI && cosang < cos(lim)) continue;
+                    }
+                }
+                double u[3], tau, margin;
+                int sa = ko_apparent(j->e, sk, j->tref[k], fr->epoch, o, u, &tau);
+                if (sa != KO_OK) {
+                    if (j->status && j->status[bi] == KO_OK) j->status[bi] = sa;
+                    continue;
+                }
+                if (ko_in_polygon(fr, u, &margin)) {
+                    ko_hit h;
+                    h.frame = fid;
+                    h.body = bi;
+                    h.status = 0;
+                    ko_radec(u, &h.ra, &h.dec);
+                    h.margin = margin;
+                    h.tau = tau;
+                    hit_push(&j->out, &h);
+                }
+            }
+        }
+    }
+    free(st_stops);
+    return NULL;
+}
+
+static const double *g_sort_ep;
+static int cmp_epoch(const void *a, const void *b)
+{
+    int64_t i = *(const int64_t *)a, k = *(const int64_t *)b;
+    double x = g_sort_ep[i], y = g_sort_ep[k];
+    if (x < y) return -1;
+    if (x > y) return 1;
+    return (i < k) ? -1 : (i > k);
+}
+
+static int cmp_hit(const void *a, const void *b)
+{
+    const ko_hit *x = (const ko_hit *)a, *y = (const ko_hit *)b;
+    if (x->frame != y->frame) return (x->frame < y->frame) ? -1 : 1;
+    return (x->body < y->body) ? -1 : (x->body > y->body);
+}
+
+int ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *states,
+                 const double *epochs, int64_t n, const ko_frame *frames, int64_t n_frames,
+                 const double *observers, int64_t n_obs, const ko_survey_opts *opt,
+                 const int32_t *body_subset, int64_t n_subset, ko_hit *hits, int64_t capacity,
+                 int64_t *n_hits, int32_t *status, int n_threads, ko_stats *stats)
+{
+    (void)n_obs;
+    if (n_threads < 1) n_threads = 1;
+    /* sort FoVs by epoch (Sec. 2: "grouping the FoVs into batches based on time") */
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (n_frames ? n_frames : 1));
+    double *ep_all = (double *)malloc(sizeof(double) * (n_frames ? n_frames : 1));
+    for (int64_t i = 0; i < n_frames; i++) { order[i] = i; ep_all[i] = frames[i].epoch; }
+    g_sort_ep = ep_all;
+    qsort(order, n_frames, sizeof(int64_t), cmp_epoch);
+    double *ep = (double *)malloc(sizeof(double) * (n_frames ? n_frames : 1));
+    for (int64_t i = 0; i < n_frames; i++) ep[i] = ep_all[order[i]];
+    int64_t *bstart = (int64_t *)malloc(sizeof(int64_t) * (n_frames ? n_frames : 1));
+    double *tref = (double *)malloc(sizeof(double) * (n_frames ? n_frames : 1));
+    int64_t nb = ko_make_batches(ep, n_frames, opt->batch_span, opt->twobody_max, bstart, tref);
+    /* frame centres for the optional prefilter: normalized sum of vertex
+     * directions v_k = n_k x n_{k+1}, radius = max vertex angle */
+    double (*centre)[4] = (double (*)[4])malloc(sizeof(double) * 4 * (n_frames ? n_frames : 1));
+    for (int64_t i = 0; i < n_frames; i++) {
+        const ko_frame *f = &frames[i];
+        double vs[KO_MAX_EDGES][3], cs[3] = {0, 0, 0};
+        int ne = f->n_edges;
+        for (int k = 0; k < ne; k++) {
+            const double *a = f->normals[k], *b = f->normals[(k + 1) % ne];
+            double x[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2],
+                           a[0] * b[1] - a[1] * b[0]};
+            double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            double sum_n[3] = {0, 0, 0};
+            for (int q = 0; q < ne; q++)
+                for (int c = 0; c < 3; c++) sum_n[c] += f->normals[q][c];
+            if (x[0] * sum_n[0] + x[1] * sum_n[1] + x[2] * sum_n[2] < 0) xn = -xn;
+            for (int c = 0; c < 3; c++) { vs[k][c] = x[c] / xn; cs[c] += vs[k][c]; }
+        }
+        double cn = sqrt(cs[0] * cs[0] + cs[1] * cs[1] + cs[2] * cs[2]);
+        double rad = 0.0;
+        for (int c = 0; c < 3; c++) centre[i][c] = cs[c] / cn;
+        for (int k = 0; k < ne; k++) {
+            double dd = vs[k][0] * centre[i][0] + vs[k][1] * centre[i][1] + vs[k][2] * centre[i][2];
+            double ang = acos(fmax(-1.0, fmin(1.0, dd)));
+            if (ang > rad) rad = ang;
+        }
+        centre[i][3] = rad;
+    }
+    int64_t nsub = body_subset ? n_subset : n;
+    fov_job *jobs = (fov_job *)calloc(n_threads, sizeof(fov_job));
+    pthread_t *th = (pthread_t *)calloc(n_threads, sizeof(pthread_t));
+    for (int k = 0; k < n_threads; k++) {
+        fov_job *j = &jobs[k];
+        j->e = e; j->fm = fm; j->states = states; j->epochs = epochs; j->n = n;
+        j->frames = frames; j->order = order; j->observers = observers; j->opt = opt;
+        j->subset = body_subset; j->n_subset = nsub; j->nb = nb; j->bstart = bstart;
+        j->tref = tref; j->n_frames = n_frames; j->status = status; j->tid = k;
+        j->nt = n_threads; j->centre = centre;
+        pthread_create(&th[k], NULL, fov_worker, j);
+    }
+    int64_t total = 0;
+    for (int k = 0; k < n_threads; k++) {
+        pthread_join(th[k], NULL);
+        total += jobs[k].out.n;
+        if (stats) {
+            stats->steps += jobs[k].stats.steps;
+            stats->rejected += jobs[k].stats.rejected;
+            stats->force_evals += jobs[k].stats.force_evals;
+            stats->iterations += jobs[k].stats.iterations;
+        }
+    }
+    ko_hit *all = (ko_hit *)malloc(sizeof(ko_hit) * (total ? total : 1));
+    int64_t pos = 0;
+    for (int k = 0; k < n_threads; k++) {
+        memcpy(all + pos, jobs[k].out.h, jobs[k].out.n * sizeof(ko_hit));
+        pos += jobs[k].out.n;
+        free(jobs[k].out.h);
+    }
+    qsort(all, total, sizeof(ko_hit), cmp_hit);
+    *n_hits = total;
+    int rc = 0;
+    if (total > capacity) rc = -3;
+    else if (hits) memcpy(hits, all, total * sizeof(ko_hit));
+    free(all); free(jobs); free(th); free(order); free(ep_all); free(ep); free(bstart);
+    free(tref); free(centre);
+    return rc;
+}

@@ -1,0 +1,133 @@
+/*
+ * kete_oracle.h -- plain, slow, FP64 CPU oracle of the survey-prediction path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code with
+ * the CUDA path; the two meet only on the seeded input files.
+ *
+ * What it computes (each function cites the passage it follows):
+ *   - planetary ephemeris lookup: Chebyshev series per segment (App. A, Sec. 3.2)
+ *   - acceleration: Newton + GR (Eq. A.3) + J2 (Eq. A.4), summed as Eq. A.1
+ *   - Gauss-Radau 15th-order step with IAS15 corrector convergence and step
+ *     control, predictor removed (Sec. 3.2, App. A.6)
+ *   - universal-variable two-body propagation + light-delay iteration (Sec. 2)
+ *   - spherical-polygon FoV test by inward normals (Sec. 3.1)
+ *   - time batching of FoVs into <= 3-day groups with n-body to the batch
+ *     midpoint (Sec. 2)
+ *   - RA/Dec in equatorial J2000 (App. A.1)
+ *
+ * Parity pins: see tests/test_oracle_*.py (closed-form Kepler, conservation
+ * laws, time reversal, GR perihelion advance, J2 nodal regression, light-time
+ * closed forms, gnomonic FoV test, brute-force FoV, batching rules).
+ * The full force model with planets on is "parity unpinned" by the paper:
+ * no worked example exists; it is held only by the invariants above.
+ */
+#ifndef KETE_ORACLE_H
+#define KETE_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KO_MAX_BODIES 16
+#define KO_MAX_EDGES 4
+
+/* status codes (per body) */
+#define KO_OK 0
+#define KO_STEP_CAP 1
+#define KO_OUT_OF_SPAN 2
+#define KO_NONFINITE 3
+#define KO_KEPLER_FAIL 4
+
+typedef struct {
+    int n_bodies, n_coef, n_seg;
+    double t_start, seg_len;
+    double gm[KO_MAX_BODIES];
+    double *coef;           /* [body][seg][3][coef] */
+} ko_ephem;
+
+typedef struct {
+    uint32_t body_mask;     /* bodies whose gravity acts (bit b = table body b) */
+    uint32_t gr_mask;       /* bodies with the GR term of Eq. A.3 */
+    uint32_t j2_mask;       /* bodies with the J2 term of Eq. A.4 */
+    int32_t max_iter;       /* corrector iteration cap */
+    double j2[KO_MAX_BODIES];
+    double radius[KO_MAX_BODIES];    /* AU */
+    double pole_ra[KO_MAX_BODIES];   /* radians, equatorial J2000 */
+    double pole_dec[KO_MAX_BODIES];
+    double eps;             /* IAS15 step-size control parameter */
+    double eps_pc;          /* corrector convergence threshold */
+    double safety;          /* IAS15 safety factor */
+    double dt_init;         /* first step of every propagation chain, days */
+    int64_t max_steps;      /* step attempts per leg */
+} ko_force_model;
+
+typedef struct {
+    double epoch;
+    int64_t observer_idx;
+    int64_t exposure_id;
+    int32_t n_edges;
+    int32_t reserved;
+    double normals[KO_MAX_EDGES][3];
+} ko_frame;
+
+typedef struct {
+    int64_t frame;
+    int32_t body;
+    int32_t status;
+    double ra, dec;          /* radians, equatorial J2000 */
+    double margin;           /* min over edges of asin(n.u/|n||u|), radians */
+    double tau;              /* light time, days */
+} ko_hit;
+
+typedef struct {
+    double batch_span;       /* <= 3 days by default (Sec. 2) */
+    double twobody_max;      /* maximum two-body interval (0 = pure n-body) */
+    double prefilter_deg;    /* 0: brute force over all frames of a batch */
+} ko_survey_opts;
+
+typedef struct {
+    int64_t steps, rejected, force_evals, iterations;
+} ko_stats;
+
+void ko_force_model_default(ko_force_model *fm);
+int  ko_ephem_load(ko_ephem *e, const void *buf, size_t n);
+void ko_ephem_free(ko_ephem *e);
+int  ko_ephem_eval(const ko_ephem *e, int body, double t, double pos[3], double vel[3]);
+
+void ko_radau_nodes(double h[8]);
+int  ko_accel(const ko_ephem *e, const ko_force_model *fm, double t,
+              const double x[3], const double v[3], double a[3]);
+int  ko_propagate(const ko_ephem *e, const ko_force_model *fm, double st[6], double *t,
+                  double t_target, double *dt, ko_stats *stats);
+int  ko_propagate_stops(const ko_ephem *e, const ko_force_model *fm, const double st0[6],
+                        double epoch, const double *stops, int64_t n_stops,
+                        double *out /* [n_stops][6] */, ko_stats *stats);
+int  ko_propagate_many(const ko_ephem *e, const ko_force_model *fm, double *states /*6xN SoA*/,
+                       double *epochs, int64_t n, double t_target, int32_t *status,
+                       int n_threads, ko_stats *stats);
+
+void ko_stumpff(double z, double *c2, double *c3);
+int  ko_kepler(double mu, const double r0[3], const double v0[3], double dt,
+               double r[3], double v[3]);
+int  ko_apparent(const ko_ephem *e, const double st_ref[6], double t_ref, double t_obs,
+                 const double obs[3], double u[3], double *tau);
+void ko_radec(const double u[3], double *ra, double *dec);
+int  ko_in_polygon(const ko_frame *f, const double u[3], double *margin);
+
+int64_t ko_make_batches(const double *epochs_sorted, int64_t n, double batch_span,
+                        double twobody_max, int64_t *batch_start, double *t_ref);
+int  ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *states,
+                  const double *epochs, int64_t n, const ko_frame *frames, int64_t n_frames,
+                  const double *observers, int64_t n_obs, const ko_survey_opts *opt,
+                  const int32_t *body_subset, int64_t n_subset, ko_hit *hits,
+                  int64_t capacity, int64_t *n_hits, int32_t *status, int n_threads,
+                  ko_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

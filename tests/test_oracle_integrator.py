@@ -1,0 +1,233 @@
+"""Pins of the oracle's ephemeris lookup, force model and Gauss-Radau/IAS15
+integrator (Sec. 3.2, App. A, App. A.2-A.3, App. A.6).
+
+Independent references: numpy's Chebyshev routines, the published Gauss-Radau
+spacings, the closed-form Kepler orbit (elliptic anomaly), conservation laws,
+time reversal, the GR perihelion advance and the J2 nodal regression rate."""
+import math
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import chebyshev as npcheb
+
+import oracle as O
+from paper_2509_04666_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+C_AU_D = 299792.458 * 86400.0 / 149597870.7
+
+
+def _golden_kv(name):
+    out = {}
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def test_radau_spacings_match_published():
+    pub = [float(l) for l in open(os.path.join(GOLD, "radau_spacings.txt"))
+           if l.strip() and not l.startswith("#")]
+    h = O.radau_nodes()
+    assert h[0] == 0.0
+    np.testing.assert_allclose(h[1:], pub, rtol=0, atol=2e-16)
+    # and they are the roots of P7 + P8 by numpy's Legendre routines
+    roots = np.sort(np.polynomial.legendre.legroots([0] * 7 + [1, 1]))
+    np.testing.assert_allclose((roots + 1) / 2, h, atol=1e-14)
+
+
+def test_chebyshev_eval_against_numpy(mb1k):
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    e = mb1k.ephem
+    rng = np.random.default_rng(0)
+    for t in rng.uniform(e.t_start, e.t_end, 200):
+        s = min(int((t - e.t_start) // e.seg_len), e.n_seg - 1)
+        tau = 2 * (t - (e.t_start + (s + 0.5) * e.seg_len)) / e.seg_len
+        for b in range(9):
+            rc, p, v = orc.ephem(b, t)
+            assert rc == 0
+            ref = [npcheb.chebval(tau, e.coef[b, s, c]) for c in range(3)]
+            dref = [npcheb.chebval(tau, npcheb.chebder(e.coef[b, s, c])) * 2 / e.seg_len
+                    for c in range(3)]
+            assert np.abs(p - ref).max() < 1e-15 * max(1, np.abs(ref).max()) * 4
+            assert np.abs(v - dref).max() < 1e-15 * max(1e-3, np.abs(dref).max()) * 40
+    assert orc.ephem(0, e.t_start - 1)[0] == O.OUT_OF_SPAN
+    assert orc.ephem(0, e.t_end + 1e-6)[0] == O.OUT_OF_SPAN
+
+
+def test_table_reproduces_planet_integration(mb1k):
+    """The fitted table tracks the generator's own planet integration."""
+    ps = W.make_planets(mb1k.seed)
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    ts = np.linspace(mb1k.ephem.t_start + 0.1, mb1k.ephem.t_end - 0.1, 37)
+    ref = W.integrate_planets(ps, ts)
+    for i, t in enumerate(ts):
+        for b in range(9):
+            _, p, v = orc.ephem(b, t)
+            assert np.abs(p - ref[i, b, :3]).max() < 1e-10
+            assert np.abs(v - ref[i, b, 3:]).max() < 1e-10
+
+
+def _sun_only_oracle(t_lo=W.T0 - 40, t_hi=W.T0 + 800, **kw):
+    orc = O.Oracle(W.static_sun_table(t_lo, t_hi, **kw).to_bytes())
+    fm = orc.force_model(body_mask=1, gr_mask=0, j2_mask=0)
+    return orc, fm
+
+
+def _kepler_closed(a, e, inc, node, peri, M0, dt):
+    n = math.sqrt(W.GM_SUN / a ** 3)
+    r, v = W.elements_to_state(np.array([a]), np.array([e]), inc, node, peri, M0 + n * dt, W.GM_SUN)
+    return np.concatenate([r[:, 0], v[:, 0]])
+
+
+@pytest.mark.parametrize("a,e,tol", [(2.7, 0.12, 1e-13), (1.1, 0.55, 1e-13),
+                                     (2.2, 0.29, 1e-13), (40.0, 0.99, 1e-12)])
+def test_integrator_reproduces_kepler_orbit(a, e, tol):
+    orc, fm = _sun_only_oracle()
+    inc, node, peri = 0.3, 1.2, 2.1
+    M0 = 6.2 if e > 0.9 else 0.4      # the e=0.99 orbit passes perihelion
+    x0 = _kepler_closed(a, e, inc, node, peri, M0, 0.0)
+    rc, st, t, dt, stats = orc.propagate(fm, x0, W.T0, W.T0 + 365.0)
+    assert rc == 0 and t == W.T0 + 365.0
+    ref = _kepler_closed(a, e, inc, node, peri, M0, 365.0)
+    assert np.abs(st[:3] - ref[:3]).max() < tol
+
+
+def test_integrator_conserves_energy_and_angular_momentum():
+    orc, fm = _sun_only_oracle()
+    mu = W.GM_SUN
+    for a, e in [(2.5, 0.15), (1.3, 0.7)]:
+        x0 = _kepler_closed(a, e, 0.5, 0.3, 1.0, 0.2, 0.0)
+        E0 = 0.5 * x0[3:] @ x0[3:] - mu / np.linalg.norm(x0[:3])
+        L0 = np.cross(x0[:3], x0[3:])
+        rc, st, *_ = orc.propagate(fm, x0, W.T0, W.T0 + 730.0)
+        assert rc == 0
+        E1 = 0.5 * st[3:] @ st[3:] - mu / np.linalg.norm(st[:3])
+        L1 = np.cross(st[:3], st[3:])
+        assert abs(E1 - E0) < 1e-13 * abs(E0)
+        assert np.linalg.norm(L1 - L0) < 1e-13 * np.linalg.norm(L0)
+
+
+def test_time_reversal_full_force_model(mb1k):
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    fm = orc.force_model()
+    for i in range(0, 1000, 97):
+        x0 = mb1k.states[:, i]
+        rc, st, t, dt, _ = orc.propagate(fm, x0, W.T0, W.T0 + 60.0)
+        rc2, back, t2, _, _ = orc.propagate(fm, st, t, W.T0)
+        assert rc == 0 and rc2 == 0 and t2 == W.T0
+        assert np.abs(back[:3] - x0[:3]).max() < 1e-11
+
+
+def test_tolerance_sweep_converges():
+    orc, fm0 = _sun_only_oracle()
+    x0 = _kepler_closed(1.2, 0.6, 0.2, 0.1, 0.3, 0.1, 0.0)
+    ref = _kepler_closed(1.2, 0.6, 0.2, 0.1, 0.3, 0.1, 400.0)
+    errs, steps = [], []
+    for eps in (1e-1, 1e-2, 1e-3, 1e-9):
+        fm = orc.force_model(body_mask=1, gr_mask=0, j2_mask=0, eps=eps)
+        _, st, _, _, stats = orc.propagate(fm, x0, W.T0, W.T0 + 400.0)
+        errs.append(np.abs(st[:3] - ref[:3]).max())
+        steps.append(stats.steps)
+    # truncation error falls with eps until round-off (~1e-14 AU) is reached
+    assert errs[0] > errs[1] > errs[2] > errs[3] or errs[3] < 5e-14
+    assert errs[0] > errs[1] > errs[2] and errs[3] < 5e-14
+    assert steps == sorted(steps)
+
+
+def _lrl_angle(st, mu):
+    r, v = st[:3], st[3:]
+    ev = np.cross(v, np.cross(r, v)) / mu - r / np.linalg.norm(r)
+    return math.atan2(ev[1], ev[0])
+
+
+def test_gr_perihelion_advance_mercury():
+    g = _golden_kv("gr_mercury.txt")
+    years = 100.0
+    orc = O.Oracle(W.static_sun_table(W.T0 - 10, W.T0 + 365.25 * years + 20).to_bytes())
+    fm = orc.force_model(body_mask=1, gr_mask=1, j2_mask=0)
+    a, e = g["a_au"], g["e"]
+    # orbit in the ecliptic plane: the LRL vector angle is the longitude of perihelion
+    x0 = _kepler_closed(a, e, 0.0, 0.0, 0.0, 0.0, 0.0)
+    T = 2 * math.pi * math.sqrt(a ** 3 / W.GM_SUN)
+    n_orb = int(years * 365.25 / T)
+    rc, st, *_ = orc.propagate(fm, x0, W.T0, W.T0 + n_orb * T)
+    assert rc == 0
+    dw = _lrl_angle(st, W.GM_SUN) - _lrl_angle(x0, W.GM_SUN)
+    per_orbit = 6 * math.pi * W.GM_SUN / (C_AU_D ** 2 * a * (1 - e * e))
+    assert dw > 0                                     # prograde advance
+    assert abs(dw / (n_orb * per_orbit) - 1) < 0.01
+    century = dw / n_orb * (36525.0 / T) * 180 / math.pi * 3600
+    assert abs(century - g["arcsec_per_century"]) < g["tolerance_arcsec"] + 0.01 * century
+
+
+def test_j2_nodal_regression_rate():
+    """d(node)/dt = -(3/2) n J2 (R/p)^2 cos i for an orbit about an oblate Sun."""
+    days = 3650.0
+    orc = O.Oracle(W.static_sun_table(W.T0 - 10, W.T0 + days + 20).to_bytes())
+    J2, R = 1e-3, 0.1
+    eps_obl = math.radians(84381.448 / 3600)
+    # pole = ecliptic north pole (RA 270 deg, Dec 90 deg - obliquity)
+    fm = orc.force_model(body_mask=1, gr_mask=0, j2_mask=1, j2={0: J2}, radius={0: R},
+                         pole_ra={0: math.radians(270.0)},
+                         pole_dec={0: math.pi / 2 - eps_obl})
+    a, e, inc = 1.0, 0.01, math.radians(20.0)
+    x0 = _kepler_closed(a, e, inc, 0.7, 0.3, 0.0, 0.0)
+    ts = np.linspace(0, days, 731)
+    nodes = []
+    st, t, dt = x0.copy(), W.T0, 0.0
+    for tt in ts:
+        rc, st, t, dt, _ = orc.propagate(fm, st, t, W.T0 + tt, dt)
+        assert rc == 0
+        hvec = np.cross(st[:3], st[3:])
+        nodes.append(math.atan2(hvec[0], -hvec[1]))
+    nodes = np.unwrap(nodes)
+    slope = np.polyfit(ts, nodes, 1)[0]
+    n = math.sqrt(W.GM_SUN / a ** 3)
+    p = a * (1 - e * e)
+    expect = -1.5 * n * J2 * (R / p) ** 2 * math.cos(inc)
+    assert slope < 0
+    assert abs(slope / expect - 1) < 0.02
+
+
+def test_planets_off_equals_sun_only_table(mb1k):
+    """Masking every planet leaves the Sun's monopole of the same table."""
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    fm_sun = orc.force_model(body_mask=1, gr_mask=0, j2_mask=0)
+    x0 = mb1k.states[:, 5]
+    _, a = orc.accel(fm_sun, W.T0, x0[:3], x0[3:])
+    _, sun, _ = orc.ephem(0, W.T0)
+    r = x0[:3] - sun
+    np.testing.assert_allclose(a, -W.GM_SUN * r / np.linalg.norm(r) ** 3, rtol=1e-14)
+
+
+@pytest.mark.parametrize("body,a_pl", [(5, 5.2044), (3, 1.0)])
+def test_planet_terms_conserve_jacobi_integral(body, a_pl):
+    """Sun + one planet on circular orbits: the Jacobi integral
+    C = 2(mu_s/r_s + mu_p/r_p) - v^2 + 2 n (x v_y - y v_x) is conserved."""
+    days = 730.0
+    tab = W.circular_pair_table(body, a_pl, W.T0 - 10, W.T0 + days + 20)
+    orc = O.Oracle(tab.to_bytes())
+    fm = orc.force_model(body_mask=(1 | (1 << body)), gr_mask=0, j2_mask=0)
+    mu_s, mu_p = tab.gm[0], tab.gm[body]
+    n = math.sqrt((mu_s + mu_p) / a_pl ** 3)
+
+    def jacobi(st, t):
+        _, ps, _ = orc.ephem(0, t)
+        _, pp, _ = orc.ephem(body, t)
+        r, v = st[:3], st[3:]
+        return (2 * (mu_s / np.linalg.norm(r - ps) + mu_p / np.linalg.norm(r - pp)) - v @ v
+                + 2 * n * (r[0] * v[1] - r[1] * v[0]))
+
+    for (a, e, inc) in [(2.6, 0.1, 0.1), (1.6, 0.3, 0.2), (3.3, 0.05, 0.0)]:
+        x0 = _kepler_closed(a, e, inc, 0.4, 1.0, 2.0, 0.0)
+        c0 = jacobi(x0, W.T0)
+        rc, st, t, *_ = orc.propagate(fm, x0, W.T0, W.T0 + days)
+        assert rc == 0
+        assert abs(jacobi(st, t) - c0) < 1e-12 * abs(c0)
+        # and the planet really perturbs the orbit (the test is not vacuous)
+        ref = _kepler_closed(a, e, inc, 0.4, 1.0, 2.0, days)
+        assert np.abs(st[:3] - ref[:3]).max() > 1e-7
