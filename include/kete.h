@@ -1,0 +1,217 @@
+/*
+ * kete.h -- C ABI of the GB300 survey-prediction library (libkete_gpu.so).
+ *
+ * The library answers the question of Sec. 2 of the Kete paper: given a list
+ * of telescope fields of view (FoVs, each with an epoch and an observer
+ * position, Sec. 3.1) and the Cartesian states of many minor bodies, which
+ * bodies fall inside which FoV.  The path it runs on the GPU:
+ *
+ *   1. planetary positions from a device-resident Chebyshev table (the
+ *      stand-in for the SPICE kernels of Sec. 3.2 / App. A);
+ *   2. n-body propagation of massless bodies under Sun + planets with the
+ *      force model of Eq. A.1 (Newton + GR of Eq. A.3 + J2 of Eq. A.4) by a
+ *      Gauss-Radau integrator with IAS15 convergence and step control and the
+ *      predictor removed (Sec. 3.2, App. A.6);
+ *   3. FoVs sorted and grouped into <= 3-day batches, bodies integrated to each
+ *      batch midpoint, then two-body propagation with light-delay correction
+ *      to each FoV epoch (Sec. 2);
+ *   4. the spherical-polygon membership test by inward great-circle normals
+ *      (Sec. 3.1), and RA/Dec of every hit (App. A.1).
+ *
+ * Units and frames (App. A.1): AU, AU/day, TDB Julian dates; states are
+ * barycentric ecliptic J2000; RA/Dec are equatorial J2000 (obliquity
+ * 84381.448 arcsec).
+ *
+ * Conventions for every call:
+ *   - Pointers marked (device) must be device memory of the context's GPU;
+ *     pointers marked (host) are host memory.  The caller owns every buffer
+ *     it passes; the library owns only its ephemeris copy and its scratch.
+ *   - All work is ordered on the context's CUDA stream.  Calls that return a
+ *     count to the host (kete_fov_check) synchronize that stream.
+ *   - Return value: KETE_OK (0) or a negative KETE_ERR_*; nothing is thrown.
+ *     kete_last_error() gives a one-line message for the last failure.
+ *   - A body whose integration fails gets a per-body status code; the other
+ *     bodies' results stay valid.
+ */
+#ifndef KETE_H
+#define KETE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KETE_MAX_BODIES 16   /* massive bodies a table may hold */
+#define KETE_MAX_EDGES 4     /* edges of one spherical polygon */
+
+/* return codes */
+#define KETE_OK 0
+#define KETE_ERR_BAD_ARG -1      /* invalid size, pointer, frame layout or option */
+#define KETE_ERR_EPHEM_SPAN -2   /* an epoch lies outside the loaded table */
+#define KETE_ERR_CAPACITY -3     /* hit buffer too small: *n_hits holds the count needed */
+#define KETE_ERR_NO_EPHEM -4     /* no ephemeris loaded */
+#define KETE_ERR_CUDA -5         /* a CUDA call failed (message in kete_last_error) */
+#define KETE_ERR_NOMEM -6        /* device allocation of library scratch failed */
+
+/* per-body status (int32, written to the caller's status array) */
+#define KETE_BODY_OK 0
+#define KETE_BODY_STEP_CAP 1      /* more than max_steps step attempts in one leg */
+#define KETE_BODY_OUT_OF_SPAN 2   /* the integrator needed planets outside the table */
+#define KETE_BODY_NONFINITE 3     /* state or acceleration became NaN/Inf */
+#define KETE_BODY_KEPLER_CAP 4    /* two-body solve did not converge (no hits emitted) */
+
+/* precision modes */
+#define KETE_FP64 0    /* everything in FP64 */
+#define KETE_MIXED 1   /* planetary perturbation terms in FP32, the rest FP64 */
+
+/* Force model and integrator controls (Eq. A.1, App. A.2-A.3, App. A.6).
+ * Bit b of a mask refers to body b of the loaded table (0 = Sun, 1..8 =
+ * Mercury, Venus, Earth-Moon, Mars, Jupiter, Saturn, Uranus, Neptune).
+ * Fill with kete_force_model_default() and change what you need. */
+typedef struct kete_force_model {
+    uint32_t body_mask;          /* bodies whose gravity acts (default 0x1FF) */
+    uint32_t gr_mask;            /* GR term of Eq. A.3 (default Sun, Earth, Jupiter) */
+    uint32_t j2_mask;            /* J2 term of Eq. A.4 (default Sun, Jupiter) */
+    int32_t precision;           /* KETE_FP64 or KETE_MIXED */
+    double j2[KETE_MAX_BODIES];  /* J2 coefficient per body */
+    double radius[KETE_MAX_BODIES];   /* equatorial radius, AU */
+    double pole_ra[KETE_MAX_BODIES];  /* pole right ascension, rad (equatorial J2000) */
+    double pole_dec[KETE_MAX_BODIES]; /* pole declination, rad */
+    double eps;                  /* IAS15 step-size control parameter (1e-9) */
+    double eps_pc;               /* corrector convergence threshold on max|db6|/max|a| (1e-16) */
+    double safety;               /* IAS15 safety factor (0.25) */
+    double dt_init;              /* first step of each propagation chain, days (4) */
+    int32_t max_iter;            /* corrector iteration cap (12) */
+    int32_t reserved;
+    int64_t max_steps;           /* step attempts per leg before KETE_BODY_STEP_CAP */
+} kete_force_model;
+
+/* One spherical polygon (Sec. 3.1).  Polygons with the same exposure_id must
+ * be contiguous and share epoch and observer_idx: together they form the
+ * union-of-detectors FoV of one exposure.  Frames must be sorted by epoch
+ * (non-decreasing).  normals[k] is the inward normal of edge k (any length);
+ * a direction u is inside iff normals[k].u > 0 for every k < n_edges. */
+typedef struct kete_frame {
+    double epoch;                /* TDB JD of the (instantaneous) observation */
+    int64_t observer_idx;        /* row of the observers array */
+    int64_t exposure_id;         /* groups the sub-fields of one exposure */
+    int32_t n_edges;             /* 3 or 4 */
+    int32_t reserved;
+    double normals[KETE_MAX_EDGES][3];
+} kete_frame;                    /* 128 bytes */
+
+/* Options of the survey driver (Sec. 2). */
+typedef struct kete_survey_opts {
+    double batch_span;           /* a batch holds epochs t with t - t_first < span (3 days) */
+    double twobody_max;          /* longest two-body interval (1.5 days); 0 = n-body to every epoch */
+    double cell_deg;             /* sky-cell size for candidate search; 0 = automatic */
+    double mem_budget_gb;        /* device scratch budget for batch states (0 = 8 GB) */
+} kete_survey_opts;
+
+/* One body inside one polygon.  Hits come back sorted by (frame, body). */
+typedef struct kete_hit {
+    int64_t frame;               /* index into the frames array */
+    int32_t body;                /* index into the states arrays */
+    int32_t flags;               /* reserved, 0 */
+    double ra;                   /* rad in [0, 2 pi), equatorial J2000, light-time corrected */
+    double dec;                  /* rad */
+} kete_hit;                      /* 32 bytes */
+
+/* Counters and device timings of the last call (CUDA events on the context
+ * stream around the named kernels). */
+typedef struct kete_stats {
+    double prop_ms;              /* propagation kernels */
+    double fov_ms;               /* everything after propagation in kete_fov_check */
+    double total_ms;             /* whole call on the stream */
+    int64_t steps;               /* accepted integrator steps */
+    int64_t rejected;            /* rejected step attempts */
+    int64_t force_evals;         /* acceleration evaluations */
+    int64_t iterations;          /* corrector iterations */
+    int64_t n_batches;
+    int64_t n_exposures;
+    int64_t n_candidates;        /* (exposure, body) pairs given the exact test */
+    int64_t n_hits;
+    int64_t prop_launches;       /* propagation kernel launches */
+    int64_t launches;            /* all kernel launches of the call */
+} kete_stats;
+
+typedef struct kete_ctx kete_ctx;
+
+/* Create a context on CUDA device `device`, ordering work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context.  Errors: KETE_ERR_BAD_ARG (null out), KETE_ERR_CUDA. */
+int kete_create(kete_ctx **out, int device, void *cuda_stream);
+/* Free the context, its ephemeris and its scratch.  NULL is a no-op. */
+void kete_destroy(kete_ctx *ctx);
+/* Change the stream later calls are ordered on. */
+int kete_set_stream(kete_ctx *ctx, void *cuda_stream);
+/* Message of the last failure on this context ("" if none). */
+const char *kete_last_error(const kete_ctx *ctx);
+
+/* Defaults: Sun + 8 planets, GR for Sun/Earth/Jupiter (App. A.2), J2 for
+ * Sun/Jupiter (App. A.3), IAS15 constants eps 1e-9, 1e-16, safety 0.25, 12
+ * corrector iterations (App. A.6), FP64. */
+void kete_force_model_default(kete_force_model *fm);
+/* Defaults: 3-day batches and 1.5-day two-body interval (Sec. 2). */
+void kete_survey_opts_default(kete_survey_opts *opt);
+
+/* Load a planetary Chebyshev table (host buffer, `nbytes` bytes) into device
+ * memory owned by the context (App. A: SPICE-like segments).  Layout:
+ * 256-byte header {char magic[8] = "KETECHB1"; int32 version = 1; int32
+ * n_bodies; int32 n_coef; int32 n_seg; double t_start; double seg_len;
+ * double gm[16] at byte 48}, then double coef[n_bodies][n_seg][3][n_coef]
+ * (ecliptic x, y, z of each body, AU; segment s covers [t_start + s L,
+ * t_start + (s+1) L) with tau = 2 (t - t_mid)/L).  Replaces any earlier table.
+ * Errors: KETE_ERR_BAD_ARG (malformed header/size), KETE_ERR_CUDA. */
+int kete_load_ephem(kete_ctx *ctx, const void *buf, size_t nbytes);
+
+/* Evaluate the loaded table for body `body` at n epochs t (device, n) into
+ * pos (device, [n][3]) and, if vel != NULL, vel (device, [n][3], AU/day).
+ * An epoch outside the table gives NaN.  Errors: BAD_ARG, NO_EPHEM, CUDA. */
+int kete_ephem_eval(kete_ctx *ctx, const double *t, int64_t n, int body, double *pos,
+                    double *vel);
+
+/* Propagate n bodies in place to t_target (Sec. 3.2, App. A).
+ * states (device, SoA [6][n]: x[n], y[n], z[n], vx[n], vy[n], vz[n]);
+ * epochs (device, [n]) give each body's epoch and are set to t_target on
+ * success; status (device, [n] int32, may be NULL) receives KETE_BODY_*.
+ * A failed body keeps its input state and epoch.
+ * Errors: BAD_ARG, NO_EPHEM, CUDA.  Per-body failures are not call errors. */
+int kete_propagate(kete_ctx *ctx, double *states, double *epochs, int64_t n, double t_target,
+                   const kete_force_model *fm, int32_t *status);
+
+/* Propagate n bodies (not modified) along the chain epoch -> stops[0] ->
+ * stops[1] -> ... (host, [n_stops], ascending), carrying the step size along
+ * the chain: the schedule kete_fov_check uses for the batch midpoints (Sec. 2,
+ * "between the median observation times of consecutive batches").
+ * out (device, [n_stops][6][n]) receives the states; a failed body gets NaN
+ * from its failing stop on.  Errors: BAD_ARG, NO_EPHEM, CUDA. */
+int kete_propagate_stops(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                         const double *stops, int64_t n_stops, const kete_force_model *fm,
+                         double *out, int32_t *status);
+
+/* Which bodies fall inside which FoV (Sec. 2, Sec. 3.1).
+ * states/epochs: as kete_propagate (device, not modified).
+ * frames (device, [n_frames]): see kete_frame; sorted by epoch.
+ * observers (device, [n_obs][3]): observer positions, AU, barycentric ecliptic.
+ * hits (device, [capacity]): receives the hits sorted by (frame, body).
+ * n_hits (host): number of hits.  If it exceeds capacity the call returns
+ * KETE_ERR_CAPACITY, writes nothing to hits and leaves the count needed in
+ * *n_hits (retry with a larger buffer).  status (device, [n], may be NULL).
+ * Errors: BAD_ARG (sizes, unsorted epochs, inconsistent exposures, bad
+ * observer index, n_edges outside 3..4), NO_EPHEM, EPHEM_SPAN (a batch epoch
+ * outside the table), CAPACITY, NOMEM, CUDA. */
+int kete_fov_check(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                   const kete_frame *frames, int64_t n_frames, const double *observers,
+                   int64_t n_obs, const kete_force_model *fm, const kete_survey_opts *opt,
+                   kete_hit *hits, int64_t capacity, int64_t *n_hits, int32_t *status);
+
+/* Copy the counters of the last call into *out (host). */
+int kete_get_stats(const kete_ctx *ctx, kete_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

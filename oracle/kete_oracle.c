@@ -28,6 +28,9 @@
  *     representable epochs it joins; the last step of a leg lands exactly on
  *     the target epoch.  Two-body intervals are formed as (t_obs - t_ref) - tau
  *     before any absolute epoch is rounded.
+ *  R11 (Sec. 2, chain of batch midpoints): a body is integrated from its epoch
+ *     to the first batch midpoint, then from each midpoint to the next; the
+ *     proposed step size is carried along the chain.
  */
 #include "kete_oracle.h"
 
@@ -402,37 +405,20 @@ int ko_propagate(const ko_ephem *e, const ko_force_model *fm, double st[6], doub
     return KO_OK;
 }
 
-/* Chain semantics: stops >= epoch are visited forward in ascending order from
- * the epoch state, stops < epoch backward in descending order; the proposed
- * step is carried along each chain, which starts from dt_init. */
+/* Chain of stops (Sec. 2: n-body integration between the median times of
+ * consecutive batches, R11): from the epoch to stops[0], then from each stop to
+ * the next in the given order.  The proposed step is carried along the chain,
+ * which starts from dt_init; a failed body gets NaN from its failing stop on. */
 int ko_propagate_stops(const ko_ephem *e, const ko_force_model *fm, const double st0[6],
                        double epoch, const double *stops, int64_t n_stops, double *out,
                        ko_stats *stats)
 {
     int status = KO_OK;
-    int64_t split = 0;
-    while (split < n_stops && stops[split] < epoch) split++;
-    for (int pass = 0; pass < 2; pass++) {
-        double st[6], t = epoch, dt = 0.0;
-        memcpy(st, st0, sizeof(st));
-        int failed = 0;
-        if (pass == 0) {
-            for (int64_t k = split; k < n_stops; k++) {
-                if (!failed) {
-                    int s = ko_propagate(e, fm, st, &t, stops[k], &dt, stats);
-                    if (s != KO_OK) { failed = 1; status = s; }
-                }
-                for (int i = 0; i < 6; i++) out[k * 6 + i] = failed ? NAN : st[i];
-            }
-        } else {
-            for (int64_t k = split - 1; k >= 0; k--) {
-                if (!failed) {
-                    int s = ko_propagate(e, fm, st, &t, stops[k], &dt, stats);
-                    if (s != KO_OK) { failed = 1; status = s; }
-                }
-                for (int i = 0; i < 6; i++) out[k * 6 + i] = failed ? NAN : st[i];
-            }
-        }
+    double st[6], t = epoch, dt = 0.0;
+    memcpy(st, st0, sizeof(st));
+    for (int64_t k = 0; k < n_stops; k++) {
+        if (status == KO_OK) status = ko_propagate(e, fm, st, &t, stops[k], &dt, stats);
+        for (int i = 0; i < 6; i++) out[k * 6 + i] = (status == KO_OK) ? st[i] : NAN;
     }
     return status;
 }

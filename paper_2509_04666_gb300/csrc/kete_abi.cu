@@ -1,0 +1,741 @@
+// kete_abi.cu -- the C ABI of libkete_gpu.so (declared in include/kete.h).
+//
+// Host orchestration only: argument checks, device scratch, launch order on
+// the context stream, the few host reads the survey driver needs (exposure and
+// batch counts, candidate and hit counts per chunk of batches).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kete_fov.h"
+#include "kete_impl.h"
+
+using namespace kete;
+
+namespace {
+
+enum Slot {
+    S_CHAIN, S_STATUS, S_STOPS, S_STOPSTATES, S_ISSTART, S_EX, S_SCANTMP, S_FCEN, S_FAUX,
+    S_EXPFIRST, S_XEPOCH, S_XOBS, S_XCEN, S_XRAD, S_XCS, S_XBATCH, S_NEXT, S_BFIRST, S_BTREF,
+    S_BO, S_BROBS, S_BTSPAN, S_BRMAX, S_BSUN, S_NBATCH, S_BANDS, S_CELLKEY, S_CELLCNT,
+    S_CELLSTART, S_CELLCUR, S_CELLEXP, S_CAND, S_EXPCNT, S_EXPOFF, S_EXPCUR, S_CANDBODY,
+    S_HITTMP, S_FRAMECNT, S_FRAMEOFF, S_FRAMECUR, S_HITGROUP, S_MAXRAD, S_NSLOTS
+};
+
+struct Scratch {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct kete_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool have_ephem = false;
+    double *d_coef = nullptr;
+    float *d_coef32 = nullptr;
+    EphemDev E{};
+    Scratch slot[S_NSLOTS];
+    DevCounters *d_ctr = nullptr;
+    DevCounters *h_ctr = nullptr;   // pinned
+    kete_stats stats{};
+    std::vector<cudaEvent_t> ev;    // pool: [0] start, [1] end, then pairs for propagation
+    int n_sm = 152;
+    int pending_prop_pairs = 0;
+};
+
+static int fail(kete_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CUDA_TRY(x)                                                                       \
+    do {                                                                                  \
+        cudaError_t _e = (x);                                                             \
+        if (_e != cudaSuccess)                                                            \
+            return fail(ctx, KETE_ERR_CUDA, "%s failed: %s", #x, cudaGetErrorString(_e)); \
+    } while (0)
+
+static cudaError_t ensure(kete_ctx *ctx, int s, size_t bytes, void **out)
+{
+    Scratch &b = ctx->slot[s];
+    if (bytes == 0) bytes = 16;
+    if (b.bytes < bytes) {
+        if (b.p) {
+            cudaError_t e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) return e;
+            cudaFree(b.p);
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        size_t want = bytes + bytes / 4;
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            e = cudaMalloc(&b.p, bytes);
+            if (e != cudaSuccess) return e;
+            want = bytes;
+        }
+        b.bytes = want;
+    }
+    *out = b.p;
+    return cudaSuccess;
+}
+
+template <typename T>
+static int get(kete_ctx *ctx, int s, size_t count, T **out)
+{
+    void *p = nullptr;
+    cudaError_t e = ensure(ctx, s, count * sizeof(T), &p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KETE_ERR_NOMEM, "device allocation of %zu bytes failed: %s",
+                    count * sizeof(T), cudaGetErrorString(e));
+    }
+    *out = (T *)p;
+    return KETE_OK;
+}
+
+#define GET(slot, n, ptr)                                  \
+    do {                                                   \
+        int _r = get(ctx, slot, (size_t)(n), &(ptr));      \
+        if (_r != KETE_OK) return _r;                      \
+    } while (0)
+
+static cudaEvent_t event_at(kete_ctx *ctx, size_t i)
+{
+    while (ctx->ev.size() <= i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ctx->ev.push_back(e);
+    }
+    return ctx->ev[i];
+}
+
+static void stats_begin(kete_ctx *ctx)
+{
+    std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->pending_prop_pairs = 0;
+    cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream);
+    cudaEventRecord(event_at(ctx, 0), ctx->stream);
+}
+
+static void prop_event(kete_ctx *ctx, bool begin)
+{
+    size_t idx = 2 + 2 * (size_t)ctx->pending_prop_pairs + (begin ? 0 : 1);
+    cudaEventRecord(event_at(ctx, idx), ctx->stream);
+    if (!begin) ctx->pending_prop_pairs++;
+}
+
+static int stats_end(kete_ctx *ctx)
+{
+    cudaEventRecord(event_at(ctx, 1), ctx->stream);
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    return KETE_OK;
+}
+
+static void stats_collect(kete_ctx *ctx)
+{
+    cudaStreamSynchronize(ctx->stream);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    ctx->stats.total_ms = ms;
+    double p = 0.0;
+    for (int k = 0; k < ctx->pending_prop_pairs; k++) {
+        float m = 0.0f;
+        cudaEventElapsedTime(&m, ctx->ev[2 + 2 * k], ctx->ev[3 + 2 * k]);
+        p += m;
+    }
+    ctx->stats.prop_ms = p;
+    ctx->stats.fov_ms = ctx->stats.total_ms - p;
+    ctx->stats.steps = (int64_t)ctx->h_ctr->steps;
+    ctx->stats.rejected = (int64_t)ctx->h_ctr->rejected;
+    ctx->stats.force_evals = (int64_t)ctx->h_ctr->force_evals;
+    ctx->stats.iterations = (int64_t)ctx->h_ctr->iterations;
+    ctx->stats.prop_launches = ctx->pending_prop_pairs;
+    ctx->pending_prop_pairs = 0;
+}
+
+extern "C" {
+
+void kete_force_model_default(kete_force_model *fm)
+{
+    if (!fm) return;
+    std::memset(fm, 0, sizeof(*fm));
+    const double deg = 3.14159265358979323846 / 180.0;
+    const double au = 149597870.7;
+    fm->body_mask = 0x1FFu;
+    fm->gr_mask = (1u << 0) | (1u << 3) | (1u << 5);   // Sun, Earth, Jupiter (App. A.2)
+    fm->j2_mask = (1u << 0) | (1u << 5);               // Sun, Jupiter (App. A.3)
+    fm->precision = KETE_FP64;
+    fm->j2[0] = 2.1961e-7;
+    fm->radius[0] = 696000.0 / au;
+    fm->pole_ra[0] = 286.13 * deg;
+    fm->pole_dec[0] = 63.87 * deg;
+    fm->j2[5] = 0.014736;
+    fm->radius[5] = 71492.0 / au;
+    fm->pole_ra[5] = 268.056595 * deg;
+    fm->pole_dec[5] = 64.495303 * deg;
+    fm->eps = 1e-9;
+    fm->eps_pc = 1e-16;
+    fm->safety = 0.25;
+    fm->dt_init = 4.0;
+    fm->max_iter = 12;
+    fm->max_steps = 1000000;
+}
+
+void kete_survey_opts_default(kete_survey_opts *opt)
+{
+    if (!opt) return;
+    opt->batch_span = 3.0;
+    opt->twobody_max = 1.5;
+    opt->cell_deg = 0.0;
+    opt->mem_budget_gb = 0.0;
+}
+
+int kete_create(kete_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return KETE_ERR_BAD_ARG;
+    *out = nullptr;
+    kete_ctx *ctx = new kete_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_ctr, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_ctr, sizeof(DevCounters));
+    if (e != cudaSuccess) {
+        delete ctx;
+        return KETE_ERR_CUDA;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+        ctx->n_sm = sms;
+    std::memset(ctx->h_ctr, 0, sizeof(DevCounters));
+    upload_radau_tables(ctx->stream);
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        kete_destroy(ctx);
+        return KETE_ERR_CUDA;
+    }
+    *out = ctx;
+    return KETE_OK;
+}
+
+void kete_destroy(kete_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    for (auto &s : ctx->slot)
+        if (s.p) cudaFree(s.p);
+    if (ctx->d_coef) cudaFree(ctx->d_coef);
+    if (ctx->d_coef32) cudaFree(ctx->d_coef32);
+    if (ctx->d_ctr) cudaFree(ctx->d_ctr);
+    if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
+    for (auto e : ctx->ev) cudaEventDestroy(e);
+    delete ctx;
+}
+
+int kete_set_stream(kete_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return KETE_OK;
+}
+
+const char *kete_last_error(const kete_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int kete_get_stats(const kete_ctx *ctx, kete_stats *out)
+{
+    if (!ctx || !out) return KETE_ERR_BAD_ARG;
+    *out = ctx->stats;
+    return KETE_OK;
+}
+
+int kete_load_ephem(kete_ctx *ctx, const void *buf, size_t nbytes)
+{
+    if (!ctx || !buf) return fail(ctx, KETE_ERR_BAD_ARG, "null context or buffer");
+    const unsigned char *p = (const unsigned char *)buf;
+    if (nbytes < 256 || std::memcmp(p, "KETECHB1", 8) != 0)
+        return fail(ctx, KETE_ERR_BAD_ARG, "not a KETECHB1 table");
+    int32_t hdr[4];
+    double td[2];
+    std::memcpy(hdr, p + 8, sizeof(hdr));
+    std::memcpy(td, p + 24, sizeof(td));
+    if (hdr[0] != 1) return fail(ctx, KETE_ERR_BAD_ARG, "unsupported table version %d", hdr[0]);
+    int nb = hdr[1], nc = hdr[2], ns = hdr[3];
+    if (nb < 1 || nb > KETE_MAX_BODIES || nc < 2 || nc > 64 || ns < 1)
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad table sizes (bodies %d, coef %d, seg %d)", nb, nc, ns);
+    if (!(td[1] > 0.0) || !std::isfinite(td[0]))
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad table span");
+    size_t ncoef = (size_t)nb * ns * 3 * nc;
+    if (nbytes < 256 + ncoef * sizeof(double))
+        return fail(ctx, KETE_ERR_BAD_ARG, "table truncated: %zu bytes, need %zu", nbytes,
+                    256 + ncoef * sizeof(double));
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    if (ctx->d_coef) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->d_coef);
+        cudaFree(ctx->d_coef32);
+        ctx->d_coef = nullptr;
+        ctx->d_coef32 = nullptr;
+    }
+    ctx->have_ephem = false;
+    std::vector<float> f32(ncoef);
+    const double *src = (const double *)(p + 256);
+    std::vector<double> f64(src, src + ncoef);
+    for (size_t i = 0; i < ncoef; i++) f32[i] = (float)f64[i];
+    CUDA_TRY(cudaMalloc(&ctx->d_coef, ncoef * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&ctx->d_coef32, ncoef * sizeof(float)));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_coef, f64.data(), ncoef * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->d_coef32, f32.data(), ncoef * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    EphemDev E{};
+    E.coef = ctx->d_coef;
+    E.coef32 = ctx->d_coef32;
+    E.t_start = td[0];
+    E.seg_len = td[1];
+    E.inv_seg = 1.0 / td[1];
+    E.t_end = td[0] + ns * td[1];
+    E.n_seg = ns;
+    E.n_coef = nc;
+    E.n_bodies = nb;
+    std::memcpy(E.gm, p + 48, sizeof(double) * KETE_MAX_BODIES);
+    ctx->E = E;
+    ctx->have_ephem = true;
+    return KETE_OK;
+}
+
+}  // extern "C"
+
+static int make_force(kete_ctx *ctx, const kete_force_model *fm_in, ForceDev &F)
+{
+    kete_force_model fm;
+    if (fm_in) fm = *fm_in;
+    else kete_force_model_default(&fm);
+    if (!(fm.eps > 0) || !(fm.safety > 0 && fm.safety < 1) || fm.max_iter < 1 || fm.max_iter > 100 ||
+        fm.max_steps < 1 || !(fm.dt_init > 0) || !(fm.eps_pc >= 0))
+        return fail(ctx, KETE_ERR_BAD_ARG, "invalid force-model controls");
+    if (fm.precision != KETE_FP64 && fm.precision != KETE_MIXED)
+        return fail(ctx, KETE_ERR_BAD_ARG, "unknown precision mode %d", fm.precision);
+    std::memset(&F, 0, sizeof(F));
+    const double eps_obl = 84381.448 / 3600.0 * 3.14159265358979323846 / 180.0;
+    const double ce = std::cos(eps_obl), se = std::sin(eps_obl);
+    uint32_t act = 0;
+    for (int m = 0; m < ctx->E.n_bodies; m++)
+        if (((fm.body_mask >> m) & 1u) && ctx->E.gm[m] != 0.0) act |= 1u << m;
+    F.active_mask = act;
+    F.gr_mask = fm.gr_mask & act;
+    F.j2_mask = fm.j2_mask & act;
+    F.precision = fm.precision;
+    for (int m = 0; m < KETE_MAX_BODIES; m++) {
+        F.j2k[m] = 1.5 * fm.j2[m] * ctx->E.gm[m] * fm.radius[m] * fm.radius[m];
+        double ra = fm.pole_ra[m], de = fm.pole_dec[m];
+        double ex = std::cos(de) * std::cos(ra), ey = std::cos(de) * std::sin(ra), ez = std::sin(de);
+        F.pole[m][0] = ex;
+        F.pole[m][1] = ce * ey + se * ez;
+        F.pole[m][2] = -se * ey + ce * ez;
+    }
+    F.eps = fm.eps;
+    F.eps_pc = fm.eps_pc;
+    F.safety = fm.safety;
+    F.dt_init = fm.dt_init;
+    F.max_iter = fm.max_iter;
+    F.max_steps = fm.max_steps;
+    return KETE_OK;
+}
+
+extern "C" int kete_ephem_eval(kete_ctx *ctx, const double *t, int64_t n, int body, double *pos,
+                               double *vel)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
+    if (n < 0 || (n > 0 && (!t || !pos)) || body < 0 || body >= ctx->E.n_bodies)
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad arguments");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(launch_ephem_eval(ctx->E, t, n, body, pos, vel, ctx->stream));
+    return KETE_OK;
+}
+
+static int run_chain(kete_ctx *ctx, const ForceDev &F, const double *states, const double *epochs,
+                     int64_t n, ChainState &cs)
+{
+    GET(S_CHAIN, 8 * n, cs.w);
+    GET(S_STATUS, n, cs.status);
+    cs.n = n;
+    CUDA_TRY(launch_chain_init(cs, states, epochs, F, ctx->stream));
+    return KETE_OK;
+}
+
+extern "C" int kete_propagate(kete_ctx *ctx, double *states, double *epochs, int64_t n,
+                              double t_target, const kete_force_model *fm, int32_t *status)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
+    if (n < 0 || n > INT32_MAX || (n > 0 && (!states || !epochs)) || !std::isfinite(t_target))
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad arguments");
+    ForceDev F;
+    int r = make_force(ctx, fm, F);
+    if (r != KETE_OK) return r;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    stats_begin(ctx);
+    if (n > 0) {
+        ChainState cs;
+        r = run_chain(ctx, F, states, epochs, n, cs);
+        if (r != KETE_OK) return r;
+        double *d_stop;
+        GET(S_STOPS, 1, d_stop);
+        CUDA_TRY(cudaMemcpyAsync(d_stop, &t_target, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        prop_event(ctx, true);
+        CUDA_TRY(launch_propagate(ctx->E, F, cs, d_stop, 1, states, n, true, ctx->d_ctr, ctx->stream));
+        prop_event(ctx, false);
+        CUDA_TRY(launch_chain_finish(cs, states, epochs, status, ctx->stream));
+        ctx->stats.launches = 3;
+    }
+    r = stats_end(ctx);
+    if (r != KETE_OK) return r;
+    stats_collect(ctx);
+    return KETE_OK;
+}
+
+extern "C" int kete_propagate_stops(kete_ctx *ctx, const double *states, const double *epochs,
+                                    int64_t n, const double *stops, int64_t n_stops,
+                                    const kete_force_model *fm, double *out, int32_t *status)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
+    if (n < 0 || n > INT32_MAX || n_stops < 0 || n_stops > INT32_MAX ||
+        (n > 0 && (!states || !epochs)) || (n_stops > 0 && (!stops || !out)))
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad arguments");
+    for (int64_t k = 0; k < n_stops; k++)
+        if (!std::isfinite(stops[k]) || (k > 0 && stops[k] < stops[k - 1]))
+            return fail(ctx, KETE_ERR_BAD_ARG, "stops must be finite and ascending");
+    ForceDev F;
+    int r = make_force(ctx, fm, F);
+    if (r != KETE_OK) return r;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    stats_begin(ctx);
+    if (n > 0 && n_stops > 0) {
+        ChainState cs;
+        r = run_chain(ctx, F, states, epochs, n, cs);
+        if (r != KETE_OK) return r;
+        double *d_stops;
+        GET(S_STOPS, n_stops, d_stops);
+        CUDA_TRY(cudaMemcpyAsync(d_stops, stops, n_stops * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        prop_event(ctx, true);
+        CUDA_TRY(launch_propagate(ctx->E, F, cs, d_stops, (int)n_stops, out, n, false, ctx->d_ctr, ctx->stream));
+        prop_event(ctx, false);
+        CUDA_TRY(launch_chain_finish(cs, nullptr, nullptr, status, ctx->stream));
+        ctx->stats.launches = 3;
+    }
+    r = stats_end(ctx);
+    if (r != KETE_OK) return r;
+    stats_collect(ctx);
+    return KETE_OK;
+}
+
+// sky-cell grid: bands of height ~cell, cells of width >= cell along each band
+static void make_bands(double cell, std::vector<int32_t> &off, std::vector<int32_t> &cnt,
+                       double &hb, int &n_bands, int &n_cells)
+{
+    const double pi = 3.14159265358979323846;
+    n_bands = std::max(1, (int)std::ceil(pi / cell));
+    hb = pi / n_bands;
+    off.assign(n_bands + 1, 0);
+    cnt.assign(n_bands, 1);
+    for (int j = 0; j < n_bands; j++) {
+        double lo = -0.5 * pi + j * hb, hi = lo + hb;
+        double closest = (lo <= 0.0 && hi >= 0.0) ? 0.0 : std::min(std::fabs(lo), std::fabs(hi));
+        int nj = (int)std::floor(2.0 * pi * std::cos(closest) / cell);
+        cnt[j] = std::max(1, nj);
+        off[j + 1] = off[j] + cnt[j];
+    }
+    n_cells = off[n_bands];
+}
+
+extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double *epochs,
+                              int64_t n, const kete_frame *frames, int64_t n_frames,
+                              const double *observers, int64_t n_obs,
+                              const kete_force_model *fm, const kete_survey_opts *opt_in,
+                              kete_hit *hits, int64_t capacity, int64_t *n_hits, int32_t *status)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
+    if (!n_hits || n < 0 || n > INT32_MAX || n_frames < 0 || n_frames >= INT32_MAX || n_obs < 0 ||
+        capacity < 0 || (n > 0 && (!states || !epochs)) ||
+        (n_frames > 0 && (!frames || !observers || n_obs == 0)) || (capacity > 0 && !hits))
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad arguments");
+    kete_survey_opts opt;
+    if (opt_in) opt = *opt_in;
+    else kete_survey_opts_default(&opt);
+    if (!(opt.batch_span >= 0) || !(opt.twobody_max >= 0) || !(opt.cell_deg >= 0) ||
+        !(opt.mem_budget_gb >= 0))
+        return fail(ctx, KETE_ERR_BAD_ARG, "invalid survey options");
+    ForceDev F;
+    int r = make_force(ctx, fm, F);
+    if (r != KETE_OK) return r;
+    *n_hits = 0;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    stats_begin(ctx);
+    int64_t launches = 0;
+    const int64_t nf = n_frames;
+    ChainState cs{};
+    if (n > 0) {
+        r = run_chain(ctx, F, states, epochs, n, cs);
+        if (r != KETE_OK) return r;
+        launches++;
+    }
+    if (nf == 0 || n == 0) {
+        if (n > 0) CUDA_TRY(launch_chain_finish(cs, nullptr, nullptr, status, st));
+        r = stats_end(ctx);
+        if (r != KETE_OK) return r;
+        stats_collect(ctx);
+        return KETE_OK;
+    }
+    // ---- frames -> exposures ------------------------------------------------
+    int32_t *is_start; int64_t *ex, *scan_tmp; double *fcen; float4 *faux; int32_t *exp_first;
+    GET(S_ISSTART, nf, is_start);
+    GET(S_EX, nf + 1, ex);
+    GET(S_FCEN, 4 * nf, fcen);
+    GET(S_FAUX, nf, faux);
+    CUDA_TRY(fov_frame_prep(frames, nf, n_obs, is_start, fcen, faux, ctx->d_ctr, st));
+    GET(S_SCANTMP, scan_tmp_elems(nf), scan_tmp);
+    CUDA_TRY(exclusive_scan(is_start, nf, ex, scan_tmp, st));
+    GET(S_EXPFIRST, nf + 1, exp_first);
+    CUDA_TRY(fov_exposure_first(is_start, ex, nf, exp_first, st));
+    launches += 3 + 2;
+    int64_t h_ne = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h_ne, ex + nf, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    int flags = ctx->h_ctr->error_flags;
+    if (flags & 1) return fail(ctx, KETE_ERR_BAD_ARG, "frames are not sorted by epoch");
+    if (flags & 2) return fail(ctx, KETE_ERR_BAD_ARG, "frames of one exposure differ in epoch or observer");
+    if (flags & 4) return fail(ctx, KETE_ERR_BAD_ARG, "observer_idx out of range");
+    if (flags & 8) return fail(ctx, KETE_ERR_BAD_ARG, "n_edges must be 3 or 4");
+    if (flags & 16) return fail(ctx, KETE_ERR_BAD_ARG, "non-finite or degenerate frame");
+    const int64_t ne = h_ne;
+    ExpArrays X;
+    GET(S_XEPOCH, ne, X.epoch);
+    GET(S_XOBS, 3 * ne, X.obs);
+    GET(S_XCEN, 3 * ne, X.cen);
+    GET(S_XRAD, ne, X.rad);
+    GET(S_XCS, ne, X.cs);
+    GET(S_XBATCH, ne, X.batch);
+    unsigned int *d_maxrad;
+    GET(S_MAXRAD, 1, d_maxrad);
+    CUDA_TRY(cudaMemsetAsync(d_maxrad, 0, sizeof(unsigned int), st));
+    CUDA_TRY(fov_exposure_prep(frames, nf, observers, fcen, exp_first, ne, X, d_maxrad, st));
+    // ---- batches (Sec. 2) ---------------------------------------------------
+    double span = std::min(opt.batch_span, 2.0 * opt.twobody_max);
+    int32_t *next, *d_nb;
+    BatchArrays B;
+    GET(S_NEXT, ne, next);
+    GET(S_BFIRST, ne + 1, B.first);
+    GET(S_BTREF, ne, B.t_ref);
+    GET(S_NBATCH, 1, d_nb);
+    CUDA_TRY(fov_batches(X.epoch, ne, span, next, B, d_nb, st));
+    launches += 3;
+    int32_t h_nb = 0;
+    unsigned int h_maxrad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h_nb, d_nb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&h_maxrad, d_maxrad, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const int32_t nb = h_nb;
+    std::vector<int32_t> h_first(nb + 1);
+    CUDA_TRY(cudaMemcpyAsync(h_first.data(), B.first, (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GET(S_BO, 3 * nb, B.O);
+    GET(S_BROBS, nb, B.robs);
+    GET(S_BTSPAN, nb, B.tspan);
+    GET(S_BRMAX, nb, B.rmax);
+    GET(S_BSUN, 6 * nb, B.sun);
+    CUDA_TRY(fov_batch_info(ctx->E, X, B, nb, ctx->d_ctr, st));
+    launches++;
+    // ---- sky cells -------------------------------------------------------------
+    float maxrad;
+    std::memcpy(&maxrad, &h_maxrad, sizeof(float));
+    const double pi = 3.14159265358979323846;
+    double cell = opt.cell_deg > 0 ? opt.cell_deg * pi / 180.0
+                                   : std::min(20.0 * pi / 180.0, std::max(0.5 * pi / 180.0, 2.0 * (double)maxrad));
+    std::vector<int32_t> boff, bcnt;
+    CellGrid G;
+    int n_bands, n_cells;
+    make_bands(cell, boff, bcnt, G.hb, n_bands, n_cells);
+    G.n_bands = n_bands;
+    G.n_cells = n_cells;
+    int32_t *d_bands;
+    GET(S_BANDS, 2 * n_bands + 1, d_bands);
+    CUDA_TRY(cudaMemcpyAsync(d_bands, boff.data(), (n_bands + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_bands + n_bands + 1, bcnt.data(), n_bands * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    G.band_off = d_bands;
+    G.band_n = d_bands + n_bands + 1;
+    // ---- chunks of batches ----------------------------------------------------
+    double budget = (opt.mem_budget_gb > 0 ? opt.mem_budget_gb : 8.0) * 1e9;
+    int64_t per_batch = 48 * n;
+    int32_t C = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)(budget / per_batch)));
+    // keep the cell CSR of a chunk modest
+    C = (int32_t)std::max<int64_t>(1, std::min<int64_t>(C, 200000000LL / std::max(1, n_cells)));
+    double *stop_states;
+    GET(S_STOPSTATES, (size_t)C * 6 * n, stop_states);
+    int32_t *frame_cnt;
+    GET(S_FRAMECNT, nf, frame_cnt);
+    CUDA_TRY(cudaMemsetAsync(frame_cnt, 0, nf * sizeof(int32_t), st));
+    unsigned long long cand_cap = ctx->slot[S_CAND].bytes / sizeof(uint2);
+    if (cand_cap < (unsigned long long)(4 * n + 1024)) cand_cap = 4 * n + 1024;
+    unsigned long long hit_cap = ctx->slot[S_HITTMP].bytes / sizeof(kete_hit);
+    if (hit_cap < (unsigned long long)(nf + 1024)) hit_cap = nf + 1024;
+    kete_hit *hit_tmp;
+    GET(S_HITTMP, hit_cap, hit_tmp);
+    hit_cap = ctx->slot[S_HITTMP].bytes / sizeof(kete_hit);
+    unsigned long long hits_total = 0, cands_total = 0;
+    for (int32_t k0 = 0; k0 < nb; k0 += C) {
+        const int32_t k1 = std::min(nb, k0 + C), nk = k1 - k0;
+        const int32_t e0 = h_first[k0], e1 = h_first[k1];
+        const int32_t nek = e1 - e0;
+        // propagation to the batch midpoints of this chunk
+        prop_event(ctx, true);
+        CUDA_TRY(launch_propagate(ctx->E, F, cs, B.t_ref + k0, nk, stop_states, n, false, ctx->d_ctr, st));
+        prop_event(ctx, false);
+        launches++;
+        // exposures of the chunk into sky cells
+        const int64_t nkeys = (int64_t)nk * n_cells;
+        int32_t *ckey, *ccnt, *ccur, *cexp; int64_t *cstart;
+        GET(S_CELLKEY, nek, ckey);
+        GET(S_CELLCNT, nkeys, ccnt);
+        GET(S_CELLCUR, nkeys, ccur);
+        GET(S_CELLSTART, nkeys + 1, cstart);
+        GET(S_CELLEXP, nek, cexp);
+        GET(S_SCANTMP, std::max(scan_tmp_elems(nkeys), scan_tmp_elems(nf)), scan_tmp);
+        CUDA_TRY(cudaMemsetAsync(ccnt, 0, nkeys * sizeof(int32_t), st));
+        CUDA_TRY(cudaMemsetAsync(ccur, 0, nkeys * sizeof(int32_t), st));
+        CUDA_TRY(fov_cell_keys(X, G, e0, e1, k0, ckey, ccnt, st));
+        CUDA_TRY(exclusive_scan(ccnt, nkeys, cstart, scan_tmp, st));
+        CUDA_TRY(fov_cell_scatter(e0, e1, ckey, cstart, ccur, cexp, st));
+        launches += 4;
+        // candidate (exposure, body) pairs
+        int32_t *exp_cnt;
+        GET(S_EXPCNT, ne, exp_cnt);
+        unsigned long long ncand = 0;
+        for (int attempt = 0; attempt < 3; attempt++) {
+            uint2 *cand;
+            GET(S_CAND, cand_cap, cand);
+            cand_cap = ctx->slot[S_CAND].bytes / sizeof(uint2);
+            CUDA_TRY(cudaMemsetAsync(exp_cnt + e0, 0, nek * sizeof(int32_t), st));
+            CUDA_TRY(cudaMemsetAsync(&ctx->d_ctr->candidates, 0, sizeof(unsigned long long), st));
+            CandArgs ca;
+            ca.X = X; ca.B = B; ca.G = G; ca.stop_states = stop_states; ca.n = n; ca.k0 = k0;
+            ca.nk = nk; ca.cell_start = cstart; ca.cell_exp = cexp; ca.cand = cand;
+            ca.cap = cand_cap; ca.exp_cnt = exp_cnt; ca.ctr = ctx->d_ctr; ca.mu_sun = ctx->E.gm[0];
+            CUDA_TRY(fov_candidates(ca, st));
+            launches++;
+            CUDA_TRY(cudaMemcpyAsync(&ncand, &ctx->d_ctr->candidates, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            if (ncand <= cand_cap) break;
+            cand_cap = ncand + ncand / 2 + 1024;
+        }
+        if (ncand > cand_cap)
+            return fail(ctx, KETE_ERR_NOMEM, "candidate buffer could not grow to %llu pairs", ncand);
+        cands_total += ncand;
+        int64_t *exp_off; int32_t *exp_cur, *cand_body;
+        GET(S_EXPOFF, nek + 1, exp_off);
+        GET(S_EXPCUR, nek, exp_cur);
+        GET(S_CANDBODY, ncand, cand_body);
+        CUDA_TRY(exclusive_scan(exp_cnt + e0, nek, exp_off, scan_tmp, st));
+        CUDA_TRY(cudaMemsetAsync(exp_cur, 0, nek * sizeof(int32_t), st));
+        CUDA_TRY(fov_cand_scatter((const uint2 *)ctx->slot[S_CAND].p, ncand, exp_off, e0, exp_cur, cand_body, st));
+        launches += 3;
+        // exact two-body + light time + polygon test
+        for (int attempt = 0; attempt < 3; attempt++) {
+            CUDA_TRY(cudaMemcpyAsync(&ctx->d_ctr->hits, &hits_total, sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+            ExactArgs xa;
+            xa.E = ctx->E; xa.X = X; xa.B = B; xa.frames = frames; xa.faux = faux;
+            xa.stop_states = stop_states; xa.n = n; xa.k0 = k0; xa.e_begin = e0; xa.e_end = e1;
+            xa.exp_off = exp_off; xa.cand_body = cand_body; xa.exp_first = exp_first;
+            xa.hits = hit_tmp; xa.cap = hit_cap; xa.frame_cnt = frame_cnt; xa.status = cs.status;
+            xa.ctr = ctx->d_ctr;
+            CUDA_TRY(fov_exact(xa, ctx->n_sm, st));
+            launches++;
+            unsigned long long nh = 0;
+            CUDA_TRY(cudaMemcpyAsync(&nh, &ctx->d_ctr->hits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            if (nh <= hit_cap) {
+                hits_total = nh;
+                break;
+            }
+            // grow the hit buffer, keep earlier chunks' hits, redo this chunk
+            int32_t fa = 0, fb = 0;
+            CUDA_TRY(cudaMemcpy(&fa, exp_first + e0, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaMemcpy(&fb, exp_first + e1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaMemsetAsync(frame_cnt + fa, 0, (size_t)(fb - fa) * sizeof(int32_t), st));
+            unsigned long long want = nh + nh / 2 + 1024;
+            kete_hit *bigger = nullptr;
+            CUDA_TRY(cudaMalloc(&bigger, want * sizeof(kete_hit)));
+            if (hits_total)
+                CUDA_TRY(cudaMemcpyAsync(bigger, hit_tmp, hits_total * sizeof(kete_hit), cudaMemcpyDeviceToDevice, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            cudaFree(ctx->slot[S_HITTMP].p);
+            ctx->slot[S_HITTMP].p = bigger;
+            ctx->slot[S_HITTMP].bytes = want * sizeof(kete_hit);
+            hit_tmp = bigger;
+            hit_cap = want;
+        }
+        if (hits_total > hit_cap)
+            return fail(ctx, KETE_ERR_NOMEM, "hit buffer could not grow to %llu hits", hits_total);
+    }
+    ctx->stats.n_batches = nb;
+    ctx->stats.n_exposures = ne;
+    ctx->stats.n_candidates = (int64_t)cands_total;
+    ctx->stats.n_hits = (int64_t)hits_total;
+    *n_hits = (int64_t)hits_total;
+    CUDA_TRY(launch_chain_finish(cs, nullptr, nullptr, status, st));
+    launches++;
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (ctx->h_ctr->error_flags & 32) {
+        ctx->stats.launches = launches;
+        return fail(ctx, KETE_ERR_EPHEM_SPAN, "a batch midpoint lies outside the ephemeris table");
+    }
+    if ((int64_t)hits_total > capacity) {
+        r = stats_end(ctx);
+        stats_collect(ctx);
+        ctx->stats.launches = launches;
+        return fail(ctx, KETE_ERR_CAPACITY, "hit buffer holds %lld, %llu needed", (long long)capacity,
+                    hits_total);
+    }
+    if (hits_total > 0) {
+        int64_t *frame_off; int32_t *frame_cur; kete_hit *grouped;
+        GET(S_FRAMEOFF, nf + 1, frame_off);
+        GET(S_FRAMECUR, nf, frame_cur);
+        GET(S_HITGROUP, hits_total, grouped);
+        CUDA_TRY(exclusive_scan(frame_cnt, nf, frame_off, scan_tmp, st));
+        CUDA_TRY(cudaMemsetAsync(frame_cur, 0, nf * sizeof(int32_t), st));
+        CUDA_TRY(fov_order_hits(hit_tmp, hits_total, frame_off, nf, frame_cur, grouped, hits, ctx->n_sm, st));
+        launches += 4;
+    }
+    r = stats_end(ctx);
+    if (r != KETE_OK) return r;
+    stats_collect(ctx);
+    ctx->stats.n_batches = nb;
+    ctx->stats.n_exposures = ne;
+    ctx->stats.n_candidates = (int64_t)cands_total;
+    ctx->stats.n_hits = (int64_t)hits_total;
+    ctx->stats.launches = launches;
+    return KETE_OK;
+}

@@ -1,0 +1,699 @@
+// kete_fov.cu -- the FoV stage of the survey path (Sec. 2, Sec. 3.1, App. A.1).
+//
+//   frame prep   validate frames, find exposure boundaries, circumscribed cap
+//                of every polygon (from its vertices n_k x n_{k+1})
+//   exposures    epoch, observer, cap covering all sub-fields
+//   batching     greedy <= span batches over epoch-sorted exposures, t_ref =
+//                midpoint of first and last epoch (Sec. 2)
+//   batch info   mean observer, observer spread, time spread, Sun state at t_ref
+//   sky cells    per batch, exposures bucketed by the sky cell of their centre
+//   candidates   per (body, batch): conservative motion + parallax radius,
+//                enumerate nearby cells, cap test against each exposure
+//   exact test   per candidate: heliocentric universal-variable two-body from
+//                t_ref, light-delay iteration, polygon test of every
+//                sub-field (strict n.u > 0), RA/Dec
+//   ordering     hits grouped by frame, sorted by body within a frame
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "kete_device.cuh"
+#include "kete_fov.h"
+
+namespace kete {
+
+constexpr float kPadF = 2e-4f;        // radians added to every float cap test
+constexpr double kSunSpeedMax = 5e-5; // bound on the barycentric Sun speed, AU/day
+
+__device__ __forceinline__ void set_flag(DevCounters *c, int bit) { atomicOr(&c->error_flags, 1 << bit); }
+
+__device__ __forceinline__ double dot3(const double *a, const double *b)
+{
+    return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+
+// warp-aggregated append: returns this lane's slot
+__device__ __forceinline__ unsigned long long agg_append(unsigned long long *ctr)
+{
+    unsigned mask = __activemask();
+    int leader = __ffs(mask) - 1;
+    int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+// ---------------------------------------------------------------------------
+// frames
+// ---------------------------------------------------------------------------
+__global__ void k_frame_prep(const kete_frame *__restrict__ fr, int64_t nf, int64_t n_obs,
+                             int32_t *__restrict__ is_start, double *__restrict__ fcen,
+                             float4 *__restrict__ faux, DevCounters *ctr)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const kete_frame f = fr[i];
+    bool start = (i == 0) || (fr[i - 1].exposure_id != f.exposure_id);
+    is_start[i] = start ? 1 : 0;
+    if (i > 0) {
+        double pe = fr[i - 1].epoch;
+        if (!(f.epoch >= pe)) set_flag(ctr, 0);
+        if (!start && (pe != f.epoch || fr[i - 1].observer_idx != f.observer_idx)) set_flag(ctr, 1);
+    }
+    if (f.observer_idx < 0 || f.observer_idx >= n_obs) set_flag(ctr, 2);
+    int ne = f.n_edges;
+    if (ne < 3 || ne > KETE_MAX_EDGES) {
+        set_flag(ctr, 3);
+        ne = 3;
+    }
+    if (!isfinite(f.epoch)) set_flag(ctr, 4);
+    // vertices v_k = n_k x n_{k+1}, oriented towards the sum of inward normals
+    double sn[3] = {0, 0, 0};
+    for (int k = 0; k < ne; k++)
+        for (int c = 0; c < 3; c++) sn[c] += f.normals[k][c];
+    double cen[3] = {0, 0, 0};
+    double vx[KETE_MAX_EDGES][3];
+    bool bad = false;
+    for (int k = 0; k < ne; k++) {
+        const double *a = f.normals[k], *b = f.normals[(k + 1) % ne];
+        double v0 = a[1] * b[2] - a[2] * b[1];
+        double v1 = a[2] * b[0] - a[0] * b[2];
+        double v2 = a[0] * b[1] - a[1] * b[0];
+        double vn = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+        if (!(vn > 0.0) || !isfinite(vn)) bad = true;
+        if (v0 * sn[0] + v1 * sn[1] + v2 * sn[2] < 0.0) vn = -vn;
+        vx[k][0] = v0 / vn;
+        vx[k][1] = v1 / vn;
+        vx[k][2] = v2 / vn;
+        for (int c = 0; c < 3; c++) cen[c] += vx[k][c];
+    }
+    double cn = sqrt(dot3(cen, cen));
+    double rad = 0.0;
+    if (bad || !(cn > 0.0)) {
+        set_flag(ctr, 4);
+        cen[0] = 1.0; cen[1] = 0.0; cen[2] = 0.0;
+        rad = kPi;
+    } else {
+        for (int c = 0; c < 3; c++) cen[c] /= cn;
+        for (int k = 0; k < ne; k++) {
+            double d = fmin(1.0, fmax(-1.0, dot3(cen, vx[k])));
+            rad = fmax(rad, acos(d));
+        }
+        // a polygon wider than ~80 deg is treated as covering everything
+        if (rad > 1.4) rad = kPi;
+    }
+    fcen[3 * i + 0] = cen[0];
+    fcen[3 * i + 1] = cen[1];
+    fcen[3 * i + 2] = cen[2];
+    fcen[3 * nf + i] = rad;
+    float cr = (rad >= kPi) ? -2.0f : cosf((float)rad + kPadF);
+    faux[i] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], cr);
+}
+
+__global__ void k_exposure_first(const int32_t *__restrict__ is_start,
+                                 const int64_t *__restrict__ ex, int64_t nf,
+                                 int32_t *__restrict__ exp_first)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    if (is_start[i]) exp_first[ex[i]] = (int32_t)i;
+    if (i == nf - 1) exp_first[ex[i] + is_start[i]] = (int32_t)nf;
+}
+
+__global__ void k_exposure_prep(const kete_frame *__restrict__ fr, int64_t nf,
+                                const double *__restrict__ observers,
+                                const double *__restrict__ fcen, const int32_t *__restrict__ exp_first,
+                                int64_t ne, ExpArrays X, unsigned int *max_rad_bits)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    int32_t f0 = exp_first[e], f1 = exp_first[e + 1];
+    const kete_frame &f = fr[f0];
+    X.epoch[e] = f.epoch;
+    int64_t oi = f.observer_idx;
+    for (int c = 0; c < 3; c++) X.obs[3 * e + c] = observers[3 * oi + c];
+    double s[3] = {0, 0, 0};
+    bool huge = false;
+    for (int32_t k = f0; k < f1; k++) {
+        for (int c = 0; c < 3; c++) s[c] += fcen[3 * k + c];
+        if (fcen[3 * nf + k] >= kPi) huge = true;
+    }
+    double sn = sqrt(dot3(s, s));
+    double rad = 0.0;
+    if (!(sn > 0.0)) huge = true;
+    else {
+        for (int c = 0; c < 3; c++) s[c] /= sn;
+        for (int32_t k = f0; k < f1; k++) {
+            double d = fmin(1.0, fmax(-1.0, dot3(s, fcen + 3 * k)));
+            rad = fmax(rad, acos(d) + fcen[3 * nf + k]);
+        }
+    }
+    if (huge || rad > 1.4) {
+        rad = kPi;
+        s[0] = 1.0; s[1] = 0.0; s[2] = 0.0;
+    }
+    for (int c = 0; c < 3; c++) X.cen[3 * e + c] = s[c];
+    X.rad[e] = rad;
+    float r = (float)rad;
+    X.cs[e] = make_float2(rad >= kPi ? -2.0f : cosf(r), rad >= kPi ? 0.0f : sinf(r));
+    atomicMax(max_rad_bits, __float_as_uint(r));
+}
+
+// next[e]: first exposure that cannot join a batch starting at e (Sec. 2)
+__global__ void k_batch_next(const double *__restrict__ ep, int64_t ne, double span,
+                             int32_t *__restrict__ next)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    double t0 = ep[e];
+    int64_t lo = e + 1, hi = ne;   // first j in [lo, hi) with !(ep[j]==t0 || ep[j]-t0 < span)
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        double tj = ep[mid];
+        bool joins = (tj == t0) || (tj - t0 < span);
+        if (joins) lo = mid + 1;
+        else hi = mid;
+    }
+    next[e] = (int32_t)lo;
+}
+
+__global__ void k_batch_walk(const double *__restrict__ ep, const int32_t *__restrict__ next,
+                             int64_t ne, int32_t *__restrict__ batch_first,
+                             double *__restrict__ t_ref, int32_t *n_batches)
+{
+    int32_t e = 0, k = 0;
+    while (e < ne) {
+        int32_t nx = next[e];
+        batch_first[k] = e;
+        t_ref[k] = 0.5 * (ep[e] + ep[nx - 1]);
+        k++;
+        e = nx;
+    }
+    batch_first[k] = (int32_t)ne;
+    *n_batches = k;
+}
+
+// one block per batch: observer mean/spread, time spread, Sun state at t_ref
+__global__ void k_batch_info(EphemDev E, ExpArrays X, BatchArrays B, int32_t n_batches,
+                             DevCounters *ctr)
+{
+    const int k = blockIdx.x;
+    if (k >= n_batches) return;
+    const int32_t e0 = B.first[k], e1 = B.first[k + 1];
+    const double tr = B.t_ref[k];
+    __shared__ double red[4][32];
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        s0 += X.obs[3 * e + 0];
+        s1 += X.obs[3 * e + 1];
+        s2 += X.obs[3 * e + 2];
+        X.batch[e] = k;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) { red[0][w] = s0; red[1][w] = s1; red[2][w] = s2; }
+    __syncthreads();
+    __shared__ double O[3];
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int q = 0; q < nw; q++) { a += red[0][q]; b += red[1][q]; c += red[2][q]; }
+        double inv = 1.0 / (double)(e1 - e0);
+        O[0] = a * inv; O[1] = b * inv; O[2] = c * inv;
+    }
+    __syncthreads();
+    double robs = 0, tsp = 0, rmax = 0;
+    for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        double d0 = X.obs[3 * e] - O[0], d1 = X.obs[3 * e + 1] - O[1], d2 = X.obs[3 * e + 2] - O[2];
+        robs = fmax(robs, sqrt(d0 * d0 + d1 * d1 + d2 * d2));
+        tsp = fmax(tsp, fabs(X.epoch[e] - tr));
+        rmax = fmax(rmax, X.rad[e]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        robs = fmax(robs, __shfl_xor_sync(0xffffffffu, robs, o));
+        tsp = fmax(tsp, __shfl_xor_sync(0xffffffffu, tsp, o));
+        rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    }
+    __syncthreads();
+    if (l == 0) { red[0][w] = robs; red[1][w] = tsp; red[2][w] = rmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int q = 0; q < nw; q++) {
+            a = fmax(a, red[0][q]); b = fmax(b, red[1][q]); c = fmax(c, red[2][q]);
+        }
+        for (int q = 0; q < 3; q++) B.O[3 * k + q] = O[q];
+        B.robs[k] = a * (1.0 + 1e-12) + 1e-12;
+        B.tspan[k] = b;
+        B.rmax[k] = c;
+        Seg g;
+        double p[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+        if (ephem_seg(E, tr, g)) {
+            cheb_pos_vel(ephem_coef(E, 0, g.s), E.n_coef, g.tau, 2.0 * E.inv_seg, p, v);
+        } else {
+            set_flag(ctr, 5);
+        }
+        for (int q = 0; q < 3; q++) { B.sun[6 * k + q] = p[q]; B.sun[6 * k + 3 + q] = v[q]; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sky cells: latitude bands of height hb, n_j cells of longitude per band
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_of(const CellGrid &G, double lat, double lon)
+{
+    int j = (int)floor((lat + 0.5 * kPi) / G.hb);
+    j = j < 0 ? 0 : (j >= G.n_bands ? G.n_bands - 1 : j);
+    int nj = G.band_n[j];
+    int i = (int)floor(lon / (kTwoPi / nj));
+    i = i < 0 ? 0 : (i >= nj ? nj - 1 : i);
+    return G.band_off[j] + i;
+}
+
+__global__ void k_cell_keys(ExpArrays X, CellGrid G, int32_t e_begin, int32_t e_end, int32_t k0,
+                            int32_t *__restrict__ key, int32_t *__restrict__ cnt)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t e = e_begin + (int32_t)q;
+    if (e >= e_end) return;
+    const double *c = X.cen + 3 * e;
+    double lat = asin(fmin(1.0, fmax(-1.0, c[2])));
+    double lon = atan2(c[1], c[0]);
+    if (lon < 0.0) lon += kTwoPi;
+    int kk = (X.batch[e] - k0) * G.n_cells + cell_of(G, lat, lon);
+    key[q] = kk;
+    atomicAdd(&cnt[kk], 1);
+}
+
+__global__ void k_cell_scatter(int32_t e_begin, int32_t e_end, const int32_t *__restrict__ key,
+                               const int64_t *__restrict__ start, int32_t *__restrict__ cursor,
+                               int32_t *__restrict__ cell_exp)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t e = e_begin + (int32_t)q;
+    if (e >= e_end) return;
+    int kk = key[q];
+    int pos = atomicAdd(&cursor[kk], 1);
+    cell_exp[start[kk] + pos] = e;
+}
+
+// ---------------------------------------------------------------------------
+// candidates: thread per (body, batch of the chunk)
+// ---------------------------------------------------------------------------
+struct CandCtx {
+    ExpArrays X;
+    BatchArrays B;
+    CellGrid G;
+    const double *stop_states;   // [C][6][n]
+    int64_t n;
+    int32_t k0, nk;              // chunk batches [k0, k0+nk)
+    const int64_t *cell_start;   // [nk * n_cells + 1]
+    const int32_t *cell_exp;
+    uint2 *cand;                 // (exposure, body)
+    unsigned long long cap;
+    int32_t *exp_cnt;            // per exposure (global index)
+    DevCounters *ctr;
+    double mu_sun;
+};
+
+__device__ __forceinline__ void test_exposure(const CandCtx &C, int32_t e, const double p[3],
+                                              double s, int32_t body)
+{
+    const double *o = C.X.obs + 3 * e;
+    double q0 = p[0] - o[0], q1 = p[1] - o[1], q2 = p[2] - o[2];
+    float Q = (float)sqrt(q0 * q0 + q1 * q1 + q2 * q2);
+    const double *c = C.X.cen + 3 * e;
+    float2 cs = C.X.cs[e];
+    bool pass;
+    float sig = (float)s / Q;
+    if (cs.x < -1.5f || sig >= 0.999f) {
+        pass = true;
+    } else {
+        float cosang = (float)(q0 * c[0] + q1 * c[1] + q2 * c[2]) / Q;
+        // cos(r + delta) with sin(delta) = s/Q, padded by kPadF
+        float cd = sqrtf(1.0f - sig * sig);
+        float lim = cs.x * cd - cs.y * sig;       // cos(r + delta)
+        pass = cosang >= lim - kPadF * (cs.y * cd + cs.x * sig) - 1e-6f - kPadF;
+    }
+    if (pass) {
+        unsigned long long slot = agg_append(&C.ctr->candidates);
+        if (slot < C.cap) C.cand[slot] = make_uint2((unsigned)e, (unsigned)body);
+        atomicAdd(&C.exp_cnt[e], 1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_candidates(CandCtx C)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= C.n * C.nk) return;
+    const int32_t kl = (int32_t)(idx / C.n);
+    const int32_t i = (int32_t)(idx - (int64_t)kl * C.n);
+    const int32_t k = C.k0 + kl;
+    const double *st = C.stop_states + (int64_t)kl * 6 * C.n;
+    double p[3] = {st[i], st[C.n + i], st[2 * C.n + i]};
+    if (!isfinite(p[0])) return;
+    double v[3] = {st[3 * C.n + i], st[4 * C.n + i], st[5 * C.n + i]};
+    const double *O = C.B.O + 3 * k;
+    const double *sun = C.B.sun + 6 * k;
+    const double robs = C.B.robs[k];
+    double d[3] = {p[0] - O[0], p[1] - O[1], p[2] - O[2]};
+    double D = sqrt(dot3(d, d));
+    double h[3] = {p[0] - sun[0], p[1] - sun[1], p[2] - sun[2]};
+    double vh[3] = {v[0] - sun[3], v[1] - sun[4], v[2] - sun[5]};
+    double rh = sqrt(dot3(h, h));
+    double vn = sqrt(dot3(vh, vh));
+    // time offsets from t_ref: frame epochs within tspan, light time below tau_max
+    double T = C.B.tspan[k] + (D + robs + 1.0) * kInvC;
+    // heliocentric displacement bound valid while the body stays beyond rh/2
+    double disp = vn * T + 2.0 * C.mu_sun * T * T / (rh * rh);
+    double s = disp + kSunSpeedMax * T + 1e-9;
+    bool all = (disp > 0.5 * rh) || (s + robs >= 0.99 * D);
+    double rho = all ? kPi : asin((s + robs) / D);
+    double R = rho + C.B.rmax[k] + 4.0 * (double)kPadF;
+    const int32_t e0 = C.B.first[k], e1 = C.B.first[k + 1];
+    if (all || R >= 1.2) {
+        for (int32_t e = e0; e < e1; e++) test_exposure(C, e, p, all ? 1e30 : s, i);
+        return;
+    }
+    // enumerate the cells within R of the body's direction from the mean observer
+    const double lat = asin(fmin(1.0, fmax(-1.0, d[2] / D)));
+    double lon = atan2(d[1], d[0]);
+    if (lon < 0.0) lon += kTwoPi;
+    const CellGrid &G = C.G;
+    int jlo = (int)floor((lat - R + 0.5 * kPi) / G.hb);
+    int jhi = (int)floor((lat + R + 0.5 * kPi) / G.hb);
+    jlo = jlo < 0 ? 0 : jlo;
+    jhi = jhi >= G.n_bands ? G.n_bands - 1 : jhi;
+    double dlon;
+    if (fabs(lat) + R >= 0.5 * kPi - 1e-9) dlon = kPi;
+    else dlon = asin(fmin(1.0, sin(R) / cos(lat))) + 4.0 * (double)kPadF;
+    const int64_t base = (int64_t)kl * G.n_cells;
+    for (int j = jlo; j <= jhi; j++) {
+        const int nj = G.band_n[j];
+        const double w = kTwoPi / nj;
+        int64_t lo_key, hi_key;   // inclusive cell ranges (up to two)
+        int ilo = (int)floor((lon - dlon) / w), ihi = (int)floor((lon + dlon) / w);
+        int nr = 0;
+        int64_t rl[2], rh2[2];
+        if (dlon >= kPi || ihi - ilo + 1 >= nj) {
+            rl[0] = 0; rh2[0] = nj - 1; nr = 1;
+        } else if (ilo < 0) {
+            rl[0] = 0; rh2[0] = ihi; rl[1] = ilo + nj; rh2[1] = nj - 1; nr = 2;
+        } else if (ihi >= nj) {
+            rl[0] = ilo; rh2[0] = nj - 1; rl[1] = 0; rh2[1] = ihi - nj; nr = 2;
+        } else {
+            rl[0] = ilo; rh2[0] = ihi; nr = 1;
+        }
+        for (int r = 0; r < nr; r++) {
+            lo_key = base + G.band_off[j] + rl[r];
+            hi_key = base + G.band_off[j] + rh2[r];
+            int64_t a = C.cell_start[lo_key], b = C.cell_start[hi_key + 1];
+            for (int64_t q = a; q < b; q++) test_exposure(C, C.cell_exp[q], p, s, i);
+        }
+    }
+}
+
+__global__ void k_cand_scatter(const uint2 *__restrict__ cand, unsigned long long nc,
+                               const int64_t *__restrict__ exp_off, int32_t e_begin,
+                               int32_t *__restrict__ cursor, int32_t *__restrict__ cand_body)
+{
+    unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nc) return;
+    uint2 c = cand[q];
+    int32_t el = (int32_t)c.x - e_begin;
+    int pos = atomicAdd(&cursor[el], 1);
+    cand_body[exp_off[el] + pos] = (int32_t)c.y;
+}
+
+// ---------------------------------------------------------------------------
+// exact test: one warp per exposure, lanes over its candidate bodies
+// ---------------------------------------------------------------------------
+struct ExactCtx {
+    EphemDev E;
+    ExpArrays X;
+    BatchArrays B;
+    const kete_frame *frames;
+    const float4 *faux;
+    const double *stop_states;
+    int64_t n;
+    int32_t k0, e_begin, e_end;
+    const int64_t *exp_off;      // chunk-relative
+    const int32_t *cand_body;
+    const int32_t *exp_first;
+    kete_hit *hits;
+    unsigned long long cap;
+    int32_t *frame_cnt;
+    int32_t *status;
+    DevCounters *ctr;
+    double cos_eps, sin_eps;
+};
+
+// heliocentric position at t_ref + dt (Sun re-added at that epoch)
+__device__ __forceinline__ bool twobody_pos(const EphemDev &E, double mu, double sqmu,
+                                            const double hr[3], const double hv[3], double t_ref,
+                                            double dt, double &chi, double pos[3])
+{
+    double r[3], v[3];
+    bool ok = kepler_uv(mu, sqmu, hr, hv, dt, chi, r, v);
+    Seg g;
+    double sp[3] = {0, 0, 0};
+    if (ephem_seg(E, t_ref + dt, g)) cheb_pos(ephem_coef(E, 0, g.s), E.n_coef, g.tau, sp);
+    else ok = false;
+    pos[0] = sp[0] + r[0];
+    pos[1] = sp[1] + r[1];
+    pos[2] = sp[2] + r[2];
+    return ok;
+}
+
+__global__ void __launch_bounds__(128) k_exact(ExactCtx C)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t nexp = C.e_end - C.e_begin;
+    const int32_t warp = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t nwarps = (int32_t)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const double mu = C.E.gm[0];
+    const double sqmu = sqrt(mu);
+    for (int32_t el = warp; el < nexp; el += nwarps) {
+        const int32_t e = C.e_begin + el;
+        const int32_t k = C.X.batch[e];
+        const int32_t kl = k - C.k0;
+        const double t_ref = C.B.t_ref[k];
+        const double dt_obs = C.X.epoch[e] - t_ref;
+        const double o[3] = {C.X.obs[3 * e], C.X.obs[3 * e + 1], C.X.obs[3 * e + 2]};
+        const double *sun = C.B.sun + 6 * k;
+        const int32_t f0 = C.exp_first[e], f1 = C.exp_first[e + 1];
+        const int64_t c0 = C.exp_off[el], c1 = C.exp_off[el + 1];
+        const double *st = C.stop_states + (int64_t)kl * 6 * C.n;
+        for (int64_t q = c0 + lane; q < c1; q += 32) {
+            const int32_t i = C.cand_body[q];
+            double hr[3], hv[3];
+            for (int c = 0; c < 3; c++) {
+                hr[c] = st[c * C.n + i] - sun[c];
+                hv[c] = st[(3 + c) * C.n + i] - sun[3 + c];
+            }
+            // light delay (Sec. 2): tau0 = |r(t)-o|/c, three fixed iterations
+            double chi = 0.0, pos[3];
+            bool ok = twobody_pos(C.E, mu, sqmu, hr, hv, t_ref, dt_obs, chi, pos);
+            double u[3] = {pos[0] - o[0], pos[1] - o[1], pos[2] - o[2]};
+            double tau = sqrt(dot3(u, u)) * kInvC;
+            for (int it = 0; it < 3; it++) {
+                ok &= twobody_pos(C.E, mu, sqmu, hr, hv, t_ref, dt_obs - tau, chi, pos);
+                u[0] = pos[0] - o[0]; u[1] = pos[1] - o[1]; u[2] = pos[2] - o[2];
+                tau = sqrt(dot3(u, u)) * kInvC;
+            }
+            ok &= twobody_pos(C.E, mu, sqmu, hr, hv, t_ref, dt_obs - tau, chi, pos);
+            u[0] = pos[0] - o[0]; u[1] = pos[1] - o[1]; u[2] = pos[2] - o[2];
+            if (!ok) {
+                if (C.status) atomicCAS(&C.status[i], KETE_BODY_OK, KETE_BODY_KEPLER_CAP);
+                continue;
+            }
+            const double un = sqrt(dot3(u, u));
+            const float uf[3] = {(float)(u[0] / un), (float)(u[1] / un), (float)(u[2] / un)};
+            bool have_radec = false;
+            double ra = 0.0, dec = 0.0;
+            for (int32_t f = f0; f < f1; f++) {
+                const float4 a = C.faux[f];
+                if (a.x * uf[0] + a.y * uf[1] + a.z * uf[2] < a.w) continue;
+                const kete_frame &fr = C.frames[f];
+                bool inside = true;
+                for (int kq = 0; kq < fr.n_edges; kq++) {
+                    const double *nv = fr.normals[kq];
+                    if (!(fma(nv[0], u[0], fma(nv[1], u[1], nv[2] * u[2])) > 0.0)) inside = false;
+                }
+                if (!inside) continue;
+                if (!have_radec) {
+                    radec(u, C.cos_eps, C.sin_eps, ra, dec);
+                    have_radec = true;
+                }
+                unsigned long long slot = agg_append(&C.ctr->hits);
+                if (slot < C.cap) {
+                    kete_hit hh;
+                    hh.frame = f;
+                    hh.body = i;
+                    hh.flags = 0;
+                    hh.ra = ra;
+                    hh.dec = dec;
+                    C.hits[slot] = hh;
+                }
+                atomicAdd(&C.frame_cnt[f], 1);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ordering: group hits by frame, sort each frame's hits by body
+// ---------------------------------------------------------------------------
+__global__ void k_hit_scatter(const kete_hit *__restrict__ src, unsigned long long nh,
+                              const int64_t *__restrict__ frame_off, int32_t *__restrict__ cursor,
+                              kete_hit *__restrict__ dst)
+{
+    unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nh) return;
+    kete_hit h = src[q];
+    int pos = atomicAdd(&cursor[h.frame], 1);
+    dst[frame_off[h.frame] + pos] = h;
+}
+
+// warp per frame: rank of each hit = number of hits of the frame with a
+// smaller body index (body indices are unique within a frame)
+__global__ void k_hit_rank(const kete_hit *__restrict__ src, const int64_t *__restrict__ frame_off,
+                           int64_t nf, kete_hit *__restrict__ dst)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t f = warp; f < nf; f += nwarps) {
+        const int64_t a = frame_off[f], b = frame_off[f + 1];
+        const int64_t m = b - a;
+        if (m == 0) continue;
+        if (m == 1) {
+            if (lane == 0) dst[a] = src[a];
+            continue;
+        }
+        for (int64_t j = lane; j < m; j += 32) {
+            const int32_t bj = src[a + j].body;
+            int64_t rank = 0;
+            for (int64_t q = 0; q < m; q++) rank += (src[a + q].body < bj) ? 1 : 0;
+            dst[a + rank] = src[a + j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+static unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+#define KLAUNCH(...)                            \
+    do {                                        \
+        __VA_ARGS__;                            \
+        cudaError_t _e = cudaGetLastError();    \
+        if (_e != cudaSuccess) return _e;       \
+    } while (0)
+
+cudaError_t fov_frame_prep(const kete_frame *frames, int64_t nf, int64_t n_obs, int32_t *is_start,
+                           double *fcen, float4 *faux, DevCounters *ctr, cudaStream_t st)
+{
+    if (nf > 0) KLAUNCH(k_frame_prep<<<grid_for(nf, 128), 128, 0, st>>>(frames, nf, n_obs, is_start, fcen, faux, ctr));
+    return cudaSuccess;
+}
+
+cudaError_t fov_exposure_first(const int32_t *is_start, const int64_t *ex, int64_t nf,
+                               int32_t *exp_first, cudaStream_t st)
+{
+    if (nf > 0) KLAUNCH(k_exposure_first<<<grid_for(nf, 256), 256, 0, st>>>(is_start, ex, nf, exp_first));
+    return cudaSuccess;
+}
+
+cudaError_t fov_exposure_prep(const kete_frame *frames, int64_t nf, const double *observers,
+                              const double *fcen, const int32_t *exp_first, int64_t ne,
+                              ExpArrays X, unsigned int *max_rad_bits, cudaStream_t st)
+{
+    if (ne > 0) KLAUNCH(k_exposure_prep<<<grid_for(ne, 128), 128, 0, st>>>(frames, nf, observers, fcen, exp_first, ne, X, max_rad_bits));
+    return cudaSuccess;
+}
+
+cudaError_t fov_batches(const double *ep, int64_t ne, double span, int32_t *next,
+                        BatchArrays B, int32_t *n_batches, cudaStream_t st)
+{
+    if (ne <= 0) return cudaSuccess;
+    KLAUNCH(k_batch_next<<<grid_for(ne, 256), 256, 0, st>>>(ep, ne, span, next));
+    KLAUNCH(k_batch_walk<<<1, 1, 0, st>>>(ep, next, ne, B.first, B.t_ref, n_batches));
+    return cudaSuccess;
+}
+
+cudaError_t fov_batch_info(const EphemDev &E, ExpArrays X, BatchArrays B, int32_t nb,
+                           DevCounters *ctr, cudaStream_t st)
+{
+    if (nb > 0) KLAUNCH(k_batch_info<<<nb, 256, 0, st>>>(E, X, B, nb, ctr));
+    return cudaSuccess;
+}
+
+cudaError_t fov_cell_keys(ExpArrays X, CellGrid G, int32_t e0, int32_t e1, int32_t k0,
+                          int32_t *key, int32_t *cnt, cudaStream_t st)
+{
+    if (e1 > e0) KLAUNCH(k_cell_keys<<<grid_for(e1 - e0, 256), 256, 0, st>>>(X, G, e0, e1, k0, key, cnt));
+    return cudaSuccess;
+}
+
+cudaError_t fov_cell_scatter(int32_t e0, int32_t e1, const int32_t *key, const int64_t *start,
+                             int32_t *cursor, int32_t *cell_exp, cudaStream_t st)
+{
+    if (e1 > e0) KLAUNCH(k_cell_scatter<<<grid_for(e1 - e0, 256), 256, 0, st>>>(e0, e1, key, start, cursor, cell_exp));
+    return cudaSuccess;
+}
+
+cudaError_t fov_candidates(const CandArgs &a, cudaStream_t st)
+{
+    CandCtx C;
+    C.X = a.X; C.B = a.B; C.G = a.G; C.stop_states = a.stop_states; C.n = a.n; C.k0 = a.k0;
+    C.nk = a.nk; C.cell_start = a.cell_start; C.cell_exp = a.cell_exp; C.cand = a.cand;
+    C.cap = a.cap; C.exp_cnt = a.exp_cnt; C.ctr = a.ctr; C.mu_sun = a.mu_sun;
+    int64_t tot = a.n * (int64_t)a.nk;
+    if (tot > 0) KLAUNCH(k_candidates<<<grid_for(tot, 256), 256, 0, st>>>(C));
+    return cudaSuccess;
+}
+
+cudaError_t fov_cand_scatter(const uint2 *cand, unsigned long long nc, const int64_t *exp_off,
+                             int32_t e_begin, int32_t *cursor, int32_t *cand_body, cudaStream_t st)
+{
+    if (nc > 0) KLAUNCH(k_cand_scatter<<<grid_for((int64_t)nc, 256), 256, 0, st>>>(cand, nc, exp_off, e_begin, cursor, cand_body));
+    return cudaSuccess;
+}
+
+cudaError_t fov_exact(const ExactArgs &a, int n_sm, cudaStream_t st)
+{
+    ExactCtx C;
+    C.E = a.E; C.X = a.X; C.B = a.B; C.frames = a.frames; C.faux = a.faux;
+    C.stop_states = a.stop_states; C.n = a.n; C.k0 = a.k0; C.e_begin = a.e_begin;
+    C.e_end = a.e_end; C.exp_off = a.exp_off; C.cand_body = a.cand_body;
+    C.exp_first = a.exp_first; C.hits = a.hits; C.cap = a.cap; C.frame_cnt = a.frame_cnt;
+    C.status = a.status; C.ctr = a.ctr;
+    const double eps = 84381.448 / 3600.0 * (kPi / 180.0);
+    C.cos_eps = cos(eps);
+    C.sin_eps = sin(eps);
+    int64_t nexp = a.e_end - a.e_begin;
+    if (nexp <= 0) return cudaSuccess;
+    int64_t blocks = (nexp * 32 + 127) / 128;
+    int64_t cap_blocks = (int64_t)n_sm * 16;
+    if (blocks > cap_blocks) blocks = cap_blocks;
+    KLAUNCH(k_exact<<<(unsigned)blocks, 128, 0, st>>>(C));
+    return cudaSuccess;
+}
+
+cudaError_t fov_order_hits(const kete_hit *tmp, unsigned long long nh, const int64_t *frame_off,
+                           int64_t nf, int32_t *cursor, kete_hit *grouped, kete_hit *out,
+                           int n_sm, cudaStream_t st)
+{
+    if (nh == 0) return cudaSuccess;
+    KLAUNCH(k_hit_scatter<<<grid_for((int64_t)nh, 256), 256, 0, st>>>(tmp, nh, frame_off, cursor, grouped));
+    int64_t blocks = (nf * 32 + 255) / 256;
+    if (blocks > (int64_t)n_sm * 32) blocks = (int64_t)n_sm * 32;
+    KLAUNCH(k_hit_rank<<<(unsigned)blocks, 256, 0, st>>>(grouped, frame_off, nf, out));
+    return cudaSuccess;
+}
+
+}  // namespace kete

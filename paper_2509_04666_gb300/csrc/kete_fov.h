@@ -1,0 +1,104 @@
+// kete_fov.h -- device arrays and launchers of the FoV stage (Sec. 2, Sec. 3.1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kete_impl.h"
+
+namespace kete {
+
+// per exposure (a union of sub-field polygons sharing epoch and observer)
+struct ExpArrays {
+    double *epoch;     // [E]
+    double *obs;       // [E][3]
+    double *cen;       // [E][3] unit centre of the covering cap
+    double *rad;       // [E] cap radius, rad (pi = covers everything)
+    float2 *cs;        // [E] (cos r, sin r) of the cap, cos = -2 when r = pi
+    int32_t *batch;    // [E]
+};
+
+// per batch of exposures (<= span in time, Sec. 2)
+struct BatchArrays {
+    int32_t *first;    // [K+1] first exposure of each batch
+    double *t_ref;     // [K] batch midpoint: the n-body stop
+    double *O;         // [K][3] mean observer
+    double *robs;      // [K] max distance of an exposure's observer from O
+    double *tspan;     // [K] max |t_e - t_ref|
+    double *rmax;      // [K] max exposure cap radius
+    double *sun;       // [K][6] Sun position and velocity at t_ref
+};
+
+// latitude-band sky cells
+struct CellGrid {
+    const int32_t *band_off;   // [n_bands+1] first cell of each band
+    const int32_t *band_n;     // [n_bands] cells in each band
+    double hb;                 // band height, rad
+    int32_t n_bands, n_cells;
+};
+
+struct CandArgs {
+    ExpArrays X;
+    BatchArrays B;
+    CellGrid G;
+    const double *stop_states;
+    int64_t n;
+    int32_t k0, nk;
+    const int64_t *cell_start;
+    const int32_t *cell_exp;
+    uint2 *cand;
+    unsigned long long cap;
+    int32_t *exp_cnt;
+    DevCounters *ctr;
+    double mu_sun;
+};
+
+struct ExactArgs {
+    EphemDev E;
+    ExpArrays X;
+    BatchArrays B;
+    const kete_frame *frames;
+    const float4 *faux;
+    const double *stop_states;
+    int64_t n;
+    int32_t k0, e_begin, e_end;
+    const int64_t *exp_off;
+    const int32_t *cand_body;
+    const int32_t *exp_first;
+    kete_hit *hits;
+    unsigned long long cap;
+    int32_t *frame_cnt;
+    int32_t *status;
+    DevCounters *ctr;
+};
+
+cudaError_t fov_frame_prep(const kete_frame *frames, int64_t nf, int64_t n_obs, int32_t *is_start,
+                           double *fcen, float4 *faux, DevCounters *ctr, cudaStream_t st);
+cudaError_t fov_exposure_first(const int32_t *is_start, const int64_t *ex, int64_t nf,
+                               int32_t *exp_first, cudaStream_t st);
+cudaError_t fov_exposure_prep(const kete_frame *frames, int64_t nf, const double *observers,
+                              const double *fcen, const int32_t *exp_first, int64_t ne,
+                              ExpArrays X, unsigned int *max_rad_bits, cudaStream_t st);
+cudaError_t fov_batches(const double *ep, int64_t ne, double span, int32_t *next, BatchArrays B,
+                        int32_t *n_batches, cudaStream_t st);
+cudaError_t fov_batch_info(const EphemDev &E, ExpArrays X, BatchArrays B, int32_t nb,
+                           DevCounters *ctr, cudaStream_t st);
+cudaError_t fov_cell_keys(ExpArrays X, CellGrid G, int32_t e0, int32_t e1, int32_t k0,
+                          int32_t *key, int32_t *cnt, cudaStream_t st);
+cudaError_t fov_cell_scatter(int32_t e0, int32_t e1, const int32_t *key, const int64_t *start,
+                             int32_t *cursor, int32_t *cell_exp, cudaStream_t st);
+cudaError_t fov_candidates(const CandArgs &a, cudaStream_t st);
+cudaError_t fov_cand_scatter(const uint2 *cand, unsigned long long nc, const int64_t *exp_off,
+                             int32_t e_begin, int32_t *cursor, int32_t *cand_body, cudaStream_t st);
+cudaError_t fov_exact(const ExactArgs &a, int n_sm, cudaStream_t st);
+cudaError_t fov_order_hits(const kete_hit *tmp, unsigned long long nh, const int64_t *frame_off,
+                           int64_t nf, int32_t *cursor, kete_hit *grouped, kete_hit *out,
+                           int n_sm, cudaStream_t st);
+
+// kete_scan.cu: exclusive prefix sum of int32 counts into int64 offsets
+// (out has n+1 entries; out[n] = total).  tmp must hold scan_tmp_elems(n).
+size_t scan_tmp_elems(int64_t n);
+cudaError_t exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *tmp,
+                           cudaStream_t st);
+
+}  // namespace kete

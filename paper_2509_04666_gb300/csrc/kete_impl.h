@@ -1,0 +1,63 @@
+// kete_impl.h -- internal types shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/kete.h"
+
+namespace kete {
+
+// device view of the loaded Chebyshev table
+struct EphemDev {
+    const double *coef;      // [body][seg][3][n_coef]
+    const float *coef32;     // the same table in FP32 (mixed-precision planets)
+    double t_start, t_end, seg_len, inv_seg;
+    int n_seg, n_coef, n_bodies, pad;
+    double gm[KETE_MAX_BODIES];
+};
+
+// device view of a force model (derived quantities precomputed on the host)
+struct ForceDev {
+    uint32_t active_mask;    // body_mask with massless bodies removed
+    uint32_t gr_mask, j2_mask;
+    int32_t precision;
+    double j2k[KETE_MAX_BODIES];        // 1.5 * J2 * mu * R^2
+    double pole[KETE_MAX_BODIES][3];    // unit pole, ecliptic J2000
+    double eps, eps_pc, safety, dt_init;
+    int32_t max_iter, pad;
+    int64_t max_steps;
+};
+
+// device counters accumulated by the kernels
+struct DevCounters {
+    unsigned long long steps, rejected, force_evals, iterations;
+    unsigned long long candidates, hits;
+    int error_flags;         // bit 0: unsorted epochs, 1: exposure mismatch, 2: bad observer,
+                             // 3: bad n_edges, 4: non-finite frame, 5: batch epoch outside table
+    int pad;
+};
+
+// per-body working state of a propagation chain: [8][n] = x,y,z,vx,vy,vz,t,dt
+struct ChainState {
+    double *w;
+    int32_t *status;
+    int64_t n;
+};
+
+// launch helpers implemented in the .cu files ---------------------------------
+void upload_radau_tables(cudaStream_t st);            // kete_prop.cu
+cudaError_t launch_ephem_eval(const EphemDev &E, const double *t, int64_t n, int body,
+                              double *pos, double *vel, cudaStream_t st);
+cudaError_t launch_chain_init(ChainState cs, const double *states, const double *epochs,
+                              const ForceDev &F, cudaStream_t st);
+cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
+                             const double *stops_dev, int n_stops, double *out,
+                             int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
+                             cudaStream_t st);
+cudaError_t launch_chain_finish(ChainState cs, double *states, double *epochs,
+                                int32_t *status, cudaStream_t st);
+
+}  // namespace kete

@@ -1,0 +1,351 @@
+// kete_prop.cu -- n-body propagation of massless bodies (Sec. 3.2, App. A, App. A.6).
+//
+// One thread integrates one body along its chain of stops (the body's epoch,
+// then every stop in order).  Each step is a 15th-order Gauss-Radau step in the
+// IAS15 form (Newton-basis coefficients g, power-basis coefficients b, 8
+// spacings), with the predictor removed: every step starts from b = 0 and the
+// corrector iterates until max|db6|/max|a| < eps_pc, the error stops falling
+// (after 3 iterations) or max_iter is reached.  Step control follows IAS15:
+// dt_new = dt (eps / (max|b6|/max|a|))^(1/7), reject below safety*dt, grow at
+// most 1/safety.  Every loop is bounded: max_iter corrector iterations,
+// max_steps step attempts per leg, after which the body gets a status code.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "kete_device.cuh"
+
+namespace kete {
+
+__constant__ RadauTables g_rt;
+
+// Gauss-Radau spacings on [0, 1] (Everhart 1985, 30 published digits)
+static const double kRadauH[8] = {
+    0.0,
+    0.0562625605369221464656521910318,
+    0.180240691736892364987579942780,
+    0.352624717113169637373907769648,
+    0.547153626330555383001448554766,
+    0.734210177215410531523210605558,
+    0.885320946839095768090359771030,
+    0.977520613561287501891174488626,
+};
+
+void upload_radau_tables(cudaStream_t st)
+{
+    RadauTables t;
+    std::memset(&t, 0, sizeof(t));
+    for (int n = 0; n < 8; n++) t.h[n] = kRadauH[n];
+    for (int n = 0; n < 8; n++)
+        for (int k = 0; k < n; k++) t.rinv[n][k] = 1.0 / (kRadauH[n] - kRadauH[k]);
+    // Newton basis N_n(s) = s (s-h_1)...(s-h_{n-1}); c[n][m] = coefficient of
+    // s^(m+1) in N_n, built by the recurrence N_n = N_{n-1} (s - h_{n-1}).
+    double poly[8] = {1, 0, 0, 0, 0, 0, 0, 0};   // coefficients of prod (s-h_i), s^0 first
+    for (int n = 1; n <= 7; n++) {
+        if (n >= 2) {
+            double nxt[8] = {0};
+            for (int p = 0; p < 7; p++) {
+                nxt[p + 1] += poly[p];
+                nxt[p] -= kRadauH[n - 1] * poly[p];
+            }
+            std::memcpy(poly, nxt, sizeof(poly));
+        }
+        for (int m = 0; m < 7; m++) t.c[n][m] = (m < n) ? poly[m] : 0.0;
+    }
+    cudaMemcpyToSymbolAsync(g_rt, &t, sizeof(t), 0, cudaMemcpyHostToDevice, st);
+}
+
+struct Cnt {
+    unsigned long long steps, rejected, evals, iters;
+};
+
+// One Gauss-Radau attempt of size h from (t, x0, v0) with a0 = a(t, x0, v0).
+__device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &F, double t,
+                                             const double x0[3], const double v0[3],
+                                             const double a0[3], double h, double x1[3],
+                                             double v1[3], double &err, Cnt &cnt)
+{
+    double b[7][3], g[7][3];
+#pragma unroll
+    for (int m = 0; m < 7; m++)
+#pragma unroll
+        for (int i = 0; i < 3; i++) b[m][i] = g[m][i] = 0.0;
+    double amax = 0.0, pc_prev = 0.0;
+    for (int it = 1; it <= F.max_iter; it++) {
+        double b6o[3] = {b[6][0], b[6][1], b[6][2]};
+        double F7[3];
+#pragma unroll
+        for (int n = 1; n <= 7; n++) {
+            const double s = g_rt.h[n];
+            const double sh = s * h;
+            double xn[3], vn[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                // x(s) = x0 + s h v0 + (s h)^2 [a0/2 + s(b0/6 + s(b1/12 + ... + s b6/72))]
+                double px = b[6][i] * (1.0 / 72.0);
+                px = fma(px, s, b[5][i] * (1.0 / 56.0));
+                px = fma(px, s, b[4][i] * (1.0 / 42.0));
+                px = fma(px, s, b[3][i] * (1.0 / 30.0));
+                px = fma(px, s, b[2][i] * (1.0 / 20.0));
+                px = fma(px, s, b[1][i] * (1.0 / 12.0));
+                px = fma(px, s, b[0][i] * (1.0 / 6.0));
+                px = fma(px, s, a0[i] * 0.5);
+                xn[i] = fma(sh * sh, px, fma(sh, v0[i], x0[i]));
+                // v(s) = v0 + s h [a0 + s(b0/2 + s(b1/3 + ... + s b6/8))]
+                double pv = b[6][i] * 0.125;
+                pv = fma(pv, s, b[5][i] * (1.0 / 7.0));
+                pv = fma(pv, s, b[4][i] * (1.0 / 6.0));
+                pv = fma(pv, s, b[3][i] * 0.2);
+                pv = fma(pv, s, b[2][i] * 0.25);
+                pv = fma(pv, s, b[1][i] * (1.0 / 3.0));
+                pv = fma(pv, s, b[0][i] * 0.5);
+                pv = fma(pv, s, a0[i]);
+                vn[i] = fma(sh, pv, v0[i]);
+            }
+            double Fn[3];
+            int st = accel_fp64(E, F, t + sh, xn, vn, Fn);
+            cnt.evals++;
+            if (st != KETE_BODY_OK) return st;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                double gn = (Fn[i] - a0[i]) * g_rt.rinv[n][0];
+#pragma unroll
+                for (int k = 1; k < n; k++) gn = (gn - g[k - 1][i]) * g_rt.rinv[n][k];
+                double dg = gn - g[n - 1][i];
+                g[n - 1][i] = gn;
+#pragma unroll
+                for (int m = 0; m < n; m++) b[m][i] = fma(g_rt.c[n][m], dg, b[m][i]);
+                if (n == 7) F7[i] = Fn[i];
+            }
+        }
+        cnt.iters++;
+        double db = 0.0;
+        amax = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            db = fmax(db, fabs(b[6][i] - b6o[i]));
+            amax = fmax(amax, fabs(F7[i]));
+        }
+        double pc = db / amax;
+        if (!isfinite(pc)) return KETE_BODY_NONFINITE;
+        if (pc < F.eps_pc) break;
+        if (it >= 3 && pc >= pc_prev) break;
+        pc_prev = pc;
+    }
+    double bmax = fmax(fabs(b[6][0]), fmax(fabs(b[6][1]), fabs(b[6][2])));
+    err = bmax / amax;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        double px = a0[i] * 0.5 + b[0][i] * (1.0 / 6.0) + b[1][i] * (1.0 / 12.0) +
+                    b[2][i] * (1.0 / 20.0) + b[3][i] * (1.0 / 30.0) + b[4][i] * (1.0 / 42.0) +
+                    b[5][i] * (1.0 / 56.0) + b[6][i] * (1.0 / 72.0);
+        double pv = a0[i] + b[0][i] * 0.5 + b[1][i] * (1.0 / 3.0) + b[2][i] * 0.25 +
+                    b[3][i] * 0.2 + b[4][i] * (1.0 / 6.0) + b[5][i] * (1.0 / 7.0) +
+                    b[6][i] * 0.125;
+        x1[i] = fma(h * h, px, fma(h, v0[i], x0[i]));
+        v1[i] = fma(h, pv, v0[i]);
+    }
+    if (!(isfinite(x1[0]) && isfinite(x1[1]) && isfinite(x1[2]) && isfinite(v1[0]) &&
+          isfinite(v1[1]) && isfinite(v1[2])))
+        return KETE_BODY_NONFINITE;
+    return KETE_BODY_OK;
+}
+
+// Integrate (x, v, t) to `target` exactly; dt is the carried step proposal.
+__device__ int integrate_to(const EphemDev &E, const ForceDev &F, double x[3], double v[3],
+                            double &t, double &dt, double target, Cnt &cnt)
+{
+    if (t == target) return KETE_BODY_OK;
+    const double dir = (target >= t) ? 1.0 : -1.0;
+    if (dt == 0.0 || ((dt > 0.0) != (dir > 0.0))) dt = dir * fabs(dt == 0.0 ? F.dt_init : dt);
+    long long attempts = 0;
+    while (t != target) {
+        double a0[3];
+        int st = accel_fp64(E, F, t, x, v, a0);
+        cnt.evals++;
+        if (st != KETE_BODY_OK) return st;
+        for (;;) {
+            if (++attempts > F.max_steps) return KETE_BODY_STEP_CAP;
+            const double remaining = target - t;
+            const bool clamped = fabs(dt) >= fabs(remaining);
+            // the step is the exact difference of the representable epochs it joins
+            const double t_new = clamped ? target : t + dt;
+            const double h = t_new - t;
+            double x1[3], v1[3], err;
+            st = radau_attempt(E, F, t, x, v, a0, h, x1, v1, err, cnt);
+            if (st != KETE_BODY_OK) return st;
+            double dt_new;
+            if (isfinite(err) && err >= 2.2250738585072014e-308)
+                dt_new = pow(F.eps / err, 1.0 / 7.0) * h;
+            else
+                dt_new = h / F.safety;
+            if (fabs(dt_new / h) < F.safety) {
+                dt = dt_new;
+                cnt.rejected++;
+                continue;
+            }
+            if (fabs(dt_new / h) > 1.0 / F.safety) dt_new = h / F.safety;
+            dt = dt_new;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                x[i] = x1[i];
+                v[i] = v1[i];
+            }
+            t = t_new;
+            cnt.steps++;
+            break;
+        }
+    }
+    return KETE_BODY_OK;
+}
+
+__device__ __forceinline__ void flush_counters(const Cnt &c, DevCounters *ctr)
+{
+    unsigned long long s = c.steps, r = c.rejected, e = c.evals, it = c.iters;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        it += __shfl_xor_sync(0xffffffffu, it, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&ctr->steps, s);
+        atomicAdd(&ctr->rejected, r);
+        atomicAdd(&ctr->force_evals, e);
+        atomicAdd(&ctr->iterations, it);
+    }
+}
+
+// One thread per body: advance its chain through stops[0..n_stops) and write
+// the state at each stop to out[k][c][i] (stride out_stride between rows).
+__global__ void __launch_bounds__(128) k_propagate(EphemDev E, ForceDev F, ChainState cs,
+                                                   const double *__restrict__ stops, int n_stops,
+                                                   double *__restrict__ out, int64_t out_stride,
+                                                   int keep_on_fail, DevCounters *ctr)
+{
+    const int64_t n = cs.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    Cnt cnt = {0, 0, 0, 0};
+    if (i < n) {
+        double x[3], v[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            x[c] = cs.w[c * n + i];
+            v[c] = cs.w[(3 + c) * n + i];
+        }
+        double t = cs.w[6 * n + i], dt = cs.w[7 * n + i];
+        int status = cs.status[i];
+        for (int k = 0; k < n_stops; k++) {
+            if (status == KETE_BODY_OK) status = integrate_to(E, F, x, v, t, dt, stops[k], cnt);
+            double *o = out + (int64_t)k * 6 * out_stride;
+            if (status == KETE_BODY_OK) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    o[c * out_stride + i] = x[c];
+                    o[(3 + c) * out_stride + i] = v[c];
+                }
+            } else if (!keep_on_fail) {
+#pragma unroll
+                for (int c = 0; c < 6; c++) o[c * out_stride + i] = __longlong_as_double(0x7ff8000000000000ll);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            cs.w[c * n + i] = x[c];
+            cs.w[(3 + c) * n + i] = v[c];
+        }
+        cs.w[6 * n + i] = t;
+        cs.w[7 * n + i] = dt;
+        cs.status[i] = status;
+    }
+    flush_counters(cnt, ctr);
+}
+
+__global__ void k_chain_init(ChainState cs, const double *__restrict__ states,
+                             const double *__restrict__ epochs)
+{
+    const int64_t n = cs.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool ok = true;
+    for (int c = 0; c < 6; c++) {
+        double q = states[c * n + i];
+        cs.w[c * n + i] = q;
+        ok = ok && isfinite(q);
+    }
+    double t = epochs[i];
+    cs.w[6 * n + i] = t;
+    cs.w[7 * n + i] = 0.0;
+    cs.status[i] = (ok && isfinite(t)) ? KETE_BODY_OK : KETE_BODY_NONFINITE;
+}
+
+__global__ void k_chain_finish(ChainState cs, double *__restrict__ epochs,
+                               int32_t *__restrict__ status)
+{
+    const int64_t n = cs.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = cs.status[i];
+    if (epochs && s == KETE_BODY_OK) epochs[i] = cs.w[6 * n + i];
+    if (status) status[i] = s;
+}
+
+__global__ void k_ephem_eval(EphemDev E, const double *__restrict__ t, int64_t n, int body,
+                             double *__restrict__ pos, double *__restrict__ vel)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Seg g;
+    double p[3], v[3];
+    if (!ephem_seg(E, t[i], g)) {
+        for (int c = 0; c < 3; c++) {
+            pos[3 * i + c] = __longlong_as_double(0x7ff8000000000000ll);
+            if (vel) vel[3 * i + c] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        return;
+    }
+    cheb_pos_vel(ephem_coef(E, body, g.s), E.n_coef, g.tau, 2.0 * E.inv_seg, p, v);
+    for (int c = 0; c < 3; c++) {
+        pos[3 * i + c] = p[c];
+        if (vel) vel[3 * i + c] = v[c];
+    }
+}
+
+static unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+cudaError_t launch_ephem_eval(const EphemDev &E, const double *t, int64_t n, int body,
+                              double *pos, double *vel, cudaStream_t st)
+{
+    if (n > 0) k_ephem_eval<<<grid_for(n, 256), 256, 0, st>>>(E, t, n, body, pos, vel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain_init(ChainState cs, const double *states, const double *epochs,
+                              const ForceDev &, cudaStream_t st)
+{
+    if (cs.n > 0) k_chain_init<<<grid_for(cs.n, 256), 256, 0, st>>>(cs, states, epochs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
+                             const double *stops_dev, int n_stops, double *out,
+                             int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
+                             cudaStream_t st)
+{
+    if (cs.n > 0 && n_stops > 0)
+        k_propagate<<<grid_for(cs.n, 128), 128, 0, st>>>(E, F, cs, stops_dev, n_stops, out,
+                                                         out_stride, keep_on_fail ? 1 : 0, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain_finish(ChainState cs, double *states, double *epochs, int32_t *status,
+                                cudaStream_t st)
+{
+    (void)states;
+    if (cs.n > 0) k_chain_finish<<<grid_for(cs.n, 256), 256, 0, st>>>(cs, epochs, status);
+    return cudaGetLastError();
+}
+
+}  // namespace kete

@@ -1,0 +1,245 @@
+"""Thin Python binding of libkete_gpu.so (include/kete.h).
+
+Argument marshalling only: every step of the survey path runs in the CUDA
+library.  Tensors are torch CUDA tensors passed by ``data_ptr()``; work is
+ordered on the current torch stream of the context's device.  If the library
+is missing the binding raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkete_gpu.so")
+
+OK, ERR_BAD_ARG, ERR_EPHEM_SPAN, ERR_CAPACITY, ERR_NO_EPHEM, ERR_CUDA, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
+BODY_OK, BODY_STEP_CAP, BODY_OUT_OF_SPAN, BODY_NONFINITE, BODY_KEPLER_CAP = 0, 1, 2, 3, 4
+FP64, MIXED = 0, 1
+
+EXPORTS = ["kete_create", "kete_destroy", "kete_set_stream", "kete_last_error",
+           "kete_force_model_default", "kete_survey_opts_default", "kete_load_ephem",
+           "kete_ephem_eval", "kete_propagate", "kete_propagate_stops", "kete_fov_check",
+           "kete_get_stats"]
+
+
+class KeteError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"kete error {code}: {msg}")
+        self.code = code
+
+
+class ForceModel(C.Structure):
+    _fields_ = [("body_mask", C.c_uint32), ("gr_mask", C.c_uint32), ("j2_mask", C.c_uint32),
+                ("precision", C.c_int32), ("j2", C.c_double * 16), ("radius", C.c_double * 16),
+                ("pole_ra", C.c_double * 16), ("pole_dec", C.c_double * 16),
+                ("eps", C.c_double), ("eps_pc", C.c_double), ("safety", C.c_double),
+                ("dt_init", C.c_double), ("max_iter", C.c_int32), ("reserved", C.c_int32),
+                ("max_steps", C.c_int64)]
+
+
+class SurveyOpts(C.Structure):
+    _fields_ = [("batch_span", C.c_double), ("twobody_max", C.c_double),
+                ("cell_deg", C.c_double), ("mem_budget_gb", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("prop_ms", C.c_double), ("fov_ms", C.c_double), ("total_ms", C.c_double),
+                ("steps", C.c_int64), ("rejected", C.c_int64), ("force_evals", C.c_int64),
+                ("iterations", C.c_int64), ("n_batches", C.c_int64), ("n_exposures", C.c_int64),
+                ("n_candidates", C.c_int64), ("n_hits", C.c_int64), ("prop_launches", C.c_int64),
+                ("launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libkete_gpu.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
+        L.kete_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+        L.kete_destroy.argtypes = [vp]
+        L.kete_destroy.restype = None
+        L.kete_set_stream.argtypes = [vp, vp]
+        L.kete_last_error.argtypes = [vp]
+        L.kete_last_error.restype = C.c_char_p
+        L.kete_force_model_default.argtypes = [C.POINTER(ForceModel)]
+        L.kete_force_model_default.restype = None
+        L.kete_survey_opts_default.argtypes = [C.POINTER(SurveyOpts)]
+        L.kete_survey_opts_default.restype = None
+        L.kete_load_ephem.argtypes = [vp, C.c_char_p, C.c_size_t]
+        L.kete_ephem_eval.argtypes = [vp, vp, i64, C.c_int, vp, vp]
+        L.kete_propagate.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(ForceModel), vp]
+        L.kete_propagate_stops.argtypes = [vp, vp, vp, i64, C.POINTER(C.c_double), i64,
+                                           C.POINTER(ForceModel), vp, vp]
+        L.kete_fov_check.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, C.POINTER(ForceModel),
+                                     C.POINTER(SurveyOpts), vp, i64, C.POINTER(i64), vp]
+        L.kete_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        _lib = L
+    return _lib
+
+
+def force_model(**kw) -> ForceModel:
+    """Default force model (App. A defaults) with keyword overrides; per-body
+    arrays (j2, radius, pole_ra, pole_dec) take {body_index: value} dicts."""
+    fm = ForceModel()
+    lib().kete_force_model_default(C.byref(fm))
+    for k, v in kw.items():
+        if k in ("j2", "radius", "pole_ra", "pole_dec"):
+            arr = getattr(fm, k)
+            for i, x in v.items():
+                arr[i] = x
+        else:
+            setattr(fm, k, v)
+    return fm
+
+
+def survey_opts(**kw) -> SurveyOpts:
+    o = SurveyOpts()
+    lib().kete_survey_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _dev_f64(t, name, shape=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def frames_to_device(frames: np.ndarray, device) -> torch.Tensor:
+    """kete_frame records (128 bytes each, numpy structured array) -> CUDA bytes."""
+    raw = np.ascontiguousarray(frames).view(np.uint8).reshape(-1)
+    return torch.from_numpy(raw.copy()).to(device)
+
+
+def decode_hits(h: torch.Tensor, n: int):
+    """kete_hit rows (int64 [n, 4] view) -> dict of CPU tensors."""
+    h = h[:n].cpu()
+    return {"frame": h[:, 0].clone(),
+            "body": (h[:, 1] & 0xFFFFFFFF).to(torch.int32),
+            "ra": h[:, 2].clone().view(torch.float64),
+            "dec": h[:, 3].clone().view(torch.float64)}
+
+
+class Kete:
+    """One library context (device-resident ephemeris + scratch) on one GPU."""
+
+    def __init__(self, device: int = 0):
+        self.device = torch.device("cuda", device)
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            rc = lib().kete_create(C.byref(self._h), device, C.c_void_p(stream))
+        if rc != OK:
+            raise KeteError(rc, "kete_create failed")
+
+    def close(self):
+        if self._h:
+            lib().kete_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        lib().kete_set_stream(self._h, C.c_void_p(s))
+
+    def _check(self, rc):
+        if rc != OK:
+            raise KeteError(rc, lib().kete_last_error(self._h).decode())
+
+    # -- calls with the ABI's names ------------------------------------------
+    def load_ephem(self, table: bytes):
+        self._sync_stream()
+        self._check(lib().kete_load_ephem(self._h, table, len(table)))
+
+    def ephem_eval(self, t: torch.Tensor, body: int):
+        n = t.numel()
+        _dev_f64(t, "t")
+        pos = torch.empty((n, 3), dtype=torch.float64, device=t.device)
+        vel = torch.empty((n, 3), dtype=torch.float64, device=t.device)
+        self._sync_stream()
+        self._check(lib().kete_ephem_eval(self._h, t.data_ptr(), n, body, pos.data_ptr(),
+                                          vel.data_ptr()))
+        return pos, vel
+
+    def propagate(self, states, epochs, t_target, fm=None, status=None):
+        """In-place propagation of states [6, n] / epochs [n] to t_target."""
+        n = epochs.numel()
+        _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
+        if status is None:
+            status = torch.zeros(n, dtype=torch.int32, device=states.device)
+        fm = fm or force_model()
+        self._sync_stream()
+        self._check(lib().kete_propagate(self._h, states.data_ptr(), epochs.data_ptr(), n,
+                                         float(t_target), C.byref(fm), status.data_ptr()))
+        return status
+
+    def propagate_stops(self, states, epochs, stops, fm=None):
+        n = epochs.numel()
+        _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
+        st = np.ascontiguousarray(stops, dtype=np.float64)
+        out = torch.empty((len(st), 6, n), dtype=torch.float64, device=states.device)
+        status = torch.zeros(n, dtype=torch.int32, device=states.device)
+        fm = fm or force_model()
+        self._sync_stream()
+        self._check(lib().kete_propagate_stops(
+            self._h, states.data_ptr(), epochs.data_ptr(), n,
+            st.ctypes.data_as(C.POINTER(C.c_double)), len(st), C.byref(fm), out.data_ptr(),
+            status.data_ptr()))
+        return out, status
+
+    def fov_check(self, states, epochs, frames_dev, observers, fm=None, opts=None,
+                  capacity=None, hits=None):
+        """Which bodies fall inside which FoV.  Returns (hits int64 [cap, 4],
+        n_hits, status).  Grows the hit buffer once if it was too small."""
+        n = epochs.numel()
+        _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
+        _dev_f64(observers, "observers")
+        if not (frames_dev.is_cuda and frames_dev.dtype == torch.uint8 and frames_dev.numel() % 128 == 0):
+            raise TypeError("frames must be a CUDA uint8 tensor of 128-byte kete_frame records")
+        nf = frames_dev.numel() // 128
+        n_obs = observers.numel() // 3
+        fm = fm or force_model()
+        opts = opts or survey_opts()
+        status = torch.zeros(n, dtype=torch.int32, device=states.device)
+        if hits is None:
+            cap = capacity if capacity is not None else max(1024, 4 * nf)
+            hits = torch.empty((cap, 4), dtype=torch.int64, device=states.device)
+        nh = C.c_int64(0)
+        self._sync_stream()
+        for attempt in range(2):
+            rc = lib().kete_fov_check(self._h, states.data_ptr(), epochs.data_ptr(), n,
+                                      frames_dev.data_ptr(), nf, observers.data_ptr(), n_obs,
+                                      C.byref(fm), C.byref(opts), hits.data_ptr(), hits.shape[0],
+                                      C.byref(nh), status.data_ptr())
+            if rc == ERR_CAPACITY and attempt == 0:
+                hits = torch.empty((nh.value + 1024, 4), dtype=torch.int64, device=states.device)
+                continue
+            self._check(rc)
+            break
+        return hits, nh.value, status
+
+    def get_stats(self) -> dict:
+        s = Stats()
+        self._check(lib().kete_get_stats(self._h, C.byref(s)))
+        return s.as_dict()

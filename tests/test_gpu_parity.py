@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (from the accuracy targets of the survey path): heliocentric
+positions within 1e-9 AU, sky positions within 1 mas (4.85e-9 rad), FoV
+membership identical outside a 1e-9 rad band around the polygon edges; the
+ephemeris lookup within 1e-14 AU of the oracle's textbook Chebyshev sum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_04666_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MAS = math.radians(1.0 / 3.6e6)
+EDGE = 1e-9
+
+
+@pytest.fixture(scope="module")
+def K():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_04666_gb300 import build as B, kete
+    B.build()
+    k = kete.Kete(0)
+    yield k
+    k.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _hits_gpu(K, w, fm=None, opts=None, capacity=None):
+    from paper_2509_04666_gb300 import kete
+    K.load_ephem(w.ephem.to_bytes())
+    hits, nh, status = K.fov_check(_dev(w.states), _dev(w.epochs), kete.frames_to_device(w.frames, "cuda"),
+                                   _dev(w.observers), fm=fm, opts=opts, capacity=capacity)
+    return kete.decode_hits(hits, nh), status.cpu().numpy()
+
+
+def _compare_hits(got, ref, edge=EDGE, sky_tol=MAS):
+    g = {(int(f), int(b)): (ra, de) for f, b, ra, de in
+         zip(got["frame"].tolist(), got["body"].tolist(), got["ra"].tolist(), got["dec"].tolist())}
+    r = {(int(h["frame"]), int(h["body"])): h for h in ref}
+    only = set(g) ^ set(r)
+    bad = [k for k in only if k not in r or abs(r[k]["margin"]) >= edge]
+    assert not bad, f"{len(bad)} hits differ outside the edge band, e.g. {bad[:5]}"
+    worst = 0.0
+    for key in set(g) & set(r):
+        ra, de = g[key]
+        dra = (ra - r[key]["ra"] + math.pi) % (2 * math.pi) - math.pi
+        worst = max(worst, math.hypot(dra * math.cos(de), de - r[key]["dec"]))
+    assert worst < sky_tol, worst
+    # order: sorted by (frame, body)
+    keys = list(zip(got["frame"].tolist(), got["body"].tolist()))
+    assert keys == sorted(keys)
+    return worst
+
+
+def test_ephemeris_lookup_matches_oracle(K, mb1k):
+    import torch
+    K.load_ephem(mb1k.ephem.to_bytes())
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    rng = np.random.default_rng(1)
+    t = np.concatenate([rng.uniform(mb1k.ephem.t_start, mb1k.ephem.t_end, 500),
+                        [mb1k.ephem.t_start, mb1k.ephem.t_end,
+                         mb1k.ephem.t_start + mb1k.ephem.seg_len]])
+    for body in range(9):
+        pos, vel = K.ephem_eval(_dev(t), body)
+        pos = pos.cpu().numpy(); vel = vel.cpu().numpy()
+        for i, ti in enumerate(t):
+            _, p, v = orc.ephem(body, ti)
+            assert np.abs(pos[i] - p).max() < 1e-14 * max(1, np.abs(p).max())
+            assert np.abs(vel[i] - v).max() < 1e-15 * 50
+    pos, _ = K.ephem_eval(_dev(np.array([mb1k.ephem.t_end + 1.0])), 0)
+    assert torch.isnan(pos).all()
+
+
+def test_propagate_matches_oracle(K, mb1k):
+    import torch
+    K.load_ephem(mb1k.ephem.to_bytes())
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    fm_o = orc.force_model()
+    st = _dev(mb1k.states.copy()); ep = _dev(mb1k.epochs.copy())
+    t1 = W.T0 + 60.0
+    status = K.propagate(st, ep, t1)
+    ref, ref_ep, ref_status, _ = orc.propagate_many(fm_o, mb1k.states, mb1k.epochs, t1)
+    assert (status.cpu().numpy() == 0).all() and (ref_status == 0).all()
+    assert (ep.cpu().numpy() == t1).all()
+    err = np.abs(st.cpu().numpy()[:3] - ref[:3]).max()
+    assert err < 1e-9, err
+    stats = K.get_stats()
+    assert stats["steps"] > 0 and stats["force_evals"] > stats["steps"]
+
+
+def test_propagate_stops_matches_oracle(K, mb1k):
+    K.load_ephem(mb1k.ephem.to_bytes())
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    stops = np.array([W.T0 - 10.0, W.T0 + 1.3, W.T0 + 4.2, W.T0 + 7.0, W.T0 + 45.0])
+    idx = np.arange(0, 1000, 7)
+    st = mb1k.states[:, idx]
+    out, status = K.propagate_stops(_dev(st), _dev(mb1k.epochs[idx]), stops)
+    out = out.cpu().numpy()
+    for j, i in enumerate(idx):
+        rc, ref, _ = orc.propagate_stops(orc.force_model(), st[:, j], W.T0, stops)
+        assert rc == 0
+        assert np.abs(out[:, :3, j] - ref[:, :3]).max() < 1e-9
+
+
+def test_step_controls_match_oracle_counts(K):
+    """Same accept/reject schedule on a closed-form Kepler orbit (Sun only)."""
+    tab = W.static_sun_table(W.T0 - 10, W.T0 + 420)
+    K.load_ephem(tab.to_bytes())
+    orc = O.Oracle(tab.to_bytes())
+    from paper_2509_04666_gb300 import kete
+    r, v = W.elements_to_state(np.array([1.2, 2.6]), np.array([0.6, 0.1]), 0.2, 0.1, 0.3,
+                               np.array([0.1, 2.0]), W.GM_SUN)
+    st = np.concatenate([r, v])
+    fm = kete.force_model(body_mask=1, gr_mask=0, j2_mask=0)
+    s = _dev(st.copy()); e = _dev(np.full(2, W.T0))
+    K.propagate(s, e, W.T0 + 400.0, fm=fm)
+    g = K.get_stats()
+    steps = 0
+    for j in range(2):
+        rc, ref, _, _, stats = orc.propagate(orc.force_model(body_mask=1, gr_mask=0, j2_mask=0),
+                                             st[:, j], W.T0, W.T0 + 400.0)
+        steps += stats.steps
+        assert np.abs(s.cpu().numpy()[:3, j] - ref[:3]).max() < 1e-12
+    assert g["steps"] == steps
+
+
+def test_fov_check_matches_oracle_small(K, mb1k):
+    got, status = _hits_gpu(K, mb1k)
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    ref, ref_status, _ = orc.fov_check(orc.force_model(), mb1k.states, mb1k.epochs, mb1k.frames,
+                                       mb1k.observers)
+    assert len(ref) >= 5
+    _compare_hits(got, ref)
+    assert (status == 0).all()
+
+
+def test_fov_check_matches_oracle_dense(K, mb1k_dense):
+    w = mb1k_dense
+    got, _ = _hits_gpu(K, w)
+    orc = O.Oracle(w.ephem.to_bytes())
+    ref, _, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, w.frames, w.observers)
+    assert len(ref) > 100
+    _compare_hits(got, ref)
+
+
+def test_fov_check_pure_nbody_interval(K, mb1k_dense):
+    """Two-body interval 0: n-body to every FoV epoch (Sec. 2)."""
+    from paper_2509_04666_gb300 import kete
+    w = mb1k_dense
+    got, _ = _hits_gpu(K, w, opts=kete.survey_opts(twobody_max=0.0))
+    orc = O.Oracle(w.ephem.to_bytes())
+    ref, _, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, w.frames, w.observers,
+                              twobody_max=0.0)
+    _compare_hits(got, ref)
+
+
+def test_fov_check_multi_detector_exposures(K):
+    """Union-of-polygons exposures (8x8 sub-fields, ground observer)."""
+    w = W.ztf1y(n_bodies=1500, n_exposures=60, days=6)
+    got, _ = _hits_gpu(K, w)
+    orc = O.Oracle(w.ephem.to_bytes())
+    ref, _, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, w.frames, w.observers,
+                              prefilter_deg=8.0)
+    assert len(ref) > 20
+    _compare_hits(got, ref)
+
+
+def test_fov_check_capacity_and_edge_cases(K, mb1k_dense):
+    import torch
+    from paper_2509_04666_gb300 import kete
+    w = mb1k_dense
+    K.load_ephem(w.ephem.to_bytes())
+    fr = kete.frames_to_device(w.frames, "cuda")
+    st, ep, ob = _dev(w.states), _dev(w.epochs), _dev(w.observers)
+    # too small a buffer: CAPACITY with the count needed
+    import ctypes as C
+    hits = torch.empty((1, 4), dtype=torch.int64, device="cuda")
+    nh = C.c_int64(0)
+    status = torch.zeros(w.n_bodies, dtype=torch.int32, device="cuda")
+    rc = kete.lib().kete_fov_check(K._h, st.data_ptr(), ep.data_ptr(), w.n_bodies, fr.data_ptr(),
+                                   len(w.frames), ob.data_ptr(), len(w.observers),
+                                   C.byref(kete.force_model()), C.byref(kete.survey_opts()),
+                                   hits.data_ptr(), 1, C.byref(nh), status.data_ptr())
+    assert rc == kete.ERR_CAPACITY and nh.value > 100
+    # no frames / no bodies
+    _, n0, _ = K.fov_check(st, ep, fr[:0], ob)
+    assert n0 == 0
+    _, n1, _ = K.fov_check(st[:, :0].contiguous(), ep[:0].contiguous(), fr, ob)
+    assert n1 == 0
+    # unsorted frames are rejected
+    bad = w.frames[::-1].copy()
+    with pytest.raises(kete.KeteError) as ei:
+        K.fov_check(st, ep, kete.frames_to_device(bad, "cuda"), ob)
+    assert ei.value.code == kete.ERR_BAD_ARG
+    # observer index out of range
+    bad = w.frames.copy(); bad["observer_idx"][3] = len(w.observers) + 5
+    with pytest.raises(kete.KeteError):
+        K.fov_check(st, ep, kete.frames_to_device(bad, "cuda"), ob)
+    # a NaN body and a body out of the table's span fail alone
+    s2 = w.states.copy(); s2[0, 0] = np.nan
+    e2 = w.epochs.copy(); e2[1] = w.ephem.t_end + 100.0
+    h2, n2, status2 = K.fov_check(_dev(s2), _dev(e2), fr, ob)
+    status2 = status2.cpu().numpy()
+    assert status2[0] == kete.BODY_NONFINITE and status2[1] == kete.BODY_OUT_OF_SPAN
+    got = kete.decode_hits(h2, n2)
+    assert not set(got["body"].tolist()) & {0, 1}
+
+
+def test_fov_check_exposure_layout_errors(K, mb1k):
+    from paper_2509_04666_gb300 import kete
+    K.load_ephem(mb1k.ephem.to_bytes())
+    st, ep, ob = _dev(mb1k.states), _dev(mb1k.epochs), _dev(mb1k.observers)
+    bad = mb1k.frames.copy(); bad["exposure_id"][5] = bad["exposure_id"][4]
+    with pytest.raises(kete.KeteError):
+        K.fov_check(st, ep, kete.frames_to_device(bad, "cuda"), ob)
+    bad = mb1k.frames.copy(); bad["n_edges"][2] = 7
+    with pytest.raises(kete.KeteError):
+        K.fov_check(st, ep, kete.frames_to_device(bad, "cuda"), ob)
