@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the survey-prediction path on GB300.
+
+One step = one full survey prediction (Sec. 2): 757,000 synthetic bodies
+(2 % NEOs) propagated over 365 days under Sun + 8 planets with GR and J2,
+batched at <= 3-day midpoints, light-time-corrected two-body to every epoch of
+a WISE-like stream of 1.2 M square 0.78 deg frames, polygon test, hits sorted.
+
+value = body-days propagated per second for the whole job (N GPUs x bodies x
+365 days / step time); the same line carries the body x frame checks per
+second.  Inputs are resident in HBM when a timed step starts; e2e repeats the
+step through the host-buffer path (host -> device copies and the hit list
+back inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("body-days propagated/s and body×frame FoV checks/s at ≤1 mas vs FP64 oracle, "
+          "1 GB300")
+MAS = math.radians(1.0 / 3.6e6)
+
+# DRAM traffic of one k_propagate launch from an ncu capture (profiles/
+# k_propagate_wise1y.md); valid only while the kernel source is unchanged.
+PROFILED_TRAFFIC = {"src_sha": None, "bytes_per_body_stop": None}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kete_prop.cu", "kete_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2509_04666_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def flops_per_eval(n_active, n_gr, n_j2, n_coef):
+    """FP64 FLOPs of one acceleration evaluation as the kernel computes it
+    (FMA = 2): Clenshaw position (3 per term per coordinate), position +
+    velocity for GR bodies, Newton, GR (Eq. A.3) and J2 (Eq. A.4) terms."""
+    cheb_pos = 3 * (3 * (n_coef - 1) + 3)
+    cheb_posvel = cheb_pos + 3 * (4 * (n_coef - 1) + 1)
+    newton, gr, j2 = 19, 27, 21
+    return ((n_active - n_gr) * (cheb_pos + newton) + n_gr * (cheb_posvel + newton + gr)
+            + n_j2 * j2 + 10)
+
+
+FLOPS_PER_ITER = 1482    # 7 substep predictors (x and v) + g/b updates + convergence test
+FLOPS_PER_ATTEMPT = 130  # final x1, v1 and step control
+
+
+def algorithmic_flops(st, fpe):
+    return (st["force_evals"] * fpe + st["iterations"] * FLOPS_PER_ITER
+            + (st["steps"] + st["rejected"]) * FLOPS_PER_ATTEMPT)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(args, rank):
+    from paper_2509_04666_gb300 import workloads as W
+    kw = {}
+    if args.n_bodies:
+        kw["n_bodies"] = args.n_bodies
+    if args.n_frames:
+        kw["n_frames"] = args.n_frames
+    seed = W.SEED_BASE + 1 + 1000 * rank
+    return W.wise1y(seed=seed, **kw)
+
+
+def workload_name(w, args):
+    return (f"wise1y: {w.n_bodies} bodies (2% NEOs) x {len(w.frames)} square 0.78 deg frames "
+            f"(WISE-like scan from a 1-AU orbit), 365 d, Sun+8 planets, GR+J2, "
+            f"{'FP64' if args.precision == 'fp64' else 'mixed FP32/FP64'}")
+
+
+def oracle_sample(w, n_sample, n_threads=None):
+    """The FP64 CPU oracle, as it stands, on a bounded body sample."""
+    import oracle as O
+    orc = O.Oracle(w.ephem.to_bytes())
+    sub = np.linspace(0, w.n_bodies - 1, n_sample).astype(np.int32)
+    nt = n_threads or os.cpu_count()
+    t0 = time.perf_counter()
+    hits, status, stats = orc.fov_check(orc.force_model(), w.states, w.epochs, w.frames, w.observers,
+                                        prefilter_deg=1.0, subset=sub, n_threads=nt)
+    dt = time.perf_counter() - t0
+    return sub, hits, dt, nt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = make_workload(args, 0)
+    n_sample = args.ref_sample
+    times = []
+    for i in range(args.warmup + args.steps):
+        sub, hits, dt, nt = oracle_sample(w, n_sample)
+        if i >= args.warmup:
+            times.append(dt)
+    t = statistics.mean(times)
+    value = n_sample * 365.0 / t
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "body-days/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w, args), "sample_bodies": n_sample},
+        "cpu_baseline": {"value": value, "unit": "body-days/s", "cores": nt, "kind": "oracle",
+                         "sample": f"{n_sample} evenly spaced bodies x all {len(w.frames)} frames, full year"},
+        "e2e": {"value": value, "unit": "body-days/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def peak_fma(fp64: bool):
+    import ctypes as C
+    from paper_2509_04666_gb300 import build as B
+    L = C.CDLL(B.PEAK_LIB)
+    L.kete_peak_fma.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
+    v = C.c_double(0)
+    rc = L.kete_peak_fma(1 if fp64 else 0, 4096 if fp64 else 65536, 152 * 8, 256, 3, C.byref(v))
+    return v.value if rc == 0 else None
+
+
+def run_gb300(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2509_04666_gb300 import build as B, kete
+    B.build()
+    dev = torch.device("cuda", local)
+    w = make_workload(args, rank)
+    K = kete.Kete(local)
+    K.load_ephem(w.ephem.to_bytes())
+    fm = kete.force_model(precision=kete.MIXED if args.precision == "mixed" else kete.FP64)
+    st = torch.from_numpy(w.states.copy()).to(dev)
+    ep = torch.from_numpy(w.epochs.copy()).to(dev)
+    fr = kete.frames_to_device(w.frames, dev)
+    ob = torch.from_numpy(np.ascontiguousarray(w.observers)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # first call sizes the hit buffer
+    hits, nh, status = K.fov_check(st, ep, fr, ob, fm=fm)
+    hits = torch.empty((int(nh * 1.1) + 4096, 4), dtype=torch.int64, device=dev)
+
+    def step():
+        return K.fov_check(st, ep, fr, ob, fm=fm, hits=hits)
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream(dev)
+    times, stats = [], []
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    with Clocks(local) as clk:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)                       # L2 flush between steps (256 MB write)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, nh, status = step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stats.append(K.get_stats())
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    clocks = clk.summary()
+    ms = statistics.mean(times)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    n, nf = w.n_bodies, len(w.frames)
+    value = world * n * 365.0 / (ms / 1e3)
+    checks = world * n * nf / (ms / 1e3)
+    # ---- roofline of the dominant kernel (k_propagate, FP64 ALU bound) --------
+    s0 = stats[-1]
+    fm_py = fm
+    n_active = bin(fm_py.body_mask & 0x1FF).count("1")
+    fpe = flops_per_eval(n_active, bin(fm_py.gr_mask & 0x1FF).count("1"),
+                         bin(fm_py.j2_mask & 0x1FF).count("1"), w.ephem.n_coef)
+    flops = statistics.mean(algorithmic_flops(s, fpe) for s in stats)
+    prop_ms = statistics.mean(s["prop_ms"] for s in stats)
+    achieved = flops / (prop_ms / 1e3) / 1e12
+    peak_nominal = 152 * 2 * 2 * 2.07e9 / 1e12      # SMs x FP64 FMA/clk x 2 x max clock
+    peak_probe = peak_fma(True)
+    src_sha = kernel_source_sha()
+    traffic = None
+    if PROFILED_TRAFFIC["src_sha"] == src_sha and PROFILED_TRAFFIC["bytes_per_body_stop"]:
+        traffic = PROFILED_TRAFFIC["bytes_per_body_stop"] * n * s0["n_batches"] / max(1, s0["prop_launches"])
+    # ---- e2e: the public call with host buffers ----------------------------------
+    e2e = None
+    if not args.no_e2e:
+        h_st = torch.from_numpy(w.states.copy()).pin_memory()
+        h_ep = torch.from_numpy(w.epochs.copy()).pin_memory()
+        h_fr = torch.from_numpy(np.ascontiguousarray(w.frames).view(np.uint8).reshape(-1).copy()).pin_memory()
+        h_ob = torch.from_numpy(np.ascontiguousarray(w.observers)).pin_memory()
+        e_times, d2h = [], 0
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            d_st = h_st.to(dev, non_blocking=True); d_ep = h_ep.to(dev, non_blocking=True)
+            d_fr = h_fr.to(dev, non_blocking=True); d_ob = h_ob.to(dev, non_blocking=True)
+            hh, nhh, _ = K.fov_check(d_st, d_ep, d_fr, d_ob, fm=fm, hits=hits)
+            out = hh[:nhh].cpu()
+            t1 = time.perf_counter()
+            if i >= args.warmup:
+                e_times.append(t1 - t0)
+                d2h = out.numel() * 8
+        h2d = sum(t.numel() * t.element_size() for t in (h_st, h_ep, h_fr, h_ob))
+        et = statistics.mean(e_times)
+        e2e = {"value": world * n * 365.0 / et, "unit": "body-days/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": et * 1e3}
+    # ---- CPU baseline (the oracle as it stands) + sampled accuracy ------------------
+    cpu = None
+    accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sub, ref, dt, nt = oracle_sample(w, args.ref_sample)
+        cpu = {"value": len(sub) * 365.0 / dt, "unit": "body-days/s", "cores": nt, "kind": "oracle",
+               "sample": f"{len(sub)} evenly spaced bodies x all {nf} frames, full year, "
+                         f"{dt:.1f} s"}
+        got = kete.decode_hits(hits, nh)
+        keep = np.isin(got["body"].numpy(), sub)
+        g = {(int(f), int(b)): (ra, de) for f, b, ra, de in
+             zip(got["frame"].numpy()[keep], got["body"].numpy()[keep], got["ra"].numpy()[keep],
+                 got["dec"].numpy()[keep])}
+        r = {(int(h["frame"]), int(h["body"])): h for h in ref}
+        mism = [k for k in set(g) ^ set(r) if k not in r or abs(r[k]["margin"]) >= 1e-9]
+        worst = 0.0
+        for key in set(g) & set(r):
+            ra, de = g[key]
+            dra = (ra - r[key]["ra"] + math.pi) % (2 * math.pi) - math.pi
+            worst = max(worst, math.hypot(dra * math.cos(de), de - r[key]["dec"]))
+        accuracy = {"sampled_bodies": len(sub), "oracle_hits": len(r), "gpu_hits": len(g),
+                    "mismatch_outside_edge_band": len(mism), "max_sky_err_mas": worst / MAS}
+    out = {
+        "metric": METRIC, "value": value, "unit": "body-days/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": workload_name(w, args), "n_bodies": n, "n_frames": nf, "days": 365,
+                   "batches": s0["n_batches"], "precision": args.precision,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "fov_checks_per_s": checks,
+        "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": achieved,
+                     "peak": peak_nominal, "unit": "TFLOP/s", "frac": achieved / peak_nominal,
+                     "traffic": traffic, "peak_probe_measured": (peak_probe or 0) / 1e12,
+                     "flops_per_launch": flops / max(1, s0["prop_launches"]),
+                     "prop_ms_per_step": prop_ms, "peak_basis": "152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
+        "cpu_baseline": cpu,
+        "accuracy": accuracy,
+        "e2e": e2e,
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "clocks": clocks,
+        "counters": {k: s0[k] for k in ("steps", "rejected", "force_evals", "iterations",
+                                        "n_batches", "n_exposures", "n_candidates", "n_hits")},
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    K.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n-bodies", type=int, default=0)
+    ap.add_argument("--n-frames", type=int, default=0)
+    ap.add_argument("--ref-sample", type=int, default=768)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -135,6 +135,10 @@ typedef struct kete_stats {
     int64_t n_hits;
     int64_t prop_launches;       /* propagation kernel launches */
     int64_t launches;            /* all kernel launches of the call */
+    double prep_ms;              /* frame/exposure preparation, batching, sky cells */
+    double cand_ms;              /* candidate search */
+    double exact_ms;             /* two-body + light-time + polygon test */
+    double order_ms;             /* hit ordering */
 } kete_stats;
 
 typedef struct kete_ctx kete_ctx;

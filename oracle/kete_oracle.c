@@ -27,7 +27,11 @@
  *     dates, so every step is taken as the exact difference of the two
  *     representable epochs it joins; the last step of a leg lands exactly on
  *     the target epoch.  Two-body intervals are formed as (t_obs - t_ref) - tau
- *     before any absolute epoch is rounded.
+ *     before any absolute epoch is rounded, and the planets are evaluated at
+ *     (epoch, offset) pairs: the Chebyshev argument is 2((t0 - t_mid) + off)/L,
+ *     so substep epochs carry no rounding of the absolute date (which would
+ *     otherwise add noise the corrector's b6 estimate amplifies near planets).
+ *     A step that rounds to zero length ends the leg with KO_STEP_CAP.
  *  R11 (Sec. 2, chain of batch midpoints): a body is integrated from its epoch
  *     to the first batch midpoint, then from each midpoint to the next; the
  *     proposed step size is carried along the chain.
@@ -66,7 +70,7 @@ void ko_force_model_default(ko_force_model *fm)
     fm->eps_pc = 1e-16;
     fm->safety = 0.25;
     fm->dt_init = 4.0;
-    fm->max_steps = 1000000;
+    fm->max_steps = 100000;
 }
 
 /* ---- ephemeris table (App. A: SPICE-like segment lookup) ----------------- */
@@ -101,18 +105,22 @@ void ko_ephem_free(ko_ephem *e)
     e->coef = NULL;
 }
 
-/* Position (and velocity) of table body `body` at t: sum_k c_k T_k(tau) with
- * T_k from the textbook three-term recurrence; velocity from dT_k/dtau =
- * k U_{k-1}(tau) and dtau/dt = 2/L. */
-int ko_ephem_eval(const ko_ephem *e, int body, double t, double pos[3], double vel[3])
+/* Position (and velocity) of table body `body` at t0 + off: sum_k c_k T_k(tau)
+ * with T_k from the textbook three-term recurrence; velocity from dT_k/dtau =
+ * k U_{k-1}(tau) and dtau/dt = 2/L.  The Chebyshev argument is formed as
+ * 2((t0 - t_mid) + off)/L so that a small offset from an epoch is not rounded
+ * to the resolution of an absolute Julian date (R10). */
+static int ephem_eval_off(const ko_ephem *e, int body, double t0, double off, double pos[3],
+                          double vel[3])
 {
+    double t = t0 + off;
     double t_end = e->t_start + e->n_seg * e->seg_len;
     if (!(t >= e->t_start && t <= t_end)) return KO_OUT_OF_SPAN;
     int64_t s = (int64_t)floor((t - e->t_start) / e->seg_len);
     if (s < 0) s = 0;
     if (s > e->n_seg - 1) s = e->n_seg - 1;
     double t_mid = e->t_start + ((double)s + 0.5) * e->seg_len;
-    double tau = 2.0 * (t - t_mid) / e->seg_len;
+    double tau = 2.0 * ((t0 - t_mid) + off) / e->seg_len;
     double T[64], U[64];
     int nc = e->n_coef;
     T[0] = 1.0;
@@ -134,6 +142,11 @@ int ko_ephem_eval(const ko_ephem *e, int body, double t, double pos[3], double v
     return KO_OK;
 }
 
+int ko_ephem_eval(const ko_ephem *e, int body, double t, double pos[3], double vel[3])
+{
+    return ephem_eval_off(e, body, t, 0.0, pos, vel);
+}
+
 /* ---- force model: Eq. A.1 = sum over masses of Newton + A.3 + A.4 -------- */
 static void pole_vector(double ra, double dec, double p[3])
 {
@@ -144,15 +157,16 @@ static void pole_vector(double ra, double dec, double p[3])
     p[2] = -se * eq[1] + ce * eq[2];
 }
 
-int ko_accel(const ko_ephem *e, const ko_force_model *fm, double t, const double x[3],
-             const double v[3], double a[3])
+/* acceleration at epoch t0 + off (Eq. A.1); see ephem_eval_off for the offset */
+static int accel_off(const ko_ephem *e, const ko_force_model *fm, double t0, double off,
+                     const double x[3], const double v[3], double a[3])
 {
     const double c = c_au_per_day();
     a[0] = a[1] = a[2] = 0.0;
     for (int m = 0; m < e->n_bodies; m++) {
         if (!((fm->body_mask >> m) & 1u) || e->gm[m] == 0.0) continue;
         double pm[3], vm[3];
-        int st = ko_ephem_eval(e, m, t, pm, vm);
+        int st = ephem_eval_off(e, m, t0, off, pm, vm);
         if (st != KO_OK) return st;
         double mu = e->gm[m];
         double r[3] = {x[0] - pm[0], x[1] - pm[1], x[2] - pm[2]};
@@ -195,6 +209,12 @@ int ko_accel(const ko_ephem *e, const ko_force_model *fm, double t, const double
         }
     }
     return KO_OK;
+}
+
+int ko_accel(const ko_ephem *e, const ko_force_model *fm, double t, const double x[3],
+             const double v[3], double a[3])
+{
+    return accel_off(e, fm, t, 0.0, x, v, a);
 }
 
 /* ---- Gauss-Radau spacings: roots of P7(x)+P8(x) on [-1,1], h=(x+1)/2 ----- */
@@ -312,7 +332,7 @@ static int radau_attempt(const ko_ephem *e, const ko_force_model *fm, double t,
                 xn[i] = x0[i] + v0[i] * dt * s + dt * dt * acc;
                 vn[i] = v0[i] + dt * vacc;
             }
-            int st = ko_accel(e, fm, t + s * dt, xn, vn, F[n]);
+            int st = accel_off(e, fm, t, s * dt, xn, vn, F[n]);
             if (stats) stats->force_evals++;
             if (st != KO_OK) return st;
             /* Newton divided difference g_n from F_0..F_n and g_1..g_{n-1} */
@@ -380,6 +400,7 @@ int ko_propagate(const ko_ephem *e, const ko_force_model *fm, double st[6], doub
              * it joins, so that the sum of the steps equals the elapsed time */
             double t_new = clamped ? t_target : *t + *dt;
             double h = t_new - *t;
+            if (h == 0.0) return KO_STEP_CAP;   /* step below the epoch resolution */
             double x1[3], v1[3], err;
             int s1 = radau_attempt(e, fm, *t, x0, v0, a0, h, x1, v1, &err, stats);
             if (s1 != KO_OK) return s1;
@@ -565,7 +586,7 @@ static int twobody_pos(const ko_ephem *e, const double helio[6], double t_ref, d
                        double pos[3])
 {
     double sun[3], r[3], v[3];
-    int s = ko_ephem_eval(e, 0, t_ref + dt, sun, NULL);
+    int s = ephem_eval_off(e, 0, t_ref, dt, sun, NULL);
     if (s != KO_OK) return s;
     s = ko_kepler(e->gm[0], helio, helio + 3, dt, r, v);
     if (s != KO_OK) return s;
@@ -789,28 +810,42 @@ int ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *stat
     int64_t *bstart = (int64_t *)malloc(sizeof(int64_t) * (n_frames ? n_frames : 1));
     double *tref = (double *)malloc(sizeof(double) * (n_frames ? n_frames : 1));
     int64_t nb = ko_make_batches(ep, n_frames, opt->batch_span, opt->twobody_max, bstart, tref);
-    /* frame centres for the optional prefilter: normalized sum of vertex
-     * directions v_k = n_k x n_{k+1}, radius = max vertex angle */
+    /* frame centres for the optional prefilter: the polygon's vertices are the
+     * intersections n_a x n_b (either sign) lying in every other half-space;
+     * centre = normalized sum of the vertices, radius = largest vertex angle */
     double (*centre)[4] = (double (*)[4])malloc(sizeof(double) * 4 * (n_frames ? n_frames : 1));
     for (int64_t i = 0; i < n_frames; i++) {
         const ko_frame *f = &frames[i];
-        double vs[KO_MAX_EDGES][3], cs[3] = {0, 0, 0};
-        int ne = f->n_edges;
-        for (int k = 0; k < ne; k++) {
-            const double *a = f->normals[k], *b = f->normals[(k + 1) % ne];
-            double x[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2],
-                           a[0] * b[1] - a[1] * b[0]};
-            double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-            double sum_n[3] = {0, 0, 0};
-            for (int q = 0; q < ne; q++)
-                for (int c = 0; c < 3; c++) sum_n[c] += f->normals[q][c];
-            if (x[0] * sum_n[0] + x[1] * sum_n[1] + x[2] * sum_n[2] < 0) xn = -xn;
-            for (int c = 0; c < 3; c++) { vs[k][c] = x[c] / xn; cs[c] += vs[k][c]; }
-        }
+        double vs[2 * KO_MAX_EDGES * KO_MAX_EDGES][3], cs[3] = {0, 0, 0};
+        int ne = f->n_edges, nv = 0;
+        for (int a = 0; a < ne; a++)
+            for (int b = a + 1; b < ne; b++) {
+                const double *p = f->normals[a], *q = f->normals[b];
+                double x[3] = {p[1] * q[2] - p[2] * q[1], p[2] * q[0] - p[0] * q[2],
+                               p[0] * q[1] - p[1] * q[0]};
+                double xn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+                if (!(xn > 0)) continue;
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    int ok = 1;
+                    for (int c = 0; c < ne; c++) {
+                        if (c == a || c == b) continue;
+                        const double *m = f->normals[c];
+                        if (sg * (m[0] * x[0] + m[1] * x[1] + m[2] * x[2]) < 0) ok = 0;
+                    }
+                    if (!ok) continue;
+                    for (int c = 0; c < 3; c++) { vs[nv][c] = sg * x[c] / xn; cs[c] += vs[nv][c]; }
+                    nv++;
+                }
+            }
         double cn = sqrt(cs[0] * cs[0] + cs[1] * cs[1] + cs[2] * cs[2]);
         double rad = 0.0;
+        if (nv < 3 || !(cn > 0)) {
+            centre[i][0] = 1.0; centre[i][1] = 0.0; centre[i][2] = 0.0;
+            centre[i][3] = M_PI;
+            continue;
+        }
         for (int c = 0; c < 3; c++) centre[i][c] = cs[c] / cn;
-        for (int k = 0; k < ne; k++) {
+        for (int k = 0; k < nv; k++) {
             double dd = vs[k][0] * centre[i][0] + vs[k][1] * centre[i][1] + vs[k][2] * centre[i][2];
             double ang = acos(fmax(-1.0, fmin(1.0, dd)));
             if (ang > rad) rad = ang;

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkete_gpu.so")
+PEAK_LIB = os.path.join(HERE, "libkete_peak.so")
 SOURCES = ["kete_prop.cu", "kete_fov.cu", "kete_scan.cu", "kete_abi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC"]
@@ -61,6 +62,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc, "-shared", *ARCH, "-o", tmp, *objs])
         os.replace(tmp, LIB)
+    peak_src = os.path.join(CSRC, "kete_peak.cu")
+    if force or _stale(PEAK_LIB, [peak_src]):
+        tmp = PEAK_LIB + f".tmp{os.getpid()}"
+        run([nvcc, *FLAGS, *ARCH, "-shared", peak_src, "-o", tmp])
+        os.replace(tmp, PEAK_LIB)
     return LIB
 
 

@@ -50,7 +50,25 @@ struct kete_ctx {
     std::vector<cudaEvent_t> ev;    // pool: [0] start, [1] end, then pairs for propagation
     int n_sm = 152;
     int pending_prop_pairs = 0;
+    // phase timers: pairs of events per phase (prep, candidates, exact, order)
+    std::vector<cudaEvent_t> phase_ev[4];
+    int phase_n[4] = {0, 0, 0, 0};
 };
+
+enum Phase { PH_PREP = 0, PH_CAND = 1, PH_EXACT = 2, PH_ORDER = 3 };
+
+static void phase_mark(kete_ctx *ctx, int ph, bool begin)
+{
+    size_t idx = 2 * (size_t)ctx->phase_n[ph] + (begin ? 0 : 1);
+    auto &v = ctx->phase_ev[ph];
+    while (v.size() <= idx) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        v.push_back(e);
+    }
+    cudaEventRecord(v[idx], ctx->stream);
+    if (!begin) ctx->phase_n[ph]++;
+}
 
 static int fail(kete_ctx *c, int code, const char *fmt, ...)
 {
@@ -130,6 +148,7 @@ static void stats_begin(kete_ctx *ctx)
 {
     std::memset(&ctx->stats, 0, sizeof(ctx->stats));
     ctx->pending_prop_pairs = 0;
+    for (int q = 0; q < 4; q++) ctx->phase_n[q] = 0;
     cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream);
     cudaEventRecord(event_at(ctx, 0), ctx->stream);
 }
@@ -169,6 +188,18 @@ static void stats_collect(kete_ctx *ctx)
     ctx->stats.iterations = (int64_t)ctx->h_ctr->iterations;
     ctx->stats.prop_launches = ctx->pending_prop_pairs;
     ctx->pending_prop_pairs = 0;
+    double *dst[4] = {&ctx->stats.prep_ms, &ctx->stats.cand_ms, &ctx->stats.exact_ms,
+                      &ctx->stats.order_ms};
+    for (int q = 0; q < 4; q++) {
+        double acc = 0.0;
+        for (int k = 0; k < ctx->phase_n[q]; k++) {
+            float m = 0.0f;
+            cudaEventElapsedTime(&m, ctx->phase_ev[q][2 * k], ctx->phase_ev[q][2 * k + 1]);
+            acc += m;
+        }
+        *dst[q] = acc;
+        ctx->phase_n[q] = 0;
+    }
 }
 
 extern "C" {
@@ -196,7 +227,7 @@ void kete_force_model_default(kete_force_model *fm)
     fm->safety = 0.25;
     fm->dt_init = 4.0;
     fm->max_iter = 12;
-    fm->max_steps = 1000000;
+    fm->max_steps = 100000;
 }
 
 void kete_survey_opts_default(kete_survey_opts *opt)
@@ -249,6 +280,8 @@ void kete_destroy(kete_ctx *ctx)
     if (ctx->d_ctr) cudaFree(ctx->d_ctr);
     if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
     for (auto e : ctx->ev) cudaEventDestroy(e);
+    for (auto &v : ctx->phase_ev)
+        for (auto e : v) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -515,6 +548,7 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
     GET(S_EX, nf + 1, ex);
     GET(S_FCEN, 4 * nf, fcen);
     GET(S_FAUX, nf, faux);
+    phase_mark(ctx, PH_PREP, true);
     CUDA_TRY(fov_frame_prep(frames, nf, n_obs, is_start, fcen, faux, ctx->d_ctr, st));
     GET(S_SCANTMP, scan_tmp_elems(nf), scan_tmp);
     CUDA_TRY(exclusive_scan(is_start, nf, ex, scan_tmp, st));
@@ -567,6 +601,7 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
     GET(S_BRMAX, nb, B.rmax);
     GET(S_BSUN, 6 * nb, B.sun);
     CUDA_TRY(fov_batch_info(ctx->E, X, B, nb, ctx->d_ctr, st));
+    phase_mark(ctx, PH_PREP, false);
     launches++;
     // ---- sky cells -------------------------------------------------------------
     float maxrad;
@@ -623,6 +658,7 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
         GET(S_CELLSTART, nkeys + 1, cstart);
         GET(S_CELLEXP, nek, cexp);
         GET(S_SCANTMP, std::max(scan_tmp_elems(nkeys), scan_tmp_elems(nf)), scan_tmp);
+        phase_mark(ctx, PH_CAND, true);
         CUDA_TRY(cudaMemsetAsync(ccnt, 0, nkeys * sizeof(int32_t), st));
         CUDA_TRY(cudaMemsetAsync(ccur, 0, nkeys * sizeof(int32_t), st));
         CUDA_TRY(fov_cell_keys(X, G, e0, e1, k0, ckey, ccnt, st));
@@ -660,6 +696,7 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
         CUDA_TRY(exclusive_scan(exp_cnt + e0, nek, exp_off, scan_tmp, st));
         CUDA_TRY(cudaMemsetAsync(exp_cur, 0, nek * sizeof(int32_t), st));
         CUDA_TRY(fov_cand_scatter((const uint2 *)ctx->slot[S_CAND].p, ncand, exp_off, e0, exp_cur, cand_body, st));
+        phase_mark(ctx, PH_CAND, false);
         launches += 3;
         // exact two-body + light time + polygon test
         for (int attempt = 0; attempt < 3; attempt++) {
@@ -670,7 +707,9 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
             xa.exp_off = exp_off; xa.cand_body = cand_body; xa.exp_first = exp_first;
             xa.hits = hit_tmp; xa.cap = hit_cap; xa.frame_cnt = frame_cnt; xa.status = cs.status;
             xa.ctr = ctx->d_ctr;
+            phase_mark(ctx, PH_EXACT, true);
             CUDA_TRY(fov_exact(xa, ctx->n_sm, st));
+            phase_mark(ctx, PH_EXACT, false);
             launches++;
             unsigned long long nh = 0;
             CUDA_TRY(cudaMemcpyAsync(&nh, &ctx->d_ctr->hits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -724,9 +763,11 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
         GET(S_FRAMEOFF, nf + 1, frame_off);
         GET(S_FRAMECUR, nf, frame_cur);
         GET(S_HITGROUP, hits_total, grouped);
+        phase_mark(ctx, PH_ORDER, true);
         CUDA_TRY(exclusive_scan(frame_cnt, nf, frame_off, scan_tmp, st));
         CUDA_TRY(cudaMemsetAsync(frame_cur, 0, nf * sizeof(int32_t), st));
         CUDA_TRY(fov_order_hits(hit_tmp, hits_total, frame_off, nf, frame_cur, grouped, hits, ctx->n_sm, st));
+        phase_mark(ctx, PH_ORDER, false);
         launches += 4;
     }
     r = stats_end(ctx);

@@ -39,14 +39,18 @@ struct Seg {
     double tau;
 };
 
-__device__ __forceinline__ bool ephem_seg(const EphemDev &E, double t, Seg &g)
+// Segment and Chebyshev argument at the epoch t0 + off.  tau is formed as
+// 2((t0 - t_mid) + off)/L so that a small offset (a substep, a light-time
+// interval) is never rounded to the resolution of an absolute Julian date.
+__device__ __forceinline__ bool ephem_seg(const EphemDev &E, double t0, double off, Seg &g)
 {
+    const double t = t0 + off;
     if (!(t >= E.t_start && t <= E.t_end)) return false;
     int s = (int)floor((t - E.t_start) * E.inv_seg);
     s = s < 0 ? 0 : (s > E.n_seg - 1 ? E.n_seg - 1 : s);
     double t_mid = E.t_start + ((double)s + 0.5) * E.seg_len;
     g.s = s;
-    g.tau = 2.0 * (t - t_mid) * E.inv_seg;
+    g.tau = 2.0 * ((t0 - t_mid) + off) * E.inv_seg;
     return true;
 }
 
@@ -102,12 +106,13 @@ __device__ __forceinline__ const double *ephem_coef(const EphemDev &E, int body,
 //           z = r.p with p the body's pole; the same vector written in the
 //           body's equatorial frame is the component form of Eq. A.4)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, double t,
-                                          const double x[3], const double v[3], double a[3])
+__device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, double t0,
+                                          double off, const double x[3], const double v[3],
+                                          double a[3])
 {
     Seg g;
     a[0] = a[1] = a[2] = 0.0;
-    if (!ephem_seg(E, t, g)) return KETE_BODY_OUT_OF_SPAN;
+    if (!ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
     const double dtau_dt = 2.0 * E.inv_seg;
     for (int m = 0; m < E.n_bodies; m++) {
         if (!((F.active_mask >> m) & 1u)) continue;

@@ -1,7 +1,7 @@
 // kete_fov.cu -- the FoV stage of the survey path (Sec. 2, Sec. 3.1, App. A.1).
 //
 //   frame prep   validate frames, find exposure boundaries, circumscribed cap
-//                of every polygon (from its vertices n_k x n_{k+1})
+//                of every polygon (from its vertices, found in any edge order)
 //   exposures    epoch, observer, cap covering all sub-fields
 //   batching     greedy <= span batches over epoch-sorted exposures, t_ref =
 //                midpoint of first and last epoch (Sec. 2)
@@ -68,26 +68,38 @@ __global__ void k_frame_prep(const kete_frame *__restrict__ fr, int64_t nf, int6
         ne = 3;
     }
     if (!isfinite(f.epoch)) set_flag(ctr, 4);
-    // vertices v_k = n_k x n_{k+1}, oriented towards the sum of inward normals
-    double sn[3] = {0, 0, 0};
-    for (int k = 0; k < ne; k++)
-        for (int c = 0; c < 3; c++) sn[c] += f.normals[k][c];
+    // vertices: intersections n_a x n_b (either sign) that satisfy every
+    // other half-space; independent of the order the edges are listed in
     double cen[3] = {0, 0, 0};
-    double vx[KETE_MAX_EDGES][3];
+    double vx[2 * KETE_MAX_EDGES * (KETE_MAX_EDGES - 1) / 2][3];
+    int nv = 0;
     bool bad = false;
-    for (int k = 0; k < ne; k++) {
-        const double *a = f.normals[k], *b = f.normals[(k + 1) % ne];
-        double v0 = a[1] * b[2] - a[2] * b[1];
-        double v1 = a[2] * b[0] - a[0] * b[2];
-        double v2 = a[0] * b[1] - a[1] * b[0];
-        double vn = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-        if (!(vn > 0.0) || !isfinite(vn)) bad = true;
-        if (v0 * sn[0] + v1 * sn[1] + v2 * sn[2] < 0.0) vn = -vn;
-        vx[k][0] = v0 / vn;
-        vx[k][1] = v1 / vn;
-        vx[k][2] = v2 / vn;
-        for (int c = 0; c < 3; c++) cen[c] += vx[k][c];
+    for (int a = 0; a < ne; a++) {
+        double na = sqrt(dot3(f.normals[a], f.normals[a]));
+        if (!(na > 0.0) || !isfinite(na)) bad = true;
+        for (int b = a + 1; b < ne; b++) {
+            const double *A = f.normals[a], *Bn = f.normals[b];
+            double v[3] = {A[1] * Bn[2] - A[2] * Bn[1], A[2] * Bn[0] - A[0] * Bn[2],
+                           A[0] * Bn[1] - A[1] * Bn[0]};
+            double vn = sqrt(dot3(v, v));
+            if (!(vn > 0.0)) continue;
+            for (int sgn = 0; sgn < 2; sgn++) {
+                double w[3] = {v[0] / vn, v[1] / vn, v[2] / vn};
+                if (sgn) { w[0] = -w[0]; w[1] = -w[1]; w[2] = -w[2]; }
+                bool ok = true;
+                for (int c = 0; c < ne; c++) {
+                    if (c == a || c == b) continue;
+                    double nc = sqrt(dot3(f.normals[c], f.normals[c]));
+                    if (dot3(f.normals[c], w) < -1e-12 * nc) ok = false;
+                }
+                if (ok && nv < 2 * KETE_MAX_EDGES * (KETE_MAX_EDGES - 1) / 2) {
+                    for (int q = 0; q < 3; q++) { vx[nv][q] = w[q]; cen[q] += w[q]; }
+                    nv++;
+                }
+            }
+        }
     }
+    if (nv < 3) bad = true;
     double cn = sqrt(dot3(cen, cen));
     double rad = 0.0;
     if (bad || !(cn > 0.0)) {
@@ -96,7 +108,7 @@ __global__ void k_frame_prep(const kete_frame *__restrict__ fr, int64_t nf, int6
         rad = kPi;
     } else {
         for (int c = 0; c < 3; c++) cen[c] /= cn;
-        for (int k = 0; k < ne; k++) {
+        for (int k = 0; k < nv; k++) {
             double d = fmin(1.0, fmax(-1.0, dot3(cen, vx[k])));
             rad = fmax(rad, acos(d));
         }
@@ -252,7 +264,7 @@ __global__ void k_batch_info(EphemDev E, ExpArrays X, BatchArrays B, int32_t n_b
         B.rmax[k] = c;
         Seg g;
         double p[3] = {0, 0, 0}, v[3] = {0, 0, 0};
-        if (ephem_seg(E, tr, g)) {
+        if (ephem_seg(E, tr, 0.0, g)) {
             cheb_pos_vel(ephem_coef(E, 0, g.s), E.n_coef, g.tau, 2.0 * E.inv_seg, p, v);
         } else {
             set_flag(ctr, 5);
@@ -461,7 +473,7 @@ __device__ __forceinline__ bool twobody_pos(const EphemDev &E, double mu, double
     bool ok = kepler_uv(mu, sqmu, hr, hv, dt, chi, r, v);
     Seg g;
     double sp[3] = {0, 0, 0};
-    if (ephem_seg(E, t_ref + dt, g)) cheb_pos(ephem_coef(E, 0, g.s), E.n_coef, g.tau, sp);
+    if (ephem_seg(E, t_ref, dt, g)) cheb_pos(ephem_coef(E, 0, g.s), E.n_coef, g.tau, sp);
     else ok = false;
     pos[0] = sp[0] + r[0];
     pos[1] = sp[1] + r[1];

@@ -104,7 +104,7 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
                 vn[i] = fma(sh, pv, v0[i]);
             }
             double Fn[3];
-            int st = accel_fp64(E, F, t + sh, xn, vn, Fn);
+            int st = accel_fp64(E, F, t, sh, xn, vn, Fn);
             cnt.evals++;
             if (st != KETE_BODY_OK) return st;
 #pragma unroll
@@ -162,7 +162,7 @@ __device__ int integrate_to(const EphemDev &E, const ForceDev &F, double x[3], d
     long long attempts = 0;
     while (t != target) {
         double a0[3];
-        int st = accel_fp64(E, F, t, x, v, a0);
+        int st = accel_fp64(E, F, t, 0.0, x, v, a0);
         cnt.evals++;
         if (st != KETE_BODY_OK) return st;
         for (;;) {
@@ -172,6 +172,7 @@ __device__ int integrate_to(const EphemDev &E, const ForceDev &F, double x[3], d
             // the step is the exact difference of the representable epochs it joins
             const double t_new = clamped ? target : t + dt;
             const double h = t_new - t;
+            if (h == 0.0) return KETE_BODY_STEP_CAP;   // step below the epoch resolution
             double x1[3], v1[3], err;
             st = radau_attempt(E, F, t, x, v, a0, h, x1, v1, err, cnt);
             if (st != KETE_BODY_OK) return st;
@@ -299,7 +300,7 @@ __global__ void k_ephem_eval(EphemDev E, const double *__restrict__ t, int64_t n
     if (i >= n) return;
     Seg g;
     double p[3], v[3];
-    if (!ephem_seg(E, t[i], g)) {
+    if (!ephem_seg(E, t[i], 0.0, g)) {
         for (int c = 0; c < 3; c++) {
             pos[3 * i + c] = __longlong_as_double(0x7ff8000000000000ll);
             if (vel) vel[3 * i + c] = __longlong_as_double(0x7ff8000000000000ll);

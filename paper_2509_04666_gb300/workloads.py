@@ -352,7 +352,8 @@ def population(seed: int, ps: PlanetSystem, n_mb: int, n_neo: int = 0, n_trojan:
 # Fields of view: square spherical polygons with inward great-circle normals
 # ---------------------------------------------------------------------------
 def square_normals(centre, e_axis, half_width):
-    """Inward normals m = p sin h - t cos h, t in {+e, -e, +n, -n} (Sec. 3.1)."""
+    """Inward normals m = p sin h - t cos h of the edges t = +e, +n, -e, -n, in
+    that (cyclic) order around the square (Sec. 3.1)."""
     p = centre / np.linalg.norm(centre, axis=-1, keepdims=True)
     e = e_axis - (e_axis * p).sum(-1, keepdims=True) * p
     e /= np.linalg.norm(e, axis=-1, keepdims=True)
@@ -360,8 +361,8 @@ def square_normals(centre, e_axis, half_width):
     sh, ch = math.sin(half_width), math.cos(half_width)
     out = np.empty(p.shape[:-1] + (4, 3))
     out[..., 0, :] = p * sh - e * ch
-    out[..., 1, :] = p * sh + e * ch
-    out[..., 2, :] = p * sh - n * ch
+    out[..., 1, :] = p * sh - n * ch
+    out[..., 2, :] = p * sh + e * ch
     out[..., 3, :] = p * sh + n * ch
     return out
 

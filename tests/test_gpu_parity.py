@@ -176,6 +176,22 @@ def test_fov_check_multi_detector_exposures(K):
     _compare_hits(got, ref)
 
 
+def test_fov_check_edge_order_does_not_matter(K, mb1k_dense):
+    """The polygon is the intersection of its half-spaces: listing the edges in
+    another order gives the same hits."""
+    w = mb1k_dense
+    shuffled = w.frames.copy()
+    rng = np.random.default_rng(4)
+    for i in range(len(shuffled)):
+        shuffled["normals"][i] = shuffled["normals"][i][rng.permutation(4)]
+    from dataclasses import replace
+    w2 = replace(w, frames=shuffled)
+    a, _ = _hits_gpu(K, w)
+    b, _ = _hits_gpu(K, w2)
+    for key in ("frame", "body", "ra", "dec"):
+        assert np.array_equal(a[key].numpy(), b[key].numpy())
+
+
 def test_fov_check_capacity_and_edge_cases(K, mb1k_dense):
     import torch
     from paper_2509_04666_gb300 import kete
@@ -227,3 +243,18 @@ def test_fov_check_exposure_layout_errors(K, mb1k):
     bad = mb1k.frames.copy(); bad["n_edges"][2] = 7
     with pytest.raises(kete.KeteError):
         K.fov_check(st, ep, kete.frames_to_device(bad, "cuda"), ob)
+
+
+def test_close_encounter_matches_oracle(K, mb1k):
+    """A 0.01 AU Earth encounter: GPU and oracle agree through the encounter."""
+    from test_oracle_integrator import _earth_encounter_body
+    K.load_ephem(mb1k.ephem.to_bytes())
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    st0 = np.stack([_earth_encounter_body(orc, W.T0 + 12.0, miss=m) for m in (0.003, 0.01, 0.03)], 1)
+    s = _dev(st0.copy()); e = _dev(np.full(3, W.T0))
+    status = K.propagate(s, e, W.T0 + 25.0)
+    assert (status.cpu().numpy() == 0).all()
+    for j in range(3):
+        rc, ref, *_ = orc.propagate(orc.force_model(), st0[:, j], W.T0, W.T0 + 25.0)
+        assert rc == 0
+        assert np.abs(s.cpu().numpy()[:3, j] - ref[:3]).max() < 1e-9
