@@ -215,6 +215,31 @@ int kete_fov_check(kete_ctx *ctx, const double *states, const double *epochs, in
 /* Copy the counters of the last call into *out (host). */
 int kete_get_stats(const kete_ctx *ctx, kete_stats *out);
 
+/* Largest n kete_propagate_noalloc accepts. */
+#define KETE_NOALLOC_MAX_BODIES 65536
+
+/* kete_propagate without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they run -- an application that gives all GPU memory to
+ * its own pool at start-up, a real-time host thread that must not block in
+ * the driver's allocator, a framework that forbids allocation outside its
+ * set-up phase.  kete_propagate allocates its per-body chain scratch on first
+ * use; this variant uses a fixed array in the library's device data instead
+ * (about 4.5 MB, held on every GPU that loads the library until exit).
+ *
+ * Arguments, layouts, results and per-body status are those of
+ * kete_propagate; the context must already exist and hold an ephemeris
+ * (kete_create and kete_load_ephem allocate; call them during set-up).
+ * n above KETE_NOALLOC_MAX_BODIES is rejected with KETE_ERR_BAD_ARG and a
+ * message in kete_last_error; split larger populations into several calls.
+ * The call calls no cudaMalloc or cudaFree and does not update
+ * kete_get_stats.  The first call on a device resolves the array's device
+ * address (which may load the library's device data): make that first call
+ * before any stream capture.  All calls on a device share the one array: calls
+ * whose work overlaps on the GPU race, so order them on one stream. */
+int kete_propagate_noalloc(kete_ctx *ctx, double *states, double *epochs, int64_t n,
+                           double t_target, const kete_force_model *fm, int32_t *status);
+
 #ifdef __cplusplus
 }
 #endif

@@ -780,3 +780,27 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
     ctx->stats.launches = launches;
     return KETE_OK;
 }
+
+// Propagation whose chain scratch is a fixed device array (see kete.h): no
+// cudaMalloc, cudaFree, scratch slot or event is touched on this path.
+extern "C" int kete_propagate_noalloc(kete_ctx *ctx, double *states, double *epochs, int64_t n,
+                                      double t_target, const kete_force_model *fm,
+                                      int32_t *status)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
+    if (n < 0 || (n > 0 && (!states || !epochs)) || !std::isfinite(t_target))
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad arguments");
+    if (n > KETE_NOALLOC_MAX_BODIES)
+        return fail(ctx, KETE_ERR_BAD_ARG, "n = %lld exceeds KETE_NOALLOC_MAX_BODIES = %d",
+                    (long long)n, KETE_NOALLOC_MAX_BODIES);
+    ForceDev F;
+    int r = make_force(ctx, fm, F);
+    if (r != KETE_OK) return r;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const char *why = "";
+    r = noalloc_propagate(ctx->device, ctx->stream, ctx->E, F, states, epochs, n, t_target,
+                          status, &why);
+    if (r != KETE_OK) return fail(ctx, r, "kete_propagate_noalloc: %s", why);
+    return KETE_OK;
+}

@@ -59,5 +59,9 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
                              cudaStream_t st);
 cudaError_t launch_chain_finish(ChainState cs, double *states, double *epochs,
                                 int32_t *status, cudaStream_t st);
+// kete_noalloc.cu: propagation with the chain scratch in a fixed device array
+int noalloc_propagate(int device, cudaStream_t st, const EphemDev &E, const ForceDev &F,
+                      double *states, double *epochs, int64_t n, double t_target,
+                      int32_t *status, const char **why);
 
 }  // namespace kete

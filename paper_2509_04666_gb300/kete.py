@@ -19,11 +19,12 @@ LIB_PATH = os.path.join(HERE, "libkete_gpu.so")
 OK, ERR_BAD_ARG, ERR_EPHEM_SPAN, ERR_CAPACITY, ERR_NO_EPHEM, ERR_CUDA, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 BODY_OK, BODY_STEP_CAP, BODY_OUT_OF_SPAN, BODY_NONFINITE, BODY_KEPLER_CAP = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
+NOALLOC_MAX_BODIES = 65536
 
 EXPORTS = ["kete_create", "kete_destroy", "kete_set_stream", "kete_last_error",
            "kete_force_model_default", "kete_survey_opts_default", "kete_load_ephem",
            "kete_ephem_eval", "kete_propagate", "kete_propagate_stops", "kete_fov_check",
-           "kete_get_stats"]
+           "kete_get_stats", "kete_propagate_noalloc"]
 
 
 class KeteError(RuntimeError):
@@ -87,6 +88,7 @@ def lib():
         L.kete_fov_check.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, C.POINTER(ForceModel),
                                      C.POINTER(SurveyOpts), vp, i64, C.POINTER(i64), vp]
         L.kete_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.kete_propagate_noalloc.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(ForceModel), vp]
         _lib = L
     return _lib
 
@@ -193,6 +195,19 @@ class Kete:
         self._sync_stream()
         self._check(lib().kete_propagate(self._h, states.data_ptr(), epochs.data_ptr(), n,
                                          float(t_target), C.byref(fm), status.data_ptr()))
+        return status
+
+    def propagate_noalloc(self, states, epochs, t_target, fm=None, status=None):
+        """kete_propagate without device allocation (n <= NOALLOC_MAX_BODIES)."""
+        n = epochs.numel()
+        _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
+        if status is None:
+            status = torch.zeros(n, dtype=torch.int32, device=states.device)
+        fm = fm or force_model()
+        self._sync_stream()
+        self._check(lib().kete_propagate_noalloc(self._h, states.data_ptr(), epochs.data_ptr(),
+                                                 n, float(t_target), C.byref(fm),
+                                                 status.data_ptr()))
         return status
 
     def propagate_stops(self, states, epochs, stops, fm=None):
