@@ -49,24 +49,39 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def flops_per_eval(n_active, n_gr, n_j2, n_coef):
-    """FP64 FLOPs of one acceleration evaluation as the kernel computes it
-    (FMA = 2): Clenshaw position (3 per term per coordinate), position +
-    velocity for GR bodies, Newton, GR (Eq. A.3) and J2 (Eq. A.4) terms."""
-    cheb_pos = 3 * (3 * (n_coef - 1) + 3)
-    cheb_posvel = cheb_pos + 3 * (4 * (n_coef - 1) + 1)
-    newton, gr, j2 = 19, 27, 21
-    return ((n_active - n_gr) * (cheb_pos + newton) + n_gr * (cheb_posvel + newton + gr)
-            + n_j2 * j2 + 10)
+def _bits(m):
+    return bin(m & 0x1FF).count("1")
 
 
-FLOPS_PER_ITER = 1482    # 7 substep predictors (x and v) + g/b updates + convergence test
-FLOPS_PER_ATTEMPT = 130  # final x1, v1 and step control
-
-
-def algorithmic_flops(st, fpe):
-    return (st["force_evals"] * fpe + st["iterations"] * FLOPS_PER_ITER
-            + (st["steps"] + st["rejected"]) * FLOPS_PER_ATTEMPT)
+def prop_flops(st, fm, n_coef, mixed):
+    """Algorithmic FLOPs of k_propagate from its counters (FMA = 2), as the
+    kernel computes them for the force model fm:
+      per force evaluation from node rows: per active mass 25 (Newton incl.
+        relative position and velocity), +25 per GR mass (Eq. A.3), +21 per J2
+        mass (Eq. A.4);
+      per-thread evaluation (step not spanning a whole leg): + a Clenshaw sum
+        of position and velocity per mass, 3 x (7 (n_coef - 1) + 4);
+      per corrector iteration: 7 substep predictors (x, v) and the g/b
+        updates, 1440 (+48 for the FP64-part b6 in mixed precision);
+      per step attempt: final x, v and step control, 121.
+    In mixed precision the FP64 work of an evaluation is the Sun's monopole
+    (19) plus, per-thread, the Sun's Clenshaw sum; the planetary terms are FP32.
+    Returns (fp64_flops, fp32_flops)."""
+    act, gr, j2 = _bits(fm.body_mask), _bits(fm.gr_mask), _bits(fm.j2_mask)
+    cheb = 3 * (7 * (n_coef - 1) + 4)
+    evals, node = st["force_evals"], st["node_evals"]
+    attempts = st["steps"] + st["rejected"]
+    if not mixed:
+        per = 25 * act + 25 * gr + 21 * j2
+        f64 = evals * per + (evals - node) * (act * cheb + 10)
+        f64 += st["iterations"] * 1440 + attempts * 121
+        return f64, 0
+    f64 = evals * 19 + (evals - node) * (cheb + 10) + st["iterations"] * 1488 + attempts * 121
+    f64 += st["steps"] * 8 * (act - 1)          # close-planet check at each step start
+    sun_gr, sun_j2 = fm.gr_mask & 1, fm.j2_mask & 1
+    per32 = 25 * (act - 1) + 25 * (gr - sun_gr) + 21 * (j2 - sun_j2) + 25 * sun_gr + 21 * sun_j2
+    f32 = evals * per32 + (evals - node) * (act - 1) * cheb
+    return f64, f32
 
 
 class Clocks:
@@ -176,6 +191,26 @@ def run_reference(args):
     return 0
 
 
+def compare_sample(kete, hits, nh, sub, ref):
+    """GPU hits restricted to the sampled bodies vs the oracle's hits."""
+    got = kete.decode_hits(hits, nh)
+    keep = np.isin(got["body"].numpy(), sub)
+    g = {(int(f), int(b)): (ra, de) for f, b, ra, de in
+         zip(got["frame"].numpy()[keep], got["body"].numpy()[keep], got["ra"].numpy()[keep],
+             got["dec"].numpy()[keep])}
+    r = {(int(h["frame"]), int(h["body"])): h for h in ref}
+    worst = 0.0
+    for key in set(g) & set(r):
+        ra, de = g[key]
+        dra = (ra - r[key]["ra"] + math.pi) % (2 * math.pi) - math.pi
+        worst = max(worst, math.hypot(dra * math.cos(de), de - r[key]["dec"]))
+    band = max(1e-9, 2 * worst)
+    mism = [k for k in set(g) ^ set(r) if k not in r or abs(r[k]["margin"]) >= band]
+    return {"sampled_bodies": len(sub), "oracle_hits": len(r), "gpu_hits": len(g),
+            "edge_band_rad": band, "mismatch_outside_edge_band": len(mism),
+            "max_sky_err_mas": worst / MAS}
+
+
 def peak_fma(fp64: bool):
     import ctypes as C
     from paper_2509_04666_gb300 import build as B
@@ -248,11 +283,9 @@ def run_gb300(args):
     checks = world * n * nf / (ms / 1e3)
     # ---- roofline of the dominant kernel (k_propagate, FP64 ALU bound) --------
     s0 = stats[-1]
-    fm_py = fm
-    n_active = bin(fm_py.body_mask & 0x1FF).count("1")
-    fpe = flops_per_eval(n_active, bin(fm_py.gr_mask & 0x1FF).count("1"),
-                         bin(fm_py.j2_mask & 0x1FF).count("1"), w.ephem.n_coef)
-    flops = statistics.mean(algorithmic_flops(s, fpe) for s in stats)
+    mixed = args.precision == "mixed"
+    flops = statistics.mean(prop_flops(s, fm, w.ephem.n_coef, mixed)[0] for s in stats)
+    flops32 = statistics.mean(prop_flops(s, fm, w.ephem.n_coef, mixed)[1] for s in stats)
     prop_ms = statistics.mean(s["prop_ms"] for s in stats)
     achieved = flops / (prop_ms / 1e3) / 1e12
     peak_nominal = 152 * 2 * 2 * 2.07e9 / 1e12      # SMs x FP64 FMA/clk x 2 x max clock
@@ -293,20 +326,30 @@ def run_gb300(args):
         cpu = {"value": len(sub) * 365.0 / dt, "unit": "body-days/s", "cores": nt, "kind": "oracle",
                "sample": f"{len(sub)} evenly spaced bodies x all {nf} frames, full year, "
                          f"{dt:.1f} s"}
-        got = kete.decode_hits(hits, nh)
-        keep = np.isin(got["body"].numpy(), sub)
-        g = {(int(f), int(b)): (ra, de) for f, b, ra, de in
-             zip(got["frame"].numpy()[keep], got["body"].numpy()[keep], got["ra"].numpy()[keep],
-                 got["dec"].numpy()[keep])}
-        r = {(int(h["frame"]), int(h["body"])): h for h in ref}
-        mism = [k for k in set(g) ^ set(r) if k not in r or abs(r[k]["margin"]) >= 1e-9]
-        worst = 0.0
-        for key in set(g) & set(r):
-            ra, de = g[key]
-            dra = (ra - r[key]["ra"] + math.pi) % (2 * math.pi) - math.pi
-            worst = max(worst, math.hypot(dra * math.cos(de), de - r[key]["dec"]))
-        accuracy = {"sampled_bodies": len(sub), "oracle_hits": len(r), "gpu_hits": len(g),
-                    "mismatch_outside_edge_band": len(mism), "max_sky_err_mas": worst / MAS}
+        accuracy = compare_sample(kete, hits, nh, sub, ref)
+    # ---- the mixed-precision form on the same workload (speedup at accuracy) ------
+    mixed_leg = None
+    if args.precision == "fp64" and not args.no_mixed:
+        fm_m = kete.force_model(precision=kete.MIXED)
+        hm = torch.empty_like(hits)
+        K.fov_check(st, ep, fr, ob, fm=fm_m, hits=hm)
+        mt = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, nhm, _ = K.fov_check(st, ep, fr, ob, fm=fm_m, hits=hm)
+            e1.record(stream)
+            e1.synchronize()
+            mt.append(e0.elapsed_time(e1))
+        mm = statistics.mean(mt)
+        sm = K.get_stats()
+        f64m, f32m = prop_flops(sm, fm_m, w.ephem.n_coef, True)
+        mixed_leg = {"value": world * n * 365.0 / (mm / 1e3), "ms_per_step": mm,
+                     "speedup_vs_fp64": ms / mm, "prop_ms": sm["prop_ms"],
+                     "prop_fp64_tflops": f64m / (sm["prop_ms"] / 1e3) / 1e12,
+                     "prop_fp32_tflops": f32m / (sm["prop_ms"] / 1e3) / 1e12,
+                     "accuracy": compare_sample(kete, hm, nhm, sub, ref) if cpu else None}
     out = {
         "metric": METRIC, "value": value, "unit": "body-days/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -320,14 +363,18 @@ def run_gb300(args):
                      "peak": peak_nominal, "unit": "TFLOP/s", "frac": achieved / peak_nominal,
                      "traffic": traffic, "peak_probe_measured": (peak_probe or 0) / 1e12,
                      "flops_per_launch": flops / max(1, s0["prop_launches"]),
+                     "fp32_tflops_alongside": flops32 / (prop_ms / 1e3) / 1e12,
                      "prop_ms_per_step": prop_ms, "peak_basis": "152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
         "cpu_baseline": cpu,
         "accuracy": accuracy,
+        "mixed_precision": mixed_leg,
         "e2e": e2e,
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "clocks": clocks,
-        "counters": {k: s0[k] for k in ("steps", "rejected", "force_evals", "iterations",
-                                        "n_batches", "n_exposures", "n_candidates", "n_hits")},
+        "counters": {k: s0[k] for k in ("steps", "rejected", "force_evals", "node_evals",
+                                        "iterations", "n_batches", "n_exposures",
+                                        "n_candidates", "n_hits")},
+        "phases_ms": {k: s0[k] for k in ("prop_ms", "prep_ms", "cand_ms", "exact_ms", "order_ms")},
         "wall_s_timed": t_wall,
     }
     if rank == 0:
@@ -350,6 +397,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=768)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -139,6 +139,8 @@ typedef struct kete_stats {
     double cand_ms;              /* candidate search */
     double exact_ms;             /* two-body + light-time + polygon test */
     double order_ms;             /* hit ordering */
+    int64_t node_evals;          /* force evaluations served by batch node rows (steps that
+                                    span a whole leg between consecutive stops) */
 } kete_stats;
 
 typedef struct kete_ctx kete_ctx;

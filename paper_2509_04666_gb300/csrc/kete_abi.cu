@@ -25,7 +25,8 @@ enum Slot {
     S_EXPFIRST, S_XEPOCH, S_XOBS, S_XCEN, S_XRAD, S_XCS, S_XBATCH, S_NEXT, S_BFIRST, S_BTREF,
     S_BO, S_BROBS, S_BTSPAN, S_BRMAX, S_BSUN, S_NBATCH, S_BANDS, S_CELLKEY, S_CELLCNT,
     S_CELLSTART, S_CELLCUR, S_CELLEXP, S_CAND, S_EXPCNT, S_EXPOFF, S_EXPCUR, S_CANDBODY,
-    S_HITTMP, S_FRAMECNT, S_FRAMEOFF, S_FRAMECUR, S_HITGROUP, S_MAXRAD, S_NSLOTS
+    S_HITTMP, S_FRAMECNT, S_FRAMEOFF, S_FRAMECUR, S_HITGROUP, S_MAXRAD, S_NT_T0, S_NT_H,
+    S_NT_R64, S_NT_R32, S_NSLOTS
 };
 
 struct Scratch {
@@ -186,6 +187,7 @@ static void stats_collect(kete_ctx *ctx)
     ctx->stats.rejected = (int64_t)ctx->h_ctr->rejected;
     ctx->stats.force_evals = (int64_t)ctx->h_ctr->force_evals;
     ctx->stats.iterations = (int64_t)ctx->h_ctr->iterations;
+    ctx->stats.node_evals = (int64_t)ctx->h_ctr->node_evals;
     ctx->stats.prop_launches = ctx->pending_prop_pairs;
     ctx->pending_prop_pairs = 0;
     double *dst[4] = {&ctx->stats.prep_ms, &ctx->stats.cand_ms, &ctx->stats.exact_ms,
@@ -406,6 +408,27 @@ extern "C" int kete_ephem_eval(kete_ctx *ctx, const double *t, int64_t n, int bo
     return KETE_OK;
 }
 
+// Planet states at the Gauss-Radau node epochs of every leg of a chain of stops.
+static int node_table(kete_ctx *ctx, const double *stops_dev, int n_stops, const double *epochs,
+                      NodeTable &nt)
+{
+    const int nb = ctx->E.n_bodies;
+    double *t0, *h, *r64;
+    float *r32;
+    GET(S_NT_T0, n_stops, t0);
+    GET(S_NT_H, n_stops, h);
+    GET(S_NT_R64, (size_t)n_stops * 8 * nb * 6, r64);
+    GET(S_NT_R32, (size_t)n_stops * 8 * nb * 6, r32);
+    CUDA_TRY(launch_node_table(ctx->E, stops_dev, n_stops, epochs, t0, h, r64, r32, ctx->stream));
+    nt.t0 = t0;
+    nt.h = h;
+    nt.row64 = r64;
+    nt.row32 = r32;
+    nt.n_legs = n_stops;
+    nt.nb = nb;
+    return KETE_OK;
+}
+
 static int run_chain(kete_ctx *ctx, const ForceDev &F, const double *states, const double *epochs,
                      int64_t n, ChainState &cs)
 {
@@ -435,11 +458,14 @@ extern "C" int kete_propagate(kete_ctx *ctx, double *states, double *epochs, int
         double *d_stop;
         GET(S_STOPS, 1, d_stop);
         CUDA_TRY(cudaMemcpyAsync(d_stop, &t_target, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        NodeTable nt;
+        r = node_table(ctx, d_stop, 1, epochs, nt);
+        if (r != KETE_OK) return r;
         prop_event(ctx, true);
-        CUDA_TRY(launch_propagate(ctx->E, F, cs, d_stop, 1, states, n, true, ctx->d_ctr, ctx->stream));
+        CUDA_TRY(launch_propagate(ctx->E, F, cs, d_stop, 1, states, n, true, ctx->d_ctr, ctx->stream, &nt, 0));
         prop_event(ctx, false);
         CUDA_TRY(launch_chain_finish(cs, states, epochs, status, ctx->stream));
-        ctx->stats.launches = 3;
+        ctx->stats.launches = 4;
     }
     r = stats_end(ctx);
     if (r != KETE_OK) return r;
@@ -471,11 +497,14 @@ extern "C" int kete_propagate_stops(kete_ctx *ctx, const double *states, const d
         double *d_stops;
         GET(S_STOPS, n_stops, d_stops);
         CUDA_TRY(cudaMemcpyAsync(d_stops, stops, n_stops * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        NodeTable nt;
+        r = node_table(ctx, d_stops, (int)n_stops, epochs, nt);
+        if (r != KETE_OK) return r;
         prop_event(ctx, true);
-        CUDA_TRY(launch_propagate(ctx->E, F, cs, d_stops, (int)n_stops, out, n, false, ctx->d_ctr, ctx->stream));
+        CUDA_TRY(launch_propagate(ctx->E, F, cs, d_stops, (int)n_stops, out, n, false, ctx->d_ctr, ctx->stream, &nt, 0));
         prop_event(ctx, false);
         CUDA_TRY(launch_chain_finish(cs, nullptr, nullptr, status, ctx->stream));
-        ctx->stats.launches = 3;
+        ctx->stats.launches = 4;
     }
     r = stats_end(ctx);
     if (r != KETE_OK) return r;
@@ -639,6 +668,10 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
     kete_hit *hit_tmp;
     GET(S_HITTMP, hit_cap, hit_tmp);
     hit_cap = ctx->slot[S_HITTMP].bytes / sizeof(kete_hit);
+    NodeTable nt;
+    r = node_table(ctx, B.t_ref, nb, epochs, nt);
+    if (r != KETE_OK) return r;
+    launches++;
     unsigned long long hits_total = 0, cands_total = 0;
     for (int32_t k0 = 0; k0 < nb; k0 += C) {
         const int32_t k1 = std::min(nb, k0 + C), nk = k1 - k0;
@@ -646,7 +679,7 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
         const int32_t nek = e1 - e0;
         // propagation to the batch midpoints of this chunk
         prop_event(ctx, true);
-        CUDA_TRY(launch_propagate(ctx->E, F, cs, B.t_ref + k0, nk, stop_states, n, false, ctx->d_ctr, st));
+        CUDA_TRY(launch_propagate(ctx->E, F, cs, B.t_ref + k0, nk, stop_states, n, false, ctx->d_ctr, st, &nt, k0));
         prop_event(ctx, false);
         launches++;
         // exposures of the chunk into sky cells

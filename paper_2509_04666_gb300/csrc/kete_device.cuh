@@ -29,6 +29,7 @@ struct RadauTables {
     double h[8];
     double rinv[8][8];   // 1 / (h_n - h_k), k < n
     double c[8][7];      // c[n][m]: d b_m / d g_n  (Newton -> power basis)
+    double w7[8];        // 1 / prod_{k != n} (h_n - h_k): b6 = g7 = sum_n w7[n] F_n
 };
 
 // ---------------------------------------------------------------------------
@@ -106,58 +107,210 @@ __device__ __forceinline__ const double *ephem_coef(const EphemDev &E, int body,
 //           z = r.p with p the body's pole; the same vector written in the
 //           body's equatorial frame is the component form of Eq. A.4)
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+
+// the three terms of one mass, accumulated into a[]; w = relative velocity
+template <typename T>
+__device__ __forceinline__ void mass_terms(T mu, T j2k, const T *P, bool newton, bool gr, bool j2,
+                                           const T r[3], const T w[3], T a[3])
+{
+    T rr = fma(r[0], r[0], fma(r[1], r[1], r[2] * r[2]));
+    T ri = rsqrt_t<T>(rr);
+    T ri2 = ri * ri;
+    T ri3 = ri2 * ri;
+    T f = newton ? -mu * ri3 : (T)0;
+    if (gr) {
+        T ww = fma(w[0], w[0], fma(w[1], w[1], w[2] * w[2]));
+        T rw = fma(r[0], w[0], fma(r[1], w[1], r[2] * w[2]));
+        T k = mu * ri3 * (T)kInvC2;
+        f = fma(k, fma((T)4 * mu, ri, -ww), f);
+        T fw = (T)4 * k * rw;
+        a[0] = fma(fw, w[0], a[0]);
+        a[1] = fma(fw, w[1], a[1]);
+        a[2] = fma(fw, w[2], a[2]);
+    }
+    if (j2) {
+        T z = fma(r[0], P[0], fma(r[1], P[1], r[2] * P[2]));
+        T psi = j2k * ri3 * ri2;   // 1.5 J2 mu R^2 / r^5
+        T q = (T)5 * z * z * ri2;
+        f = fma(-psi, (T)1 - q, f);
+        T fp = (T)-2 * psi * z;
+        a[0] = fma(fp, P[0], a[0]);
+        a[1] = fma(fp, P[1], a[1]);
+        a[2] = fma(fp, P[2], a[2]);
+    }
+    a[0] = fma(f, r[0], a[0]);
+    a[1] = fma(f, r[1], a[1]);
+    a[2] = fma(f, r[2], a[2]);
+}
+
+// Planet state (position, velocity) of body m by Clenshaw, out of line: the
+// per-thread path used when a step does not span a whole batch leg.
+static __device__ __noinline__ void cheb_state64(const EphemDev &E, int m, int s, double tau,
+                                          double *out6)
+{
+    double p[3], v[3];
+    cheb_pos_vel(ephem_coef(E, m, s), E.n_coef, tau, 2.0 * E.inv_seg, p, v);
+    out6[0] = p[0]; out6[1] = p[1]; out6[2] = p[2];
+    out6[3] = v[0]; out6[4] = v[1]; out6[5] = v[2];
+}
+
+// FP32 Clenshaw of body m (mixed precision, planets only)
+__device__ __forceinline__ void cheb_state32(const EphemDev &E, int m, int s, float tau,
+                                             float *out6)
+{
+    const float *c = E.coef32 + ((size_t)m * E.n_seg + s) * 3 * E.n_coef;
+    const float dtau_dt = (float)(2.0 * E.inv_seg);
+    for (int d = 0; d < 3; d++) {
+        const float *cd = c + d * E.n_coef;
+        float b1 = 0.f, b2 = 0.f, u1 = 0.f, u2 = 0.f;
+        for (int k = E.n_coef - 1; k >= 1; k--) {
+            float ck = __ldg(cd + k);
+            float b0 = fmaf(2.f * tau, b1, ck - b2);
+            float u0 = fmaf(2.f * tau, u1, (float)k * ck - u2);
+            b2 = b1; b1 = b0; u2 = u1; u1 = u0;
+        }
+        out6[d] = fmaf(tau, b1, __ldg(cd) - b2);
+        out6[3 + d] = u1 * dtau_dt;
+    }
+}
+
+// Node rows: planet states at one Gauss-Radau node epoch of a batch leg,
+// shared by every body whose step spans that whole leg.
+//   row64[m*6 + 0..5]  barycentric position, velocity (FP64)
+//   row32[m*6 + 0..2]  position relative to the Sun, [3..5] velocity (FP32)
+// A null row64 means "evaluate the table here" (per-thread path).
+
+// Full-FP64 acceleration.
 __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, double t0,
-                                          double off, const double x[3], const double v[3],
-                                          double a[3])
+                                          double off, const double *__restrict__ row64,
+                                          const double x[3], const double v[3], double a[3])
 {
     Seg g;
     a[0] = a[1] = a[2] = 0.0;
-    if (!ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
-    const double dtau_dt = 2.0 * E.inv_seg;
+    if (!row64 && !ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
     for (int m = 0; m < E.n_bodies; m++) {
         if (!((F.active_mask >> m) & 1u)) continue;
-        const double mu = E.gm[m];
-        const double *c = ephem_coef(E, m, g.s);
-        const bool gr = (F.gr_mask >> m) & 1u;
-        double p[3], pv[3];
-        if (gr)
-            cheb_pos_vel(c, E.n_coef, g.tau, dtau_dt, p, pv);
-        else
-            cheb_pos(c, E.n_coef, g.tau, p);
-        double r0 = x[0] - p[0], r1 = x[1] - p[1], r2 = x[2] - p[2];
-        double rr = fma(r0, r0, fma(r1, r1, r2 * r2));
-        double ri = rsqrt(rr);
-        double ri2 = ri * ri;
-        double ri3 = ri2 * ri;
-        double f = -mu * ri3;
-        if (gr) {
-            double w0 = v[0] - pv[0], w1 = v[1] - pv[1], w2 = v[2] - pv[2];
-            double ww = fma(w0, w0, fma(w1, w1, w2 * w2));
-            double rw = fma(r0, w0, fma(r1, w1, r2 * w2));
-            double k = mu * ri3 * kInvC2;
-            double fr = k * fma(4.0 * mu, ri, -ww);
-            double fw = 4.0 * k * rw;
-            f += fr;
-            a[0] = fma(fw, w0, a[0]);
-            a[1] = fma(fw, w1, a[1]);
-            a[2] = fma(fw, w2, a[2]);
+        const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
+        double st[6];
+        if (row64) {
+#pragma unroll
+            for (int q = 0; q < 6; q++) st[q] = __ldg(row64 + 6 * m + q);
+        } else {
+            cheb_state64(E, m, g.s, g.tau, st);
         }
-        if ((F.j2_mask >> m) & 1u) {
-            const double *P = F.pole[m];
-            double z = fma(r0, P[0], fma(r1, P[1], r2 * P[2]));
-            double psi = F.j2k[m] * ri3 * ri2;   // 1.5 J2 mu R^2 / r^5
-            double q = 5.0 * z * z * ri2;
-            f = fma(-psi, 1.0 - q, f);
-            double fp = -2.0 * psi * z;
-            a[0] = fma(fp, P[0], a[0]);
-            a[1] = fma(fp, P[1], a[1]);
-            a[2] = fma(fp, P[2], a[2]);
-        }
-        a[0] = fma(f, r0, a[0]);
-        a[1] = fma(f, r1, a[1]);
-        a[2] = fma(f, r2, a[2]);
+        double r[3] = {x[0] - st[0], x[1] - st[1], x[2] - st[2]};
+        double w[3] = {v[0] - st[3], v[1] - st[4], v[2] - st[5]};
+        mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r, w, a);
     }
     return KETE_BODY_OK;
+}
+
+// Mixed precision: the Sun's monopole in FP64; the Sun's GR and
+// J2 and every planet in FP32 -- except planets flagged in `close` (within
+// kCloseAu at the start of the step), which stay in FP64.  `as` receives the
+// FP64 part alone: it is smooth in time, so the step-size control estimates
+// its error from it (FP32 rounding noise would otherwise dominate b6).
+constexpr double kCloseAu = 0.05;
+
+__device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F, double t0,
+                                           double off, const double *__restrict__ row64,
+                                           const float *__restrict__ row32, uint32_t close,
+                                           const double x[3], const double v[3], double a[3],
+                                           double as[3])
+{
+    Seg g;
+    as[0] = as[1] = as[2] = 0.0;
+    if (!row64 && !ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
+    double sun[6];
+    if (row64) {
+#pragma unroll
+        for (int q = 0; q < 6; q++) sun[q] = __ldg(row64 + q);
+    } else {
+        cheb_state64(E, 0, g.s, g.tau, sun);
+    }
+    const double d[3] = {x[0] - sun[0], x[1] - sun[1], x[2] - sun[2]};
+    const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
+    const float vf[3] = {(float)v[0], (float)v[1], (float)v[2]};
+    float af[3] = {0.f, 0.f, 0.f};
+    if (F.active_mask & 1u) {
+        // Sun monopole, FP64
+        double rr = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
+        double ri = rsqrt(rr);
+        double f = -E.gm[0] * ri * ri * ri;
+        as[0] = f * d[0];
+        as[1] = f * d[1];
+        as[2] = f * d[2];
+        // the Sun's GR and J2 corrections, FP32 (relative size 1e-8, 1e-13)
+        const bool gr = F.gr_mask & 1u, j2 = F.j2_mask & 1u;
+        if (gr || j2) {
+            float w[3] = {vf[0] - (float)sun[3], vf[1] - (float)sun[4], vf[2] - (float)sun[5]};
+            float P[3] = {(float)F.pole[0][0], (float)F.pole[0][1], (float)F.pole[0][2]};
+            mass_terms<float>((float)E.gm[0], (float)F.j2k[0], P, false, gr, j2, df, w, af);
+        }
+    }
+    const float tau32 = row64 ? 0.f : (float)g.tau;
+    for (int m = 1; m < E.n_bodies; m++) {
+        if (!((F.active_mask >> m) & 1u)) continue;
+        const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
+        if ((close >> m) & 1u) {
+            double st[6];
+            if (row64) {
+#pragma unroll
+                for (int q = 0; q < 6; q++) st[q] = __ldg(row64 + 6 * m + q);
+            } else {
+                cheb_state64(E, m, g.s, g.tau, st);
+            }
+            double r[3] = {x[0] - st[0], x[1] - st[1], x[2] - st[2]};
+            double w[3] = {v[0] - st[3], v[1] - st[4], v[2] - st[5]};
+            mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r, w, as);
+            continue;
+        }
+        float st[6];
+        if (row32) {
+#pragma unroll
+            for (int q = 0; q < 6; q++) st[q] = __ldg(row32 + 6 * m + q);
+        } else {
+            cheb_state32(E, m, g.s, tau32, st);
+            st[0] -= (float)sun[0]; st[1] -= (float)sun[1]; st[2] -= (float)sun[2];
+        }
+        float r[3] = {df[0] - st[0], df[1] - st[1], df[2] - st[2]};
+        float w[3] = {vf[0] - st[3], vf[1] - st[4], vf[2] - st[5]};
+        float P[3] = {(float)F.pole[m][0], (float)F.pole[m][1], (float)F.pole[m][2]};
+        mass_terms<float>((float)E.gm[m], (float)F.j2k[m], P, true, gr, j2, r, w, af);
+    }
+    a[0] = as[0] + (double)af[0];
+    a[1] = as[1] + (double)af[1];
+    a[2] = as[2] + (double)af[2];
+    return KETE_BODY_OK;
+}
+
+// planets within kCloseAu of x (bit m set), from FP64 positions
+__device__ __forceinline__ uint32_t close_planets(const EphemDev &E, const ForceDev &F, double t0,
+                                                  const double *__restrict__ row64,
+                                                  const double x[3])
+{
+    uint32_t close = 0;
+    Seg g;
+    if (!row64 && !ephem_seg(E, t0, 0.0, g)) return 0;
+    for (int m = 1; m < E.n_bodies; m++) {
+        if (!((F.active_mask >> m) & 1u)) continue;
+        double st[6];
+        if (row64) {
+            st[0] = __ldg(row64 + 6 * m); st[1] = __ldg(row64 + 6 * m + 1); st[2] = __ldg(row64 + 6 * m + 2);
+        } else {
+            cheb_state64(E, m, g.s, g.tau, st);
+        }
+        double r0 = x[0] - st[0], r1 = x[1] - st[1], r2 = x[2] - st[2];
+        // 2x margin: the set is held for the whole step
+        if (r0 * r0 + r1 * r1 + r2 * r2 < 4.0 * kCloseAu * kCloseAu) close |= 1u << m;
+    }
+    return close;
 }
 
 // ---------------------------------------------------------------------------

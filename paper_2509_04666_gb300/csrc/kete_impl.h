@@ -35,9 +35,20 @@ struct ForceDev {
 struct DevCounters {
     unsigned long long steps, rejected, force_evals, iterations;
     unsigned long long candidates, hits;
+    unsigned long long node_evals;   // force evaluations served by batch node rows
     int error_flags;         // bit 0: unsorted epochs, 1: exposure mismatch, 2: bad observer,
                              // 3: bad n_edges, 4: non-finite frame, 5: batch epoch outside table
     int pad;
+};
+
+// planet states at the 8 Gauss-Radau node epochs of each leg of a chain of
+// stops (leg k runs from t0[k] to t0[k] + h[k]); h[k] is NaN when the leg
+// cannot use the rows (a node outside the table)
+struct NodeTable {
+    const double *t0, *h;
+    const double *row64;   // [leg][8][n_bodies][6] FP64 barycentric pos, vel
+    const float *row32;    // [leg][8][n_bodies][6] FP32 heliocentric pos, vel
+    int n_legs, nb;
 };
 
 // per-body working state of a propagation chain: [8][n] = x,y,z,vx,vy,vz,t,dt
@@ -53,10 +64,13 @@ cudaError_t launch_ephem_eval(const EphemDev &E, const double *t, int64_t n, int
                               double *pos, double *vel, cudaStream_t st);
 cudaError_t launch_chain_init(ChainState cs, const double *states, const double *epochs,
                               const ForceDev &F, cudaStream_t st);
+cudaError_t launch_node_table(const EphemDev &E, const double *stops_dev, int n_stops,
+                              const double *epoch0, double *t0, double *h, double *row64,
+                              float *row32, cudaStream_t st);
 cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
                              const double *stops_dev, int n_stops, double *out,
                              int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
-                             cudaStream_t st);
+                             cudaStream_t st, const NodeTable *nt = nullptr, int leg0 = 0);
 cudaError_t launch_chain_finish(ChainState cs, double *states, double *epochs,
                                 int32_t *status, cudaStream_t st);
 // kete_noalloc.cu: propagation with the chain scratch in a fixed device array

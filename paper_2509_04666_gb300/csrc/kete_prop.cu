@@ -53,18 +53,51 @@ void upload_radau_tables(cudaStream_t st)
         }
         for (int m = 0; m < 7; m++) t.c[n][m] = (m < n) ? poly[m] : 0.0;
     }
+    // leading coefficient of the interpolant through the 8 nodes
+    for (int n = 0; n < 8; n++) {
+        double p = 1.0;
+        for (int k = 0; k < 8; k++)
+            if (k != n) p *= (kRadauH[n] - kRadauH[k]);
+        t.w7[n] = 1.0 / p;
+    }
     cudaMemcpyToSymbolAsync(g_rt, &t, sizeof(t), 0, cudaMemcpyHostToDevice, st);
 }
 
 struct Cnt {
-    unsigned long long steps, rejected, evals, iters;
+    unsigned long long steps, rejected, evals, iters, node_evals;
 };
 
-// One Gauss-Radau attempt of size h from (t, x0, v0) with a0 = a(t, x0, v0).
+// Rows of the node table for leg kg, or null when the step (t, h) does not span
+// that whole leg.
+struct LegRows {
+    const double *r64;
+    const float *r32;
+    int stride64;   // doubles per node
+};
+
+// Force evaluation dispatch by precision mode.
+template <int MODE>
+__device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, double t0, double off,
+                                     const double *row64, const float *row32, uint32_t close,
+                                     const double x[3], const double v[3], double a[3],
+                                     double as[3])
+{
+    if (MODE == KETE_MIXED)
+        return accel_mixed(E, F, t0, off, row64, row32, close, x, v, a, as);
+    int st = accel_fp64(E, F, t0, off, row64, x, v, a);
+    as[0] = a[0]; as[1] = a[1]; as[2] = a[2];
+    return st;
+}
+
+// One Gauss-Radau attempt of size h from (t, x0, v0) with a0 = a(t, x0, v0)
+// (as0: its FP64 part).  rows != null: the step spans the whole leg and the
+// planets come from the node rows (node n at rows.r64 + n * stride).
+template <int MODE>
 __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &F, double t,
                                              const double x0[3], const double v0[3],
-                                             const double a0[3], double h, double x1[3],
-                                             double v1[3], double &err, Cnt &cnt)
+                                             const double a0[3], const double as0[3],
+                                             uint32_t close, double h, LegRows rows,
+                                             double x1[3], double v1[3], double &err, Cnt &cnt)
 {
     double b[7][3], g[7][3];
 #pragma unroll
@@ -72,9 +105,14 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
 #pragma unroll
         for (int i = 0; i < 3; i++) b[m][i] = g[m][i] = 0.0;
     double amax = 0.0, pc_prev = 0.0;
+    double gs7[3] = {0.0, 0.0, 0.0};   // b6 of the FP64 part (mixed precision)
     for (int it = 1; it <= F.max_iter; it++) {
         double b6o[3] = {b[6][0], b[6][1], b[6][2]};
         double F7[3];
+        if (MODE == KETE_MIXED) {
+#pragma unroll
+            for (int i = 0; i < 3; i++) gs7[i] = g_rt.w7[0] * as0[i];
+        }
 #pragma unroll
         for (int n = 1; n <= 7; n++) {
             const double s = g_rt.h[n];
@@ -103,9 +141,12 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
                 pv = fma(pv, s, a0[i]);
                 vn[i] = fma(sh, pv, v0[i]);
             }
-            double Fn[3];
-            int st = accel_fp64(E, F, t, sh, xn, vn, Fn);
+            double Fn[3], Fs[3];
+            const double *r64 = rows.r64 ? rows.r64 + n * rows.stride64 : nullptr;
+            const float *r32 = rows.r32 ? rows.r32 + n * rows.stride64 : nullptr;
+            int st = accel<MODE>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs);
             cnt.evals++;
+            if (r64) cnt.node_evals++;
             if (st != KETE_BODY_OK) return st;
 #pragma unroll
             for (int i = 0; i < 3; i++) {
@@ -117,6 +158,7 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
 #pragma unroll
                 for (int m = 0; m < n; m++) b[m][i] = fma(g_rt.c[n][m], dg, b[m][i]);
                 if (n == 7) F7[i] = Fn[i];
+                if (MODE == KETE_MIXED) gs7[i] = fma(g_rt.w7[n], Fs[i], gs7[i]);
             }
         }
         cnt.iters++;
@@ -133,7 +175,11 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
         if (it >= 3 && pc >= pc_prev) break;
         pc_prev = pc;
     }
-    double bmax = fmax(fabs(b[6][0]), fmax(fabs(b[6][1]), fabs(b[6][2])));
+    // step-size error estimate: max|b6| / max|a|; in mixed precision b6 of the
+    // smooth FP64 part (FP32 rounding is not smooth and b6 would amplify it)
+    double bmax = (MODE == KETE_MIXED)
+                      ? fmax(fabs(gs7[0]), fmax(fabs(gs7[1]), fabs(gs7[2])))
+                      : fmax(fabs(b[6][0]), fmax(fabs(b[6][1]), fabs(b[6][2])));
     err = bmax / amax;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
@@ -153,17 +199,36 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
 }
 
 // Integrate (x, v, t) to `target` exactly; dt is the carried step proposal.
-__device__ int integrate_to(const EphemDev &E, const ForceDev &F, double x[3], double v[3],
-                            double &t, double &dt, double target, Cnt &cnt)
+// nt (may be null) gives the node rows of leg kg of the chain.
+template <int MODE>
+__device__ int integrate_to(const EphemDev &E, const ForceDev &F, const NodeTable *nt, int kg,
+                            double x[3], double v[3], double &t, double &dt, double target,
+                            Cnt &cnt)
 {
     if (t == target) return KETE_BODY_OK;
     const double dir = (target >= t) ? 1.0 : -1.0;
     if (dt == 0.0 || ((dt > 0.0) != (dir > 0.0))) dt = dir * fabs(dt == 0.0 ? F.dt_init : dt);
     long long attempts = 0;
+    double leg_t0 = 0.0, leg_h = __longlong_as_double(0x7ff8000000000000ll);
+    const double *leg64 = nullptr;
+    const float *leg32 = nullptr;
+    const int stride = nt ? nt->nb * 6 : 0;
+    if (nt) {
+        leg_t0 = __ldg(nt->t0 + kg);
+        leg_h = __ldg(nt->h + kg);
+        leg64 = nt->row64 + (size_t)kg * 8 * stride;
+        leg32 = nt->row32 + (size_t)kg * 8 * stride;
+    }
     while (t != target) {
-        double a0[3];
-        int st = accel_fp64(E, F, t, 0.0, x, v, a0);
+        // rows of node 0 serve a0 whenever the step starts at the leg start
+        const bool at_start = nt && (t == leg_t0) && isfinite(leg_h);
+        double a0[3], as0[3];
+        uint32_t close = 0;
+        if (MODE == KETE_MIXED) close = close_planets(E, F, t, at_start ? leg64 : nullptr, x);
+        int st = accel<MODE>(E, F, t, 0.0, at_start ? leg64 : nullptr,
+                             at_start ? leg32 : nullptr, close, x, v, a0, as0);
         cnt.evals++;
+        if (at_start) cnt.node_evals++;
         if (st != KETE_BODY_OK) return st;
         for (;;) {
             if (++attempts > F.max_steps) return KETE_BODY_STEP_CAP;
@@ -173,8 +238,13 @@ __device__ int integrate_to(const EphemDev &E, const ForceDev &F, double x[3], d
             const double t_new = clamped ? target : t + dt;
             const double h = t_new - t;
             if (h == 0.0) return KETE_BODY_STEP_CAP;   // step below the epoch resolution
+            LegRows rows = {nullptr, nullptr, stride};
+            if (at_start && h == leg_h) {
+                rows.r64 = leg64;
+                rows.r32 = leg32;
+            }
             double x1[3], v1[3], err;
-            st = radau_attempt(E, F, t, x, v, a0, h, x1, v1, err, cnt);
+            st = radau_attempt<MODE>(E, F, t, x, v, a0, as0, close, h, rows, x1, v1, err, cnt);
             if (st != KETE_BODY_OK) return st;
             double dt_new;
             if (isfinite(err) && err >= 2.2250738585072014e-308)
@@ -203,32 +273,41 @@ __device__ int integrate_to(const EphemDev &E, const ForceDev &F, double x[3], d
 
 __device__ __forceinline__ void flush_counters(const Cnt &c, DevCounters *ctr)
 {
-    unsigned long long s = c.steps, r = c.rejected, e = c.evals, it = c.iters;
+    unsigned long long s = c.steps, r = c.rejected, e = c.evals, it = c.iters, ne = c.node_evals;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, o);
         r += __shfl_xor_sync(0xffffffffu, r, o);
         e += __shfl_xor_sync(0xffffffffu, e, o);
         it += __shfl_xor_sync(0xffffffffu, it, o);
+        ne += __shfl_xor_sync(0xffffffffu, ne, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&ctr->steps, s);
         atomicAdd(&ctr->rejected, r);
         atomicAdd(&ctr->force_evals, e);
         atomicAdd(&ctr->iterations, it);
+        atomicAdd(&ctr->node_evals, ne);
     }
 }
 
 // One thread per body: advance its chain through stops[0..n_stops) and write
 // the state at each stop to out[k][c][i] (stride out_stride between rows).
-__global__ void __launch_bounds__(128) k_propagate(EphemDev E, ForceDev F, ChainState cs,
+// Stop k of this launch is leg leg0 + k of the node table (if any).
+#ifndef KETE_PROP_MIN_BLOCKS
+#define KETE_PROP_MIN_BLOCKS 1   // resident blocks per SM asked of the register allocator
+#endif
+
+template <int MODE>
+__global__ void __launch_bounds__(128, KETE_PROP_MIN_BLOCKS) k_propagate(EphemDev E, ForceDev F, ChainState cs,
                                                    const double *__restrict__ stops, int n_stops,
                                                    double *__restrict__ out, int64_t out_stride,
-                                                   int keep_on_fail, DevCounters *ctr)
+                                                   int keep_on_fail, DevCounters *ctr,
+                                                   NodeTable nt, int use_nt, int leg0)
 {
     const int64_t n = cs.n;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    Cnt cnt = {0, 0, 0, 0};
+    Cnt cnt = {0, 0, 0, 0, 0};
     if (i < n) {
         double x[3], v[3];
 #pragma unroll
@@ -239,7 +318,9 @@ __global__ void __launch_bounds__(128) k_propagate(EphemDev E, ForceDev F, Chain
         double t = cs.w[6 * n + i], dt = cs.w[7 * n + i];
         int status = cs.status[i];
         for (int k = 0; k < n_stops; k++) {
-            if (status == KETE_BODY_OK) status = integrate_to(E, F, x, v, t, dt, stops[k], cnt);
+            if (status == KETE_BODY_OK)
+                status = integrate_to<MODE>(E, F, use_nt ? &nt : nullptr, leg0 + k, x, v, t, dt,
+                                            stops[k], cnt);
             double *o = out + (int64_t)k * 6 * out_stride;
             if (status == KETE_BODY_OK) {
 #pragma unroll
@@ -262,6 +343,46 @@ __global__ void __launch_bounds__(128) k_propagate(EphemDev E, ForceDev F, Chain
         cs.status[i] = status;
     }
     flush_counters(cnt, ctr);
+}
+
+// Node table: thread per (leg k, node n, body m).  Leg 0 starts at the first
+// body's epoch (*epoch0, device), leg k > 0 at stops[k-1]; h is their exact
+// difference, as the integrator forms it.
+__global__ void k_node_table(EphemDev E, const double *__restrict__ stops, int n_stops,
+                             const double *__restrict__ epoch0, double *__restrict__ t0,
+                             double *__restrict__ hh,
+                             double *__restrict__ row64, float *__restrict__ row32)
+{
+    const int nb = E.n_bodies;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_stops * 8 * nb) return;
+    const int m = (int)(idx % nb);
+    const int n = (int)((idx / nb) % 8);
+    const int k = (int)(idx / (8 * nb));
+    const double ts = (k == 0) ? epoch0[0] : stops[k - 1];
+    const double h = stops[k] - ts;
+    const double off = g_rt.h[n] * h;
+    Seg g;
+    double st[6], sun[6];
+    const bool ok = ephem_seg(E, ts, off, g);
+    double *o64 = row64 + (((int64_t)k * 8 + n) * nb + m) * 6;
+    float *o32 = row32 + (((int64_t)k * 8 + n) * nb + m) * 6;
+    if (ok) {
+        cheb_pos_vel(ephem_coef(E, m, g.s), E.n_coef, g.tau, 2.0 * E.inv_seg, st, st + 3);
+        cheb_pos_vel(ephem_coef(E, 0, g.s), E.n_coef, g.tau, 2.0 * E.inv_seg, sun, sun + 3);
+        for (int q = 0; q < 6; q++) o64[q] = st[q];
+        for (int q = 0; q < 3; q++) {
+            o32[q] = (float)(st[q] - sun[q]);
+            o32[3 + q] = (float)st[3 + q];
+        }
+    }
+    if (m == 0 && n == 0) {
+        t0[k] = ts;
+        hh[k] = h;
+    }
+    // any node of the leg outside the table: the leg uses the per-thread path
+    __syncwarp(__activemask());
+    if (!ok) hh[k] = __longlong_as_double(0x7ff8000000000000ll);
 }
 
 __global__ void k_chain_init(ChainState cs, const double *__restrict__ states,
@@ -330,14 +451,31 @@ cudaError_t launch_chain_init(ChainState cs, const double *states, const double 
     return cudaGetLastError();
 }
 
+cudaError_t launch_node_table(const EphemDev &E, const double *stops_dev, int n_stops,
+                              const double *epoch0, double *t0, double *h, double *row64,
+                              float *row32, cudaStream_t st)
+{
+    int64_t tot = (int64_t)n_stops * 8 * E.n_bodies;
+    if (tot > 0) k_node_table<<<grid_for(tot, 128), 128, 0, st>>>(E, stops_dev, n_stops, epoch0, t0, h, row64, row32);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
                              const double *stops_dev, int n_stops, double *out,
                              int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
-                             cudaStream_t st)
+                             cudaStream_t st, const NodeTable *nt, int leg0)
 {
-    if (cs.n > 0 && n_stops > 0)
-        k_propagate<<<grid_for(cs.n, 128), 128, 0, st>>>(E, F, cs, stops_dev, n_stops, out,
-                                                         out_stride, keep_on_fail ? 1 : 0, ctr);
+    if (cs.n > 0 && n_stops > 0) {
+        NodeTable t{};
+        if (nt) t = *nt;
+        unsigned grid = grid_for(cs.n, 128);
+        if (F.precision == KETE_MIXED)
+            k_propagate<KETE_MIXED><<<grid, 128, 0, st>>>(E, F, cs, stops_dev, n_stops, out, out_stride,
+                                                          keep_on_fail ? 1 : 0, ctr, t, nt ? 1 : 0, leg0);
+        else
+            k_propagate<KETE_FP64><<<grid, 128, 0, st>>>(E, F, cs, stops_dev, n_stops, out, out_stride,
+                                                         keep_on_fail ? 1 : 0, ctr, t, nt ? 1 : 0, leg0);
+    }
     return cudaGetLastError();
 }
 

@@ -53,7 +53,7 @@ class Stats(C.Structure):
                 ("iterations", C.c_int64), ("n_batches", C.c_int64), ("n_exposures", C.c_int64),
                 ("n_candidates", C.c_int64), ("n_hits", C.c_int64), ("prop_launches", C.c_int64),
                 ("launches", C.c_int64), ("prep_ms", C.c_double), ("cand_ms", C.c_double),
-                ("exact_ms", C.c_double), ("order_ms", C.c_double)]
+                ("exact_ms", C.c_double), ("order_ms", C.c_double), ("node_evals", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

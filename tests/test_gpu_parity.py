@@ -258,3 +258,47 @@ def test_close_encounter_matches_oracle(K, mb1k):
         rc, ref, *_ = orc.propagate(orc.force_model(), st0[:, j], W.T0, W.T0 + 25.0)
         assert rc == 0
         assert np.abs(s.cpu().numpy()[:3, j] - ref[:3]).max() < 1e-9
+
+
+def test_mixed_precision_propagation_within_tolerance(K, mb1k):
+    """FP32 planetary terms (FP64 Sun monopole, accumulation, step control on
+    the FP64 part): positions stay within 1e-9 AU of the FP64 oracle."""
+    from paper_2509_04666_gb300 import kete
+    K.load_ephem(mb1k.ephem.to_bytes())
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    stops = W.T0 + np.arange(1.5, 60.0, 3.0)
+    st = mb1k.states
+    out, status = K.propagate_stops(_dev(st), _dev(mb1k.epochs), stops,
+                                    fm=kete.force_model(precision=kete.MIXED))
+    assert (status.cpu().numpy() == 0).all()
+    out = out.cpu().numpy()
+    worst = 0.0
+    for j in range(0, mb1k.n_bodies, 9):
+        rc, ref, _ = orc.propagate_stops(orc.force_model(), st[:, j], W.T0, stops)
+        worst = max(worst, np.abs(out[:, :3, j] - ref[:, :3]).max())
+    assert worst < 1e-9, worst
+
+
+def test_mixed_precision_fov_check(K, mb1k_dense):
+    from paper_2509_04666_gb300 import kete
+    w = mb1k_dense
+    got, status = _hits_gpu(K, w, fm=kete.force_model(precision=kete.MIXED))
+    orc = O.Oracle(w.ephem.to_bytes())
+    ref, _, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, w.frames, w.observers)
+    worst = _compare_hits(got, ref, edge=2 * MAS, sky_tol=MAS)
+    assert (status == 0).all()
+
+
+def test_mixed_precision_close_encounter(K, mb1k):
+    """Planets within 0.05 AU stay in FP64: a 0.003 AU Earth pass stays at 1e-9 AU."""
+    from test_oracle_integrator import _earth_encounter_body
+    from paper_2509_04666_gb300 import kete
+    K.load_ephem(mb1k.ephem.to_bytes())
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    st0 = np.stack([_earth_encounter_body(orc, W.T0 + 12.0, miss=m) for m in (0.003, 0.01, 0.03)], 1)
+    s = _dev(st0.copy()); e = _dev(np.full(3, W.T0))
+    status = K.propagate(s, e, W.T0 + 25.0, fm=kete.force_model(precision=kete.MIXED))
+    assert (status.cpu().numpy() == 0).all()
+    for j in range(3):
+        rc, ref, *_ = orc.propagate(orc.force_model(), st0[:, j], W.T0, W.T0 + 25.0)
+        assert np.abs(s.cpu().numpy()[:3, j] - ref[:3]).max() < 1e-9
