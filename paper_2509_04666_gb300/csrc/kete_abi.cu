@@ -26,7 +26,7 @@ enum Slot {
     S_BO, S_BROBS, S_BTSPAN, S_BRMAX, S_BSUN, S_NBATCH, S_BANDS, S_CELLKEY, S_CELLCNT,
     S_CELLSTART, S_CELLCUR, S_CELLEXP, S_CAND, S_EXPCNT, S_EXPOFF, S_EXPCUR, S_CANDBODY,
     S_HITTMP, S_FRAMECNT, S_FRAMEOFF, S_FRAMECUR, S_HITGROUP, S_MAXRAD, S_NT_T0, S_NT_H,
-    S_NT_R64, S_NT_R32, S_NSLOTS
+    S_NT_R64, S_NT_R32, S_XSUN, S_XOBSREL, S_NSLOTS
 };
 
 struct Scratch {
@@ -602,10 +602,13 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
     GET(S_XRAD, ne, X.rad);
     GET(S_XCS, ne, X.cs);
     GET(S_XBATCH, ne, X.batch);
+    GET(S_XSUN, 6 * ne, X.sun);
+    GET(S_XOBSREL, ne, X.obs_rel);
     unsigned int *d_maxrad;
     GET(S_MAXRAD, 1, d_maxrad);
     CUDA_TRY(cudaMemsetAsync(d_maxrad, 0, sizeof(unsigned int), st));
-    CUDA_TRY(fov_exposure_prep(frames, nf, observers, fcen, exp_first, ne, X, d_maxrad, st));
+    CUDA_TRY(fov_exposure_prep(ctx->E, frames, nf, observers, fcen, exp_first, ne, X, d_maxrad,
+                               ctx->d_ctr, st));
     // ---- batches (Sec. 2) ---------------------------------------------------
     double span = std::min(opt.batch_span, 2.0 * opt.twobody_max);
     int32_t *next, *d_nb;
@@ -782,7 +785,7 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
     CUDA_TRY(cudaStreamSynchronize(st));
     if (ctx->h_ctr->error_flags & 32) {
         ctx->stats.launches = launches;
-        return fail(ctx, KETE_ERR_EPHEM_SPAN, "a batch midpoint lies outside the ephemeris table");
+        return fail(ctx, KETE_ERR_EPHEM_SPAN, "a batch midpoint or frame epoch lies outside the ephemeris table");
     }
     if ((int64_t)hits_total > capacity) {
         r = stats_end(ctx);

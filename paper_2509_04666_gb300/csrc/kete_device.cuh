@@ -316,11 +316,28 @@ __device__ __forceinline__ uint32_t close_planets(const EphemDev &E, const Force
 // ---------------------------------------------------------------------------
 // universal-variable two-body propagation
 // ---------------------------------------------------------------------------
-// Stumpff C(z), S(z): nested (Horner) form of the power series for |z| < 1,
-// closed trigonometric / hyperbolic forms otherwise.
+// Stumpff C(z), S(z): nested (Horner) form of the power series for |z| < 1
+// (six terms when |z| < 1e-3, eleven otherwise), closed trigonometric /
+// hyperbolic forms beyond.
 __device__ __forceinline__ void stumpff(double z, double &C, double &S)
 {
-    if (fabs(z) < 1.0) {
+    if (fabs(z) < 1e-3) {
+        // six terms of each series: the first omitted term is below 2e-20
+        double c = fma(-z * (1.0 / (13.0 * 14.0)), 1.0, 1.0);
+        c = fma(-z * (1.0 / (11.0 * 12.0)), c, 1.0);
+        c = fma(-z * (1.0 / (9.0 * 10.0)), c, 1.0);
+        c = fma(-z * (1.0 / (7.0 * 8.0)), c, 1.0);
+        c = fma(-z * (1.0 / (5.0 * 6.0)), c, 1.0);
+        c = fma(-z * (1.0 / (3.0 * 4.0)), c, 1.0);
+        C = 0.5 * c;
+        double s = fma(-z * (1.0 / (14.0 * 15.0)), 1.0, 1.0);
+        s = fma(-z * (1.0 / (12.0 * 13.0)), s, 1.0);
+        s = fma(-z * (1.0 / (10.0 * 11.0)), s, 1.0);
+        s = fma(-z * (1.0 / (8.0 * 9.0)), s, 1.0);
+        s = fma(-z * (1.0 / (6.0 * 7.0)), s, 1.0);
+        s = fma(-z * (1.0 / (4.0 * 5.0)), s, 1.0);
+        S = s * (1.0 / 6.0);
+    } else if (fabs(z) < 1.0) {
         // C = 1/2 (1 - z/(3.4) (1 - z/(5.6) (1 - ...)))
         double c = 1.0, s = 1.0;
         c = fma(-z * (1.0 / (23.0 * 24.0)), c, 1.0);

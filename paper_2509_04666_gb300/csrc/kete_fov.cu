@@ -133,16 +133,28 @@ __global__ void k_exposure_first(const int32_t *__restrict__ is_start,
     if (i == nf - 1) exp_first[ex[i] + is_start[i]] = (int32_t)nf;
 }
 
-__global__ void k_exposure_prep(const kete_frame *__restrict__ fr, int64_t nf,
+__global__ void k_exposure_prep(EphemDev E, const kete_frame *__restrict__ fr, int64_t nf,
                                 const double *__restrict__ observers,
                                 const double *__restrict__ fcen, const int32_t *__restrict__ exp_first,
-                                int64_t ne, ExpArrays X, unsigned int *max_rad_bits)
+                                int64_t ne, ExpArrays X, unsigned int *max_rad_bits,
+                                DevCounters *ctr)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     int32_t f0 = exp_first[e], f1 = exp_first[e + 1];
     const kete_frame &f = fr[f0];
     X.epoch[e] = f.epoch;
+    // the Sun at the exposure epoch: every candidate of the exposure re-adds it
+    Seg g;
+    double sp[3] = {0, 0, 0}, sv[3] = {0, 0, 0};
+    if (ephem_seg(E, f.epoch, 0.0, g))
+        cheb_pos_vel(ephem_coef(E, 0, g.s), E.n_coef, g.tau, 2.0 * E.inv_seg, sp, sv);
+    else
+        set_flag(ctr, 5);
+    for (int c = 0; c < 3; c++) {
+        X.sun[6 * e + c] = sp[c];
+        X.sun[6 * e + 3 + c] = sv[c];
+    }
     int64_t oi = f.observer_idx;
     for (int c = 0; c < 3; c++) X.obs[3 * e + c] = observers[3 * oi + c];
     double s[3] = {0, 0, 0};
@@ -241,6 +253,7 @@ __global__ void k_batch_info(EphemDev E, ExpArrays X, BatchArrays B, int32_t n_b
     double robs = 0, tsp = 0, rmax = 0;
     for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         double d0 = X.obs[3 * e] - O[0], d1 = X.obs[3 * e + 1] - O[1], d2 = X.obs[3 * e + 2] - O[2];
+        X.obs_rel[e] = make_float4((float)d0, (float)d1, (float)d2, 0.f);
         robs = fmax(robs, sqrt(d0 * d0 + d1 * d1 + d2 * d2));
         tsp = fmax(tsp, fabs(X.epoch[e] - tr));
         rmax = fmax(rmax, X.rad[e]);
@@ -332,24 +345,28 @@ struct CandCtx {
     double mu_sun;
 };
 
-__device__ __forceinline__ void test_exposure(const CandCtx &C, int32_t e, const double p[3],
-                                              double s, int32_t body)
+// Cap test of one exposure for a body at pb = p - O (FP32, relative to the
+// batch's mean observer O): the body's apparent direction from the exposure's
+// observer can move by at most asin(s/Q) during the batch, so the exposure is
+// a candidate iff angle(pb - (o - O), centre) <= r + asin(s/Q) (+ padding for
+// the FP32 rounding of the offsets, ~1e-7 of a few AU).
+__device__ __forceinline__ void test_exposure(const CandCtx &C, int32_t e, const float pb[3],
+                                              float s, int32_t body)
 {
-    const double *o = C.X.obs + 3 * e;
-    double q0 = p[0] - o[0], q1 = p[1] - o[1], q2 = p[2] - o[2];
-    float Q = (float)sqrt(q0 * q0 + q1 * q1 + q2 * q2);
-    const double *c = C.X.cen + 3 * e;
-    float2 cs = C.X.cs[e];
+    const float4 o = C.X.obs_rel[e];
+    const float q0 = pb[0] - o.x, q1 = pb[1] - o.y, q2 = pb[2] - o.z;
+    const float Q = sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
+    const float2 cs = C.X.cs[e];
     bool pass;
-    float sig = (float)s / Q;
+    const float sig = s / Q;
     if (cs.x < -1.5f || sig >= 0.999f) {
         pass = true;
     } else {
-        float cosang = (float)(q0 * c[0] + q1 * c[1] + q2 * c[2]) / Q;
-        // cos(r + delta) with sin(delta) = s/Q, padded by kPadF
-        float cd = sqrtf(1.0f - sig * sig);
-        float lim = cs.x * cd - cs.y * sig;       // cos(r + delta)
-        pass = cosang >= lim - kPadF * (cs.y * cd + cs.x * sig) - 1e-6f - kPadF;
+        const double *c = C.X.cen + 3 * e;
+        const float cosang = (q0 * (float)c[0] + q1 * (float)c[1] + q2 * (float)c[2]) / Q;
+        const float cd = sqrtf(1.0f - sig * sig);
+        const float lim = cs.x * cd - cs.y * sig;                 // cos(r + delta)
+        pass = cosang >= lim - kPadF * (cs.y * cd + cs.x * sig) - 2e-6f - kPadF;
     }
     if (pass) {
         unsigned long long slot = agg_append(&C.ctr->candidates);
@@ -366,52 +383,54 @@ __global__ void __launch_bounds__(256) k_candidates(CandCtx C)
     const int32_t i = (int32_t)(idx - (int64_t)kl * C.n);
     const int32_t k = C.k0 + kl;
     const double *st = C.stop_states + (int64_t)kl * 6 * C.n;
-    double p[3] = {st[i], st[C.n + i], st[2 * C.n + i]};
+    const double p[3] = {st[i], st[C.n + i], st[2 * C.n + i]};
     if (!isfinite(p[0])) return;
-    double v[3] = {st[3 * C.n + i], st[4 * C.n + i], st[5 * C.n + i]};
+    const double v[3] = {st[3 * C.n + i], st[4 * C.n + i], st[5 * C.n + i]};
     const double *O = C.B.O + 3 * k;
     const double *sun = C.B.sun + 6 * k;
-    const double robs = C.B.robs[k];
-    double d[3] = {p[0] - O[0], p[1] - O[1], p[2] - O[2]};
-    double D = sqrt(dot3(d, d));
-    double h[3] = {p[0] - sun[0], p[1] - sun[1], p[2] - sun[2]};
-    double vh[3] = {v[0] - sun[3], v[1] - sun[4], v[2] - sun[5]};
-    double rh = sqrt(dot3(h, h));
-    double vn = sqrt(dot3(vh, vh));
+    const float robs = (float)C.B.robs[k];
+    // FP32 from here on: a conservative prefilter, padded for its rounding
+    const float d[3] = {(float)(p[0] - O[0]), (float)(p[1] - O[1]), (float)(p[2] - O[2])};
+    const float D = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float h[3] = {(float)(p[0] - sun[0]), (float)(p[1] - sun[1]), (float)(p[2] - sun[2])};
+    const float vh[3] = {(float)(v[0] - sun[3]), (float)(v[1] - sun[4]), (float)(v[2] - sun[5])};
+    const float rh = sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    const float vn = sqrtf(vh[0] * vh[0] + vh[1] * vh[1] + vh[2] * vh[2]);
     // time offsets from t_ref: frame epochs within tspan, light time below tau_max
-    double T = C.B.tspan[k] + (D + robs + 1.0) * kInvC;
-    // heliocentric displacement bound valid while the body stays beyond rh/2
-    double disp = vn * T + 2.0 * C.mu_sun * T * T / (rh * rh);
-    double s = disp + kSunSpeedMax * T + 1e-9;
-    bool all = (disp > 0.5 * rh) || (s + robs >= 0.99 * D);
-    double rho = all ? kPi : asin((s + robs) / D);
-    double R = rho + C.B.rmax[k] + 4.0 * (double)kPadF;
+    const float T = (float)C.B.tspan[k] + (D + robs + 1.0f) * (float)kInvC;
+    // heliocentric displacement bound, valid while the body stays beyond rh/2
+    const float disp = vn * T + 2.0f * (float)C.mu_sun * T * T / (rh * rh);
+    const float s = (disp + (float)kSunSpeedMax * T) * 1.0001f + 1e-6f;
+    const bool all = (disp > 0.5f * rh) || (s + robs >= 0.99f * D) || (D < 0.05f);
+    const float rho = all ? (float)kPi : asinf((s + robs) / D);
+    const float R = rho + (float)C.B.rmax[k] + 4.0f * kPadF;
     const int32_t e0 = C.B.first[k], e1 = C.B.first[k + 1];
-    if (all || R >= 1.2) {
-        for (int32_t e = e0; e < e1; e++) test_exposure(C, e, p, all ? 1e30 : s, i);
+    const float pb[3] = {d[0], d[1], d[2]};
+    if (all || R >= 1.2f) {
+        for (int32_t e = e0; e < e1; e++) test_exposure(C, e, pb, all ? 1e30f : s, i);
         return;
     }
     // enumerate the cells within R of the body's direction from the mean observer
-    const double lat = asin(fmin(1.0, fmax(-1.0, d[2] / D)));
-    double lon = atan2(d[1], d[0]);
-    if (lon < 0.0) lon += kTwoPi;
+    const float lat = asinf(fminf(1.0f, fmaxf(-1.0f, d[2] / D)));
+    float lon = atan2f(d[1], d[0]);
+    if (lon < 0.0f) lon += (float)kTwoPi;
     const CellGrid &G = C.G;
-    int jlo = (int)floor((lat - R + 0.5 * kPi) / G.hb);
-    int jhi = (int)floor((lat + R + 0.5 * kPi) / G.hb);
+    const float hb = (float)G.hb;
+    int jlo = (int)floorf((lat - R + 0.5f * (float)kPi) / hb);
+    int jhi = (int)floorf((lat + R + 0.5f * (float)kPi) / hb);
     jlo = jlo < 0 ? 0 : jlo;
     jhi = jhi >= G.n_bands ? G.n_bands - 1 : jhi;
-    double dlon;
-    if (fabs(lat) + R >= 0.5 * kPi - 1e-9) dlon = kPi;
-    else dlon = asin(fmin(1.0, sin(R) / cos(lat))) + 4.0 * (double)kPadF;
+    float dlon;
+    if (fabsf(lat) + R >= 0.5f * (float)kPi - 1e-4f) dlon = (float)kPi;
+    else dlon = asinf(fminf(1.0f, sinf(R) / cosf(lat))) + 4.0f * kPadF;
     const int64_t base = (int64_t)kl * G.n_cells;
     for (int j = jlo; j <= jhi; j++) {
         const int nj = G.band_n[j];
-        const double w = kTwoPi / nj;
-        int64_t lo_key, hi_key;   // inclusive cell ranges (up to two)
-        int ilo = (int)floor((lon - dlon) / w), ihi = (int)floor((lon + dlon) / w);
+        const float w = (float)kTwoPi / nj;
+        int ilo = (int)floorf((lon - dlon) / w), ihi = (int)floorf((lon + dlon) / w);
         int nr = 0;
         int64_t rl[2], rh2[2];
-        if (dlon >= kPi || ihi - ilo + 1 >= nj) {
+        if (dlon >= (float)kPi || ihi - ilo + 1 >= nj) {
             rl[0] = 0; rh2[0] = nj - 1; nr = 1;
         } else if (ilo < 0) {
             rl[0] = 0; rh2[0] = ihi; rl[1] = ilo + nj; rh2[1] = nj - 1; nr = 2;
@@ -421,10 +440,10 @@ __global__ void __launch_bounds__(256) k_candidates(CandCtx C)
             rl[0] = ilo; rh2[0] = ihi; nr = 1;
         }
         for (int r = 0; r < nr; r++) {
-            lo_key = base + G.band_off[j] + rl[r];
-            hi_key = base + G.band_off[j] + rh2[r];
-            int64_t a = C.cell_start[lo_key], b = C.cell_start[hi_key + 1];
-            for (int64_t q = a; q < b; q++) test_exposure(C, C.cell_exp[q], p, s, i);
+            const int64_t lo_key = base + G.band_off[j] + rl[r];
+            const int64_t hi_key = base + G.band_off[j] + rh2[r];
+            const int64_t a = C.cell_start[lo_key], b = C.cell_start[hi_key + 1];
+            for (int64_t q = a; q < b; q++) test_exposure(C, C.cell_exp[q], pb, s, i);
         }
     }
 }
@@ -464,20 +483,19 @@ struct ExactCtx {
     double cos_eps, sin_eps;
 };
 
-// heliocentric position at t_ref + dt (Sun re-added at that epoch)
-__device__ __forceinline__ bool twobody_pos(const EphemDev &E, double mu, double sqmu,
-                                            const double hr[3], const double hv[3], double t_ref,
-                                            double dt, double &chi, double pos[3])
+// Position at t_ref + dt_obs - tau: heliocentric universal-variable two-body
+// from the batch state, plus the Sun at t_obs - tau taken from the Sun's state
+// at the exposure epoch, S - V tau (the neglected term, a_sun tau^2 / 2 with
+// |a_sun| ~ 1e-8 AU/day^2, stays below 2e-11 AU for tau < 0.06 day).
+__device__ __forceinline__ bool twobody_pos(double mu, double sqmu, const double hr[3],
+                                            const double hv[3], const double *sun_obs,
+                                            double dt_obs, double tau, double &chi, double pos[3])
 {
     double r[3], v[3];
-    bool ok = kepler_uv(mu, sqmu, hr, hv, dt, chi, r, v);
-    Seg g;
-    double sp[3] = {0, 0, 0};
-    if (ephem_seg(E, t_ref, dt, g)) cheb_pos(ephem_coef(E, 0, g.s), E.n_coef, g.tau, sp);
-    else ok = false;
-    pos[0] = sp[0] + r[0];
-    pos[1] = sp[1] + r[1];
-    pos[2] = sp[2] + r[2];
+    bool ok = kepler_uv(mu, sqmu, hr, hv, dt_obs - tau, chi, r, v);
+    pos[0] = fma(-tau, sun_obs[3], sun_obs[0]) + r[0];
+    pos[1] = fma(-tau, sun_obs[4], sun_obs[1]) + r[1];
+    pos[2] = fma(-tau, sun_obs[5], sun_obs[2]) + r[2];
     return ok;
 }
 
@@ -497,6 +515,8 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
         const double dt_obs = C.X.epoch[e] - t_ref;
         const double o[3] = {C.X.obs[3 * e], C.X.obs[3 * e + 1], C.X.obs[3 * e + 2]};
         const double *sun = C.B.sun + 6 * k;
+        const double sun_obs[6] = {C.X.sun[6 * e], C.X.sun[6 * e + 1], C.X.sun[6 * e + 2],
+                                   C.X.sun[6 * e + 3], C.X.sun[6 * e + 4], C.X.sun[6 * e + 5]};
         const int32_t f0 = C.exp_first[e], f1 = C.exp_first[e + 1];
         const int64_t c0 = C.exp_off[el], c1 = C.exp_off[el + 1];
         const double *st = C.stop_states + (int64_t)kl * 6 * C.n;
@@ -509,15 +529,15 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
             }
             // light delay (Sec. 2): tau0 = |r(t)-o|/c, three fixed iterations
             double chi = 0.0, pos[3];
-            bool ok = twobody_pos(C.E, mu, sqmu, hr, hv, t_ref, dt_obs, chi, pos);
+            bool ok = twobody_pos(mu, sqmu, hr, hv, sun_obs, dt_obs, 0.0, chi, pos);
             double u[3] = {pos[0] - o[0], pos[1] - o[1], pos[2] - o[2]};
             double tau = sqrt(dot3(u, u)) * kInvC;
             for (int it = 0; it < 3; it++) {
-                ok &= twobody_pos(C.E, mu, sqmu, hr, hv, t_ref, dt_obs - tau, chi, pos);
+                ok &= twobody_pos(mu, sqmu, hr, hv, sun_obs, dt_obs, tau, chi, pos);
                 u[0] = pos[0] - o[0]; u[1] = pos[1] - o[1]; u[2] = pos[2] - o[2];
                 tau = sqrt(dot3(u, u)) * kInvC;
             }
-            ok &= twobody_pos(C.E, mu, sqmu, hr, hv, t_ref, dt_obs - tau, chi, pos);
+            ok &= twobody_pos(mu, sqmu, hr, hv, sun_obs, dt_obs, tau, chi, pos);
             u[0] = pos[0] - o[0]; u[1] = pos[1] - o[1]; u[2] = pos[2] - o[2];
             if (!ok) {
                 if (C.status) atomicCAS(&C.status[i], KETE_BODY_OK, KETE_BODY_KEPLER_CAP);
@@ -620,11 +640,12 @@ cudaError_t fov_exposure_first(const int32_t *is_start, const int64_t *ex, int64
     return cudaSuccess;
 }
 
-cudaError_t fov_exposure_prep(const kete_frame *frames, int64_t nf, const double *observers,
-                              const double *fcen, const int32_t *exp_first, int64_t ne,
-                              ExpArrays X, unsigned int *max_rad_bits, cudaStream_t st)
+cudaError_t fov_exposure_prep(const EphemDev &E, const kete_frame *frames, int64_t nf,
+                              const double *observers, const double *fcen,
+                              const int32_t *exp_first, int64_t ne, ExpArrays X,
+                              unsigned int *max_rad_bits, DevCounters *ctr, cudaStream_t st)
 {
-    if (ne > 0) KLAUNCH(k_exposure_prep<<<grid_for(ne, 128), 128, 0, st>>>(frames, nf, observers, fcen, exp_first, ne, X, max_rad_bits));
+    if (ne > 0) KLAUNCH(k_exposure_prep<<<grid_for(ne, 128), 128, 0, st>>>(E, frames, nf, observers, fcen, exp_first, ne, X, max_rad_bits, ctr));
     return cudaSuccess;
 }
 

@@ -16,6 +16,8 @@ struct ExpArrays {
     double *rad;       // [E] cap radius, rad (pi = covers everything)
     float2 *cs;        // [E] (cos r, sin r) of the cap, cos = -2 when r = pi
     int32_t *batch;    // [E]
+    double *sun;       // [E][6] Sun position and velocity at the exposure epoch
+    float4 *obs_rel;   // [E] observer minus its batch's mean observer (FP32), w unused
 };
 
 // per batch of exposures (<= span in time, Sec. 2)
@@ -76,9 +78,10 @@ cudaError_t fov_frame_prep(const kete_frame *frames, int64_t nf, int64_t n_obs, 
                            double *fcen, float4 *faux, DevCounters *ctr, cudaStream_t st);
 cudaError_t fov_exposure_first(const int32_t *is_start, const int64_t *ex, int64_t nf,
                                int32_t *exp_first, cudaStream_t st);
-cudaError_t fov_exposure_prep(const kete_frame *frames, int64_t nf, const double *observers,
-                              const double *fcen, const int32_t *exp_first, int64_t ne,
-                              ExpArrays X, unsigned int *max_rad_bits, cudaStream_t st);
+cudaError_t fov_exposure_prep(const EphemDev &E, const kete_frame *frames, int64_t nf,
+                              const double *observers, const double *fcen,
+                              const int32_t *exp_first, int64_t ne, ExpArrays X,
+                              unsigned int *max_rad_bits, DevCounters *ctr, cudaStream_t st);
 cudaError_t fov_batches(const double *ep, int64_t ne, double span, int32_t *next, BatchArrays B,
                         int32_t *n_batches, cudaStream_t st);
 cudaError_t fov_batch_info(const EphemDev &E, ExpArrays X, BatchArrays B, int32_t nb,
