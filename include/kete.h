@@ -141,7 +141,14 @@ typedef struct kete_stats {
     double order_ms;             /* hit ordering */
     int64_t node_evals;          /* force evaluations served by batch node rows (steps that
                                     span a whole leg between consecutive stops) */
+    int64_t prop_kind;           /* propagation launch used: KETE_PROP_STATIC or _WORK_STEALING */
+    int64_t prop_block;          /* its threads per block */
 } kete_stats;
+
+/* propagation launch variants (kete_set_propagation, kete_autotune) */
+#define KETE_PROP_STATIC 0         /* one body per thread, one launch per chunk of stops */
+#define KETE_PROP_WORK_STEALING 1  /* persistent: lanes take bodies from an atomic counter and
+                                      advance one step attempt per iteration */
 
 typedef struct kete_ctx kete_ctx;
 
@@ -216,6 +223,24 @@ int kete_fov_check(kete_ctx *ctx, const double *states, const double *epochs, in
 
 /* Copy the counters of the last call into *out (host). */
 int kete_get_stats(const kete_ctx *ctx, kete_stats *out);
+
+/* Choose how the propagation kernel of `precision` (KETE_FP64 / KETE_MIXED)
+ * is launched by later calls: kind KETE_PROP_STATIC or
+ * KETE_PROP_WORK_STEALING, block 32..128 threads (multiple of 32).  Both
+ * produce identical results; they differ in load balance when bodies need
+ * very different numbers of steps.  Default: work stealing, 128.
+ * Errors: BAD_ARG. */
+int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block);
+
+/* Autotuner: time every launch variant (static 128; work stealing 64 and 128)
+ * on an evenly strided sample of up to `max_sample` of the n bodies (device
+ * states [6][n] / epochs [n], not modified) propagated along the chain of
+ * stops (host, ascending) with force model fm, keep the fastest for fm's
+ * precision, and report it in *kind / *block (host, may be NULL).
+ * Errors: BAD_ARG, NO_EPHEM, NOMEM, CUDA. */
+int kete_autotune(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                  const double *stops, int64_t n_stops, const kete_force_model *fm,
+                  int64_t max_sample, int32_t *kind, int32_t *block);
 
 /* Largest n kete_propagate_noalloc accepts. */
 #define KETE_NOALLOC_MAX_BODIES 65536

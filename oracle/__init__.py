@@ -54,6 +54,9 @@ class Stats(C.Structure):
                 ("iterations", C.c_int64)]
 
 
+OBS_DTYPE = np.dtype([("epoch", "<f8"), ("ra", "<f8"), ("dec", "<f8"), ("obs", "<f8", (3,))])
+assert OBS_DTYPE.itemsize == 48
+
 HIT_DTYPE = np.dtype([("frame", "<i8"), ("body", "<i4"), ("status", "<i4"), ("ra", "<f8"),
                       ("dec", "<f8"), ("margin", "<f8"), ("tau", "<f8")])
 
@@ -83,6 +86,11 @@ def lib():
         L.ko_in_polygon.argtypes = [C.c_void_p, d, d]
         L.ko_make_batches.argtypes = [d, C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p]
         L.ko_make_batches.restype = C.c_int64
+        L.ko_body_loss.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, C.c_double,
+                                   C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, d,
+                                   C.c_void_p, C.c_void_p]
+        L.ko_propagate_stm.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, d, d,
+                                       C.c_double, d, C.POINTER(Stats)]
         L.ko_fov_check.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, d, C.c_int64,
                                    C.c_void_p, C.c_int64, d, C.c_int64, C.POINTER(SurveyOpts),
                                    C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
@@ -167,6 +175,27 @@ class Oracle:
         rc = lib().ko_apparent(C.byref(self.eph), _dp(st), t_ref, t_obs, _dp(o), _dp(u),
                                C.byref(tau))
         return rc, u, tau.value
+
+    def propagate_stm(self, fm, state, t, t_target, dt=0.0):
+        st = np.ascontiguousarray(state, float).copy()
+        phi = np.eye(6).ravel().copy()
+        tt = C.c_double(t); dd = C.c_double(dt); stats = Stats()
+        rc = lib().ko_propagate_stm(C.byref(self.eph), C.byref(fm), _dp(st), _dp(phi), C.byref(tt),
+                                    t_target, C.byref(dd), C.byref(stats))
+        return rc, st, phi.reshape(6, 6), tt.value, dd.value, stats
+
+    def body_loss(self, fm, state, epoch, obs, batch_span=3.0, twobody_max=1.5, ckpt_days=8.0,
+                  grad=True):
+        """Loss of one body's observations; (rc, loss, pred [m,2], grad [6] or None)."""
+        st = np.ascontiguousarray(state, float)
+        ob = np.ascontiguousarray(obs, OBS_DTYPE)
+        loss = C.c_double()
+        pred = np.zeros((len(ob), 2))
+        g = np.zeros(6)
+        rc = lib().ko_body_loss(C.byref(self.eph), C.byref(fm), _dp(st), epoch, ob.ctypes.data,
+                                len(ob), batch_span, twobody_max, ckpt_days, C.byref(loss),
+                                pred.ctypes.data, g.ctypes.data if grad else None)
+        return rc, loss.value, pred, (g if grad else None)
 
     def fov_check(self, fm, states, epochs, frames, observers, batch_span=3.0, twobody_max=1.5,
                   prefilter_deg=0.0, subset=None, n_threads=None):

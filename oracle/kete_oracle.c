@@ -36,6 +36,13 @@
  *     so substep epochs carry no rounding of the absolute date (which would
  *     otherwise add noise the corrector's b6 estimate amplifies near planets).
  *     A step that rounds to zero length ends the leg with KO_STEP_CAP.
+ *  R12 (close encounters, not in the paper): with a planet within 0.1 AU at
+ *     the step start, the body-planet vector at a substep is formed as
+ *     (x0 - p(t0)) + (dx - dp) from the displacements since the step start
+ *     (dp by a recurrence on Chebyshev differences), and the step ends at the
+ *     next table segment boundary.  The force is unchanged; its rounding noise
+ *     (~1e-16 AU of ~1 AU coordinates, large relative to a 0.001 AU distance)
+ *     no longer reaches b6, which would otherwise shrink the step forever.
  *  R11 (Sec. 2, chain of batch midpoints): a body is integrated from its epoch
  *     to the first batch midpoint, then from each midpoint to the next; the
  *     proposed step size is carried along the chain.
@@ -151,6 +158,51 @@ int ko_ephem_eval(const ko_ephem *e, int body, double t, double pos[3], double v
     return ephem_eval_off(e, body, t, 0.0, pos, vel);
 }
 
+/* p(t0 + off) - p(t0) of table body `body`, both read from the segment that
+ * holds t0 (R12): sum_k c_k (T_k(tau1) - T_k(tau0)) with the differences from
+ * D_1 = tau1 - tau0, D_{k+1} = 2 tau1 D_k - D_{k-1} + 2 (tau1 - tau0) T_k(tau0),
+ * so that a small displacement is not formed as the difference of two rounded
+ * positions of size ~1 AU. */
+static int ephem_delta(const ko_ephem *e, int body, double t0, double off, double dp[3])
+{
+    double t_end = e->t_start + e->n_seg * e->seg_len;
+    if (!(t0 >= e->t_start && t0 <= t_end)) return KO_OUT_OF_SPAN;
+    int64_t s = (int64_t)floor((t0 - e->t_start) / e->seg_len);
+    if (s < 0) s = 0;
+    if (s > e->n_seg - 1) s = e->n_seg - 1;
+    double t_mid = e->t_start + ((double)s + 0.5) * e->seg_len;
+    double tau0 = 2.0 * (t0 - t_mid) / e->seg_len;
+    double dtau = 2.0 * off / e->seg_len;
+    double tau1 = tau0 + dtau;
+    int nc = e->n_coef;
+    double T[64], D[64];
+    T[0] = 1.0;
+    T[1] = tau0;
+    for (int k = 2; k < nc; k++) T[k] = 2.0 * tau0 * T[k - 1] - T[k - 2];
+    D[0] = 0.0;
+    D[1] = dtau;
+    for (int k = 1; k + 1 < nc; k++) D[k + 1] = 2.0 * tau1 * D[k] - D[k - 1] + 2.0 * dtau * T[k];
+    for (int c = 0; c < 3; c++) {
+        const double *cf = e->coef + (((size_t)body * e->n_seg + s) * 3 + c) * nc;
+        double sum = 0.0;
+        for (int k = 1; k < nc; k++) sum += cf[k] * D[k];
+        dp[c] = sum;
+    }
+    return KO_OK;
+}
+
+/* Close encounter (R12): the planet nearest the body at the step start, if it
+ * is within KO_CLOSE_AU; its relative position at a substep is
+ * (x0 - p(t0)) + (dx - dp) with dx, dp the body's and the planet's
+ * displacements since the step start. */
+#define KO_CLOSE_AU 0.1
+typedef struct {
+    int m;               /* table body, -1: none */
+    double t0;           /* step start */
+    double d0[3];        /* x0 - p_m(t0) */
+    double dx[3];        /* body displacement x(t0 + off) - x0 of the current call */
+} ko_close;
+
 /* ---- force model: Eq. A.1 = sum over masses of Newton + A.3 + A.4 -------- */
 static void pole_vector(double ra, double dec, double p[3])
 {
@@ -162,8 +214,17 @@ static void pole_vector(double ra, double dec, double p[3])
 }
 
 /* acceleration at epoch t0 + off (Eq. A.1); see ephem_eval_off for the offset */
+static int accel_off_cl(const ko_ephem *e, const ko_force_model *fm, double t0, double off,
+                        const double x[3], const double v[3], double a[3], const ko_close *cl);
+
 static int accel_off(const ko_ephem *e, const ko_force_model *fm, double t0, double off,
                      const double x[3], const double v[3], double a[3])
+{
+    return accel_off_cl(e, fm, t0, off, x, v, a, NULL);
+}
+
+static int accel_off_cl(const ko_ephem *e, const ko_force_model *fm, double t0, double off,
+                        const double x[3], const double v[3], double a[3], const ko_close *cl)
 {
     const double c = c_au_per_day();
     a[0] = a[1] = a[2] = 0.0;
@@ -174,6 +235,12 @@ static int accel_off(const ko_ephem *e, const ko_force_model *fm, double t0, dou
         if (st != KO_OK) return st;
         double mu = e->gm[m];
         double r[3] = {x[0] - pm[0], x[1] - pm[1], x[2] - pm[2]};
+        if (cl && cl->m == m) {
+            double dp[3];
+            st = ephem_delta(e, m, cl->t0, off, dp);
+            if (st != KO_OK) return st;
+            for (int i = 0; i < 3; i++) r[i] = cl->d0[i] + (cl->dx[i] - dp[i]);
+        }
         double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
         double rn = sqrt(r2);
         double r3 = r2 * rn;
@@ -309,7 +376,7 @@ static int finite3(const double *x)
 static int radau_attempt(const ko_ephem *e, const ko_force_model *fm, double t,
                          const double x0[3], const double v0[3], const double a0[3],
                          double dt, double x1[3], double v1[3], double *err,
-                         ko_stats *stats)
+                         ko_stats *stats, ko_close *cl)
 {
     const ko_radau *R = radau();
     double g[8][3], b[7][3], F[8][3];
@@ -333,10 +400,12 @@ static int radau_attempt(const ko_ephem *e, const ko_force_model *fm, double t,
                     vacc += b[k][i] * sp / (k + 2.0);
                     sp *= s;
                 }
-                xn[i] = x0[i] + v0[i] * dt * s + dt * dt * acc;
+                double dxn = v0[i] * dt * s + dt * dt * acc;
+                xn[i] = x0[i] + dxn;
                 vn[i] = v0[i] + dt * vacc;
+                if (cl) cl->dx[i] = dxn;
             }
-            int st = accel_off(e, fm, t, s * dt, xn, vn, F[n]);
+            int st = accel_off_cl(e, fm, t, s * dt, xn, vn, F[n], cl);
             if (stats) stats->force_evals++;
             if (st != KO_OK) return st;
             /* Newton divided difference g_n from F_0..F_n and g_1..g_{n-1} */
@@ -384,6 +453,39 @@ static int radau_attempt(const ko_ephem *e, const ko_force_model *fm, double t,
     return KO_OK;
 }
 
+/* Encounter set-up at a step start (R12): the nearest active planet within
+ * KO_CLOSE_AU, and, if there is one, the step limit moved to the next table
+ * segment boundary in the direction of motion (no step of an encounter
+ * straddles a boundary of the piecewise planet polynomials). */
+static int find_close(const ko_ephem *e, const ko_force_model *fm, double t, const double x[3],
+                      double dir, ko_close *cl, double *t_stop, double t_target)
+{
+    cl->m = -1;
+    cl->t0 = t;
+    double best = KO_CLOSE_AU;
+    for (int m = 1; m < e->n_bodies; m++) {
+        if (!((fm->body_mask >> m) & 1u) || e->gm[m] == 0.0) continue;
+        double p[3];
+        int st = ko_ephem_eval(e, m, t, p, NULL);
+        if (st != KO_OK) return st;
+        double d = sqrt((x[0] - p[0]) * (x[0] - p[0]) + (x[1] - p[1]) * (x[1] - p[1]) +
+                        (x[2] - p[2]) * (x[2] - p[2]));
+        if (d < best) {
+            best = d;
+            cl->m = m;
+            for (int i = 0; i < 3; i++) cl->d0[i] = x[i] - p[i];
+        }
+    }
+    *t_stop = t_target;
+    if (cl->m >= 0) {
+        double k = floor((t - e->t_start) / e->seg_len);
+        double b = (dir > 0) ? e->t_start + (k + 1.0) * e->seg_len : e->t_start + k * e->seg_len;
+        if (dir < 0 && b == t) b = e->t_start + (k - 1.0) * e->seg_len;
+        if ((dir > 0 && b < t_target) || (dir < 0 && b > t_target)) *t_stop = b;
+    }
+    return KO_OK;
+}
+
 /* Integrate (st, *t) to t_target exactly; *dt is the proposed step (carried). */
 int ko_propagate(const ko_ephem *e, const ko_force_model *fm, double st[6], double *t,
                  double t_target, double *dt, ko_stats *stats)
@@ -393,20 +495,26 @@ int ko_propagate(const ko_ephem *e, const ko_force_model *fm, double st[6], doub
     if (*dt == 0.0 || (*dt > 0) != (dir > 0)) *dt = dir * fabs(*dt == 0.0 ? fm->dt_init : *dt);
     while (*t != t_target) {
         double x0[3] = {st[0], st[1], st[2]}, v0[3] = {st[3], st[4], st[5]}, a0[3];
-        int s0 = ko_accel(e, fm, *t, x0, v0, a0);
+        ko_close cl;
+        double t_stop = t_target;
+        int s0 = find_close(e, fm, *t, x0, dir, &cl, &t_stop, t_target);
+        if (s0 != KO_OK) return s0;
+        for (int i = 0; i < 3; i++) cl.dx[i] = 0.0;
+        s0 = accel_off_cl(e, fm, *t, 0.0, x0, v0, a0, cl.m >= 0 ? &cl : NULL);
         if (stats) stats->force_evals++;
         if (s0 != KO_OK) return s0;
         for (;;) {
             if (++attempts > fm->max_steps) return KO_STEP_CAP;
-            double remaining = t_target - *t;
+            double remaining = t_stop - *t;
             int clamped = fabs(*dt) >= fabs(remaining);
             /* the step is the exact difference of the two representable epochs
              * it joins, so that the sum of the steps equals the elapsed time */
-            double t_new = clamped ? t_target : *t + *dt;
+            double t_new = clamped ? t_stop : *t + *dt;
             double h = t_new - *t;
             if (h == 0.0) return KO_STEP_CAP;   /* step below the epoch resolution */
             double x1[3], v1[3], err;
-            int s1 = radau_attempt(e, fm, *t, x0, v0, a0, h, x1, v1, &err, stats);
+            int s1 = radau_attempt(e, fm, *t, x0, v0, a0, h, x1, v1, &err, stats,
+                                   cl.m >= 0 ? &cl : NULL);
             if (s1 != KO_OK) return s1;
             /* IAS15 step-size control */
             double dt_new;
@@ -894,4 +1002,322 @@ int ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *stat
     free(all); free(jobs); free(th); free(order); free(ep_all); free(ep); free(bstart);
     free(tref); free(centre);
     return rc;
+}
+
+/* ---- variational equations and the orbit-fit loss (adjoint reference) ---- */
+
+/* Jacobians J_x = da/dx, J_v = da/dv of Eq. A.1 at (t0 + off, x, v) by central
+ * differences (steps 1e-7 AU, 1e-9 AU/day). */
+static int accel_jacobian(const ko_ephem *e, const ko_force_model *fm, double t0, double off,
+                          const double x[3], const double v[3], double Jx[3][3], double Jv[3][3])
+{
+    const double hx = 1e-7, hv = 1e-9;
+    for (int k = 0; k < 3; k++) {
+        double xp[3] = {x[0], x[1], x[2]}, xm[3] = {x[0], x[1], x[2]};
+        double vp[3] = {v[0], v[1], v[2]}, vm[3] = {v[0], v[1], v[2]};
+        double ap[3], am[3];
+        xp[k] += hx;
+        xm[k] -= hx;
+        int s = accel_off(e, fm, t0, off, xp, v, ap);
+        if (s == KO_OK) s = accel_off(e, fm, t0, off, xm, v, am);
+        if (s != KO_OK) return s;
+        for (int i = 0; i < 3; i++) Jx[i][k] = (ap[i] - am[i]) / (2.0 * hx);
+        vp[k] += hv;
+        vm[k] -= hv;
+        s = accel_off(e, fm, t0, off, x, vp, ap);
+        if (s == KO_OK) s = accel_off(e, fm, t0, off, x, vm, am);
+        if (s != KO_OK) return s;
+        for (int i = 0; i < 3; i++) Jv[i][k] = (ap[i] - am[i]) / (2.0 * hv);
+    }
+    return KO_OK;
+}
+
+/* One Gauss-Radau attempt of the body (identical arithmetic to radau_attempt)
+ * carrying the 6 columns of Phi as variational particles: column c has
+ * position Phi[0..2][c], velocity Phi[3..5][c] and acceleration
+ * J_x dx + J_v dv at the body's substep state.  The body alone decides
+ * convergence and the error estimate. */
+static int radau_attempt_stm(const ko_ephem *e, const ko_force_model *fm, double t,
+                             const double x0[3], const double v0[3], const double a0[3],
+                             const double P0[36], const double Pa0[18], double dt,
+                             double x1[3], double v1[3], double P1[36], double *err,
+                             ko_stats *stats, ko_close *cl)
+{
+    const ko_radau *R = radau();
+    double g[8][3], b[7][3], F[8][3];
+    double gv[8][18], bv[7][18], Fv[8][18];   /* variational: 6 columns x 3 */
+    memset(g, 0, sizeof(g));
+    memset(b, 0, sizeof(b));
+    memset(gv, 0, sizeof(gv));
+    memset(bv, 0, sizeof(bv));
+    for (int i = 0; i < 3; i++) F[0][i] = a0[i];
+    for (int q = 0; q < 18; q++) Fv[0][q] = Pa0[q];
+    double pc_prev = 0.0, amax = 0.0;
+    for (int it = 1; it <= fm->max_iter; it++) {
+        double b6_old[3] = {b[6][0], b[6][1], b[6][2]};
+        for (int n = 1; n <= 7; n++) {
+            double s = R->h[n];
+            double xn[3], vn[3];
+            for (int i = 0; i < 3; i++) {
+                double acc = a0[i] * s * s / 2.0;
+                double vacc = a0[i] * s;
+                double sp = s * s;
+                for (int k = 0; k < 7; k++) {
+                    acc += b[k][i] * sp * s / ((k + 2.0) * (k + 3.0));
+                    vacc += b[k][i] * sp / (k + 2.0);
+                    sp *= s;
+                }
+                double dxn = v0[i] * dt * s + dt * dt * acc;
+                xn[i] = x0[i] + dxn;
+                vn[i] = v0[i] + dt * vacc;
+                if (cl) cl->dx[i] = dxn;
+            }
+            /* variational particles at the substep */
+            double dxn[18], dvn[18];
+            for (int c = 0; c < 6; c++)
+                for (int i = 0; i < 3; i++) {
+                    int q = 3 * c + i;
+                    double acc = Pa0[q] * s * s / 2.0, vacc = Pa0[q] * s, sp = s * s;
+                    for (int k = 0; k < 7; k++) {
+                        acc += bv[k][q] * sp * s / ((k + 2.0) * (k + 3.0));
+                        vacc += bv[k][q] * sp / (k + 2.0);
+                        sp *= s;
+                    }
+                    dxn[q] = P0[i * 6 + c] + P0[(3 + i) * 6 + c] * dt * s + dt * dt * acc;
+                    dvn[q] = P0[(3 + i) * 6 + c] + dt * vacc;
+                }
+            int st = accel_off_cl(e, fm, t, s * dt, xn, vn, F[n], cl);
+            if (stats) stats->force_evals++;
+            if (st != KO_OK) return st;
+            double Jx[3][3], Jv[3][3];
+            st = accel_jacobian(e, fm, t, s * dt, xn, vn, Jx, Jv);
+            if (st != KO_OK) return st;
+            for (int c = 0; c < 6; c++)
+                for (int i = 0; i < 3; i++) {
+                    double a = 0.0;
+                    for (int k = 0; k < 3; k++)
+                        a += Jx[i][k] * dxn[3 * c + k] + Jv[i][k] * dvn[3 * c + k];
+                    Fv[n][3 * c + i] = a;
+                }
+            for (int i = 0; i < 3; i++) {
+                double d = (F[n][i] - F[0][i]) / (R->h[n] - R->h[0]);
+                for (int k = 1; k < n; k++) d = (d - g[k][i]) / (R->h[n] - R->h[k]);
+                g[n][i] = d;
+            }
+            for (int q = 0; q < 18; q++) {
+                double d = (Fv[n][q] - Fv[0][q]) / (R->h[n] - R->h[0]);
+                for (int k = 1; k < n; k++) d = (d - gv[k][q]) / (R->h[n] - R->h[k]);
+                gv[n][q] = d;
+            }
+            for (int mm = 0; mm < 7; mm++) {
+                for (int i = 0; i < 3; i++) {
+                    double sum = 0.0;
+                    for (int j = mm + 1; j <= 7; j++) sum += R->C[j][mm] * g[j][i];
+                    b[mm][i] = sum;
+                }
+                for (int q = 0; q < 18; q++) {
+                    double sum = 0.0;
+                    for (int j = mm + 1; j <= 7; j++) sum += R->C[j][mm] * gv[j][q];
+                    bv[mm][q] = sum;
+                }
+            }
+        }
+        if (stats) stats->iterations++;
+        double db = 0.0;
+        amax = 0.0;
+        for (int i = 0; i < 3; i++) {
+            double d = fabs(b[6][i] - b6_old[i]);
+            if (d > db) db = d;
+            if (fabs(F[7][i]) > amax) amax = fabs(F[7][i]);
+        }
+        double pc = db / amax;
+        if (!isfinite(pc)) return KO_NONFINITE;
+        if (pc < fm->eps_pc) break;
+        if (it >= 3 && pc >= pc_prev) break;
+        pc_prev = pc;
+    }
+    double bmax = 0.0;
+    for (int i = 0; i < 3; i++)
+        if (fabs(b[6][i]) > bmax) bmax = fabs(b[6][i]);
+    *err = bmax / amax;
+    for (int i = 0; i < 3; i++) {
+        double acc = a0[i] / 2.0, vacc = a0[i];
+        for (int k = 0; k < 7; k++) {
+            acc += b[k][i] / ((k + 2.0) * (k + 3.0));
+            vacc += b[k][i] / (k + 2.0);
+        }
+        x1[i] = x0[i] + v0[i] * dt + dt * dt * acc;
+        v1[i] = v0[i] + dt * vacc;
+    }
+    for (int c = 0; c < 6; c++)
+        for (int i = 0; i < 3; i++) {
+            int q = 3 * c + i;
+            double acc = Pa0[q] / 2.0, vacc = Pa0[q];
+            for (int k = 0; k < 7; k++) {
+                acc += bv[k][q] / ((k + 2.0) * (k + 3.0));
+                vacc += bv[k][q] / (k + 2.0);
+            }
+            P1[i * 6 + c] = P0[i * 6 + c] + P0[(3 + i) * 6 + c] * dt + dt * dt * acc;
+            P1[(3 + i) * 6 + c] = P0[(3 + i) * 6 + c] + dt * vacc;
+        }
+    if (!finite3(x1) || !finite3(v1)) return KO_NONFINITE;
+    return KO_OK;
+}
+
+int ko_propagate_stm(const ko_ephem *e, const ko_force_model *fm, double st[6], double phi[36],
+                     double *t, double t_target, double *dt, ko_stats *stats)
+{
+    int64_t attempts = 0;
+    double dir = (t_target >= *t) ? 1.0 : -1.0;
+    if (*dt == 0.0 || (*dt > 0) != (dir > 0)) *dt = dir * fabs(*dt == 0.0 ? fm->dt_init : *dt);
+    while (*t != t_target) {
+        double x0[3] = {st[0], st[1], st[2]}, v0[3] = {st[3], st[4], st[5]}, a0[3];
+        ko_close cl;
+        double t_stop = t_target;
+        int s0 = find_close(e, fm, *t, x0, dir, &cl, &t_stop, t_target);
+        if (s0 != KO_OK) return s0;
+        for (int i = 0; i < 3; i++) cl.dx[i] = 0.0;
+        s0 = accel_off_cl(e, fm, *t, 0.0, x0, v0, a0, cl.m >= 0 ? &cl : NULL);
+        if (stats) stats->force_evals++;
+        if (s0 != KO_OK) return s0;
+        double Jx[3][3], Jv[3][3], Pa0[18];
+        s0 = accel_jacobian(e, fm, *t, 0.0, x0, v0, Jx, Jv);
+        if (s0 != KO_OK) return s0;
+        for (int c = 0; c < 6; c++)
+            for (int i = 0; i < 3; i++) {
+                double a = 0.0;
+                for (int k = 0; k < 3; k++)
+                    a += Jx[i][k] * phi[k * 6 + c] + Jv[i][k] * phi[(3 + k) * 6 + c];
+                Pa0[3 * c + i] = a;
+            }
+        for (;;) {
+            if (++attempts > fm->max_steps) return KO_STEP_CAP;
+            double remaining = t_stop - *t;
+            int clamped = fabs(*dt) >= fabs(remaining);
+            double t_new = clamped ? t_stop : *t + *dt;
+            double h = t_new - *t;
+            if (h == 0.0) return KO_STEP_CAP;
+            double x1[3], v1[3], P1[36], err;
+            int s1 = radau_attempt_stm(e, fm, *t, x0, v0, a0, phi, Pa0, h, x1, v1, P1, &err, stats,
+                                       cl.m >= 0 ? &cl : NULL);
+            if (s1 != KO_OK) return s1;
+            double dt_new;
+            if (isnormal(err))
+                dt_new = pow(fm->eps / err, 1.0 / 7.0) * h;
+            else
+                dt_new = h / fm->safety;
+            if (fabs(dt_new / h) < fm->safety) {
+                *dt = dt_new;
+                if (stats) stats->rejected++;
+                continue;
+            }
+            if (fabs(dt_new / h) > 1.0 / fm->safety) dt_new = h / fm->safety;
+            *dt = dt_new;
+            for (int i = 0; i < 3; i++) { st[i] = x1[i]; st[3 + i] = v1[i]; }
+            memcpy(phi, P1, sizeof(P1));
+            *t = t_new;
+            if (stats) stats->steps++;
+            break;
+        }
+    }
+    return KO_OK;
+}
+
+static double wrap_pi(double a)
+{
+    while (a > M_PI) a -= 2.0 * M_PI;
+    while (a <= -M_PI) a += 2.0 * M_PI;
+    return a;
+}
+
+/* residual (wrap(RA - RA_obs) cos Dec_obs, Dec - Dec_obs) of one observation
+ * predicted from the batch state y at t_ref */
+static int obs_residual(const ko_ephem *e, const double y[6], double t_ref, const ko_obs *o,
+                        double res[2], double *ra_out, double *dec_out)
+{
+    double u[3], tau, ra, dec;
+    int s = ko_apparent(e, y, t_ref, o->epoch, o->obs, u, &tau);
+    if (s != KO_OK) return s;
+    ko_radec(u, &ra, &dec);
+    res[0] = wrap_pi(ra - o->ra) * cos(o->dec);
+    res[1] = dec - o->dec;
+    if (ra_out) *ra_out = ra;
+    if (dec_out) *dec_out = dec;
+    return KO_OK;
+}
+
+static int cmp_dbl(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x < y) ? -1 : (x > y);
+}
+
+int ko_body_loss(const ko_ephem *e, const ko_force_model *fm, const double st0[6], double epoch0,
+                 const ko_obs *obs, int m, double batch_span, double twobody_max,
+                 double ckpt_days, double *loss, double *pred, double grad_var[6])
+{
+    for (int j = 1; j < m; j++)
+        if (obs[j].epoch < obs[j - 1].epoch) return -1;
+    double *ep = (double *)malloc(sizeof(double) * (m ? m : 1));
+    int64_t *bs = (int64_t *)malloc(sizeof(int64_t) * (m ? m : 1));
+    double *tref = (double *)malloc(sizeof(double) * (m ? m : 1));
+    for (int j = 0; j < m; j++) ep[j] = obs[j].epoch;
+    int64_t nb = ko_make_batches(ep, m, batch_span, twobody_max, bs, tref);
+    /* stops: batch midpoints and the checkpoint grid up to the last midpoint */
+    int cap = (int)nb + 4096;
+    double *stops = (double *)malloc(sizeof(double) * cap);
+    int ns = 0;
+    for (int64_t k = 0; k < nb; k++) stops[ns++] = tref[k];
+    if (nb > 0 && ckpt_days > 0)
+        for (int k = 1; epoch0 + k * ckpt_days < tref[nb - 1] && ns < cap; k++)
+            stops[ns++] = epoch0 + k * ckpt_days;
+    qsort(stops, ns, sizeof(double), cmp_dbl);
+    double y[6], phi[36], t = epoch0, dt = 0.0, L = 0.0;
+    memcpy(y, st0, sizeof(y));
+    for (int r = 0; r < 36; r++) phi[r] = (r % 7 == 0) ? 1.0 : 0.0;
+    if (grad_var) memset(grad_var, 0, 6 * sizeof(double));
+    int status = KO_OK;
+    int64_t kb = 0;
+    for (int q = 0; q < ns && status == KO_OK; q++) {
+        if (grad_var) status = ko_propagate_stm(e, fm, y, phi, &t, stops[q], &dt, NULL);
+        else status = ko_propagate(e, fm, y, &t, stops[q], &dt, NULL);
+        if (status != KO_OK) break;
+        if (kb < nb && stops[q] == tref[kb]) {
+            int64_t j0 = bs[kb], j1 = (kb + 1 < nb) ? bs[kb + 1] : m;
+            for (int64_t j = j0; j < j1 && status == KO_OK; j++) {
+                double res[2], ra, dec;
+                status = obs_residual(e, y, tref[kb], &obs[j], res, &ra, &dec);
+                if (status != KO_OK) break;
+                L += res[0] * res[0] + res[1] * res[1];
+                if (pred) { pred[2 * j] = ra; pred[2 * j + 1] = dec; }
+                if (!grad_var) continue;
+                /* d res / d y(t_ref) by central differences */
+                double dr[2][6];
+                for (int c = 0; c < 6; c++) {
+                    double h = (c < 3) ? 1e-7 : 1e-9;
+                    double yp[6], ym[6], rp[2], rm[2];
+                    memcpy(yp, y, sizeof(yp));
+                    memcpy(ym, y, sizeof(ym));
+                    yp[c] += h;
+                    ym[c] -= h;
+                    status = obs_residual(e, yp, tref[kb], &obs[j], rp, NULL, NULL);
+                    if (status == KO_OK) status = obs_residual(e, ym, tref[kb], &obs[j], rm, NULL, NULL);
+                    if (status != KO_OK) break;
+                    dr[0][c] = wrap_pi(rp[0] - rm[0]) / (2.0 * h);
+                    dr[1][c] = (rp[1] - rm[1]) / (2.0 * h);
+                }
+                /* dL/dy0 += 2 res^T (dres/dy) Phi */
+                for (int c0 = 0; c0 < 6; c0++) {
+                    double acc = 0.0;
+                    for (int c = 0; c < 6; c++)
+                        acc += (2.0 * res[0] * dr[0][c] + 2.0 * res[1] * dr[1][c]) * phi[c * 6 + c0];
+                    grad_var[c0] += acc;
+                }
+            }
+            kb++;
+        }
+    }
+    *loss = L;
+    free(ep); free(bs); free(tref); free(stops);
+    return status;
 }

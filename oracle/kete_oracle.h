@@ -93,6 +93,13 @@ typedef struct {
     int64_t steps, rejected, force_evals, iterations;
 } ko_stats;
 
+/* one astrometric observation of one body (48 bytes) */
+typedef struct {
+    double epoch;            /* TDB JD */
+    double ra, dec;          /* observed, radians (equatorial J2000) */
+    double obs[3];           /* observer position, barycentric ecliptic AU */
+} ko_obs;
+
 void ko_force_model_default(ko_force_model *fm);
 int  ko_ephem_load(ko_ephem *e, const void *buf, size_t n);
 void ko_ephem_free(ko_ephem *e);
@@ -126,6 +133,24 @@ int  ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *sta
                   const int32_t *body_subset, int64_t n_subset, ko_hit *hits,
                   int64_t capacity, int64_t *n_hits, int32_t *status, int n_threads,
                   ko_stats *stats);
+
+/* Orbit-fit loss of one body and its gradient w.r.t. the initial state.
+ * Forward model: the body's observation epochs (sorted) are batched by the
+ * <= batch_span rule, the n-body chain visits the union of the batch midpoints
+ * and the checkpoint grid epoch0 + ckpt_days * k, then two-body + light time +
+ * RA/Dec per observation (Sec. 2).  loss = sum (wrap(RA-RA_obs) cos Dec_obs)^2
+ * + (Dec-Dec_obs)^2.  pred (may be NULL): [m][2] model RA, Dec.
+ * grad_var (may be NULL): dL/d(x0, v0) by the variational equations (6x6
+ * state-transition matrix integrated with the body, Jacobians of Eq. A.1 by
+ * central differences) chained with central-difference partials of the
+ * observation operator. */
+int  ko_body_loss(const ko_ephem *e, const ko_force_model *fm, const double st0[6], double epoch0,
+                  const ko_obs *obs, int m, double batch_span, double twobody_max,
+                  double ckpt_days, double *loss, double *pred, double grad_var[6]);
+/* the state-transition matrix Phi (6x6, row-major, Phi[r*6+c] = dy_r/dy0_c)
+ * propagated with the body along exactly the body's own step sequence */
+int  ko_propagate_stm(const ko_ephem *e, const ko_force_model *fm, double st[6], double phi[36],
+                      double *t, double t_target, double *dt, ko_stats *stats);
 
 #ifdef __cplusplus
 }

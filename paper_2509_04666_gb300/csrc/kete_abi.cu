@@ -26,7 +26,8 @@ enum Slot {
     S_BO, S_BROBS, S_BTSPAN, S_BRMAX, S_BSUN, S_NBATCH, S_BANDS, S_CELLKEY, S_CELLCNT,
     S_CELLSTART, S_CELLCUR, S_CELLEXP, S_CAND, S_EXPCNT, S_EXPOFF, S_EXPCUR, S_CANDBODY,
     S_HITTMP, S_FRAMECNT, S_FRAMEOFF, S_FRAMECUR, S_HITGROUP, S_MAXRAD, S_NT_T0, S_NT_H,
-    S_NT_R64, S_NT_R32, S_XSUN, S_XOBSREL, S_NSLOTS
+    S_NT_R64, S_NT_R32, S_XSUN, S_XOBSREL, S_NEXTBODY, S_TUNE_ST, S_TUNE_EP, S_TUNE_OUT,
+    S_NSLOTS
 };
 
 struct Scratch {
@@ -54,6 +55,7 @@ struct kete_ctx {
     // phase timers: pairs of events per phase (prep, candidates, exact, order)
     std::vector<cudaEvent_t> phase_ev[4];
     int phase_n[4] = {0, 0, 0, 0};
+    PropVariant var[2] = {{PROP_WORK_STEALING, 128}, {PROP_WORK_STEALING, 128}};   // per precision
 };
 
 enum Phase { PH_PREP = 0, PH_CAND = 1, PH_EXACT = 2, PH_ORDER = 3 };
@@ -408,6 +410,21 @@ extern "C" int kete_ephem_eval(kete_ctx *ctx, const double *t, int64_t n, int bo
     return KETE_OK;
 }
 
+// Launch the propagation kernel with the context's variant for F's precision.
+static int propagate(kete_ctx *ctx, const ForceDev &F, ChainState cs, const double *stops_dev,
+                     int n_stops, double *out, int64_t stride, bool keep_on_fail,
+                     const NodeTable *nt, int leg0)
+{
+    PropVariant var = ctx->var[F.precision == KETE_MIXED ? 1 : 0];
+    unsigned long long *next = nullptr;
+    if (var.kind == PROP_WORK_STEALING) GET(S_NEXTBODY, 1, next);
+    ctx->stats.prop_kind = var.kind;
+    ctx->stats.prop_block = var.block;
+    CUDA_TRY(launch_propagate(ctx->E, F, cs, stops_dev, n_stops, out, stride, keep_on_fail,
+                              ctx->d_ctr, ctx->stream, nt, leg0, var, next));
+    return KETE_OK;
+}
+
 // Planet states at the Gauss-Radau node epochs of every leg of a chain of stops.
 static int node_table(kete_ctx *ctx, const double *stops_dev, int n_stops, const double *epochs,
                       NodeTable &nt)
@@ -462,7 +479,8 @@ extern "C" int kete_propagate(kete_ctx *ctx, double *states, double *epochs, int
         r = node_table(ctx, d_stop, 1, epochs, nt);
         if (r != KETE_OK) return r;
         prop_event(ctx, true);
-        CUDA_TRY(launch_propagate(ctx->E, F, cs, d_stop, 1, states, n, true, ctx->d_ctr, ctx->stream, &nt, 0));
+        r = propagate(ctx, F, cs, d_stop, 1, states, n, true, &nt, 0);
+        if (r != KETE_OK) return r;
         prop_event(ctx, false);
         CUDA_TRY(launch_chain_finish(cs, states, epochs, status, ctx->stream));
         ctx->stats.launches = 4;
@@ -501,7 +519,8 @@ extern "C" int kete_propagate_stops(kete_ctx *ctx, const double *states, const d
         r = node_table(ctx, d_stops, (int)n_stops, epochs, nt);
         if (r != KETE_OK) return r;
         prop_event(ctx, true);
-        CUDA_TRY(launch_propagate(ctx->E, F, cs, d_stops, (int)n_stops, out, n, false, ctx->d_ctr, ctx->stream, &nt, 0));
+        r = propagate(ctx, F, cs, d_stops, (int)n_stops, out, n, false, &nt, 0);
+        if (r != KETE_OK) return r;
         prop_event(ctx, false);
         CUDA_TRY(launch_chain_finish(cs, nullptr, nullptr, status, ctx->stream));
         ctx->stats.launches = 4;
@@ -682,7 +701,8 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
         const int32_t nek = e1 - e0;
         // propagation to the batch midpoints of this chunk
         prop_event(ctx, true);
-        CUDA_TRY(launch_propagate(ctx->E, F, cs, B.t_ref + k0, nk, stop_states, n, false, ctx->d_ctr, st, &nt, k0));
+        r = propagate(ctx, F, cs, B.t_ref + k0, nk, stop_states, n, false, &nt, k0);
+        if (r != KETE_OK) return r;
         prop_event(ctx, false);
         launches++;
         // exposures of the chunk into sky cells
@@ -838,5 +858,78 @@ extern "C" int kete_propagate_noalloc(kete_ctx *ctx, double *states, double *epo
     r = noalloc_propagate(ctx->device, ctx->stream, ctx->E, F, states, epochs, n, t_target,
                           status, &why);
     if (r != KETE_OK) return fail(ctx, r, "kete_propagate_noalloc: %s", why);
+    return KETE_OK;
+}
+
+extern "C" int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    if ((precision != KETE_FP64 && precision != KETE_MIXED) ||
+        (kind != KETE_PROP_STATIC && kind != KETE_PROP_WORK_STEALING) || block < 32 ||
+        block > 128 || block % 32 != 0)
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad propagation variant (precision %d, kind %d, block %d)",
+                    precision, kind, block);
+    ctx->var[precision == KETE_MIXED ? 1 : 0] = PropVariant{kind, block};
+    return KETE_OK;
+}
+
+extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                             const double *stops, int64_t n_stops, const kete_force_model *fm,
+                             int64_t max_sample, int32_t *kind, int32_t *block)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
+    if (n <= 0 || n > INT32_MAX || !states || !epochs || n_stops <= 0 || n_stops > INT32_MAX ||
+        !stops || max_sample <= 0)
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad arguments");
+    for (int64_t k = 0; k < n_stops; k++)
+        if (!std::isfinite(stops[k]) || (k > 0 && stops[k] < stops[k - 1]))
+            return fail(ctx, KETE_ERR_BAD_ARG, "stops must be finite and ascending");
+    ForceDev F;
+    int r = make_force(ctx, fm, F);
+    if (r != KETE_OK) return r;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int64_t m = std::min(n, max_sample);
+    const int64_t stride = n / m;
+    double *sst, *sep, *out, *d_stops;
+    GET(S_TUNE_ST, 6 * m, sst);
+    GET(S_TUNE_EP, m, sep);
+    GET(S_TUNE_OUT, (size_t)n_stops * 6 * m, out);
+    GET(S_STOPS, n_stops, d_stops);
+    CUDA_TRY(cudaMemcpyAsync(d_stops, stops, n_stops * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(launch_gather_bodies(states, epochs, n, stride, m, sst, sep, st));
+    const PropVariant cands[3] = {{PROP_STATIC, 128}, {PROP_WORK_STEALING, 64},
+                                  {PROP_WORK_STEALING, 128}};
+    const PropVariant saved = ctx->var[F.precision == KETE_MIXED ? 1 : 0];
+    float best_ms = 1e30f;
+    PropVariant best = saved;
+    cudaEvent_t e0 = event_at(ctx, 0), e1 = event_at(ctx, 1);
+    for (int c = 0; c < 3; c++) {
+        ctx->var[F.precision == KETE_MIXED ? 1 : 0] = cands[c];
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; rep++) {   // the first run warms up
+            ChainState cs;
+            r = run_chain(ctx, F, sst, sep, m, cs);
+            if (r != KETE_OK) return r;
+            NodeTable nt;
+            r = node_table(ctx, d_stops, (int)n_stops, sep, nt);
+            if (r != KETE_OK) return r;
+            CUDA_TRY(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
+            CUDA_TRY(cudaEventRecord(e0, st));
+            r = propagate(ctx, F, cs, d_stops, (int)n_stops, out, m, false, &nt, 0);
+            if (r != KETE_OK) return r;
+            CUDA_TRY(cudaEventRecord(e1, st));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cands[c];
+        }
+    }
+    ctx->var[F.precision == KETE_MIXED ? 1 : 0] = best;
+    if (kind) *kind = best.kind;
+    if (block) *block = best.block;
     return KETE_OK;
 }

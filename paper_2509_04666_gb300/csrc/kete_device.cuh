@@ -180,6 +180,43 @@ __device__ __forceinline__ void cheb_state32(const EphemDev &E, int m, int s, fl
     }
 }
 
+// p(t0 + off) - p(t0) of body m from the segment holding t0: Chebyshev
+// differences D_k = T_k(tau1) - T_k(tau0) by D_{k+1} = 2 tau1 D_k - D_{k-1} +
+// 2 (tau1 - tau0) T_k(tau0), so a small planet displacement is not the
+// difference of two rounded ~1 AU positions (close-encounter path).
+static __device__ __noinline__ void cheb_delta64(const EphemDev &E, int m, double t0, double off,
+                                                 double *dp)
+{
+    int s = (int)floor((t0 - E.t_start) * E.inv_seg);
+    s = s < 0 ? 0 : (s > E.n_seg - 1 ? E.n_seg - 1 : s);
+    const double t_mid = E.t_start + ((double)s + 0.5) * E.seg_len;
+    const double tau0 = 2.0 * (t0 - t_mid) * E.inv_seg;
+    const double dtau = 2.0 * off * E.inv_seg;
+    const double tau1 = tau0 + dtau;
+    const double *c = ephem_coef(E, m, s);
+    double acc[3] = {0.0, 0.0, 0.0};
+    double Tm1 = 1.0, T = tau0;          // T_{k-1}(tau0), T_k(tau0)
+    double Dm1 = 0.0, D = dtau;          // D_{k-1}, D_k
+    for (int k = 1; k < E.n_coef; k++) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) acc[d] = fma(__ldg(c + d * E.n_coef + k), D, acc[d]);
+        const double Dn = fma(2.0 * tau1, D, fma(2.0 * dtau, T, -Dm1));
+        const double Tn = fma(2.0 * tau0, T, -Tm1);
+        Dm1 = D; D = Dn;
+        Tm1 = T; T = Tn;
+    }
+    dp[0] = acc[0]; dp[1] = acc[1]; dp[2] = acc[2];
+}
+
+// Close encounter: the nearest planet within kEncounterAu of the body at the
+// step start.  At a substep its relative position is d0 + (dx - dp(off)).
+constexpr double kEncounterAu = 0.1;
+struct Encounter {
+    int m;            // table body, -1: none
+    double t0;        // step start
+    double d0[3];     // x0 - p_m(t0)
+};
+
 // Node rows: planet states at one Gauss-Radau node epoch of a batch leg,
 // shared by every body whose step spans that whole leg.
 //   row64[m*6 + 0..5]  barycentric position, velocity (FP64)
@@ -187,12 +224,20 @@ __device__ __forceinline__ void cheb_state32(const EphemDev &E, int m, int s, fl
 // A null row64 means "evaluate the table here" (per-thread path).
 
 // Full-FP64 acceleration.
+// detect (step start, off = 0): also record in enc the nearest planet within
+// kEncounterAu and its relative position; otherwise enc is read.
 __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, double t0,
                                           double off, const double *__restrict__ row64,
-                                          const double x[3], const double v[3], double a[3])
+                                          const double x[3], const double v[3], double a[3],
+                                          Encounter &enc, const double dx[3], bool detect)
 {
     Seg g;
     a[0] = a[1] = a[2] = 0.0;
+    if (detect) {
+        enc.m = -1;
+        enc.t0 = t0;
+    }
+    double best = kEncounterAu * kEncounterAu;
     if (!row64 && !ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
     for (int m = 0; m < E.n_bodies; m++) {
         if (!((F.active_mask >> m) & 1u)) continue;
@@ -205,6 +250,20 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
             cheb_state64(E, m, g.s, g.tau, st);
         }
         double r[3] = {x[0] - st[0], x[1] - st[1], x[2] - st[2]};
+        if (detect) {
+            const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            if (m > 0 && rr < best) {
+                best = rr;
+                enc.m = m;
+                enc.d0[0] = r[0]; enc.d0[1] = r[1]; enc.d0[2] = r[2];
+            }
+        } else if (m == enc.m) {
+            double dp[3];
+            cheb_delta64(E, m, enc.t0, off, dp);
+            r[0] = enc.d0[0] + (dx[0] - dp[0]);
+            r[1] = enc.d0[1] + (dx[1] - dp[1]);
+            r[2] = enc.d0[2] + (dx[2] - dp[2]);
+        }
         double w[3] = {v[0] - st[3], v[1] - st[4], v[2] - st[5]};
         mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r, w, a);
     }
@@ -218,14 +277,24 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
 // its error from it (FP32 rounding noise would otherwise dominate b6).
 constexpr double kCloseAu = 0.05;
 
+// detect (step start, off = 0): planets within 2 kCloseAu go to FP64 and are
+// recorded in `close` (held for the step), and the nearest within kEncounterAu
+// in enc; otherwise close and enc are read.
 __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F, double t0,
                                            double off, const double *__restrict__ row64,
-                                           const float *__restrict__ row32, uint32_t close,
+                                           const float *__restrict__ row32, uint32_t &close,
                                            const double x[3], const double v[3], double a[3],
-                                           double as[3])
+                                           double as[3], Encounter &enc, const double dx[3],
+                                           bool detect)
 {
     Seg g;
     as[0] = as[1] = as[2] = 0.0;
+    if (detect) {
+        close = 0;
+        enc.m = -1;
+        enc.t0 = t0;
+    }
+    double best = kEncounterAu * kEncounterAu;
     if (!row64 && !ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
     double sun[6];
     if (row64) {
@@ -258,19 +327,6 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
     for (int m = 1; m < E.n_bodies; m++) {
         if (!((F.active_mask >> m) & 1u)) continue;
         const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
-        if ((close >> m) & 1u) {
-            double st[6];
-            if (row64) {
-#pragma unroll
-                for (int q = 0; q < 6; q++) st[q] = __ldg(row64 + 6 * m + q);
-            } else {
-                cheb_state64(E, m, g.s, g.tau, st);
-            }
-            double r[3] = {x[0] - st[0], x[1] - st[1], x[2] - st[2]};
-            double w[3] = {v[0] - st[3], v[1] - st[4], v[2] - st[5]};
-            mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r, w, as);
-            continue;
-        }
         float st[6];
         if (row32) {
 #pragma unroll
@@ -280,6 +336,42 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
             st[0] -= (float)sun[0]; st[1] -= (float)sun[1]; st[2] -= (float)sun[2];
         }
         float r[3] = {df[0] - st[0], df[1] - st[1], df[2] - st[2]};
+        if (detect && r[0] * r[0] + r[1] * r[1] + r[2] * r[2] < (float)(4.0 * kCloseAu * kCloseAu))
+            close |= 1u << m;
+        if ((close >> m) & 1u) {
+            double st[6];
+            if (row64) {
+#pragma unroll
+                for (int q = 0; q < 6; q++) st[q] = __ldg(row64 + 6 * m + q);
+            } else {
+                cheb_state64(E, m, g.s, g.tau, st);
+            }
+            double s64[6];
+            if (row64) {
+#pragma unroll
+                for (int q = 0; q < 6; q++) s64[q] = __ldg(row64 + 6 * m + q);
+            } else {
+                cheb_state64(E, m, g.s, g.tau, s64);
+            }
+            double r64[3] = {x[0] - s64[0], x[1] - s64[1], x[2] - s64[2]};
+            if (detect) {
+                const double rr = r64[0] * r64[0] + r64[1] * r64[1] + r64[2] * r64[2];
+                if (rr < best) {
+                    best = rr;
+                    enc.m = m;
+                    enc.d0[0] = r64[0]; enc.d0[1] = r64[1]; enc.d0[2] = r64[2];
+                }
+            } else if (m == enc.m) {
+                double dp[3];
+                cheb_delta64(E, m, enc.t0, off, dp);
+                r64[0] = enc.d0[0] + (dx[0] - dp[0]);
+                r64[1] = enc.d0[1] + (dx[1] - dp[1]);
+                r64[2] = enc.d0[2] + (dx[2] - dp[2]);
+            }
+            double w[3] = {v[0] - s64[3], v[1] - s64[4], v[2] - s64[5]};
+            mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r64, w, as);
+            continue;
+        }
         float w[3] = {vf[0] - st[3], vf[1] - st[4], vf[2] - st[5]};
         float P[3] = {(float)F.pole[m][0], (float)F.pole[m][1], (float)F.pole[m][2]};
         mass_terms<float>((float)E.gm[m], (float)F.j2k[m], P, true, gr, j2, r, w, af);
@@ -288,29 +380,6 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
     a[1] = as[1] + (double)af[1];
     a[2] = as[2] + (double)af[2];
     return KETE_BODY_OK;
-}
-
-// planets within kCloseAu of x (bit m set), from FP64 positions
-__device__ __forceinline__ uint32_t close_planets(const EphemDev &E, const ForceDev &F, double t0,
-                                                  const double *__restrict__ row64,
-                                                  const double x[3])
-{
-    uint32_t close = 0;
-    Seg g;
-    if (!row64 && !ephem_seg(E, t0, 0.0, g)) return 0;
-    for (int m = 1; m < E.n_bodies; m++) {
-        if (!((F.active_mask >> m) & 1u)) continue;
-        double st[6];
-        if (row64) {
-            st[0] = __ldg(row64 + 6 * m); st[1] = __ldg(row64 + 6 * m + 1); st[2] = __ldg(row64 + 6 * m + 2);
-        } else {
-            cheb_state64(E, m, g.s, g.tau, st);
-        }
-        double r0 = x[0] - st[0], r1 = x[1] - st[1], r2 = x[2] - st[2];
-        // 2x margin: the set is held for the whole step
-        if (r0 * r0 + r1 * r1 + r2 * r2 < 4.0 * kCloseAu * kCloseAu) close |= 1u << m;
-    }
-    return close;
 }
 
 // ---------------------------------------------------------------------------

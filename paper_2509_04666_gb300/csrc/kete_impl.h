@@ -67,10 +67,21 @@ cudaError_t launch_chain_init(ChainState cs, const double *states, const double 
 cudaError_t launch_node_table(const EphemDev &E, const double *stops_dev, int n_stops,
                               const double *epoch0, double *t0, double *h, double *row64,
                               float *row32, cudaStream_t st);
+// how the propagation kernel is launched (chosen by the autotuner)
+enum PropKind { PROP_STATIC = 0, PROP_WORK_STEALING = 1 };
+struct PropVariant {
+    int kind;    // PropKind
+    int block;   // threads per block (<= 128)
+};
 cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
                              const double *stops_dev, int n_stops, double *out,
                              int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
-                             cudaStream_t st, const NodeTable *nt = nullptr, int leg0 = 0);
+                             cudaStream_t st, const NodeTable *nt = nullptr, int leg0 = 0,
+                             PropVariant var = PropVariant{PROP_STATIC, 128},
+                             unsigned long long *next_body = nullptr);
+int propagate_ws_blocks(int block, int mode);
+cudaError_t launch_gather_bodies(const double *st, const double *ep, int64_t n, int64_t stride,
+                                 int64_t m, double *dst, double *dep, cudaStream_t s);
 cudaError_t launch_chain_finish(ChainState cs, double *states, double *epochs,
                                 int32_t *status, cudaStream_t st);
 // kete_noalloc.cu: propagation with the chain scratch in a fixed device array

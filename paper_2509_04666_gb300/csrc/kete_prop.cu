@@ -1,7 +1,7 @@
 // kete_prop.cu -- n-body propagation of massless bodies (Sec. 3.2, App. A, App. A.6).
 //
-// One thread integrates one body along its chain of stops (the body's epoch,
-// then every stop in order).  Each step is a 15th-order Gauss-Radau step in the
+// Each lane integrates one body at a time along its chain of stops (the
+// body's epoch, then every stop in order).  Each step is a 15th-order Gauss-Radau step in the
 // IAS15 form (Newton-basis coefficients g, power-basis coefficients b, 8
 // spacings), with the predictor removed: every step starts from b = 0 and the
 // corrector iterates until max|db6|/max|a| < eps_pc, the error stops falling
@@ -76,15 +76,17 @@ struct LegRows {
 };
 
 // Force evaluation dispatch by precision mode.
+// detect: the evaluation at a step start, which also finds the planets near
+// the body (see accel_fp64 / accel_mixed).
 template <int MODE>
 __device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, double t0, double off,
-                                     const double *row64, const float *row32, uint32_t close,
+                                     const double *row64, const float *row32, uint32_t &close,
                                      const double x[3], const double v[3], double a[3],
-                                     double as[3])
+                                     double as[3], Encounter &enc, const double dx[3], bool detect)
 {
     if (MODE == KETE_MIXED)
-        return accel_mixed(E, F, t0, off, row64, row32, close, x, v, a, as);
-    int st = accel_fp64(E, F, t0, off, row64, x, v, a);
+        return accel_mixed(E, F, t0, off, row64, row32, close, x, v, a, as, enc, dx, detect);
+    int st = accel_fp64(E, F, t0, off, row64, x, v, a, enc, dx, detect);
     as[0] = a[0]; as[1] = a[1]; as[2] = a[2];
     return st;
 }
@@ -96,8 +98,9 @@ template <int MODE>
 __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &F, double t,
                                              const double x0[3], const double v0[3],
                                              const double a0[3], const double as0[3],
-                                             uint32_t close, double h, LegRows rows,
-                                             double x1[3], double v1[3], double &err, Cnt &cnt)
+                                             uint32_t close, Encounter enc, double h,
+                                             LegRows rows, double x1[3], double v1[3],
+                                             double &err, Cnt &cnt)
 {
     double b[7][3], g[7][3];
 #pragma unroll
@@ -117,7 +120,7 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
         for (int n = 1; n <= 7; n++) {
             const double s = g_rt.h[n];
             const double sh = s * h;
-            double xn[3], vn[3];
+            double xn[3], vn[3], dxn[3];
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 // x(s) = x0 + s h v0 + (s h)^2 [a0/2 + s(b0/6 + s(b1/12 + ... + s b6/72))]
@@ -129,7 +132,8 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
                 px = fma(px, s, b[1][i] * (1.0 / 12.0));
                 px = fma(px, s, b[0][i] * (1.0 / 6.0));
                 px = fma(px, s, a0[i] * 0.5);
-                xn[i] = fma(sh * sh, px, fma(sh, v0[i], x0[i]));
+                dxn[i] = fma(sh * sh, px, sh * v0[i]);   // displacement since the step start
+                xn[i] = x0[i] + dxn[i];
                 // v(s) = v0 + s h [a0 + s(b0/2 + s(b1/3 + ... + s b6/8))]
                 double pv = b[6][i] * 0.125;
                 pv = fma(pv, s, b[5][i] * (1.0 / 7.0));
@@ -144,7 +148,7 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
             double Fn[3], Fs[3];
             const double *r64 = rows.r64 ? rows.r64 + n * rows.stride64 : nullptr;
             const float *r32 = rows.r32 ? rows.r32 + n * rows.stride64 : nullptr;
-            int st = accel<MODE>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs);
+            int st = accel<MODE>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs, enc, dxn, false);
             cnt.evals++;
             if (r64) cnt.node_evals++;
             if (st != KETE_BODY_OK) return st;
@@ -183,12 +187,20 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
     err = bmax / amax;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        double px = a0[i] * 0.5 + b[0][i] * (1.0 / 6.0) + b[1][i] * (1.0 / 12.0) +
-                    b[2][i] * (1.0 / 20.0) + b[3][i] * (1.0 / 30.0) + b[4][i] * (1.0 / 42.0) +
-                    b[5][i] * (1.0 / 56.0) + b[6][i] * (1.0 / 72.0);
-        double pv = a0[i] + b[0][i] * 0.5 + b[1][i] * (1.0 / 3.0) + b[2][i] * 0.25 +
-                    b[3][i] * 0.2 + b[4][i] * (1.0 / 6.0) + b[5][i] * (1.0 / 7.0) +
-                    b[6][i] * 0.125;
+        double px = fma(b[6][i], 1.0 / 72.0, b[5][i] * (1.0 / 56.0));
+        px = fma(b[4][i], 1.0 / 42.0, px);
+        px = fma(b[3][i], 1.0 / 30.0, px);
+        px = fma(b[2][i], 1.0 / 20.0, px);
+        px = fma(b[1][i], 1.0 / 12.0, px);
+        px = fma(b[0][i], 1.0 / 6.0, px);
+        px = fma(a0[i], 0.5, px);
+        double pv = fma(b[6][i], 0.125, b[5][i] * (1.0 / 7.0));
+        pv = fma(b[4][i], 1.0 / 6.0, pv);
+        pv = fma(b[3][i], 0.2, pv);
+        pv = fma(b[2][i], 0.25, pv);
+        pv = fma(b[1][i], 1.0 / 3.0, pv);
+        pv = fma(b[0][i], 0.5, pv);
+        pv = pv + a0[i];
         x1[i] = fma(h * h, px, fma(h, v0[i], x0[i]));
         v1[i] = fma(h, pv, v0[i]);
     }
@@ -198,77 +210,112 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
     return KETE_BODY_OK;
 }
 
-// Integrate (x, v, t) to `target` exactly; dt is the carried step proposal.
-// nt (may be null) gives the node rows of leg kg of the chain.
-template <int MODE>
-__device__ int integrate_to(const EphemDev &E, const ForceDev &F, const NodeTable *nt, int kg,
-                            double x[3], double v[3], double &t, double &dt, double target,
-                            Cnt &cnt)
+// Per-body integrator state between step attempts.
+struct StepState {
+    double a0[3], as0[3];   // acceleration at the step start (and its FP64 part)
+    uint32_t close;         // planets near the body at the step start (mixed precision)
+    Encounter enc;          // nearest planet within kEncounterAu (close-encounter path)
+    double t_stop;          // end of the step's range: the target, or the next table
+                            // segment boundary during an encounter
+    bool have_a0;           // a0 valid for (x, v, t): kept across a rejection
+};
+
+// Node-table view of leg kg (null pointers: no rows).
+struct LegView {
+    double t0, h;
+    const double *r64;
+    const float *r32;
+    int stride;
+};
+
+__device__ __forceinline__ LegView leg_view(const NodeTable *nt, int kg)
 {
-    if (t == target) return KETE_BODY_OK;
-    const double dir = (target >= t) ? 1.0 : -1.0;
-    if (dt == 0.0 || ((dt > 0.0) != (dir > 0.0))) dt = dir * fabs(dt == 0.0 ? F.dt_init : dt);
-    long long attempts = 0;
-    double leg_t0 = 0.0, leg_h = __longlong_as_double(0x7ff8000000000000ll);
-    const double *leg64 = nullptr;
-    const float *leg32 = nullptr;
-    const int stride = nt ? nt->nb * 6 : 0;
+    LegView L;
+    L.t0 = 0.0;
+    L.h = __longlong_as_double(0x7ff8000000000000ll);
+    L.r64 = nullptr;
+    L.r32 = nullptr;
+    L.stride = 0;
     if (nt) {
-        leg_t0 = __ldg(nt->t0 + kg);
-        leg_h = __ldg(nt->h + kg);
-        leg64 = nt->row64 + (size_t)kg * 8 * stride;
-        leg32 = nt->row32 + (size_t)kg * 8 * stride;
+        L.stride = nt->nb * 6;
+        L.t0 = __ldg(nt->t0 + kg);
+        L.h = __ldg(nt->h + kg);
+        L.r64 = nt->row64 + (size_t)kg * 8 * L.stride;
+        L.r32 = nt->row32 + (size_t)kg * 8 * L.stride;
     }
-    while (t != target) {
-        // rows of node 0 serve a0 whenever the step starts at the leg start
-        const bool at_start = nt && (t == leg_t0) && isfinite(leg_h);
-        double a0[3], as0[3];
-        uint32_t close = 0;
-        if (MODE == KETE_MIXED) close = close_planets(E, F, t, at_start ? leg64 : nullptr, x);
-        int st = accel<MODE>(E, F, t, 0.0, at_start ? leg64 : nullptr,
-                             at_start ? leg32 : nullptr, close, x, v, a0, as0);
+    return L;
+}
+
+// One step attempt of (x, v, t) toward `target` (t != target).  Accepted: the
+// state advances and dt holds the next proposal.  Rejected: dt shrinks and a0
+// is kept.  Returns a KETE_BODY_* status.
+template <int MODE>
+__device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, const LegView &L,
+                                         double x[3], double v[3], double &t, double &dt,
+                                         double target, StepState &S, Cnt &cnt)
+{
+    // rows of node 0 serve a0 whenever the step starts at the leg start
+    const bool at_start = L.r64 && (t == L.t0) && isfinite(L.h);
+    if (!S.have_a0) {
+        const double zero[3] = {0.0, 0.0, 0.0};
+        int st = accel<MODE>(E, F, t, 0.0, at_start ? L.r64 : nullptr, at_start ? L.r32 : nullptr,
+                             S.close, x, v, S.a0, S.as0, S.enc, zero, true);
         cnt.evals++;
         if (at_start) cnt.node_evals++;
         if (st != KETE_BODY_OK) return st;
-        for (;;) {
-            if (++attempts > F.max_steps) return KETE_BODY_STEP_CAP;
-            const double remaining = target - t;
-            const bool clamped = fabs(dt) >= fabs(remaining);
-            // the step is the exact difference of the representable epochs it joins
-            const double t_new = clamped ? target : t + dt;
-            const double h = t_new - t;
-            if (h == 0.0) return KETE_BODY_STEP_CAP;   // step below the epoch resolution
-            LegRows rows = {nullptr, nullptr, stride};
-            if (at_start && h == leg_h) {
-                rows.r64 = leg64;
-                rows.r32 = leg32;
-            }
-            double x1[3], v1[3], err;
-            st = radau_attempt<MODE>(E, F, t, x, v, a0, as0, close, h, rows, x1, v1, err, cnt);
-            if (st != KETE_BODY_OK) return st;
-            double dt_new;
-            if (isfinite(err) && err >= 2.2250738585072014e-308)
-                dt_new = pow(F.eps / err, 1.0 / 7.0) * h;
-            else
-                dt_new = h / F.safety;
-            if (fabs(dt_new / h) < F.safety) {
-                dt = dt_new;
-                cnt.rejected++;
-                continue;
-            }
-            if (fabs(dt_new / h) > 1.0 / F.safety) dt_new = h / F.safety;
-            dt = dt_new;
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                x[i] = x1[i];
-                v[i] = v1[i];
-            }
-            t = t_new;
-            cnt.steps++;
-            break;
+        // during an encounter no step straddles a boundary of the planet polynomials
+        S.t_stop = target;
+        if (S.enc.m >= 0) {
+            const double k = floor((t - E.t_start) * E.inv_seg);
+            double b = (target > t) ? E.t_start + (k + 1.0) * E.seg_len : E.t_start + k * E.seg_len;
+            if (target < t && b == t) b = E.t_start + (k - 1.0) * E.seg_len;
+            if ((target > t && b < target) || (target < t && b > target)) S.t_stop = b;
         }
+        S.have_a0 = true;
     }
+    const double remaining = S.t_stop - t;
+    const bool clamped = fabs(dt) >= fabs(remaining);
+    // the step is the exact difference of the representable epochs it joins
+    const double t_new = clamped ? S.t_stop : t + dt;
+    const double h = t_new - t;
+    if (h == 0.0) return KETE_BODY_STEP_CAP;   // step below the epoch resolution
+    LegRows rows = {nullptr, nullptr, L.stride};
+    if (at_start && h == L.h) {
+        rows.r64 = L.r64;
+        rows.r32 = L.r32;
+    }
+    double x1[3], v1[3], err;
+    int st = radau_attempt<MODE>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, h, rows, x1, v1,
+                                 err, cnt);
+    if (st != KETE_BODY_OK) return st;
+    double dt_new;
+    if (isfinite(err) && err >= 2.2250738585072014e-308)
+        dt_new = pow(F.eps / err, 1.0 / 7.0) * h;
+    else
+        dt_new = h / F.safety;
+    if (fabs(dt_new / h) < F.safety) {   // reject: retry from the same a0
+        dt = dt_new;
+        cnt.rejected++;
+        return KETE_BODY_OK;
+    }
+    if (fabs(dt_new / h) > 1.0 / F.safety) dt_new = h / F.safety;
+    dt = dt_new;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        x[i] = x1[i];
+        v[i] = v1[i];
+    }
+    t = t_new;
+    S.have_a0 = false;
+    cnt.steps++;
     return KETE_BODY_OK;
+}
+
+// orient the carried step toward the next stop (|dt| kept; dt_init to start)
+__device__ __forceinline__ void aim_step(const ForceDev &F, double t, double target, double &dt)
+{
+    const double dir = (target >= t) ? 1.0 : -1.0;
+    if (dt == 0.0 || ((dt > 0.0) != (dir > 0.0))) dt = dir * fabs(dt == 0.0 ? F.dt_init : dt);
 }
 
 __device__ __forceinline__ void flush_counters(const Cnt &c, DevCounters *ctr)
@@ -291,36 +338,87 @@ __device__ __forceinline__ void flush_counters(const Cnt &c, DevCounters *ctr)
     }
 }
 
-// One thread per body: advance its chain through stops[0..n_stops) and write
-// the state at each stop to out[k][c][i] (stride out_stride between rows).
-// Stop k of this launch is leg leg0 + k of the node table (if any).
 #ifndef KETE_PROP_MIN_BLOCKS
 #define KETE_PROP_MIN_BLOCKS 1   // resident blocks per SM asked of the register allocator
 #endif
 
+// The propagation kernel.  Each lane owns one body at a time and advances it
+// one step attempt per loop iteration along its chain of stops, writing the
+// state at every stop to out[k][c][i] (stride out_stride between rows) and the
+// chain state back when it is done.  Stop k of this launch is leg leg0 + k of
+// the node table (if any).
+//   refill = 0 (static): lane j of the grid takes body j and then idles;
+//   refill = 1 (work stealing, persistent grid): a lane whose body is done
+//   takes the next one from an atomic counter (warp-aggregated), so a body
+//   needing hundreds of steps no longer idles the other 31 lanes of its warp.
+// Both schedules run the same instructions per body: results are identical.
 template <int MODE>
-__global__ void __launch_bounds__(128, KETE_PROP_MIN_BLOCKS) k_propagate(EphemDev E, ForceDev F, ChainState cs,
-                                                   const double *__restrict__ stops, int n_stops,
-                                                   double *__restrict__ out, int64_t out_stride,
-                                                   int keep_on_fail, DevCounters *ctr,
-                                                   NodeTable nt, int use_nt, int leg0)
+__global__ void __launch_bounds__(128, KETE_PROP_MIN_BLOCKS)
+k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ stops,
+            int n_stops, double *__restrict__ out, int64_t out_stride, int keep_on_fail,
+            DevCounters *ctr, NodeTable nt, int use_nt, int leg0,
+            unsigned long long *__restrict__ next_body, int refill)
 {
     const int64_t n = cs.n;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     Cnt cnt = {0, 0, 0, 0, 0};
-    if (i < n) {
-        double x[3], v[3];
+    int64_t i = -1;           // current body (-1: none; n: no work left)
+    int k = 0;                // next stop of the body
+    double x[3], v[3], t = 0.0, dt = 0.0;
+    int status = KETE_BODY_OK;
+    long long attempts = 0;
+    StepState S;
+    S.have_a0 = false;
+    LegView L = leg_view(nullptr, 0);
+    bool first = true;
+    for (;;) {
+        // lanes without a body take the next ones
+        const bool need = (i < 0);
+        const unsigned m = __ballot_sync(FULL, need);
+        if (m) {
+            unsigned long long base = 0;
+            const int leader = __ffs(m) - 1;
+            if (refill) {
+                if (lane == leader) base = atomicAdd(next_body, (unsigned long long)__popc(m));
+                base = __shfl_sync(FULL, base, leader);
+            }
+            if (need) {
+                unsigned long long mine = base + __popc(m & ((1u << lane) - 1u));
+                if (!refill)   // static: one body per lane, taken on the first pass
+                    mine = first ? (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x
+                                 : (unsigned long long)n;
+                if (mine < (unsigned long long)n) {
+                    i = (int64_t)mine;
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            x[c] = cs.w[c * n + i];
-            v[c] = cs.w[(3 + c) * n + i];
+                    for (int c = 0; c < 3; c++) {
+                        x[c] = cs.w[c * n + i];
+                        v[c] = cs.w[(3 + c) * n + i];
+                    }
+                    t = cs.w[6 * n + i];
+                    dt = cs.w[7 * n + i];
+                    status = cs.status[i];
+                    k = 0;
+                    attempts = 0;
+                    S.have_a0 = false;
+                    L = leg_view(use_nt ? &nt : nullptr, leg0);
+                    if (status == KETE_BODY_OK && n_stops > 0) aim_step(F, t, stops[0], dt);
+                } else {
+                    i = n;   // drained
+                }
+            }
         }
-        double t = cs.w[6 * n + i], dt = cs.w[7 * n + i];
-        int status = cs.status[i];
-        for (int k = 0; k < n_stops; k++) {
-            if (status == KETE_BODY_OK)
-                status = integrate_to<MODE>(E, F, use_nt ? &nt : nullptr, leg0 + k, x, v, t, dt,
-                                            stops[k], cnt);
+        first = false;
+        const bool active = (i >= 0 && i < n);
+        if (!__any_sync(FULL, active)) break;
+        if (!active) continue;
+        if (k < n_stops && status == KETE_BODY_OK && t != stops[k]) {
+            if (++attempts > F.max_steps) status = KETE_BODY_STEP_CAP;
+            else status = step_once<MODE>(E, F, L, x, v, t, dt, stops[k], S, cnt);
+            if (status == KETE_BODY_OK && t != stops[k]) continue;
+        }
+        // the body is at stop k (or failed): record it and move on
+        while (k < n_stops && (status != KETE_BODY_OK || t == stops[k])) {
             double *o = out + (int64_t)k * 6 * out_stride;
             if (status == KETE_BODY_OK) {
 #pragma unroll
@@ -332,7 +430,16 @@ __global__ void __launch_bounds__(128, KETE_PROP_MIN_BLOCKS) k_propagate(EphemDe
 #pragma unroll
                 for (int c = 0; c < 6; c++) o[c * out_stride + i] = __longlong_as_double(0x7ff8000000000000ll);
             }
+            k++;
+            attempts = 0;
+            S.have_a0 = false;
+            if (k < n_stops) {
+                L = leg_view(use_nt ? &nt : nullptr, leg0 + k);
+                if (status == KETE_BODY_OK) aim_step(F, t, stops[k], dt);
+            }
         }
+        if (k < n_stops) continue;
+        // all stops done: write the chain state back and free the lane
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             cs.w[c * n + i] = x[c];
@@ -341,6 +448,7 @@ __global__ void __launch_bounds__(128, KETE_PROP_MIN_BLOCKS) k_propagate(EphemDe
         cs.w[6 * n + i] = t;
         cs.w[7 * n + i] = dt;
         cs.status[i] = status;
+        i = -1;
     }
     flush_counters(cnt, ctr);
 }
@@ -435,6 +543,18 @@ __global__ void k_ephem_eval(EphemDev E, const double *__restrict__ t, int64_t n
     }
 }
 
+// strided sample of bodies: dst[c][j] = src[c][j * stride] (autotuner)
+__global__ void k_gather_bodies(const double *__restrict__ st, const double *__restrict__ ep,
+                                int64_t n, int64_t stride, int64_t m, double *__restrict__ dst,
+                                double *__restrict__ dep)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int64_t i = j * stride;
+    for (int c = 0; c < 6; c++) dst[c * m + j] = st[c * n + i];
+    dep[j] = ep[i];
+}
+
 static unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
 cudaError_t launch_ephem_eval(const EphemDev &E, const double *t, int64_t n, int body,
@@ -460,22 +580,49 @@ cudaError_t launch_node_table(const EphemDev &E, const double *stops_dev, int n_
     return cudaGetLastError();
 }
 
+int propagate_ws_blocks(int block, int mode)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (mode == KETE_MIXED)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<KETE_MIXED>, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<KETE_FP64>, block, 0);
+    return (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+}
+
 cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
                              const double *stops_dev, int n_stops, double *out,
                              int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
-                             cudaStream_t st, const NodeTable *nt, int leg0)
+                             cudaStream_t st, const NodeTable *nt, int leg0, PropVariant var,
+                             unsigned long long *next_body)
 {
-    if (cs.n > 0 && n_stops > 0) {
-        NodeTable t{};
-        if (nt) t = *nt;
-        unsigned grid = grid_for(cs.n, 128);
-        if (F.precision == KETE_MIXED)
-            k_propagate<KETE_MIXED><<<grid, 128, 0, st>>>(E, F, cs, stops_dev, n_stops, out, out_stride,
-                                                          keep_on_fail ? 1 : 0, ctr, t, nt ? 1 : 0, leg0);
-        else
-            k_propagate<KETE_FP64><<<grid, 128, 0, st>>>(E, F, cs, stops_dev, n_stops, out, out_stride,
-                                                         keep_on_fail ? 1 : 0, ctr, t, nt ? 1 : 0, leg0);
+    if (cs.n <= 0 || n_stops <= 0) return cudaGetLastError();
+    NodeTable t{};
+    if (nt) t = *nt;
+    const int kof = keep_on_fail ? 1 : 0, unt = nt ? 1 : 0;
+    const int block = (var.block > 0 && var.block <= 128) ? var.block : 128;
+    int refill = 0;
+    int64_t grid = (cs.n + block - 1) / block;
+    if (var.kind == PROP_WORK_STEALING && next_body) {
+        cudaError_t e = cudaMemsetAsync(next_body, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        refill = 1;
+        int64_t persistent = propagate_ws_blocks(block, F.precision);
+        if (grid > persistent) grid = persistent;
     }
+    if (F.precision == KETE_MIXED)
+        k_propagate<KETE_MIXED><<<(unsigned)grid, block, 0, st>>>(E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, next_body, refill);
+    else
+        k_propagate<KETE_FP64><<<(unsigned)grid, block, 0, st>>>(E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, next_body, refill);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_bodies(const double *st, const double *ep, int64_t n, int64_t stride,
+                                 int64_t m, double *dst, double *dep, cudaStream_t s)
+{
+    if (m > 0) k_gather_bodies<<<grid_for(m, 256), 256, 0, s>>>(st, ep, n, stride, m, dst, dep);
     return cudaGetLastError();
 }
 

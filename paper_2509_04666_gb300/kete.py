@@ -19,12 +19,13 @@ LIB_PATH = os.path.join(HERE, "libkete_gpu.so")
 OK, ERR_BAD_ARG, ERR_EPHEM_SPAN, ERR_CAPACITY, ERR_NO_EPHEM, ERR_CUDA, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 BODY_OK, BODY_STEP_CAP, BODY_OUT_OF_SPAN, BODY_NONFINITE, BODY_KEPLER_CAP = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
+PROP_STATIC, PROP_WORK_STEALING = 0, 1
 NOALLOC_MAX_BODIES = 65536
 
 EXPORTS = ["kete_create", "kete_destroy", "kete_set_stream", "kete_last_error",
            "kete_force_model_default", "kete_survey_opts_default", "kete_load_ephem",
            "kete_ephem_eval", "kete_propagate", "kete_propagate_stops", "kete_fov_check",
-           "kete_get_stats", "kete_propagate_noalloc"]
+           "kete_get_stats", "kete_propagate_noalloc", "kete_set_propagation", "kete_autotune"]
 
 
 class KeteError(RuntimeError):
@@ -53,7 +54,8 @@ class Stats(C.Structure):
                 ("iterations", C.c_int64), ("n_batches", C.c_int64), ("n_exposures", C.c_int64),
                 ("n_candidates", C.c_int64), ("n_hits", C.c_int64), ("prop_launches", C.c_int64),
                 ("launches", C.c_int64), ("prep_ms", C.c_double), ("cand_ms", C.c_double),
-                ("exact_ms", C.c_double), ("order_ms", C.c_double), ("node_evals", C.c_int64)]
+                ("exact_ms", C.c_double), ("order_ms", C.c_double), ("node_evals", C.c_int64),
+                ("prop_kind", C.c_int64), ("prop_block", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +91,10 @@ def lib():
                                      C.POINTER(SurveyOpts), vp, i64, C.POINTER(i64), vp]
         L.kete_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.kete_propagate_noalloc.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(ForceModel), vp]
+        L.kete_set_propagation.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.kete_autotune.argtypes = [vp, vp, vp, i64, C.POINTER(C.c_double), i64,
+                                    C.POINTER(ForceModel), i64, C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -254,6 +260,22 @@ class Kete:
             self._check(rc)
             break
         return hits, nh.value, status
+
+    def set_propagation(self, precision: int, kind: int, block: int = 128):
+        self._check(lib().kete_set_propagation(self._h, precision, kind, block))
+
+    def autotune(self, states, epochs, stops, fm=None, max_sample=32768):
+        """Time the propagation launch variants on a body sample; keep the fastest."""
+        n = epochs.numel()
+        _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
+        st = np.ascontiguousarray(stops, dtype=np.float64)
+        fm = fm or force_model()
+        kind = C.c_int32(); block = C.c_int32()
+        self._sync_stream()
+        self._check(lib().kete_autotune(self._h, states.data_ptr(), epochs.data_ptr(), n,
+                                        st.ctypes.data_as(C.POINTER(C.c_double)), len(st),
+                                        C.byref(fm), max_sample, C.byref(kind), C.byref(block)))
+        return kind.value, block.value
 
     def get_stats(self) -> dict:
         s = Stats()

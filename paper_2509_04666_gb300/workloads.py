@@ -22,9 +22,10 @@ ZTF / WISE runs of Sec. 2, whose metadata and MPC orbits are not available:
                   90 deg solar-elongation great circle (WISE-like).
 * ``ztf1y``    -- same bodies, 150,000 night-time exposures of 8x8 sub-fields of
                   0.87 deg from a rotating ground site (ZTF-like).
-* ``adjoint90``-- 100,000 bodies, 90 days, 20 observations per body.
+* ``adjoint90``-- 100,000 bodies, 90 days, 20 observations per body, noise
+                  draws and state offsets for the orbit-fit gradient.
 * ``ragged1y`` -- 500,000 mixed population (main belt, NEOs with forced Earth
-                  encounters, Trojans, comets), 365 days.
+                  encounters (label 4), Trojans, comets), 365 days.
 """
 from __future__ import annotations
 
@@ -570,6 +571,118 @@ def ztf1y(n_bodies=757_000, n_exposures=150_000, seed=None, days=365, neo_frac=0
     eph = build_ephemeris(ps, T0 - 64.0, T0 + days + 80.0)
     return Workload("ztf1y", seed, eph, states, np.full(n_bodies, T0), frames, obs,
                     T0 + days, labels, centre, h)
+
+
+def state_to_elements(r, v, mu):
+    """Heliocentric state (3, n) -> elliptic elements (a, e, i, node, peri, M)."""
+    r = np.asarray(r, float); v = np.asarray(v, float)
+    rn = np.linalg.norm(r, axis=0)
+    h = np.cross(r.T, v.T).T
+    hn = np.linalg.norm(h, axis=0)
+    inc = np.arccos(np.clip(h[2] / hn, -1, 1))
+    node = np.arctan2(h[0], -h[1])
+    ev = (np.cross(v.T, h.T).T / mu) - r / rn
+    e = np.linalg.norm(ev, axis=0)
+    a = 1.0 / (2.0 / rn - (v * v).sum(0) / mu)
+    # argument of perihelion and true anomaly in the orbital plane
+    nvec = np.stack([np.cos(node), np.sin(node), np.zeros_like(node)])
+    w_dir = np.cross(h.T, nvec.T).T / hn
+    peri = np.arctan2((ev * w_dir).sum(0), (ev * nvec).sum(0))
+    nu = np.arctan2((r * np.cross(h.T, ev.T).T / hn).sum(0), (r * ev).sum(0))
+    E = 2.0 * np.arctan2(np.sqrt(1 - e) * np.sin(nu / 2), np.sqrt(1 + e) * np.cos(nu / 2))
+    M = E - e * np.sin(E)
+    return a, e, inc, node, peri, M
+
+
+def ragged1y(n_bodies=500_000, seed=None, days=365.0):
+    """Mixed population with very uneven step counts (see module doc):
+    60 % main belt, 20 % NEOs of which 5 % pass 0.001-0.01 AU from the Earth,
+    10 % Jupiter Trojans, 10 % comets (e ~ U[0.7, 0.99], q ~ U[0.5, 3] AU).
+
+    An encounter is placed at t_enc ~ U(30, 335) d at the chosen miss distance
+    from the generator's Earth with a 5-20 km/s relative velocity, and carried
+    back to T0 along the heliocentric conic through that state (a construction
+    aid: planetary perturbations move the actual closest approach a little)."""
+    seed = SEED_BASE + 4 if seed is None else seed
+    ps = make_planets(seed)
+    n_neo = n_bodies // 5
+    n_troj = n_bodies // 10
+    n_com = n_bodies // 10
+    n_mb = n_bodies - n_neo - n_troj - n_com
+    states, labels = population(seed, ps, n_mb, n_neo, n_troj, n_com)
+    n_force = n_neo // 20
+    rng = _rng(seed, 5)
+    t_enc = rng.uniform(30.0, 335.0, n_force)
+    miss = rng.uniform(0.001, 0.01, n_force)
+    vrel = rng.uniform(5.0, 20.0, n_force) * 86400.0 / AU_KM
+    st_enc = integrate_planets(ps, t_enc + T0)
+    sun_p, sun_v = st_enc[:, 0, :3], st_enc[:, 0, 3:]
+    ear_p, ear_v = st_enc[:, 3, :3], st_enc[:, 3, 3:]
+    forced = np.zeros((6, n_force))
+    todo = np.arange(n_force)
+    while todo.size:
+        d = rng.normal(size=(todo.size, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+        u = rng.normal(size=(todo.size, 3))
+        u -= (u * d).sum(1, keepdims=True) * d
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        r = ear_p[todo] + miss[todo, None] * d - sun_p[todo]
+        v = ear_v[todo] + vrel[todo, None] * u - sun_v[todo]
+        with np.errstate(invalid="ignore"):
+            a, e, inc, node, peri, M = state_to_elements(r.T, v.T, GM_SUN)
+        ok = (e < 0.95) & (a > 0) & (a * (1 - e) > 0.2)
+        idx = todo[ok]
+        n_mean = np.sqrt(GM_SUN / a[ok] ** 3)
+        r0, v0 = elements_to_state(a[ok], e[ok], inc[ok], node[ok], peri[ok],
+                                   M[ok] - n_mean * t_enc[idx], GM_SUN)
+        forced[:3, idx] = r0 + ps.pos0[0][:, None]
+        forced[3:, idx] = v0 + ps.vel0[0][:, None]
+        todo = todo[~ok]
+    first_neo = n_mb
+    states[:, first_neo:first_neo + n_force] = forced
+    labels = labels.copy()
+    labels[first_neo:first_neo + n_force] = 4
+    eph = build_ephemeris(ps, T0 - 64.0, T0 + days + 80.0)
+    w = Workload("ragged1y", seed, eph, states, np.full(n_bodies, T0),
+                 np.zeros(0, FRAME_DTYPE), np.zeros((0, 3)), T0 + days, labels)
+    w.meta["t_enc"] = t_enc
+    w.meta["miss"] = miss
+    return w
+
+
+OBS_DTYPE = np.dtype([("epoch", "<f8"), ("ra", "<f8"), ("dec", "<f8"), ("obs", "<f8", (3,))])
+assert OBS_DTYPE.itemsize == 48
+
+
+def adjoint90(n_bodies=100_000, n_obs=20, days=90.0, seed=None, neo_frac=0.02):
+    """Orbit-fit inputs: bodies drawn as in wise1y, n_obs observation epochs per
+    body ~ U[T0, T0 + days] (sorted) seen from the circular 1-AU observer of
+    wise1y, N(0, 0.1 arcsec) noise draws for each (RA cos Dec, Dec), and
+    Gaussian offsets (1e-6 AU, 1e-8 AU/day per component) giving the states at
+    which the gradient is evaluated.  The observed RA/Dec are left at zero: a
+    forward model fills them (truth prediction + noise)."""
+    seed = SEED_BASE + 3 if seed is None else seed
+    ps = make_planets(seed)
+    n_neo = int(round(neo_frac * n_bodies))
+    states, labels = population(seed, ps, n_bodies - n_neo, n_neo)
+    rng = _rng(seed, 6)
+    ep = np.sort(rng.uniform(T0, T0 + days, (n_bodies, n_obs)), axis=1)
+    # observer: Sun + unit circle in the ecliptic (Sun interpolated from hourly samples)
+    t_s = T0 + np.arange(0, days * 24 + 25) / 24.0
+    sun = integrate_planets(ps, t_s)[:, 0, :3]
+    flat = ep.ravel()
+    sun_at = np.stack([np.interp(flat, t_s, sun[:, c]) for c in range(3)], -1)
+    theta = 0.3 + GAUSS_K * (flat - T0)
+    obs_pos = sun_at + np.stack([np.cos(theta), np.sin(theta), np.zeros_like(theta)], -1)
+    obs = np.zeros((n_bodies, n_obs), OBS_DTYPE)
+    obs["epoch"] = ep
+    obs["obs"] = obs_pos.reshape(n_bodies, n_obs, 3)
+    noise = rng.normal(0.0, math.radians(0.1 / 3600.0), (n_bodies, n_obs, 2))
+    off = np.concatenate([rng.normal(0, 1e-6, (3, n_bodies)), rng.normal(0, 1e-8, (3, n_bodies))])
+    eph = build_ephemeris(ps, T0 - 64.0, T0 + days + 80.0)
+    w = Workload("adjoint90", seed, eph, states, np.full(n_bodies, T0), np.zeros(0, FRAME_DTYPE),
+                 np.zeros((0, 3)), T0 + days, labels)
+    w.meta.update(obs=obs, noise=noise, offsets=off)
+    return w
 
 
 def propagation_only(name, n_bodies, days, seed_offset, n_neo=0, n_trojan=0, n_comet=0,

@@ -1,0 +1,94 @@
+"""Pins of the oracle's orbit-fit gradient: the state-transition matrix from
+the variational equations (symplectic for conservative forces; equal to
+finite differences of the pinned two-body solution) and the gradient of the
+loss (equal to central finite differences of the loss)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_04666_gb300 import workloads as W
+
+OMEGA = np.block([[np.zeros((3, 3)), np.eye(3)], [-np.eye(3), np.zeros((3, 3))]])
+
+
+def test_stm_is_symplectic_without_gr(mb1k):
+    orc = O.Oracle(mb1k.ephem.to_bytes())
+    fm = orc.force_model(gr_mask=0)
+    for i in (3, 400, 777):
+        rc, st, phi, t, dt, _ = orc.propagate_stm(fm, mb1k.states[:, i], W.T0, W.T0 + 30.0)
+        assert rc == 0
+        assert np.abs(phi.T @ OMEGA @ phi - OMEGA).max() < 1e-7 * np.abs(phi).max() ** 2
+        assert abs(np.linalg.det(phi) - 1.0) < 1e-7
+
+
+def test_stm_matches_finite_differences_of_kepler():
+    """Sun only: Phi equals central differences of the universal-variable
+    two-body solution (pinned against the anomaly solution)."""
+    orc = O.Oracle(W.static_sun_table(W.T0 - 10, W.T0 + 120).to_bytes())
+    fm = orc.force_model(body_mask=1, gr_mask=0, j2_mask=0)
+    r0, v0 = W.elements_to_state(np.array([1.4]), np.array([0.4]), 0.3, 1.0, 2.0, 0.7, W.GM_SUN)
+    y0 = np.concatenate([r0[:, 0], v0[:, 0]])
+    rc, st, phi, *_ = orc.propagate_stm(fm, y0, W.T0, W.T0 + 100.0)
+    assert rc == 0
+    fd = np.zeros((6, 6))
+    for c in range(6):
+        h = 1e-6 if c < 3 else 1e-8
+        yp, ym = y0.copy(), y0.copy()
+        yp[c] += h; ym[c] -= h
+        _, rp, vp = O.kepler(W.GM_SUN, yp[:3], yp[3:], 100.0)
+        _, rm, vm = O.kepler(W.GM_SUN, ym[:3], ym[3:], 100.0)
+        fd[:, c] = (np.concatenate([rp, vp]) - np.concatenate([rm, vm])) / (2 * h)
+    assert np.abs(phi - fd).max() < 1e-6 * np.abs(fd).max()
+
+
+@pytest.fixture(scope="module")
+def adj_small():
+    from conftest import cached_workload
+    return cached_workload("adjoint90", n_bodies=40, n_obs=20)
+
+
+def _observations(orc, fm, w, i, truth_offset=True):
+    """Observed RA/Dec = oracle prediction from the truth state + the noise draws."""
+    obs = w.meta["obs"][i].copy()
+    rc, loss, pred, _ = orc.body_loss(fm, w.states[:, i], W.T0, obs, grad=False)
+    assert rc == 0
+    obs["ra"] = pred[:, 0] + w.meta["noise"][i, :, 0] / np.cos(pred[:, 1])
+    obs["dec"] = pred[:, 1] + w.meta["noise"][i, :, 1]
+    return obs
+
+
+def test_loss_vanishes_on_its_own_predictions(adj_small):
+    w = adj_small
+    orc = O.Oracle(w.ephem.to_bytes())
+    fm = orc.force_model()
+    obs = w.meta["obs"][0].copy()
+    _, _, pred, _ = orc.body_loss(fm, w.states[:, 0], W.T0, obs, grad=False)
+    obs["ra"], obs["dec"] = pred[:, 0], pred[:, 1]
+    rc, loss, _, g = orc.body_loss(fm, w.states[:, 0], W.T0, obs)
+    assert rc == 0 and loss == 0.0
+    assert np.abs(g).max() == 0.0
+
+
+@pytest.mark.parametrize("i", [0, 7, 19, 33])
+def test_variational_gradient_matches_finite_differences(adj_small, i):
+    w = adj_small
+    orc = O.Oracle(w.ephem.to_bytes())
+    fm = orc.force_model()
+    obs = _observations(orc, fm, w, i)
+    y = w.states[:, i] + w.meta["offsets"][:, i]
+    rc, loss, _, g = orc.body_loss(fm, y, W.T0, obs)
+    assert rc == 0 and loss > 0
+    for hx, hv in ((1e-7, 1e-9), (1e-8, 1e-10)):
+        fd = np.zeros(6)
+        for c in range(6):
+            h = hx if c < 3 else hv
+            yp, ym = y.copy(), y.copy()
+            yp[c] += h; ym[c] -= h
+            _, lp, _, _ = orc.body_loss(fm, yp, W.T0, obs, grad=False)
+            _, lm, _, _ = orc.body_loss(fm, ym, W.T0, obs, grad=False)
+            fd[c] = (lp - lm) / (2 * h)
+        scale = np.abs(g[:3]).max(), np.abs(g[3:]).max()
+        assert np.abs(g[:3] - fd[:3]).max() < 1e-6 * scale[0], (g, fd)
+        assert np.abs(g[3:] - fd[3:]).max() < 1e-6 * scale[1], (g, fd)
