@@ -1291,10 +1291,15 @@ int ko_body_loss(const ko_ephem *e, const ko_force_model *fm, const double st0[6
                 L += res[0] * res[0] + res[1] * res[1];
                 if (pred) { pred[2 * j] = ra; pred[2 * j + 1] = dec; }
                 if (!grad_var) continue;
-                /* d res / d y(t_ref) by central differences */
+                /* d res / d y(t_ref) by central differences, step 1e-7 in
+                 * position (AU) and velocity (AU/day): |t_obs - t_ref| is at
+                 * most a few days, so the velocity step moves the apparent
+                 * position by < 1e-6 AU (truncation < 1e-12 relative) while
+                 * the rounding of an RA difference (~1e-15 rad) stays below
+                 * 1e-8 of the partial */
                 double dr[2][6];
                 for (int c = 0; c < 6; c++) {
-                    double h = (c < 3) ? 1e-7 : 1e-9;
+                    double h = 1e-7;
                     double yp[6], ym[6], rp[2], rm[2];
                     memcpy(yp, y, sizeof(yp));
                     memcpy(ym, y, sizeof(ym));

@@ -92,3 +92,29 @@ def test_variational_gradient_matches_finite_differences(adj_small, i):
         scale = np.abs(g[:3]).max(), np.abs(g[3:]).max()
         assert np.abs(g[:3] - fd[:3]).max() < 1e-6 * scale[0], (g, fd)
         assert np.abs(g[3:] - fd[3:]).max() < 1e-6 * scale[1], (g, fd)
+
+
+@pytest.mark.parametrize("i,k", [(13, 1), (5, 2), (21, 1)])
+def test_gradient_of_few_observations_matches_finite_differences(adj_small, i, k):
+    """Rows of one or two observations soon after the initial epoch, where the
+    velocity part of the gradient rests on the observation partials alone."""
+    w = adj_small
+    orc = O.Oracle(w.ephem.to_bytes())
+    fm = orc.force_model()
+    obs = _observations(orc, fm, w, i)[:k]
+    y = w.states[:, i] + w.meta["offsets"][:, i]
+    rc, loss, _, g = orc.body_loss(fm, y, W.T0, obs)
+    assert rc == 0 and loss > 0
+    def cd(c, h):
+        yp, ym = y.copy(), y.copy()
+        yp[c] += h; ym[c] -= h
+        return (orc.body_loss(fm, yp, W.T0, obs, grad=False)[1]
+                - orc.body_loss(fm, ym, W.T0, obs, grad=False)[1]) / (2 * h)
+    # Richardson-extrapolated central differences (error O(h^4)), steps large
+    # enough that the rounding of the loss stays below 1e-9 of the gradient
+    fd = np.zeros(6)
+    for c in range(6):
+        h = 1e-6 if c < 3 else 1e-7
+        fd[c] = (4.0 * cd(c, h / 2) - cd(c, h)) / 3.0
+    assert np.abs(g[:3] - fd[:3]).max() < 1e-7 * np.abs(g[:3]).max(), (g, fd)
+    assert np.abs(g[3:] - fd[3:]).max() < 1e-7 * np.abs(g[3:]).max(), (g, fd)
