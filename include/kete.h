@@ -242,6 +242,45 @@ int kete_autotune(kete_ctx *ctx, const double *states, const double *epochs, int
                   const double *stops, int64_t n_stops, const kete_force_model *fm,
                   int64_t max_sample, int32_t *kind, int32_t *block);
 
+/* One astrometric observation of one body (48 bytes). */
+typedef struct kete_obs {
+    double epoch;                /* TDB JD; NaN marks an unused slot (at the end of a row) */
+    double ra, dec;              /* observed, rad, equatorial J2000 */
+    double obs[3];               /* observer position, AU, barycentric ecliptic */
+} kete_obs;
+
+#define KETE_ADJ_MAX_OBS 32      /* observations per body (m) */
+#define KETE_ADJ_MAX_STEPS 256   /* integrator steps per body kept for the backward pass */
+#define KETE_BODY_ADJ_CAP 5      /* status: more steps than KETE_ADJ_MAX_STEPS (no gradient) */
+
+/* Orbit-fit loss and its gradient by the adjoint of the propagation and sky
+ * projection (differentiation of the path of Sec. 2 / App. A).
+ * Forward model of body i: its observations obs[i][0..m) (device, [n][m],
+ * sorted by epoch) are batched by the <= batch_span rule (opt, Sec. 2); the
+ * n-body chain visits the batch midpoints and the checkpoint grid
+ * epochs[i] + ckpt_days * k (k >= 1, before the last midpoint); two-body +
+ * light time + RA/Dec give each observation's prediction.
+ *   loss[i] = sum_j (wrap(RA_j - RA_obs_j) cos Dec_obs_j)^2 + (Dec_j - Dec_obs_j)^2
+ * (device, [n]); grad (device, [6][n], may be NULL) = d loss[i] / d(x0, v0)
+ * from the adjoint equations integrated backward over every stored forward
+ * step (Newtonian Jacobians; the GR and J2 contributions to da/dx, below
+ * 1e-8 relative, and da/dv are omitted), plus the partials of the two-body,
+ * light-time and RA/Dec map by forward-mode differentiation; pred (device,
+ * [n][m][2], may be NULL) = predicted RA, Dec.  FP64 only (fm->precision is
+ * ignored).  status (device, [n], may be NULL).
+ * ckpt_days: 0 (no grid) or >= 1e-3; a body whose grid would exceed 65536
+ * checkpoints gets KETE_BODY_STEP_CAP.  A body with more than
+ * KETE_ADJ_MAX_STEPS steps keeps its loss and predictions, gets
+ * KETE_BODY_ADJ_CAP and a NaN gradient; any other failing body gets NaN loss
+ * and gradient and its KETE_BODY_* code.  Scratch: about 100 KB per body,
+ * processed in chunks within opt->mem_budget_gb (0 = 8 GB).
+ * Errors: BAD_ARG (m outside 1..KETE_ADJ_MAX_OBS, unsorted observations, bad
+ * ckpt_days), NO_EPHEM, NOMEM, CUDA. */
+int kete_adjoint(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                 const kete_obs *obs, int32_t m, const kete_force_model *fm,
+                 const kete_survey_opts *opt, double ckpt_days, double *loss, double *grad,
+                 double *pred, int32_t *status);
+
 /* Largest n kete_propagate_noalloc accepts. */
 #define KETE_NOALLOC_MAX_BODIES 65536
 

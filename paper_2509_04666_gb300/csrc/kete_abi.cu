@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "kete_adjoint.h"
 #include "kete_fov.h"
 #include "kete_impl.h"
 
@@ -27,6 +28,7 @@ enum Slot {
     S_CELLSTART, S_CELLCUR, S_CELLEXP, S_CAND, S_EXPCNT, S_EXPOFF, S_EXPCUR, S_CANDBODY,
     S_HITTMP, S_FRAMECNT, S_FRAMEOFF, S_FRAMECUR, S_HITGROUP, S_MAXRAD, S_NT_T0, S_NT_H,
     S_NT_R64, S_NT_R32, S_XSUN, S_XOBSREL, S_NEXTBODY, S_TUNE_ST, S_TUNE_EP, S_TUNE_OUT,
+    S_ADJ_REC, S_ADJ_NREC, S_ADJ_NBAT, S_ADJ_BIDX, S_ADJ_YREF, S_ADJ_GJUMP, S_ADJ_STATUS,
     S_NSLOTS
 };
 
@@ -262,7 +264,8 @@ int kete_create(kete_ctx **out, int device, void *cuda_stream)
         ctx->n_sm = sms;
     std::memset(ctx->h_ctr, 0, sizeof(DevCounters));
     upload_radau_tables(ctx->stream);
-    e = cudaStreamSynchronize(ctx->stream);
+    e = upload_adjoint_tables(ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         kete_destroy(ctx);
         return KETE_ERR_CUDA;
@@ -931,5 +934,88 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
     ctx->var[F.precision == KETE_MIXED ? 1 : 0] = best;
     if (kind) *kind = best.kind;
     if (block) *block = best.block;
+    return KETE_OK;
+}
+
+extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                            const kete_obs *obs, int32_t m, const kete_force_model *fm,
+                            const kete_survey_opts *opt_in, double ckpt_days, double *loss,
+                            double *grad, double *pred, int32_t *status)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
+    if (n < 0 || n > INT32_MAX || m < 1 || m > KETE_ADJ_MAX_OBS ||
+        (n > 0 && (!states || !epochs || !obs || !loss)) ||
+        !(ckpt_days == 0.0 || ckpt_days >= 1e-3) || !std::isfinite(ckpt_days))
+        return fail(ctx, KETE_ERR_BAD_ARG,
+                    "bad arguments (m must lie in 1..%d, ckpt_days 0 or >= 1e-3)", KETE_ADJ_MAX_OBS);
+    kete_survey_opts opt;
+    if (opt_in) opt = *opt_in;
+    else kete_survey_opts_default(&opt);
+    if (!(opt.batch_span > 0) || !(opt.twobody_max >= 0) || !(opt.mem_budget_gb >= 0))
+        return fail(ctx, KETE_ERR_BAD_ARG, "invalid survey options");
+    kete_force_model fm64;
+    if (fm) fm64 = *fm;
+    else kete_force_model_default(&fm64);
+    fm64.precision = KETE_FP64;
+    ForceDev F;
+    int r = make_force(ctx, &fm64, F);
+    if (r != KETE_OK) return r;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    stats_begin(ctx);
+    if (n > 0) {
+        const double eps_obl = 84381.448 / 3600.0 * 3.14159265358979323846 / 180.0;
+        AdjProblem P;
+        P.states = states;
+        P.epochs = epochs;
+        P.n = n;
+        P.obs = obs;
+        P.m = m;
+        P.span = std::min(opt.batch_span, 2.0 * opt.twobody_max);
+        P.ckpt = ckpt_days;
+        P.cos_eps = std::cos(eps_obl);
+        P.sin_eps = std::sin(eps_obl);
+        P.loss = loss;
+        P.grad = grad;
+        P.pred = pred;
+        P.status = status;
+        P.ctr = ctx->d_ctr;
+        // scratch per chunk of bodies within the memory budget
+        const int cap = KETE_ADJ_MAX_STEPS;
+        const size_t per_body = (size_t)cap * kAdjRec * sizeof(double) +
+                                (size_t)m * (sizeof(int32_t) + 12 * sizeof(double)) +
+                                3 * sizeof(int32_t);
+        const double budget = (opt.mem_budget_gb > 0 ? opt.mem_budget_gb : 8.0) * 1073741824.0;
+        int64_t chunk = (int64_t)(budget / (double)per_body);
+        chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, n));
+        AdjBuffers B;
+        B.cap = cap;
+        GET(S_ADJ_REC, (size_t)chunk * cap * kAdjRec, B.rec);
+        GET(S_ADJ_NREC, chunk, B.n_rec);
+        GET(S_ADJ_NBAT, chunk, B.nbat);
+        GET(S_ADJ_BIDX, (size_t)chunk * m, B.bidx);
+        GET(S_ADJ_YREF, (size_t)chunk * m * 6, B.yref);
+        GET(S_ADJ_GJUMP, (size_t)chunk * m * 6, B.gjump);
+        GET(S_ADJ_STATUS, chunk, B.status);
+        int launches = 0;
+        for (int64_t i0 = 0; i0 < n; i0 += chunk) {
+            const int64_t nc = std::min(chunk, n - i0);
+            prop_event(ctx, true);
+            CUDA_TRY(launch_adjoint_forward(ctx->E, F, B, P, i0, nc, ctx->stream));
+            prop_event(ctx, false);
+            CUDA_TRY(launch_adjoint_observe(ctx->E, B, P, i0, nc, ctx->stream));
+            launches += 2;
+            if (grad) {
+                CUDA_TRY(launch_adjoint_backward(B, P, i0, nc, ctx->stream));
+                launches++;
+            }
+        }
+        ctx->stats.launches = launches;
+    }
+    r = stats_end(ctx);
+    if (r != KETE_OK) return r;
+    stats_collect(ctx);
+    if (ctx->h_ctr->error_flags & (1 << 6))
+        return fail(ctx, KETE_ERR_BAD_ARG, "observations of a body are not sorted by epoch");
     return KETE_OK;
 }

@@ -1,0 +1,683 @@
+// kete_adjoint.cu -- orbit-fit loss and its gradient with respect to each
+// body's initial state by the adjoint method (differentiation of the path of
+// Sec. 2: n-body propagation of App. A, two-body + light time, RA/Dec).
+//
+// Three kernels per chunk of bodies:
+//   k_adj_forward   one lane per body.  The body's observations are batched
+//                   by the <= span rule (Sec. 2); the chain visits the batch
+//                   midpoints and the checkpoint grid in ascending order with
+//                   the same Gauss-Radau steps as the propagation kernel.
+//                   Every accepted step leaves a record in device memory: its
+//                   start and end epochs and the Newtonian da/dx at its 8
+//                   Gauss-Radau nodes, taken from the force evaluations the
+//                   step already makes.  The state at each batch midpoint is
+//                   kept for the sky projection.
+//   k_adj_observe   one warp per body, one lane per observation: prediction,
+//                   residual, loss term and dL/dy(t_ref) through RA/Dec, the
+//                   light-time fixed point (implicit derivative) and the
+//                   universal-variable two-body map (forward-mode dual numbers
+//                   at the converged universal anomaly).
+//   k_adj_backward  one lane per body: mu = lambda_v obeys mu'' = J(t) mu
+//                   (lambda_x = -mu'), integrated backward over every recorded
+//                   step by collocation on the step's 9 sample epochs (its 8
+//                   nodes and its end); dL/dy(t_ref) is added at each batch
+//                   midpoint.  dL/dx0 = -mu'(t0), dL/dv0 = mu(t0).
+// The backward pass evaluates no force and reads no ephemeris: every Jacobian
+// it needs was recorded by the forward pass.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "kete_adjoint.h"
+#include "kete_step.cuh"
+
+namespace kete {
+
+// ---------------------------------------------------------------------------
+// backward collocation weights
+// ---------------------------------------------------------------------------
+// Sample points of one step in the backward variable s = (t_end - t) / h:
+// sig[0] = 0 (the step end), sig[n] = 1 - h_{8-n} (forward node 8-n),
+// sig[8] = 1 (the step start).  With F(s) interpolated through the 9 points,
+//   mu(sig_n)  = mu_0 + sig_n mu'_0 + sum_k W2[n][k] F_k
+//   mu'(sig_n) = mu'_0 + sum_k W1[n][k] F_k
+// where W1[n][k] = int_0^sig_n l_k(s) ds, W2[n][k] = int_0^sig_n (sig_n - s) l_k(s) ds.
+struct AdjTables {
+    double sig[9];
+    double W1[9][9];
+    double W2[9][9];
+};
+static __constant__ AdjTables g_adj;
+
+static void fill_adj_tables(AdjTables &T)
+{
+    RadauTables rt;
+    fill_radau_tables(rt);
+    long double sg[9];
+    sg[0] = 0.0L;
+    for (int n = 1; n <= 7; n++) sg[n] = 1.0L - (long double)rt.h[8 - n];
+    sg[8] = 1.0L;
+    for (int n = 0; n < 9; n++) T.sig[n] = (double)sg[n];
+    for (int k = 0; k < 9; k++) {
+        // l_k(s) = prod_{j != k} (s - sg_j) / (sg_k - sg_j), power basis
+        long double c[9] = {1.0L, 0, 0, 0, 0, 0, 0, 0, 0};
+        long double den = 1.0L;
+        int deg = 0;
+        for (int j = 0; j < 9; j++) {
+            if (j == k) continue;
+            for (int p = deg + 1; p >= 1; p--) c[p] = c[p - 1] - sg[j] * c[p];
+            c[0] = -sg[j] * c[0];
+            deg++;
+            den *= (sg[k] - sg[j]);
+        }
+        for (int n = 0; n < 9; n++) {
+            long double w1 = 0.0L, w2 = 0.0L, sp = sg[n];
+            for (int p = 0; p <= 8; p++) {
+                w1 += c[p] * sp / (p + 1);
+                w2 += c[p] * sp * sg[n] / ((p + 1) * (p + 2));
+                sp *= sg[n];
+            }
+            T.W1[n][k] = (double)(w1 / den);
+            T.W2[n][k] = (double)(w2 / den);
+        }
+    }
+}
+
+cudaError_t upload_adjoint_tables(cudaStream_t st)
+{
+    cudaError_t e = upload_step_tables(st);
+    if (e != cudaSuccess) return e;
+    static AdjTables T;
+    static bool filled = false;
+    if (!filled) {
+        fill_adj_tables(T);
+        filled = true;
+    }
+    return cudaMemcpyToSymbolAsync(g_adj, &T, sizeof(T), 0, cudaMemcpyHostToDevice, st);
+}
+
+// ---------------------------------------------------------------------------
+// batches of one body's observations (the <= span rule of Sec. 2)
+// ---------------------------------------------------------------------------
+// The batch starting at j0 ends before the returned index; tref = midpoint.
+__device__ __forceinline__ int next_batch(const kete_obs *o, int mi, int j0, double span,
+                                          double &tref)
+{
+    const double e0 = o[j0].epoch;
+    int j = j0;
+    while (j + 1 < mi) {
+        const double e = o[j + 1].epoch;
+        if (!(e == e0 || e - e0 < span)) break;
+        j++;
+    }
+    tref = 0.5 * (e0 + o[j].epoch);
+    return j + 1;
+}
+
+// observations in use: those before the first non-finite epoch
+__device__ __forceinline__ int obs_count(const kete_obs *o, int m)
+{
+    int mi = 0;
+    while (mi < m && isfinite(o[mi].epoch)) mi++;
+    return mi;
+}
+
+// ---------------------------------------------------------------------------
+// forward pass
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    Cnt cnt = {0, 0, 0, 0, 0};
+    if (i < nc) {
+        const int64_t gi = i0 + i;
+        const kete_obs *o = P.obs + gi * P.m;
+        double x[3], v[3];
+        bool fin = true;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            x[c] = P.states[c * P.n + gi];
+            v[c] = P.states[(3 + c) * P.n + gi];
+            fin = fin && isfinite(x[c]) && isfinite(v[c]);
+        }
+        const double epoch0 = P.epochs[gi];
+        double t = epoch0, dt = 0.0;
+        int status = (fin && isfinite(epoch0)) ? KETE_BODY_OK : KETE_BODY_NONFINITE;
+        const int mi = obs_count(o, P.m);
+        for (int j = 1; j < mi; j++)
+            if (o[j].epoch < o[j - 1].epoch) {
+                atomicOr(&P.ctr->error_flags, 1 << 6);
+                status = KETE_BODY_NONFINITE;
+            }
+        // number of batches and the last midpoint (the checkpoint grid ends there)
+        int nb = 0;
+        double t_last = epoch0;
+        for (int j0 = 0; j0 < mi; nb++) j0 = next_batch(o, mi, j0, P.span, t_last);
+        double *rec = B.rec + (size_t)i * B.cap * kAdjRec;
+        int count = 0;          // accepted steps recorded
+        bool capped = false;    // more steps than the record holds
+        StepState S;
+        const LegView L = leg_view(nullptr, 0);
+        int kb = 0, j0 = 0, j1 = 0;
+        double tref = 0.0;
+        if (mi > 0) j1 = next_batch(o, mi, 0, P.span, tref);
+        int kc = 1;
+        double tc = epoch0 + (double)kc * P.ckpt;
+        bool ckpt_ok = P.ckpt > 0.0 && tc < t_last;
+        while (status == KETE_BODY_OK && kb < nb) {
+            const bool mid = !(ckpt_ok && tc < tref);
+            const double ts = mid ? tref : tc;
+            aim_step(F, t, ts, dt);
+            S.have_a0 = false;
+            long long attempts = 0;
+            while (t != ts && status == KETE_BODY_OK) {
+                if (++attempts > F.max_steps) {
+                    status = KETE_BODY_STEP_CAP;
+                    break;
+                }
+                const int slot = count < B.cap - 1 ? count : B.cap - 2;
+                double *r = rec + (size_t)slot * kAdjRec;
+                const double t_prev = t;
+                status = step_once<KETE_FP64, true>(E, F, L, x, v, t, dt, ts, S, cnt, r + 2);
+                if (status == KETE_BODY_OK && t != t_prev) {
+                    r[0] = t_prev;
+                    r[1] = t;
+                    if (count < B.cap - 1) count++;
+                    else capped = true;
+                }
+            }
+            if (status != KETE_BODY_OK) break;
+            if (mid) {
+                double *y = B.yref + ((size_t)i * P.m + kb) * 6;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    y[c] = x[c];
+                    y[3 + c] = v[c];
+                }
+                B.bidx[(size_t)i * P.m + kb] = count;
+                if (ckpt_ok && tc == tref) {   // a checkpoint on the midpoint: one stop
+                    kc++;
+                    tc = epoch0 + (double)kc * P.ckpt;
+                    ckpt_ok = tc < t_last;
+                }
+                kb++;
+                j0 = j1;
+                if (kb < nb) j1 = next_batch(o, mi, j0, P.span, tref);
+            } else {
+                if (++kc > kAdjMaxCkpt) {   // bounded work per body
+                    status = KETE_BODY_STEP_CAP;
+                    break;
+                }
+                tc = epoch0 + (double)kc * P.ckpt;
+                ckpt_ok = tc < t_last;
+            }
+        }
+        if (status == KETE_BODY_OK && !capped) {
+            // terminal record: da/dx at the final state closes the last step
+            double *r = rec + (size_t)count * kAdjRec;
+            double a[3];
+            Encounter enc;
+            const double zero[3] = {0.0, 0.0, 0.0};
+            double J[6];
+            status = accel_fp64<true>(E, F, t, 0.0, nullptr, x, v, a, enc, zero, true, J);
+            cnt.evals++;
+            r[0] = t;
+            r[1] = t;
+#pragma unroll
+            for (int q = 0; q < 6; q++) r[2 + q] = J[q];
+            count++;
+        }
+        if (status == KETE_BODY_OK && capped) status = KETE_BODY_ADJ_CAP;
+        B.n_rec[i] = (status == KETE_BODY_OK) ? count : 0;
+        B.nbat[i] = nb;
+        B.status[i] = status;
+    }
+    flush_counters(cnt, P.ctr);
+}
+
+// ---------------------------------------------------------------------------
+// observation operator and its partials
+// ---------------------------------------------------------------------------
+// forward-mode dual number with 6 tangents (d/d r0, d/d v0)
+struct D6 {
+    double v, d[6];
+};
+__device__ __forceinline__ D6 dconst(double a)
+{
+    D6 r;
+    r.v = a;
+#pragma unroll
+    for (int q = 0; q < 6; q++) r.d[q] = 0.0;
+    return r;
+}
+__device__ __forceinline__ D6 operator+(const D6 &a, const D6 &b)
+{
+    D6 r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int q = 0; q < 6; q++) r.d[q] = a.d[q] + b.d[q];
+    return r;
+}
+__device__ __forceinline__ D6 operator-(const D6 &a, const D6 &b)
+{
+    D6 r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int q = 0; q < 6; q++) r.d[q] = a.d[q] - b.d[q];
+    return r;
+}
+__device__ __forceinline__ D6 operator*(const D6 &a, const D6 &b)
+{
+    D6 r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int q = 0; q < 6; q++) r.d[q] = fma(a.d[q], b.v, a.v * b.d[q]);
+    return r;
+}
+__device__ __forceinline__ D6 operator*(double s, const D6 &a)
+{
+    D6 r;
+    r.v = s * a.v;
+#pragma unroll
+    for (int q = 0; q < 6; q++) r.d[q] = s * a.d[q];
+    return r;
+}
+__device__ __forceinline__ D6 operator+(double s, const D6 &a)
+{
+    D6 r = a;
+    r.v = s + a.v;
+    return r;
+}
+__device__ __forceinline__ D6 dinv(const D6 &a)
+{
+    D6 r;
+    r.v = 1.0 / a.v;
+    const double k = -r.v * r.v;
+#pragma unroll
+    for (int q = 0; q < 6; q++) r.d[q] = k * a.d[q];
+    return r;
+}
+__device__ __forceinline__ D6 dsqrt(const D6 &a)
+{
+    D6 r;
+    r.v = sqrt(a.v);
+    const double k = 0.5 / r.v;
+#pragma unroll
+    for (int q = 0; q < 6; q++) r.d[q] = k * a.d[q];
+    return r;
+}
+
+// dC/dz, dS/dz of the Stumpff functions: power series for |z| < 1
+// (sum_k>=1 (-1)^k k z^(k-1) / (2k+2)!, resp. / (2k+3)!), else
+// (1 - zS - 2C) / 2z and (C - 3S) / 2z.
+__device__ __forceinline__ void stumpff_dz(double z, double C, double S, double &dC, double &dS)
+{
+    if (fabs(z) < 1.0) {
+        double tc = -1.0 / 24.0, ts = -1.0 / 120.0;
+        dC = tc;
+        dS = ts;
+        for (int k = 1; k < 14; k++) {
+            const double kk = (double)k;
+            tc *= -z * (kk + 1.0) / (kk * (2.0 * kk + 3.0) * (2.0 * kk + 4.0));
+            ts *= -z * (kk + 1.0) / (kk * (2.0 * kk + 4.0) * (2.0 * kk + 5.0));
+            dC += tc;
+            dS += ts;
+        }
+    } else {
+        dC = (1.0 - z * S - 2.0 * C) / (2.0 * z);
+        dS = (C - 3.0 * S) / (2.0 * z);
+    }
+}
+
+__device__ __forceinline__ void stumpff_dual(const D6 &z, D6 &C, D6 &S)
+{
+    double c, s, dc, ds;
+    stumpff(z.v, c, s);
+    stumpff_dz(z.v, c, s, dc, ds);
+    C.v = c;
+    S.v = s;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        C.d[q] = dc * z.d[q];
+        S.d[q] = ds * z.d[q];
+    }
+}
+
+// Jr[i][c] = d r_i(dt) / d(r0, v0)_c of the universal-variable solution, at
+// fixed dt, from the converged universal anomaly chi: one Newton step of
+// Kepler's equation in dual numbers starting at chi carries the implicit
+// derivative of chi.
+__device__ void kepler_jacobian(double mu, double sqmu, const double r0[3], const double v0[3],
+                                double dt, double chi, double Jr[3][6])
+{
+    D6 R[3], V[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        R[c] = dconst(r0[c]);
+        R[c].d[c] = 1.0;
+        V[c] = dconst(v0[c]);
+        V[c].d[3 + c] = 1.0;
+    }
+    const D6 rn0 = dsqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+    const D6 vv = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    const D6 rv = R[0] * V[0] + R[1] * V[1] + R[2] * V[2];
+    const D6 alpha = 2.0 * dinv(rn0) - (1.0 / mu) * vv;
+    const D6 A = (1.0 / sqmu) * rv;
+    const D6 B = 1.0 + (-1.0) * (alpha * rn0);
+    // Kepler's equation at fixed chi: F = A chi^2 C + B chi^3 S + rn0 chi - sqmu dt
+    const double x2 = chi * chi;
+    D6 C, S;
+    stumpff_dual(x2 * alpha, C, S);
+    const D6 Fk = (-sqmu * dt) + (x2 * (A * C) + (x2 * chi) * (B * S) + chi * rn0);
+    const double z = x2 * alpha.v;
+    const double dF = A.v * chi * (1.0 - z * S.v) + B.v * x2 * C.v + rn0.v;
+    D6 X = (-1.0 / dF) * Fk;
+    X.v = chi;   // the value stays the converged root; the tangent is -F_p / F_chi
+    const D6 X2 = X * X;
+    D6 C2, S2;
+    stumpff_dual(X2 * alpha, C2, S2);
+    const D6 f = 1.0 + (-1.0) * (X2 * C2 * dinv(rn0));
+    const D6 g = dt + (-1.0 / sqmu) * (X2 * X * S2);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const D6 ri = f * R[i] + g * V[i];
+#pragma unroll
+        for (int c = 0; c < 6; c++) Jr[i][c] = ri.d[c];
+    }
+}
+
+__device__ __forceinline__ bool sun_at(const EphemDev &E, double t0, double off, double p[3],
+                                       double v[3])
+{
+    Seg g;
+    if (!ephem_seg(E, t0, off, g)) return false;
+    cheb_pos_vel(ephem_coef(E, 0, g.s), E.n_coef, g.tau, 2.0 * E.inv_seg, p, v);
+    return true;
+}
+
+__device__ __forceinline__ double wrap_pi(double a)
+{
+    while (a > kPi) a -= kTwoPi;
+    while (a <= -kPi) a += kTwoPi;
+    return a;
+}
+
+// warp per body, lane per observation (m <= 32)
+__global__ void __launch_bounds__(128)
+k_adj_observe(EphemDev E, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
+{
+    __shared__ double sh[4][32][7];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 4 + w;
+    if (i >= nc) return;   // whole warp
+    const int64_t gi = i0 + i;
+    const kete_obs *o = P.obs + gi * P.m;
+    const int mi = obs_count(o, P.m);
+    int st = B.status[i];
+    // this lane's batch
+    int kb = -1, j0 = 0, j1 = 0;
+    double tref = 0.0;
+    {
+        int b = 0, s0 = 0;
+        while (s0 < mi) {
+            double tr;
+            const int s1 = next_batch(o, mi, s0, P.span, tr);
+            if (lane >= s0 && lane < s1) {
+                kb = b;
+                j0 = s0;
+                j1 = s1;
+                tref = tr;
+            }
+            s0 = s1;
+            b++;
+        }
+    }
+    double Lj = 0.0, gj[6] = {0, 0, 0, 0, 0, 0};
+    double ra = __longlong_as_double(0x7ff8000000000000ll), dec = ra;
+    bool bad = false;
+    const bool mine = (lane < mi) && (st == KETE_BODY_OK || st == KETE_BODY_ADJ_CAP);
+    if (mine) {
+        const double *y = B.yref + ((size_t)i * P.m + kb) * 6;
+        const kete_obs ob = o[lane];
+        double sp[3], sv[3], hr[3], hv[3];
+        bool ok = sun_at(E, tref, 0.0, sp, sv);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            hr[c] = y[c] - sp[c];
+            hv[c] = y[3 + c] - sv[c];
+        }
+        const double mu = E.gm[0], sqmu = sqrt(mu);
+        const double dt_obs = ob.epoch - tref;   // intervals before absolute epochs
+        double chi = 0.0, r[3], vh[3], pos[3], su[3], svel[3], tau = 0.0;
+        // position at the epoch t_ref + d: Sun there plus the two-body offset
+        auto at = [&](double d) {
+            bool good = sun_at(E, tref, d, su, svel);
+            good = kepler_uv(mu, sqmu, hr, hv, d, chi, r, vh) && good;
+#pragma unroll
+            for (int c = 0; c < 3; c++) pos[c] = su[c] + r[c];
+            return good;
+        };
+        auto dist = [&]() {
+            const double d0 = pos[0] - ob.obs[0], d1 = pos[1] - ob.obs[1], d2 = pos[2] - ob.obs[2];
+            return sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        };
+        ok = at(dt_obs) && ok;
+        tau = dist() * kInvC;
+        for (int it = 0; it < 3; it++) {
+            ok = at(dt_obs - tau) && ok;
+            tau = dist() * kInvC;
+        }
+        const double dfin = dt_obs - tau;
+        ok = at(dfin) && ok;
+        if (!ok) {
+            bad = true;
+        } else {
+            const double u[3] = {pos[0] - ob.obs[0], pos[1] - ob.obs[1], pos[2] - ob.obs[2]};
+            radec(u, P.cos_eps, P.sin_eps, ra, dec);
+            const double cd = cos(ob.dec);
+            const double r0 = wrap_pi(ra - ob.ra) * cd, r1 = dec - ob.dec;
+            Lj = r0 * r0 + r1 * r1;
+            // dL_j/du: RA/Dec partials in the equatorial frame, rotated back
+            const double X = u[0];
+            const double Y = P.cos_eps * u[1] - P.sin_eps * u[2];
+            const double Z = P.sin_eps * u[1] + P.cos_eps * u[2];
+            const double rxy2 = X * X + Y * Y, rxy = sqrt(rxy2), uu = rxy2 + Z * Z;
+            const double ka = 2.0 * r0 * cd / rxy2;
+            const double kd = 2.0 * r1 / (uu * rxy);
+            const double gX = -ka * Y - kd * X * Z;
+            const double gY = ka * X - kd * Y * Z;
+            const double gZ = kd * rxy2;
+            double wv[3] = {gX, P.cos_eps * gY + P.sin_eps * gZ, -P.sin_eps * gY + P.cos_eps * gZ};
+            // light time: u = P(t_obs - tau) - obs with tau = |u| / c, so
+            // du = P_y dy - Pdot dtau, dtau = rho.P_y dy / (c + rho.Pdot)
+            const double un = sqrt(uu);
+            const double rh[3] = {u[0] / un, u[1] / un, u[2] / un};
+            const double pd[3] = {vh[0] + svel[0], vh[1] + svel[1], vh[2] + svel[2]};
+            const double wp = wv[0] * pd[0] + wv[1] * pd[1] + wv[2] * pd[2];
+            const double den = kC + (rh[0] * pd[0] + rh[1] * pd[1] + rh[2] * pd[2]);
+#pragma unroll
+            for (int c = 0; c < 3; c++) wv[c] -= (wp / den) * rh[c];
+            double Jr[3][6];
+            kepler_jacobian(mu, sqmu, hr, hv, dfin, chi, Jr);
+#pragma unroll
+            for (int c = 0; c < 6; c++) gj[c] = wv[0] * Jr[0][c] + wv[1] * Jr[1][c] + wv[2] * Jr[2][c];
+        }
+        if (P.pred) {
+            P.pred[(gi * P.m + lane) * 2] = ra;
+            P.pred[(gi * P.m + lane) * 2 + 1] = dec;
+        }
+    } else if (P.pred && lane < P.m) {
+        P.pred[(gi * P.m + lane) * 2] = ra;
+        P.pred[(gi * P.m + lane) * 2 + 1] = dec;
+    }
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    sh[w][lane][0] = Lj;
+#pragma unroll
+    for (int c = 0; c < 6; c++) sh[w][lane][1 + c] = gj[c];
+    __syncwarp();
+    // loss in observation order; gradient jumps summed per batch in order
+    if (lane == 0) {
+        double L = 0.0;
+        for (int j = 0; j < mi; j++) L += sh[w][j][0];
+        const bool ok = (st == KETE_BODY_OK || st == KETE_BODY_ADJ_CAP) && !any_bad;
+        if (any_bad && st == KETE_BODY_OK) st = KETE_BODY_KEPLER_CAP;
+        P.loss[gi] = ok ? L : __longlong_as_double(0x7ff8000000000000ll);
+        B.status[i] = st;
+        if (P.status) P.status[gi] = st;
+    }
+    if (mine && lane == j0) {
+        double g[6] = {0, 0, 0, 0, 0, 0};
+        for (int j = j0; j < j1; j++)
+#pragma unroll
+            for (int c = 0; c < 6; c++) g[c] += sh[w][j][1 + c];
+        double *dst = B.gjump + ((size_t)i * P.m + kb) * 6;
+#pragma unroll
+        for (int c = 0; c < 6; c++) dst[c] = g[c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward pass
+// ---------------------------------------------------------------------------
+// sample k of a step in the backward order (see AdjTables): J at sig[k]
+__device__ __forceinline__ const double *jac_sample(const double *r, const double *r_next, int k)
+{
+    if (k == 0) return r_next + 2;            // step end = next record's node 0
+    return r + 2 + 6 * (8 - k);               // forward node 8-k (k = 8: node 0)
+}
+
+__device__ __forceinline__ void jmul(const double *J, const double m[3], double out[3])
+{
+    const double j0 = __ldg(J), j1 = __ldg(J + 1), j2 = __ldg(J + 2), j3 = __ldg(J + 3),
+                 j4 = __ldg(J + 4), j5 = __ldg(J + 5);
+    out[0] = fma(j0, m[0], fma(j1, m[1], j2 * m[2]));
+    out[1] = fma(j1, m[0], fma(j3, m[1], j4 * m[2]));
+    out[2] = fma(j2, m[0], fma(j4, m[1], j5 * m[2]));
+}
+
+__global__ void __launch_bounds__(128)
+k_adj_backward(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const int64_t gi = i0 + i;
+    const int st = B.status[i];
+    if (st != KETE_BODY_OK) {
+        for (int c = 0; c < 6; c++) P.grad[c * P.n + gi] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    const int count = B.n_rec[i];
+    int kb = B.nbat[i] - 1;
+    const double *rec = B.rec + (size_t)i * B.cap * kAdjRec;
+    const int32_t *bidx = B.bidx + (size_t)i * P.m;
+    const double *gjump = B.gjump + (size_t)i * P.m * 6;
+    double mu[3] = {0, 0, 0}, mud[3] = {0, 0, 0};   // lambda_v and d lambda_v / dt
+    for (int s = count - 2; s >= -1; s--) {
+        // jumps of the batches whose midpoint the chain reached after s+1 steps
+        while (kb >= 0 && bidx[kb] == s + 1) {
+            const double *g = gjump + kb * 6;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                mud[c] -= g[c];       // lambda_x += dL/dx
+                mu[c] += g[3 + c];    // lambda_v += dL/dv
+            }
+            kb--;
+        }
+        if (s < 0) break;
+        if (mu[0] == 0.0 && mu[1] == 0.0 && mu[2] == 0.0 && mud[0] == 0.0 && mud[1] == 0.0 &&
+            mud[2] == 0.0)
+            continue;
+        const double *r = rec + (size_t)s * kAdjRec;
+        const double *rn = r + kAdjRec;
+        const double h = __ldg(r + 1) - __ldg(r);
+        const double h2 = h * h;
+        // s-derivative at the step end: d mu / ds = -h d mu / dt
+        const double q0[3] = {-h * mud[0], -h * mud[1], -h * mud[2]};
+        double Fk[9][3], mk[9][3];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) mk[k][c] = fma(g_adj.sig[k], q0[c], mu[c]);
+            jmul(jac_sample(r, rn, k), mk[k], Fk[k]);
+#pragma unroll
+            for (int c = 0; c < 3; c++) Fk[k][c] *= h2;
+        }
+        // Picard iteration of the collocation equations (a linear system with
+        // contraction ~ h^2 |J|); at most 12 sweeps
+        for (int it = 0; it < 12; it++) {
+            double delta = 0.0, size = 0.0;
+#pragma unroll
+            for (int k = 1; k < 9; k++) {
+                double nm[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    double acc = fma(g_adj.sig[k], q0[c], mu[c]);
+#pragma unroll
+                    for (int j = 0; j < 9; j++) acc = fma(g_adj.W2[k][j], Fk[j][c], acc);
+                    nm[c] = acc;
+                }
+                if (k == 8) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        delta = fmax(delta, fabs(nm[c] - mk[8][c]));
+                        size = fmax(size, fabs(nm[c]));
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 3; c++) mk[k][c] = nm[c];
+            }
+#pragma unroll
+            for (int k = 1; k < 9; k++) {
+                jmul(jac_sample(r, rn, k), mk[k], Fk[k]);
+#pragma unroll
+                for (int c = 0; c < 3; c++) Fk[k][c] *= h2;
+            }
+            if (delta <= 1e-16 * size) break;
+        }
+        double q8[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            double acc = q0[c];
+#pragma unroll
+            for (int j = 0; j < 9; j++) acc = fma(g_adj.W1[8][j], Fk[j][c], acc);
+            q8[c] = acc;
+            mu[c] = mk[8][c];
+            mud[c] = -q8[c] / h;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        P.grad[c * P.n + gi] = -mud[c];
+        P.grad[(3 + c) * P.n + gi] = mu[c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+cudaError_t launch_adjoint_forward(const EphemDev &E, const ForceDev &F, const AdjBuffers &B,
+                                   const AdjProblem &P, int64_t i0, int64_t nc, cudaStream_t st)
+{
+    if (nc > 0) k_adj_forward<<<blocks_for(nc, 128), 128, 0, st>>>(E, F, B, P, i0, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_observe(const EphemDev &E, const AdjBuffers &B, const AdjProblem &P,
+                                   int64_t i0, int64_t nc, cudaStream_t st)
+{
+    if (nc > 0) k_adj_observe<<<blocks_for(nc, 4), 128, 0, st>>>(E, B, P, i0, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_backward(const AdjBuffers &B, const AdjProblem &P, int64_t i0,
+                                    int64_t nc, cudaStream_t st)
+{
+    if (nc > 0) k_adj_backward<<<blocks_for(nc, 128), 128, 0, st>>>(B, P, i0, nc);
+    return cudaGetLastError();
+}
+
+}  // namespace kete

@@ -1,0 +1,51 @@
+// kete_adjoint.h -- device buffers and launchers of the adjoint (kete_adjoint.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kete_impl.h"
+
+namespace kete {
+
+// one record per accepted step: t_start, t_end, then the symmetric Newtonian
+// da/dx (xx, xy, xz, yy, yz, zz) at the step's 8 Gauss-Radau nodes; a final
+// record (t_end = t_start) holds da/dx at the last state in node 0's place
+constexpr int kAdjRec = 2 + 8 * 6;
+// checkpoint stops per body before the chain gives up (KETE_BODY_STEP_CAP)
+constexpr int kAdjMaxCkpt = 1 << 16;
+
+// the problem (caller's arrays; states and grad are [6][n], obs [n][m])
+struct AdjProblem {
+    const double *states, *epochs;
+    int64_t n;
+    const kete_obs *obs;
+    int32_t m;
+    double span, ckpt;
+    double cos_eps, sin_eps;
+    double *loss, *grad, *pred;
+    int32_t *status;
+    DevCounters *ctr;
+};
+
+// library scratch for one chunk of nc bodies
+struct AdjBuffers {
+    double *rec;       // [nc][cap][kAdjRec]
+    int32_t cap;       // records per body
+    int32_t *n_rec;    // [nc] records written (0: no gradient)
+    int32_t *nbat;     // [nc] batches
+    int32_t *bidx;     // [nc][m] steps taken when batch k's midpoint was reached
+    double *yref;      // [nc][m][6] state at batch k's midpoint
+    double *gjump;     // [nc][m][6] dL/dy(t_ref) of batch k
+    int32_t *status;   // [nc]
+};
+
+cudaError_t upload_adjoint_tables(cudaStream_t st);
+cudaError_t launch_adjoint_forward(const EphemDev &E, const ForceDev &F, const AdjBuffers &B,
+                                   const AdjProblem &P, int64_t i0, int64_t nc, cudaStream_t st);
+cudaError_t launch_adjoint_observe(const EphemDev &E, const AdjBuffers &B, const AdjProblem &P,
+                                   int64_t i0, int64_t nc, cudaStream_t st);
+cudaError_t launch_adjoint_backward(const AdjBuffers &B, const AdjProblem &P, int64_t i0,
+                                    int64_t nc, cudaStream_t st);
+
+}  // namespace kete

@@ -223,16 +223,41 @@ struct Encounter {
 //   row32[m*6 + 0..2]  position relative to the Sun, [3..5] velocity (FP32)
 // A null row64 means "evaluate the table here" (per-thread path).
 
+// Newtonian part of da/dx for one mass, accumulated into the symmetric J
+// (xx, xy, xz, yy, yz, zz):  -mu/|r|^3 (I - 3 r r^T / |r|^2).
+__device__ __forceinline__ void newton_jacobian(double mu, const double r[3], double J[6])
+{
+    const double rr = fma(r[0], r[0], fma(r[1], r[1], r[2] * r[2]));
+    const double ri = rsqrt(rr);
+    const double ri2 = ri * ri;
+    const double f = -mu * ri2 * ri;
+    const double k = -3.0 * f * ri2;
+    J[0] = fma(k * r[0], r[0], J[0] + f);
+    J[1] = fma(k * r[0], r[1], J[1]);
+    J[2] = fma(k * r[0], r[2], J[2]);
+    J[3] = fma(k * r[1], r[1], J[3] + f);
+    J[4] = fma(k * r[1], r[2], J[4]);
+    J[5] = fma(k * r[2], r[2], J[5] + f);
+}
+
 // Full-FP64 acceleration.
 // detect (step start, off = 0): also record in enc the nearest planet within
 // kEncounterAu and its relative position; otherwise enc is read.
+// JAC: also return in J the Newtonian da/dx (see newton_jacobian), from the
+// same relative vectors as the force.
+template <bool JAC = false>
 __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, double t0,
                                           double off, const double *__restrict__ row64,
                                           const double x[3], const double v[3], double a[3],
-                                          Encounter &enc, const double dx[3], bool detect)
+                                          Encounter &enc, const double dx[3], bool detect,
+                                          double *J = nullptr)
 {
     Seg g;
     a[0] = a[1] = a[2] = 0.0;
+    if (JAC) {
+#pragma unroll
+        for (int q = 0; q < 6; q++) J[q] = 0.0;
+    }
     if (detect) {
         enc.m = -1;
         enc.t0 = t0;
@@ -266,6 +291,7 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
         }
         double w[3] = {v[0] - st[3], v[1] - st[4], v[2] - st[5]};
         mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r, w, a);
+        if (JAC) newton_jacobian(E.gm[m], r, J);
     }
     return KETE_BODY_OK;
 }

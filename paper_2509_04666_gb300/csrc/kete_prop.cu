@@ -14,329 +14,11 @@
 #include <cmath>
 #include <cstring>
 
-#include "kete_device.cuh"
+#include "kete_step.cuh"
 
 namespace kete {
 
-__constant__ RadauTables g_rt;
-
-// Gauss-Radau spacings on [0, 1] (Everhart 1985, 30 published digits)
-static const double kRadauH[8] = {
-    0.0,
-    0.0562625605369221464656521910318,
-    0.180240691736892364987579942780,
-    0.352624717113169637373907769648,
-    0.547153626330555383001448554766,
-    0.734210177215410531523210605558,
-    0.885320946839095768090359771030,
-    0.977520613561287501891174488626,
-};
-
-void upload_radau_tables(cudaStream_t st)
-{
-    RadauTables t;
-    std::memset(&t, 0, sizeof(t));
-    for (int n = 0; n < 8; n++) t.h[n] = kRadauH[n];
-    for (int n = 0; n < 8; n++)
-        for (int k = 0; k < n; k++) t.rinv[n][k] = 1.0 / (kRadauH[n] - kRadauH[k]);
-    // Newton basis N_n(s) = s (s-h_1)...(s-h_{n-1}); c[n][m] = coefficient of
-    // s^(m+1) in N_n, built by the recurrence N_n = N_{n-1} (s - h_{n-1}).
-    double poly[8] = {1, 0, 0, 0, 0, 0, 0, 0};   // coefficients of prod (s-h_i), s^0 first
-    for (int n = 1; n <= 7; n++) {
-        if (n >= 2) {
-            double nxt[8] = {0};
-            for (int p = 0; p < 7; p++) {
-                nxt[p + 1] += poly[p];
-                nxt[p] -= kRadauH[n - 1] * poly[p];
-            }
-            std::memcpy(poly, nxt, sizeof(poly));
-        }
-        for (int m = 0; m < 7; m++) t.c[n][m] = (m < n) ? poly[m] : 0.0;
-    }
-    // leading coefficient of the interpolant through the 8 nodes
-    for (int n = 0; n < 8; n++) {
-        double p = 1.0;
-        for (int k = 0; k < 8; k++)
-            if (k != n) p *= (kRadauH[n] - kRadauH[k]);
-        t.w7[n] = 1.0 / p;
-    }
-    cudaMemcpyToSymbolAsync(g_rt, &t, sizeof(t), 0, cudaMemcpyHostToDevice, st);
-}
-
-struct Cnt {
-    unsigned long long steps, rejected, evals, iters, node_evals;
-};
-
-// Rows of the node table for leg kg, or null when the step (t, h) does not span
-// that whole leg.
-struct LegRows {
-    const double *r64;
-    const float *r32;
-    int stride64;   // doubles per node
-};
-
-// Force evaluation dispatch by precision mode.
-// detect: the evaluation at a step start, which also finds the planets near
-// the body (see accel_fp64 / accel_mixed).
-template <int MODE>
-__device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, double t0, double off,
-                                     const double *row64, const float *row32, uint32_t &close,
-                                     const double x[3], const double v[3], double a[3],
-                                     double as[3], Encounter &enc, const double dx[3], bool detect)
-{
-    if (MODE == KETE_MIXED)
-        return accel_mixed(E, F, t0, off, row64, row32, close, x, v, a, as, enc, dx, detect);
-    int st = accel_fp64(E, F, t0, off, row64, x, v, a, enc, dx, detect);
-    as[0] = a[0]; as[1] = a[1]; as[2] = a[2];
-    return st;
-}
-
-// One Gauss-Radau attempt of size h from (t, x0, v0) with a0 = a(t, x0, v0)
-// (as0: its FP64 part).  rows != null: the step spans the whole leg and the
-// planets come from the node rows (node n at rows.r64 + n * stride).
-template <int MODE>
-__device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &F, double t,
-                                             const double x0[3], const double v0[3],
-                                             const double a0[3], const double as0[3],
-                                             uint32_t close, Encounter enc, double h,
-                                             LegRows rows, double x1[3], double v1[3],
-                                             double &err, Cnt &cnt)
-{
-    double b[7][3], g[7][3];
-#pragma unroll
-    for (int m = 0; m < 7; m++)
-#pragma unroll
-        for (int i = 0; i < 3; i++) b[m][i] = g[m][i] = 0.0;
-    double amax = 0.0, pc_prev = 0.0;
-    double gs7[3] = {0.0, 0.0, 0.0};   // b6 of the FP64 part (mixed precision)
-    for (int it = 1; it <= F.max_iter; it++) {
-        double b6o[3] = {b[6][0], b[6][1], b[6][2]};
-        double F7[3];
-        if (MODE == KETE_MIXED) {
-#pragma unroll
-            for (int i = 0; i < 3; i++) gs7[i] = g_rt.w7[0] * as0[i];
-        }
-#pragma unroll
-        for (int n = 1; n <= 7; n++) {
-            const double s = g_rt.h[n];
-            const double sh = s * h;
-            double xn[3], vn[3], dxn[3];
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                // x(s) = x0 + s h v0 + (s h)^2 [a0/2 + s(b0/6 + s(b1/12 + ... + s b6/72))]
-                double px = b[6][i] * (1.0 / 72.0);
-                px = fma(px, s, b[5][i] * (1.0 / 56.0));
-                px = fma(px, s, b[4][i] * (1.0 / 42.0));
-                px = fma(px, s, b[3][i] * (1.0 / 30.0));
-                px = fma(px, s, b[2][i] * (1.0 / 20.0));
-                px = fma(px, s, b[1][i] * (1.0 / 12.0));
-                px = fma(px, s, b[0][i] * (1.0 / 6.0));
-                px = fma(px, s, a0[i] * 0.5);
-                dxn[i] = fma(sh * sh, px, sh * v0[i]);   // displacement since the step start
-                xn[i] = x0[i] + dxn[i];
-                // v(s) = v0 + s h [a0 + s(b0/2 + s(b1/3 + ... + s b6/8))]
-                double pv = b[6][i] * 0.125;
-                pv = fma(pv, s, b[5][i] * (1.0 / 7.0));
-                pv = fma(pv, s, b[4][i] * (1.0 / 6.0));
-                pv = fma(pv, s, b[3][i] * 0.2);
-                pv = fma(pv, s, b[2][i] * 0.25);
-                pv = fma(pv, s, b[1][i] * (1.0 / 3.0));
-                pv = fma(pv, s, b[0][i] * 0.5);
-                pv = fma(pv, s, a0[i]);
-                vn[i] = fma(sh, pv, v0[i]);
-            }
-            double Fn[3], Fs[3];
-            const double *r64 = rows.r64 ? rows.r64 + n * rows.stride64 : nullptr;
-            const float *r32 = rows.r32 ? rows.r32 + n * rows.stride64 : nullptr;
-            int st = accel<MODE>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs, enc, dxn, false);
-            cnt.evals++;
-            if (r64) cnt.node_evals++;
-            if (st != KETE_BODY_OK) return st;
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                double gn = (Fn[i] - a0[i]) * g_rt.rinv[n][0];
-#pragma unroll
-                for (int k = 1; k < n; k++) gn = (gn - g[k - 1][i]) * g_rt.rinv[n][k];
-                double dg = gn - g[n - 1][i];
-                g[n - 1][i] = gn;
-#pragma unroll
-                for (int m = 0; m < n; m++) b[m][i] = fma(g_rt.c[n][m], dg, b[m][i]);
-                if (n == 7) F7[i] = Fn[i];
-                if (MODE == KETE_MIXED) gs7[i] = fma(g_rt.w7[n], Fs[i], gs7[i]);
-            }
-        }
-        cnt.iters++;
-        double db = 0.0;
-        amax = 0.0;
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            db = fmax(db, fabs(b[6][i] - b6o[i]));
-            amax = fmax(amax, fabs(F7[i]));
-        }
-        double pc = db / amax;
-        if (!isfinite(pc)) return KETE_BODY_NONFINITE;
-        if (pc < F.eps_pc) break;
-        if (it >= 3 && pc >= pc_prev) break;
-        pc_prev = pc;
-    }
-    // step-size error estimate: max|b6| / max|a|; in mixed precision b6 of the
-    // smooth FP64 part (FP32 rounding is not smooth and b6 would amplify it)
-    double bmax = (MODE == KETE_MIXED)
-                      ? fmax(fabs(gs7[0]), fmax(fabs(gs7[1]), fabs(gs7[2])))
-                      : fmax(fabs(b[6][0]), fmax(fabs(b[6][1]), fabs(b[6][2])));
-    err = bmax / amax;
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        double px = fma(b[6][i], 1.0 / 72.0, b[5][i] * (1.0 / 56.0));
-        px = fma(b[4][i], 1.0 / 42.0, px);
-        px = fma(b[3][i], 1.0 / 30.0, px);
-        px = fma(b[2][i], 1.0 / 20.0, px);
-        px = fma(b[1][i], 1.0 / 12.0, px);
-        px = fma(b[0][i], 1.0 / 6.0, px);
-        px = fma(a0[i], 0.5, px);
-        double pv = fma(b[6][i], 0.125, b[5][i] * (1.0 / 7.0));
-        pv = fma(b[4][i], 1.0 / 6.0, pv);
-        pv = fma(b[3][i], 0.2, pv);
-        pv = fma(b[2][i], 0.25, pv);
-        pv = fma(b[1][i], 1.0 / 3.0, pv);
-        pv = fma(b[0][i], 0.5, pv);
-        pv = pv + a0[i];
-        x1[i] = fma(h * h, px, fma(h, v0[i], x0[i]));
-        v1[i] = fma(h, pv, v0[i]);
-    }
-    if (!(isfinite(x1[0]) && isfinite(x1[1]) && isfinite(x1[2]) && isfinite(v1[0]) &&
-          isfinite(v1[1]) && isfinite(v1[2])))
-        return KETE_BODY_NONFINITE;
-    return KETE_BODY_OK;
-}
-
-// Per-body integrator state between step attempts.
-struct StepState {
-    double a0[3], as0[3];   // acceleration at the step start (and its FP64 part)
-    uint32_t close;         // planets near the body at the step start (mixed precision)
-    Encounter enc;          // nearest planet within kEncounterAu (close-encounter path)
-    double t_stop;          // end of the step's range: the target, or the next table
-                            // segment boundary during an encounter
-    bool have_a0;           // a0 valid for (x, v, t): kept across a rejection
-};
-
-// Node-table view of leg kg (null pointers: no rows).
-struct LegView {
-    double t0, h;
-    const double *r64;
-    const float *r32;
-    int stride;
-};
-
-__device__ __forceinline__ LegView leg_view(const NodeTable *nt, int kg)
-{
-    LegView L;
-    L.t0 = 0.0;
-    L.h = __longlong_as_double(0x7ff8000000000000ll);
-    L.r64 = nullptr;
-    L.r32 = nullptr;
-    L.stride = 0;
-    if (nt) {
-        L.stride = nt->nb * 6;
-        L.t0 = __ldg(nt->t0 + kg);
-        L.h = __ldg(nt->h + kg);
-        L.r64 = nt->row64 + (size_t)kg * 8 * L.stride;
-        L.r32 = nt->row32 + (size_t)kg * 8 * L.stride;
-    }
-    return L;
-}
-
-// One step attempt of (x, v, t) toward `target` (t != target).  Accepted: the
-// state advances and dt holds the next proposal.  Rejected: dt shrinks and a0
-// is kept.  Returns a KETE_BODY_* status.
-template <int MODE>
-__device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, const LegView &L,
-                                         double x[3], double v[3], double &t, double &dt,
-                                         double target, StepState &S, Cnt &cnt)
-{
-    // rows of node 0 serve a0 whenever the step starts at the leg start
-    const bool at_start = L.r64 && (t == L.t0) && isfinite(L.h);
-    if (!S.have_a0) {
-        const double zero[3] = {0.0, 0.0, 0.0};
-        int st = accel<MODE>(E, F, t, 0.0, at_start ? L.r64 : nullptr, at_start ? L.r32 : nullptr,
-                             S.close, x, v, S.a0, S.as0, S.enc, zero, true);
-        cnt.evals++;
-        if (at_start) cnt.node_evals++;
-        if (st != KETE_BODY_OK) return st;
-        // during an encounter no step straddles a boundary of the planet polynomials
-        S.t_stop = target;
-        if (S.enc.m >= 0) {
-            const double k = floor((t - E.t_start) * E.inv_seg);
-            double b = (target > t) ? E.t_start + (k + 1.0) * E.seg_len : E.t_start + k * E.seg_len;
-            if (target < t && b == t) b = E.t_start + (k - 1.0) * E.seg_len;
-            if ((target > t && b < target) || (target < t && b > target)) S.t_stop = b;
-        }
-        S.have_a0 = true;
-    }
-    const double remaining = S.t_stop - t;
-    const bool clamped = fabs(dt) >= fabs(remaining);
-    // the step is the exact difference of the representable epochs it joins
-    const double t_new = clamped ? S.t_stop : t + dt;
-    const double h = t_new - t;
-    if (h == 0.0) return KETE_BODY_STEP_CAP;   // step below the epoch resolution
-    LegRows rows = {nullptr, nullptr, L.stride};
-    if (at_start && h == L.h) {
-        rows.r64 = L.r64;
-        rows.r32 = L.r32;
-    }
-    double x1[3], v1[3], err;
-    int st = radau_attempt<MODE>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, h, rows, x1, v1,
-                                 err, cnt);
-    if (st != KETE_BODY_OK) return st;
-    double dt_new;
-    if (isfinite(err) && err >= 2.2250738585072014e-308)
-        dt_new = pow(F.eps / err, 1.0 / 7.0) * h;
-    else
-        dt_new = h / F.safety;
-    if (fabs(dt_new / h) < F.safety) {   // reject: retry from the same a0
-        dt = dt_new;
-        cnt.rejected++;
-        return KETE_BODY_OK;
-    }
-    if (fabs(dt_new / h) > 1.0 / F.safety) dt_new = h / F.safety;
-    dt = dt_new;
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        x[i] = x1[i];
-        v[i] = v1[i];
-    }
-    t = t_new;
-    S.have_a0 = false;
-    cnt.steps++;
-    return KETE_BODY_OK;
-}
-
-// orient the carried step toward the next stop (|dt| kept; dt_init to start)
-__device__ __forceinline__ void aim_step(const ForceDev &F, double t, double target, double &dt)
-{
-    const double dir = (target >= t) ? 1.0 : -1.0;
-    if (dt == 0.0 || ((dt > 0.0) != (dir > 0.0))) dt = dir * fabs(dt == 0.0 ? F.dt_init : dt);
-}
-
-__device__ __forceinline__ void flush_counters(const Cnt &c, DevCounters *ctr)
-{
-    unsigned long long s = c.steps, r = c.rejected, e = c.evals, it = c.iters, ne = c.node_evals;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        r += __shfl_xor_sync(0xffffffffu, r, o);
-        e += __shfl_xor_sync(0xffffffffu, e, o);
-        it += __shfl_xor_sync(0xffffffffu, it, o);
-        ne += __shfl_xor_sync(0xffffffffu, ne, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&ctr->steps, s);
-        atomicAdd(&ctr->rejected, r);
-        atomicAdd(&ctr->force_evals, e);
-        atomicAdd(&ctr->iterations, it);
-        atomicAdd(&ctr->node_evals, ne);
-    }
-}
+void upload_radau_tables(cudaStream_t st) { upload_step_tables(st); }
 
 #ifndef KETE_PROP_MIN_BLOCKS
 #define KETE_PROP_MIN_BLOCKS 1   // resident blocks per SM asked of the register allocator

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libkete_gpu.so")
 
 OK, ERR_BAD_ARG, ERR_EPHEM_SPAN, ERR_CAPACITY, ERR_NO_EPHEM, ERR_CUDA, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 BODY_OK, BODY_STEP_CAP, BODY_OUT_OF_SPAN, BODY_NONFINITE, BODY_KEPLER_CAP = 0, 1, 2, 3, 4
+BODY_ADJ_CAP = 5
+ADJ_MAX_OBS, ADJ_MAX_STEPS = 32, 256
 FP64, MIXED = 0, 1
 PROP_STATIC, PROP_WORK_STEALING = 0, 1
 NOALLOC_MAX_BODIES = 65536
@@ -25,7 +27,8 @@ NOALLOC_MAX_BODIES = 65536
 EXPORTS = ["kete_create", "kete_destroy", "kete_set_stream", "kete_last_error",
            "kete_force_model_default", "kete_survey_opts_default", "kete_load_ephem",
            "kete_ephem_eval", "kete_propagate", "kete_propagate_stops", "kete_fov_check",
-           "kete_get_stats", "kete_propagate_noalloc", "kete_set_propagation", "kete_autotune"]
+           "kete_get_stats", "kete_propagate_noalloc", "kete_set_propagation", "kete_autotune",
+           "kete_adjoint"]
 
 
 class KeteError(RuntimeError):
@@ -95,6 +98,8 @@ def lib():
         L.kete_autotune.argtypes = [vp, vp, vp, i64, C.POINTER(C.c_double), i64,
                                     C.POINTER(ForceModel), i64, C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32)]
+        L.kete_adjoint.argtypes = [vp, vp, vp, i64, vp, C.c_int32, C.POINTER(ForceModel),
+                                   C.POINTER(SurveyOpts), dbl, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -261,6 +266,36 @@ class Kete:
             break
         return hits, nh.value, status
 
+    def adjoint(self, states, epochs, obs, fm=None, opts=None, ckpt_days=8.0, grad=True,
+                pred=False):
+        """Orbit-fit loss per body and, with grad, dL/d(x0, v0) [6, n].
+
+        obs: float64 CUDA tensor [n, m, 6] of kete_obs records (epoch, ra, dec,
+        observer x, y, z), sorted by epoch per body, NaN epochs padding the
+        end of a row.  Returns (loss [n], grad [6, n] or None, pred [n, m, 2]
+        or None, status [n])."""
+        n = epochs.numel()
+        _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
+        if obs.dim() != 3 or obs.shape[0] != n or obs.shape[2] != 6:
+            raise ValueError("obs must have shape [n, m, 6]")
+        m = obs.shape[1]
+        _dev_f64(obs, "obs")
+        dev = states.device
+        loss = torch.empty(n, dtype=torch.float64, device=dev)
+        g = torch.empty((6, n), dtype=torch.float64, device=dev) if grad else None
+        pr = torch.empty((n, m, 2), dtype=torch.float64, device=dev) if pred else None
+        status = torch.zeros(n, dtype=torch.int32, device=dev)
+        fm = fm or force_model()
+        opts = opts or survey_opts()
+        self._sync_stream()
+        self._check(lib().kete_adjoint(self._h, states.data_ptr(), epochs.data_ptr(), n,
+                                       obs.data_ptr(), m, C.byref(fm), C.byref(opts),
+                                       float(ckpt_days), loss.data_ptr(),
+                                       g.data_ptr() if g is not None else None,
+                                       pr.data_ptr() if pr is not None else None,
+                                       status.data_ptr()))
+        return loss, g, pr, status
+
     def set_propagation(self, precision: int, kind: int, block: int = 128):
         self._check(lib().kete_set_propagation(self._h, precision, kind, block))
 
@@ -281,3 +316,27 @@ class Kete:
         s = Stats()
         self._check(lib().kete_get_stats(self._h, C.byref(s)))
         return s.as_dict()
+
+
+class OrbitFitLoss(torch.autograd.Function):
+    """Per-body orbit-fit loss as a differentiable function of the initial
+    states [6, n]; the backward pass returns the adjoint gradient computed by
+    kete_adjoint in the same call as the loss."""
+
+    @staticmethod
+    def forward(ctx, states, engine, epochs, obs, fm=None, opts=None, ckpt_days=8.0):
+        loss, g, _, status = engine.adjoint(states.detach().contiguous(), epochs, obs, fm=fm,
+                                            opts=opts, ckpt_days=ckpt_days, grad=True)
+        ctx.save_for_backward(g)
+        ctx.mark_non_differentiable(status)
+        return loss, status
+
+    @staticmethod
+    def backward(ctx, grad_loss, grad_status):
+        (g,) = ctx.saved_tensors
+        return g * grad_loss.unsqueeze(0), None, None, None, None, None, None
+
+
+def orbit_fit_loss(engine, states, epochs, obs, fm=None, opts=None, ckpt_days=8.0):
+    """Differentiable per-body loss [n] (and status) of initial states [6, n]."""
+    return OrbitFitLoss.apply(states, engine, epochs, obs, fm, opts, ckpt_days)
