@@ -221,6 +221,172 @@ def peak_fma(fp64: bool):
     return v.value if rc == 0 else None
 
 
+def adj_flops(st, fm, n_coef):
+    """Algorithmic FP64 FLOPs of the adjoint's forward kernel: the propagation
+    count of prop_flops with every evaluation per-thread (per-body stops share
+    no node rows) plus the Newtonian da/dx of each mass at every evaluation
+    (26 FLOPs)."""
+    s = dict(st)
+    s["node_evals"] = 0
+    f64, _ = prop_flops(s, fm, n_coef, False)
+    return f64 + st["force_evals"] * _bits(fm.body_mask) * 26
+
+
+def _timed(stream, fn, flush, reps):
+    import torch
+    out, times = None, []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.mean(times), out
+
+
+def adjoint_leg(args, K, dev, flush, stream, peak):
+    """Orbit-fit loss + gradient of 100,000 bodies (20 observations each over
+    90 days, 8-day checkpoints).  Observed RA/Dec for the timed run are the
+    GPU's truth predictions plus N(0, 0.1") noise; the sampled parity check
+    uses observations the oracle makes itself."""
+    import concurrent.futures as cf
+    import torch
+    import oracle as O
+    from paper_2509_04666_gb300 import kete, workloads as W
+    w = W.adjoint90(n_bodies=args.adj_bodies)
+    n, m = w.n_bodies, w.meta["obs"].shape[1]
+    K.load_ephem(w.ephem.to_bytes())
+    fm = kete.force_model()
+    ep = torch.full((n,), W.T0, dtype=torch.float64, device=dev)
+    truth = torch.from_numpy(w.states.copy()).to(dev)
+    y = torch.from_numpy(w.states + w.meta["offsets"]).to(dev)
+    obs = w.meta["obs"].copy()
+    ob = torch.from_numpy(obs.view(np.float64).reshape(n, m, 6).copy()).to(dev)
+    _, _, pred, status = K.adjoint(truth, ep, ob, fm=fm, grad=False, pred=True)
+    pred = pred.cpu().numpy()
+    obs["ra"] = pred[..., 0] + w.meta["noise"][..., 0] / np.cos(pred[..., 1])
+    obs["dec"] = pred[..., 1] + w.meta["noise"][..., 1]
+    ob = torch.from_numpy(obs.view(np.float64).reshape(n, m, 6).copy()).to(dev)
+    opts = kete.survey_opts(mem_budget_gb=24.0)    # one chunk: ~105 KB of step records a body
+    call = lambda: K.adjoint(y, ep, ob, fm=fm, opts=opts, ckpt_days=8.0)
+    call()
+    ms, (loss, g, _, status) = _timed(stream, call, flush, 3)
+    st = K.get_stats()
+    flops = adj_flops(st, fm, w.ephem.n_coef)
+    fwd_tf = flops / (st["prop_ms"] / 1e3) / 1e12
+    ok = int((status == 0).sum().item())
+    # sampled parity: observations and reference gradient from the oracle alone
+    orc = O.Oracle(w.ephem.to_bytes())
+    fmo = orc.force_model()
+    sub = np.linspace(0, n - 1, args.adj_sample).astype(np.int64)
+    y_np = w.states + w.meta["offsets"]
+
+    def one(i):
+        o = w.meta["obs"][i].copy()
+        _, _, p, _ = orc.body_loss(fmo, w.states[:, i], W.T0, o, grad=False)
+        o["ra"] = p[:, 0] + w.meta["noise"][i, :, 0] / np.cos(p[:, 1])
+        o["dec"] = p[:, 1] + w.meta["noise"][i, :, 1]
+        t0 = time.perf_counter()
+        rc, L, _, gi = orc.body_loss(fmo, y_np[:, i], W.T0, o)
+        return o, rc, L, gi, time.perf_counter() - t0
+
+    nt = os.cpu_count()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(nt) as ex:
+        res = list(ex.map(one, sub))
+    wall = time.perf_counter() - t0
+    so = np.stack([r[0] for r in res])
+    loss_r = np.array([r[2] for r in res]); g_r = np.stack([r[3] for r in res], 1)
+    ls, gs, _, ss = K.adjoint(torch.from_numpy(y_np[:, sub].copy()).to(dev),
+                              ep[:len(sub)].contiguous(),
+                              torch.from_numpy(so.view(np.float64).reshape(len(sub), m, 6).copy()).to(dev),
+                              fm=fm, ckpt_days=8.0)
+    ls, gs = ls.cpu().numpy(), gs.cpu().numpy()
+    rel_x = np.abs(gs[:3] - g_r[:3]).max(0) / np.abs(g_r[:3]).max(0)
+    rel_v = np.abs(gs[3:] - g_r[3:]).max(0) / np.abs(g_r[3:]).max(0)
+    cpu_rate = len(sub) * 90.0 / wall
+    return {
+        "workload": f"adjoint90: {n} bodies (2% NEOs), {m} observations each over 90 d from a "
+                    f"1-AU circular observer, 8-day checkpoints, loss + dL/d(x0,v0), FP64",
+        "value": n * 90.0 / (ms / 1e3), "unit": "body-days/s (loss + gradient)",
+        "bodies_per_s": n / (ms / 1e3), "ms_per_step": ms, "forward_ms": st["prop_ms"],
+        "bodies_ok": ok, "steps": st["steps"], "force_evals": st["force_evals"],
+        "roofline": {"bound": "alu", "kernel": "k_adj_forward", "achieved": fwd_tf, "peak": peak,
+                     "unit": "TFLOP/s", "frac": fwd_tf / peak, "traffic": None},
+        "parity": {"sampled_bodies": len(sub), "max_rel_grad_x": float(rel_x.max()),
+                   "max_rel_grad_v": float(rel_v.max()),
+                   "max_rel_loss": float((np.abs(ls - loss_r) / loss_r).max()),
+                   "oracle": "variational equations + central-difference partials"},
+        "cpu_baseline": {"value": cpu_rate, "unit": "body-days/s (loss + gradient)", "cores": nt,
+                         "kind": "oracle", "sample": f"{len(sub)} evenly spaced bodies, "
+                         f"{wall:.1f} s wall incl. making their observations"},
+    }
+
+
+def ragged_leg(args, K, dev, flush, stream):
+    """500,000 bodies of very uneven step counts (main belt, NEOs with forced
+    Earth encounters, Trojans, comets) over 365 d: plain FP64 against the
+    mixed-precision form, and work stealing against the static schedule."""
+    import torch
+    import oracle as O
+    from paper_2509_04666_gb300 import kete, workloads as W
+    w = W.ragged1y(n_bodies=args.ragged_bodies)
+    n = w.n_bodies
+    K.load_ephem(w.ephem.to_bytes())
+    st0 = torch.from_numpy(w.states.copy()).to(dev)
+    t_end = W.T0 + 365.0
+    out = {"workload": f"ragged1y: {n} bodies (60% main belt, 20% NEOs of which 5% pass "
+                       f"0.001-0.01 AU from the Earth, 10% Trojans, 10% comets), 365 d"}
+    res = {}
+    for name, prec, kind in (("fp64", kete.FP64, kete.PROP_WORK_STEALING),
+                             ("mixed", kete.MIXED, kete.PROP_WORK_STEALING),
+                             ("fp64_static", kete.FP64, kete.PROP_STATIC)):
+        K.set_propagation(prec, kind, 128)
+        fm = kete.force_model(precision=prec)
+        box = {}
+
+        def call():
+            s = st0.clone(); e = torch.full((n,), W.T0, dtype=torch.float64, device=dev)
+            box["st"] = s
+            return K.propagate(s, e, t_end, fm=fm)
+        call()
+        ms, status = _timed(stream, call, flush, 2)
+        stt = K.get_stats()
+        res[name] = (box["st"].cpu().numpy(), status.cpu().numpy())
+        out[name] = {"value": n * 365.0 / (ms / 1e3), "unit": "body-days/s", "ms": ms,
+                     "prop_ms": stt["prop_ms"], "steps": stt["steps"]}
+    K.set_propagation(kete.FP64, kete.PROP_WORK_STEALING, 128)
+    K.set_propagation(kete.MIXED, kete.PROP_WORK_STEALING, 128)
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    out["work_stealing_speedup_vs_static"] = out["fp64_static"]["ms"] / out["fp64"]["ms"]
+    # accuracy on a sample (every population, all forced encounters in it)
+    orc = O.Oracle(w.ephem.to_bytes())
+    enc = np.nonzero(w.labels == 4)[0]
+    sub = np.unique(np.concatenate([np.linspace(0, n - 1, args.ref_sample).astype(np.int64),
+                                    enc[:: max(1, len(enc) // 64)]]))
+    t0 = time.perf_counter()
+    ref, _, rst, _ = orc.propagate_many(orc.force_model(), w.states[:, sub], w.epochs[sub], t_end)
+    dt = time.perf_counter() - t0
+    _, pe, _ = orc.ephem(3, t_end)
+    acc = {}
+    for name in ("fp64", "mixed"):
+        s, stat = res[name]
+        d = np.linalg.norm(s[:3, sub] - ref[:3], axis=0)
+        rho = np.linalg.norm(ref[:3] - pe[:, None], axis=0)
+        by = {}
+        for lab, nm in ((0, "main_belt"), (1, "neo"), (2, "trojan"), (3, "comet"), (4, "encounter")):
+            k = w.labels[sub] == lab
+            if k.any():
+                by[nm] = {"max_au": float(d[k].max()), "max_sky_mas_from_earth": float((d[k] / rho[k]).max() / MAS)}
+        acc[name] = {"bodies_ok": int((stat == 0).sum()), "sample": len(sub), "by_population": by}
+    out["accuracy"] = acc
+    out["cpu_baseline"] = {"value": len(sub) * 365.0 / dt, "unit": "body-days/s", "kind": "oracle",
+                           "cores": os.cpu_count(), "sample": f"{len(sub)} bodies, {dt:.1f} s"}
+    return out
+
+
 def run_gb300(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -350,6 +516,11 @@ def run_gb300(args):
                      "prop_fp64_tflops": f64m / (sm["prop_ms"] / 1e3) / 1e12,
                      "prop_fp32_tflops": f32m / (sm["prop_ms"] / 1e3) / 1e12,
                      "accuracy": compare_sample(kete, hm, nhm, sub, ref) if cpu else None}
+    adjoint = ragged = None
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        adjoint = adjoint_leg(args, K, dev, flush, stream, peak_nominal)
+    if rank == 0 and world == 1 and not args.no_ragged:
+        ragged = ragged_leg(args, K, dev, flush, stream)
     out = {
         "metric": METRIC, "value": value, "unit": "body-days/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -368,6 +539,8 @@ def run_gb300(args):
         "cpu_baseline": cpu,
         "accuracy": accuracy,
         "mixed_precision": mixed_leg,
+        "adjoint": adjoint,
+        "ragged": ragged,
         "e2e": e2e,
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "clocks": clocks,
@@ -398,6 +571,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--adj-bodies", type=int, default=100_000)
+    ap.add_argument("--adj-sample", type=int, default=512)
+    ap.add_argument("--ragged-bodies", type=int, default=500_000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -988,6 +988,8 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
         const double budget = (opt.mem_budget_gb > 0 ? opt.mem_budget_gb : 8.0) * 1073741824.0;
         int64_t chunk = (int64_t)(budget / (double)per_body);
         chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, n));
+        const int64_t n_chunks = (n + chunk - 1) / chunk;   // even chunks
+        chunk = (n + n_chunks - 1) / n_chunks;
         AdjBuffers B;
         B.cap = cap;
         GET(S_ADJ_REC, (size_t)chunk * cap * kAdjRec, B.rec);
@@ -997,11 +999,13 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
         GET(S_ADJ_YREF, (size_t)chunk * m * 6, B.yref);
         GET(S_ADJ_GJUMP, (size_t)chunk * m * 6, B.gjump);
         GET(S_ADJ_STATUS, chunk, B.status);
+        unsigned long long *next = nullptr;
+        GET(S_NEXTBODY, 1, next);
         int launches = 0;
         for (int64_t i0 = 0; i0 < n; i0 += chunk) {
             const int64_t nc = std::min(chunk, n - i0);
             prop_event(ctx, true);
-            CUDA_TRY(launch_adjoint_forward(ctx->E, F, B, P, i0, nc, ctx->stream));
+            CUDA_TRY(launch_adjoint_forward(ctx->E, F, B, P, i0, nc, next, ctx->stream));
             prop_event(ctx, false);
             CUDA_TRY(launch_adjoint_observe(ctx->E, B, P, i0, nc, ctx->stream));
             launches += 2;

@@ -3,7 +3,8 @@
 // Sec. 2: n-body propagation of App. A, two-body + light time, RA/Dec).
 //
 // Three kernels per chunk of bodies:
-//   k_adj_forward   one lane per body.  The body's observations are batched
+//   k_adj_forward   one lane per body at a time (work stealing).  The body's
+//                   observations are batched
 //                   by the <= span rule (Sec. 2); the chain visits the batch
 //                   midpoints and the checkpoint grid in ascending order with
 //                   the same Gauss-Radau steps as the propagation kernel.
@@ -126,57 +127,120 @@ __device__ __forceinline__ int obs_count(const kete_obs *o, int m)
 // ---------------------------------------------------------------------------
 // forward pass
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
-k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
+// Per-lane walk over one body's stops: the batch midpoints and the checkpoint
+// grid epoch0 + k ckpt (before the last midpoint), merged in ascending order.
+struct StopWalk {
+    int mi, nb;          // observations in use, batches
+    int kb, j1;          // next batch, end of its observations
+    double tref;         // its midpoint
+    int kc;              // next checkpoint index
+    double tc, t_last;   // its epoch, the last midpoint
+    bool ckpt_ok;        // tc is a stop
+};
+
+// the next stop of the walk (call only while w.kb < w.nb); mid: a midpoint
+__device__ __forceinline__ double walk_target(const StopWalk &w, bool &mid)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    mid = !(w.ckpt_ok && w.tc < w.tref);
+    return mid ? w.tref : w.tc;
+}
+
+__device__ __forceinline__ void walk_next_ckpt(StopWalk &w, double epoch0, double ckpt)
+{
+    w.kc++;
+    w.tc = epoch0 + (double)w.kc * ckpt;
+    w.ckpt_ok = w.tc < w.t_last;
+}
+
+// One lane per body at a time, one step attempt per loop iteration (lanes of a
+// warp stay in step while their bodies sit at different stops).  refill = 1:
+// persistent grid, a lane whose body is done takes the next one from *next.
+__global__ void __launch_bounds__(128)
+k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc,
+              unsigned long long *__restrict__ next, int refill)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     Cnt cnt = {0, 0, 0, 0, 0};
-    if (i < nc) {
-        const int64_t gi = i0 + i;
-        const kete_obs *o = P.obs + gi * P.m;
-        double x[3], v[3];
-        bool fin = true;
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            x[c] = P.states[c * P.n + gi];
-            v[c] = P.states[(3 + c) * P.n + gi];
-            fin = fin && isfinite(x[c]) && isfinite(v[c]);
-        }
-        const double epoch0 = P.epochs[gi];
-        double t = epoch0, dt = 0.0;
-        int status = (fin && isfinite(epoch0)) ? KETE_BODY_OK : KETE_BODY_NONFINITE;
-        const int mi = obs_count(o, P.m);
-        for (int j = 1; j < mi; j++)
-            if (o[j].epoch < o[j - 1].epoch) {
-                atomicOr(&P.ctr->error_flags, 1 << 6);
-                status = KETE_BODY_NONFINITE;
+    int64_t i = -1;   // current body (chunk index); -1: none; nc: no work left
+    double x[3], v[3], t = 0.0, dt = 0.0, epoch0 = 0.0, ts = 0.0;
+    bool mid = false, capped = false;
+    int status = KETE_BODY_OK, count = 0;
+    long long attempts = 0;
+    const kete_obs *o = nullptr;
+    StopWalk W;
+    StepState S;
+    S.have_a0 = false;
+    const LegView L = leg_view(nullptr, 0);
+    double *rec = nullptr;
+    bool first = true;
+    for (;;) {
+        const bool need = (i < 0);
+        const unsigned m = __ballot_sync(FULL, need);
+        if (m) {
+            unsigned long long base = 0;
+            const int leader = __ffs(m) - 1;
+            if (refill) {
+                if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(m));
+                base = __shfl_sync(FULL, base, leader);
             }
-        // number of batches and the last midpoint (the checkpoint grid ends there)
-        int nb = 0;
-        double t_last = epoch0;
-        for (int j0 = 0; j0 < mi; nb++) j0 = next_batch(o, mi, j0, P.span, t_last);
-        double *rec = B.rec + (size_t)i * B.cap * kAdjRec;
-        int count = 0;          // accepted steps recorded
-        bool capped = false;    // more steps than the record holds
-        StepState S;
-        const LegView L = leg_view(nullptr, 0);
-        int kb = 0, j0 = 0, j1 = 0;
-        double tref = 0.0;
-        if (mi > 0) j1 = next_batch(o, mi, 0, P.span, tref);
-        int kc = 1;
-        double tc = epoch0 + (double)kc * P.ckpt;
-        bool ckpt_ok = P.ckpt > 0.0 && tc < t_last;
-        while (status == KETE_BODY_OK && kb < nb) {
-            const bool mid = !(ckpt_ok && tc < tref);
-            const double ts = mid ? tref : tc;
-            aim_step(F, t, ts, dt);
-            S.have_a0 = false;
-            long long attempts = 0;
-            while (t != ts && status == KETE_BODY_OK) {
-                if (++attempts > F.max_steps) {
-                    status = KETE_BODY_STEP_CAP;
-                    break;
+            if (need) {
+                unsigned long long mine = base + __popc(m & ((1u << lane) - 1u));
+                if (!refill)
+                    mine = first ? (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x
+                                 : (unsigned long long)nc;
+                if (mine < (unsigned long long)nc) {
+                    i = (int64_t)mine;
+                    const int64_t gi = i0 + i;
+                    o = P.obs + gi * P.m;
+                    bool fin = true;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        x[c] = P.states[c * P.n + gi];
+                        v[c] = P.states[(3 + c) * P.n + gi];
+                        fin = fin && isfinite(x[c]) && isfinite(v[c]);
+                    }
+                    epoch0 = P.epochs[gi];
+                    t = epoch0;
+                    dt = 0.0;
+                    status = (fin && isfinite(epoch0)) ? KETE_BODY_OK : KETE_BODY_NONFINITE;
+                    W.mi = obs_count(o, P.m);
+                    for (int j = 1; j < W.mi; j++)
+                        if (o[j].epoch < o[j - 1].epoch) {
+                            atomicOr(&P.ctr->error_flags, 1 << 6);
+                            status = KETE_BODY_NONFINITE;
+                        }
+                    // batches and the last midpoint (the checkpoint grid ends there)
+                    W.nb = 0;
+                    W.t_last = epoch0;
+                    for (int j0 = 0; j0 < W.mi; W.nb++) j0 = next_batch(o, W.mi, j0, P.span, W.t_last);
+                    W.kb = 0;
+                    W.j1 = (W.mi > 0) ? next_batch(o, W.mi, 0, P.span, W.tref) : 0;
+                    W.kc = 1;
+                    W.tc = epoch0 + P.ckpt;
+                    W.ckpt_ok = P.ckpt > 0.0 && W.tc < W.t_last;
+                    rec = B.rec + (size_t)i * B.cap * kAdjRec;
+                    count = 0;
+                    capped = false;
+                    attempts = 0;
+                    S.have_a0 = false;
+                    if (W.kb < W.nb) {
+                        ts = walk_target(W, mid);
+                        aim_step(F, t, ts, dt);
+                    }
+                } else {
+                    i = nc;
                 }
+            }
+        }
+        first = false;
+        const bool active = (i >= 0 && i < nc);
+        if (!__any_sync(FULL, active)) break;
+        if (!active) continue;
+        if (status == KETE_BODY_OK && W.kb < W.nb && t != ts) {
+            if (++attempts > F.max_steps) {
+                status = KETE_BODY_STEP_CAP;
+            } else {
                 const int slot = count < B.cap - 1 ? count : B.cap - 2;
                 double *r = rec + (size_t)slot * kAdjRec;
                 const double t_prev = t;
@@ -188,39 +252,41 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
                     else capped = true;
                 }
             }
-            if (status != KETE_BODY_OK) break;
+            if (status == KETE_BODY_OK && t != ts) continue;
+        }
+        // at the stop ts (or failed): bookkeeping, then the next stop
+        if (status == KETE_BODY_OK && W.kb < W.nb) {
             if (mid) {
-                double *y = B.yref + ((size_t)i * P.m + kb) * 6;
+                double *y = B.yref + ((size_t)i * P.m + W.kb) * 6;
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     y[c] = x[c];
                     y[3 + c] = v[c];
                 }
-                B.bidx[(size_t)i * P.m + kb] = count;
-                if (ckpt_ok && tc == tref) {   // a checkpoint on the midpoint: one stop
-                    kc++;
-                    tc = epoch0 + (double)kc * P.ckpt;
-                    ckpt_ok = tc < t_last;
-                }
-                kb++;
-                j0 = j1;
-                if (kb < nb) j1 = next_batch(o, mi, j0, P.span, tref);
+                B.bidx[(size_t)i * P.m + W.kb] = count;
+                if (W.ckpt_ok && W.tc == W.tref) walk_next_ckpt(W, epoch0, P.ckpt);   // one stop
+                W.kb++;
+                if (W.kb < W.nb) W.j1 = next_batch(o, W.mi, W.j1, P.span, W.tref);
+            } else if (W.kc >= kAdjMaxCkpt) {   // bounded work per body
+                status = KETE_BODY_STEP_CAP;
             } else {
-                if (++kc > kAdjMaxCkpt) {   // bounded work per body
-                    status = KETE_BODY_STEP_CAP;
-                    break;
-                }
-                tc = epoch0 + (double)kc * P.ckpt;
-                ckpt_ok = tc < t_last;
+                walk_next_ckpt(W, epoch0, P.ckpt);
+            }
+            if (status == KETE_BODY_OK && W.kb < W.nb) {
+                ts = walk_target(W, mid);
+                aim_step(F, t, ts, dt);
+                S.have_a0 = false;
+                attempts = 0;
+                continue;
             }
         }
+        // the body is done
         if (status == KETE_BODY_OK && !capped) {
             // terminal record: da/dx at the final state closes the last step
             double *r = rec + (size_t)count * kAdjRec;
-            double a[3];
+            double a[3], J[6];
             Encounter enc;
             const double zero[3] = {0.0, 0.0, 0.0};
-            double J[6];
             status = accel_fp64<true>(E, F, t, 0.0, nullptr, x, v, a, enc, zero, true, J);
             cnt.evals++;
             r[0] = t;
@@ -231,8 +297,9 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
         }
         if (status == KETE_BODY_OK && capped) status = KETE_BODY_ADJ_CAP;
         B.n_rec[i] = (status == KETE_BODY_OK) ? count : 0;
-        B.nbat[i] = nb;
+        B.nbat[i] = W.nb;
         B.status[i] = status;
+        i = -1;
     }
     flush_counters(cnt, P.ctr);
 }
@@ -660,9 +727,24 @@ k_adj_backward(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
 static unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 cudaError_t launch_adjoint_forward(const EphemDev &E, const ForceDev &F, const AdjBuffers &B,
-                                   const AdjProblem &P, int64_t i0, int64_t nc, cudaStream_t st)
+                                   const AdjProblem &P, int64_t i0, int64_t nc,
+                                   unsigned long long *next, cudaStream_t st)
 {
-    if (nc > 0) k_adj_forward<<<blocks_for(nc, 128), 128, 0, st>>>(E, F, B, P, i0, nc);
+    if (nc <= 0) return cudaGetLastError();
+    int64_t grid = blocks_for(nc, 128);
+    int refill = 0;
+    if (next) {   // persistent grid with work stealing
+        cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_forward, 128, 0);
+        const int64_t persistent = (int64_t)(sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+        if (grid > persistent) grid = persistent;
+        refill = 1;
+    }
+    k_adj_forward<<<(unsigned)grid, 128, 0, st>>>(E, F, B, P, i0, nc, next, refill);
     return cudaGetLastError();
 }
 

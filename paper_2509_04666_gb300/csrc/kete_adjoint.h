@@ -41,8 +41,10 @@ struct AdjBuffers {
 };
 
 cudaError_t upload_adjoint_tables(cudaStream_t st);
+// next != null: persistent grid with work stealing from the counter *next
 cudaError_t launch_adjoint_forward(const EphemDev &E, const ForceDev &F, const AdjBuffers &B,
-                                   const AdjProblem &P, int64_t i0, int64_t nc, cudaStream_t st);
+                                   const AdjProblem &P, int64_t i0, int64_t nc,
+                                   unsigned long long *next, cudaStream_t st);
 cudaError_t launch_adjoint_observe(const EphemDev &E, const AdjBuffers &B, const AdjProblem &P,
                                    int64_t i0, int64_t nc, cudaStream_t st);
 cudaError_t launch_adjoint_backward(const AdjBuffers &B, const AdjProblem &P, int64_t i0,
