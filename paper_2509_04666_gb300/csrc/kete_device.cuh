@@ -55,42 +55,50 @@ __device__ __forceinline__ bool ephem_seg(const EphemDev &E, double t0, double o
     return true;
 }
 
-// position of one body: sum_k c_k T_k(tau) by Clenshaw's recurrence
+// position of one body: sum_k c_k T_k(tau) by Clenshaw's recurrence.  The
+// three coordinates' recurrences run interleaved (independent chains).
 __device__ __forceinline__ void cheb_pos(const double *__restrict__ c, int nc, double tau,
                                          double p[3])
 {
+    const double t2 = 2.0 * tau;
+    double b1[3] = {0.0, 0.0, 0.0}, b2[3] = {0.0, 0.0, 0.0};
+    for (int k = nc - 1; k >= 1; k--) {
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const double *cd = c + d * nc;
-        double b1 = 0.0, b2 = 0.0;
-        for (int k = nc - 1; k >= 1; k--) {
-            double b0 = fma(2.0 * tau, b1, __ldg(cd + k) - b2);
-            b2 = b1;
-            b1 = b0;
+        for (int d = 0; d < 3; d++) {
+            const double b0 = fma(t2, b1[d], __ldg(c + d * nc + k) - b2[d]);
+            b2[d] = b1[d];
+            b1[d] = b0;
         }
-        p[d] = fma(tau, b1, __ldg(cd) - b2);
     }
+#pragma unroll
+    for (int d = 0; d < 3; d++) p[d] = fma(tau, b1[d], __ldg(c + d * nc) - b2[d]);
 }
 
-// position and d/dtau (T_k' = k U_{k-1}, Clenshaw on the U series)
+// position and d/dtau (T_k' = k U_{k-1}, Clenshaw on the U series), the six
+// recurrences interleaved
 __device__ __forceinline__ void cheb_pos_vel(const double *__restrict__ c, int nc, double tau,
                                              double dtau_dt, double p[3], double v[3])
 {
+    const double t2 = 2.0 * tau;
+    double b1[3] = {0.0, 0.0, 0.0}, b2[3] = {0.0, 0.0, 0.0};
+    double u1[3] = {0.0, 0.0, 0.0}, u2[3] = {0.0, 0.0, 0.0};
+    for (int k = nc - 1; k >= 1; k--) {
+        const double kk = (double)k;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double ck = __ldg(c + d * nc + k);
+            const double b0 = fma(t2, b1[d], ck - b2[d]);
+            const double u0 = fma(t2, u1[d], kk * ck - u2[d]);
+            b2[d] = b1[d];
+            b1[d] = b0;
+            u2[d] = u1[d];
+            u1[d] = u0;
+        }
+    }
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        const double *cd = c + d * nc;
-        double b1 = 0.0, b2 = 0.0, u1 = 0.0, u2 = 0.0;
-        for (int k = nc - 1; k >= 1; k--) {
-            double ck = __ldg(cd + k);
-            double b0 = fma(2.0 * tau, b1, ck - b2);
-            double u0 = fma(2.0 * tau, u1, (double)k * ck - u2);
-            b2 = b1;
-            b1 = b0;
-            u2 = u1;
-            u1 = u0;
-        }
-        p[d] = fma(tau, b1, __ldg(cd) - b2);
-        v[d] = u1 * dtau_dt;
+        p[d] = fma(tau, b1[d], __ldg(c + d * nc) - b2[d]);
+        v[d] = u1[d] * dtau_dt;
     }
 }
 
@@ -149,34 +157,55 @@ __device__ __forceinline__ void mass_terms(T mu, T j2k, const T *P, bool newton,
     a[2] = fma(f, r[2], a[2]);
 }
 
-// Planet state (position, velocity) of body m by Clenshaw, out of line: the
-// per-thread path used when a step does not span a whole batch leg.
+// Planet state of body m by Clenshaw, out of line: the per-thread path used
+// when a step does not span a whole batch leg.  vel: also the velocity (the
+// GR term of Eq. A.3 is the only one that needs it); otherwise out6[3..5]
+// are left unset.
 static __device__ __noinline__ void cheb_state64(const EphemDev &E, int m, int s, double tau,
-                                          double *out6)
+                                                 double *out6, bool vel = true)
 {
-    double p[3], v[3];
-    cheb_pos_vel(ephem_coef(E, m, s), E.n_coef, tau, 2.0 * E.inv_seg, p, v);
-    out6[0] = p[0]; out6[1] = p[1]; out6[2] = p[2];
-    out6[3] = v[0]; out6[4] = v[1]; out6[5] = v[2];
+    if (vel) {
+        cheb_pos_vel(ephem_coef(E, m, s), E.n_coef, tau, 2.0 * E.inv_seg, out6, out6 + 3);
+    } else {
+        cheb_pos(ephem_coef(E, m, s), E.n_coef, tau, out6);
+    }
 }
 
-// FP32 Clenshaw of body m (mixed precision, planets only)
+// FP32 Clenshaw of body m (mixed precision, planets only), the recurrences
+// interleaved; vel as in cheb_state64
 __device__ __forceinline__ void cheb_state32(const EphemDev &E, int m, int s, float tau,
-                                             float *out6)
+                                             float *out6, bool vel = true)
 {
     const float *c = E.coef32 + ((size_t)m * E.n_seg + s) * 3 * E.n_coef;
+    const int nc = E.n_coef;
     const float dtau_dt = (float)(2.0 * E.inv_seg);
-    for (int d = 0; d < 3; d++) {
-        const float *cd = c + d * E.n_coef;
-        float b1 = 0.f, b2 = 0.f, u1 = 0.f, u2 = 0.f;
-        for (int k = E.n_coef - 1; k >= 1; k--) {
-            float ck = __ldg(cd + k);
-            float b0 = fmaf(2.f * tau, b1, ck - b2);
-            float u0 = fmaf(2.f * tau, u1, (float)k * ck - u2);
-            b2 = b1; b1 = b0; u2 = u1; u1 = u0;
+    const float t2 = 2.f * tau;
+    float b1[3] = {0.f, 0.f, 0.f}, b2[3] = {0.f, 0.f, 0.f};
+    float u1[3] = {0.f, 0.f, 0.f}, u2[3] = {0.f, 0.f, 0.f};
+    if (vel) {
+        for (int k = nc - 1; k >= 1; k--) {
+            const float kk = (float)k;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const float ck = __ldg(c + d * nc + k);
+                const float b0 = fmaf(t2, b1[d], ck - b2[d]);
+                const float u0 = fmaf(t2, u1[d], kk * ck - u2[d]);
+                b2[d] = b1[d]; b1[d] = b0; u2[d] = u1[d]; u1[d] = u0;
+            }
         }
-        out6[d] = fmaf(tau, b1, __ldg(cd) - b2);
-        out6[3 + d] = u1 * dtau_dt;
+    } else {
+        for (int k = nc - 1; k >= 1; k--) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const float b0 = fmaf(t2, b1[d], __ldg(c + d * nc + k) - b2[d]);
+                b2[d] = b1[d]; b1[d] = b0;
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        out6[d] = fmaf(tau, b1[d], __ldg(c + d * nc) - b2[d]);
+        if (vel) out6[3 + d] = u1[d] * dtau_dt;
     }
 }
 
@@ -267,12 +296,12 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
     for (int m = 0; m < E.n_bodies; m++) {
         if (!((F.active_mask >> m) & 1u)) continue;
         const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
-        double st[6];
+        double st[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (row64) {
 #pragma unroll
             for (int q = 0; q < 6; q++) st[q] = __ldg(row64 + 6 * m + q);
         } else {
-            cheb_state64(E, m, g.s, g.tau, st);
+            cheb_state64(E, m, g.s, g.tau, st, gr);
         }
         double r[3] = {x[0] - st[0], x[1] - st[1], x[2] - st[2]};
         if (detect) {
@@ -353,31 +382,24 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
     for (int m = 1; m < E.n_bodies; m++) {
         if (!((F.active_mask >> m) & 1u)) continue;
         const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
-        float st[6];
+        float st[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (row32) {
 #pragma unroll
             for (int q = 0; q < 6; q++) st[q] = __ldg(row32 + 6 * m + q);
         } else {
-            cheb_state32(E, m, g.s, tau32, st);
+            cheb_state32(E, m, g.s, tau32, st, gr);
             st[0] -= (float)sun[0]; st[1] -= (float)sun[1]; st[2] -= (float)sun[2];
         }
         float r[3] = {df[0] - st[0], df[1] - st[1], df[2] - st[2]};
         if (detect && r[0] * r[0] + r[1] * r[1] + r[2] * r[2] < (float)(4.0 * kCloseAu * kCloseAu))
             close |= 1u << m;
         if ((close >> m) & 1u) {
-            double st[6];
-            if (row64) {
-#pragma unroll
-                for (int q = 0; q < 6; q++) st[q] = __ldg(row64 + 6 * m + q);
-            } else {
-                cheb_state64(E, m, g.s, g.tau, st);
-            }
-            double s64[6];
+            double s64[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
             if (row64) {
 #pragma unroll
                 for (int q = 0; q < 6; q++) s64[q] = __ldg(row64 + 6 * m + q);
             } else {
-                cheb_state64(E, m, g.s, g.tau, s64);
+                cheb_state64(E, m, g.s, g.tau, s64, gr);
             }
             double r64[3] = {x[0] - s64[0], x[1] - s64[1], x[2] - s64[2]};
             if (detect) {
