@@ -387,6 +387,43 @@ def ragged_leg(args, K, dev, flush, stream):
     return out
 
 
+def run_leg(args):
+    """One leg alone (--leg adjoint|ragged), e.g. for a profiler; prints the
+    leg's own JSON object, not the benchmark line."""
+    import torch
+    from paper_2509_04666_gb300 import build as B, kete
+    B.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    K = kete.Kete(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    if args.leg == "adjoint":
+        out = adjoint_leg(args, K, dev, flush, stream, peak)
+    else:
+        out = ragged_leg(args, K, dev, flush, stream)
+    print(json.dumps({"leg": args.leg, **out}))
+    K.close()
+    return 0
+
+
+def fp64_lane_probe():
+    """FP64 FMA warp-instructions per second with 32 and with 1 active lane
+    per warp (the cost of an FP64 instruction does not shrink with its mask)."""
+    import ctypes as C
+    from paper_2509_04666_gb300 import build as B
+    L = C.CDLL(B.PEAK_LIB)
+    L.kete_peak_fma_lanes.argtypes = [C.c_int, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int,
+                                      C.POINTER(C.c_double)]
+    out = {}
+    for lanes in (32, 1):
+        v = C.c_double(0)
+        rc = L.kete_peak_fma_lanes(1, lanes, 4096, 152 * 8, 256, 2, C.byref(v))
+        out[f"active_{lanes}"] = v.value if rc == 0 else None
+    return out
+
+
 def run_gb300(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -456,6 +493,7 @@ def run_gb300(args):
     achieved = flops / (prop_ms / 1e3) / 1e12
     peak_nominal = 152 * 2 * 2 * 2.07e9 / 1e12      # SMs x FP64 FMA/clk x 2 x max clock
     peak_probe = peak_fma(True)
+    lane_probe = fp64_lane_probe()
     src_sha = kernel_source_sha()
     traffic = None
     if PROFILED_TRAFFIC["src_sha"] == src_sha and PROFILED_TRAFFIC["bytes_per_body_stop"]:
@@ -535,7 +573,8 @@ def run_gb300(args):
                      "traffic": traffic, "peak_probe_measured": (peak_probe or 0) / 1e12,
                      "flops_per_launch": flops / max(1, s0["prop_launches"]),
                      "fp32_tflops_alongside": flops32 / (prop_ms / 1e3) / 1e12,
-                     "prop_ms_per_step": prop_ms, "peak_basis": "152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
+                     "prop_ms_per_step": prop_ms, "peak_basis": "152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+                     "fp64_warp_inst_per_s": lane_probe},
         "cpu_baseline": cpu,
         "accuracy": accuracy,
         "mixed_precision": mixed_leg,
@@ -576,9 +615,13 @@ def main():
     ap.add_argument("--adj-bodies", type=int, default=100_000)
     ap.add_argument("--adj-sample", type=int, default=512)
     ap.add_argument("--ragged-bodies", type=int, default=500_000)
+    ap.add_argument("--leg", default="all", choices=["all", "adjoint", "ragged"],
+                    help="run one leg alone (profiling); the default prints the benchmark line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg != "all":
+        return run_leg(args)
     return run_gb300(args)
 
 
