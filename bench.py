@@ -340,10 +340,12 @@ def ragged_leg(args, K, dev, flush, stream):
     out = {"workload": f"ragged1y: {n} bodies (60% main belt, 20% NEOs of which 5% pass "
                        f"0.001-0.01 AU from the Earth, 10% Trojans, 10% comets), 365 d"}
     res = {}
-    for name, prec, kind in (("fp64", kete.FP64, kete.PROP_WORK_STEALING),
-                             ("mixed", kete.MIXED, kete.PROP_WORK_STEALING),
-                             ("fp64_static", kete.FP64, kete.PROP_STATIC)):
-        K.set_propagation(prec, kind, 128)
+    for name, prec, kind, split in (("fp64", kete.FP64, kete.PROP_WORK_STEALING, 0),
+                                    ("mixed", kete.MIXED, kete.PROP_WORK_STEALING, 0),
+                                    ("fp64_static", kete.FP64, kete.PROP_STATIC, 0),
+                                    ("fp64_split8", kete.FP64, kete.PROP_WORK_STEALING, 8),
+                                    ("mixed_split8", kete.MIXED, kete.PROP_WORK_STEALING, 8)):
+        K.set_propagation(prec, kind, 128, split, 64 if split else 0)
         fm = kete.force_model(precision=prec)
         box = {}
 
@@ -356,7 +358,7 @@ def ragged_leg(args, K, dev, flush, stream):
         stt = K.get_stats()
         res[name] = (box["st"].cpu().numpy(), status.cpu().numpy())
         out[name] = {"value": n * 365.0 / (ms / 1e3), "unit": "body-days/s", "ms": ms,
-                     "prop_ms": stt["prop_ms"], "steps": stt["steps"]}
+                     "prop_ms": stt["prop_ms"], "steps": stt["steps"], "deferred": stt["deferred"]}
     K.set_propagation(kete.FP64, kete.PROP_WORK_STEALING, 128)
     K.set_propagation(kete.MIXED, kete.PROP_WORK_STEALING, 128)
     out["mixed_speedup_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]

@@ -143,6 +143,9 @@ typedef struct kete_stats {
                                     span a whole leg between consecutive stops) */
     int64_t prop_kind;           /* propagation launch used: KETE_PROP_STATIC or _WORK_STEALING */
     int64_t prop_block;          /* its threads per block */
+    int64_t prop_split;          /* lanes per set-aside long body (0: no second phase) */
+    int64_t prop_budget;         /* step attempts per stop before a body is set aside */
+    int64_t deferred;            /* bodies set aside and finished by the split phase */
 } kete_stats;
 
 /* propagation launch variants (kete_set_propagation, kete_autotune) */
@@ -228,19 +231,31 @@ int kete_get_stats(const kete_ctx *ctx, kete_stats *out);
  * is launched by later calls: kind KETE_PROP_STATIC or
  * KETE_PROP_WORK_STEALING, block 32..128 threads (multiple of 32).  Both
  * produce identical results; they differ in load balance when bodies need
- * very different numbers of steps.  Default: work stealing, 128.
+ * very different numbers of steps.  split_lanes 4, 8 or 16 (0 or 1: off) with
+ * defer_steps > 0 adds a second phase: a body that has made more than
+ * defer_steps step attempts per stop reached is set aside at a step boundary
+ * and finished by a persistent launch in which split_lanes lanes share each
+ * body's force evaluations (the masses split over the lanes, partial sums
+ * combined by shuffles).  Which bodies are set aside depends on each body
+ * alone, so the static and work-stealing schedules still agree bit for bit;
+ * a set-aside body's force sums are added in another order than in one lane
+ * (differences at the rounding level).  Default: work stealing, 128, no split.
  * Errors: BAD_ARG. */
-int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block);
+int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block, int split_lanes,
+                         int defer_steps);
 
-/* Autotuner: time every launch variant (static 128; work stealing 64 and 128)
- * on an evenly strided sample of up to `max_sample` of the n bodies (device
- * states [6][n] / epochs [n], not modified) propagated along the chain of
- * stops (host, ascending) with force model fm, keep the fastest for fm's
- * precision, and report it in *kind / *block (host, may be NULL).
+/* Autotuner: time every launch variant (static 128; work stealing 64 and 128;
+ * work stealing 128 with long bodies set aside after 64 attempts per stop for
+ * 8 or 4 lanes each, or after 24 for 8 lanes) on an evenly strided sample of up
+ * to `max_sample` of the n bodies (device states [6][n] / epochs [n], not
+ * modified) propagated along the chain of stops (host, ascending) with force
+ * model fm, keep the fastest for fm's precision, and report it in *kind,
+ * *block, *split_lanes, *defer_steps (host, each may be NULL).
  * Errors: BAD_ARG, NO_EPHEM, NOMEM, CUDA. */
 int kete_autotune(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
                   const double *stops, int64_t n_stops, const kete_force_model *fm,
-                  int64_t max_sample, int32_t *kind, int32_t *block);
+                  int64_t max_sample, int32_t *kind, int32_t *block, int32_t *split_lanes,
+                  int32_t *defer_steps);
 
 /* One astrometric observation of one body (48 bytes). */
 typedef struct kete_obs {

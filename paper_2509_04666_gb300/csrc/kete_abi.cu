@@ -29,6 +29,7 @@ enum Slot {
     S_HITTMP, S_FRAMECNT, S_FRAMEOFF, S_FRAMECUR, S_HITGROUP, S_MAXRAD, S_NT_T0, S_NT_H,
     S_NT_R64, S_NT_R32, S_XSUN, S_XOBSREL, S_NEXTBODY, S_TUNE_ST, S_TUNE_EP, S_TUNE_OUT,
     S_ADJ_REC, S_ADJ_NREC, S_ADJ_NBAT, S_ADJ_BIDX, S_ADJ_YREF, S_ADJ_GJUMP, S_ADJ_STATUS,
+    S_KSTOP, S_DEFER_LIST, S_DEFER_CNT,
     S_NSLOTS
 };
 
@@ -192,6 +193,7 @@ static void stats_collect(kete_ctx *ctx)
     ctx->stats.force_evals = (int64_t)ctx->h_ctr->force_evals;
     ctx->stats.iterations = (int64_t)ctx->h_ctr->iterations;
     ctx->stats.node_evals = (int64_t)ctx->h_ctr->node_evals;
+    ctx->stats.deferred = (int64_t)ctx->h_ctr->deferred;
     ctx->stats.prop_launches = ctx->pending_prop_pairs;
     ctx->pending_prop_pairs = 0;
     double *dst[4] = {&ctx->stats.prep_ms, &ctx->stats.cand_ms, &ctx->stats.exact_ms,
@@ -421,10 +423,21 @@ static int propagate(kete_ctx *ctx, const ForceDev &F, ChainState cs, const doub
     PropVariant var = ctx->var[F.precision == KETE_MIXED ? 1 : 0];
     unsigned long long *next = nullptr;
     if (var.kind == PROP_WORK_STEALING) GET(S_NEXTBODY, 1, next);
+    PropDefer defer{}, *dp = nullptr;
+    if (var.split > 1 && var.budget > 0) {
+        unsigned long long *cnt;
+        GET(S_DEFER_LIST, cs.n, defer.list);
+        GET(S_DEFER_CNT, 2, cnt);
+        defer.count = cnt;
+        defer.next = cnt + 1;
+        dp = &defer;
+    }
     ctx->stats.prop_kind = var.kind;
     ctx->stats.prop_block = var.block;
+    ctx->stats.prop_split = var.split;
+    ctx->stats.prop_budget = var.budget;
     CUDA_TRY(launch_propagate(ctx->E, F, cs, stops_dev, n_stops, out, stride, keep_on_fail,
-                              ctx->d_ctr, ctx->stream, nt, leg0, var, next));
+                              ctx->d_ctr, ctx->stream, nt, leg0, var, next, dp));
     return KETE_OK;
 }
 
@@ -454,6 +467,7 @@ static int run_chain(kete_ctx *ctx, const ForceDev &F, const double *states, con
 {
     GET(S_CHAIN, 8 * n, cs.w);
     GET(S_STATUS, n, cs.status);
+    GET(S_KSTOP, n, cs.kstop);
     cs.n = n;
     CUDA_TRY(launch_chain_init(cs, states, epochs, F, ctx->stream));
     return KETE_OK;
@@ -864,21 +878,29 @@ extern "C" int kete_propagate_noalloc(kete_ctx *ctx, double *states, double *epo
     return KETE_OK;
 }
 
-extern "C" int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block)
+extern "C" int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block,
+                                    int split_lanes, int defer_steps)
 {
     if (!ctx) return KETE_ERR_BAD_ARG;
+    const bool split_ok = split_lanes == 0 || split_lanes == 1 || split_lanes == 4 ||
+                          split_lanes == 8 || split_lanes == 16;
     if ((precision != KETE_FP64 && precision != KETE_MIXED) ||
         (kind != KETE_PROP_STATIC && kind != KETE_PROP_WORK_STEALING) || block < 32 ||
-        block > 128 || block % 32 != 0)
-        return fail(ctx, KETE_ERR_BAD_ARG, "bad propagation variant (precision %d, kind %d, block %d)",
-                    precision, kind, block);
-    ctx->var[precision == KETE_MIXED ? 1 : 0] = PropVariant{kind, block};
+        block > 128 || block % 32 != 0 || !split_ok || defer_steps < 0)
+        return fail(ctx, KETE_ERR_BAD_ARG,
+                    "bad propagation variant (precision %d, kind %d, block %d, split %d, defer %d)",
+                    precision, kind, block, split_lanes, defer_steps);
+    PropVariant v{kind, block};
+    v.split = split_lanes > 1 ? split_lanes : 0;
+    v.budget = v.split ? defer_steps : 0;
+    ctx->var[precision == KETE_MIXED ? 1 : 0] = v;
     return KETE_OK;
 }
 
 extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
                              const double *stops, int64_t n_stops, const kete_force_model *fm,
-                             int64_t max_sample, int32_t *kind, int32_t *block)
+                             int64_t max_sample, int32_t *kind, int32_t *block,
+                             int32_t *split_lanes, int32_t *defer_steps)
 {
     if (!ctx) return KETE_ERR_BAD_ARG;
     if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
@@ -902,13 +924,21 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
     GET(S_STOPS, n_stops, d_stops);
     CUDA_TRY(cudaMemcpyAsync(d_stops, stops, n_stops * sizeof(double), cudaMemcpyHostToDevice, st));
     CUDA_TRY(launch_gather_bodies(states, epochs, n, stride, m, sst, sep, st));
-    const PropVariant cands[3] = {{PROP_STATIC, 128}, {PROP_WORK_STEALING, 64},
-                                  {PROP_WORK_STEALING, 128}};
+    PropVariant cands[6] = {{PROP_STATIC, 128}, {PROP_WORK_STEALING, 64},
+                            {PROP_WORK_STEALING, 128}, {PROP_WORK_STEALING, 128},
+                            {PROP_WORK_STEALING, 128}, {PROP_WORK_STEALING, 128}};
+    cands[3].split = 8;
+    cands[3].budget = 64;
+    cands[4].split = 4;
+    cands[4].budget = 64;
+    cands[5].split = 8;
+    cands[5].budget = 24;
+    const int n_cands = 6;
     const PropVariant saved = ctx->var[F.precision == KETE_MIXED ? 1 : 0];
     float best_ms = 1e30f;
     PropVariant best = saved;
     cudaEvent_t e0 = event_at(ctx, 0), e1 = event_at(ctx, 1);
-    for (int c = 0; c < 3; c++) {
+    for (int c = 0; c < n_cands; c++) {
         ctx->var[F.precision == KETE_MIXED ? 1 : 0] = cands[c];
         float ms = 0.0f;
         for (int rep = 0; rep < 2; rep++) {   // the first run warms up
@@ -934,6 +964,8 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
     ctx->var[F.precision == KETE_MIXED ? 1 : 0] = best;
     if (kind) *kind = best.kind;
     if (block) *block = best.block;
+    if (split_lanes) *split_lanes = best.split;
+    if (defer_steps) *defer_steps = best.budget;
     return KETE_OK;
 }
 

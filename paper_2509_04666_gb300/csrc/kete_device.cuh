@@ -108,6 +108,38 @@ __device__ __forceinline__ const double *ephem_coef(const EphemDev &E, int body,
 }
 
 // ---------------------------------------------------------------------------
+// Lane groups: G consecutive lanes (G a power of two, <= 32) integrating one
+// body together.  Every lane of a group holds the same integrator state and
+// runs the same control flow; in a force evaluation lane `rank` takes the
+// masses m = rank, rank + G, ... and the partial sums are combined by a
+// butterfly of shuffles, which leaves the same bits in every lane (each pair
+// adds the same two values).  G = 1 is the plain one-lane-per-body form.
+// ---------------------------------------------------------------------------
+template <int G>
+struct LaneGroup {
+    static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "G");
+    __device__ __forceinline__ static int rank() { return G == 1 ? 0 : (int)(threadIdx.x & (G - 1)); }
+    __device__ __forceinline__ static unsigned mask()
+    {
+        if (G == 32) return 0xffffffffu;
+        return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(G - 1));
+    }
+    template <typename T>
+    __device__ __forceinline__ static T sum(T v)
+    {
+#pragma unroll
+        for (int o = G / 2; o >= 1; o /= 2) v += __shfl_xor_sync(mask(), v, o);
+        return v;
+    }
+    __device__ __forceinline__ static uint32_t bit_or(uint32_t v)
+    {
+#pragma unroll
+        for (int o = G / 2; o >= 1; o /= 2) v |= __shfl_xor_sync(mask(), v, o);
+        return v;
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Force model (Eq. A.1): for each active mass m with r = x - x_m, v = v - v_m:
 //   Newton  -mu r / |r|^3
 //   GR      mu / (c^2 |r|^3) [ (4 mu/|r| - |v|^2) r + 4 (r.v) v ]       (Eq. A.3)
@@ -246,6 +278,28 @@ struct Encounter {
     double d0[3];     // x0 - p_m(t0)
 };
 
+// the group's nearest candidate (ties to the lower table index, as the
+// one-lane loop over m in order)
+template <int G>
+__device__ __forceinline__ void encounter_reduce(double &best, Encounter &enc)
+{
+#pragma unroll
+    for (int o = G / 2; o >= 1; o /= 2) {
+        const unsigned gm = LaneGroup<G>::mask();
+        const double ob = __shfl_xor_sync(gm, best, o);
+        const int om = __shfl_xor_sync(gm, enc.m, o);
+        double od[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) od[c] = __shfl_xor_sync(gm, enc.d0[c], o);
+        if (ob < best || (ob == best && om < enc.m)) {
+            best = ob;
+            enc.m = om;
+#pragma unroll
+            for (int c = 0; c < 3; c++) enc.d0[c] = od[c];
+        }
+    }
+}
+
 // Node rows: planet states at one Gauss-Radau node epoch of a batch leg,
 // shared by every body whose step spans that whole leg.
 //   row64[m*6 + 0..5]  barycentric position, velocity (FP64)
@@ -273,8 +327,8 @@ __device__ __forceinline__ void newton_jacobian(double mu, const double r[3], do
 // detect (step start, off = 0): also record in enc the nearest planet within
 // kEncounterAu and its relative position; otherwise enc is read.
 // JAC: also return in J the Newtonian da/dx (see newton_jacobian), from the
-// same relative vectors as the force.
-template <bool JAC = false>
+// same relative vectors as the force.  G: lanes per body (see LaneGroup).
+template <bool JAC = false, int G = 1>
 __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, double t0,
                                           double off, const double *__restrict__ row64,
                                           const double x[3], const double v[3], double a[3],
@@ -293,7 +347,7 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
     }
     double best = kEncounterAu * kEncounterAu;
     if (!row64 && !ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
-    for (int m = 0; m < E.n_bodies; m++) {
+    for (int m = LaneGroup<G>::rank(); m < E.n_bodies; m += G) {
         if (!((F.active_mask >> m) & 1u)) continue;
         const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
         double st[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -322,6 +376,15 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
         mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r, w, a);
         if (JAC) newton_jacobian(E.gm[m], r, J);
     }
+    if (G > 1) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) a[c] = LaneGroup<G>::sum(a[c]);
+        if (JAC) {
+#pragma unroll
+            for (int q = 0; q < 6; q++) J[q] = LaneGroup<G>::sum(J[q]);
+        }
+        if (detect) encounter_reduce<G>(best, enc);
+    }
     return KETE_BODY_OK;
 }
 
@@ -334,7 +397,9 @@ constexpr double kCloseAu = 0.05;
 
 // detect (step start, off = 0): planets within 2 kCloseAu go to FP64 and are
 // recorded in `close` (held for the step), and the nearest within kEncounterAu
-// in enc; otherwise close and enc are read.
+// in enc; otherwise close and enc are read.  G: lanes per body (LaneGroup);
+// the Sun's terms belong to rank 0, every lane forms the Sun-relative position.
+template <int G = 1>
 __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F, double t0,
                                            double off, const double *__restrict__ row64,
                                            const float *__restrict__ row32, uint32_t &close,
@@ -362,7 +427,8 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
     const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
     const float vf[3] = {(float)v[0], (float)v[1], (float)v[2]};
     float af[3] = {0.f, 0.f, 0.f};
-    if (F.active_mask & 1u) {
+    const int rk = LaneGroup<G>::rank();
+    if (rk == 0 && (F.active_mask & 1u)) {
         // Sun monopole, FP64
         double rr = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
         double ri = rsqrt(rr);
@@ -379,7 +445,7 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
         }
     }
     const float tau32 = row64 ? 0.f : (float)g.tau;
-    for (int m = 1; m < E.n_bodies; m++) {
+    for (int m = (rk == 0 ? G : rk); m < E.n_bodies; m += G) {
         if (!((F.active_mask >> m) & 1u)) continue;
         const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
         float st[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -423,6 +489,17 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
         float w[3] = {vf[0] - st[3], vf[1] - st[4], vf[2] - st[5]};
         float P[3] = {(float)F.pole[m][0], (float)F.pole[m][1], (float)F.pole[m][2]};
         mass_terms<float>((float)E.gm[m], (float)F.j2k[m], P, true, gr, j2, r, w, af);
+    }
+    if (G > 1) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            as[c] = LaneGroup<G>::sum(as[c]);
+            af[c] = LaneGroup<G>::sum(af[c]);
+        }
+        if (detect) {
+            close = LaneGroup<G>::bit_or(close);
+            encounter_reduce<G>(best, enc);
+        }
     }
     a[0] = as[0] + (double)af[0];
     a[1] = as[1] + (double)af[1];

@@ -36,6 +36,7 @@ struct DevCounters {
     unsigned long long steps, rejected, force_evals, iterations;
     unsigned long long candidates, hits;
     unsigned long long node_evals;   // force evaluations served by batch node rows
+    unsigned long long deferred;     // bodies set aside for the split second phase
     int error_flags;         // bit 0: unsorted epochs, 1: exposure mismatch, 2: bad observer,
                              // 3: bad n_edges, 4: non-finite frame, 5: batch epoch outside table
     int pad;
@@ -51,11 +52,29 @@ struct NodeTable {
     int n_legs, nb;
 };
 
-// per-body working state of a propagation chain: [8][n] = x,y,z,vx,vy,vz,t,dt
+// per-body working state of a propagation chain: [8][n] = x,y,z,vx,vy,vz,t,dt;
+// kstop[n] (may be null): the stop a set-aside body resumes at
 struct ChainState {
     double *w;
     int32_t *status;
     int64_t n;
+    int32_t *kstop = nullptr;
+};
+
+// where a propagation launch takes its bodies from (see k_propagate)
+struct PropQueue {
+    const int32_t *list = nullptr;               // bodies to take; null: 0..n-1
+    const unsigned long long *list_n = nullptr;  // how many (device)
+    int32_t *defer = nullptr;                    // set-aside bodies are appended here
+    unsigned long long *defer_n = nullptr;
+    int budget = 0;                              // step attempts per stop reached
+};
+
+// scratch of the two-phase (split) launch
+struct PropDefer {
+    int32_t *list;                 // [n]
+    unsigned long long *count;     // set-aside bodies
+    unsigned long long *next;      // work-stealing counter of the second phase
 };
 
 // launch helpers implemented in the .cu files ---------------------------------
@@ -70,15 +89,18 @@ cudaError_t launch_node_table(const EphemDev &E, const double *stops_dev, int n_
 // how the propagation kernel is launched (chosen by the autotuner)
 enum PropKind { PROP_STATIC = 0, PROP_WORK_STEALING = 1 };
 struct PropVariant {
-    int kind;    // PropKind
-    int block;   // threads per block (<= 128)
+    int kind;         // PropKind
+    int block;        // threads per block (<= 128)
+    int split = 0;    // lanes per body for long bodies (4, 8, 16; 0 or 1: none)
+    int budget = 0;   // step attempts per stop after which a body is set aside
 };
 cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
                              const double *stops_dev, int n_stops, double *out,
                              int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
                              cudaStream_t st, const NodeTable *nt = nullptr, int leg0 = 0,
                              PropVariant var = PropVariant{PROP_STATIC, 128},
-                             unsigned long long *next_body = nullptr);
+                             unsigned long long *next_body = nullptr,
+                             PropDefer *defer = nullptr);
 int propagate_ws_blocks(int block, int mode);
 cudaError_t launch_gather_bodies(const double *st, const double *ep, int64_t n, int64_t stride,
                                  int64_t m, double *dst, double *dep, cudaStream_t s);

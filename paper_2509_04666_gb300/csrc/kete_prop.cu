@@ -24,54 +24,64 @@ void upload_radau_tables(cudaStream_t st) { upload_step_tables(st); }
 #define KETE_PROP_MIN_BLOCKS 1   // resident blocks per SM asked of the register allocator
 #endif
 
-// The propagation kernel.  Each lane owns one body at a time and advances it
-// one step attempt per loop iteration along its chain of stops, writing the
-// state at every stop to out[k][c][i] (stride out_stride between rows) and the
-// chain state back when it is done.  Stop k of this launch is leg leg0 + k of
-// the node table (if any).
-//   refill = 0 (static): lane j of the grid takes body j and then idles;
-//   refill = 1 (work stealing, persistent grid): a lane whose body is done
+// The propagation kernel.  Each group of G lanes (G = 1: one lane) owns one
+// body at a time and advances it one step attempt per loop iteration along its
+// chain of stops, writing the state at every stop to out[k][c][i] (stride
+// out_stride between rows) and the chain state back when it is done.  Stop k
+// of this launch is leg leg0 + k of the node table (if any).
+//   refill = 0 (static): group j of the grid takes body j and then idles;
+//   refill = 1 (work stealing, persistent grid): a group whose body is done
 //   takes the next one from an atomic counter (warp-aggregated), so a body
-//   needing hundreds of steps no longer idles the other 31 lanes of its warp.
+//   needing hundreds of steps no longer idles the rest of its warp.
 // Both schedules run the same instructions per body: results are identical.
-template <int MODE>
+// Queue q: the bodies come from q.list (q.list_n of them, device) instead of
+// 0..n-1, each resuming at its saved stop cs.kstop[i]; with q.defer set, a
+// body that has made more than q.budget step attempts per stop reached is
+// set aside at its next step boundary (state and stop saved, index appended
+// to q.defer) for a second launch with more lanes per body.
+template <int MODE, int G>
 __global__ void __launch_bounds__(128, KETE_PROP_MIN_BLOCKS)
 k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ stops,
             int n_stops, double *__restrict__ out, int64_t out_stride, int keep_on_fail,
             DevCounters *ctr, NodeTable nt, int use_nt, int leg0,
-            unsigned long long *__restrict__ next_body, int refill)
+            unsigned long long *__restrict__ next_body, int refill, PropQueue q)
 {
     const int64_t n = cs.n;
+    const unsigned long long n_items = q.list ? *q.list_n : (unsigned long long)n;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const int grank = LaneGroup<G>::rank();
+    const bool writer = (grank == 0);
     Cnt cnt = {0, 0, 0, 0, 0};
     int64_t i = -1;           // current body (-1: none; n: no work left)
     int k = 0;                // next stop of the body
     double x[3], v[3], t = 0.0, dt = 0.0;
     int status = KETE_BODY_OK;
-    long long attempts = 0;
+    long long attempts = 0, body_attempts = 0;
     StepState S;
     S.have_a0 = false;
     LegView L = leg_view(nullptr, 0);
     bool first = true;
     for (;;) {
-        // lanes without a body take the next ones
+        // groups without a body take the next ones
         const bool need = (i < 0);
         const unsigned m = __ballot_sync(FULL, need);
         if (m) {
             unsigned long long base = 0;
             const int leader = __ffs(m) - 1;
             if (refill) {
-                if (lane == leader) base = atomicAdd(next_body, (unsigned long long)__popc(m));
+                if (lane == leader) base = atomicAdd(next_body, (unsigned long long)(__popc(m) / G));
                 base = __shfl_sync(FULL, base, leader);
             }
             if (need) {
-                unsigned long long mine = base + __popc(m & ((1u << lane) - 1u));
-                if (!refill)   // static: one body per lane, taken on the first pass
-                    mine = first ? (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x
-                                 : (unsigned long long)n;
-                if (mine < (unsigned long long)n) {
-                    i = (int64_t)mine;
+                // needing groups before this one, in lane order
+                const unsigned before = m & ((1u << (lane - grank)) - 1u);
+                unsigned long long mine = base + (unsigned long long)(__popc(before) / G);
+                if (!refill)   // static: one body per group, taken on the first pass
+                    mine = first ? ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) / G
+                                 : n_items;
+                if (mine < n_items) {
+                    i = q.list ? (int64_t)q.list[mine] : (int64_t)mine;
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
                         x[c] = cs.w[c * n + i];
@@ -80,11 +90,12 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
                     t = cs.w[6 * n + i];
                     dt = cs.w[7 * n + i];
                     status = cs.status[i];
-                    k = 0;
+                    k = q.list ? cs.kstop[i] : 0;
                     attempts = 0;
+                    body_attempts = 0;
                     S.have_a0 = false;
-                    L = leg_view(use_nt ? &nt : nullptr, leg0);
-                    if (status == KETE_BODY_OK && n_stops > 0) aim_step(F, t, stops[0], dt);
+                    L = leg_view(use_nt ? &nt : nullptr, leg0 + k);
+                    if (status == KETE_BODY_OK && k < n_stops) aim_step(F, t, stops[k], dt);
                 } else {
                     i = n;   // drained
                 }
@@ -95,22 +106,44 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
         if (!__any_sync(FULL, active)) break;
         if (!active) continue;
         if (k < n_stops && status == KETE_BODY_OK && t != stops[k]) {
+            if (q.defer && !S.have_a0 && body_attempts >= (long long)q.budget * (k + 1)) {
+                // set the body aside at this step boundary
+                if (writer) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        cs.w[c * n + i] = x[c];
+                        cs.w[(3 + c) * n + i] = v[c];
+                    }
+                    cs.w[6 * n + i] = t;
+                    cs.w[7 * n + i] = dt;
+                    cs.status[i] = status;
+                    cs.kstop[i] = k;
+                    q.defer[atomicAdd(q.defer_n, 1ull)] = (int32_t)i;
+                    atomicAdd(&ctr->deferred, 1ull);
+                }
+                i = -1;
+                continue;
+            }
+            body_attempts++;
             if (++attempts > F.max_steps) status = KETE_BODY_STEP_CAP;
-            else status = step_once<MODE>(E, F, L, x, v, t, dt, stops[k], S, cnt);
+            else status = step_once<MODE, false, G>(E, F, L, x, v, t, dt, stops[k], S, cnt);
             if (status == KETE_BODY_OK && t != stops[k]) continue;
         }
         // the body is at stop k (or failed): record it and move on
         while (k < n_stops && (status != KETE_BODY_OK || t == stops[k])) {
             double *o = out + (int64_t)k * 6 * out_stride;
-            if (status == KETE_BODY_OK) {
+            if (writer) {
+                if (status == KETE_BODY_OK) {
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    o[c * out_stride + i] = x[c];
-                    o[(3 + c) * out_stride + i] = v[c];
+                    for (int c = 0; c < 3; c++) {
+                        o[c * out_stride + i] = x[c];
+                        o[(3 + c) * out_stride + i] = v[c];
+                    }
+                } else if (!keep_on_fail) {
+#pragma unroll
+                    for (int c = 0; c < 6; c++)
+                        o[c * out_stride + i] = __longlong_as_double(0x7ff8000000000000ll);
                 }
-            } else if (!keep_on_fail) {
-#pragma unroll
-                for (int c = 0; c < 6; c++) o[c * out_stride + i] = __longlong_as_double(0x7ff8000000000000ll);
             }
             k++;
             attempts = 0;
@@ -121,18 +154,20 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
             }
         }
         if (k < n_stops) continue;
-        // all stops done: write the chain state back and free the lane
+        // all stops done: write the chain state back and free the group
+        if (writer) {
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            cs.w[c * n + i] = x[c];
-            cs.w[(3 + c) * n + i] = v[c];
+            for (int c = 0; c < 3; c++) {
+                cs.w[c * n + i] = x[c];
+                cs.w[(3 + c) * n + i] = v[c];
+            }
+            cs.w[6 * n + i] = t;
+            cs.w[7 * n + i] = dt;
+            cs.status[i] = status;
         }
-        cs.w[6 * n + i] = t;
-        cs.w[7 * n + i] = dt;
-        cs.status[i] = status;
         i = -1;
     }
-    flush_counters(cnt, ctr);
+    flush_counters<G>(cnt, ctr);
 }
 
 // Node table: thread per (leg k, node n, body m).  Leg 0 starts at the first
@@ -262,29 +297,57 @@ cudaError_t launch_node_table(const EphemDev &E, const double *stops_dev, int n_
     return cudaGetLastError();
 }
 
-int propagate_ws_blocks(int block, int mode)
+template <int MODE, int G>
+static int ws_blocks(int block)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (mode == KETE_MIXED)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<KETE_MIXED>, block, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<KETE_FP64>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<MODE, G>, block, 0);
     return (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+}
+
+int propagate_ws_blocks(int block, int mode)
+{
+    return mode == KETE_MIXED ? ws_blocks<KETE_MIXED, 1>(block) : ws_blocks<KETE_FP64, 1>(block);
+}
+
+template <int MODE, int G>
+static void launch_k(int64_t grid, int block, cudaStream_t st, const EphemDev &E,
+                     const ForceDev &F, ChainState cs, const double *stops, int n_stops,
+                     double *out, int64_t stride, int kof, DevCounters *ctr, NodeTable t, int unt,
+                     int leg0, unsigned long long *next, int refill, PropQueue q)
+{
+    k_propagate<MODE, G><<<(unsigned)grid, block, 0, st>>>(E, F, cs, stops, n_stops, out, stride,
+                                                          kof, ctr, t, unt, leg0, next, refill, q);
+}
+
+template <int MODE>
+static void launch_split(int G, int64_t grid, int block, cudaStream_t st, const EphemDev &E,
+                         const ForceDev &F, ChainState cs, const double *stops, int n_stops,
+                         double *out, int64_t stride, int kof, DevCounters *ctr, NodeTable t,
+                         int unt, int leg0, unsigned long long *next, PropQueue q)
+{
+    if (G == 4)
+        launch_k<MODE, 4>(grid, block, st, E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, 1, q);
+    else if (G == 16)
+        launch_k<MODE, 16>(grid, block, st, E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, 1, q);
+    else
+        launch_k<MODE, 8>(grid, block, st, E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, 1, q);
 }
 
 cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
                              const double *stops_dev, int n_stops, double *out,
                              int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
                              cudaStream_t st, const NodeTable *nt, int leg0, PropVariant var,
-                             unsigned long long *next_body)
+                             unsigned long long *next_body, PropDefer *defer)
 {
     if (cs.n <= 0 || n_stops <= 0) return cudaGetLastError();
     NodeTable t{};
     if (nt) t = *nt;
     const int kof = keep_on_fail ? 1 : 0, unt = nt ? 1 : 0;
     const int block = (var.block > 0 && var.block <= 128) ? var.block : 128;
+    const bool mixed = F.precision == KETE_MIXED;
     int refill = 0;
     int64_t grid = (cs.n + block - 1) / block;
     if (var.kind == PROP_WORK_STEALING && next_body) {
@@ -294,10 +357,36 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
         int64_t persistent = propagate_ws_blocks(block, F.precision);
         if (grid > persistent) grid = persistent;
     }
-    if (F.precision == KETE_MIXED)
-        k_propagate<KETE_MIXED><<<(unsigned)grid, block, 0, st>>>(E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, next_body, refill);
+    // phase 1: one lane per body; with a split variant, long bodies are set aside
+    PropQueue q{};
+    const bool split = var.split > 1 && var.budget > 0 && defer && cs.kstop;
+    if (split) {
+        cudaError_t e = cudaMemsetAsync(defer->count, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        q.defer = defer->list;
+        q.defer_n = defer->count;
+        q.budget = var.budget;
+    }
+    if (mixed)
+        launch_k<KETE_MIXED, 1>(grid, block, st, E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, next_body, refill, q);
     else
-        k_propagate<KETE_FP64><<<(unsigned)grid, block, 0, st>>>(E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, next_body, refill);
+        launch_k<KETE_FP64, 1>(grid, block, st, E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, next_body, refill, q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !split) return e;
+    // phase 2: the set-aside bodies, var.split lanes each, persistent grid
+    e = cudaMemsetAsync(defer->next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    PropQueue q2{};
+    q2.list = defer->list;
+    q2.list_n = defer->count;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid2 = (int64_t)(sms > 0 ? sms : 152) * 2;
+    if (mixed)
+        launch_split<KETE_MIXED>(var.split, grid2, 128, st, E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, defer->next, q2);
+    else
+        launch_split<KETE_FP64>(var.split, grid2, 128, st, E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, defer->next, q2);
     return cudaGetLastError();
 }
 

@@ -81,7 +81,8 @@ struct LegRows {
 // detect: the evaluation at a step start, which also finds the planets near
 // the body (see accel_fp64 / accel_mixed).
 // JAC (FP64 only): also store the Newtonian da/dx at this point to jout[0..5].
-template <int MODE, bool JAC = false>
+// G: lanes per body (LaneGroup).
+template <int MODE, bool JAC = false, int G = 1>
 __device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, double t0, double off,
                                      const double *row64, const float *row32, uint32_t &close,
                                      const double x[3], const double v[3], double a[3],
@@ -90,9 +91,9 @@ __device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, doubl
 {
     static_assert(!(JAC && MODE == KETE_MIXED), "Jacobian capture is FP64 only");
     if (MODE == KETE_MIXED)
-        return accel_mixed(E, F, t0, off, row64, row32, close, x, v, a, as, enc, dx, detect);
+        return accel_mixed<G>(E, F, t0, off, row64, row32, close, x, v, a, as, enc, dx, detect);
     double J[6];
-    int st = accel_fp64<JAC>(E, F, t0, off, row64, x, v, a, enc, dx, detect, J);
+    int st = accel_fp64<JAC, G>(E, F, t0, off, row64, x, v, a, enc, dx, detect, J);
     as[0] = a[0]; as[1] = a[1]; as[2] = a[2];
     if (JAC) {
 #pragma unroll
@@ -106,7 +107,7 @@ __device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, doubl
 // planets come from the node rows (node n at rows.r64 + n * stride).
 // JAC: every node evaluation also stores da/dx at node n to jrec[6n..6n+5];
 // the last corrector iteration's values remain.
-template <int MODE, bool JAC = false>
+template <int MODE, bool JAC = false, int G = 1>
 __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &F, double t,
                                              const double x0[3], const double v0[3],
                                              const double a0[3], const double as0[3],
@@ -160,8 +161,8 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
             double Fn[3], Fs[3];
             const double *r64 = rows.r64 ? rows.r64 + n * rows.stride64 : nullptr;
             const float *r32 = rows.r32 ? rows.r32 + n * rows.stride64 : nullptr;
-            int st = accel<MODE, JAC>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs, enc, dxn,
-                                      false, JAC ? jrec + 6 * n : nullptr);
+            int st = accel<MODE, JAC, G>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs, enc, dxn,
+                                         false, JAC ? jrec + 6 * n : nullptr);
             cnt.evals++;
             if (r64) cnt.node_evals++;
             if (st != KETE_BODY_OK) return st;
@@ -264,7 +265,7 @@ __device__ __forceinline__ LegView leg_view(const NodeTable *nt, int kg)
 // is kept.  Returns a KETE_BODY_* status.
 // JAC: da/dx at the 8 nodes of the attempt go to jrec[6n..6n+5] (see
 // radau_attempt); after an accepted step they describe that step.
-template <int MODE, bool JAC = false>
+template <int MODE, bool JAC = false, int G = 1>
 __device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, const LegView &L,
                                          double x[3], double v[3], double &t, double &dt,
                                          double target, StepState &S, Cnt &cnt,
@@ -274,9 +275,9 @@ __device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, c
     const bool at_start = L.r64 && (t == L.t0) && isfinite(L.h);
     if (!S.have_a0) {
         const double zero[3] = {0.0, 0.0, 0.0};
-        int st = accel<MODE, JAC>(E, F, t, 0.0, at_start ? L.r64 : nullptr,
-                                  at_start ? L.r32 : nullptr, S.close, x, v, S.a0, S.as0, S.enc,
-                                  zero, true, jrec);
+        int st = accel<MODE, JAC, G>(E, F, t, 0.0, at_start ? L.r64 : nullptr,
+                                     at_start ? L.r32 : nullptr, S.close, x, v, S.a0, S.as0,
+                                     S.enc, zero, true, jrec);
         cnt.evals++;
         if (at_start) cnt.node_evals++;
         if (st != KETE_BODY_OK) return st;
@@ -302,8 +303,8 @@ __device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, c
         rows.r32 = L.r32;
     }
     double x1[3], v1[3], err;
-    int st = radau_attempt<MODE, JAC>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, h, rows, x1,
-                                      v1, err, cnt, jrec);
+    int st = radau_attempt<MODE, JAC, G>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, h, rows,
+                                         x1, v1, err, cnt, jrec);
     if (st != KETE_BODY_OK) return st;
     double dt_new;
     if (isfinite(err) && err >= 2.2250738585072014e-308)
@@ -335,9 +336,14 @@ __device__ __forceinline__ void aim_step(const ForceDev &F, double t, double tar
     if (dt == 0.0 || ((dt > 0.0) != (dir > 0.0))) dt = dir * fabs(dt == 0.0 ? F.dt_init : dt);
 }
 
+// warp sums of the lanes' counters into ctr; with G lanes per body only the
+// rank-0 lane of a group counts
+template <int G = 1>
 __device__ __forceinline__ void flush_counters(const Cnt &c, DevCounters *ctr)
 {
-    unsigned long long s = c.steps, r = c.rejected, e = c.evals, it = c.iters, ne = c.node_evals;
+    const unsigned long long w = (LaneGroup<G>::rank() == 0) ? 1ull : 0ull;
+    unsigned long long s = w * c.steps, r = w * c.rejected, e = w * c.evals, it = w * c.iters,
+                       ne = w * c.node_evals;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, o);

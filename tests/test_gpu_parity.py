@@ -330,18 +330,48 @@ def test_work_stealing_equals_static(K, mb1k, ragged_small):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_ragged_population_matches_oracle(K, ragged_small, precision):
+def test_split_phase_is_schedule_independent(K, mb1k, ragged_small, precision):
+    """With long bodies set aside for lane groups, the static and work-stealing
+    first phases still give identical results (deferral depends on the body
+    alone), for every group size; and bodies really are set aside."""
+    from paper_2509_04666_gb300 import kete
+    for w, stops, defer in ((mb1k, W.T0 + np.array([20.0, 40.0, 60.0]), 2),
+                            (ragged_small, np.array([W.T0 + 120.0]), 24)):
+        K.load_ephem(w.ephem.to_bytes())
+        fm = kete.force_model(precision=precision)
+        for split in (4, 8, 16):
+            res = []
+            for kind, block in ((kete.PROP_STATIC, 128), (kete.PROP_WORK_STEALING, 64),
+                                (kete.PROP_WORK_STEALING, 128)):
+                K.set_propagation(precision, kind, block, split, defer)
+                out, status = K.propagate_stops(_dev(w.states), _dev(w.epochs), stops, fm=fm)
+                st = K.get_stats()
+                assert st["prop_split"] == split and st["deferred"] > 0
+                res.append((out.cpu().numpy(), status.cpu().numpy(), st["deferred"]))
+            for out, status, nd in res[1:]:
+                assert np.array_equal(np.nan_to_num(out, nan=7.0), np.nan_to_num(res[0][0], nan=7.0))
+                assert np.array_equal(status, res[0][1]) and nd == res[0][2]
+    K.set_propagation(precision, kete.PROP_WORK_STEALING, 128)
+
+
+@pytest.mark.parametrize("precision,split", [(0, 0), (1, 0), (0, 8), (1, 8), (0, 4)])
+def test_ragged_population_matches_oracle(K, ragged_small, precision, split):
     """Main belt, NEOs (some forced to 0.001-0.01 AU Earth encounters), Trojans
     and comets to e = 0.99 over 365 days in one leg: within 1e-9 AU; in mixed
     precision the forced encounters amplify FP32 rounding of the Earth's pull
-    before the pass, and are held to 5e-9 AU (1 mas seen from 1 AU)."""
+    before the pass, and are held to 5e-9 AU (1 mas seen from 1 AU).  split:
+    bodies past 24 step attempts finish with that many lanes each."""
     from paper_2509_04666_gb300 import kete
     w = ragged_small
     K.load_ephem(w.ephem.to_bytes())
+    K.set_propagation(precision, kete.PROP_WORK_STEALING, 128, split, 24 if split else 0)
     orc = O.Oracle(w.ephem.to_bytes())
     fm = kete.force_model(precision=precision)
     s = _dev(w.states.copy()); e = _dev(w.epochs.copy())
     status = K.propagate(s, e, W.T0 + 365.0, fm=fm)
+    if split:
+        assert K.get_stats()["deferred"] > 0
+    K.set_propagation(precision, kete.PROP_WORK_STEALING, 128)
     status = status.cpu().numpy()
     got = s.cpu().numpy()
     idx = list(np.nonzero(w.labels == 4)[0]) + list(range(0, w.n_bodies, 37))
@@ -360,11 +390,13 @@ def test_autotune_picks_a_variant(K, ragged_small):
     from paper_2509_04666_gb300 import kete
     w = ragged_small
     K.load_ephem(w.ephem.to_bytes())
-    kind, block = K.autotune(_dev(w.states), _dev(w.epochs), np.array([W.T0 + 30.0]),
-                             max_sample=1000)
+    kind, block, split, defer = K.autotune(_dev(w.states), _dev(w.epochs),
+                                           np.array([W.T0 + 30.0]), max_sample=1000)
     assert kind in (kete.PROP_STATIC, kete.PROP_WORK_STEALING) and block in (64, 128)
+    assert split in (0, 4, 8) and (defer > 0) == (split > 0)
     s = _dev(w.states.copy()); e = _dev(w.epochs.copy())
     K.propagate(s, e, W.T0 + 30.0)
     st = K.get_stats()
-    assert (st["prop_kind"], st["prop_block"]) == (kind, block)
+    assert (st["prop_kind"], st["prop_block"], st["prop_split"], st["prop_budget"]) == \
+        (kind, block, split, defer)
     K.set_propagation(kete.FP64, kete.PROP_WORK_STEALING, 128)
