@@ -146,6 +146,7 @@ typedef struct kete_stats {
     int64_t prop_split;          /* lanes per set-aside long body (0: no second phase) */
     int64_t prop_budget;         /* step attempts per stop before a body is set aside */
     int64_t deferred;            /* bodies set aside and finished by the split phase */
+    int64_t prop_order;          /* 1: bodies were taken most expensive first */
 } kete_stats;
 
 /* propagation launch variants (kete_set_propagation, kete_autotune) */
@@ -239,23 +240,28 @@ int kete_get_stats(const kete_ctx *ctx, kete_stats *out);
  * combined by shuffles).  Which bodies are set aside depends on each body
  * alone, so the static and work-stealing schedules still agree bit for bit;
  * a set-aside body's force sums are added in another order than in one lane
- * (differences at the rounding level).  Default: work stealing, 128, no split.
+ * (differences at the rounding level).  cost_order != 0: lanes take the bodies
+ * most expensive first (cost estimated from each body's heliocentric conic:
+ * steps ~ integral dt / r^1.5), so a warp holds bodies of similar cost; this
+ * changes only the schedule, not any result.  Default: work stealing, 128, no
+ * split, cost order.
  * Errors: BAD_ARG. */
 int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block, int split_lanes,
-                         int defer_steps);
+                         int defer_steps, int cost_order);
 
-/* Autotuner: time every launch variant (static 128; work stealing 64 and 128;
- * work stealing 128 with long bodies set aside after 64 attempts per stop for
- * 8 or 4 lanes each, or after 24 for 8 lanes) on an evenly strided sample of up
- * to `max_sample` of the n bodies (device states [6][n] / epochs [n], not
- * modified) propagated along the chain of stops (host, ascending) with force
- * model fm, keep the fastest for fm's precision, and report it in *kind,
- * *block, *split_lanes, *defer_steps (host, each may be NULL).
+/* Autotuner: time every launch variant (static 128, work stealing 64 and 128,
+ * each in index and in cost order; work stealing 128 in cost order with long
+ * bodies set aside after 64 attempts per stop for 8 or 4 lanes each, or after
+ * 24 for 8 lanes) on an evenly strided sample of up to `max_sample` of the n
+ * bodies (device states [6][n] / epochs [n], not modified) propagated along
+ * the chain of stops (host, ascending) with force model fm, keep the fastest
+ * for fm's precision, and report it in *kind, *block, *split_lanes,
+ * *defer_steps, *cost_order (host, each may be NULL).
  * Errors: BAD_ARG, NO_EPHEM, NOMEM, CUDA. */
 int kete_autotune(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
                   const double *stops, int64_t n_stops, const kete_force_model *fm,
                   int64_t max_sample, int32_t *kind, int32_t *block, int32_t *split_lanes,
-                  int32_t *defer_steps);
+                  int32_t *defer_steps, int32_t *cost_order);
 
 /* One astrometric observation of one body (48 bytes). */
 typedef struct kete_obs {

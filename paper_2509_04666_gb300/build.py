@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkete_gpu.so")
 PEAK_LIB = os.path.join(HERE, "libkete_peak.so")
 SOURCES = ["kete_prop.cu", "kete_fov.cu", "kete_scan.cu", "kete_abi.cu", "kete_noalloc.cu",
-           "kete_adjoint.cu"]
+           "kete_adjoint.cu", "kete_order.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC"]
 

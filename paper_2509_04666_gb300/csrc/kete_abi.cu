@@ -16,6 +16,7 @@
 #include "kete_adjoint.h"
 #include "kete_fov.h"
 #include "kete_impl.h"
+#include "kete_order.h"
 
 using namespace kete;
 
@@ -29,7 +30,8 @@ enum Slot {
     S_HITTMP, S_FRAMECNT, S_FRAMEOFF, S_FRAMECUR, S_HITGROUP, S_MAXRAD, S_NT_T0, S_NT_H,
     S_NT_R64, S_NT_R32, S_XSUN, S_XOBSREL, S_NEXTBODY, S_TUNE_ST, S_TUNE_EP, S_TUNE_OUT,
     S_ADJ_REC, S_ADJ_NREC, S_ADJ_NBAT, S_ADJ_BIDX, S_ADJ_YREF, S_ADJ_GJUMP, S_ADJ_STATUS,
-    S_KSTOP, S_DEFER_LIST, S_DEFER_CNT,
+    S_KSTOP, S_DEFER_LIST, S_DEFER_CNT, S_ORDER, S_ORDER_KEY, S_ORDER_HIST, S_ORDER_OFF,
+    S_ORDER_SCAN, S_ORDER_N, S_ADJ_TEND,
     S_NSLOTS
 };
 
@@ -58,7 +60,8 @@ struct kete_ctx {
     // phase timers: pairs of events per phase (prep, candidates, exact, order)
     std::vector<cudaEvent_t> phase_ev[4];
     int phase_n[4] = {0, 0, 0, 0};
-    PropVariant var[2] = {{PROP_WORK_STEALING, 128}, {PROP_WORK_STEALING, 128}};   // per precision
+    PropVariant var[2] = {{PROP_WORK_STEALING, 128, 0, 0, 1},
+                          {PROP_WORK_STEALING, 128, 0, 0, 1}};   // per precision
 };
 
 enum Phase { PH_PREP = 0, PH_CAND = 1, PH_EXACT = 2, PH_ORDER = 3 };
@@ -394,6 +397,11 @@ static int make_force(kete_ctx *ctx, const kete_force_model *fm_in, ForceDev &F)
         F.pole[m][1] = ce * ey + se * ez;
         F.pole[m][2] = -se * ey + ce * ez;
     }
+    for (int m = 0; m < KETE_MAX_BODIES; m++) {
+        F.gm32[m] = (float)ctx->E.gm[m];
+        F.j2k32[m] = (float)F.j2k[m];
+        for (int c = 0; c < 3; c++) F.pole32[m][c] = (float)F.pole[m][c];
+    }
     F.eps = fm.eps;
     F.eps_pc = fm.eps_pc;
     F.safety = fm.safety;
@@ -415,6 +423,35 @@ extern "C" int kete_ephem_eval(kete_ctx *ctx, const double *t, int64_t n, int bo
     return KETE_OK;
 }
 
+// Bodies (states [6][stride] SoA, epochs [n], device) most expensive first
+// over [epoch, end]: end = the last stop (stops_dev, device) or t_end_i[i]
+// (device) per body.  *order_n receives a device copy of n, the kernels'
+// queue length.
+static int cost_order(kete_ctx *ctx, const double *states, int64_t stride, const double *epochs,
+                      int64_t n, const double *stops_dev, int n_stops, const double *t_end_i,
+                      int32_t **order, unsigned long long **order_n)
+{
+    OrderScratch s;
+    const size_t nh = order_hist_elems(n);
+    GET(S_ORDER, n, *order);
+    GET(S_ORDER_KEY, n, s.key);
+    GET(S_ORDER_HIST, nh, s.hist);
+    GET(S_ORDER_OFF, nh + 1, s.off);
+    GET(S_ORDER_SCAN, scan_tmp_elems((int64_t)nh), s.scan_tmp);
+    GET(S_ORDER_N, 1, *order_n);
+    double t_end = 0.0;
+    if (!t_end_i) {
+        CUDA_TRY(cudaMemcpyAsync(&t_end, stops_dev + (n_stops - 1), sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    const unsigned long long nn = (unsigned long long)n;
+    CUDA_TRY(cudaMemcpyAsync(*order_n, &nn, sizeof(nn), cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(order_by_cost(ctx->E, states, stride, epochs, n, t_end, t_end_i, s, *order,
+                           ctx->stream));
+    return KETE_OK;
+}
+
 // Launch the propagation kernel with the context's variant for F's precision.
 static int propagate(kete_ctx *ctx, const ForceDev &F, ChainState cs, const double *stops_dev,
                      int n_stops, double *out, int64_t stride, bool keep_on_fail,
@@ -432,12 +469,20 @@ static int propagate(kete_ctx *ctx, const ForceDev &F, ChainState cs, const doub
         defer.next = cnt + 1;
         dp = &defer;
     }
+    int32_t *order = nullptr;
+    unsigned long long *order_n = nullptr;
+    if (var.order) {
+        int r = cost_order(ctx, cs.w, cs.n, cs.w + 6 * cs.n, cs.n, stops_dev, n_stops, nullptr,
+                           &order, &order_n);
+        if (r != KETE_OK) return r;
+    }
     ctx->stats.prop_kind = var.kind;
     ctx->stats.prop_block = var.block;
     ctx->stats.prop_split = var.split;
     ctx->stats.prop_budget = var.budget;
+    ctx->stats.prop_order = var.order;
     CUDA_TRY(launch_propagate(ctx->E, F, cs, stops_dev, n_stops, out, stride, keep_on_fail,
-                              ctx->d_ctr, ctx->stream, nt, leg0, var, next, dp));
+                              ctx->d_ctr, ctx->stream, nt, leg0, var, next, dp, order, order_n));
     return KETE_OK;
 }
 
@@ -879,7 +924,7 @@ extern "C" int kete_propagate_noalloc(kete_ctx *ctx, double *states, double *epo
 }
 
 extern "C" int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block,
-                                    int split_lanes, int defer_steps)
+                                    int split_lanes, int defer_steps, int cost_order_on)
 {
     if (!ctx) return KETE_ERR_BAD_ARG;
     const bool split_ok = split_lanes == 0 || split_lanes == 1 || split_lanes == 4 ||
@@ -893,6 +938,7 @@ extern "C" int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int 
     PropVariant v{kind, block};
     v.split = split_lanes > 1 ? split_lanes : 0;
     v.budget = v.split ? defer_steps : 0;
+    v.order = cost_order_on ? 1 : 0;
     ctx->var[precision == KETE_MIXED ? 1 : 0] = v;
     return KETE_OK;
 }
@@ -900,7 +946,7 @@ extern "C" int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int 
 extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
                              const double *stops, int64_t n_stops, const kete_force_model *fm,
                              int64_t max_sample, int32_t *kind, int32_t *block,
-                             int32_t *split_lanes, int32_t *defer_steps)
+                             int32_t *split_lanes, int32_t *defer_steps, int32_t *cost_order)
 {
     if (!ctx) return KETE_ERR_BAD_ARG;
     if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
@@ -924,16 +970,22 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
     GET(S_STOPS, n_stops, d_stops);
     CUDA_TRY(cudaMemcpyAsync(d_stops, stops, n_stops * sizeof(double), cudaMemcpyHostToDevice, st));
     CUDA_TRY(launch_gather_bodies(states, epochs, n, stride, m, sst, sep, st));
-    PropVariant cands[6] = {{PROP_STATIC, 128}, {PROP_WORK_STEALING, 64},
-                            {PROP_WORK_STEALING, 128}, {PROP_WORK_STEALING, 128},
-                            {PROP_WORK_STEALING, 128}, {PROP_WORK_STEALING, 128}};
-    cands[3].split = 8;
-    cands[3].budget = 64;
-    cands[4].split = 4;
-    cands[4].budget = 64;
-    cands[5].split = 8;
-    cands[5].budget = 24;
-    const int n_cands = 6;
+    // schedules x cost order, then the split variants (with cost order)
+    PropVariant cands[9];
+    const int kinds[3][2] = {{PROP_STATIC, 128}, {PROP_WORK_STEALING, 64}, {PROP_WORK_STEALING, 128}};
+    int n_cands = 0;
+    for (int o = 0; o < 2; o++)
+        for (int q = 0; q < 3; q++) {
+            cands[n_cands] = PropVariant{kinds[q][0], kinds[q][1]};
+            cands[n_cands++].order = o;
+        }
+    const int splits[3][2] = {{8, 64}, {4, 64}, {8, 24}};
+    for (int q = 0; q < 3; q++) {
+        cands[n_cands] = PropVariant{PROP_WORK_STEALING, 128};
+        cands[n_cands].split = splits[q][0];
+        cands[n_cands].budget = splits[q][1];
+        cands[n_cands++].order = 1;
+    }
     const PropVariant saved = ctx->var[F.precision == KETE_MIXED ? 1 : 0];
     float best_ms = 1e30f;
     PropVariant best = saved;
@@ -966,6 +1018,7 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
     if (block) *block = best.block;
     if (split_lanes) *split_lanes = best.split;
     if (defer_steps) *defer_steps = best.budget;
+    if (cost_order) *cost_order = best.order;
     return KETE_OK;
 }
 
@@ -1034,10 +1087,22 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
         unsigned long long *next = nullptr;
         GET(S_NEXTBODY, 1, next);
         int launches = 0;
+        double *t_end;
+        GET(S_ADJ_TEND, chunk, t_end);
+        const bool order_on = ctx->var[0].order != 0;
         for (int64_t i0 = 0; i0 < n; i0 += chunk) {
             const int64_t nc = std::min(chunk, n - i0);
             prop_event(ctx, true);
-            CUDA_TRY(launch_adjoint_forward(ctx->E, F, B, P, i0, nc, next, ctx->stream));
+            int32_t *order = nullptr;
+            if (order_on) {   // most expensive bodies first (schedule only)
+                unsigned long long *order_n;
+                CUDA_TRY(launch_adjoint_last_epoch(P, i0, nc, t_end, ctx->stream));
+                int r2 = cost_order(ctx, states + i0, n, epochs + i0, nc, nullptr, 0, t_end,
+                                    &order, &order_n);
+                if (r2 != KETE_OK) return r2;
+                launches += 5;
+            }
+            CUDA_TRY(launch_adjoint_forward(ctx->E, F, B, P, i0, nc, next, ctx->stream, order));
             prop_event(ctx, false);
             CUDA_TRY(launch_adjoint_observe(ctx->E, B, P, i0, nc, ctx->stream));
             launches += 2;

@@ -157,7 +157,7 @@ __device__ __forceinline__ void walk_next_ckpt(StopWalk &w, double epoch0, doubl
 // persistent grid, a lane whose body is done takes the next one from *next.
 __global__ void __launch_bounds__(128)
 k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc,
-              unsigned long long *__restrict__ next, int refill)
+              unsigned long long *__restrict__ next, int refill, const int32_t *__restrict__ order)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -190,7 +190,7 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
                     mine = first ? (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x
                                  : (unsigned long long)nc;
                 if (mine < (unsigned long long)nc) {
-                    i = (int64_t)mine;
+                    i = order ? (int64_t)order[mine] : (int64_t)mine;
                     const int64_t gi = i0 + i;
                     o = P.obs + gi * P.m;
                     bool fin = true;
@@ -726,9 +726,27 @@ k_adj_backward(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
 // ---------------------------------------------------------------------------
 static unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
+// last observation epoch of each body of the chunk (its chain's end)
+__global__ void k_adj_last_epoch(AdjProblem P, int64_t i0, int64_t nc, double *__restrict__ t_end)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const kete_obs *o = P.obs + (i0 + i) * P.m;
+    const int mi = obs_count(o, P.m);
+    t_end[i] = mi > 0 ? o[mi - 1].epoch : P.epochs[i0 + i];
+}
+
+cudaError_t launch_adjoint_last_epoch(const AdjProblem &P, int64_t i0, int64_t nc, double *t_end,
+                                      cudaStream_t st)
+{
+    if (nc > 0) k_adj_last_epoch<<<blocks_for(nc, 256), 256, 0, st>>>(P, i0, nc, t_end);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_forward(const EphemDev &E, const ForceDev &F, const AdjBuffers &B,
                                    const AdjProblem &P, int64_t i0, int64_t nc,
-                                   unsigned long long *next, cudaStream_t st)
+                                   unsigned long long *next, cudaStream_t st,
+                                   const int32_t *order)
 {
     if (nc <= 0) return cudaGetLastError();
     int64_t grid = blocks_for(nc, 128);
@@ -744,7 +762,7 @@ cudaError_t launch_adjoint_forward(const EphemDev &E, const ForceDev &F, const A
         if (grid > persistent) grid = persistent;
         refill = 1;
     }
-    k_adj_forward<<<(unsigned)grid, 128, 0, st>>>(E, F, B, P, i0, nc, next, refill);
+    k_adj_forward<<<(unsigned)grid, 128, 0, st>>>(E, F, B, P, i0, nc, next, refill, order);
     return cudaGetLastError();
 }
 

@@ -41,10 +41,15 @@ struct AdjBuffers {
 };
 
 cudaError_t upload_adjoint_tables(cudaStream_t st);
-// next != null: persistent grid with work stealing from the counter *next
+// next != null: persistent grid with work stealing from the counter *next;
+// order != null: lanes take the chunk's bodies in that order
 cudaError_t launch_adjoint_forward(const EphemDev &E, const ForceDev &F, const AdjBuffers &B,
                                    const AdjProblem &P, int64_t i0, int64_t nc,
-                                   unsigned long long *next, cudaStream_t st);
+                                   unsigned long long *next, cudaStream_t st,
+                                   const int32_t *order = nullptr);
+// t_end[i] = the last observation epoch of chunk body i (its epoch if none)
+cudaError_t launch_adjoint_last_epoch(const AdjProblem &P, int64_t i0, int64_t nc, double *t_end,
+                                      cudaStream_t st);
 cudaError_t launch_adjoint_observe(const EphemDev &E, const AdjBuffers &B, const AdjProblem &P,
                                    int64_t i0, int64_t nc, cudaStream_t st);
 cudaError_t launch_adjoint_backward(const AdjBuffers &B, const AdjProblem &P, int64_t i0,

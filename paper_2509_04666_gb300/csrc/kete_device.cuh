@@ -440,10 +440,10 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
         const bool gr = F.gr_mask & 1u, j2 = F.j2_mask & 1u;
         if (gr || j2) {
             float w[3] = {vf[0] - (float)sun[3], vf[1] - (float)sun[4], vf[2] - (float)sun[5]};
-            float P[3] = {(float)F.pole[0][0], (float)F.pole[0][1], (float)F.pole[0][2]};
-            mass_terms<float>((float)E.gm[0], (float)F.j2k[0], P, false, gr, j2, df, w, af);
+            mass_terms<float>(F.gm32[0], F.j2k32[0], F.pole32[0], false, gr, j2, df, w, af);
         }
     }
+    const float sunf[3] = {(float)sun[0], (float)sun[1], (float)sun[2]};
     const float tau32 = row64 ? 0.f : (float)g.tau;
     for (int m = (rk == 0 ? G : rk); m < E.n_bodies; m += G) {
         if (!((F.active_mask >> m) & 1u)) continue;
@@ -454,7 +454,7 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
             for (int q = 0; q < 6; q++) st[q] = __ldg(row32 + 6 * m + q);
         } else {
             cheb_state32(E, m, g.s, tau32, st, gr);
-            st[0] -= (float)sun[0]; st[1] -= (float)sun[1]; st[2] -= (float)sun[2];
+            st[0] -= sunf[0]; st[1] -= sunf[1]; st[2] -= sunf[2];
         }
         float r[3] = {df[0] - st[0], df[1] - st[1], df[2] - st[2]};
         if (detect && r[0] * r[0] + r[1] * r[1] + r[2] * r[2] < (float)(4.0 * kCloseAu * kCloseAu))
@@ -487,8 +487,7 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
             continue;
         }
         float w[3] = {vf[0] - st[3], vf[1] - st[4], vf[2] - st[5]};
-        float P[3] = {(float)F.pole[m][0], (float)F.pole[m][1], (float)F.pole[m][2]};
-        mass_terms<float>((float)E.gm[m], (float)F.j2k[m], P, true, gr, j2, r, w, af);
+        mass_terms<float>(F.gm32[m], F.j2k32[m], F.pole32[m], true, gr, j2, r, w, af);
     }
     if (G > 1) {
 #pragma unroll

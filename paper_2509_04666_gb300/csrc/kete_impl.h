@@ -29,6 +29,10 @@ struct ForceDev {
     double eps, eps_pc, safety, dt_init;
     int32_t max_iter, pad;
     int64_t max_steps;
+    // FP32 copies for the mixed-precision planetary terms (rounded once here)
+    float gm32[KETE_MAX_BODIES];
+    float j2k32[KETE_MAX_BODIES];
+    float pole32[KETE_MAX_BODIES][3];
 };
 
 // device counters accumulated by the kernels
@@ -65,6 +69,7 @@ struct ChainState {
 struct PropQueue {
     const int32_t *list = nullptr;               // bodies to take; null: 0..n-1
     const unsigned long long *list_n = nullptr;  // how many (device)
+    int resume = 0;                              // bodies resume at cs.kstop (else stop 0)
     int32_t *defer = nullptr;                    // set-aside bodies are appended here
     unsigned long long *defer_n = nullptr;
     int budget = 0;                              // step attempts per stop reached
@@ -93,6 +98,7 @@ struct PropVariant {
     int block;        // threads per block (<= 128)
     int split = 0;    // lanes per body for long bodies (4, 8, 16; 0 or 1: none)
     int budget = 0;   // step attempts per stop after which a body is set aside
+    int order = 0;    // take bodies most expensive first (kete_order.cu)
 };
 cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
                              const double *stops_dev, int n_stops, double *out,
@@ -100,7 +106,8 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
                              cudaStream_t st, const NodeTable *nt = nullptr, int leg0 = 0,
                              PropVariant var = PropVariant{PROP_STATIC, 128},
                              unsigned long long *next_body = nullptr,
-                             PropDefer *defer = nullptr);
+                             PropDefer *defer = nullptr, const int32_t *order = nullptr,
+                             const unsigned long long *order_n = nullptr);
 int propagate_ws_blocks(int block, int mode);
 cudaError_t launch_gather_bodies(const double *st, const double *ep, int64_t n, int64_t stride,
                                  int64_t m, double *dst, double *dep, cudaStream_t s);

@@ -35,7 +35,7 @@ void upload_radau_tables(cudaStream_t st) { upload_step_tables(st); }
 //   needing hundreds of steps no longer idles the rest of its warp.
 // Both schedules run the same instructions per body: results are identical.
 // Queue q: the bodies come from q.list (q.list_n of them, device) instead of
-// 0..n-1, each resuming at its saved stop cs.kstop[i]; with q.defer set, a
+// 0..n-1, resuming at their saved stops cs.kstop[i] if q.resume; with q.defer set, a
 // body that has made more than q.budget step attempts per stop reached is
 // set aside at its next step boundary (state and stop saved, index appended
 // to q.defer) for a second launch with more lanes per body.
@@ -90,7 +90,7 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
                     t = cs.w[6 * n + i];
                     dt = cs.w[7 * n + i];
                     status = cs.status[i];
-                    k = q.list ? cs.kstop[i] : 0;
+                    k = q.resume ? cs.kstop[i] : 0;
                     attempts = 0;
                     body_attempts = 0;
                     S.have_a0 = false;
@@ -340,7 +340,8 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
                              const double *stops_dev, int n_stops, double *out,
                              int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
                              cudaStream_t st, const NodeTable *nt, int leg0, PropVariant var,
-                             unsigned long long *next_body, PropDefer *defer)
+                             unsigned long long *next_body, PropDefer *defer,
+                             const int32_t *order, const unsigned long long *order_n)
 {
     if (cs.n <= 0 || n_stops <= 0) return cudaGetLastError();
     NodeTable t{};
@@ -359,6 +360,10 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
     }
     // phase 1: one lane per body; with a split variant, long bodies are set aside
     PropQueue q{};
+    if (order && order_n) {
+        q.list = order;
+        q.list_n = order_n;
+    }
     const bool split = var.split > 1 && var.budget > 0 && defer && cs.kstop;
     if (split) {
         cudaError_t e = cudaMemsetAsync(defer->count, 0, sizeof(unsigned long long), st);
@@ -379,6 +384,7 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
     PropQueue q2{};
     q2.list = defer->list;
     q2.list_n = defer->count;
+    q2.resume = 1;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -59,7 +59,7 @@ class Stats(C.Structure):
                 ("launches", C.c_int64), ("prep_ms", C.c_double), ("cand_ms", C.c_double),
                 ("exact_ms", C.c_double), ("order_ms", C.c_double), ("node_evals", C.c_int64),
                 ("prop_kind", C.c_int64), ("prop_block", C.c_int64), ("prop_split", C.c_int64),
-                ("prop_budget", C.c_int64), ("deferred", C.c_int64)]
+                ("prop_budget", C.c_int64), ("deferred", C.c_int64), ("prop_order", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,11 +95,12 @@ def lib():
                                      C.POINTER(SurveyOpts), vp, i64, C.POINTER(i64), vp]
         L.kete_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.kete_propagate_noalloc.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(ForceModel), vp]
-        L.kete_set_propagation.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.kete_set_propagation.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                           C.c_int]
         L.kete_autotune.argtypes = [vp, vp, vp, i64, C.POINTER(C.c_double), i64,
                                     C.POINTER(ForceModel), i64, C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                                    C.POINTER(C.c_int32)]
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.kete_adjoint.argtypes = [vp, vp, vp, i64, vp, C.c_int32, C.POINTER(ForceModel),
                                    C.POINTER(SurveyOpts), dbl, vp, vp, vp, vp]
         _lib = L
@@ -299,9 +300,9 @@ class Kete:
         return loss, g, pr, status
 
     def set_propagation(self, precision: int, kind: int, block: int = 128, split: int = 0,
-                        defer_steps: int = 0):
+                        defer_steps: int = 0, cost_order: bool = True):
         self._check(lib().kete_set_propagation(self._h, precision, kind, block, split,
-                                               defer_steps))
+                                               defer_steps, 1 if cost_order else 0))
 
     def autotune(self, states, epochs, stops, fm=None, max_sample=32768):
         """Time the propagation launch variants on a body sample; keep the fastest."""
@@ -309,13 +310,13 @@ class Kete:
         _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
         st = np.ascontiguousarray(stops, dtype=np.float64)
         fm = fm or force_model()
-        kind = C.c_int32(); block = C.c_int32(); split = C.c_int32(); defer = C.c_int32()
+        kind, block, split, defer, order = (C.c_int32() for _ in range(5))
         self._sync_stream()
         self._check(lib().kete_autotune(self._h, states.data_ptr(), epochs.data_ptr(), n,
                                         st.ctypes.data_as(C.POINTER(C.c_double)), len(st),
                                         C.byref(fm), max_sample, C.byref(kind), C.byref(block),
-                                        C.byref(split), C.byref(defer)))
-        return kind.value, block.value, split.value, defer.value
+                                        C.byref(split), C.byref(defer), C.byref(order)))
+        return kind.value, block.value, split.value, defer.value, order.value
 
     def get_stats(self) -> dict:
         s = Stats()

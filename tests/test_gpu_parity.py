@@ -317,11 +317,13 @@ def test_work_stealing_equals_static(K, mb1k, ragged_small):
     for w, stops in ((mb1k, W.T0 + np.arange(1.5, 60.0, 3.0)), (ragged_small, np.array([W.T0 + 120.0]))):
         K.load_ephem(w.ephem.to_bytes())
         res = []
-        for kind, block in ((kete.PROP_STATIC, 128), (kete.PROP_WORK_STEALING, 64),
-                            (kete.PROP_WORK_STEALING, 128)):
-            K.set_propagation(kete.FP64, kind, block)
+        for kind, block, order in ((kete.PROP_STATIC, 128, False), (kete.PROP_WORK_STEALING, 64, False),
+                                   (kete.PROP_WORK_STEALING, 128, False), (kete.PROP_STATIC, 128, True),
+                                   (kete.PROP_WORK_STEALING, 128, True)):
+            K.set_propagation(kete.FP64, kind, block, cost_order=order)
             out, status = K.propagate_stops(_dev(w.states), _dev(w.epochs), stops)
-            assert K.get_stats()["prop_kind"] == kind
+            st = K.get_stats()
+            assert st["prop_kind"] == kind and st["prop_order"] == int(order)
             res.append((out.cpu().numpy(), status.cpu().numpy()))
         for out, status in res[1:]:
             assert np.array_equal(np.nan_to_num(out, nan=7.0), np.nan_to_num(res[0][0], nan=7.0))
@@ -390,13 +392,13 @@ def test_autotune_picks_a_variant(K, ragged_small):
     from paper_2509_04666_gb300 import kete
     w = ragged_small
     K.load_ephem(w.ephem.to_bytes())
-    kind, block, split, defer = K.autotune(_dev(w.states), _dev(w.epochs),
-                                           np.array([W.T0 + 30.0]), max_sample=1000)
+    kind, block, split, defer, order = K.autotune(_dev(w.states), _dev(w.epochs),
+                                                  np.array([W.T0 + 30.0]), max_sample=1000)
     assert kind in (kete.PROP_STATIC, kete.PROP_WORK_STEALING) and block in (64, 128)
-    assert split in (0, 4, 8) and (defer > 0) == (split > 0)
+    assert split in (0, 4, 8) and (defer > 0) == (split > 0) and order in (0, 1)
     s = _dev(w.states.copy()); e = _dev(w.epochs.copy())
     K.propagate(s, e, W.T0 + 30.0)
     st = K.get_stats()
-    assert (st["prop_kind"], st["prop_block"], st["prop_split"], st["prop_budget"]) == \
-        (kind, block, split, defer)
+    assert (st["prop_kind"], st["prop_block"], st["prop_split"], st["prop_budget"],
+            st["prop_order"]) == (kind, block, split, defer, order)
     K.set_propagation(kete.FP64, kete.PROP_WORK_STEALING, 128)
