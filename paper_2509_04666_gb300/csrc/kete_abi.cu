@@ -57,6 +57,7 @@ struct kete_ctx {
     std::vector<cudaEvent_t> ev;    // pool: [0] start, [1] end, then pairs for propagation
     int n_sm = 152;
     int pending_prop_pairs = 0;
+    int64_t extra_launches = 0;     // ordering and second-phase launches of this call
     // phase timers: pairs of events per phase (prep, candidates, exact, order)
     std::vector<cudaEvent_t> phase_ev[4];
     int phase_n[4] = {0, 0, 0, 0};
@@ -157,6 +158,7 @@ static void stats_begin(kete_ctx *ctx)
 {
     std::memset(&ctx->stats, 0, sizeof(ctx->stats));
     ctx->pending_prop_pairs = 0;
+    ctx->extra_launches = 0;
     for (int q = 0; q < 4; q++) ctx->phase_n[q] = 0;
     cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream);
     cudaEventRecord(event_at(ctx, 0), ctx->stream);
@@ -198,6 +200,7 @@ static void stats_collect(kete_ctx *ctx)
     ctx->stats.node_evals = (int64_t)ctx->h_ctr->node_evals;
     ctx->stats.deferred = (int64_t)ctx->h_ctr->deferred;
     ctx->stats.prop_launches = ctx->pending_prop_pairs;
+    ctx->stats.launches += ctx->extra_launches;
     ctx->pending_prop_pairs = 0;
     double *dst[4] = {&ctx->stats.prep_ms, &ctx->stats.cand_ms, &ctx->stats.exact_ms,
                       &ctx->stats.order_ms};
@@ -449,6 +452,7 @@ static int cost_order(kete_ctx *ctx, const double *states, int64_t stride, const
     CUDA_TRY(cudaMemcpyAsync(*order_n, &nn, sizeof(nn), cudaMemcpyHostToDevice, ctx->stream));
     CUDA_TRY(order_by_cost(ctx->E, states, stride, epochs, n, t_end, t_end_i, s, *order,
                            ctx->stream));
+    ctx->extra_launches += order_launches(n);
     return KETE_OK;
 }
 
@@ -483,6 +487,7 @@ static int propagate(kete_ctx *ctx, const ForceDev &F, ChainState cs, const doub
     ctx->stats.prop_order = var.order;
     CUDA_TRY(launch_propagate(ctx->E, F, cs, stops_dev, n_stops, out, stride, keep_on_fail,
                               ctx->d_ctr, ctx->stream, nt, leg0, var, next, dp, order, order_n));
+    if (dp) ctx->extra_launches += 1;   // the second phase
     return KETE_OK;
 }
 
@@ -872,7 +877,7 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
     if ((int64_t)hits_total > capacity) {
         r = stats_end(ctx);
         stats_collect(ctx);
-        ctx->stats.launches = launches;
+        ctx->stats.launches = launches + ctx->extra_launches;
         return fail(ctx, KETE_ERR_CAPACITY, "hit buffer holds %lld, %llu needed", (long long)capacity,
                     hits_total);
     }
@@ -895,7 +900,7 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
     ctx->stats.n_exposures = ne;
     ctx->stats.n_candidates = (int64_t)cands_total;
     ctx->stats.n_hits = (int64_t)hits_total;
-    ctx->stats.launches = launches;
+    ctx->stats.launches = launches + ctx->extra_launches;
     return KETE_OK;
 }
 
@@ -1100,7 +1105,7 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
                 int r2 = cost_order(ctx, states + i0, n, epochs + i0, nc, nullptr, 0, t_end,
                                     &order, &order_n);
                 if (r2 != KETE_OK) return r2;
-                launches += 5;
+                launches += 1;
             }
             CUDA_TRY(launch_adjoint_forward(ctx->E, F, B, P, i0, nc, next, ctx->stream, order));
             prop_event(ctx, false);

@@ -101,6 +101,7 @@ cudaError_t fov_order_hits(const kete_hit *tmp, unsigned long long nh, const int
 // kete_scan.cu: exclusive prefix sum of int32 counts into int64 offsets
 // (out has n+1 entries; out[n] = total).  tmp must hold scan_tmp_elems(n).
 size_t scan_tmp_elems(int64_t n);
+int scan_launches(int64_t n);   // kernel launches of exclusive_scan over n
 cudaError_t exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *tmp,
                            cudaStream_t st);
 

@@ -120,6 +120,11 @@ cudaError_t order_by_cost(const EphemDev &E, const double *states, int64_t strid
     return cudaGetLastError();
 }
 
+int order_launches(int64_t n)
+{
+    return n <= 0 ? 0 : 3 + scan_launches((int64_t)order_hist_elems(n));
+}
+
 size_t order_hist_elems(int64_t n)
 {
     return (size_t)kOrderBuckets * (size_t)((n + kOrderTile - 1) / kOrderTile);

@@ -17,6 +17,7 @@ struct OrderScratch {
 };
 
 size_t order_hist_elems(int64_t n);
+int order_launches(int64_t n);   // kernel launches of order_by_cost over n bodies
 
 // order[0..n) = the n bodies (states [6][stride] SoA, epochs [n]) most
 // expensive first over [epoch, t_end] (t_end_i: per-body end epochs, or null

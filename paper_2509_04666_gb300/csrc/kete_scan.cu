@@ -85,6 +85,12 @@ static cudaError_t scan_impl(const T *in, int64_t n, int64_t *out, int64_t *tmp,
     return cudaGetLastError();
 }
 
+int scan_launches(int64_t n)
+{
+    int64_t nb = tiles_of(n);
+    return nb <= 1 ? 1 : 2 + scan_launches(nb);
+}
+
 cudaError_t exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *tmp,
                            cudaStream_t st)
 {
