@@ -36,14 +36,16 @@ METRIC = ("body-days propagated/s and body×frame FoV checks/s at ≤1 mas vs FP
           "1 GB300")
 MAS = math.radians(1.0 / 3.6e6)
 
-# DRAM traffic of one k_propagate launch from an ncu capture (profiles/
-# k_propagate_wise1y.md); valid only while the kernel source is unchanged.
-PROFILED_TRAFFIC = {"src_sha": "805ce17aa16aa3c6", "bytes_per_body_stop": 23.1}
+# DRAM traffic of one k_propagate launch from an ncu capture of a smaller case
+# of the same workload (profiles/k_propagate_wise1y.md: 100k bodies x 20 stops,
+# 397 MB), per body-stop, scaled to the full launch by its body-stops; valid
+# only while the kernel source is unchanged.
+PROFILED_TRAFFIC = {"src_sha": "32c57162fe0a6722", "bytes_per_body_stop": 198.6}
 
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("kete_prop.cu", "kete_device.cuh"):
+    for f in ("kete_prop.cu", "kete_device.cuh", "kete_step.cuh", "kete_order.cu"):
         with open(os.path.join(ROOT, "paper_2509_04666_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
