@@ -483,20 +483,48 @@ struct ExactCtx {
     double cos_eps, sin_eps;
 };
 
-// Position at t_ref + dt_obs - tau: heliocentric universal-variable two-body
-// from the batch state, plus the Sun at t_obs - tau taken from the Sun's state
-// at the exposure epoch, S - V tau (the neglected term, a_sun tau^2 / 2 with
-// |a_sun| ~ 1e-8 AU/day^2, stays below 2e-11 AU for tau < 0.06 day).
-__device__ __forceinline__ bool twobody_pos(double mu, double sqmu, const double hr[3],
-                                            const double hv[3], const double *sun_obs,
-                                            double dt_obs, double tau, double &chi, double pos[3])
+// Position at t_ref + dt_obs - tau.  The heliocentric two-body state is
+// solved once, at dt_obs (universal variables from the batch state); the
+// light-time iterations move it back by tau with its Taylor expansion,
+//   r(dt_obs - tau) = r - v tau + a tau^2 / 2 - j tau^3 / 6,
+// a = -mu r / |r|^3, j = da/dt.  The first neglected term, tau^4 |r4| / 24
+// with the fourth derivative |r4| ~ 3 (mu/|r|^3)^2 |r|, stays below 2e-13 AU
+// for bodies beyond 0.2 AU of the Sun seen from near 1 AU
+// (tau < (|r| + 1.1 AU) / c), and below 1e-17 AU in the main belt.  The Sun
+// at t_obs - tau comes from its state at the exposure epoch, S - V tau (the
+// neglected term, a_sun tau^2 / 2 with |a_sun| ~ 1e-8 AU/day^2, stays below
+// 2e-11 AU for tau < 0.06 day).
+struct TwoBodyLT {
+    double r[3], mv[3], a2[3], mj6[3];   // r, -v, a/2, -j/6 at dt_obs
+};
+
+__device__ __forceinline__ bool twobody_at(double mu, double sqmu, const double hr[3],
+                                           const double hv[3], double dt_obs, double &chi,
+                                           TwoBodyLT &T)
 {
-    double r[3], v[3];
-    bool ok = kepler_uv(mu, sqmu, hr, hv, dt_obs - tau, chi, r, v);
-    pos[0] = fma(-tau, sun_obs[3], sun_obs[0]) + r[0];
-    pos[1] = fma(-tau, sun_obs[4], sun_obs[1]) + r[1];
-    pos[2] = fma(-tau, sun_obs[5], sun_obs[2]) + r[2];
+    double v[3];
+    const bool ok = kepler_uv(mu, sqmu, hr, hv, dt_obs, chi, T.r, v);
+    const double rr = dot3(T.r, T.r);
+    const double rn = sqrt(rr);
+    const double k = -mu / (rr * rn);
+    const double q = 3.0 * dot3(T.r, v) / rr;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        T.mv[c] = -v[c];
+        T.a2[c] = 0.5 * k * T.r[c];
+        T.mj6[c] = -(k / 6.0) * fma(-q, T.r[c], v[c]);
+    }
     return ok;
+}
+
+__device__ __forceinline__ void twobody_pos(const TwoBodyLT &T, const double *sun_obs, double tau,
+                                            double pos[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const double p = fma(fma(fma(T.mj6[c], tau, T.a2[c]), tau, T.mv[c]), tau, T.r[c]);
+        pos[c] = fma(-tau, sun_obs[3 + c], sun_obs[c]) + p;
+    }
 }
 
 __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
@@ -529,15 +557,17 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
             }
             // light delay (Sec. 2): tau0 = |r(t)-o|/c, three fixed iterations
             double chi = 0.0, pos[3];
-            bool ok = twobody_pos(mu, sqmu, hr, hv, sun_obs, dt_obs, 0.0, chi, pos);
+            TwoBodyLT T;
+            const bool ok = twobody_at(mu, sqmu, hr, hv, dt_obs, chi, T);
+            twobody_pos(T, sun_obs, 0.0, pos);
             double u[3] = {pos[0] - o[0], pos[1] - o[1], pos[2] - o[2]};
             double tau = sqrt(dot3(u, u)) * kInvC;
             for (int it = 0; it < 3; it++) {
-                ok &= twobody_pos(mu, sqmu, hr, hv, sun_obs, dt_obs, tau, chi, pos);
+                twobody_pos(T, sun_obs, tau, pos);
                 u[0] = pos[0] - o[0]; u[1] = pos[1] - o[1]; u[2] = pos[2] - o[2];
                 tau = sqrt(dot3(u, u)) * kInvC;
             }
-            ok &= twobody_pos(mu, sqmu, hr, hv, sun_obs, dt_obs, tau, chi, pos);
+            twobody_pos(T, sun_obs, tau, pos);
             u[0] = pos[0] - o[0]; u[1] = pos[1] - o[1]; u[2] = pos[2] - o[2];
             if (!ok) {
                 if (C.status) atomicCAS(&C.status[i], KETE_BODY_OK, KETE_BODY_KEPLER_CAP);
