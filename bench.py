@@ -165,6 +165,23 @@ def oracle_sample(w, n_sample, n_threads=None):
     return sub, hits, dt, nt
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the step time of the slowest
+    replica); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, ms):
+    """Whole-job throughput: every replica processes units_per_rank in the
+    (max-over-ranks) step time ms."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -480,14 +497,10 @@ def run_gb300(args):
     if dist:
         dist.barrier()
     clocks = clk.summary()
-    ms = statistics.mean(times)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(statistics.mean(times), dist, dev)
     n, nf = w.n_bodies, len(w.frames)
-    value = world * n * 365.0 / (ms / 1e3)
-    checks = world * n * nf / (ms / 1e3)
+    value = job_rate(world, n * 365.0, ms)
+    checks = job_rate(world, n * nf, ms)
     # ---- roofline of the dominant kernel (k_propagate, FP64 ALU bound) --------
     s0 = stats[-1]
     mixed = args.precision == "mixed"
