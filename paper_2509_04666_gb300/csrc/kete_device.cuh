@@ -30,6 +30,8 @@ struct RadauTables {
     double rinv[8][8];   // 1 / (h_n - h_k), k < n
     double c[8][7];      // c[n][m]: d b_m / d g_n  (Newton -> power basis)
     double w7[8];        // 1 / prod_{k != n} (h_n - h_k): b6 = g7 = sum_n w7[n] F_n
+    double wx[8][7];     // h_n^(k+1) / ((k+2)(k+3)): weight of b_k in x at node n
+    double wv[8][7];     // h_n^(k+1) / (k+2): weight of b_k in v at node n
 };
 
 // ---------------------------------------------------------------------------

@@ -48,6 +48,15 @@ static inline void fill_radau_tables(RadauTables &t)
         }
         for (int m = 0; m < 7; m++) t.c[n][m] = (m < n) ? poly[m] : 0.0;
     }
+    // predictor weights of the power-basis coefficients at each node
+    for (int n = 0; n < 8; n++) {
+        double sp = kRadauH[n];
+        for (int k = 0; k < 7; k++) {
+            t.wx[n][k] = sp / ((k + 2.0) * (k + 3.0));
+            t.wv[n][k] = sp / (k + 2.0);
+            sp *= kRadauH[n];
+        }
+    }
     // leading coefficient of the interpolant through the 8 nodes
     for (int n = 0; n < 8; n++) {
         double p = 1.0;
@@ -136,26 +145,20 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
             double xn[3], vn[3], dxn[3];
 #pragma unroll
             for (int i = 0; i < 3; i++) {
-                // x(s) = x0 + s h v0 + (s h)^2 [a0/2 + s(b0/6 + s(b1/12 + ... + s b6/72))]
-                double px = b[6][i] * (1.0 / 72.0);
-                px = fma(px, s, b[5][i] * (1.0 / 56.0));
-                px = fma(px, s, b[4][i] * (1.0 / 42.0));
-                px = fma(px, s, b[3][i] * (1.0 / 30.0));
-                px = fma(px, s, b[2][i] * (1.0 / 20.0));
-                px = fma(px, s, b[1][i] * (1.0 / 12.0));
-                px = fma(px, s, b[0][i] * (1.0 / 6.0));
-                px = fma(px, s, a0[i] * 0.5);
+                // x(s) = x0 + s h v0 + (s h)^2 [a0/2 + sum_k b_k s^(k+1) / ((k+2)(k+3))]
+                // v(s) = v0 + s h [a0 + sum_k b_k s^(k+1) / (k+2)]
+                // with the node's weights from the table (smallest terms first)
+                double px = b[6][i] * g_rt.wx[n][6];
+                double pv = b[6][i] * g_rt.wv[n][6];
+#pragma unroll
+                for (int k = 5; k >= 0; k--) {
+                    px = fma(b[k][i], g_rt.wx[n][k], px);
+                    pv = fma(b[k][i], g_rt.wv[n][k], pv);
+                }
+                px = fma(a0[i], 0.5, px);
+                pv = pv + a0[i];
                 dxn[i] = fma(sh * sh, px, sh * v0[i]);   // displacement since the step start
                 xn[i] = x0[i] + dxn[i];
-                // v(s) = v0 + s h [a0 + s(b0/2 + s(b1/3 + ... + s b6/8))]
-                double pv = b[6][i] * 0.125;
-                pv = fma(pv, s, b[5][i] * (1.0 / 7.0));
-                pv = fma(pv, s, b[4][i] * (1.0 / 6.0));
-                pv = fma(pv, s, b[3][i] * 0.2);
-                pv = fma(pv, s, b[2][i] * 0.25);
-                pv = fma(pv, s, b[1][i] * (1.0 / 3.0));
-                pv = fma(pv, s, b[0][i] * 0.5);
-                pv = fma(pv, s, a0[i]);
                 vn[i] = fma(sh, pv, v0[i]);
             }
             double Fn[3], Fs[3];
