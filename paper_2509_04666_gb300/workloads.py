@@ -513,8 +513,9 @@ def _site_zenith_eq(t):
 def ztf_frames(ps, n_exposures=150_000, days=365, grid=8, sub_deg=0.87, seed_rng=None):
     """ZTF-like exposures: 8x8 sub-fields of 0.87 deg from a rotating ground site."""
     rng = seed_rng
-    # night-time samples every 2 minutes; Sun altitude < -12 deg at the site
-    ts = T0 + np.arange(0, days * 720) / 720.0
+    # night-time samples every 30 s (an exposure + readout cadence); Sun
+    # altitude < -12 deg at the site: ~370,000 night samples in a year
+    ts = T0 + np.arange(0, days * 2880) / 2880.0
     st = integrate_planets(ps, np.linspace(T0, T0 + days, days * 4 + 1))
     tt = np.linspace(T0, T0 + days, days * 4 + 1)
     sun = np.stack([np.interp(ts, tt, st[:, 0, c]) for c in range(3)], -1)
@@ -524,8 +525,10 @@ def ztf_frames(ps, n_exposures=150_000, days=365, grid=8, sub_deg=0.87, seed_rng
     zen = _site_zenith_eq(ts)
     night = (zen * sdir).sum(1) < math.sin(math.radians(-12.0))
     tn = ts[night]
+    if n_exposures > tn.size:
+        raise ValueError(f"{n_exposures} exposures do not fit {tn.size} night-time slots")
     ep = np.sort(rng.choice(tn, n_exposures, replace=False)
-                 + rng.uniform(0, 1.0 / 720.0, n_exposures))
+                 + rng.uniform(0, 1.0 / 2880.0, n_exposures))
     # pointings: Dec in [-30, 90], altitude > 30 deg at the exposure epoch
     zen_e = _site_zenith_eq(ep)
     cen = np.empty((n_exposures, 3))
