@@ -453,7 +453,11 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
         float st[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (row32) {
 #pragma unroll
-            for (int q = 0; q < 6; q++) st[q] = __ldg(row32 + 6 * m + q);
+            for (int q = 0; q < 3; q++) st[q] = __ldg(row32 + 6 * m + q);
+            if (gr) {
+#pragma unroll
+                for (int q = 3; q < 6; q++) st[q] = __ldg(row32 + 6 * m + q);
+            }
         } else {
             cheb_state32(E, m, g.s, tau32, st, gr);
             st[0] -= sunf[0]; st[1] -= sunf[1]; st[2] -= sunf[2];
