@@ -49,6 +49,10 @@ class SurveyOpts(C.Structure):
                 ("prefilter_deg", C.c_double)]
 
 
+class Mag(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("p1", C.c_double), ("p2", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("rejected", C.c_int64), ("force_evals", C.c_int64),
                 ("iterations", C.c_int64)]
@@ -83,6 +87,8 @@ def lib():
         L.ko_kepler.argtypes = [C.c_double, d, d, C.c_double, d, d]
         L.ko_apparent.argtypes = [C.POINTER(Ephem), d, C.c_double, C.c_double, d, d, d]
         L.ko_radec.argtypes = [d, d, d]
+        L.ko_magnitude.argtypes = [C.POINTER(Ephem), d, C.c_double, C.c_double, d,
+                                   C.POINTER(Mag), d, d, d, d]
         L.ko_in_polygon.argtypes = [C.c_void_p, d, d]
         L.ko_make_batches.argtypes = [d, C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p]
         L.ko_make_batches.restype = C.c_int64
@@ -175,6 +181,14 @@ class Oracle:
         rc = lib().ko_apparent(C.byref(self.eph), _dp(st), t_ref, t_obs, _dp(o), _dp(u),
                                C.byref(tau))
         return rc, u, tau.value
+
+    def magnitude(self, st_ref, t_ref, t_obs, obs, kind, p1, p2):
+        """(rc, mag, r_h, delta, alpha_deg) of a body seen at t_obs from obs."""
+        st = np.ascontiguousarray(st_ref, float); o = np.ascontiguousarray(obs, float)
+        out = [C.c_double() for _ in range(4)]
+        rc = lib().ko_magnitude(C.byref(self.eph), _dp(st), t_ref, t_obs, _dp(o),
+                                C.byref(Mag(kind, 0, p1, p2)), *[C.byref(x) for x in out])
+        return (rc,) + tuple(x.value for x in out)
 
     def propagate_stm(self, fm, state, t, t_target, dt=0.0):
         st = np.ascontiguousarray(state, float).copy()

@@ -741,6 +741,47 @@ int ko_apparent(const ko_ephem *e, const double st_ref[6], double t_ref, double 
     return KO_OK;
 }
 
+/* Apparent magnitudes (Sec. 3.3: V by the H-G system of Bowell et al. 1989 in
+ * its two-exponential form; appendix: the comet total and nucleus
+ * magnitudes).  Geometry from the light-time corrected apparent vector. */
+int ko_magnitude(const ko_ephem *e, const double st_ref[6], double t_ref, double t_obs,
+                 const double obs[3], const ko_mag *p, double *mag, double *r_h,
+                 double *delta, double *alpha_deg)
+{
+    double u[3], tau, sun[3];
+    int s = ko_apparent(e, st_ref, t_ref, t_obs, obs, u, &tau);
+    if (s != KO_OK) return s;
+    /* body and Sun at the emission epoch t_obs - tau */
+    s = ephem_eval_off(e, 0, t_ref, (t_obs - t_ref) - tau, sun, NULL);
+    if (s != KO_OK) return s;
+    double rv[3];
+    for (int i = 0; i < 3; i++) rv[i] = (obs[i] + u[i]) - sun[i];
+    const double rh = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+    const double dl = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    /* angle at the body between the directions to the Sun (-rv) and to the
+     * observer (-u) */
+    double ca = (rv[0] * u[0] + rv[1] * u[1] + rv[2] * u[2]) / (rh * dl);
+    if (ca > 1.0) ca = 1.0;
+    if (ca < -1.0) ca = -1.0;
+    const double alpha = acos(ca);
+    double m = NAN;
+    if (p && p->kind == 1) {
+        const double t = tan(0.5 * alpha);
+        const double phi1 = exp(-3.33 * pow(t, 0.63));
+        const double phi2 = exp(-1.87 * pow(t, 1.22));
+        m = p->p1 + 5.0 * log10(rh * dl) - 2.5 * log10((1.0 - p->p2) * phi1 + p->p2 * phi2);
+    } else if (p && p->kind == 2) {
+        m = p->p1 + 5.0 * log10(dl) + p->p2 * log10(rh);
+    } else if (p && p->kind == 3) {
+        m = p->p1 + 5.0 * log10(dl) + p->p2 * log10(rh) + 0.035 * (alpha * 180.0 / M_PI);
+    }
+    if (mag) *mag = m;
+    if (r_h) *r_h = rh;
+    if (delta) *delta = dl;
+    if (alpha_deg) *alpha_deg = alpha * 180.0 / M_PI;
+    return KO_OK;
+}
+
 /* RA/Dec of an ecliptic vector: rotate by the obliquity to equatorial J2000. */
 void ko_radec(const double u[3], double *ra, double *dec)
 {

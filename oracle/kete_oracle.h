@@ -134,6 +134,27 @@ int  ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *sta
                   int64_t capacity, int64_t *n_hits, int32_t *status, int n_threads,
                   ko_stats *stats);
 
+/* Magnitude model of one body (Sec. 3.3 flux estimation; comet magnitudes of
+ * the appendix): kind 1 = asteroid V by the H-G system (p1 = H, p2 = G);
+ * kind 2 = comet total T_mag (p1 = M1, p2 = K1); kind 3 = comet nucleus
+ * N_mag (p1 = M2, p2 = K2).  kind 0: no magnitude. */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double p1, p2;
+} ko_mag;
+
+/* Apparent magnitude of a body seen at t_obs from obs, its state st_ref at
+ * t_ref propagated by two-body + light time (ko_apparent): r_h = |body - Sun|
+ * at t_obs - tau, delta = |u|, alpha = Sun-body-observer angle (degrees).
+ *   H-G:    V = H + 5 log10(r_h delta) - 2.5 log10((1-G) Phi1 + G Phi2),
+ *           Phi_i = exp(-A_i tan(alpha/2)^B_i), A = (3.33, 1.87), B = (0.63, 1.22)
+ *   comet:  M + 5 log10(delta) + K log10(r_h) (+ 0.035 alpha for N_mag)
+ * mag, r_h, delta, alpha_deg: outputs (each may be NULL). */
+int  ko_magnitude(const ko_ephem *e, const double st_ref[6], double t_ref, double t_obs,
+                  const double obs[3], const ko_mag *p, double *mag, double *r_h,
+                  double *delta, double *alpha_deg);
+
 /* Orbit-fit loss of one body and its gradient w.r.t. the initial state.
  * Forward model: the body's observation epochs (sorted) are batched by the
  * <= batch_span rule, the n-body chain visits the union of the batch midpoints
