@@ -571,6 +571,31 @@ def run_gb300(args):
                      "prop_fp64_tflops": f64m / (sm["prop_ms"] / 1e3) / 1e12,
                      "prop_fp32_tflops": f32m / (sm["prop_ms"] / 1e3) / 1e12,
                      "accuracy": compare_sample(kete, hm, nhm, sub, ref) if cpu else None}
+    # ---- per-hit magnitudes fused into the exact test (kete_fov_check_mag) ----------
+    mag_leg = None
+    if rank == 0 and world == 1 and not args.no_mag:
+        from paper_2509_04666_gb300 import workloads as W
+        mp = kete.mag_params_to_device(W.mag_params(w.labels), dev)
+        hg = torch.empty_like(hits)
+        K.fov_check(st, ep, fr, ob, fm=fm, hits=hg, mag_params=mp)
+        gt, ex = [], []
+        for _ in range(2):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, nhg, _ = K.fov_check(st, ep, fr, ob, fm=fm, hits=hg, mag_params=mp)
+            e1.record(stream)
+            e1.synchronize()
+            gt.append(e0.elapsed_time(e1))
+            ex.append(K.get_stats()["exact_ms"])
+        mg = hg[:nhg, 1].cpu().numpy()
+        mags = (mg >> 32).astype(np.uint32).view(np.float32)
+        same = bool(nhg == nh) and bool(torch.equal(hg[:nhg, 0], hits[:nh, 0]))
+        mag_leg = {"ms_per_step": statistics.mean(gt), "exact_ms": statistics.mean(ex),
+                   "exact_ms_without": statistics.mean(s["exact_ms"] for s in stats),
+                   "n_hits": int(nhg), "finite": int(np.isfinite(mags).sum()),
+                   "median_mag": float(np.nanmedian(mags)) if np.isfinite(mags).any() else None,
+                   "hit_list_unchanged": same}
     adjoint = ragged = None
     if rank == 0 and world == 1 and not args.no_adjoint:
         adjoint = adjoint_leg(args, K, dev, flush, stream, peak_nominal)
@@ -595,6 +620,7 @@ def run_gb300(args):
         "cpu_baseline": cpu,
         "accuracy": accuracy,
         "mixed_precision": mixed_leg,
+        "magnitudes": mag_leg,
         "adjoint": adjoint,
         "ragged": ragged,
         "e2e": e2e,
@@ -628,6 +654,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-mag", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--adj-bodies", type=int, default=100_000)
     ap.add_argument("--adj-sample", type=int, default=512)

@@ -114,7 +114,7 @@ typedef struct kete_survey_opts {
 typedef struct kete_hit {
     int64_t frame;               /* index into the frames array */
     int32_t body;                /* index into the states arrays */
-    int32_t flags;               /* reserved, 0 */
+    float mag;                   /* apparent magnitude (kete_fov_check_mag), else NaN */
     double ra;                   /* rad in [0, 2 pi), equatorial J2000, light-time corrected */
     double dec;                  /* rad */
 } kete_hit;                      /* 32 bytes */
@@ -224,6 +224,37 @@ int kete_fov_check(kete_ctx *ctx, const double *states, const double *epochs, in
                    const kete_frame *frames, int64_t n_frames, const double *observers,
                    int64_t n_obs, const kete_force_model *fm, const kete_survey_opts *opt,
                    kete_hit *hits, int64_t capacity, int64_t *n_hits, int32_t *status);
+
+/* Magnitude model of one body (Sec. 3.3 flux estimation; the comet
+ * magnitudes of the appendix), 24 bytes:
+ *   KETE_MAG_HG           asteroid V by the H-G system (Bowell et al. 1989,
+ *                         two-exponential form): p1 = H, p2 = G
+ *   KETE_MAG_COMET_TOTAL  T_mag = M1 + 5 log10(delta) + K1 log10(r_h): p1 = M1, p2 = K1
+ *   KETE_MAG_COMET_NUCLEUS N_mag = M2 + 5 log10(delta) + K2 log10(r_h)
+ *                         + 0.035 (phase angle in degrees): p1 = M2, p2 = K2
+ *   KETE_MAG_NONE         no magnitude (NaN)
+ * r_h = heliocentric distance of the body at the light-emission epoch, delta =
+ * observer distance, phase = Sun-body-observer angle. */
+#define KETE_MAG_NONE 0
+#define KETE_MAG_HG 1
+#define KETE_MAG_COMET_TOTAL 2
+#define KETE_MAG_COMET_NUCLEUS 3
+typedef struct kete_mag_params {
+    int32_t kind;
+    int32_t reserved;
+    double p1, p2;
+} kete_mag_params;
+
+/* kete_fov_check that also gives every hit its apparent magnitude, computed
+ * in the exact FoV test from the same light-time corrected geometry (FP32
+ * magnitude arithmetic, ~1e-5 mag).  mag_params: device, [n], one model per
+ * body (may be NULL: magnitudes NaN).  Everything else, errors included, as
+ * kete_fov_check. */
+int kete_fov_check_mag(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                       const kete_frame *frames, int64_t n_frames, const double *observers,
+                       int64_t n_obs, const kete_force_model *fm, const kete_survey_opts *opt,
+                       const kete_mag_params *mag_params, kete_hit *hits, int64_t capacity,
+                       int64_t *n_hits, int32_t *status);
 
 /* Copy the counters of the last call into *out (host). */
 int kete_get_stats(const kete_ctx *ctx, kete_stats *out);

@@ -617,11 +617,12 @@ static void make_bands(double cell, std::vector<int32_t> &off, std::vector<int32
     n_cells = off[n_bands];
 }
 
-extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double *epochs,
-                              int64_t n, const kete_frame *frames, int64_t n_frames,
-                              const double *observers, int64_t n_obs,
-                              const kete_force_model *fm, const kete_survey_opts *opt_in,
-                              kete_hit *hits, int64_t capacity, int64_t *n_hits, int32_t *status)
+static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epochs,
+                          int64_t n, const kete_frame *frames, int64_t n_frames,
+                          const double *observers, int64_t n_obs,
+                          const kete_force_model *fm, const kete_survey_opts *opt_in,
+                          const kete_mag_params *mag, kete_hit *hits, int64_t capacity,
+                          int64_t *n_hits, int32_t *status)
 {
     if (!ctx) return KETE_ERR_BAD_ARG;
     if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
@@ -830,6 +831,7 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
             xa.exp_off = exp_off; xa.cand_body = cand_body; xa.exp_first = exp_first;
             xa.hits = hit_tmp; xa.cap = hit_cap; xa.frame_cnt = frame_cnt; xa.status = cs.status;
             xa.ctr = ctx->d_ctr;
+            xa.mag = mag;
             phase_mark(ctx, PH_EXACT, true);
             CUDA_TRY(fov_exact(xa, ctx->n_sm, st));
             phase_mark(ctx, PH_EXACT, false);
@@ -902,6 +904,27 @@ extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double 
     ctx->stats.n_hits = (int64_t)hits_total;
     ctx->stats.launches = launches + ctx->extra_launches;
     return KETE_OK;
+}
+
+extern "C" int kete_fov_check(kete_ctx *ctx, const double *states, const double *epochs,
+                              int64_t n, const kete_frame *frames, int64_t n_frames,
+                              const double *observers, int64_t n_obs,
+                              const kete_force_model *fm, const kete_survey_opts *opt,
+                              kete_hit *hits, int64_t capacity, int64_t *n_hits, int32_t *status)
+{
+    return fov_check_impl(ctx, states, epochs, n, frames, n_frames, observers, n_obs, fm, opt,
+                          nullptr, hits, capacity, n_hits, status);
+}
+
+extern "C" int kete_fov_check_mag(kete_ctx *ctx, const double *states, const double *epochs,
+                                  int64_t n, const kete_frame *frames, int64_t n_frames,
+                                  const double *observers, int64_t n_obs,
+                                  const kete_force_model *fm, const kete_survey_opts *opt,
+                                  const kete_mag_params *mag_params, kete_hit *hits,
+                                  int64_t capacity, int64_t *n_hits, int32_t *status)
+{
+    return fov_check_impl(ctx, states, epochs, n, frames, n_frames, observers, n_obs, fm, opt,
+                          mag_params, hits, capacity, n_hits, status);
 }
 
 // Propagation whose chain scratch is a fixed device array (see kete.h): no

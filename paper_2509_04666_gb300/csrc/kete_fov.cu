@@ -481,7 +481,39 @@ struct ExactCtx {
     int32_t *status;
     DevCounters *ctr;
     double cos_eps, sin_eps;
+    const kete_mag_params *mag;
 };
+
+// Apparent magnitude (Sec. 3.3; comet appendix) from the heliocentric
+// position p of the body at emission and the apparent vector u (|u| = dl):
+// H-G V = H + 5 log10(r dl) - 2.5 log10((1-G) Phi1 + G Phi2) with
+// Phi_i = exp(-A_i tan(alpha/2)^B_i), A = (3.33, 1.87), B = (0.63, 1.22);
+// comets M + 5 log10(dl) + K log10(r) (+ 0.035 per degree of phase for the
+// nucleus).  The half-angle tangent comes from the FP64 cross and dot
+// products, tan(alpha/2) = |p x u| / (r dl + p.u): an FP32 arc cosine of the
+// cosine would lose alpha to ~3e-4 rad near opposition, where the H-G phase
+// function is steepest (its slope in tan(alpha/2) is unbounded at zero).  The
+// laws themselves run in FP32 (a magnitude needs ~1e-4).
+__device__ __forceinline__ float apparent_mag(const kete_mag_params &P, const double p[3],
+                                              const double u[3], double dl)
+{
+    if (P.kind < KETE_MAG_HG || P.kind > KETE_MAG_COMET_NUCLEUS)
+        return __int_as_float(0x7fc00000);
+    const double r = sqrt(dot3(p, p));
+    const double cx = p[1] * u[2] - p[2] * u[1], cy = p[2] * u[0] - p[0] * u[2],
+                 cz = p[0] * u[1] - p[1] * u[0];
+    const float t = (float)(sqrt(cx * cx + cy * cy + cz * cz) / fma(r, dl, dot3(p, u)));
+    const float lr = log10f((float)r), ld = log10f((float)dl);
+    const float p1 = (float)P.p1, p2 = (float)P.p2;
+    if (P.kind == KETE_MAG_HG) {
+        const float phi1 = expf(-3.33f * powf(t, 0.63f));
+        const float phi2 = expf(-1.87f * powf(t, 1.22f));
+        return p1 + 5.f * (lr + ld) - 2.5f * log10f((1.f - p2) * phi1 + p2 * phi2);
+    }
+    float m = p1 + 5.f * ld + p2 * lr;
+    if (P.kind == KETE_MAG_COMET_NUCLEUS) m += 0.035f * (2.f * atanf(t) * (180.f / (float)kPi));
+    return m;
+}
 
 // Position at t_ref + dt_obs - tau.  The heliocentric two-body state is
 // solved once, at dt_obs (universal variables from the batch state); the
@@ -596,7 +628,14 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
                     kete_hit hh;
                     hh.frame = f;
                     hh.body = i;
-                    hh.flags = 0;
+                    hh.mag = __int_as_float(0x7fc00000);
+                    if (C.mag) {
+                        // heliocentric position at emission: pos minus the Sun there
+                        const double ph[3] = {pos[0] - fma(-tau, sun_obs[3], sun_obs[0]),
+                                              pos[1] - fma(-tau, sun_obs[4], sun_obs[1]),
+                                              pos[2] - fma(-tau, sun_obs[5], sun_obs[2])};
+                        hh.mag = apparent_mag(C.mag[i], ph, u, un);
+                    }
                     hh.ra = ra;
                     hh.dec = dec;
                     C.hits[slot] = hh;
@@ -734,7 +773,7 @@ cudaError_t fov_exact(const ExactArgs &a, int n_sm, cudaStream_t st)
     C.stop_states = a.stop_states; C.n = a.n; C.k0 = a.k0; C.e_begin = a.e_begin;
     C.e_end = a.e_end; C.exp_off = a.exp_off; C.cand_body = a.cand_body;
     C.exp_first = a.exp_first; C.hits = a.hits; C.cap = a.cap; C.frame_cnt = a.frame_cnt;
-    C.status = a.status; C.ctr = a.ctr;
+    C.status = a.status; C.ctr = a.ctr; C.mag = a.mag;
     const double eps = 84381.448 / 3600.0 * (kPi / 180.0);
     C.cos_eps = cos(eps);
     C.sin_eps = sin(eps);

@@ -72,6 +72,7 @@ struct ExactArgs {
     int32_t *frame_cnt;
     int32_t *status;
     DevCounters *ctr;
+    const kete_mag_params *mag = nullptr;   // [n] magnitude models, or null
 };
 
 cudaError_t fov_frame_prep(const kete_frame *frames, int64_t nf, int64_t n_obs, int32_t *is_start,

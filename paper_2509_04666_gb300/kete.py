@@ -28,7 +28,8 @@ EXPORTS = ["kete_create", "kete_destroy", "kete_set_stream", "kete_last_error",
            "kete_force_model_default", "kete_survey_opts_default", "kete_load_ephem",
            "kete_ephem_eval", "kete_propagate", "kete_propagate_stops", "kete_fov_check",
            "kete_get_stats", "kete_propagate_noalloc", "kete_set_propagation", "kete_autotune",
-           "kete_adjoint"]
+           "kete_adjoint", "kete_fov_check_mag"]
+MAG_NONE, MAG_HG, MAG_COMET_TOTAL, MAG_COMET_NUCLEUS = 0, 1, 2, 3
 
 
 class KeteError(RuntimeError):
@@ -94,6 +95,8 @@ def lib():
         L.kete_fov_check.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, C.POINTER(ForceModel),
                                      C.POINTER(SurveyOpts), vp, i64, C.POINTER(i64), vp]
         L.kete_get_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.kete_fov_check_mag.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, C.POINTER(ForceModel),
+                                         C.POINTER(SurveyOpts), vp, vp, i64, C.POINTER(i64), vp]
         L.kete_propagate_noalloc.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(ForceModel), vp]
         L.kete_set_propagation.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                            C.c_int]
@@ -144,11 +147,20 @@ def frames_to_device(frames: np.ndarray, device) -> torch.Tensor:
     return torch.from_numpy(raw.copy()).to(device)
 
 
+def mag_params_to_device(params: np.ndarray, device) -> torch.Tensor:
+    """kete_mag_params records (24 bytes: kind, reserved, p1, p2) -> CUDA bytes."""
+    a = np.ascontiguousarray(params)
+    if a.dtype.itemsize != 24:
+        raise TypeError("magnitude parameters must be 24-byte kete_mag_params records")
+    return torch.from_numpy(a.view(np.uint8).reshape(-1).copy()).to(device)
+
+
 def decode_hits(h: torch.Tensor, n: int):
     """kete_hit rows (int64 [n, 4] view) -> dict of CPU tensors."""
     h = h[:n].cpu()
     return {"frame": h[:, 0].clone(),
             "body": (h[:, 1] & 0xFFFFFFFF).to(torch.int32),
+            "mag": (h[:, 1] >> 32).to(torch.int32).view(torch.float32),
             "ra": h[:, 2].clone().view(torch.float64),
             "dec": h[:, 3].clone().view(torch.float64)}
 
@@ -239,9 +251,11 @@ class Kete:
         return out, status
 
     def fov_check(self, states, epochs, frames_dev, observers, fm=None, opts=None,
-                  capacity=None, hits=None):
+                  capacity=None, hits=None, mag_params=None):
         """Which bodies fall inside which FoV.  Returns (hits int64 [cap, 4],
-        n_hits, status).  Grows the hit buffer once if it was too small."""
+        n_hits, status).  Grows the hit buffer once if it was too small.
+        mag_params (CUDA bytes of n kete_mag_params, see mag_params_to_device):
+        also give every hit its apparent magnitude (kete_fov_check_mag)."""
         n = epochs.numel()
         _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
         _dev_f64(observers, "observers")
@@ -258,10 +272,19 @@ class Kete:
         nh = C.c_int64(0)
         self._sync_stream()
         for attempt in range(2):
-            rc = lib().kete_fov_check(self._h, states.data_ptr(), epochs.data_ptr(), n,
-                                      frames_dev.data_ptr(), nf, observers.data_ptr(), n_obs,
-                                      C.byref(fm), C.byref(opts), hits.data_ptr(), hits.shape[0],
-                                      C.byref(nh), status.data_ptr())
+            if mag_params is None:
+                rc = lib().kete_fov_check(self._h, states.data_ptr(), epochs.data_ptr(), n,
+                                          frames_dev.data_ptr(), nf, observers.data_ptr(), n_obs,
+                                          C.byref(fm), C.byref(opts), hits.data_ptr(),
+                                          hits.shape[0], C.byref(nh), status.data_ptr())
+            else:
+                if not (mag_params.is_cuda and mag_params.numel() == 24 * n):
+                    raise TypeError("mag_params must hold n kete_mag_params records on the GPU")
+                rc = lib().kete_fov_check_mag(self._h, states.data_ptr(), epochs.data_ptr(), n,
+                                              frames_dev.data_ptr(), nf, observers.data_ptr(),
+                                              n_obs, C.byref(fm), C.byref(opts),
+                                              mag_params.data_ptr(), hits.data_ptr(),
+                                              hits.shape[0], C.byref(nh), status.data_ptr())
             if rc == ERR_CAPACITY and attempt == 0:
                 hits = torch.empty((nh.value + 1024, 4), dtype=torch.int64, device=states.device)
                 continue

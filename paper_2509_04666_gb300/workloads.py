@@ -656,6 +656,29 @@ OBS_DTYPE = np.dtype([("epoch", "<f8"), ("ra", "<f8"), ("dec", "<f8"), ("obs", "
 assert OBS_DTYPE.itemsize == 48
 
 
+MAG_DTYPE = np.dtype([("kind", "<i4"), ("reserved", "<i4"), ("p1", "<f8"), ("p2", "<f8")])
+assert MAG_DTYPE.itemsize == 24
+
+
+def mag_params(labels, seed=SEED_BASE + 7):
+    """Magnitude models per body: asteroids H ~ U[10, 20], G ~ U[0.05, 0.35]
+    (H-G); comets (label 3) alternately total (M1 ~ U[5, 15], K1 ~ U[5, 15])
+    and nucleus (M2, K2 alike) magnitudes; every 50th body none."""
+    labels = np.asarray(labels)
+    rng = _rng(seed, 8)
+    n = labels.size
+    out = np.zeros(n, MAG_DTYPE)
+    out["kind"] = 1
+    out["p1"] = rng.uniform(10.0, 20.0, n)
+    out["p2"] = rng.uniform(0.05, 0.35, n)
+    com = np.nonzero(labels == 3)[0]
+    out["kind"][com] = np.where(np.arange(com.size) % 2 == 0, 2, 3)
+    out["p1"][com] = rng.uniform(5.0, 15.0, com.size)
+    out["p2"][com] = rng.uniform(5.0, 15.0, com.size)
+    out["kind"][::50] = 0
+    return out
+
+
 def adjoint90(n_bodies=100_000, n_obs=20, days=90.0, seed=None, neo_frac=0.02):
     """Orbit-fit inputs: bodies drawn as in wise1y, n_obs observation epochs per
     body ~ U[T0, T0 + days] (sorted) seen from the circular 1-AU observer of
