@@ -36,12 +36,47 @@ class Ephem(C.Structure):
                 ("gm", C.c_double * 16), ("coef", C.POINTER(C.c_double))]
 
 
+class NonGrav(C.Structure):
+    """ko_nongrav: beta (Eq. A.6); a1..a3, alpha, r0, m, n, k, dt (Eq. A.7)."""
+    _fields_ = [(f, C.c_double) for f in ("a1", "a2", "a3", "alpha", "r0", "m", "n", "k",
+                                          "dt", "beta")]
+
+
+NG_FIELDS = ("a1", "a2", "a3", "alpha", "r0", "m", "n", "k", "dt", "beta")
+NG_DTYPE = np.dtype([(f, "<f8") for f in NG_FIELDS])
+
+
+def comet_ng(a1=0.0, a2=0.0, a3=0.0, dt=0.0):
+    """JPL comet model with its default g(r) (App. A.5)."""
+    return NonGrav(a1, a2, a3, 0.1112620426, 2.808, 2.15, 5.093, 4.6142, dt, 0.0)
+
+
+def asteroid_ng(a1=0.0, a2=0.0, a3=0.0, dt=0.0):
+    """The same model with the asteroid defaults, g(r) = 1/r^2 (App. A.5)."""
+    return NonGrav(a1, a2, a3, 1.0, 1.0, 2.0, 1.0, 0.0, dt, 0.0)
+
+
+def dust_ng(beta):
+    """Radiation pressure with Poynting-Robertson drag (Eq. A.6)."""
+    return NonGrav(0, 0, 0, 0, 1.0, 0, 0, 0, 0, beta)
+
+
+def _ng_array(ng, n):
+    """Per-body non-gravitational records (any array with NG_FIELDS) -> ko_nongrav[n]."""
+    if ng is None:
+        return None
+    out = np.zeros(n, NG_DTYPE)
+    for f in NG_FIELDS:
+        out[f] = ng[f]
+    return out
+
+
 class ForceModel(C.Structure):
     _fields_ = [("body_mask", C.c_uint32), ("gr_mask", C.c_uint32), ("j2_mask", C.c_uint32),
                 ("max_iter", C.c_int32), ("j2", C.c_double * 16), ("radius", C.c_double * 16),
                 ("pole_ra", C.c_double * 16), ("pole_dec", C.c_double * 16),
                 ("eps", C.c_double), ("eps_pc", C.c_double), ("safety", C.c_double),
-                ("dt_init", C.c_double), ("max_steps", C.c_int64)]
+                ("dt_init", C.c_double), ("max_steps", C.c_int64), ("ng", NonGrav)]
 
 
 class SurveyOpts(C.Structure):
@@ -82,7 +117,8 @@ def lib():
         L.ko_propagate_stops.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, C.c_double,
                                          d, C.c_int64, d, C.POINTER(Stats)]
         L.ko_propagate_many.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, d, C.c_int64,
-                                        C.c_double, C.c_void_p, C.c_int, C.POINTER(Stats)]
+                                        C.c_double, C.c_void_p, C.c_int, C.POINTER(Stats),
+                                        C.c_void_p]
         L.ko_stumpff.argtypes = [C.c_double, d, d]
         L.ko_kepler.argtypes = [C.c_double, d, d, C.c_double, d, d]
         L.ko_apparent.argtypes = [C.POINTER(Ephem), d, C.c_double, C.c_double, d, d, d]
@@ -100,7 +136,8 @@ def lib():
         L.ko_fov_check.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, d, C.c_int64,
                                    C.c_void_p, C.c_int64, d, C.c_int64, C.POINTER(SurveyOpts),
                                    C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
-                                   C.POINTER(C.c_int64), C.c_void_p, C.c_int, C.POINTER(Stats)]
+                                   C.POINTER(C.c_int64), C.c_void_p, C.c_int, C.POINTER(Stats),
+                                   C.c_void_p]
         _lib = L
     return _lib
 
@@ -166,13 +203,15 @@ class Oracle:
                                       _dp(stops), len(stops), _dp(out), C.byref(stats))
         return rc, out, stats
 
-    def propagate_many(self, fm, states, epochs, t_target, n_threads=None):
+    def propagate_many(self, fm, states, epochs, t_target, n_threads=None, nongrav=None):
         st = np.ascontiguousarray(states, float).copy()
         ep = np.ascontiguousarray(epochs, float).copy()
         n = ep.size
         status = np.zeros(n, np.int32); stats = Stats()
+        ng = _ng_array(nongrav, n)
         lib().ko_propagate_many(C.byref(self.eph), C.byref(fm), _dp(st), _dp(ep), n, t_target,
-                                status.ctypes.data, n_threads or os.cpu_count(), C.byref(stats))
+                                status.ctypes.data, n_threads or os.cpu_count(), C.byref(stats),
+                                None if ng is None else ng.ctypes.data)
         return st, ep, status, stats
 
     def apparent(self, st_ref, t_ref, t_obs, obs):
@@ -212,7 +251,7 @@ class Oracle:
         return rc, loss.value, pred, (g if grad else None)
 
     def fov_check(self, fm, states, epochs, frames, observers, batch_span=3.0, twobody_max=1.5,
-                  prefilter_deg=0.0, subset=None, n_threads=None):
+                  prefilter_deg=0.0, subset=None, n_threads=None, nongrav=None):
         st = np.ascontiguousarray(states, float)
         ep = np.ascontiguousarray(epochs, float)
         fr = np.ascontiguousarray(frames)
@@ -226,11 +265,12 @@ class Oracle:
                 _dp(ob), len(ob), C.byref(opts), None if sub is None else sub.ctypes.data,
                 0 if sub is None else len(sub)]
         nt = n_threads or os.cpu_count()
+        ng = _ng_array(nongrav, n)
         cap = 0
         hits = np.zeros(1, HIT_DTYPE)
         for _ in range(2):
             rc = lib().ko_fov_check(*args, hits.ctypes.data, cap, C.byref(nh), status.ctypes.data,
-                                    nt, C.byref(stats))
+                                    nt, C.byref(stats), None if ng is None else ng.ctypes.data)
             if rc == 0:
                 return hits[: nh.value].copy(), status, stats
             cap = nh.value

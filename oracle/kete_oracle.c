@@ -203,6 +203,54 @@ typedef struct {
     double dx[3];        /* body displacement x(t0 + off) - x0 of the current call */
 } ko_close;
 
+/* ---- optional non-gravitational terms (App. A.4, A.5) --------------------- */
+static int ng_active(const ko_nongrav *p)
+{
+    return p->beta != 0.0 || p->a1 != 0.0 || p->a2 != 0.0 || p->a3 != 0.0;
+}
+
+/* Added to a: the non-gravitational acceleration of a body at heliocentric
+ * position r and velocity w (mu = the Sun's GM).
+ *   Eq. A.6 (radiation pressure + Poynting-Robertson drag), read as
+ *     beta mu / |r|^2 [(1 - rdot/c) rhat - w/c],  rdot = rhat . w
+ *   (the printed "(1 - v/c)" factor of the radial term is the radial speed).
+ *   Eq. A.7 (JPL comet model): g(r') (A1 rhat' + A2 that' + A3 nhat') with
+ *   (r', w') the two-body state dt days earlier, nhat' = r' x w' / |r' x w'|,
+ *   that' = nhat' x rhat' (along the motion). */
+static int nongrav_add(const ko_nongrav *p, double mu, const double r[3], const double w[3],
+                       double a[3])
+{
+    const double c = c_au_per_day();
+    if (p->beta != 0.0) {
+        double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        double rdot = (r[0] * w[0] + r[1] * w[1] + r[2] * w[2]) / rn;
+        double f = p->beta * mu / (rn * rn);
+        for (int i = 0; i < 3; i++) a[i] += f * ((1.0 - rdot / c) * r[i] / rn - w[i] / c);
+    }
+    if (p->a1 != 0.0 || p->a2 != 0.0 || p->a3 != 0.0) {
+        double rl[3], wl[3];
+        if (p->dt != 0.0) {
+            int s = ko_kepler(mu, r, w, -p->dt, rl, wl);
+            if (s != KO_OK) return s;
+        } else {
+            memcpy(rl, r, sizeof(rl));
+            memcpy(wl, w, sizeof(wl));
+        }
+        double rn = sqrt(rl[0] * rl[0] + rl[1] * rl[1] + rl[2] * rl[2]);
+        double q = rn / p->r0;
+        double g = p->alpha * pow(q, -p->m) * pow(1.0 + pow(q, p->n), -p->k);
+        double rh[3] = {rl[0] / rn, rl[1] / rn, rl[2] / rn};
+        double h[3] = {rl[1] * wl[2] - rl[2] * wl[1], rl[2] * wl[0] - rl[0] * wl[2],
+                       rl[0] * wl[1] - rl[1] * wl[0]};
+        double hn = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+        double nh[3] = {h[0] / hn, h[1] / hn, h[2] / hn};
+        double th[3] = {nh[1] * rh[2] - nh[2] * rh[1], nh[2] * rh[0] - nh[0] * rh[2],
+                        nh[0] * rh[1] - nh[1] * rh[0]};
+        for (int i = 0; i < 3; i++) a[i] += g * (p->a1 * rh[i] + p->a2 * th[i] + p->a3 * nh[i]);
+    }
+    return KO_OK;
+}
+
 /* ---- force model: Eq. A.1 = sum over masses of Newton + A.3 + A.4 -------- */
 static void pole_vector(double ra, double dec, double p[3])
 {
@@ -278,6 +326,16 @@ static int accel_off_cl(const ko_ephem *e, const ko_force_model *fm, double t0, 
             double ab[3] = {-psi * (1.0 - q) * xb, -psi * (1.0 - q) * yb, -psi * (3.0 - q) * zb};
             for (int i = 0; i < 3; i++) a[i] += ab[0] * e1[i] + ab[1] * e2[i] + ab[2] * p[i];
         }
+    }
+    if (ng_active(&fm->ng)) {
+        /* heliocentric state: relative to table body 0, the Sun */
+        double ps[3], vs[3];
+        int st = ephem_eval_off(e, 0, t0, off, ps, vs);
+        if (st != KO_OK) return st;
+        double r[3] = {x[0] - ps[0], x[1] - ps[1], x[2] - ps[2]};
+        double w[3] = {v[0] - vs[0], v[1] - vs[1], v[2] - vs[2]};
+        st = nongrav_add(&fm->ng, e->gm[0], r, w, a);
+        if (st != KO_OK) return st;
     }
     return KO_OK;
 }
@@ -566,6 +624,7 @@ typedef struct {
     int32_t *status;
     int tid, nt;
     ko_stats stats;
+    const ko_nongrav *ng;
 } prop_job;
 
 static void *prop_worker(void *arg)
@@ -574,7 +633,9 @@ static void *prop_worker(void *arg)
     for (int64_t i = j->tid; i < j->n; i += j->nt) {
         double st[6], t = j->epochs[i], dt = 0.0;
         for (int c = 0; c < 6; c++) st[c] = j->states[c * j->n + i];
-        int s = ko_propagate(j->e, j->fm, st, &t, j->t_target, &dt, &j->stats);
+        ko_force_model fmb = *j->fm;
+        if (j->ng) fmb.ng = j->ng[i];
+        int s = ko_propagate(j->e, &fmb, st, &t, j->t_target, &dt, &j->stats);
         if (j->status) j->status[i] = s;
         if (s == KO_OK) {
             for (int c = 0; c < 6; c++) j->states[c * j->n + i] = st[c];
@@ -586,13 +647,14 @@ static void *prop_worker(void *arg)
 
 int ko_propagate_many(const ko_ephem *e, const ko_force_model *fm, double *states,
                       double *epochs, int64_t n, double t_target, int32_t *status,
-                      int n_threads, ko_stats *stats)
+                      int n_threads, ko_stats *stats, const ko_nongrav *ng_bodies)
 {
     if (n_threads < 1) n_threads = 1;
     prop_job *jobs = (prop_job *)calloc(n_threads, sizeof(prop_job));
     pthread_t *th = (pthread_t *)calloc(n_threads, sizeof(pthread_t));
     for (int k = 0; k < n_threads; k++) {
-        prop_job j = {e, fm, states, epochs, n, t_target, status, k, n_threads, {0, 0, 0, 0}};
+        prop_job j = {e, fm, states, epochs, n, t_target, status, k, n_threads, {0, 0, 0, 0},
+                      ng_bodies};
         jobs[k] = j;
         pthread_create(&th[k], NULL, prop_worker, &jobs[k]);
     }
@@ -866,6 +928,7 @@ typedef struct {
     hitbuf out;
     ko_stats stats;
     double (*centre)[4];         /* frame centre (unit) + circumradius */
+    const ko_nongrav *ng;        /* per-body non-gravitational terms or NULL */
 } fov_job;
 
 static void *fov_worker(void *arg)
@@ -877,7 +940,9 @@ static void *fov_worker(void *arg)
         int32_t bi = j->subset ? j->subset[q] : (int32_t)q;
         double st0[6];
         for (int k = 0; k < 6; k++) st0[k] = j->states[(int64_t)k * j->n + bi];
-        int s = ko_propagate_stops(j->e, j->fm, st0, j->epochs[bi], j->tref, j->nb, st_stops,
+        ko_force_model fmb = *j->fm;
+        if (j->ng) fmb.ng = j->ng[bi];
+        int s = ko_propagate_stops(j->e, &fmb, st0, j->epochs[bi], j->tref, j->nb, st_stops,
                                    &j->stats);
         if (j->status) j->status[bi] = s;
         for (int64_t k = 0; k < j->nb; k++) {
@@ -948,7 +1013,8 @@ int ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *stat
                  const double *epochs, int64_t n, const ko_frame *frames, int64_t n_frames,
                  const double *observers, int64_t n_obs, const ko_survey_opts *opt,
                  const int32_t *body_subset, int64_t n_subset, ko_hit *hits, int64_t capacity,
-                 int64_t *n_hits, int32_t *status, int n_threads, ko_stats *stats)
+                 int64_t *n_hits, int32_t *status, int n_threads, ko_stats *stats,
+                 const ko_nongrav *ng_bodies)
 {
     (void)n_obs;
     if (n_threads < 1) n_threads = 1;
@@ -1014,7 +1080,7 @@ int ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *stat
         j->frames = frames; j->order = order; j->observers = observers; j->opt = opt;
         j->subset = body_subset; j->n_subset = nsub; j->nb = nb; j->bstart = bstart;
         j->tref = tref; j->n_frames = n_frames; j->status = status; j->tid = k;
-        j->nt = n_threads; j->centre = centre;
+        j->nt = n_threads; j->centre = centre; j->ng = ng_bodies;
         pthread_create(&th[k], NULL, fov_worker, j);
     }
     int64_t total = 0;

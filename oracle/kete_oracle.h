@@ -7,7 +7,10 @@
  *
  * What it computes (each function cites the passage it follows):
  *   - planetary ephemeris lookup: Chebyshev series per segment (App. A, Sec. 3.2)
- *   - acceleration: Newton + GR (Eq. A.3) + J2 (Eq. A.4), summed as Eq. A.1
+ *   - acceleration: Newton + GR (Eq. A.3) + J2 (Eq. A.4), summed as Eq. A.1,
+ *     plus the optional non-gravitational terms: radiation pressure with
+ *     Poynting-Robertson drag (Eq. A.6) and the JPL comet model with its
+ *     thermal lag (Eq. A.7)
  *   - Gauss-Radau 15th-order step with IAS15 corrector convergence and step
  *     control, predictor removed (Sec. 3.2, App. A.6)
  *   - universal-variable two-body propagation + light-delay iteration (Sec. 2)
@@ -18,7 +21,10 @@
  *
  * Parity pins: see tests/test_oracle_*.py (closed-form Kepler, conservation
  * laws, time reversal, GR perihelion advance, J2 nodal regression, light-time
- * closed forms, gnomonic FoV test, brute-force FoV, batching rules).
+ * closed forms, gnomonic FoV test, brute-force FoV, batching rules; the
+ * non-gravitational terms against Kepler with a weakened Sun, Gauss's rate
+ * for a transverse force, the angular-momentum decay and Wyatt & Whipple's
+ * secular rate of Poynting-Robertson drag, and Galilean invariance).
  * The full force model with planets on is "parity unpinned" by the paper:
  * no worked example exists; it is held only by the invariants above.
  */
@@ -49,6 +55,18 @@ typedef struct {
     double *coef;           /* [body][seg][3][coef] */
 } ko_ephem;
 
+/* Non-gravitational parameters of one body (App. A.4-A.5).  All zero: none.
+ *   beta: radiation pressure / solar gravity ratio (Eq. A.6)
+ *   a1, a2, a3: radial, transverse, normal JPL coefficients, AU/day^2, with
+ *   g(r) = alpha (r/r0)^-m (1 + (r/r0)^n)^-k (Eq. A.7), evaluated, with the
+ *   directions, at the two-body heliocentric state dt days earlier. */
+typedef struct {
+    double a1, a2, a3;
+    double alpha, r0, m, n, k;
+    double dt;
+    double beta;
+} ko_nongrav;
+
 typedef struct {
     uint32_t body_mask;     /* bodies whose gravity acts (bit b = table body b) */
     uint32_t gr_mask;       /* bodies with the GR term of Eq. A.3 */
@@ -63,6 +81,7 @@ typedef struct {
     double safety;          /* IAS15 safety factor */
     double dt_init;         /* first step of every propagation chain, days */
     int64_t max_steps;      /* step attempts per leg */
+    ko_nongrav ng;          /* this body's non-gravitational terms (zero: none) */
 } ko_force_model;
 
 typedef struct {
@@ -113,9 +132,10 @@ int  ko_propagate(const ko_ephem *e, const ko_force_model *fm, double st[6], dou
 int  ko_propagate_stops(const ko_ephem *e, const ko_force_model *fm, const double st0[6],
                         double epoch, const double *stops, int64_t n_stops,
                         double *out /* [n_stops][6] */, ko_stats *stats);
+/* ng_bodies (may be NULL): per-body non-gravitational terms replacing fm->ng */
 int  ko_propagate_many(const ko_ephem *e, const ko_force_model *fm, double *states /*6xN SoA*/,
                        double *epochs, int64_t n, double t_target, int32_t *status,
-                       int n_threads, ko_stats *stats);
+                       int n_threads, ko_stats *stats, const ko_nongrav *ng_bodies);
 
 void ko_stumpff(double z, double *c2, double *c3);
 int  ko_kepler(double mu, const double r0[3], const double v0[3], double dt,
@@ -132,7 +152,7 @@ int  ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *sta
                   const double *observers, int64_t n_obs, const ko_survey_opts *opt,
                   const int32_t *body_subset, int64_t n_subset, ko_hit *hits,
                   int64_t capacity, int64_t *n_hits, int32_t *status, int n_threads,
-                  ko_stats *stats);
+                  ko_stats *stats, const ko_nongrav *ng_bodies);
 
 /* Magnitude model of one body (Sec. 3.3 flux estimation; comet magnitudes of
  * the appendix): kind 1 = asteroid V by the H-G system (p1 = H, p2 = G);
