@@ -359,13 +359,19 @@ def ragged_leg(args, K, dev, flush, stream):
     out = {"workload": f"ragged1y: {n} bodies (60% main belt, 20% NEOs of which 5% pass "
                        f"0.001-0.01 AU from the Earth, 10% Trojans, 10% comets), 365 d"}
     res = {}
-    for name, prec, kind, split in (("fp64", kete.FP64, kete.PROP_WORK_STEALING, 0),
-                                    ("mixed", kete.MIXED, kete.PROP_WORK_STEALING, 0),
-                                    ("fp64_static", kete.FP64, kete.PROP_STATIC, 0),
-                                    ("fp64_split8", kete.FP64, kete.PROP_WORK_STEALING, 8),
-                                    ("mixed_split8", kete.MIXED, kete.PROP_WORK_STEALING, 8)):
+    ng = W.nongrav_params(w.labels)
+    ng_dev = kete.nongrav_to_device(ng, dev)
+    for name, prec, kind, split, with_ng in (
+            ("fp64", kete.FP64, kete.PROP_WORK_STEALING, 0, False),
+            ("mixed", kete.MIXED, kete.PROP_WORK_STEALING, 0, False),
+            ("fp64_static", kete.FP64, kete.PROP_STATIC, 0, False),
+            ("fp64_split8", kete.FP64, kete.PROP_WORK_STEALING, 8, False),
+            ("mixed_split8", kete.MIXED, kete.PROP_WORK_STEALING, 8, False),
+            ("fp64_nongrav", kete.FP64, kete.PROP_WORK_STEALING, 0, True)):
         K.set_propagation(prec, kind, 128, split, 64 if split else 0)
         fm = kete.force_model(precision=prec)
+        if with_ng:
+            fm.nongrav = ng_dev.data_ptr()
         box = {}
 
         def call():
@@ -382,6 +388,9 @@ def ragged_leg(args, K, dev, flush, stream):
     K.set_propagation(kete.MIXED, kete.PROP_WORK_STEALING, 128)
     out["mixed_speedup_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
     out["work_stealing_speedup_vs_static"] = out["fp64_static"]["ms"] / out["fp64"]["ms"]
+    out["nongrav_cost_vs_fp64"] = out["fp64_nongrav"]["ms"] / out["fp64"]["ms"]
+    out["nongrav_terms"] = ("comets: JPL comet model, comet g(r), A1 logU[1e-9, 1e-7] AU/d^2, "
+                            "half lagged 5-40 d; every 10th other body: transverse 1/r^2 drift")
     # accuracy on a sample (every population, all forced encounters in it)
     orc = O.Oracle(w.ephem.to_bytes())
     enc = np.nonzero(w.labels == 4)[0]
@@ -390,11 +399,13 @@ def ragged_leg(args, K, dev, flush, stream):
     t0 = time.perf_counter()
     ref, _, rst, _ = orc.propagate_many(orc.force_model(), w.states[:, sub], w.epochs[sub], t_end)
     dt = time.perf_counter() - t0
+    ref_ng, _, _, _ = orc.propagate_many(orc.force_model(), w.states[:, sub], w.epochs[sub], t_end,
+                                         nongrav=ng[sub])
     _, pe, _ = orc.ephem(3, t_end)
     acc = {}
-    for name in ("fp64", "mixed"):
+    for name in ("fp64", "mixed", "fp64_nongrav"):
         s, stat = res[name]
-        d = np.linalg.norm(s[:3, sub] - ref[:3], axis=0)
+        d = np.linalg.norm(s[:3, sub] - (ref_ng if name == "fp64_nongrav" else ref)[:3], axis=0)
         rho = np.linalg.norm(ref[:3] - pe[:, None], axis=0)
         by = {}
         for lab, nm in ((0, "main_belt"), (1, "neo"), (2, "trojan"), (3, "comet"), (4, "encounter")):

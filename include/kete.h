@@ -66,6 +66,27 @@ extern "C" {
 #define KETE_FP64 0    /* everything in FP64 */
 #define KETE_MIXED 1   /* planetary perturbation terms in FP32, the rest FP64 */
 
+/* Non-gravitational terms of one body (App. A.4-A.5; 80 bytes).  All zero:
+ * none.  Forces act in the heliocentric frame (position and velocity
+ * relative to table body 0, the Sun, whose GM is mu below).
+ *   beta > 0: radiation pressure with Poynting-Robertson drag (Eq. A.6),
+ *     beta mu / r^2 [(1 - rdot/c) rhat - v/c], rdot = rhat . v.
+ *   a1, a2, a3 (AU/day^2, radial, transverse, normal; Eq. A.7):
+ *     g(r) (a1 rhat + a2 that + a3 nhat), g(r) = alpha (r/r0)^-m
+ *     (1 + (r/r0)^n)^-k, nhat = r x v / |r x v|, that = nhat x rhat, all
+ *     from the two-body state dt days earlier (thermal lag; dt = 0: now).
+ *     JPL comet defaults: alpha 0.1112620426, r0 2.808 AU, m 2.15,
+ *     n 5.093, k 4.6142; asteroid defaults alpha 1, r0 1, m 2, n 1, k 0
+ *     (g = 1/r^2).
+ * A failed thermal-lag two-body solve ends the body with
+ * KETE_BODY_KEPLER_CAP. */
+typedef struct kete_nongrav {
+    double a1, a2, a3;
+    double alpha, r0, m, n, k;
+    double dt;
+    double beta;
+} kete_nongrav;
+
 /* Force model and integrator controls (Eq. A.1, App. A.2-A.3, App. A.6).
  * Bit b of a mask refers to body b of the loaded table (0 = Sun, 1..8 =
  * Mercury, Venus, Earth-Moon, Mars, Jupiter, Saturn, Uranus, Neptune).
@@ -86,6 +107,13 @@ typedef struct kete_force_model {
     int32_t max_iter;            /* corrector iteration cap (12) */
     int32_t reserved;
     int64_t max_steps;           /* step attempts per leg before KETE_BODY_STEP_CAP */
+    /* Per-body non-gravitational terms: device array of one kete_nongrav per
+     * body of the call, indexed like its states (8-byte aligned), or NULL
+     * (default).  Read by kete_propagate, kete_propagate_stops,
+     * kete_propagate_noalloc and kete_fov_check(_mag); kete_adjoint refuses
+     * it (KETE_ERR_BAD_ARG: its gradient covers gravity only) and
+     * kete_autotune times its sample without it. */
+    const kete_nongrav *nongrav;
 } kete_force_model;
 
 /* One spherical polygon (Sec. 3.1).  Polygons with the same exposure_id must

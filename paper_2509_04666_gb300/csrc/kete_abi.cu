@@ -411,6 +411,9 @@ static int make_force(kete_ctx *ctx, const kete_force_model *fm_in, ForceDev &F)
     F.dt_init = fm.dt_init;
     F.max_iter = fm.max_iter;
     F.max_steps = fm.max_steps;
+    if (fm.nongrav && (reinterpret_cast<uintptr_t>(fm.nongrav) & 7u))
+        return fail(ctx, KETE_ERR_BAD_ARG, "nongrav must be 8-byte aligned");
+    F.nongrav = fm.nongrav;
     return KETE_OK;
 }
 
@@ -987,6 +990,7 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
     ForceDev F;
     int r = make_force(ctx, fm, F);
     if (r != KETE_OK) return r;
+    F.nongrav = nullptr;   // the sample is gathered: body indices differ from the caller's
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     const int64_t m = std::min(n, max_sample);
@@ -1071,6 +1075,9 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
     if (fm) fm64 = *fm;
     else kete_force_model_default(&fm64);
     fm64.precision = KETE_FP64;
+    if (fm64.nongrav)
+        return fail(ctx, KETE_ERR_BAD_ARG,
+                    "kete_adjoint differentiates gravity only: nongrav must be NULL");
     ForceDev F;
     int r = make_force(ctx, &fm64, F);
     if (r != KETE_OK) return r;

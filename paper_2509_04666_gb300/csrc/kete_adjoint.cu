@@ -171,6 +171,7 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
     StopWalk W;
     StepState S;
     S.have_a0 = false;
+    S.ng = nullptr;   // the adjoint differentiates gravity only
     const LegView L = leg_view(nullptr, 0);
     double *rec = nullptr;
     bool first = true;

@@ -325,19 +325,31 @@ __device__ __forceinline__ void newton_jacobian(double mu, const double r[3], do
     J[5] = fma(k * r[2], r[2], J[5] + f);
 }
 
+// Non-gravitational terms of one body (App. A.4-A.5), defined with the
+// two-body solver below; returned by value so that no caller array needs an
+// address.  Only bodies with kete_nongrav parameters make the call.
+struct NgOut {
+    double a[3];
+    int status;
+};
+static __device__ __noinline__ NgOut nongrav_terms(const EphemDev &E, const double *row64, Seg g,
+                                                   const kete_nongrav *P, double x0, double x1,
+                                                   double x2, double v0, double v1, double v2);
+
 // Full-FP64 acceleration.
 // detect (step start, off = 0): also record in enc the nearest planet within
 // kEncounterAu and its relative position; otherwise enc is read.
 // JAC: also return in J the Newtonian da/dx (see newton_jacobian), from the
 // same relative vectors as the force.  G: lanes per body (see LaneGroup).
+// ng: the body's non-gravitational terms (null: none), added after the sum.
 template <bool JAC = false, int G = 1>
 __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, double t0,
                                           double off, const double *__restrict__ row64,
                                           const double x[3], const double v[3], double a[3],
                                           Encounter &enc, const double dx[3], bool detect,
-                                          double *J = nullptr)
+                                          double *J = nullptr, const kete_nongrav *ng = nullptr)
 {
-    Seg g;
+    Seg g = {0, 0.0};
     a[0] = a[1] = a[2] = 0.0;
     if (JAC) {
 #pragma unroll
@@ -387,6 +399,13 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
         }
         if (detect) encounter_reduce<G>(best, enc);
     }
+    if (ng) {
+        const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2]);
+        if (o.status != KETE_BODY_OK) return o.status;
+        a[0] += o.a[0];
+        a[1] += o.a[1];
+        a[2] += o.a[2];
+    }
     return KETE_BODY_OK;
 }
 
@@ -407,9 +426,9 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
                                            const float *__restrict__ row32, uint32_t &close,
                                            const double x[3], const double v[3], double a[3],
                                            double as[3], Encounter &enc, const double dx[3],
-                                           bool detect)
+                                           bool detect, const kete_nongrav *ng = nullptr)
 {
-    Seg g;
+    Seg g = {0, 0.0};
     as[0] = as[1] = as[2] = 0.0;
     if (detect) {
         close = 0;
@@ -505,6 +524,13 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
             close = LaneGroup<G>::bit_or(close);
             encounter_reduce<G>(best, enc);
         }
+    }
+    if (ng) {   // FP64, part of the smooth FP64 sum that controls the step
+        const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2]);
+        if (o.status != KETE_BODY_OK) return o.status;
+        as[0] += o.a[0];
+        as[1] += o.a[1];
+        as[2] += o.a[2];
     }
     a[0] = as[0] + (double)af[0];
     a[1] = as[1] + (double)af[1];
@@ -624,6 +650,61 @@ __device__ __forceinline__ bool kepler_uv(double mu, double sqmu, const double r
     v[1] = fma(fd, r0[1], gd * v0[1]);
     v[2] = fma(fd, r0[2], gd * v0[2]);
     return ok;
+}
+
+// Non-gravitational terms (App. A.4-A.5) of a body at barycentric (x, v):
+// heliocentric r, w from the Sun's state at the same epoch (node row or
+// table), then radiation pressure with drag (Eq. A.6, radial-speed reading)
+// and the JPL comet model (Eq. A.7) from the two-body state dt days earlier.
+static __device__ __noinline__ NgOut nongrav_terms(const EphemDev &E, const double *row64, Seg g,
+                                                   const kete_nongrav *P, double x0, double x1,
+                                                   double x2, double v0, double v1, double v2)
+{
+    NgOut o = {{0.0, 0.0, 0.0}, KETE_BODY_OK};
+    double sun[6];
+    if (row64) {
+#pragma unroll
+        for (int q = 0; q < 6; q++) sun[q] = __ldg(row64 + q);
+    } else {
+        cheb_state64(E, 0, g.s, g.tau, sun, true);
+    }
+    const kete_nongrav p = *P;
+    const double mu = E.gm[0];
+    const double r[3] = {x0 - sun[0], x1 - sun[1], x2 - sun[2]};
+    const double w[3] = {v0 - sun[3], v1 - sun[4], v2 - sun[5]};
+    if (p.beta != 0.0) {
+        const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const double rn = sqrt(rr);
+        const double rdot = (r[0] * w[0] + r[1] * w[1] + r[2] * w[2]) / rn;
+        const double f = p.beta * mu / rr;
+        const double kr = f * (1.0 - rdot * kInvC) / rn, kw = f * kInvC;
+#pragma unroll
+        for (int c = 0; c < 3; c++) o.a[c] = kr * r[c] - kw * w[c];
+    }
+    if (p.a1 != 0.0 || p.a2 != 0.0 || p.a3 != 0.0) {
+        double rl[3] = {r[0], r[1], r[2]}, wl[3] = {w[0], w[1], w[2]};
+        if (p.dt != 0.0) {
+            double chi = 0.0;
+            if (!kepler_uv(mu, sqrt(mu), r, w, -p.dt, chi, rl, wl)) {
+                o.status = KETE_BODY_KEPLER_CAP;
+                return o;
+            }
+        }
+        const double rn = sqrt(rl[0] * rl[0] + rl[1] * rl[1] + rl[2] * rl[2]);
+        const double q = rn / p.r0;
+        const double gq = p.alpha * pow(q, -p.m) * pow(1.0 + pow(q, p.n), -p.k);
+        const double rh[3] = {rl[0] / rn, rl[1] / rn, rl[2] / rn};
+        double h[3] = {rl[1] * wl[2] - rl[2] * wl[1], rl[2] * wl[0] - rl[0] * wl[2],
+                       rl[0] * wl[1] - rl[1] * wl[0]};
+        const double hn = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+        const double nh[3] = {h[0] / hn, h[1] / hn, h[2] / hn};
+        const double th[3] = {nh[1] * rh[2] - nh[2] * rh[1], nh[2] * rh[0] - nh[0] * rh[2],
+                              nh[0] * rh[1] - nh[1] * rh[0]};
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            o.a[c] += gq * (p.a1 * rh[c] + p.a2 * th[c] + p.a3 * nh[c]);
+    }
+    return o;
 }
 
 // RA/Dec (equatorial J2000) of an ecliptic vector

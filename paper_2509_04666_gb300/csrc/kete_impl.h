@@ -33,6 +33,7 @@ struct ForceDev {
     float gm32[KETE_MAX_BODIES];
     float j2k32[KETE_MAX_BODIES];
     float pole32[KETE_MAX_BODIES][3];
+    const kete_nongrav *nongrav;        // per-body non-gravitational terms or null
 };
 
 // device counters accumulated by the kernels

@@ -39,7 +39,9 @@ void upload_radau_tables(cudaStream_t st) { upload_step_tables(st); }
 // body that has made more than q.budget step attempts per stop reached is
 // set aside at its next step boundary (state and stop saved, index appended
 // to q.defer) for a second launch with more lanes per body.
-template <int MODE, int G>
+// NG: bodies may carry non-gravitational terms (F.nongrav); the instantiation
+// without them has those branches compiled out.
+template <int MODE, int G, bool NG>
 __global__ void __launch_bounds__(128, KETE_PROP_MIN_BLOCKS)
 k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ stops,
             int n_stops, double *__restrict__ out, int64_t out_stride, int keep_on_fail,
@@ -60,6 +62,7 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
     long long attempts = 0, body_attempts = 0;
     StepState S;
     S.have_a0 = false;
+    S.ng = nullptr;
     LegView L = leg_view(nullptr, 0);
     bool first = true;
     for (;;) {
@@ -94,6 +97,7 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
                     attempts = 0;
                     body_attempts = 0;
                     S.have_a0 = false;
+                    S.ng = (NG && F.nongrav) ? F.nongrav + i : nullptr;
                     L = leg_view(use_nt ? &nt : nullptr, leg0 + k);
                     if (status == KETE_BODY_OK && k < n_stops) aim_step(F, t, stops[k], dt);
                 } else {
@@ -303,7 +307,7 @@ static int ws_blocks(int block)
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<MODE, G>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<MODE, G, false>, block, 0);
     return (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
 }
 
@@ -318,8 +322,12 @@ static void launch_k(int64_t grid, int block, cudaStream_t st, const EphemDev &E
                      double *out, int64_t stride, int kof, DevCounters *ctr, NodeTable t, int unt,
                      int leg0, unsigned long long *next, int refill, PropQueue q)
 {
-    k_propagate<MODE, G><<<(unsigned)grid, block, 0, st>>>(E, F, cs, stops, n_stops, out, stride,
-                                                          kof, ctr, t, unt, leg0, next, refill, q);
+    if (F.nongrav)
+        k_propagate<MODE, G, true><<<(unsigned)grid, block, 0, st>>>(
+            E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, refill, q);
+    else
+        k_propagate<MODE, G, false><<<(unsigned)grid, block, 0, st>>>(
+            E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, refill, q);
 }
 
 template <int MODE>

@@ -96,13 +96,13 @@ __device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, doubl
                                      const double *row64, const float *row32, uint32_t &close,
                                      const double x[3], const double v[3], double a[3],
                                      double as[3], Encounter &enc, const double dx[3], bool detect,
-                                     double *jout = nullptr)
+                                     double *jout = nullptr, const kete_nongrav *ng = nullptr)
 {
     static_assert(!(JAC && MODE == KETE_MIXED), "Jacobian capture is FP64 only");
     if (MODE == KETE_MIXED)
-        return accel_mixed<G>(E, F, t0, off, row64, row32, close, x, v, a, as, enc, dx, detect);
+        return accel_mixed<G>(E, F, t0, off, row64, row32, close, x, v, a, as, enc, dx, detect, ng);
     double J[6];
-    int st = accel_fp64<JAC, G>(E, F, t0, off, row64, x, v, a, enc, dx, detect, J);
+    int st = accel_fp64<JAC, G>(E, F, t0, off, row64, x, v, a, enc, dx, detect, J, ng);
     as[0] = a[0]; as[1] = a[1]; as[2] = a[2];
     if (JAC) {
 #pragma unroll
@@ -122,7 +122,8 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
                                              const double a0[3], const double as0[3],
                                              uint32_t close, Encounter enc, double h,
                                              LegRows rows, double x1[3], double v1[3],
-                                             double &err, Cnt &cnt, double *jrec = nullptr)
+                                             double &err, Cnt &cnt, double *jrec = nullptr,
+                                             const kete_nongrav *ng = nullptr)
 {
     double b[7][3], g[7][3];
 #pragma unroll
@@ -165,7 +166,7 @@ __device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &
             const double *r64 = rows.r64 ? rows.r64 + n * rows.stride64 : nullptr;
             const float *r32 = rows.r32 ? rows.r32 + n * rows.stride64 : nullptr;
             int st = accel<MODE, JAC, G>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs, enc, dxn,
-                                         false, JAC ? jrec + 6 * n : nullptr);
+                                         false, JAC ? jrec + 6 * n : nullptr, ng);
             cnt.evals++;
             if (r64) cnt.node_evals++;
             if (st != KETE_BODY_OK) return st;
@@ -235,6 +236,7 @@ struct StepState {
     double t_stop;          // end of the step's range: the target, or the next table
                             // segment boundary during an encounter
     bool have_a0;           // a0 valid for (x, v, t): kept across a rejection
+    const kete_nongrav *ng; // the body's non-gravitational terms (null: none)
 };
 
 // Node-table view of leg kg (null pointers: no rows).
@@ -280,7 +282,7 @@ __device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, c
         const double zero[3] = {0.0, 0.0, 0.0};
         int st = accel<MODE, JAC, G>(E, F, t, 0.0, at_start ? L.r64 : nullptr,
                                      at_start ? L.r32 : nullptr, S.close, x, v, S.a0, S.as0,
-                                     S.enc, zero, true, jrec);
+                                     S.enc, zero, true, jrec, S.ng);
         cnt.evals++;
         if (at_start) cnt.node_evals++;
         if (st != KETE_BODY_OK) return st;
@@ -307,7 +309,7 @@ __device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, c
     }
     double x1[3], v1[3], err;
     int st = radau_attempt<MODE, JAC, G>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, h, rows,
-                                         x1, v1, err, cnt, jrec);
+                                         x1, v1, err, cnt, jrec, S.ng);
     if (st != KETE_BODY_OK) return st;
     double dt_new;
     if (isfinite(err) && err >= 2.2250738585072014e-308)

@@ -44,7 +44,7 @@ class ForceModel(C.Structure):
                 ("pole_ra", C.c_double * 16), ("pole_dec", C.c_double * 16),
                 ("eps", C.c_double), ("eps_pc", C.c_double), ("safety", C.c_double),
                 ("dt_init", C.c_double), ("max_iter", C.c_int32), ("reserved", C.c_int32),
-                ("max_steps", C.c_int64)]
+                ("max_steps", C.c_int64), ("nongrav", C.c_void_p)]
 
 
 class SurveyOpts(C.Structure):
@@ -123,6 +123,17 @@ def force_model(**kw) -> ForceModel:
         else:
             setattr(fm, k, v)
     return fm
+
+
+NONGRAV_FIELDS = ("a1", "a2", "a3", "alpha", "r0", "m", "n", "k", "dt", "beta")
+
+
+def nongrav_to_device(params, device) -> torch.Tensor:
+    """Per-body non-gravitational records (a structured array with the
+    kete_nongrav fields) -> CUDA float64 [n, 10].  Set the force model's
+    nongrav to its data_ptr() and keep the tensor alive for the call."""
+    a = np.stack([np.asarray(params[f], np.float64) for f in NONGRAV_FIELDS], axis=-1)
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device)
 
 
 def survey_opts(**kw) -> SurveyOpts:

@@ -679,6 +679,42 @@ def mag_params(labels, seed=SEED_BASE + 7):
     return out
 
 
+NONGRAV_DTYPE = np.dtype([(f, "<f8") for f in ("a1", "a2", "a3", "alpha", "r0", "m", "n", "k",
+                                                "dt", "beta")])
+assert NONGRAV_DTYPE.itemsize == 80
+
+
+def nongrav_params(labels, seed=SEED_BASE + 9, dust_frac=0.0, yarkovsky_every=10):
+    """Non-gravitational terms per body (kete_nongrav records).
+    Comets (label 3): JPL comet model with the comet g(r) (alpha 0.1112620426,
+    r0 2.808 AU, m 2.15, n 5.093, k 4.6142), A1 ~ logU[1e-9, 1e-7] AU/d^2,
+    A2 = +-logU[1e-10, 1e-8], A3 ~ N(0, 1e-9); half of them with a thermal
+    lag dt ~ U[5, 40] d.  Every `yarkovsky_every`-th other body: a transverse
+    A2 ~ N(0, 1e-13) with g = 1/r^2 (asteroid defaults).  A `dust_frac` share
+    of the rest: radiation pressure beta ~ logU[1e-3, 0.1]."""
+    labels = np.asarray(labels)
+    n = labels.size
+    rng = _rng(seed, 9)
+    out = np.zeros(n, NONGRAV_DTYPE)
+    com = np.nonzero(labels == 3)[0]
+    out["alpha"][com], out["r0"][com], out["m"][com] = 0.1112620426, 2.808, 2.15
+    out["n"][com], out["k"][com] = 5.093, 4.6142
+    out["a1"][com] = 10.0 ** rng.uniform(-9.0, -7.0, com.size)
+    out["a2"][com] = np.where(rng.uniform(size=com.size) < 0.5, -1.0, 1.0) \
+        * 10.0 ** rng.uniform(-10.0, -8.0, com.size)
+    out["a3"][com] = rng.normal(0.0, 1e-9, com.size)
+    lag = rng.uniform(5.0, 40.0, com.size)
+    out["dt"][com] = np.where(np.arange(com.size) % 2 == 0, lag, 0.0)
+    rest = np.nonzero(labels != 3)[0]
+    yk = rest[::yarkovsky_every] if yarkovsky_every else rest[:0]
+    out["alpha"][yk], out["r0"][yk], out["m"][yk], out["n"][yk] = 1.0, 1.0, 2.0, 1.0
+    out["a2"][yk] = rng.normal(0.0, 1e-13, yk.size)
+    others = np.setdiff1d(rest, yk)
+    dust = others[rng.uniform(size=others.size) < dust_frac]
+    out["beta"][dust] = 10.0 ** rng.uniform(-3.0, -1.0, dust.size)
+    return out
+
+
 def adjoint90(n_bodies=100_000, n_obs=20, days=90.0, seed=None, neo_frac=0.02):
     """Orbit-fit inputs: bodies drawn as in wise1y, n_obs observation epochs per
     body ~ U[T0, T0 + days] (sorted) seen from the circular 1-AU observer of

@@ -52,11 +52,13 @@ def test_struct_layouts_match_header(tmp_path):
     prog.write_text('#include "kete.h"\n#include <stdio.h>\n#include <stddef.h>\n'
                     'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(kete_force_model),'
                     ' sizeof(kete_frame), sizeof(kete_survey_opts), sizeof(kete_hit),'
-                    ' sizeof(kete_stats), offsetof(kete_frame, normals)); printf("%zu %zu\\n",'
-                    ' sizeof(kete_obs), sizeof(kete_mag_params)); return 0;}\n')
+                    ' sizeof(kete_stats), offsetof(kete_frame, normals)); printf("%zu %zu %zu\\n",'
+                    ' sizeof(kete_obs), sizeof(kete_mag_params), sizeof(kete_nongrav));'
+                    ' return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
-    fm, fr, so, hit, stats, noff, ob, mg = map(int, subprocess.check_output([str(exe)]).split())
+    fm, fr, so, hit, stats, noff, ob, mg, ng = map(int,
+                                                   subprocess.check_output([str(exe)]).split())
     assert fm == C.sizeof(kete.ForceModel)
     assert so == C.sizeof(kete.SurveyOpts)
     assert stats == C.sizeof(kete.Stats)
@@ -65,6 +67,7 @@ def test_struct_layouts_match_header(tmp_path):
     assert hit == 32
     assert ob == W.OBS_DTYPE.itemsize == 48
     assert mg == W.MAG_DTYPE.itemsize == 24
+    assert ng == W.NONGRAV_DTYPE.itemsize == 80
 
 
 def test_force_model_defaults_without_gpu(libpath):
