@@ -102,7 +102,10 @@ def test_nongrav_terms_act_and_zero_terms_change_nothing(K, pop):
     # all-zero records: bit for bit the gravity-only result
     assert np.array_equal(zero, plain)
     moved = np.abs(withng[:3] - plain[:3]).max(axis=0)
-    assert (moved[w.labels == 3] > 1e-6).mean() > 0.9            # comets: ~1e-4 AU in a year
+    # comets: g(r) falls as r^-(m + n k) ~ r^-26 beyond r0 = 2.8 AU, so only the
+    # comets that come in close during the year move by much
+    com = moved[w.labels == 3]
+    assert com.max() > 1e-5 and (com > 1e-6).sum() >= 10, np.sort(com)[-12:]
     assert (moved[ng["beta"] > 0] > 1e-5).all()                  # dust: a weaker Sun
     untouched = (ng["a1"] == 0) & (ng["a2"] == 0) & (ng["a3"] == 0) & (ng["beta"] == 0)
     assert (moved[untouched] == 0).all()
