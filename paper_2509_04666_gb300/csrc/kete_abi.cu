@@ -435,7 +435,7 @@ extern "C" int kete_ephem_eval(kete_ctx *ctx, const double *t, int64_t n, int bo
 // queue length.
 static int cost_order(kete_ctx *ctx, const double *states, int64_t stride, const double *epochs,
                       int64_t n, const double *stops_dev, int n_stops, const double *t_end_i,
-                      int32_t **order, unsigned long long **order_n)
+                      const kete_nongrav *ng, int32_t **order, unsigned long long **order_n)
 {
     OrderScratch s;
     const size_t nh = order_hist_elems(n);
@@ -453,9 +453,9 @@ static int cost_order(kete_ctx *ctx, const double *states, int64_t stride, const
     }
     const unsigned long long nn = (unsigned long long)n;
     CUDA_TRY(cudaMemcpyAsync(*order_n, &nn, sizeof(nn), cudaMemcpyHostToDevice, ctx->stream));
-    CUDA_TRY(order_by_cost(ctx->E, states, stride, epochs, n, t_end, t_end_i, s, *order,
+    CUDA_TRY(order_by_cost(ctx->E, states, stride, epochs, n, t_end, t_end_i, ng, s, *order,
                            ctx->stream));
-    ctx->extra_launches += order_launches(n);
+    ctx->extra_launches += order_launches(n, ng);
     return KETE_OK;
 }
 
@@ -480,7 +480,7 @@ static int propagate(kete_ctx *ctx, const ForceDev &F, ChainState cs, const doub
     unsigned long long *order_n = nullptr;
     if (var.order) {
         int r = cost_order(ctx, cs.w, cs.n, cs.w + 6 * cs.n, cs.n, stops_dev, n_stops, nullptr,
-                           &order, &order_n);
+                           F.nongrav, &order, &order_n);
         if (r != KETE_OK) return r;
     }
     ctx->stats.prop_kind = var.kind;
@@ -1133,7 +1133,7 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
                 unsigned long long *order_n;
                 CUDA_TRY(launch_adjoint_last_epoch(P, i0, nc, t_end, ctx->stream));
                 int r2 = cost_order(ctx, states + i0, n, epochs + i0, nc, nullptr, 0, t_end,
-                                    &order, &order_n);
+                                    nullptr, &order, &order_n);
                 if (r2 != KETE_OK) return r2;
                 launches += 1;
             }

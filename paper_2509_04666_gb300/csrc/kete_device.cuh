@@ -692,7 +692,11 @@ static __device__ __noinline__ NgOut nongrav_terms(const EphemDev &E, const doub
         }
         const double rn = sqrt(rl[0] * rl[0] + rl[1] * rl[1] + rl[2] * rl[2]);
         const double q = rn / p.r0;
-        const double gq = p.alpha * pow(q, -p.m) * pow(1.0 + pow(q, p.n), -p.k);
+        // g(r); the asteroid form (m = 2, k = 0: alpha / q^2) without pow
+        double gq = p.alpha;
+        if (p.m == 2.0) gq /= q * q;
+        else gq *= pow(q, -p.m);
+        if (p.k != 0.0) gq *= pow(1.0 + pow(q, p.n), -p.k);
         const double rh[3] = {rl[0] / rn, rl[1] / rn, rl[2] / rn};
         double h[3] = {rl[1] * wl[2] - rl[2] * wl[1], rl[2] * wl[0] - rl[0] * wl[2],
                        rl[0] * wl[1] - rl[1] * wl[0]};

@@ -9,8 +9,12 @@
 // scales with the local dynamical time r^1.5 / sqrt(mu), so the number of
 // steps over [t, t_end] is about  integral dt / (c r^1.5),  evaluated at 8
 // epochs of the two-body motion.  A stable counting sort on 256 log-spaced
-// buckets gives the order.  The order changes only which lane takes which
-// body: every body's arithmetic, and so every result, is unchanged.
+// buckets gives the order.  With non-gravitational terms the bodies are first
+// grouped by class (thermal-lag terms, which cost a two-body solve per force
+// evaluation; other terms; none), so that a warp's lanes take the extra work
+// together or not at all: 3 x 256 buckets.  The order changes only which lane
+// takes which body: every body's arithmetic, and so every result, is
+// unchanged.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,13 +25,19 @@
 
 namespace kete {
 
-constexpr int kOrderBuckets = 256;
+constexpr int kCostBuckets = 256;               // per class
+constexpr int kMaxClasses = 3;
+constexpr int kMaxBuckets = kCostBuckets * kMaxClasses;
 constexpr int kOrderTile = 1024;   // elements per block of the counting sort
 
-// bucket of body i: 255 for the most expensive bodies, 0 for the cheapest
+static int n_classes(const kete_nongrav *ng) { return ng ? kMaxClasses : 1; }
+
+// key of body i: class (lagged terms, other terms, none) first, then cost,
+// most expensive first (ascending key)
 __global__ void k_order_keys(EphemDev E, const double *__restrict__ w, int64_t stride,
                              const double *__restrict__ epochs, int64_t n, double t_end,
-                             const double *__restrict__ t_end_i, uint8_t *__restrict__ key)
+                             const double *__restrict__ t_end_i, const kete_nongrav *__restrict__ ng,
+                             uint16_t *__restrict__ key)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -56,34 +66,40 @@ __global__ void k_order_keys(EphemDev E, const double *__restrict__ w, int64_t s
     // log-spaced buckets, 16 per octave above cost 2^-4
     int b = 0;
     if (cost > 0.0 && isfinite(cost)) b = (int)floor(16.0 * (log2(cost) + 4.0));
-    b = b < 0 ? 0 : (b > kOrderBuckets - 1 ? kOrderBuckets - 1 : b);
-    key[i] = (uint8_t)(kOrderBuckets - 1 - b);   // ascending key = descending cost
+    b = b < 0 ? 0 : (b > kCostBuckets - 1 ? kCostBuckets - 1 : b);
+    int cls = 0;   // 0: thermal-lag terms, 1: other terms, 2: none (without ng: 0)
+    if (ng) {
+        const kete_nongrav p = ng[i];
+        const bool jpl = p.a1 != 0.0 || p.a2 != 0.0 || p.a3 != 0.0;
+        cls = (jpl && p.dt != 0.0) ? 0 : ((jpl || p.beta != 0.0) ? 1 : 2);
+    }
+    key[i] = (uint16_t)(cls * kCostBuckets + (kCostBuckets - 1 - b));
 }
 
 // hist[key][tile]: the keys of each tile of kOrderTile bodies
-__global__ void k_order_hist(const uint8_t *__restrict__ key, int64_t n, int32_t *__restrict__ hist,
-                             int64_t n_tiles)
+__global__ void k_order_hist(const uint16_t *__restrict__ key, int64_t n, int n_buckets,
+                             int32_t *__restrict__ hist, int64_t n_tiles)
 {
-    __shared__ int32_t cnt[kOrderBuckets];
-    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) cnt[b] = 0;
+    __shared__ int32_t cnt[kMaxBuckets];
+    for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kOrderTile;
     for (int j = threadIdx.x; j < kOrderTile; j += blockDim.x)
         if (base + j < n) atomicAdd(&cnt[key[base + j]], 1);
     __syncthreads();
-    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
+    for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
         hist[(int64_t)b * n_tiles + blockIdx.x] = cnt[b];
 }
 
 // stable scatter: within a tile, bodies of equal key keep their index order
 // (warps in turn, lanes by rank among equal keys)
 __global__ void __launch_bounds__(256)
-k_order_scatter(const uint8_t *__restrict__ key, int64_t n, const int64_t *__restrict__ off,
-                int64_t n_tiles, int32_t *__restrict__ order)
+k_order_scatter(const uint16_t *__restrict__ key, int64_t n, int n_buckets,
+                const int64_t *__restrict__ off, int64_t n_tiles, int32_t *__restrict__ order)
 {
-    __shared__ int64_t next[kOrderBuckets];
+    __shared__ int64_t next[kMaxBuckets];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
+    for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
         next[b] = off[(int64_t)b * n_tiles + blockIdx.x];
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kOrderTile;
@@ -105,29 +121,32 @@ k_order_scatter(const uint8_t *__restrict__ key, int64_t n, const int64_t *__res
 
 cudaError_t order_by_cost(const EphemDev &E, const double *states, int64_t stride,
                           const double *epochs, int64_t n, double t_end, const double *t_end_i,
-                          OrderScratch s, int32_t *order, cudaStream_t st)
+                          const kete_nongrav *ng, OrderScratch s, int32_t *order, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const int64_t n_tiles = (n + kOrderTile - 1) / kOrderTile;
+    const int nb = kCostBuckets * n_classes(ng);
     k_order_keys<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(E, states, stride, epochs, n, t_end,
-                                                              t_end_i, s.key);
-    k_order_hist<<<(unsigned)n_tiles, 256, 0, st>>>(s.key, n, s.hist, n_tiles);
+                                                              t_end_i, ng, s.key);
+    k_order_hist<<<(unsigned)n_tiles, 256, 0, st>>>(s.key, n, nb, s.hist, n_tiles);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = exclusive_scan(s.hist, (int64_t)kOrderBuckets * n_tiles, s.off, s.scan_tmp, st);
+    e = exclusive_scan(s.hist, (int64_t)nb * n_tiles, s.off, s.scan_tmp, st);
     if (e != cudaSuccess) return e;
-    k_order_scatter<<<(unsigned)n_tiles, 256, 0, st>>>(s.key, n, s.off, n_tiles, order);
+    k_order_scatter<<<(unsigned)n_tiles, 256, 0, st>>>(s.key, n, nb, s.off, n_tiles, order);
     return cudaGetLastError();
 }
 
-int order_launches(int64_t n)
+int order_launches(int64_t n, const kete_nongrav *ng)
 {
-    return n <= 0 ? 0 : 3 + scan_launches((int64_t)order_hist_elems(n));
+    if (n <= 0) return 0;
+    const int64_t n_tiles = (n + kOrderTile - 1) / kOrderTile;
+    return 3 + scan_launches((int64_t)kCostBuckets * n_classes(ng) * n_tiles);
 }
 
 size_t order_hist_elems(int64_t n)
 {
-    return (size_t)kOrderBuckets * (size_t)((n + kOrderTile - 1) / kOrderTile);
+    return (size_t)kMaxBuckets * (size_t)((n + kOrderTile - 1) / kOrderTile);
 }
 
 }  // namespace kete
