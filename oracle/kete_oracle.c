@@ -863,6 +863,17 @@ int ko_in_polygon(const ko_frame *f, const double u[3], double *margin)
     int inside = 1;
     double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     double mg = INFINITY;
+    if (f->n_edges == 0) {
+        /* cone (Sec. 3.1): inside iff the angle between u and the centre
+         * normals[0] is below the radius normals[1][0] */
+        const double *cv = f->normals[0];
+        const double rho = f->normals[1][0];
+        double cn = sqrt(cv[0] * cv[0] + cv[1] * cv[1] + cv[2] * cv[2]);
+        double d = cv[0] * u[0] + cv[1] * u[1] + cv[2] * u[2];
+        inside = d > cos(rho) * cn * un;
+        if (margin) *margin = rho - acos(fmax(-1.0, fmin(1.0, d / (cn * un))));
+        return inside;
+    }
     for (int k = 0; k < f->n_edges; k++) {
         const double *nv = f->normals[k];
         double d = nv[0] * u[0] + nv[1] * u[1] + nv[2] * u[2];
@@ -1035,6 +1046,13 @@ int ko_fov_check(const ko_ephem *e, const ko_force_model *fm, const double *stat
     double (*centre)[4] = (double (*)[4])malloc(sizeof(double) * 4 * (n_frames ? n_frames : 1));
     for (int64_t i = 0; i < n_frames; i++) {
         const ko_frame *f = &frames[i];
+        if (f->n_edges == 0) {          /* cone: its own centre and radius */
+            const double *cv = f->normals[0];
+            double cn = sqrt(cv[0] * cv[0] + cv[1] * cv[1] + cv[2] * cv[2]);
+            for (int c = 0; c < 3; c++) centre[i][c] = cv[c] / cn;
+            centre[i][3] = f->normals[1][0];
+            continue;
+        }
         double vs[2 * KO_MAX_EDGES * KO_MAX_EDGES][3], cs[3] = {0, 0, 0};
         int ne = f->n_edges, nv = 0;
         for (int a = 0; a < ne; a++)

@@ -143,6 +143,11 @@ int  ko_kepler(double mu, const double r0[3], const double v0[3], double dt,
 int  ko_apparent(const ko_ephem *e, const double st_ref[6], double t_ref, double t_obs,
                  const double obs[3], double u[3], double *tau);
 void ko_radec(const double u[3], double *ra, double *dec);
+/* FoV membership (Sec. 3.1).  n_edges 3..4: spherical polygon, inside iff
+ * normals[k].u > 0 for every edge; margin = min over edges of the angle of u
+ * above the edge's plane.  n_edges 0: cone of centre normals[0] and angular
+ * radius normals[1][0] (radians), inside iff angle(u, centre) < radius;
+ * margin = radius - angle.  Points on the boundary are outside. */
 int  ko_in_polygon(const ko_frame *f, const double u[3], double *margin);
 
 int64_t ko_make_batches(const double *epochs_sorted, int64_t n, double batch_span,

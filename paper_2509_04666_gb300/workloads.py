@@ -352,6 +352,22 @@ def population(seed: int, ps: PlanetSystem, n_mb: int, n_neo: int = 0, n_trojan:
 # ---------------------------------------------------------------------------
 # Fields of view: square spherical polygons with inward great-circle normals
 # ---------------------------------------------------------------------------
+def cone_frames(frames, which, radius):
+    """Turn frames[which] into cones (n_edges 0, Sec. 3.1): centre = the
+    frame's own centre direction (sum of its inward normals' axis, i.e. the
+    normalised sum of the normals), angular radius `radius` (radians) in
+    normals[1][0]; the rest of the record is zero."""
+    out = frames.copy()
+    idx = np.arange(len(frames))[which]
+    c = frames["normals"][idx].sum(axis=1)
+    c /= np.linalg.norm(c, axis=-1, keepdims=True)
+    out["n_edges"][idx] = 0
+    out["normals"][idx] = 0.0
+    out["normals"][idx, 0, :] = c
+    out["normals"][idx, 1, 0] = radius
+    return out
+
+
 def square_normals(centre, e_axis, half_width):
     """Inward normals m = p sin h - t cos h of the edges t = +e, +n, -e, -n, in
     that (cyclic) order around the square (Sec. 3.1)."""

@@ -114,6 +114,52 @@ def test_fov_boundary_is_outside():
     assert margin == 0.0
 
 
+def _cone(c, rho):
+    fr = np.zeros(1, W.FRAME_DTYPE)[0]
+    fr["n_edges"] = 0
+    fr["normals"][0] = c
+    fr["normals"][1][0] = rho
+    return fr
+
+
+def test_cone_matches_angular_distance():
+    """Cone FoVs (Sec. 3.1): inside iff the angle to the centre, taken here
+    as atan2(|c x u|, c.u), is below the radius."""
+    rng = np.random.default_rng(12)
+    n_checked = 0
+    for _ in range(200):
+        c = rng.normal(size=3) * rng.uniform(0.1, 10)
+        rho = rng.uniform(0.001, 1.5)
+        fr = _cone(c, rho)
+        for _ in range(20):
+            # directions spread around the boundary
+            u = c / np.linalg.norm(c) + rng.normal(size=3) * rng.uniform(0.0, 2.0 * rho)
+            u *= rng.uniform(0.1, 30) / np.linalg.norm(u)
+            ang = math.atan2(np.linalg.norm(np.cross(c, u)), c @ u)
+            inside, margin = O.in_polygon(fr, u)
+            assert abs(margin - (rho - ang)) < 1e-7
+            if abs(ang - rho) > 1e-12:
+                assert inside == (ang < rho)
+                n_checked += 1
+        assert not O.in_polygon(fr, -c)[0] and O.in_polygon(fr, c)[0]
+    assert n_checked > 3000
+    # a hemisphere: the boundary (c.u = 0) is outside
+    assert not O.in_polygon(_cone([0, 0, 1.0], math.pi / 2), np.array([1.0, 0, 0]))[0]
+    assert O.in_polygon(_cone([0, 0, 1.0], math.pi / 2), np.array([1.0, 0, 1e-9]))[0]
+
+
+def test_cone_frames_prefilter_equals_brute_force(mb1k_dense):
+    w = mb1k_dense
+    fr = W.cone_frames(w.frames, slice(0, None, 2), math.radians(0.6))
+    orc = O.Oracle(w.ephem.to_bytes())
+    fm = orc.force_model()
+    brute, _, _ = orc.fov_check(fm, w.states, w.epochs, fr, w.observers)
+    fast, _, _ = orc.fov_check(fm, w.states, w.epochs, fr, w.observers, prefilter_deg=0.5)
+    cones = fr["n_edges"][brute["frame"]] == 0
+    assert cones.sum() > 50 and (~cones).sum() > 50
+    np.testing.assert_array_equal(brute[["frame", "body"]], fast[["frame", "body"]])
+
+
 def test_radec_known_directions():
     eps = math.radians(84381.448 / 3600)
     ra, dec = O.radec(np.array([2.0, 0, 0]))
