@@ -116,16 +116,23 @@ typedef struct kete_force_model {
     const kete_nongrav *nongrav;
 } kete_force_model;
 
-/* One spherical polygon (Sec. 3.1).  Polygons with the same exposure_id must
- * be contiguous and share epoch and observer_idx: together they form the
- * union-of-detectors FoV of one exposure.  Frames must be sorted by epoch
- * (non-decreasing).  normals[k] is the inward normal of edge k (any length);
- * a direction u is inside iff normals[k].u > 0 for every k < n_edges. */
+/* One FoV patch (Sec. 3.1): a spherical polygon or a cone.  Patches with the
+ * same exposure_id must be contiguous and share epoch and observer_idx:
+ * together they form the union-of-detectors FoV of one exposure.  Frames
+ * must be sorted by epoch (non-decreasing).
+ *   n_edges 3..4, polygon: normals[k] is the inward normal of edge k (any
+ *   length); a direction u is inside iff normals[k].u > 0 for every k.
+ *   n_edges 0 (KETE_FRAME_CONE), cone: normals[0] is the centre direction
+ *   (any length), normals[1][0] the angular radius in radians (0 < r < pi);
+ *   u is inside iff its angle to the centre is below r.
+ * Boundary points are outside.  An extended exposure is approximated by
+ * several instantaneous frames along it (see the binding's streak_frames). */
+#define KETE_FRAME_CONE 0
 typedef struct kete_frame {
     double epoch;                /* TDB JD of the (instantaneous) observation */
     int64_t observer_idx;        /* row of the observers array */
     int64_t exposure_id;         /* groups the sub-fields of one exposure */
-    int32_t n_edges;             /* 3 or 4 */
+    int32_t n_edges;             /* 3 or 4 (polygon), 0 (cone) */
     int32_t reserved;
     double normals[KETE_MAX_EDGES][3];
 } kete_frame;                    /* 128 bytes */
@@ -246,7 +253,7 @@ int kete_propagate_stops(kete_ctx *ctx, const double *states, const double *epoc
  * KETE_ERR_CAPACITY, writes nothing to hits and leaves the count needed in
  * *n_hits (retry with a larger buffer).  status (device, [n], may be NULL).
  * Errors: BAD_ARG (sizes, unsorted epochs, inconsistent exposures, bad
- * observer index, n_edges outside 3..4), NO_EPHEM, EPHEM_SPAN (a batch epoch
+ * observer index, n_edges not 0, 3 or 4), NO_EPHEM, EPHEM_SPAN (a batch epoch
  * outside the table), CAPACITY, NOMEM, CUDA. */
 int kete_fov_check(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
                    const kete_frame *frames, int64_t n_frames, const double *observers,

@@ -682,7 +682,7 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
     if (flags & 1) return fail(ctx, KETE_ERR_BAD_ARG, "frames are not sorted by epoch");
     if (flags & 2) return fail(ctx, KETE_ERR_BAD_ARG, "frames of one exposure differ in epoch or observer");
     if (flags & 4) return fail(ctx, KETE_ERR_BAD_ARG, "observer_idx out of range");
-    if (flags & 8) return fail(ctx, KETE_ERR_BAD_ARG, "n_edges must be 3 or 4");
+    if (flags & 8) return fail(ctx, KETE_ERR_BAD_ARG, "n_edges must be 3 or 4 (polygon) or 0 (cone)");
     if (flags & 16) return fail(ctx, KETE_ERR_BAD_ARG, "non-finite or degenerate frame");
     const int64_t ne = h_ne;
     ExpArrays X;

@@ -63,11 +63,30 @@ __global__ void k_frame_prep(const kete_frame *__restrict__ fr, int64_t nf, int6
     }
     if (f.observer_idx < 0 || f.observer_idx >= n_obs) set_flag(ctr, 2);
     int ne = f.n_edges;
-    if (ne < 3 || ne > KETE_MAX_EDGES) {
+    if (ne != KETE_FRAME_CONE && (ne < 3 || ne > KETE_MAX_EDGES)) {
         set_flag(ctr, 3);
         ne = 3;
     }
     if (!isfinite(f.epoch)) set_flag(ctr, 4);
+    if (f.n_edges == KETE_FRAME_CONE) {
+        // cone: its own centre and radius
+        const double cn = sqrt(dot3(f.normals[0], f.normals[0]));
+        const double rho = f.normals[1][0];
+        double cen[3] = {1.0, 0.0, 0.0}, rad = kPi;
+        if (!(cn > 0.0) || !isfinite(cn) || !(rho > 0.0 && rho < kPi)) {
+            set_flag(ctr, 4);
+        } else {
+            for (int c = 0; c < 3; c++) cen[c] = f.normals[0][c] / cn;
+            rad = rho > 1.4 ? kPi : rho;   // as for polygons: wide cones cover everything
+        }
+        fcen[3 * i + 0] = cen[0];
+        fcen[3 * i + 1] = cen[1];
+        fcen[3 * i + 2] = cen[2];
+        fcen[3 * nf + i] = rad;
+        const float cr = (rad >= kPi) ? -2.0f : cosf((float)rad + kPadF);
+        faux[i] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], cr);
+        return;
+    }
     // vertices: intersections n_a x n_b (either sign) that satisfy every
     // other half-space; independent of the order the edges are listed in
     double cen[3] = {0, 0, 0};
@@ -614,6 +633,13 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
                 if (a.x * uf[0] + a.y * uf[1] + a.z * uf[2] < a.w) continue;
                 const kete_frame &fr = C.frames[f];
                 bool inside = true;
+                if (fr.n_edges == KETE_FRAME_CONE) {
+                    // angle(u, centre) < r  <=>  c.u > |c| |u| cos r
+                    const double *cv = fr.normals[0];
+                    const double cn = sqrt(dot3(cv, cv));
+                    inside = fma(cv[0], u[0], fma(cv[1], u[1], cv[2] * u[2])) >
+                             cos(fr.normals[1][0]) * cn * un;
+                }
                 for (int kq = 0; kq < fr.n_edges; kq++) {
                     const double *nv = fr.normals[kq];
                     if (!(fma(nv[0], u[0], fma(nv[1], u[1], nv[2] * u[2])) > 0.0)) inside = false;

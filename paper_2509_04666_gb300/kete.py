@@ -166,6 +166,43 @@ def mag_params_to_device(params: np.ndarray, device) -> torch.Tensor:
     return torch.from_numpy(a.view(np.uint8).reshape(-1).copy()).to(device)
 
 
+FRAME_CONE = 0
+
+
+def streak_frames(frame, t_start: float, t_end: float, observer_idx, exposure_id0: int):
+    """An extended exposure as len(observer_idx) instantaneous frames (Sec. 3.1:
+    extended events are approximated by several observations): copies of
+    `frame` (a kete_frame record, polygon or cone) at the midpoints of equal
+    sub-intervals of [t_start, t_end], sub-frame k seen from observers row
+    observer_idx[k], each its own exposure (ids exposure_id0 + k)."""
+    obs = np.asarray(observer_idx, np.int64)
+    k = obs.size
+    out = np.repeat(np.asarray(frame).reshape(1), k)
+    out["epoch"] = t_start + (np.arange(k) + 0.5) * (t_end - t_start) / k
+    out["observer_idx"] = obs
+    out["exposure_id"] = exposure_id0 + np.arange(k)
+    return out
+
+
+def merge_streak_hits(hits: dict, parent) -> dict:
+    """Union of the hits of each extended exposure: parent[f] names the
+    exposure frame f belongs to.  One row per (exposure, body), the earliest
+    sub-frame's (frames are sorted by epoch, hits by frame), sorted by
+    (exposure, body)."""
+    parent = np.asarray(parent, np.int64)
+    f = np.asarray(hits["frame"], np.int64)
+    b = np.asarray(hits["body"], np.int64)
+    key = parent[f] * (int(b.max()) + 1 if b.size else 1) + b
+    order = np.lexsort((f, key))               # by key, then earliest frame
+    key_s = key[order]
+    first = np.ones(key_s.size, bool)
+    first[1:] = key_s[1:] != key_s[:-1]
+    keep = order[first]
+    out = {k: np.asarray(v)[keep] for k, v in hits.items()}
+    out["exposure"] = parent[f[keep]]
+    return out
+
+
 def decode_hits(h: torch.Tensor, n: int):
     """kete_hit rows (int64 [n, 4] view) -> dict of CPU tensors."""
     h = h[:n].cpu()
