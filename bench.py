@@ -419,6 +419,67 @@ def ragged_leg(args, K, dev, flush, stream):
     return out
 
 
+def longspan_leg(args, K, dev, flush, stream):
+    """Backward propagation over decades and centuries: 20,000 bodies of the
+    survey population carried back 50 years, and 1,000 clones of a
+    Jupiter-family comet (JPL comet model) carried back 170 years, one lane
+    per body against lane groups of 8."""
+    import torch
+    import oracle as O
+    from paper_2509_04666_gb300 import kete, workloads as W
+    out = {}
+    legs = (("catalogue", W.backward_catalogue(n_bodies=args.back_bodies, years=50.0), None,
+             (("fp64", kete.FP64, 0), ("mixed", kete.MIXED, 0))),
+            ("clones", W.clones(n_clones=1000, years=170.0), "nongrav",
+             (("fp64", kete.FP64, 0), ("fp64_split8", kete.FP64, 8),
+              ("mixed_split8", kete.MIXED, 8))))
+    for leg, w, ngkey, variants in legs:
+        n = w.n_bodies
+        days = abs(w.t_end - W.T0)
+        K.load_ephem(w.ephem.to_bytes())
+        ng = w.meta[ngkey] if ngkey else None
+        ng_dev = kete.nongrav_to_device(ng, dev) if ng is not None else None
+        st0 = torch.from_numpy(w.states.copy()).to(dev)
+        res = {"workload": (f"{n} bodies of the survey population, {days / 365.25:.0f} years back"
+                            if leg == "catalogue" else
+                            f"{n} clones of a Jupiter-family comet (q 1.06 AU, JPL comet model), "
+                            f"{days / 365.25:.0f} years back")}
+        got = {}
+        for name, prec, split in variants:
+            K.set_propagation(prec, kete.PROP_WORK_STEALING, 128, split, 4 if split else 0)
+            fm = kete.force_model(precision=prec)
+            if ng_dev is not None:
+                fm.nongrav = ng_dev.data_ptr()
+            box = {}
+
+            def call():
+                s = st0.clone(); e = torch.full((n,), W.T0, dtype=torch.float64, device=dev)
+                box["st"] = s
+                return K.propagate(s, e, w.t_end, fm=fm)
+            call()
+            ms, status = _timed(stream, call, flush, 2)
+            stt = K.get_stats()
+            got[name] = box["st"].cpu().numpy()
+            res[name] = {"value": n * days / (ms / 1e3), "unit": "body-days/s", "ms": ms,
+                         "steps": stt["steps"], "deferred": stt["deferred"],
+                         "bodies_ok": int((status.cpu().numpy() == 0).sum())}
+        K.set_propagation(kete.FP64, kete.PROP_WORK_STEALING, 128)
+        K.set_propagation(kete.MIXED, kete.PROP_WORK_STEALING, 128)
+        # the oracle on a bounded sample: accuracy and the CPU rate
+        orc = O.Oracle(w.ephem.to_bytes())
+        sub = np.linspace(0, n - 1, 16 if leg == "clones" else 48).astype(np.int64)
+        t0 = time.perf_counter()
+        ref, _, _, _ = orc.propagate_many(orc.force_model(), w.states[:, sub], w.epochs[sub],
+                                          w.t_end, nongrav=None if ng is None else ng[sub])
+        dt = time.perf_counter() - t0
+        res["max_err_au"] = {k: float(np.abs(v[:3, sub] - ref[:3]).max()) for k, v in got.items()}
+        res["cpu_baseline"] = {"value": len(sub) * days / dt, "unit": "body-days/s",
+                               "kind": "oracle", "cores": min(os.cpu_count(), len(sub)),
+                               "sample": f"{len(sub)} bodies, {dt:.1f} s"}
+        out[leg] = res
+    return out
+
+
 def run_leg(args):
     """One leg alone (--leg adjoint|ragged), e.g. for a profiler; prints the
     leg's own JSON object, not the benchmark line."""
@@ -433,6 +494,8 @@ def run_leg(args):
     peak = 152 * 2 * 2 * 2.07e9 / 1e12
     if args.leg == "adjoint":
         out = adjoint_leg(args, K, dev, flush, stream, peak)
+    elif args.leg == "longspan":
+        out = longspan_leg(args, K, dev, flush, stream)
     else:
         out = ragged_leg(args, K, dev, flush, stream)
     print(json.dumps({"leg": args.leg, **out}))
@@ -607,7 +670,9 @@ def run_gb300(args):
                    "n_hits": int(nhg), "finite": int(np.isfinite(mags).sum()),
                    "median_mag": float(np.nanmedian(mags)) if np.isfinite(mags).any() else None,
                    "hit_list_unchanged": same}
-    adjoint = ragged = None
+    adjoint = ragged = longspan = None
+    if rank == 0 and world == 1 and not args.no_longspan:
+        longspan = longspan_leg(args, K, dev, flush, stream)
     if rank == 0 and world == 1 and not args.no_adjoint:
         adjoint = adjoint_leg(args, K, dev, flush, stream, peak_nominal)
     if rank == 0 and world == 1 and not args.no_ragged:
@@ -634,6 +699,7 @@ def run_gb300(args):
         "magnitudes": mag_leg,
         "adjoint": adjoint,
         "ragged": ragged,
+        "longspan": longspan,
         "e2e": e2e,
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "clocks": clocks,
@@ -666,11 +732,13 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-mag", action="store_true")
+    ap.add_argument("--no-longspan", action="store_true")
+    ap.add_argument("--back-bodies", type=int, default=20_000)
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--adj-bodies", type=int, default=100_000)
     ap.add_argument("--adj-sample", type=int, default=512)
     ap.add_argument("--ragged-bodies", type=int, default=500_000)
-    ap.add_argument("--leg", default="all", choices=["all", "adjoint", "ragged"],
+    ap.add_argument("--leg", default="all", choices=["all", "adjoint", "ragged", "longspan"],
                     help="run one leg alone (profiling); the default prints the benchmark line")
     args = ap.parse_args()
     if args.impl == "reference":

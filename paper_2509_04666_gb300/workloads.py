@@ -672,6 +672,57 @@ OBS_DTYPE = np.dtype([("epoch", "<f8"), ("ra", "<f8"), ("dec", "<f8"), ("obs", "
 assert OBS_DTYPE.itemsize == 48
 
 
+def backward_catalogue(n_bodies=20_000, years=50.0, seed=None, neo_frac=0.02):
+    """Whole-catalogue backward propagation (the pre-discovery use: every
+    numbered body carried back decades to an old plate epoch): wise1y's
+    population at T0 propagated to T0 - years (365.25-day years); the table
+    spans [T0 - years - 64 d, T0 + 64 d]."""
+    seed = SEED_BASE + 1 if seed is None else seed
+    ps = make_planets(seed)
+    n_neo = int(round(neo_frac * n_bodies))
+    states, labels = population(seed, ps, n_bodies - n_neo, n_neo)
+    t_end = T0 - 365.25 * years
+    eph = build_ephemeris(ps, t_end - 64.0, T0 + 64.0)
+    return Workload("backward", seed, eph, states, np.full(n_bodies, T0),
+                    np.zeros(0, FRAME_DTYPE), np.zeros((0, 3)), t_end, labels)
+
+
+# elements of the nominal Jupiter-family comet of the clone workload (a
+# 103P-like orbit: q ~ 1.06 AU, aphelion near Jupiter's orbit)
+CLONE_ELEMENTS = dict(a=3.47, e=0.694, inc=13.6, node=219.8, peri=181.3, M=0.0)
+
+
+def clones(n_clones=1000, years=170.0, seed=None):
+    """Monte-Carlo clones of one Jupiter-family comet propagated back over
+    centuries (the orbital-evolution use): the nominal orbit CLONE_ELEMENTS
+    (at perihelion at T0) plus Gaussian state offsets, sigma 1e-6 AU and
+    1e-8 AU/day per axis (a stand-in for a fit covariance); every clone
+    carries the JPL comet model with comet g(r), A1 = 1e-8 and A2 = 5e-10
+    AU/day^2 scattered by 5 % (meta['nongrav']).  Propagated to
+    T0 - years."""
+    seed = SEED_BASE + 11 if seed is None else seed
+    ps = make_planets(seed)
+    el = CLONE_ELEMENTS
+    r, v = elements_to_state(np.array([el["a"]]), np.array([el["e"]]), math.radians(el["inc"]),
+                             math.radians(el["node"]), math.radians(el["peri"]), el["M"],
+                             GM_SUN)
+    nominal = np.concatenate([r[:, 0] + ps.pos0[0], v[:, 0] + ps.vel0[0]])
+    rng = _rng(seed, 12)
+    states = nominal[:, None] + np.concatenate(
+        [rng.normal(0.0, 1e-6, (3, n_clones)), rng.normal(0.0, 1e-8, (3, n_clones))])
+    ng = np.zeros(n_clones, NONGRAV_DTYPE)
+    ng["alpha"], ng["r0"], ng["m"], ng["n"], ng["k"] = 0.1112620426, 2.808, 2.15, 5.093, 4.6142
+    ng["a1"] = 1e-8 * (1.0 + 0.05 * rng.normal(size=n_clones))
+    ng["a2"] = 5e-10 * (1.0 + 0.05 * rng.normal(size=n_clones))
+    t_end = T0 - 365.25 * years
+    eph = build_ephemeris(ps, t_end - 64.0, T0 + 64.0)
+    w = Workload("clones", seed, eph, states, np.full(n_clones, T0), np.zeros(0, FRAME_DTYPE),
+                 np.zeros((0, 3)), t_end, np.full(n_clones, 3, np.int8))
+    w.meta["nongrav"] = ng
+    w.meta["nominal"] = nominal
+    return w
+
+
 MAG_DTYPE = np.dtype([("kind", "<i4"), ("reserved", "<i4"), ("p1", "<f8"), ("p2", "<f8")])
 assert MAG_DTYPE.itemsize == 24
 
