@@ -671,7 +671,7 @@ def run_gb300(args):
                    "median_mag": float(np.nanmedian(mags)) if np.isfinite(mags).any() else None,
                    "hit_list_unchanged": same}
     adjoint = ragged = longspan = None
-    if rank == 0 and world == 1 and not args.no_longspan:
+    if rank == 0 and world == 1 and args.longspan:
         longspan = longspan_leg(args, K, dev, flush, stream)
     if rank == 0 and world == 1 and not args.no_adjoint:
         adjoint = adjoint_leg(args, K, dev, flush, stream, peak_nominal)
@@ -732,7 +732,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-mag", action="store_true")
-    ap.add_argument("--no-longspan", action="store_true")
+    ap.add_argument("--longspan", action="store_true",
+                    help="add the long-span leg (decades back; ~3 min) to the benchmark line")
     ap.add_argument("--back-bodies", type=int, default=20_000)
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--adj-bodies", type=int, default=100_000)
