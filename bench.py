@@ -38,9 +38,9 @@ MAS = math.radians(1.0 / 3.6e6)
 
 # DRAM traffic of one k_propagate launch from an ncu capture of a smaller case
 # of the same workload (profiles/k_propagate_wise1y.md: 100k bodies x 21 stops,
-# 389 MB), per body-stop, scaled to the full launch by its body-stops; valid
+# 385 MB), per body-stop, scaled to the full launch by its body-stops; valid
 # only while the kernel source is unchanged.
-PROFILED_TRAFFIC = {"src_sha": "b7125a756ce3d333", "bytes_per_body_stop": 185.3}
+PROFILED_TRAFFIC = {"src_sha": "67db26f011c52cb0", "bytes_per_body_stop": 183.2}
 
 
 def kernel_source_sha():
