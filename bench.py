@@ -61,28 +61,34 @@ def prop_flops(st, fm, n_coef, mixed):
       per force evaluation from node rows: per active mass 25 (Newton incl.
         relative position and velocity), +25 per GR mass (Eq. A.3), +21 per J2
         mass (Eq. A.4);
-      per-thread evaluation (step not spanning a whole leg): + a Clenshaw sum
-        of position and velocity per mass, 3 x (7 (n_coef - 1) + 4);
+      per-thread evaluation (step not spanning a whole leg): + 10 for the
+        segment lookup, + per mass the position series and per GR mass the
+        velocity series.  FP64 series are summed upward with the basis made on
+        the fly (three coordinates): position 6 + 8 (n_coef - 2), velocity
+        9 (n_coef - 2) + 3.  FP32 series (mixed precision) by Clenshaw:
+        position 3 (3 (n_coef - 1) + 3), velocity 3 (4 (n_coef - 1) + 1);
       per corrector iteration: 7 substep predictors (x, v) and the g/b
         updates, 1440 (+48 for the FP64-part b6 in mixed precision);
       per step attempt: final x, v and step control, 121.
     In mixed precision the FP64 work of an evaluation is the Sun's monopole
-    (19) plus, per-thread, the Sun's Clenshaw sum; the planetary terms are FP32.
-    Returns (fp64_flops, fp32_flops)."""
+    (19) plus, per-thread, the Sun's position and velocity series; the
+    planetary terms are FP32.  Returns (fp64_flops, fp32_flops)."""
     act, gr, j2 = _bits(fm.body_mask), _bits(fm.gr_mask), _bits(fm.j2_mask)
-    cheb = 3 * (7 * (n_coef - 1) + 4)
+    pos64, vel64 = 6 + 8 * (n_coef - 2), 9 * (n_coef - 2) + 3
+    pos32, vel32 = 3 * (3 * (n_coef - 1) + 3), 3 * (4 * (n_coef - 1) + 1)
     evals, node = st["force_evals"], st["node_evals"]
     attempts = st["steps"] + st["rejected"]
     if not mixed:
         per = 25 * act + 25 * gr + 21 * j2
-        f64 = evals * per + (evals - node) * (act * cheb + 10)
+        f64 = evals * per + (evals - node) * (act * pos64 + gr * vel64 + 10)
         f64 += st["iterations"] * 1440 + attempts * 121
         return f64, 0
-    f64 = evals * 19 + (evals - node) * (cheb + 10) + st["iterations"] * 1488 + attempts * 121
+    f64 = evals * 19 + (evals - node) * (pos64 + vel64 + 10) + st["iterations"] * 1488 \
+        + attempts * 121
     f64 += st["steps"] * 8 * (act - 1)          # close-planet check at each step start
     sun_gr, sun_j2 = fm.gr_mask & 1, fm.j2_mask & 1
     per32 = 25 * (act - 1) + 25 * (gr - sun_gr) + 21 * (j2 - sun_j2) + 25 * sun_gr + 21 * sun_j2
-    f32 = evals * per32 + (evals - node) * (act - 1) * cheb
+    f32 = evals * per32 + (evals - node) * ((act - 1) * pos32 + (gr - sun_gr) * vel32)
     return f64, f32
 
 
