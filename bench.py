@@ -171,6 +171,57 @@ def oracle_sample(w, n_sample, n_threads=None):
     return sub, hits, dt, nt
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), for the CPU-baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def measured_hbm_gbs():
+    """Copy bandwidth from MEASURED_PEAKS.json (None if absent)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return None
+
+
+# Algorithmic FP64 work of the exact FoV test per candidate (k_exact): the
+# universal-variable solve at the exposure epoch (setup 25, 4 Newton
+# iterations of ~55 with the Stumpff series, final f/g and velocity ~70, the
+# acceleration and jerk of the cubic ~30), 5 light-time evaluations of the
+# cubic (~33 each) and one polygon test (~20); the FP32 cap tests and the
+# per-hit RA/Dec are left out.
+EXACT_FLOPS_PER_CANDIDATE = 25 + 4 * 55 + 70 + 30 + 5 * 33 + 20
+
+
+def fov_stage_roofline(stats, n_bodies, peak_fp64_tflops, hbm_gbs):
+    """Rooflines of the FoV stage's two kernels from the call's counters:
+    k_exact against the FP64 peak (EXACT_FLOPS_PER_CANDIDATE per candidate),
+    the candidate search against HBM (per body and batch the 48-B stop state
+    read, per candidate 8 B written and read back)."""
+    cand = statistics.mean(s["n_candidates"] for s in stats)
+    batches = stats[-1]["n_batches"]
+    exact_ms = statistics.mean(s["exact_ms"] for s in stats)
+    cand_ms = statistics.mean(s["cand_ms"] for s in stats)
+    ex = EXACT_FLOPS_PER_CANDIDATE * cand / (exact_ms / 1e3) / 1e12
+    cbytes = n_bodies * batches * 48.0 + cand * 16.0
+    cgbs = cbytes / (cand_ms / 1e3) / 1e9
+    return {"exact": {"bound": "alu", "achieved": ex, "peak": peak_fp64_tflops, "unit": "TFLOP/s",
+                      "frac": ex / peak_fp64_tflops, "candidates": cand, "ms": exact_ms,
+                      "flops_per_candidate": EXACT_FLOPS_PER_CANDIDATE},
+            "candidates": {"bound": "hbm", "achieved": cgbs, "peak": hbm_gbs, "unit": "GB/s",
+                           "frac": cgbs / hbm_gbs if hbm_gbs else None,
+                           "bytes": cbytes, "ms": cand_ms}}
+
+
 def max_over_ranks(value, dist, device):
     """The largest of every rank's value (the step time of the slowest
     replica); the value itself without a process group."""
@@ -624,9 +675,13 @@ def run_gb300(args):
     accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sub, ref, dt, nt = oracle_sample(w, args.ref_sample)
+        sub1, _, dt1, _ = oracle_sample(w, 64, n_threads=1)
         cpu = {"value": len(sub) * 365.0 / dt, "unit": "body-days/s", "cores": nt, "kind": "oracle",
                "sample": f"{len(sub)} evenly spaced bodies x all {nf} frames, full year, "
-                         f"{dt:.1f} s"}
+                         f"{dt:.1f} s",
+               "cpu_model": cpu_model(),
+               "one_core": {"value": len(sub1) * 365.0 / dt1, "unit": "body-days/s",
+                            "sample": f"{len(sub1)} bodies, 1 thread, {dt1:.1f} s"}}
         accuracy = compare_sample(kete, hits, nh, sub, ref)
     # ---- the mixed-precision form on the same workload (speedup at accuracy) ------
     mixed_leg = None
@@ -692,6 +747,7 @@ def run_gb300(args):
                    "batches": s0["n_batches"], "precision": args.precision,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "fov_checks_per_s": checks,
+        "fov_stage": fov_stage_roofline(stats, n, peak_nominal, measured_hbm_gbs()),
         "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": achieved,
                      "peak": peak_nominal, "unit": "TFLOP/s", "frac": achieved / peak_nominal,
                      "traffic": traffic, "peak_probe_measured": (peak_probe or 0) / 1e12,
@@ -732,7 +788,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--n-bodies", type=int, default=0)
     ap.add_argument("--n-frames", type=int, default=0)
-    ap.add_argument("--ref-sample", type=int, default=768)
+    ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")

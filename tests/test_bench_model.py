@@ -1,0 +1,45 @@
+"""Host logic of bench.py's roofline models: the FLOP count of the
+propagation kernel and the FoV-stage rooflines, on hand-made counters."""
+import math
+
+import bench
+
+
+class _FM:
+    body_mask = 0x1FF
+    gr_mask = (1 << 0) | (1 << 3) | (1 << 5)
+    j2_mask = (1 << 0) | (1 << 5)
+
+
+def test_prop_flops_node_rows_and_per_thread():
+    st = {"force_evals": 10, "node_evals": 10, "steps": 0, "rejected": 0, "iterations": 0}
+    f64, f32 = bench.prop_flops(st, _FM, 12, False)
+    assert f64 == 10 * (25 * 9 + 25 * 3 + 21 * 2) and f32 == 0
+    st["node_evals"] = 0
+    f64b, _ = bench.prop_flops(st, _FM, 12, False)
+    # per-thread: segment lookup + a position series per mass + a velocity
+    # series per GR mass, summed upward (8 and 9 operations per coefficient)
+    assert f64b - f64 == 10 * (10 + 9 * (6 + 8 * 10) + 3 * (9 * 10 + 3))
+    st = {"force_evals": 0, "node_evals": 0, "steps": 2, "rejected": 1, "iterations": 5}
+    assert bench.prop_flops(st, _FM, 12, False)[0] == 5 * 1440 + 3 * 121
+
+
+def test_prop_flops_mixed_split():
+    st = {"force_evals": 4, "node_evals": 0, "steps": 1, "rejected": 0, "iterations": 1}
+    f64, f32 = bench.prop_flops(st, _FM, 12, True)
+    assert f64 == 4 * 19 + 4 * ((6 + 80) + (90 + 3) + 10) + 1488 + 121 + 8 * 8
+    per32 = 25 * 8 + 25 * 2 + 21 * 1 + 25 + 21
+    assert f32 == 4 * per32 + 4 * (8 * 3 * (3 * 11 + 3) + 2 * 3 * (4 * 11 + 1))
+
+
+def test_fov_stage_roofline():
+    stats = [{"n_candidates": 1000, "n_batches": 10, "exact_ms": 2.0, "cand_ms": 1.0}] * 3
+    r = bench.fov_stage_roofline(stats, 500, 1.0, 5000.0)
+    ex = r["exact"]
+    assert math.isclose(ex["achieved"], bench.EXACT_FLOPS_PER_CANDIDATE * 1000 / 2e-3 / 1e12)
+    assert ex["frac"] == ex["achieved"] and ex["unit"] == "TFLOP/s"
+    c = r["candidates"]
+    assert c["bytes"] == 500 * 10 * 48 + 1000 * 16
+    assert math.isclose(c["achieved"], c["bytes"] / 1e-3 / 1e9)
+    assert math.isclose(c["frac"], c["achieved"] / 5000.0)
+    assert bench.fov_stage_roofline(stats, 500, 1.0, None)["candidates"]["frac"] is None
