@@ -287,3 +287,39 @@ def test_tuned_controls_meet_the_papers_precision_goal():
     km = worst * W.AU_KM
     assert km < 70.0 and km < 1.0, km
     assert steps_tight > 1.5 * steps
+
+
+def test_planet_table_fit_and_planet_energy():
+    """The planetary table: within 2e-11 AU of the generator's own planet
+    integration at 2,000 random epochs (12 Chebyshev terms per 16-day segment;
+    Mercury sets the residual), and that integration conserves the planet
+    system's energy and angular momentum to 1e-13 over +-10 years."""
+    from conftest import cached_workload
+    w = cached_workload("mb1k")
+    ps = W.make_planets(w.seed)
+    e = w.ephem
+    ts = np.sort(np.random.default_rng(3).uniform(e.t_start + 1e-6, e.t_end - 1e-6, 2000))
+    ref = W.integrate_planets(ps, ts)
+    orc = O.Oracle(e.to_bytes())
+    worst = 0.0
+    for i, t in enumerate(ts):
+        for b in range(9):
+            _, p, _ = orc.ephem(b, t)
+            worst = max(worst, np.abs(p - ref[i, b, :3]).max())
+    assert worst < 2e-11, worst
+    st = W.integrate_planets(ps, np.array([ps.t0, ps.t0 + 3652.5, ps.t0 - 3652.5]))
+    gm = ps.gm
+
+    def energy(s):
+        ke = 0.5 * (gm[:, None] * s[:, 3:] ** 2).sum()
+        pe = -sum(gm[i] * gm[j] / np.linalg.norm(s[i, :3] - s[j, :3])
+                  for i in range(9) for j in range(i + 1, 9))
+        return ke + pe
+
+    def ang_mom(s):
+        return (gm[:, None] * np.cross(s[:, :3], s[:, 3:])).sum(0)
+
+    E0, L0 = energy(st[0]), ang_mom(st[0])
+    for k in (1, 2):
+        assert abs(energy(st[k]) - E0) < 1e-13 * abs(E0)
+        assert np.abs(ang_mom(st[k]) - L0).max() < 1e-13 * np.linalg.norm(L0)
