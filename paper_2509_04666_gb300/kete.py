@@ -112,7 +112,9 @@ def lib():
 
 def force_model(**kw) -> ForceModel:
     """Default force model (App. A defaults) with keyword overrides; per-body
-    arrays (j2, radius, pole_ra, pole_dec) take {body_index: value} dicts."""
+    arrays (j2, radius, pole_ra, pole_dec) take {body_index: value} dicts;
+    nongrav takes the CUDA tensor of nongrav_to_device (kept alive with the
+    model) or None."""
     fm = ForceModel()
     lib().kete_force_model_default(C.byref(fm))
     for k, v in kw.items():
@@ -120,9 +122,31 @@ def force_model(**kw) -> ForceModel:
             arr = getattr(fm, k)
             for i, x in v.items():
                 arr[i] = x
+        elif k == "nongrav":
+            set_nongrav(fm, v)
         else:
             setattr(fm, k, v)
     return fm
+
+
+def set_nongrav(fm: ForceModel, t) -> None:
+    """Attach per-body non-gravitational terms (nongrav_to_device) to fm."""
+    if t is None:
+        fm.nongrav = None
+        fm._nongrav = None
+        return
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.dim() == 2 and t.shape[1] == 10 and t.is_contiguous()):
+        raise TypeError("nongrav must be a contiguous CUDA float64 tensor [n, 10] "
+                        "(see nongrav_to_device)")
+    fm.nongrav = t.data_ptr()
+    fm._nongrav = t
+
+
+def _check_nongrav(fm: ForceModel, n: int) -> None:
+    t = getattr(fm, "_nongrav", None)
+    if t is not None and (t.shape[0] != n or fm.nongrav != t.data_ptr()):
+        raise TypeError(f"the force model's nongrav tensor has {t.shape[0]} rows for {n} bodies")
 
 
 NONGRAV_FIELDS = ("a1", "a2", "a3", "alpha", "r0", "m", "n", "k", "dt", "beta")
@@ -266,6 +290,7 @@ class Kete:
         if status is None:
             status = torch.zeros(n, dtype=torch.int32, device=states.device)
         fm = fm or force_model()
+        _check_nongrav(fm, n)
         self._sync_stream()
         self._check(lib().kete_propagate(self._h, states.data_ptr(), epochs.data_ptr(), n,
                                          float(t_target), C.byref(fm), status.data_ptr()))
@@ -278,6 +303,7 @@ class Kete:
         if status is None:
             status = torch.zeros(n, dtype=torch.int32, device=states.device)
         fm = fm or force_model()
+        _check_nongrav(fm, n)
         self._sync_stream()
         self._check(lib().kete_propagate_noalloc(self._h, states.data_ptr(), epochs.data_ptr(),
                                                  n, float(t_target), C.byref(fm),
@@ -291,6 +317,7 @@ class Kete:
         out = torch.empty((len(st), 6, n), dtype=torch.float64, device=states.device)
         status = torch.zeros(n, dtype=torch.int32, device=states.device)
         fm = fm or force_model()
+        _check_nongrav(fm, n)
         self._sync_stream()
         self._check(lib().kete_propagate_stops(
             self._h, states.data_ptr(), epochs.data_ptr(), n,
@@ -312,6 +339,7 @@ class Kete:
         nf = frames_dev.numel() // 128
         n_obs = observers.numel() // 3
         fm = fm or force_model()
+        _check_nongrav(fm, n)
         opts = opts or survey_opts()
         status = torch.zeros(n, dtype=torch.int32, device=states.device)
         if hits is None:
@@ -360,6 +388,7 @@ class Kete:
         pr = torch.empty((n, m, 2), dtype=torch.float64, device=dev) if pred else None
         status = torch.zeros(n, dtype=torch.int32, device=dev)
         fm = fm or force_model()
+        _check_nongrav(fm, n)
         opts = opts or survey_opts()
         self._sync_stream()
         self._check(lib().kete_adjoint(self._h, states.data_ptr(), epochs.data_ptr(), n,
@@ -381,6 +410,7 @@ class Kete:
         _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
         st = np.ascontiguousarray(stops, dtype=np.float64)
         fm = fm or force_model()
+        _check_nongrav(fm, n)
         kind, block, split, defer, order = (C.c_int32() for _ in range(5))
         self._sync_stream()
         self._check(lib().kete_autotune(self._h, states.data_ptr(), epochs.data_ptr(), n,

@@ -77,3 +77,29 @@ def test_force_model_defaults_without_gpu(libpath):
     assert fm.max_iter == 12 and fm.eps == 1e-9 and fm.safety == 0.25 and fm.eps_pc == 1e-10
     o = kete.survey_opts()
     assert o.batch_span == 3.0 and o.twobody_max == 1.5
+
+
+def test_force_model_nongrav_argument():
+    """The binding takes per-body non-gravitational terms only as a CUDA
+    float64 [n, 10] tensor, and checks its rows against the call's bodies."""
+    torch = pytest.importorskip("torch")
+    from paper_2509_04666_gb300 import kete
+    with pytest.raises(TypeError):
+        kete.force_model(nongrav=torch.zeros(3, 10, dtype=torch.float64))
+    with pytest.raises(TypeError):
+        kete.force_model(nongrav=np.zeros((3, 10)))
+    fm = kete.force_model(nongrav=None)
+    assert not fm.nongrav
+    kete._check_nongrav(fm, 5)
+
+
+def test_nongrav_records_to_rows():
+    torch = pytest.importorskip("torch")
+    from paper_2509_04666_gb300 import kete, workloads as W
+    ng = W.nongrav_params(np.array([3, 0, 0, 3, 1]), dust_frac=1.0, yarkovsky_every=2)
+    rows = kete.nongrav_to_device(ng, "cpu")
+    assert rows.shape == (5, 10) and rows.dtype == torch.float64
+    for j, f in enumerate(kete.NONGRAV_FIELDS):
+        assert np.array_equal(rows[:, j].numpy(), ng[f])
+    # the row layout is kete_nongrav's: ten doubles in declaration order
+    assert kete.NONGRAV_FIELDS == W.NONGRAV_DTYPE.names

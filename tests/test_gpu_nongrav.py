@@ -54,11 +54,8 @@ def _ng_o(rec):
 def _gpu_propagate(K, w, ng, precision=0, days=365.0):
     from paper_2509_04666_gb300 import kete
     K.load_ephem(w.ephem.to_bytes())
-    fm = kete.force_model(precision=precision)
-    keep = None
-    if ng is not None:
-        keep = kete.nongrav_to_device(ng, "cuda")
-        fm.nongrav = keep.data_ptr()
+    fm = kete.force_model(precision=precision,
+                          nongrav=None if ng is None else kete.nongrav_to_device(ng, "cuda"))
     s = _dev(w.states.copy()); e = _dev(w.epochs.copy())
     status = K.propagate(s, e, W.T0 + days, fm=fm)
     return s.cpu().numpy(), status.cpu().numpy()
@@ -101,6 +98,11 @@ def test_nongrav_terms_act_and_zero_terms_change_nothing(K, pop):
     zero, _ = _gpu_propagate(K, w, np.zeros_like(ng))
     # all-zero records: bit for bit the gravity-only result
     assert np.array_equal(zero, plain)
+    # a terms tensor whose rows do not match the bodies is refused
+    from paper_2509_04666_gb300 import kete
+    fm = kete.force_model(nongrav=kete.nongrav_to_device(ng[:10], "cuda"))
+    with pytest.raises(TypeError):
+        K.propagate(_dev(w.states.copy()), _dev(w.epochs.copy()), W.T0 + 1.0, fm=fm)
     moved = np.abs(withng[:3] - plain[:3]).max(axis=0)
     # comets: g(r) falls as r^-(m + n k) ~ r^-26 beyond r0 = 2.8 AU, so only the
     # comets that come in close during the year move by much
