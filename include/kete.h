@@ -9,14 +9,19 @@
  *   1. planetary positions from a device-resident Chebyshev table (the
  *      stand-in for the SPICE kernels of Sec. 3.2 / App. A);
  *   2. n-body propagation of massless bodies under Sun + planets with the
- *      force model of Eq. A.1 (Newton + GR of Eq. A.3 + J2 of Eq. A.4) by a
- *      Gauss-Radau integrator with IAS15 convergence and step control and the
- *      predictor removed (Sec. 3.2, App. A.6);
+ *      force model of Eq. A.1 (Newton + GR of Eq. A.3 + J2 of Eq. A.4, and
+ *      optionally per-body radiation pressure, Eq. A.6, and the JPL comet
+ *      model, Eq. A.7) by a Gauss-Radau integrator with IAS15 convergence
+ *      and step control and the predictor removed (Sec. 3.2, App. A.6), in
+ *      FP64 or with FP32 planetary terms;
  *   3. FoVs sorted and grouped into <= 3-day batches, bodies integrated to each
  *      batch midpoint, then two-body propagation with light-delay correction
  *      to each FoV epoch (Sec. 2);
- *   4. the spherical-polygon membership test by inward great-circle normals
- *      (Sec. 3.1), and RA/Dec of every hit (App. A.1).
+ *   4. the membership test of spherical polygons by inward great-circle
+ *      normals and of cones (Sec. 3.1), RA/Dec of every hit (App. A.1), and
+ *      optionally its apparent magnitude (Sec. 3.3);
+ *   5. the gradient of an orbit-fit loss through steps 2-4 with respect to
+ *      the initial states (kete_adjoint).
  *
  * Units and frames (App. A.1): AU, AU/day, TDB Julian dates; states are
  * barycentric ecliptic J2000; RA/Dec are equatorial J2000 (obliquity
