@@ -239,6 +239,23 @@ int kete_ephem_eval(kete_ctx *ctx, const double *t, int64_t n, int body, double 
 int kete_propagate(kete_ctx *ctx, double *states, double *epochs, int64_t n, double t_target,
                    const kete_force_model *fm, int32_t *status);
 
+/* kete_propagate through a chain of stops every leg_days days (the survey's
+ * batch-midpoint chain, Sec. 2, applied to a single target): the stops are
+ * epochs[0] + k leg_days toward t_target (which ends the chain), so that
+ * the bodies stay together in time and a step spanning a whole leg reads the
+ * planets from rows shared by all bodies instead of evaluating the table.
+ * For long propagations of bodies whose natural steps exceed leg_days this
+ * trades a few more steps for much cheaper force evaluations.  Results agree
+ * with a chain of stops on the same grid (kete_propagate_stops), not
+ * bit for bit with kete_propagate (another step sequence; the difference is
+ * at the integrator's truncation level).  Bodies at other epochs than
+ * epochs[0] join the chain at its first stop.  leg_days > 0; at most
+ * 10,000,000 legs.  Arguments, results and status otherwise as
+ * kete_propagate.  Errors: BAD_ARG, NO_EPHEM, NOMEM, CUDA. */
+int kete_propagate_legs(kete_ctx *ctx, double *states, double *epochs, int64_t n,
+                        double t_target, double leg_days, const kete_force_model *fm,
+                        int32_t *status);
+
 /* Propagate n bodies (not modified) along the chain epoch -> stops[0] ->
  * stops[1] -> ... (host, [n_stops], ascending), carrying the step size along
  * the chain: the schedule kete_fov_check uses for the batch midpoints (Sec. 2,

@@ -31,7 +31,7 @@ enum Slot {
     S_NT_R64, S_NT_R32, S_XSUN, S_XOBSREL, S_NEXTBODY, S_TUNE_ST, S_TUNE_EP, S_TUNE_OUT,
     S_ADJ_REC, S_ADJ_NREC, S_ADJ_NBAT, S_ADJ_BIDX, S_ADJ_YREF, S_ADJ_GJUMP, S_ADJ_STATUS,
     S_KSTOP, S_DEFER_LIST, S_DEFER_CNT, S_ORDER, S_ORDER_KEY, S_ORDER_HIST, S_ORDER_OFF,
-    S_ORDER_SCAN, S_ORDER_N, S_ADJ_TEND,
+    S_ORDER_SCAN, S_ORDER_N, S_ADJ_TEND, S_LEG_OUT,
     S_NSLOTS
 };
 
@@ -554,6 +554,73 @@ extern "C" int kete_propagate(kete_ctx *ctx, double *states, double *epochs, int
         prop_event(ctx, false);
         CUDA_TRY(launch_chain_finish(cs, states, epochs, status, ctx->stream));
         ctx->stats.launches = 4;
+    }
+    r = stats_end(ctx);
+    if (r != KETE_OK) return r;
+    stats_collect(ctx);
+    return KETE_OK;
+}
+
+extern "C" int kete_propagate_legs(kete_ctx *ctx, double *states, double *epochs, int64_t n,
+                                   double t_target, double leg_days, const kete_force_model *fm,
+                                   int32_t *status)
+{
+    if (!ctx) return KETE_ERR_BAD_ARG;
+    if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
+    if (n < 0 || n > INT32_MAX || (n > 0 && (!states || !epochs)) || !std::isfinite(t_target) ||
+        !(leg_days > 0.0) || !std::isfinite(leg_days))
+        return fail(ctx, KETE_ERR_BAD_ARG, "bad arguments (leg_days must be positive and finite)");
+    ForceDev F;
+    int r = make_force(ctx, fm, F);
+    if (r != KETE_OK) return r;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    stats_begin(ctx);
+    if (n > 0) {
+        // the grid starts at the first body's epoch
+        double e0 = 0.0;
+        CUDA_TRY(cudaMemcpyAsync(&e0, epochs, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        if (!std::isfinite(e0)) return fail(ctx, KETE_ERR_BAD_ARG, "epochs[0] is not finite");
+        const double span = t_target - e0;
+        const double n_legs = std::ceil(std::fabs(span) / leg_days);
+        if (n_legs > 1e7) return fail(ctx, KETE_ERR_BAD_ARG, "more than 10,000,000 legs");
+        const int64_t K = std::max<int64_t>(1, (int64_t)n_legs);
+        std::vector<double> stops((size_t)K);
+        const double sgn = span < 0.0 ? -1.0 : 1.0;
+        for (int64_t k = 0; k + 1 < K; k++) stops[k] = e0 + sgn * leg_days * (double)(k + 1);
+        stops[K - 1] = t_target;
+        ChainState cs;
+        r = run_chain(ctx, F, states, epochs, n, cs);
+        if (r != KETE_OK) return r;
+        double *d_stops;
+        GET(S_STOPS, K, d_stops);
+        CUDA_TRY(cudaMemcpyAsync(d_stops, stops.data(), K * sizeof(double), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+        // internal stops in chunks whose states go to scratch (at most 2 GiB),
+        // then the target alone, whose states go to the caller's array: a body
+        // that failed is not written there and keeps its input state
+        const int64_t M = K - 1;
+        const int64_t cap = std::max<int64_t>(1, ((int64_t)1 << 31) / (48 * n));
+        const int64_t C = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(M, 512), cap));
+        double *scratch = nullptr;
+        if (M > 0) GET(S_LEG_OUT, (size_t)C * 6 * (size_t)n, scratch);
+        int launches = 2;
+        prop_event(ctx, true);
+        for (int64_t j0 = 0; j0 < K;) {
+            const bool last = (j0 == M);
+            const int64_t cnt = last ? 1 : std::min(C, M - j0);
+            NodeTable nt;
+            r = node_table(ctx, d_stops + j0, (int)cnt, j0 == 0 ? epochs : d_stops + j0 - 1, nt);
+            if (r != KETE_OK) return r;
+            r = propagate(ctx, F, cs, d_stops + j0, (int)cnt, last ? states : scratch, n, true, &nt,
+                          0);
+            if (r != KETE_OK) return r;
+            launches += 2;
+            j0 += cnt;
+        }
+        prop_event(ctx, false);
+        CUDA_TRY(launch_chain_finish(cs, states, epochs, status, ctx->stream));
+        ctx->stats.launches = launches;
     }
     r = stats_end(ctx);
     if (r != KETE_OK) return r;

@@ -28,7 +28,7 @@ EXPORTS = ["kete_create", "kete_destroy", "kete_set_stream", "kete_last_error",
            "kete_force_model_default", "kete_survey_opts_default", "kete_load_ephem",
            "kete_ephem_eval", "kete_propagate", "kete_propagate_stops", "kete_fov_check",
            "kete_get_stats", "kete_propagate_noalloc", "kete_set_propagation", "kete_autotune",
-           "kete_adjoint", "kete_fov_check_mag"]
+           "kete_adjoint", "kete_fov_check_mag", "kete_propagate_legs"]
 MAG_NONE, MAG_HG, MAG_COMET_TOTAL, MAG_COMET_NUCLEUS = 0, 1, 2, 3
 
 
@@ -98,6 +98,7 @@ def lib():
         L.kete_fov_check_mag.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, C.POINTER(ForceModel),
                                          C.POINTER(SurveyOpts), vp, vp, i64, C.POINTER(i64), vp]
         L.kete_propagate_noalloc.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(ForceModel), vp]
+        L.kete_propagate_legs.argtypes = [vp, vp, vp, i64, dbl, dbl, C.POINTER(ForceModel), vp]
         L.kete_set_propagation.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                            C.c_int]
         L.kete_autotune.argtypes = [vp, vp, vp, i64, C.POINTER(C.c_double), i64,
@@ -283,8 +284,10 @@ class Kete:
                                           vel.data_ptr()))
         return pos, vel
 
-    def propagate(self, states, epochs, t_target, fm=None, status=None):
-        """In-place propagation of states [6, n] / epochs [n] to t_target."""
+    def propagate(self, states, epochs, t_target, fm=None, status=None, leg_days=None):
+        """In-place propagation of states [6, n] / epochs [n] to t_target.
+        leg_days: go through stops every leg_days days from epochs[0]
+        (kete_propagate_legs), so that the bodies share the planets' rows."""
         n = epochs.numel()
         _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
         if status is None:
@@ -292,8 +295,13 @@ class Kete:
         fm = fm or force_model()
         _check_nongrav(fm, n)
         self._sync_stream()
-        self._check(lib().kete_propagate(self._h, states.data_ptr(), epochs.data_ptr(), n,
-                                         float(t_target), C.byref(fm), status.data_ptr()))
+        if leg_days is None:
+            self._check(lib().kete_propagate(self._h, states.data_ptr(), epochs.data_ptr(), n,
+                                             float(t_target), C.byref(fm), status.data_ptr()))
+        else:
+            self._check(lib().kete_propagate_legs(self._h, states.data_ptr(), epochs.data_ptr(),
+                                                  n, float(t_target), float(leg_days),
+                                                  C.byref(fm), status.data_ptr()))
         return status
 
     def propagate_noalloc(self, states, epochs, t_target, fm=None, status=None):
