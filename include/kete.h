@@ -244,8 +244,10 @@ int kete_propagate(kete_ctx *ctx, double *states, double *epochs, int64_t n, dou
  * epochs[0] + k leg_days toward t_target (which ends the chain), so that
  * the bodies stay together in time and a step spanning a whole leg reads the
  * planets from rows shared by all bodies instead of evaluating the table.
- * For long propagations of bodies whose natural steps exceed leg_days this
- * trades a few more steps for much cheaper force evaluations.  Results agree
+ * The price is more steps wherever the natural step exceeds leg_days (with
+ * 8-day legs, main-belt bodies and comet clones take about twice as many
+ * steps, which outweighed the cheaper evaluations on GB300: 1.2-1.3x slower
+ * than kete_propagate).  Results agree
  * with a chain of stops on the same grid (kete_propagate_stops), not
  * bit for bit with kete_propagate (another step sequence; the difference is
  * at the integrator's truncation level).  Bodies at other epochs than
