@@ -40,7 +40,7 @@ MAS = math.radians(1.0 / 3.6e6)
 # of the same workload (profiles/k_propagate_wise1y.md: 100k bodies x 21 stops,
 # 385 MB), per body-stop, scaled to the full launch by its body-stops; valid
 # only while the kernel source is unchanged.
-PROFILED_TRAFFIC = {"src_sha": "67db26f011c52cb0", "bytes_per_body_stop": 183.2}
+PROFILED_TRAFFIC = {"src_sha": "cfb11c9322fcded9", "bytes_per_body_stop": 183.2}
 
 
 def kernel_source_sha():

@@ -417,7 +417,7 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
     return KETE_BODY_OK;
 }
 
-// Mixed precision: the Sun's monopole in FP64; the Sun's GR and
+// Mixed precision (FP32 planets): the Sun's monopole in FP64; the Sun's GR and
 // J2 and every planet in FP32 -- except planets flagged in `close` (within
 // kCloseAu at the start of the step), which stay in FP64.  `as` receives the
 // FP64 part alone: it is smooth in time, so the step-size control estimates
