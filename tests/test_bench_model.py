@@ -43,3 +43,17 @@ def test_fov_stage_roofline():
     assert math.isclose(c["achieved"], c["bytes"] / 1e-3 / 1e9)
     assert math.isclose(c["frac"], c["achieved"] / 5000.0)
     assert bench.fov_stage_roofline(stats, 500, 1.0, None)["candidates"]["frac"] is None
+
+
+def test_clock_summary_parses_samples():
+    """Median SM clock under load, the maximum, and any throttle reason seen."""
+    c = bench.Clocks(0)
+    c.f.write("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+              "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+              "0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+              "garbage line\n")
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    empty = bench.Clocks(0).summary()
+    assert empty["samples"] == 0 and empty["reasons"] == ["unsampled"]
