@@ -8,6 +8,7 @@ is missing the binding raises -- there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 
 import numpy as np
@@ -192,6 +193,57 @@ def mag_params_to_device(params: np.ndarray, device) -> torch.Tensor:
 
 
 FRAME_CONE = 0
+# kete_frame records (128 bytes)
+FRAME_DTYPE = np.dtype([
+    ("epoch", "<f8"), ("observer_idx", "<i8"), ("exposure_id", "<i8"),
+    ("n_edges", "<i4"), ("reserved", "<i4"), ("normals", "<f8", (4, 3)),
+])
+_OBLIQUITY = math.radians(84381.448 / 3600.0)
+
+
+def radec_to_vec(ra, dec):
+    """Unit vectors (ecliptic J2000, [..., 3]) of equatorial J2000 RA/Dec
+    (radians): the inverse of the RA/Dec the library reports."""
+    ra, dec = np.asarray(ra, float), np.asarray(dec, float)
+    x = np.cos(dec) * np.cos(ra)
+    y = np.cos(dec) * np.sin(ra)
+    z = np.sin(dec)
+    c, s_ = math.cos(_OBLIQUITY), math.sin(_OBLIQUITY)
+    return np.stack([x, c * y + s_ * z, -s_ * y + c * z], axis=-1)
+
+
+def polygon_frame(corners_radec, epoch: float, observer_idx: int, exposure_id: int = 0):
+    """A kete_frame record of the spherical polygon (Sec. 3.1) with 3 or 4
+    corners given as (RA, Dec) pairs in radians, in either winding order:
+    edge k's inward normal is c_k x c_(k+1), turned to face the corners'
+    mean direction.  The polygon must be convex and smaller than a
+    hemisphere."""
+    cr = np.asarray(corners_radec, float).reshape(-1, 2)
+    if not 3 <= len(cr) <= 4:
+        raise ValueError("a polygon frame has 3 or 4 corners")
+    v = radec_to_vec(cr[:, 0], cr[:, 1])
+    mean = v.sum(axis=0)
+    out = np.zeros(1, FRAME_DTYPE)[0]
+    out["epoch"], out["observer_idx"], out["exposure_id"] = epoch, observer_idx, exposure_id
+    out["n_edges"] = len(v)
+    for k in range(len(v)):
+        nk = np.cross(v[k], v[(k + 1) % len(v)])
+        out["normals"][k] = nk if nk @ mean > 0 else -nk
+    return out
+
+
+def cone_frame(ra: float, dec: float, radius: float, epoch: float, observer_idx: int,
+               exposure_id: int = 0):
+    """A kete_frame record of a cone (Sec. 3.1) about (RA, Dec) with angular
+    radius `radius` (all radians, 0 < radius < pi)."""
+    if not 0.0 < radius < math.pi:
+        raise ValueError("the cone's radius must lie in (0, pi)")
+    out = np.zeros(1, FRAME_DTYPE)[0]
+    out["epoch"], out["observer_idx"], out["exposure_id"] = epoch, observer_idx, exposure_id
+    out["n_edges"] = FRAME_CONE
+    out["normals"][0] = radec_to_vec(ra, dec)
+    out["normals"][1][0] = radius
+    return out
 
 
 def streak_frames(frame, t_start: float, t_end: float, observer_idx, exposure_id0: int):
