@@ -14,7 +14,10 @@
  *   - Gauss-Radau 15th-order step with IAS15 corrector convergence and step
  *     control, predictor removed (Sec. 3.2, App. A.6)
  *   - universal-variable two-body propagation + light-delay iteration (Sec. 2)
- *   - spherical-polygon FoV test by inward normals (Sec. 3.1)
+ *   - FoV test: spherical polygons by inward normals, and cones (Sec. 3.1)
+ *   - apparent magnitudes: H-G V for asteroids, comet total and nucleus
+ *     magnitudes (Sec. 3.3, App. B)
+ *   - orbit-fit loss and its gradient by the variational equations
  *   - time batching of FoVs into <= 3-day groups with n-body to the batch
  *     midpoint (Sec. 2)
  *   - RA/Dec in equatorial J2000 (App. A.1)
