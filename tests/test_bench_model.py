@@ -57,3 +57,21 @@ def test_clock_summary_parses_samples():
                  "samples": 3}
     empty = bench.Clocks(0).summary()
     assert empty["samples"] == 0 and empty["reasons"] == ["unsampled"]
+
+
+def test_truncation_by_population_on_the_ragged_sample():
+    """The oracle at eps/100 against the tuned eps: every population reported,
+    main-belt differences small, the encounters' larger."""
+    import numpy as np
+    import oracle as O
+    from conftest import cached_workload
+    w = cached_workload("ragged1y", n_bodies=2000)
+    orc = O.Oracle(w.ephem.to_bytes())
+    sub = np.unique(np.concatenate([np.arange(0, 2000, 40), np.nonzero(w.labels == 4)[0]]))
+    t_end = w.t_end
+    ref, _, rst, _ = orc.propagate_many(orc.force_model(), w.states[:, sub], w.epochs[sub], t_end)
+    tr = bench.truncation_by_population(orc, w, sub, t_end, ref, rst)
+    assert set(tr) == {"main_belt", "neo", "trojan", "comet", "encounter", "bodies"}
+    assert tr["bodies"] >= len(sub) - 2
+    assert tr["main_belt"] < 1e-10 and tr["trojan"] < 1e-10
+    assert max(tr["neo"], tr["comet"], tr["encounter"]) < 1e-6
