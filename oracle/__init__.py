@@ -103,9 +103,12 @@ _lib = None
 
 
 def lib():
+    """The oracle library: built from kete_oracle.c, or the prebuilt library
+    named by the environment variable KETE_ORACLE_LIB (the planted-mistake
+    tests point it at mutated copies built elsewhere)."""
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        L = C.CDLL(os.environ.get("KETE_ORACLE_LIB") or build())
         d = C.POINTER(C.c_double)
         L.ko_ephem_load.argtypes = [C.POINTER(Ephem), C.c_void_p, C.c_size_t]
         L.ko_ephem_eval.argtypes = [C.POINTER(Ephem), C.c_int, C.c_double, d, d]
@@ -119,6 +122,9 @@ def lib():
         L.ko_propagate_many.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, d, C.c_int64,
                                         C.c_double, C.c_void_p, C.c_int, C.POINTER(Stats),
                                         C.c_void_p]
+        L.ko_ephem_delta.argtypes = [C.POINTER(Ephem), C.c_int, C.c_double, C.c_double, d]
+        L.ko_find_close.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), C.c_double, d,
+                                    C.c_double, C.POINTER(C.c_int), d, d]
         L.ko_stumpff.argtypes = [C.c_double, d, d]
         L.ko_kepler.argtypes = [C.c_double, d, d, C.c_double, d, d]
         L.ko_apparent.argtypes = [C.POINTER(Ephem), d, C.c_double, C.c_double, d, d, d]
@@ -181,6 +187,22 @@ class Oracle:
         p = np.zeros(3); v = np.zeros(3)
         rc = lib().ko_ephem_eval(C.byref(self.eph), body, t, _dp(p), _dp(v))
         return rc, p, v
+
+    def ephem_delta(self, body, t0, off):
+        """p(t0 + off) - p(t0) of table body `body` from the segment holding t0
+        (the close-encounter displacement, reading R12)."""
+        dp = np.zeros(3)
+        rc = lib().ko_ephem_delta(C.byref(self.eph), body, t0, off, _dp(dp))
+        return rc, dp
+
+    def find_close(self, fm, t, x, t_target):
+        """Encounter set-up at a step start (R12): (rc, planet index or -1,
+        x - p_m(t), end of the step range)."""
+        m = C.c_int(-2); d0 = np.zeros(3); ts = C.c_double(0.0)
+        x = np.ascontiguousarray(x, float)
+        rc = lib().ko_find_close(C.byref(self.eph), C.byref(fm), t, _dp(x), t_target, C.byref(m),
+                                 _dp(d0), C.byref(ts))
+        return rc, m.value, d0, ts.value
 
     def accel(self, fm, t, x, v):
         a = np.zeros(3)

@@ -544,6 +544,24 @@ static int find_close(const ko_ephem *e, const ko_force_model *fm, double t, con
     return KO_OK;
 }
 
+/* Exported for the pins of R12: the planet displacement of ephem_delta and the
+ * encounter set-up of find_close (nearest planet *m, -1: none; *d0 = x -
+ * p_m(t); *t_stop = where a step starting at t toward t_target must end). */
+int ko_ephem_delta(const ko_ephem *e, int body, double t0, double off, double dp[3])
+{
+    return ephem_delta(e, body, t0, off, dp);
+}
+
+int ko_find_close(const ko_ephem *e, const ko_force_model *fm, double t, const double x[3],
+                  double t_target, int *m, double d0[3], double *t_stop)
+{
+    ko_close cl;
+    int st = find_close(e, fm, t, x, (t_target >= t) ? 1.0 : -1.0, &cl, t_stop, t_target);
+    *m = cl.m;
+    for (int i = 0; i < 3; i++) d0[i] = (cl.m >= 0) ? cl.d0[i] : 0.0;
+    return st;
+}
+
 /* Integrate (st, *t) to t_target exactly; *dt is the proposed step (carried). */
 int ko_propagate(const ko_ephem *e, const ko_force_model *fm, double st[6], double *t,
                  double t_target, double *dt, ko_stats *stats)

@@ -140,6 +140,15 @@ int  ko_propagate_many(const ko_ephem *e, const ko_force_model *fm, double *stat
                        double *epochs, int64_t n, double t_target, int32_t *status,
                        int n_threads, ko_stats *stats, const ko_nongrav *ng_bodies);
 
+/* Close encounters (R12): p(t0 + off) - p(t0) of table body `body` from the
+ * segment holding t0, by the recurrence on Chebyshev differences; and the
+ * nearest active planet within 0.1 AU of x at t (*m = -1: none), x - p_m(t)
+ * in d0, and the end of the step range toward t_target in *t_stop (the next
+ * table segment boundary during an encounter). */
+int  ko_ephem_delta(const ko_ephem *e, int body, double t0, double off, double dp[3]);
+int  ko_find_close(const ko_ephem *e, const ko_force_model *fm, double t, const double x[3],
+                   double t_target, int *m, double d0[3], double *t_stop);
+
 void ko_stumpff(double z, double *c2, double *c3);
 int  ko_kepler(double mu, const double r0[3], const double v0[3], double dt,
                double r[3], double v[3]);

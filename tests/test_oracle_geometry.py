@@ -188,6 +188,12 @@ def test_batches_greedy_three_day_rule():
         if e < len(ep):
             assert ep[e] - seg[0] >= 3.0          # greedy: the next epoch does not fit
     assert bs[0] == 0 and np.all(np.diff(bs) > 0)
+    # an epoch exactly one span after the batch start opens the next batch
+    # (R6: t - t_first < span, strict); equal epochs always share a batch
+    ep = W.T0 + np.array([0.0, 1.0, 3.0, 3.0, 5.5, 6.0, 6.0])
+    bs, tr = O.make_batches(ep, 3.0, 1.5)
+    assert list(bs) == [0, 2, 5]
+    np.testing.assert_array_equal(tr, [W.T0 + 0.5, W.T0 + 4.25, W.T0 + 6.0])
 
 
 def test_batches_zero_twobody_interval_is_per_epoch():
