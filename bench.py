@@ -37,9 +37,9 @@ METRIC = ("body-days propagated/s and body×frame FoV checks/s at ≤1 mas vs FP
 MAS = math.radians(1.0 / 3.6e6)
 
 # DRAM traffic of one k_propagate launch from an ncu capture of a smaller case
-# of the same workload (profiles/k_propagate_wise1y.md: 100k bodies x 21 stops,
-# 385 MB), per body-stop, scaled to the full launch by its body-stops; valid
-# only while the kernel source is unchanged.
+# of the same workload (100k bodies x 21 stops), per body-stop, scaled to the
+# full launch by its body-stops; valid only while the kernel source is
+# unchanged (the source hash below).
 PROFILED_TRAFFIC = {"src_sha": "cfb11c9322fcded9", "bytes_per_body_stop": 183.2}
 
 

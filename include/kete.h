@@ -404,16 +404,24 @@ int kete_adjoint(kete_ctx *ctx, const double *states, const double *epochs, int6
  * use; this variant uses a fixed array in the library's device data instead
  * (about 4.5 MB, held on every GPU that loads the library until exit).
  *
- * Arguments, layouts, results and per-body status are those of
- * kete_propagate; the context must already exist and hold an ephemeris
- * (kete_create and kete_load_ephem allocate; call them during set-up).
+ * Arguments, layouts and per-body status are those of kete_propagate; the
+ * context must already exist and hold an ephemeris (kete_create and
+ * kete_load_ephem allocate; call them during set-up).  It always runs one
+ * launch variant: the static schedule, one lane per body, bodies in index
+ * order, the planets summed per thread (no shared node rows), whatever
+ * kete_set_propagation chose -- so it is slower than kete_propagate on
+ * uneven populations, and its results agree with kete_propagate's to the
+ * integrator's truncation level, not bit for bit.
  * n above KETE_NOALLOC_MAX_BODIES is rejected with KETE_ERR_BAD_ARG and a
  * message in kete_last_error; split larger populations into several calls.
  * The call calls no cudaMalloc or cudaFree and does not update
  * kete_get_stats.  The first call on a device resolves the array's device
  * address (which may load the library's device data): make that first call
- * before any stream capture.  All calls on a device share the one array: calls
- * whose work overlaps on the GPU race, so order them on one stream. */
+ * before any stream capture.  The address is kept for the life of the
+ * process; a cudaDeviceReset of that device invalidates it, so do not call
+ * this entry point on a device after resetting it.  All calls on a device
+ * share the one array: calls whose work overlaps on the GPU race, so order
+ * them on one stream. */
 int kete_propagate_noalloc(kete_ctx *ctx, double *states, double *epochs, int64_t n,
                            double t_target, const kete_force_model *fm, int32_t *status);
 

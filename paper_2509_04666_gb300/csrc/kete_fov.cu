@@ -25,6 +25,16 @@ namespace kete {
 constexpr float kPadF = 2e-4f;        // radians added to every float cap test
 constexpr double kSunSpeedMax = 5e-5; // bound on the barycentric Sun speed, AU/day
 
+// Cosine bound of a frame's FP32 cap test in k_exact: cos(rad + kPadF) taken
+// in FP64, less an absolute slack above the rounding of the FP32 dot product
+// of two unit vectors (components rounded to FP32, three products and two
+// sums: below 4e-7).  Taken in FP32 instead, cos(rad + pad) of a frame under
+// ~3e-4 rad rounds to 1 and a body at its centre could fail the cap test.
+__device__ __forceinline__ float cap_cos(double rad)
+{
+    return (rad >= kPi) ? -2.0f : (float)(cos(rad + (double)kPadF) - 2e-6);
+}
+
 __device__ __forceinline__ void set_flag(DevCounters *c, int bit) { atomicOr(&c->error_flags, 1 << bit); }
 
 __device__ __forceinline__ double dot3(const double *a, const double *b)
@@ -83,8 +93,7 @@ __global__ void k_frame_prep(const kete_frame *__restrict__ fr, int64_t nf, int6
         fcen[3 * i + 1] = cen[1];
         fcen[3 * i + 2] = cen[2];
         fcen[3 * nf + i] = rad;
-        const float cr = (rad >= kPi) ? -2.0f : cosf((float)rad + kPadF);
-        faux[i] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], cr);
+        faux[i] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], cap_cos(rad));
         return;
     }
     // vertices: intersections n_a x n_b (either sign) that satisfy every
@@ -138,8 +147,7 @@ __global__ void k_frame_prep(const kete_frame *__restrict__ fr, int64_t nf, int6
     fcen[3 * i + 1] = cen[1];
     fcen[3 * i + 2] = cen[2];
     fcen[3 * nf + i] = rad;
-    float cr = (rad >= kPi) ? -2.0f : cosf((float)rad + kPadF);
-    faux[i] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], cr);
+    faux[i] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], cap_cos(rad));
 }
 
 __global__ void k_exposure_first(const int32_t *__restrict__ is_start,
@@ -538,16 +546,29 @@ __device__ __forceinline__ float apparent_mag(const kete_mag_params &P, const do
 // solved once, at dt_obs (universal variables from the batch state); the
 // light-time iterations move it back by tau with its Taylor expansion,
 //   r(dt_obs - tau) = r - v tau + a tau^2 / 2 - j tau^3 / 6,
-// a = -mu r / |r|^3, j = da/dt.  The first neglected term, tau^4 |r4| / 24
-// with the fourth derivative |r4| ~ 3 (mu/|r|^3)^2 |r|, stays below 2e-13 AU
-// for bodies beyond 0.2 AU of the Sun seen from near 1 AU
-// (tau < (|r| + 1.1 AU) / c), and below 1e-17 AU in the main belt.  The Sun
-// at t_obs - tau comes from its state at the exposure epoch, S - V tau (the
-// neglected term, a_sun tau^2 / 2 with |a_sun| ~ 1e-8 AU/day^2, stays below
-// 2e-11 AU for tau < 0.06 day).
+// a = -mu r / |r|^3, j = da/dt.  The first neglected term is tau^4 |r4| / 24;
+// differentiating a twice more with |r.v| <= |r||v| and d(r.v)/dt = v^2 -
+// mu/|r| bounds the fourth derivative by |r4| <= 4 mu (mu/|r| + 6 v^2) / |r|^4.
+// With twice that bound (the expansion point moves by v tau) the term is
+// below lt_taylor_bound(); main-belt bodies give ~1e-17 AU, bodies at 0.2 AU
+// from the Sun ~1e-13 AU, a sungrazer at 0.01 AU ~1e-7 AU.  Where the bound
+// exceeds kTaylorMaxAu, k_exact solves the two-body problem at every
+// light-time iterate instead, as the definition does.  The Sun at t_obs -
+// tau comes from its state at the exposure epoch, S - V tau (the neglected
+// term, a_sun tau^2 / 2 with |a_sun| ~ 1e-8 AU/day^2, stays below 2e-11 AU
+// for tau < 0.06 day).
+constexpr double kTaylorMaxAu = 1e-13;
 struct TwoBodyLT {
     double r[3], mv[3], a2[3], mj6[3];   // r, -v, a/2, -j/6 at dt_obs
 };
+
+__device__ __forceinline__ double lt_taylor_bound(double mu, const TwoBodyLT &T, double tau)
+{
+    const double rr = dot3(T.r, T.r);
+    const double vv = dot3(T.mv, T.mv);
+    const double t2 = tau * tau;
+    return t2 * t2 * mu * (mu * rsqrt(rr) + 6.0 * vv) / (3.0 * rr * rr);
+}
 
 __device__ __forceinline__ bool twobody_at(double mu, double sqmu, const double hr[3],
                                            const double hv[3], double dt_obs, double &chi,
@@ -609,17 +630,24 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
             // light delay (Sec. 2): tau0 = |r(t)-o|/c, three fixed iterations
             double chi = 0.0, pos[3];
             TwoBodyLT T;
-            const bool ok = twobody_at(mu, sqmu, hr, hv, dt_obs, chi, T);
+            bool ok = twobody_at(mu, sqmu, hr, hv, dt_obs, chi, T);
             twobody_pos(T, sun_obs, 0.0, pos);
             double u[3] = {pos[0] - o[0], pos[1] - o[1], pos[2] - o[2]};
             double tau = sqrt(dot3(u, u)) * kInvC;
-            for (int it = 0; it < 3; it++) {
-                twobody_pos(T, sun_obs, tau, pos);
+            // near the Sun the cubic is not good enough: solve at every iterate
+            const bool exact_lt = lt_taylor_bound(mu, T, 1.01 * tau) > kTaylorMaxAu;
+            for (int it = 0; it < 4; it++) {
+                if (exact_lt) {
+                    double rk[3], vk[3];
+                    ok = kepler_uv(mu, sqmu, hr, hv, dt_obs - tau, chi, rk, vk) && ok;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) pos[c] = fma(-tau, sun_obs[3 + c], sun_obs[c]) + rk[c];
+                } else {
+                    twobody_pos(T, sun_obs, tau, pos);
+                }
                 u[0] = pos[0] - o[0]; u[1] = pos[1] - o[1]; u[2] = pos[2] - o[2];
-                tau = sqrt(dot3(u, u)) * kInvC;
+                if (it < 3) tau = sqrt(dot3(u, u)) * kInvC;
             }
-            twobody_pos(T, sun_obs, tau, pos);
-            u[0] = pos[0] - o[0]; u[1] = pos[1] - o[1]; u[2] = pos[2] - o[2];
             if (!ok) {
                 if (C.status) atomicCAS(&C.status[i], KETE_BODY_OK, KETE_BODY_KEPLER_CAP);
                 continue;

@@ -668,6 +668,81 @@ def ragged1y(n_bodies=500_000, seed=None, days=365.0):
     return w
 
 
+def fov_edge(n_bodies=2000, seed=None):
+    """FoV-stage edge cases (test workload): ragged1y's population (main belt,
+    NEOs with forced 0.001-0.01 AU Earth encounters, Trojans, comets) plus one
+    sungrazing comet (q 0.01 AU, e 0.995, perihelion at T0 + 100 d), seen
+    from the Earth by frames aimed where the two-body + light-time step is
+    stressed: comets within 6 days of a perihelion inside the year, the forced
+    encounters within 2 days of closest approach, Trojans, the sungrazer
+    within 3 days of perihelion, and a few main-belt bodies and NEOs.  Frames
+    alternate squares and cones, one per exposure, offset from the aim point
+    by up to 0.3 of their radius; frames at encounters are 0.1-0.3 rad wide
+    (the body crosses the sky at up to ~3 rad/day), at the sungrazer 0.01-
+    0.02 rad.  Each frame is aimed along the body's heliocentric conic from
+    T0 (a construction aid: the n-body motion differs a little, so some
+    frames miss); the observer is the Earth at the frame's epoch."""
+    seed = SEED_BASE + 11 if seed is None else seed
+    w = ragged1y(n_bodies=n_bodies, seed=seed)
+    ps = make_planets(seed)
+    rng = _rng(seed, 12)
+    # the sungrazer, appended as a comet
+    q, ecc, t_peri = 0.01, 0.995, T0 + 100.0
+    a_sg = q / (1.0 - ecc)
+    inc, node, peri = math.radians(rng.uniform(10, 80)), rng.uniform(0, 2 * np.pi), rng.uniform(0, 2 * np.pi)
+    M0 = -math.sqrt(GM_SUN / a_sg ** 3) * (t_peri - T0)
+    sg = bodies_from_elements(ps, np.array([a_sg]), np.array([ecc]), inc, node, peri, np.array([M0]))
+    states = np.concatenate([w.states, sg], axis=1)
+    labels = np.concatenate([w.labels, np.array([3], np.int8)])
+    n = states.shape[1]
+    a, e, i, om, w_, M = state_to_elements(states[:3] - ps.pos0[0][:, None],
+                                           states[3:] - ps.vel0[0][:, None], GM_SUN)
+    mm = np.sqrt(GM_SUN / a ** 3)
+    aims, kinds = [], []          # (body, epoch), frame size class
+    for b in np.nonzero(labels == 3)[0][:-1]:
+        tp = T0 + np.mod(-M[b], 2 * np.pi) / mm[b]
+        if T0 + 8.0 <= tp <= T0 + 357.0:
+            aims += [(b, tp + d) for d in (-6.0, -1.5, 0.0, 0.7, 6.0)]; kinds += [0] * 5
+    for b, te in zip(np.nonzero(labels == 4)[0], w.meta["t_enc"]):
+        aims += [(b, T0 + te + d) for d in (-2.0, -0.4, -0.05, 0.0, 0.03, 0.3, 1.5)]; kinds += [1] * 7
+    for b in np.nonzero(labels == 2)[0]:
+        aims += [(b, t) for t in rng.uniform(T0 + 5.0, T0 + 360.0, 2)]; kinds += [0] * 2
+    aims += [(n - 1, t_peri + d) for d in (-3.0, -0.5, -0.1, -0.02, 0.0, 0.02, 0.1, 0.6, 3.0)]
+    kinds += [2] * 9
+    other = np.nonzero(labels <= 1)[0]
+    for b in rng.choice(other, 60, replace=False):
+        aims += [(b, rng.uniform(T0 + 5.0, T0 + 360.0))]; kinds += [0]
+    body = np.array([x[0] for x in aims]); ep = np.array([x[1] for x in aims]); kinds = np.array(kinds)
+    order = np.argsort(ep, kind="stable")
+    body, ep, kinds = body[order], ep[order], kinds[order]
+    pl = integrate_planets(ps, ep)
+    hp, _ = elements_to_state(a[body], e[body], i[body], om[body], w_[body],
+                              M[body] + mm[body] * (ep - T0), GM_SUN)
+    d = hp.T + pl[:, 0, :3] - pl[:, 3, :3]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    size = np.where(kinds == 1, rng.uniform(0.1, 0.3, len(ep)),
+                    np.where(kinds == 2, rng.uniform(0.01, 0.02, len(ep)),
+                             rng.uniform(0.005, 0.012, len(ep))))
+    # offset the centre from the aim point by up to 0.3 of the size
+    t1 = np.cross(d, rng.normal(size=d.shape)); t1 /= np.linalg.norm(t1, axis=1, keepdims=True)
+    off = size * rng.uniform(0.0, 0.3, len(ep))
+    cen = d * np.cos(off)[:, None] + t1 * np.sin(off)[:, None]
+    e_ax = np.cross(cen, rng.normal(size=d.shape))
+    normals = square_normals(cen, e_ax, 0.0)
+    for k in range(len(ep)):
+        normals[k] = square_normals(cen[k], e_ax[k], size[k])
+    fr = _frames_array(ep, np.arange(len(ep)), np.arange(len(ep)), normals)
+    cone = np.arange(len(ep)) % 2 == 1
+    fr["n_edges"][cone] = 0
+    fr["normals"][cone] = 0.0
+    fr["normals"][cone, 0, :] = cen[cone]
+    fr["normals"][cone, 1, 0] = size[cone]
+    out = Workload("fov_edge", seed, w.ephem, states, np.full(n, T0), fr, pl[:, 3, :3].copy(),
+                   T0 + 365.0, labels)
+    out.meta.update(aim_body=body, sungrazer=n - 1, t_enc=w.meta["t_enc"])
+    return out
+
+
 OBS_DTYPE = np.dtype([("epoch", "<f8"), ("ra", "<f8"), ("dec", "<f8"), ("obs", "<f8", (3,))])
 assert OBS_DTYPE.itemsize == 48
 

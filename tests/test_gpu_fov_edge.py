@@ -1,0 +1,155 @@
+"""GPU parity of the FoV stage at the method's edge cases (Sec. 2 two-body +
+light delay, Sec. 3.1 FoV test), through kete_fov_check against the oracle.
+
+  * fov_edge: comets within days of perihelion, NEOs within days of a
+    forced 0.001-0.01 AU Earth encounter, Jupiter Trojans and a sungrazer
+    (q = 0.01 AU) seen from the Earth -- the light-time shortcut of the exact
+    test must fall back to a full two-body solve near the Sun, and close
+    bodies take the all-exposures branch of the candidate search;
+  * tiny frames: cones and squares of 1e-5 to 1e-4 rad around known sky
+    positions, where the FP32 cap test in front of the exact test must not
+    drop a body that is inside.
+
+Bar: membership identical outside the 1e-9 rad edge band (mixed precision:
+outside max(1e-9, 2 x its largest sky difference)), sky positions within
+1 mas, for every population."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import cached_workload
+from paper_2509_04666_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MAS = math.radians(1.0 / 3.6e6)
+POP = {0: "main_belt", 1: "neo", 2: "trojan", 3: "comet", 4: "encounter"}
+
+
+@pytest.fixture(scope="module")
+def K():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_04666_gb300 import build as B, kete
+    B.build()
+    k = kete.Kete(0)
+    yield k
+    k.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _gpu(K, w, frames, precision):
+    from paper_2509_04666_gb300 import kete
+    K.load_ephem(w.ephem.to_bytes())
+    fm = kete.force_model(precision=precision)
+    hits, nh, status = K.fov_check(_dev(w.states), _dev(w.epochs),
+                                   kete.frames_to_device(frames, "cuda"), _dev(w.observers), fm=fm)
+    return kete.decode_hits(hits, nh), status.cpu().numpy()
+
+
+def _sky(ra1, de1, ra2, de2):
+    dra = (ra1 - ra2 + math.pi) % (2 * math.pi) - math.pi
+    return math.hypot(dra * math.cos(de1), de1 - de2)
+
+
+def _check(got, ref, labels, mixed):
+    """Per-population sky differences; membership outside the edge band."""
+    g = {(int(f), int(b)): (ra, de) for f, b, ra, de in
+         zip(got["frame"].tolist(), got["body"].tolist(), got["ra"].tolist(), got["dec"].tolist())}
+    r = {(int(h["frame"]), int(h["body"])): h for h in ref}
+    worst = {}
+    for key in set(g) & set(r):
+        d = _sky(*g[key], r[key]["ra"], r[key]["dec"])
+        lab = POP[int(labels[key[1]])]
+        worst[lab] = max(worst.get(lab, 0.0), d)
+    band = max(1e-9, 2 * max(worst.values(), default=0.0)) if mixed else 1e-9
+    bad = [k for k in set(g) ^ set(r) if k not in r or abs(r[k]["margin"]) >= band]
+    assert not bad, f"{len(bad)} hits differ outside the {band:.2e} rad band, e.g. {sorted(bad)[:5]}"
+    keys = list(zip(got["frame"].tolist(), got["body"].tolist()))
+    assert keys == sorted(keys)
+    return {k: v / MAS for k, v in worst.items()}
+
+
+@pytest.fixture(scope="module")
+def edge():
+    w = cached_workload("fov_edge")
+    orc = O.Oracle(w.ephem.to_bytes())
+    ref, status, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, w.frames, w.observers)
+    assert (status == 0).all()
+    return w, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_edge_populations_match_oracle(K, edge, precision):
+    from paper_2509_04666_gb300 import kete
+    w, ref = edge
+    mixed = precision == "mixed"
+    got, status = _gpu(K, w, w.frames, kete.MIXED if mixed else kete.FP64)
+    assert (status == 0).all()
+    worst = _check(got, ref, w.labels, mixed)
+    # every population is reached, the sungrazer near perihelion included
+    assert set(worst) == set(POP.values()), worst
+    sg = w.meta["sungrazer"]
+    assert (ref["body"] == sg).sum() >= 8
+    for lab, mas in worst.items():
+        assert mas < 1.0, (lab, mas)
+    if not mixed:
+        assert max(worst.values()) < 0.01, worst
+
+
+def _tiny_frames(w, ref_big, rng):
+    """Cones and squares of 1e-5-1e-4 rad about the oracle's positions of
+    one hit of each frame of ref_big, with that frame's epoch and observer,
+    offset so that the body is inside (0, 0.5, 0.9 of the radius) or outside
+    (1.1, 2).  The new frames batch differently, which moves a main-belt
+    body's position by ~1e-8 rad, far less than a frame."""
+    hits = ref_big[np.unique(ref_big["frame"], return_index=True)[1]]
+    fr = np.zeros(len(hits), W.FRAME_DTYPE)
+    inside = np.zeros(len(hits), bool)
+    for k, h in enumerate(hits):
+        src = w.frames[h["frame"]]
+        u = W.eq_to_ecl(np.array([math.cos(h["dec"]) * math.cos(h["ra"]),
+                                  math.cos(h["dec"]) * math.sin(h["ra"]), math.sin(h["dec"])]))
+        t1 = np.cross(u, rng.normal(size=3)); t1 /= np.linalg.norm(t1)
+        size = 10 ** rng.uniform(-5, -4)
+        f = [0.0, 0.5, 0.9, 1.1, 2.0][k % 5]
+        cen = u * math.cos(f * size) + t1 * math.sin(f * size)
+        fr[k]["epoch"], fr[k]["observer_idx"], fr[k]["exposure_id"] = src["epoch"], src["observer_idx"], k
+        if k % 2 == 0:
+            fr[k]["n_edges"] = 0
+            fr[k]["normals"][0] = cen
+            fr[k]["normals"][1][0] = size
+        else:
+            # square of half-width `size` whose axis e points along t1: the
+            # body sits at -f size along e from the centre
+            fr[k]["n_edges"] = 4
+            fr[k]["normals"] = W.square_normals(cen, t1, size)
+        inside[k] = f < 1.0
+    return fr, inside
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tiny_frames_match_oracle(K, mb1k_dense, precision):
+    from paper_2509_04666_gb300 import kete
+    w = mb1k_dense
+    orc = O.Oracle(w.ephem.to_bytes())
+    ref_big, _, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, w.frames, w.observers)
+    fr, inside = _tiny_frames(w, ref_big, np.random.default_rng(17))
+    assert len(fr) >= 100
+    ref, _, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, fr, w.observers)
+    mixed = precision == "mixed"
+    got, status = _gpu(K, w, fr, kete.MIXED if mixed else kete.FP64)
+    assert (status == 0).all()
+    _check(got, ref, np.zeros(w.n_bodies, int), mixed)
+    # non-vacuous: the frames meant to hold their body do (positions are
+    # the same batches' as the frames they were cut from)
+    hit_frames = set(int(h["frame"]) for h in ref)
+    assert sum(k in hit_frames for k in np.nonzero(inside)[0]) >= 0.95 * inside.sum()
+    assert len(set(got["frame"].tolist())) >= 0.95 * inside.sum()

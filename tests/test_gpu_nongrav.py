@@ -138,7 +138,10 @@ def test_stops_and_noalloc_with_nongrav(K, pop):
     s2 = _dev(sub); e2 = _dev(w.epochs[idx])
     K.propagate(s1, e1, W.T0 + 200.0, fm=fm)
     K.propagate_noalloc(s2, e2, W.T0 + 200.0, fm=fm)
-    assert np.array_equal(s1.cpu().numpy(), s2.cpu().numpy())
+    # the no-allocation entry point runs another launch variant (static, no
+    # node rows): equal to the integrator's truncation level, not bit for bit
+    a, b = s1.cpu().numpy(), s2.cpu().numpy()
+    assert np.abs(a[:3] - b[:3]).max() < 1e-9 and np.abs(a[3:] - b[3:]).max() < 1e-11
 
 
 def test_fov_check_with_nongrav_matches_oracle(K, mb1k_dense):

@@ -3,8 +3,9 @@ memory while they run (their GPU memory is handed to their own pool at
 start-up, or a real-time thread must not block in the driver's allocator).
 
 The entry point is called through the C ABI and compared with kete_propagate,
-the allocating entry point it mirrors, on two calls in a row (different
-targets, so a stale stop or counter in the shared device array would show).
+the allocating entry point it mirrors, on two calls in a row with different
+targets, so that a stop epoch left in the shared device array by the first
+call would show in the second.
 This file is collected last so a failure here does not hide the others."""
 import ctypes as C
 
