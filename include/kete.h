@@ -131,7 +131,7 @@ typedef struct kete_force_model {
  *   (any length), normals[1][0] the angular radius in radians (0 < r < pi);
  *   u is inside iff its angle to the centre is below r.
  * Boundary points are outside.  An extended exposure is approximated by
- * several instantaneous frames along it (see the binding's streak_frames). */
+ * several instantaneous frames along it (kete_fov_check_extended). */
 #define KETE_FRAME_CONE 0
 typedef struct kete_frame {
     double epoch;                /* TDB JD of the (instantaneous) observation */
@@ -314,6 +314,37 @@ int kete_fov_check_mag(kete_ctx *ctx, const double *states, const double *epochs
                        int64_t n_obs, const kete_force_model *fm, const kete_survey_opts *opt,
                        const kete_mag_params *mag_params, kete_hit *hits, int64_t capacity,
                        int64_t *n_hits, int32_t *status);
+
+/* Largest n_sub kete_fov_check_extended accepts. */
+#define KETE_EXT_MAX_SUB 64
+
+/* kete_fov_check for extended exposures (Sec. 3.1: an exposure of finite
+ * length is approximated by several instantaneous observations along it).
+ * Frame f (device, [n_frames], sorted by epoch, exposures contiguous, as in
+ * kete_fov_check) starts at frames[f].epoch and lasts durations[f] days
+ * (device, [n_frames], finite, >= 0, equal within an exposure).  It is split
+ * into n_sub (1..KETE_EXT_MAX_SUB) equal sub-intervals; sub-frame k is the
+ * same patch at epoch frames[f].epoch + ((k + 0.5) durations[f]) / n_sub seen
+ * from observers row frames[f].observer_idx + k (so each exposure owns n_sub
+ * consecutive observer rows, one per sub-epoch; rows up to observer_idx +
+ * n_sub - 1 must exist).  The sub-frames of one sub-interval of one exposure
+ * form one instantaneous exposure of the survey path; the sub-frame epochs
+ * must be non-decreasing across exposures (exposures that overlap in time
+ * are rejected with KETE_ERR_BAD_ARG).
+ * A body is in frame f if it is in any of its sub-frames: hits (device,
+ * [capacity]) receive one hit per (frame, body), frame = f, with the RA/Dec
+ * (and magnitude, if mag_params is not NULL; see kete_fov_check_mag) of the
+ * earliest sub-frame that holds it, sorted by (frame, body).  *n_hits, the
+ * CAPACITY retry and status as kete_fov_check; kete_get_stats counts the
+ * merged hits and the sub-frame exposures.  Library scratch grows with
+ * n_frames * n_sub.  Errors: as kete_fov_check, and BAD_ARG for n_sub,
+ * durations or observer rows out of range. */
+int kete_fov_check_extended(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                            const kete_frame *frames, int64_t n_frames, const double *durations,
+                            int32_t n_sub, const double *observers, int64_t n_obs,
+                            const kete_force_model *fm, const kete_survey_opts *opt,
+                            const kete_mag_params *mag_params, kete_hit *hits, int64_t capacity,
+                            int64_t *n_hits, int32_t *status);
 
 /* Copy the counters of the last call into *out (host). */
 int kete_get_stats(const kete_ctx *ctx, kete_stats *out);

@@ -32,6 +32,8 @@ enum Slot {
     S_ADJ_REC, S_ADJ_NREC, S_ADJ_NBAT, S_ADJ_BIDX, S_ADJ_YREF, S_ADJ_GJUMP, S_ADJ_STATUS,
     S_KSTOP, S_DEFER_LIST, S_DEFER_CNT, S_ORDER, S_ORDER_KEY, S_ORDER_HIST, S_ORDER_OFF,
     S_ORDER_SCAN, S_ORDER_N, S_ADJ_TEND, S_LEG_OUT,
+    S_EXT_START, S_EXT_EX, S_EXT_TMP, S_EXT_FIRST, S_EXT_SUB, S_EXT_PARENT, S_EXT_CNT,
+    S_EXT_OFF, S_EXT_CUR, S_EXT_GROUP, S_EXT_KEEP, S_EXT_KCNT, S_EXT_KOFF,
     S_NSLOTS
 };
 
@@ -668,6 +670,49 @@ extern "C" int kete_propagate_stops(kete_ctx *ctx, const double *states, const d
     return KETE_OK;
 }
 
+// Union of the sub-frames' hits (tmp, nh in any order; parent[sub-frame]) per
+// parent frame: one hit per (frame, body), the earliest sub-frame's, sorted by
+// (frame, body) into hits.  CAPACITY leaves the merged count in *n_hits.
+static int merge_extended(kete_ctx *ctx, const kete_hit *tmp, unsigned long long nh,
+                          const int32_t *parent, int64_t np, kete_hit *hits, int64_t capacity,
+                          int64_t *n_hits, int64_t &launches)
+{
+    cudaStream_t st = ctx->stream;
+    int32_t *cnt, *cur, *kcnt; int64_t *off, *koff, *scan_tmp; kete_hit *grp; int8_t *keep;
+    GET(S_EXT_CNT, np, cnt);
+    GET(S_EXT_CUR, np, cur);
+    GET(S_EXT_KCNT, np, kcnt);
+    GET(S_EXT_OFF, np + 1, off);
+    GET(S_EXT_KOFF, np + 1, koff);
+    GET(S_EXT_TMP, scan_tmp_elems(np), scan_tmp);
+    GET(S_EXT_GROUP, nh, grp);
+    GET(S_EXT_KEEP, nh, keep);
+    phase_mark(ctx, PH_ORDER, true);
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, np * sizeof(int32_t), st));
+    CUDA_TRY(cudaMemsetAsync(cur, 0, np * sizeof(int32_t), st));
+    CUDA_TRY(fov_merge_count(tmp, nh, parent, cnt, nullptr, nullptr, nullptr, false, st));
+    CUDA_TRY(exclusive_scan(cnt, np, off, scan_tmp, st));
+    CUDA_TRY(fov_merge_count(tmp, nh, parent, cnt, off, cur, grp, true, st));
+    CUDA_TRY(fov_merge_keep(grp, off, np, keep, kcnt, ctx->n_sm, st));
+    CUDA_TRY(exclusive_scan(kcnt, np, koff, scan_tmp, st));
+    int64_t merged = 0;
+    CUDA_TRY(cudaMemcpyAsync(&merged, koff + np, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    launches += 3 + 2 * scan_launches(np);
+    *n_hits = merged;
+    if (merged > capacity) {
+        phase_mark(ctx, PH_ORDER, false);
+        return fail(ctx, KETE_ERR_CAPACITY, "hit buffer holds %lld, %lld needed", (long long)capacity,
+                    (long long)merged);
+    }
+    if (merged > 0) {
+        CUDA_TRY(fov_merge_place(grp, off, keep, koff, np, hits, ctx->n_sm, st));
+        launches++;
+    }
+    phase_mark(ctx, PH_ORDER, false);
+    return KETE_OK;
+}
+
 // sky-cell grid: bands of height ~cell, cells of width >= cell along each band
 static void make_bands(double cell, std::vector<int32_t> &off, std::vector<int32_t> &cnt,
                        double &hb, int &n_bands, int &n_cells)
@@ -687,12 +732,16 @@ static void make_bands(double cell, std::vector<int32_t> &off, std::vector<int32
     n_cells = off[n_bands];
 }
 
+// The survey driver.  ext_nsub > 0: the frames are extended exposures of
+// ext_dur[f] days each (device), replaced by ext_nsub instantaneous sub-frames
+// (fov_ext_expand) whose hits are merged back per frame at the end.
 static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epochs,
                           int64_t n, const kete_frame *frames, int64_t n_frames,
                           const double *observers, int64_t n_obs,
                           const kete_force_model *fm, const kete_survey_opts *opt_in,
                           const kete_mag_params *mag, kete_hit *hits, int64_t capacity,
-                          int64_t *n_hits, int32_t *status)
+                          int64_t *n_hits, int32_t *status, const double *ext_dur = nullptr,
+                          int ext_nsub = 0)
 {
     if (!ctx) return KETE_ERR_BAD_ARG;
     if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
@@ -709,11 +758,39 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
     ForceDev F;
     int r = make_force(ctx, fm, F);
     if (r != KETE_OK) return r;
+    const bool ext = ext_nsub > 0;
+    if (ext && (ext_nsub > KETE_EXT_MAX_SUB || (n_frames > 0 && !ext_dur) ||
+                n_frames * (int64_t)ext_nsub >= INT32_MAX))
+        return fail(ctx, KETE_ERR_BAD_ARG, "extended exposures: n_sub must be 1..%d, durations "
+                    "given, n_frames * n_sub below 2^31", KETE_EXT_MAX_SUB);
     *n_hits = 0;
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     stats_begin(ctx);
     int64_t launches = 0;
+    int32_t *ext_parent = nullptr;
+    if (ext && n_frames > 0) {
+        // sub-frames of the extended exposures (Sec. 3.1)
+        int32_t *pst, *pfirst; int64_t *pex, *ptmp; kete_frame *sub;
+        GET(S_EXT_START, n_frames, pst);
+        GET(S_EXT_EX, n_frames + 1, pex);
+        GET(S_EXT_TMP, scan_tmp_elems(n_frames), ptmp);
+        GET(S_EXT_FIRST, n_frames + 1, pfirst);
+        GET(S_EXT_SUB, n_frames * ext_nsub, sub);
+        GET(S_EXT_PARENT, n_frames * ext_nsub, ext_parent);
+        CUDA_TRY(fov_ext_expand(frames, ext_dur, n_frames, ext_nsub, n_obs, pst, pex, ptmp, pfirst,
+                                sub, ext_parent, ctx->d_ctr, st));
+        launches += 3 + scan_launches(n_frames);
+        CUDA_TRY(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        const int fl = ctx->h_ctr->error_flags;
+        if (fl & 1) return fail(ctx, KETE_ERR_BAD_ARG, "frames are not sorted by epoch");
+        if (fl & 2) return fail(ctx, KETE_ERR_BAD_ARG, "frames of one exposure differ in epoch, observer or duration");
+        if (fl & 4) return fail(ctx, KETE_ERR_BAD_ARG, "observer_idx + n_sub exceeds the observer rows");
+        if (fl & 64) return fail(ctx, KETE_ERR_BAD_ARG, "exposure durations must be finite and >= 0");
+        frames = sub;
+        n_frames *= ext_nsub;
+    }
     const int64_t nf = n_frames;
     ChainState cs{};
     if (n > 0) {
@@ -746,6 +823,8 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
     CUDA_TRY(cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     int flags = ctx->h_ctr->error_flags;
+    if ((flags & 1) && ext)
+        return fail(ctx, KETE_ERR_BAD_ARG, "sub-frame epochs are not sorted: extended exposures overlap in time");
     if (flags & 1) return fail(ctx, KETE_ERR_BAD_ARG, "frames are not sorted by epoch");
     if (flags & 2) return fail(ctx, KETE_ERR_BAD_ARG, "frames of one exposure differ in epoch or observer");
     if (flags & 4) return fail(ctx, KETE_ERR_BAD_ARG, "observer_idx out of range");
@@ -946,6 +1025,20 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
         ctx->stats.launches = launches;
         return fail(ctx, KETE_ERR_EPHEM_SPAN, "a batch midpoint or frame epoch lies outside the ephemeris table");
     }
+    if (ext) {
+        r = merge_extended(ctx, hit_tmp, hits_total, ext_parent, nf / ext_nsub, hits, capacity,
+                           n_hits, launches);
+        if (r != KETE_OK) return r;
+        r = stats_end(ctx);
+        if (r != KETE_OK) return r;
+        stats_collect(ctx);
+        ctx->stats.n_batches = nb;
+        ctx->stats.n_exposures = ne;
+        ctx->stats.n_candidates = (int64_t)cands_total;
+        ctx->stats.n_hits = *n_hits;
+        ctx->stats.launches = launches + ctx->extra_launches;
+        return KETE_OK;
+    }
     if ((int64_t)hits_total > capacity) {
         r = stats_end(ctx);
         stats_collect(ctx);
@@ -995,6 +1088,20 @@ extern "C" int kete_fov_check_mag(kete_ctx *ctx, const double *states, const dou
 {
     return fov_check_impl(ctx, states, epochs, n, frames, n_frames, observers, n_obs, fm, opt,
                           mag_params, hits, capacity, n_hits, status);
+}
+
+extern "C" int kete_fov_check_extended(kete_ctx *ctx, const double *states, const double *epochs,
+                                       int64_t n, const kete_frame *frames, int64_t n_frames,
+                                       const double *durations, int32_t n_sub,
+                                       const double *observers, int64_t n_obs,
+                                       const kete_force_model *fm, const kete_survey_opts *opt,
+                                       const kete_mag_params *mag_params, kete_hit *hits,
+                                       int64_t capacity, int64_t *n_hits, int32_t *status)
+{
+    if (ctx && n_sub < 1)
+        return fail(ctx, KETE_ERR_BAD_ARG, "extended exposures: n_sub must be 1..%d", KETE_EXT_MAX_SUB);
+    return fov_check_impl(ctx, states, epochs, n, frames, n_frames, observers, n_obs, fm, opt,
+                          mag_params, hits, capacity, n_hits, status, durations, n_sub);
 }
 
 // Propagation whose chain scratch is a fixed device array (see kete.h): no

@@ -419,10 +419,14 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
 
 // Mixed precision (FP32 planets): the Sun's monopole in FP64; the Sun's GR and
 // J2 and every planet in FP32 -- except planets flagged in `close` (within
-// kCloseAu at the start of the step), which stay in FP64.  `as` receives the
+// 2 kCloseAu at the start of the step), which stay in FP64.  `as` receives the
 // FP64 part alone: it is smooth in time, so the step-size control estimates
-// its error from it (FP32 rounding noise would otherwise dominate b6).
-constexpr double kCloseAu = 0.05;
+// its error from it (FP32 rounding noise would otherwise dominate b6).  The
+// FP32 planet-relative vector carries ~6e-8 AU of rounding (the body's ~1 AU
+// Sun-relative position in FP32), a relative force error of ~2e-7 AU / d at
+// distance d; before a 0.001-0.01 AU pass that noise is amplified by 1/Delta
+// in the sky, so planets stay FP64 out to 0.2 AU.
+constexpr double kCloseAu = 0.1;
 
 // detect (step start, off = 0): planets within 2 kCloseAu go to FP64 and are
 // recorded in `close` (held for the step), and the nearest within kEncounterAu
@@ -612,7 +616,12 @@ __device__ __forceinline__ void stumpff(double z, double &C, double &S)
 
 // Heliocentric state (r0, v0) advanced by dt under mu.  chi is the universal
 // anomaly: in = initial guess (0 = none), out = solution (warm start).
-// Returns false if Newton's iteration did not converge.
+// Newton's iteration on F(chi) = A chi^2 C + B chi^3 S + r0 chi - sqrt(mu) dt
+// has converged when its step falls below 1e-15 |chi| or below the rounding
+// of F itself (4 ulps of the sum of its terms' magnitudes, divided by F'):
+// where the terms cancel (perihelion passages, short intervals) the step
+// settles into an oscillation of a few ulps of F / F' that a relative test
+// alone never accepts.  Returns false if Newton's iteration did not converge.
 __device__ __forceinline__ bool kepler_uv(double mu, double sqmu, const double r0[3],
                                           const double v0[3], double dt, double &chi,
                                           double r[3], double v[3])
@@ -631,14 +640,17 @@ __device__ __forceinline__ bool kepler_uv(double mu, double sqmu, const double r
         double x2 = chi * chi;
         z = alpha * x2;
         stumpff(z, C, S);
-        double Fv = fma(A * x2, C, fma(B * x2 * chi, S, fma(rn0, chi, -target)));
+        const double t1 = A * x2, t2 = B * x2 * chi;
+        double Fv = fma(t1, C, fma(t2, S, fma(rn0, chi, -target)));
         double dF = fma(A * chi, fma(-z, S, 1.0), fma(B * x2, C, rn0));
         double step = Fv / dF;
+        const double floor_f = 8.881784197001252e-16 *   // 4 ulps of 1
+                               (fabs(t1 * C) + fabs(t2 * S) + fabs(rn0 * chi) + fabs(target));
         // keep the iterate on the solution's side of zero and bounded in growth
         double nxt = chi - step;
         if ((nxt > 0.0) != (dt > 0.0) && dt != 0.0) nxt = 0.5 * chi;
         chi = nxt;
-        if (fabs(step) <= 1e-15 * fabs(chi) || Fv == 0.0) {
+        if (fabs(step) <= 1e-15 * fabs(chi) || fabs(step) * fabs(dF) <= floor_f || Fv == 0.0) {
             ok = true;
             break;
         }

@@ -740,6 +740,128 @@ __global__ void k_hit_rank(const kete_hit *__restrict__ src, const int64_t *__re
 }
 
 // ---------------------------------------------------------------------------
+// extended exposures (Sec. 3.1: an exposure of finite length is approximated
+// by several instantaneous observations along it)
+// ---------------------------------------------------------------------------
+// Exposure starts of the caller's frames, and their checks: bit 0 epochs not
+// sorted, bit 1 an exposure's frames differ in epoch, observer or duration,
+// bit 2 observer rows out of range, bit 6 a negative or non-finite duration.
+__global__ void k_ext_starts(const kete_frame *__restrict__ fr, const double *__restrict__ dur,
+                             int64_t nf, int n_sub, int64_t n_obs, int32_t *__restrict__ is_start,
+                             DevCounters *ctr)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const double ep = fr[i].epoch, d = dur[i];
+    const int64_t oi = fr[i].observer_idx;
+    const bool start = (i == 0) || (fr[i - 1].exposure_id != fr[i].exposure_id);
+    is_start[i] = start ? 1 : 0;
+    if (i > 0) {
+        if (!(ep >= fr[i - 1].epoch)) set_flag(ctr, 0);
+        if (!start && (fr[i - 1].epoch != ep || fr[i - 1].observer_idx != oi || dur[i - 1] != d))
+            set_flag(ctr, 1);
+    }
+    if (oi < 0 || oi > n_obs - n_sub) set_flag(ctr, 2);
+    if (!(d >= 0.0) || !isfinite(d)) set_flag(ctr, 6);
+}
+
+// Sub-frame k of frame f (exposure starting at frame f0, S frames): index
+// f0 n_sub + k S + (f - f0), epoch t + ((k + 1/2) d) / n_sub, observer row
+// observer_idx + k, exposure f0 n_sub + k -- so the sub-frames of sub-interval
+// k of one exposure form one contiguous exposure, in epoch order.
+__global__ void k_ext_expand(const kete_frame *__restrict__ fr, const double *__restrict__ dur,
+                             int64_t nf, int n_sub, const int32_t *__restrict__ is_start,
+                             const int64_t *__restrict__ ex, const int32_t *__restrict__ exp_first,
+                             kete_frame *__restrict__ sub, int32_t *__restrict__ parent)
+{
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int64_t e = ex[f] + is_start[f] - 1;   // starts up to and including f, less one
+    const int64_t f0 = exp_first[e], S = exp_first[e + 1] - f0;
+    const int64_t base = f0 * n_sub;
+    const kete_frame src = fr[f];
+    const double d = dur[f];
+    for (int k = 0; k < n_sub; k++) {
+        kete_frame o = src;
+        o.epoch = src.epoch + ((k + 0.5) * d) / (double)n_sub;
+        o.observer_idx = src.observer_idx + k;
+        o.exposure_id = base + k;
+        const int64_t j = base + (int64_t)k * S + (f - f0);
+        sub[j] = o;
+        parent[j] = (int32_t)f;
+    }
+}
+
+// hits of the sub-frames per parent frame
+__global__ void k_merge_count(const kete_hit *__restrict__ h, unsigned long long nh,
+                              const int32_t *__restrict__ parent, int32_t *__restrict__ cnt)
+{
+    const unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nh) return;
+    atomicAdd(&cnt[parent[h[q].frame]], 1);
+}
+
+__global__ void k_merge_scatter(const kete_hit *__restrict__ h, unsigned long long nh,
+                                const int32_t *__restrict__ parent, const int64_t *__restrict__ off,
+                                int32_t *__restrict__ cur, kete_hit *__restrict__ grouped)
+{
+    const unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nh) return;
+    const kete_hit x = h[q];
+    const int32_t p = parent[x.frame];
+    grouped[off[p] + atomicAdd(&cur[p], 1)] = x;   // frame still names the sub-frame
+}
+
+// Warp per parent frame: a hit is kept iff no hit of the same body comes from
+// an earlier sub-frame (sub-frame indices grow with time within a frame).
+__global__ void k_merge_keep(const kete_hit *__restrict__ g, const int64_t *__restrict__ off,
+                             int64_t np, int8_t *__restrict__ keep, int32_t *__restrict__ kept_cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < np; p += nwarps) {
+        const int64_t a = off[p], m = off[p + 1] - a;
+        int32_t c = 0;
+        for (int64_t j = lane; j < m; j += 32) {
+            const int32_t bj = g[a + j].body;
+            const int64_t sj = g[a + j].frame;
+            bool first = true;
+            for (int64_t q = 0; q < m; q++)
+                if (g[a + q].body == bj && g[a + q].frame < sj) first = false;
+            keep[a + j] = first ? 1 : 0;
+            c += first ? 1 : 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) kept_cnt[p] = c;
+    }
+}
+
+// Warp per parent frame: kept hits in body order at out[kept_off[p] + rank],
+// renamed to the parent frame.
+__global__ void k_merge_place(const kete_hit *__restrict__ g, const int64_t *__restrict__ off,
+                              const int8_t *__restrict__ keep, const int64_t *__restrict__ kept_off,
+                              int64_t np, kete_hit *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < np; p += nwarps) {
+        const int64_t a = off[p], m = off[p + 1] - a;
+        for (int64_t j = lane; j < m; j += 32) {
+            if (!keep[a + j]) continue;
+            const int32_t bj = g[a + j].body;
+            int64_t rank = 0;
+            for (int64_t q = 0; q < m; q++) rank += (keep[a + q] && g[a + q].body < bj) ? 1 : 0;
+            kete_hit x = g[a + j];
+            x.frame = p;
+            out[kept_off[p] + rank] = x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 static unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
 #define KLAUNCH(...)                            \
@@ -849,6 +971,51 @@ cudaError_t fov_order_hits(const kete_hit *tmp, unsigned long long nh, const int
     int64_t blocks = (nf * 32 + 255) / 256;
     if (blocks > (int64_t)n_sm * 32) blocks = (int64_t)n_sm * 32;
     KLAUNCH(k_hit_rank<<<(unsigned)blocks, 256, 0, st>>>(grouped, frame_off, nf, out));
+    return cudaSuccess;
+}
+
+cudaError_t fov_ext_expand(const kete_frame *frames, const double *dur, int64_t nf, int n_sub,
+                           int64_t n_obs, int32_t *is_start, int64_t *ex, int64_t *scan_tmp,
+                           int32_t *exp_first, kete_frame *sub, int32_t *parent, DevCounters *ctr,
+                           cudaStream_t st)
+{
+    if (nf <= 0) return cudaSuccess;
+    KLAUNCH(k_ext_starts<<<grid_for(nf, 256), 256, 0, st>>>(frames, dur, nf, n_sub, n_obs, is_start, ctr));
+    cudaError_t e = exclusive_scan(is_start, nf, ex, scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    KLAUNCH(k_exposure_first<<<grid_for(nf, 256), 256, 0, st>>>(is_start, ex, nf, exp_first));
+    KLAUNCH(k_ext_expand<<<grid_for(nf, 128), 128, 0, st>>>(frames, dur, nf, n_sub, is_start, ex, exp_first, sub, parent));
+    return cudaSuccess;
+}
+
+cudaError_t fov_merge_count(const kete_hit *h, unsigned long long nh, const int32_t *parent,
+                            int32_t *cnt, const int64_t *off, int32_t *cur, kete_hit *grouped,
+                            bool scatter, cudaStream_t st)
+{
+    if (nh == 0) return cudaSuccess;
+    if (!scatter) KLAUNCH(k_merge_count<<<grid_for((int64_t)nh, 256), 256, 0, st>>>(h, nh, parent, cnt));
+    else KLAUNCH(k_merge_scatter<<<grid_for((int64_t)nh, 256), 256, 0, st>>>(h, nh, parent, off, cur, grouped));
+    return cudaSuccess;
+}
+
+cudaError_t fov_merge_keep(const kete_hit *grouped, const int64_t *off, int64_t np, int8_t *keep,
+                           int32_t *kept_cnt, int n_sm, cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    int64_t blocks = (np * 32 + 255) / 256;
+    if (blocks > (int64_t)n_sm * 32) blocks = (int64_t)n_sm * 32;
+    KLAUNCH(k_merge_keep<<<(unsigned)blocks, 256, 0, st>>>(grouped, off, np, keep, kept_cnt));
+    return cudaSuccess;
+}
+
+cudaError_t fov_merge_place(const kete_hit *grouped, const int64_t *off, const int8_t *keep,
+                            const int64_t *kept_off, int64_t np, kete_hit *out, int n_sm,
+                            cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    int64_t blocks = (np * 32 + 255) / 256;
+    if (blocks > (int64_t)n_sm * 32) blocks = (int64_t)n_sm * 32;
+    KLAUNCH(k_merge_place<<<(unsigned)blocks, 256, 0, st>>>(grouped, off, keep, kept_off, np, out));
     return cudaSuccess;
 }
 

@@ -99,6 +99,27 @@ cudaError_t fov_order_hits(const kete_hit *tmp, unsigned long long nh, const int
                            int64_t nf, int32_t *cursor, kete_hit *grouped, kete_hit *out,
                            int n_sm, cudaStream_t st);
 
+// Extended exposures: validate the caller's frames against their durations
+// (device, [nf]) and n_sub, and write nf * n_sub sub-frames and each one's
+// parent frame.  Flags in ctr->error_flags: bits 0-2 as fov_frame_prep, bit 6
+// a bad duration.
+cudaError_t fov_ext_expand(const kete_frame *frames, const double *dur, int64_t nf, int n_sub,
+                           int64_t n_obs, int32_t *is_start, int64_t *ex, int64_t *scan_tmp,
+                           int32_t *exp_first, kete_frame *sub, int32_t *parent, DevCounters *ctr,
+                           cudaStream_t st);
+// Union of the sub-frames' hits per parent frame: count (scatter = false) or
+// scatter into groups by parent (scatter = true, offsets from the counts);
+// then mark the earliest sub-frame's hit of every body and count them; then
+// place those in body order, renamed to the parent frame.
+cudaError_t fov_merge_count(const kete_hit *h, unsigned long long nh, const int32_t *parent,
+                            int32_t *cnt, const int64_t *off, int32_t *cur, kete_hit *grouped,
+                            bool scatter, cudaStream_t st);
+cudaError_t fov_merge_keep(const kete_hit *grouped, const int64_t *off, int64_t np, int8_t *keep,
+                           int32_t *kept_cnt, int n_sm, cudaStream_t st);
+cudaError_t fov_merge_place(const kete_hit *grouped, const int64_t *off, const int8_t *keep,
+                            const int64_t *kept_off, int64_t np, kete_hit *out, int n_sm,
+                            cudaStream_t st);
+
 // kete_scan.cu: exclusive prefix sum of int32 counts into int64 offsets
 // (out has n+1 entries; out[n] = total).  tmp must hold scan_tmp_elems(n).
 size_t scan_tmp_elems(int64_t n);

@@ -29,7 +29,9 @@ EXPORTS = ["kete_create", "kete_destroy", "kete_set_stream", "kete_last_error",
            "kete_force_model_default", "kete_survey_opts_default", "kete_load_ephem",
            "kete_ephem_eval", "kete_propagate", "kete_propagate_stops", "kete_fov_check",
            "kete_get_stats", "kete_propagate_noalloc", "kete_set_propagation", "kete_autotune",
-           "kete_adjoint", "kete_fov_check_mag", "kete_propagate_legs"]
+           "kete_adjoint", "kete_fov_check_mag", "kete_propagate_legs",
+           "kete_fov_check_extended"]
+EXT_MAX_SUB = 64
 MAG_NONE, MAG_HG, MAG_COMET_TOTAL, MAG_COMET_NUCLEUS = 0, 1, 2, 3
 
 
@@ -98,6 +100,9 @@ def lib():
         L.kete_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.kete_fov_check_mag.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, C.POINTER(ForceModel),
                                          C.POINTER(SurveyOpts), vp, vp, i64, C.POINTER(i64), vp]
+        L.kete_fov_check_extended.argtypes = [vp, vp, vp, i64, vp, i64, vp, C.c_int32, vp, i64,
+                                              C.POINTER(ForceModel), C.POINTER(SurveyOpts), vp,
+                                              vp, i64, C.POINTER(i64), vp]
         L.kete_propagate_noalloc.argtypes = [vp, vp, vp, i64, dbl, C.POINTER(ForceModel), vp]
         L.kete_propagate_legs.argtypes = [vp, vp, vp, i64, dbl, dbl, C.POINTER(ForceModel), vp]
         L.kete_set_propagation.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -246,40 +251,6 @@ def cone_frame(ra: float, dec: float, radius: float, epoch: float, observer_idx:
     return out
 
 
-def streak_frames(frame, t_start: float, t_end: float, observer_idx, exposure_id0: int):
-    """An extended exposure as len(observer_idx) instantaneous frames (Sec. 3.1:
-    extended events are approximated by several observations): copies of
-    `frame` (a kete_frame record, polygon or cone) at the midpoints of equal
-    sub-intervals of [t_start, t_end], sub-frame k seen from observers row
-    observer_idx[k], each its own exposure (ids exposure_id0 + k)."""
-    obs = np.asarray(observer_idx, np.int64)
-    k = obs.size
-    out = np.repeat(np.asarray(frame).reshape(1), k)
-    out["epoch"] = t_start + (np.arange(k) + 0.5) * (t_end - t_start) / k
-    out["observer_idx"] = obs
-    out["exposure_id"] = exposure_id0 + np.arange(k)
-    return out
-
-
-def merge_streak_hits(hits: dict, parent) -> dict:
-    """Union of the hits of each extended exposure: parent[f] names the
-    exposure frame f belongs to.  One row per (exposure, body), the earliest
-    sub-frame's (frames are sorted by epoch, hits by frame), sorted by
-    (exposure, body)."""
-    parent = np.asarray(parent, np.int64)
-    f = np.asarray(hits["frame"], np.int64)
-    b = np.asarray(hits["body"], np.int64)
-    key = parent[f] * (int(b.max()) + 1 if b.size else 1) + b
-    order = np.lexsort((f, key))               # by key, then earliest frame
-    key_s = key[order]
-    first = np.ones(key_s.size, bool)
-    first[1:] = key_s[1:] != key_s[:-1]
-    keep = order[first]
-    out = {k: np.asarray(v)[keep] for k, v in hits.items()}
-    out["exposure"] = parent[f[keep]]
-    return out
-
-
 def decode_hits(h: torch.Tensor, n: int):
     """kete_hit rows (int64 [n, 4] view) -> dict of CPU tensors."""
     h = h[:n].cpu()
@@ -421,6 +392,44 @@ class Kete:
                                               n_obs, C.byref(fm), C.byref(opts),
                                               mag_params.data_ptr(), hits.data_ptr(),
                                               hits.shape[0], C.byref(nh), status.data_ptr())
+            if rc == ERR_CAPACITY and attempt == 0:
+                hits = torch.empty((nh.value + 1024, 4), dtype=torch.int64, device=states.device)
+                continue
+            self._check(rc)
+            break
+        return hits, nh.value, status
+
+    def fov_check_extended(self, states, epochs, frames_dev, durations, n_sub, observers,
+                           fm=None, opts=None, capacity=None, hits=None, mag_params=None):
+        """kete_fov_check_extended: frames are exposures starting at their
+        epoch and lasting durations[f] days (CUDA float64 [n_frames]), each
+        split into n_sub sub-frames seen from observer rows observer_idx + k.
+        Returns (hits int64 [cap, 4], n_hits, status) with one hit per
+        (frame, body), as fov_check."""
+        n = epochs.numel()
+        _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
+        _dev_f64(observers, "observers")
+        if not (frames_dev.is_cuda and frames_dev.dtype == torch.uint8 and frames_dev.numel() % 128 == 0):
+            raise TypeError("frames must be a CUDA uint8 tensor of 128-byte kete_frame records")
+        nf = frames_dev.numel() // 128
+        _dev_f64(durations, "durations", (nf,))
+        if mag_params is not None and not (mag_params.is_cuda and mag_params.numel() == 24 * n):
+            raise TypeError("mag_params must hold n kete_mag_params records on the GPU")
+        fm = fm or force_model()
+        _check_nongrav(fm, n)
+        opts = opts or survey_opts()
+        status = torch.zeros(n, dtype=torch.int32, device=states.device)
+        if hits is None:
+            cap = capacity if capacity is not None else max(1024, 4 * nf)
+            hits = torch.empty((cap, 4), dtype=torch.int64, device=states.device)
+        nh = C.c_int64(0)
+        self._sync_stream()
+        for attempt in range(2):
+            rc = lib().kete_fov_check_extended(
+                self._h, states.data_ptr(), epochs.data_ptr(), n, frames_dev.data_ptr(), nf,
+                durations.data_ptr(), int(n_sub), observers.data_ptr(), observers.numel() // 3,
+                C.byref(fm), C.byref(opts), None if mag_params is None else mag_params.data_ptr(),
+                hits.data_ptr(), hits.shape[0], C.byref(nh), status.data_ptr())
             if rc == ERR_CAPACITY and attempt == 0:
                 hits = torch.empty((nh.value + 1024, 4), dtype=torch.int64, device=states.device)
                 continue

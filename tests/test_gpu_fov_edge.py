@@ -94,6 +94,7 @@ def test_edge_populations_match_oracle(K, edge, precision):
     got, status = _gpu(K, w, w.frames, kete.MIXED if mixed else kete.FP64)
     assert (status == 0).all()
     worst = _check(got, ref, w.labels, mixed)
+    print(f"fov_edge {precision}: max sky difference (mas) {worst}")
     # every population is reached, the sungrazer near perihelion included
     assert set(worst) == set(POP.values()), worst
     sg = w.meta["sungrazer"]

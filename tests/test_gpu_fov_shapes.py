@@ -84,43 +84,126 @@ def test_bad_cone_radius_is_refused(K, mb1k_dense):
         assert e.value.code == kete.ERR_BAD_ARG
 
 
-def test_streak_exposures_match_oracle(K, mb1k_dense):
-    """60 one-hour exposures (half of them cones) as 6 sub-frames each, the
-    observer (the Earth of the table) moving along; the merged hits agree."""
+def _subframes(frames, durations, n_sub):
+    """The sub-frames kete_fov_check_extended defines (test-local, from its
+    header): sub-frame k of frame f at epoch + ((k + 0.5) d) / n_sub from
+    observer row observer_idx + k, sub-interval k of an exposure forming one
+    exposure, exposures in order; returns them and each one's parent frame."""
+    start = np.ones(len(frames), bool)
+    start[1:] = frames["exposure_id"][1:] != frames["exposure_id"][:-1]
+    first = np.nonzero(start)[0]
+    bounds = list(first) + [len(frames)]
+    subs, parent = [], []
+    for f0, f1 in zip(bounds[:-1], bounds[1:]):
+        for k in range(n_sub):
+            for f in range(f0, f1):
+                x = frames[f].copy()
+                x["epoch"] = frames["epoch"][f] + ((k + 0.5) * durations[f]) / n_sub
+                x["observer_idx"] = frames["observer_idx"][f] + k
+                x["exposure_id"] = f0 * n_sub + k
+                subs.append(x)
+                parent.append(f)
+    return np.array(subs, dtype=frames.dtype), np.array(parent)
+
+
+def _union(ref, parent):
+    """Per (frame, body): the hit of the earliest sub-frame."""
+    out = {}
+    for h in ref:
+        key = (int(parent[h["frame"]]), int(h["body"]))
+        if key not in out or h["frame"] < out[key]["frame"]:
+            out[key] = h
+    return out
+
+
+@pytest.mark.parametrize("n_sub", [1, 6])
+def test_extended_exposures_match_oracle(K, mb1k_dense, n_sub):
+    """60 one-hour exposures (half of them cones, one of them a union of two
+    patches) through kete_fov_check_extended, the observer (the Earth of the
+    table) at every sub-epoch; one hit per (frame, body) with the earliest
+    sub-frame's position, identical to the union of the oracle's sub-frame
+    hits outside the edge band."""
+    import torch
     from paper_2509_04666_gb300 import kete
     w = mb1k_dense
     orc = O.Oracle(w.ephem.to_bytes())
     base = W.cone_frames(w.frames, slice(0, None, 2), math.radians(0.5))
-    # the 60 frames with the most bodies in them at their own epoch
     plain, _, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, base, w.observers)
-    pick = np.argsort(-np.bincount(plain["frame"], minlength=len(base)), kind="stable")[:60]
-    sub, obs, parent = [], [], []
-    for j, f in enumerate(pick):
-        t0 = float(w.frames["epoch"][f]) - 1.0 / 48
-        rows = np.arange(len(obs), len(obs) + 6)
-        s = kete.streak_frames(base[f], t0, t0 + 1.0 / 24, rows, 6 * j)
-        for t in s["epoch"]:
-            rc, p, _ = orc.ephem(3, float(t))
-            assert rc == 0
-            obs.append(p)
-        sub.append(s)
-        parent += [j] * 6
-    fr = np.concatenate(sub)
-    order = np.argsort(fr["epoch"], kind="stable")
-    fr = fr[order]
+    # the 60 frames with the most bodies whose hour-long exposures do not overlap
+    pick = []
+    for f in np.argsort(-np.bincount(plain["frame"], minlength=len(base)), kind="stable"):
+        if all(abs(base["epoch"][f] - base["epoch"][g]) > 1.5 / 24 for g in pick):
+            pick.append(f)
+        if len(pick) == 60:
+            break
+    fr = base[np.sort(pick)].copy()
+    fr["epoch"] -= 1.0 / 48
     fr["exposure_id"] = np.arange(len(fr))
-    parent = np.asarray(parent)[order]
-    obs = np.asarray(obs)
-    got = _gpu_hits(K, w, fr, obs)
-    ref, _, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, fr, obs)
-    assert len(ref) > 100
-    _compare(got, ref)
-    mg = kete.merge_streak_hits(got, parent)
-    mr = kete.merge_streak_hits({"frame": ref["frame"], "body": ref["body"],
-                                 "margin": ref["margin"]}, parent)
-    kg = set(zip(mg["exposure"].tolist(), mg["body"].tolist()))
-    kr = set(zip(mr["exposure"].tolist(), mr["body"].tolist()))
-    # a body seen in some sub-frame on one side only sits at a boundary there
+    fr[1]["epoch"] = fr[0]["epoch"]          # frames 0 and 1: one exposure of two patches
+    fr[1]["exposure_id"] = 0
+    dur = np.full(len(fr), 1.0 / 24)
+    # n_sub observer rows per exposure: the Earth at each sub-epoch
+    obs = np.zeros((len(fr) * n_sub, 3))
+    for f in range(len(fr)):
+        fr[f]["observer_idx"] = f * n_sub
+        for k in range(n_sub):
+            rc, p, _ = orc.ephem(3, fr[f]["epoch"] + ((k + 0.5) * dur[f]) / n_sub)
+            assert rc == 0
+            obs[f * n_sub + k] = p
+    fr[1]["observer_idx"] = fr[0]["observer_idx"]
+    sub, parent = _subframes(fr, dur, n_sub)
+    ref, _, _ = orc.fov_check(orc.force_model(), w.states, w.epochs, sub, obs)
+    want = _union(ref, parent)
+    assert len(want) > 60
+    K.load_ephem(w.ephem.to_bytes())
+    hits, nh, status = K.fov_check_extended(
+        torch.from_numpy(w.states).cuda(), torch.from_numpy(w.epochs).cuda(),
+        kete.frames_to_device(fr, "cuda"), torch.from_numpy(dur).cuda(), n_sub,
+        torch.from_numpy(obs).cuda(), capacity=16)            # too small: the CAPACITY retry
+    assert (status.cpu().numpy() == 0).all()
+    got = kete.decode_hits(hits, nh)
+    g = {(int(f), int(b)): (ra, de) for f, b, ra, de in
+         zip(got["frame"].tolist(), got["body"].tolist(), got["ra"].tolist(), got["dec"].tolist())}
+    assert len(g) == nh
+    keys = list(zip(got["frame"].tolist(), got["body"].tolist()))
+    assert keys == sorted(keys)
+    # a pair on one side only: seen only in sub-frames where it sits at an edge
     near = {(int(parent[h["frame"]]), int(h["body"])) for h in ref if abs(h["margin"]) < EDGE}
-    assert not ((kg ^ kr) - near)
-    assert len(kr) > 60
+    assert not ((set(g) ^ set(want)) - near)
+    worst = 0.0
+    for key in set(g) & set(want):
+        h = want[key]
+        if abs(h["margin"]) < EDGE:
+            continue   # the earliest sub-frame may differ at an edge
+        ra, de = g[key]
+        dra = (ra - h["ra"] + math.pi) % (2 * math.pi) - math.pi
+        worst = max(worst, math.hypot(dra * math.cos(de), de - h["dec"]))
+    assert worst < MAS, worst
+    st = K.get_stats()
+    assert st["n_hits"] == nh
+
+
+def test_extended_exposures_reject_bad_input(K, mb1k_dense):
+    import torch
+    from paper_2509_04666_gb300 import kete
+    w = mb1k_dense
+    K.load_ephem(w.ephem.to_bytes())
+    fr = w.frames[:10].copy()
+    obs = np.repeat(w.observers[:1], 40, axis=0)
+    fr["observer_idx"] = np.arange(10) * 4
+    st, ep = torch.from_numpy(w.states).cuda(), torch.from_numpy(w.epochs).cuda()
+    ob = torch.from_numpy(obs).cuda()
+
+    def call(frames, dur, n_sub, observers=ob):
+        return K.fov_check_extended(st, ep, kete.frames_to_device(frames, "cuda"),
+                                    torch.from_numpy(np.asarray(dur, float)).cuda(), n_sub, observers)
+    call(fr, np.full(10, 0.001), 4)                       # valid
+    bad = [(fr, np.full(10, 0.001), 0), (fr, np.full(10, 0.001), kete.EXT_MAX_SUB + 1),
+           (fr, np.full(10, -0.001), 4), (fr, np.r_[np.full(9, 0.001), np.nan], 4),
+           (fr, np.full(10, 0.001), 5)]                  # n_sub 5: rows beyond the observers
+    long = fr.copy(); long["epoch"] = fr["epoch"][0] + np.arange(10) * 0.01
+    bad.append((long, np.full(10, 0.5), 4))              # exposures overlap in time
+    for frames, dur, n_sub in bad:
+        with pytest.raises(kete.KeteError) as e:
+            call(frames, dur, n_sub)
+        assert e.value.code == kete.ERR_BAD_ARG
