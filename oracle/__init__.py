@@ -137,6 +137,9 @@ def lib():
         L.ko_body_loss.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, C.c_double,
                                    C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, d,
                                    C.c_void_p, C.c_void_p]
+        L.ko_body_sky_jacobian.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, C.c_double,
+                                           C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                           C.c_double, d, d]
         L.ko_propagate_stm.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, d, d,
                                        C.c_double, d, C.POINTER(Stats)]
         L.ko_fov_check.argtypes = [C.POINTER(Ephem), C.POINTER(ForceModel), d, d, C.c_int64,
@@ -271,6 +274,20 @@ class Oracle:
                                 len(ob), batch_span, twobody_max, ckpt_days, C.byref(loss),
                                 pred.ctypes.data, g.ctypes.data if grad else None)
         return rc, loss.value, pred, (g if grad else None)
+
+    def sky_jacobian(self, fm, state, epoch, obs, batch_span=3.0, twobody_max=1.5,
+                     ckpt_days=8.0):
+        """Per-observation sky partials of one body: (rc, jac [m, 2, 6] =
+        d(RA, Dec)/d(x0, v0), pred [m, 2])."""
+        st = np.ascontiguousarray(state, float)
+        ob = np.ascontiguousarray(obs, OBS_DTYPE)
+        pred = np.zeros((len(ob), 2))
+        jac = np.zeros((len(ob), 2, 6))
+        rc = lib().ko_body_sky_jacobian(C.byref(self.eph), C.byref(fm), _dp(st), epoch,
+                                        ob.ctypes.data, len(ob), batch_span, twobody_max,
+                                        ckpt_days, pred.ctypes.data_as(C.POINTER(C.c_double)),
+                                        jac.ctypes.data_as(C.POINTER(C.c_double)))
+        return rc, jac, pred
 
     def fov_check(self, fm, states, epochs, frames, observers, batch_span=3.0, twobody_max=1.5,
                   prefilter_deg=0.0, subset=None, n_threads=None, nongrav=None):

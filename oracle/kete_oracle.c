@@ -1469,3 +1469,76 @@ int ko_body_loss(const ko_ephem *e, const ko_force_model *fm, const double st0[6
     free(ep); free(bs); free(tref); free(stops);
     return status;
 }
+
+/* Per-observation sky partials of one body: jac[j][0][c] = d RA_j / d y0_c and
+ * jac[j][1][c] = d Dec_j / d y0_c, y0 = (x0, v0), for every observation j:
+ * the rows of the orbit-fit Jacobian (whose J^T J gives the covariance).  The
+ * forward model is ko_body_loss's; each row is the state-transition matrix
+ * from the variational equations at the observation's batch midpoint chained
+ * with central-difference partials of RA and Dec with respect to the state
+ * there (the same steps as ko_body_loss's gradient).  pred (may be NULL):
+ * [m][2] predicted RA, Dec. */
+int ko_body_sky_jacobian(const ko_ephem *e, const ko_force_model *fm, const double st0[6],
+                         double epoch0, const ko_obs *obs, int m, double batch_span,
+                         double twobody_max, double ckpt_days, double *pred, double *jac)
+{
+    for (int j = 1; j < m; j++)
+        if (obs[j].epoch < obs[j - 1].epoch) return -1;
+    double *ep = (double *)malloc(sizeof(double) * (m ? m : 1));
+    int64_t *bs = (int64_t *)malloc(sizeof(int64_t) * (m ? m : 1));
+    double *tref = (double *)malloc(sizeof(double) * (m ? m : 1));
+    for (int j = 0; j < m; j++) ep[j] = obs[j].epoch;
+    int64_t nb = ko_make_batches(ep, m, batch_span, twobody_max, bs, tref);
+    int cap = (int)nb + 4096;
+    double *stops = (double *)malloc(sizeof(double) * cap);
+    int ns = 0;
+    for (int64_t k = 0; k < nb; k++) stops[ns++] = tref[k];
+    if (nb > 0 && ckpt_days > 0)
+        for (int k = 1; epoch0 + k * ckpt_days < tref[nb - 1] && ns < cap; k++)
+            stops[ns++] = epoch0 + k * ckpt_days;
+    qsort(stops, ns, sizeof(double), cmp_dbl);
+    double y[6], phi[36], t = epoch0, dt = 0.0;
+    memcpy(y, st0, sizeof(y));
+    for (int r = 0; r < 36; r++) phi[r] = (r % 7 == 0) ? 1.0 : 0.0;
+    int status = KO_OK;
+    int64_t kb = 0;
+    for (int q = 0; q < ns && status == KO_OK; q++) {
+        status = ko_propagate_stm(e, fm, y, phi, &t, stops[q], &dt, NULL);
+        if (status != KO_OK) break;
+        if (kb < nb && stops[q] == tref[kb]) {
+            int64_t j0 = bs[kb], j1 = (kb + 1 < nb) ? bs[kb + 1] : m;
+            for (int64_t j = j0; j < j1 && status == KO_OK; j++) {
+                double res[2], ra, dec;
+                status = obs_residual(e, y, tref[kb], &obs[j], res, &ra, &dec);
+                if (status != KO_OK) break;
+                if (pred) { pred[2 * j] = ra; pred[2 * j + 1] = dec; }
+                /* d(RA, Dec) / d y(t_ref) by central differences (the steps of
+                 * ko_body_loss's observation partials) */
+                double dr[2][6];
+                for (int c = 0; c < 6; c++) {
+                    double h = 1e-7;
+                    double yp[6], ym[6], rp[2], rm[2], rap, decp, ram, decm;
+                    memcpy(yp, y, sizeof(yp));
+                    memcpy(ym, y, sizeof(ym));
+                    yp[c] += h;
+                    ym[c] -= h;
+                    status = obs_residual(e, yp, tref[kb], &obs[j], rp, &rap, &decp);
+                    if (status == KO_OK) status = obs_residual(e, ym, tref[kb], &obs[j], rm, &ram, &decm);
+                    if (status != KO_OK) break;
+                    dr[0][c] = wrap_pi(rap - ram) / (2.0 * h);
+                    dr[1][c] = (decp - decm) / (2.0 * h);
+                }
+                /* rows: d(RA, Dec)/d y(t_ref) Phi */
+                for (int a = 0; a < 2; a++)
+                    for (int c0 = 0; c0 < 6; c0++) {
+                        double acc = 0.0;
+                        for (int c = 0; c < 6; c++) acc += dr[a][c] * phi[c * 6 + c0];
+                        jac[(j * 2 + a) * 6 + c0] = acc;
+                    }
+            }
+            kb++;
+        }
+    }
+    free(ep); free(bs); free(tref); free(stops);
+    return status;
+}

@@ -205,6 +205,13 @@ int  ko_magnitude(const ko_ephem *e, const double st_ref[6], double t_ref, doubl
 int  ko_body_loss(const ko_ephem *e, const ko_force_model *fm, const double st0[6], double epoch0,
                   const ko_obs *obs, int m, double batch_span, double twobody_max,
                   double ckpt_days, double *loss, double *pred, double grad_var[6]);
+/* Per-observation sky partials: jac [m][2][6] = d(RA_j, Dec_j)/d(x0, v0) of
+ * the forward model of ko_body_loss (state-transition matrix at each batch
+ * midpoint chained with central-difference observation partials); pred (may
+ * be NULL) [m][2]. */
+int  ko_body_sky_jacobian(const ko_ephem *e, const ko_force_model *fm, const double st0[6],
+                          double epoch0, const ko_obs *obs, int m, double batch_span,
+                          double twobody_max, double ckpt_days, double *pred, double *jac);
 /* the state-transition matrix Phi (6x6, row-major, Phi[r*6+c] = dy_r/dy0_c)
  * propagated with the body along exactly the body's own step sequence */
 int  ko_propagate_stm(const ko_ephem *e, const ko_force_model *fm, double st[6], double phi[36],

@@ -118,3 +118,53 @@ def test_gradient_of_few_observations_matches_finite_differences(adj_small, i, k
         fd[c] = (4.0 * cd(c, h / 2) - cd(c, h)) / 3.0
     assert np.abs(g[:3] - fd[:3]).max() < 1e-7 * np.abs(g[:3]).max(), (g, fd)
     assert np.abs(g[3:] - fd[3:]).max() < 1e-7 * np.abs(g[3:]).max(), (g, fd)
+
+
+@pytest.mark.parametrize("i", [0, 19, 33])
+def test_sky_jacobian_matches_finite_differences_of_the_predictions(adj_small, i):
+    """The per-observation sky partials (rows of the orbit-fit Jacobian) equal
+    central differences of the whole forward model's RA/Dec predictions --
+    n-body chain, two-body, light time -- with respect to the initial state,
+    Richardson-extrapolated (error O(h^4))."""
+    w = adj_small
+    orc = O.Oracle(w.ephem.to_bytes())
+    fm = orc.force_model()
+    obs = w.meta["obs"][i].copy()
+    y = w.states[:, i] + w.meta["offsets"][:, i]
+    rc, jac, pred = orc.sky_jacobian(fm, y, W.T0, obs)
+    assert rc == 0 and jac.shape == (len(obs), 2, 6)
+    _, _, pred_loss, _ = orc.body_loss(fm, y, W.T0, obs, grad=False)
+    assert np.array_equal(pred, pred_loss)
+
+    def cd(c, h):
+        yp, ym = y.copy(), y.copy()
+        yp[c] += h; ym[c] -= h
+        _, _, pp, _ = orc.body_loss(fm, yp, W.T0, obs, grad=False)
+        _, _, pm, _ = orc.body_loss(fm, ym, W.T0, obs, grad=False)
+        d = pp - pm
+        d[:, 0] = (d[:, 0] + math.pi) % (2 * math.pi) - math.pi
+        return d / (2 * h)
+    fd = np.zeros_like(jac)
+    for c in range(6):
+        h = 1e-6 if c < 3 else 1e-8
+        fd[:, :, c] = (4.0 * cd(c, h / 2) - cd(c, h)) / 3.0
+    for part in (slice(0, 3), slice(3, 6)):
+        scale = np.abs(fd[:, :, part]).max()
+        assert np.abs(jac[:, :, part] - fd[:, :, part]).max() < 1e-6 * scale
+
+
+def test_sky_jacobian_gives_the_loss_gradient(adj_small):
+    """Chain rule: dL/dy0 = sum_j 2 (wrap(RA_j - RA_obs) cos^2 Dec_obs dRA_j/dy0
+    + (Dec_j - Dec_obs) dDec_j/dy0) equals the loss gradient."""
+    w = adj_small
+    orc = O.Oracle(w.ephem.to_bytes())
+    fm = orc.force_model()
+    obs = _observations(orc, fm, w, 7)
+    y = w.states[:, 7] + w.meta["offsets"][:, 7]
+    rc, _, _, g = orc.body_loss(fm, y, W.T0, obs)
+    rc2, jac, pred = orc.sky_jacobian(fm, y, W.T0, obs)
+    assert rc == rc2 == 0
+    cd2 = np.cos(obs["dec"]) ** 2
+    dra = (pred[:, 0] - obs["ra"] + math.pi) % (2 * math.pi) - math.pi
+    g2 = (2 * (dra * cd2)[:, None] * jac[:, 0, :] + 2 * (pred[:, 1] - obs["dec"])[:, None] * jac[:, 1, :]).sum(0)
+    assert np.abs(g2 - g).max() < 1e-9 * np.abs(g).max()

@@ -115,6 +115,10 @@ MUTANTS = [
      [ORA_N + "test_normal_force_tilts_the_plane_only"]),
     ("nongrav_barycentric", "double r[3] = {x[0] - ps[0], x[1] - ps[1], x[2] - ps[2]};",
      "double r[3] = {x[0], x[1], x[2]};", [ORA_N + "test_nongrav_terms_follow_the_sun"]),
+    # per-observation sky partials (the orbit-fit Jacobian)
+    ("sky_jacobian_transposed_stm", "for (int c = 0; c < 6; c++) acc += dr[a][c] * phi[c * 6 + c0];",
+     "for (int c = 0; c < 6; c++) acc += dr[a][c] * phi[c0 * 6 + c];",
+     ["tests/test_oracle_adjoint.py::test_sky_jacobian_matches_finite_differences_of_the_predictions"]),
     # magnitudes (Sec. 3.3)
     ("hg_phase_constant", "const double phi1 = exp(-3.33 * pow(t, 0.63));",
      "const double phi1 = exp(-3.33 * pow(t, 1.22));", [ORA_M + "test_hg_phase_function_exponents"]),
