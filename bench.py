@@ -401,15 +401,70 @@ def adjoint_leg(args, K, dev, flush, stream, peak):
     }
 
 
+def ztf_leg(args, K, dev, flush, stream, peak_fp64, hbm_gbs):
+    """The ZTF-like survey year: 757,000 bodies (2 % NEOs) against 150,000
+    night-time exposures of 8 x 8 sub-fields of 0.87 deg (9.6 M FoVs) seen
+    from a site on the rotating Earth.  The mixed-precision form (FP32
+    planetary terms) against the plain FP64 form on the same workload, each
+    with its FoV-stage rooflines and its sky accuracy against the oracle on a
+    bounded body sample."""
+    import torch
+    from paper_2509_04666_gb300 import kete, workloads as W
+    kw = {}
+    if args.ztf_bodies:
+        kw["n_bodies"] = args.ztf_bodies
+    if args.ztf_exposures:
+        kw["n_exposures"] = args.ztf_exposures
+    w = W.ztf1y(**kw)
+    n, nf = w.n_bodies, len(w.frames)
+    K.load_ephem(w.ephem.to_bytes())
+    st = torch.from_numpy(w.states.copy()).to(dev)
+    ep = torch.from_numpy(w.epochs.copy()).to(dev)
+    fr = kete.frames_to_device(w.frames, dev)
+    ob = torch.from_numpy(np.ascontiguousarray(w.observers)).to(dev)
+    out = {"workload": f"ztf1y: {n} bodies (2% NEOs) x {len(np.unique(w.frames['exposure_id']))} "
+                       f"exposures of 8x8 0.87 deg sub-fields ({nf} FoVs) from a rotating ground "
+                       f"site, 365 d"}
+    hits = {}
+    for name, prec in (("mixed", kete.MIXED), ("fp64", kete.FP64)):
+        fm = kete.force_model(precision=prec)
+        h, nh, _ = K.fov_check(st, ep, fr, ob, fm=fm)          # sizes the hit buffer
+        h = torch.empty((int(nh * 1.1) + 4096, 4), dtype=torch.int64, device=dev)
+        ms, (h, nh, status) = _timed(stream, lambda: K.fov_check(st, ep, fr, ob, fm=fm, hits=h),
+                                     flush, 2)
+        s = K.get_stats()
+        hits[name] = (h, nh)
+        f64, f32 = prop_flops(s, fm, w.ephem.n_coef, prec == kete.MIXED)
+        out[name] = {"value": n * 365.0 / (ms / 1e3), "unit": "body-days/s", "ms_per_step": ms,
+                     "fov_checks_per_s": n * nf / (ms / 1e3), "prop_ms": s["prop_ms"],
+                     "exact_ms": s["exact_ms"], "cand_ms": s["cand_ms"], "n_hits": int(nh),
+                     "candidates": s["n_candidates"], "batches": s["n_batches"],
+                     "bodies_ok": int((status == 0).sum().item()),
+                     "prop_fp64_tflops": f64 / (s["prop_ms"] / 1e3) / 1e12,
+                     "prop_fp32_tflops": f32 / (s["prop_ms"] / 1e3) / 1e12,
+                     "fov_stage": fov_stage_roofline([s], n, peak_fp64, hbm_gbs)}
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    if not args.no_cpu_baseline:
+        sub, ref, dt, nt = oracle_sample(w, args.ztf_sample)
+        for name in ("mixed", "fp64"):
+            out[name]["accuracy"] = compare_sample(kete, *hits[name], sub, ref)
+        out["cpu_baseline"] = {"value": len(sub) * 365.0 / dt, "unit": "body-days/s",
+                               "kind": "oracle", "cores": nt,
+                               "sample": f"{len(sub)} evenly spaced bodies x all {nf} FoVs, "
+                                         f"{dt:.1f} s"}
+    return out
+
+
 POPULATIONS = ((0, "main_belt"), (1, "neo"), (2, "trojan"), (3, "comet"), (4, "encounter"))
 
 
 def truncation_by_population(orc, w, sub, t_end, ref, ref_status):
-    """The method's own truncation error on the sample: the oracle at
-    eps / 100 against the oracle at the tuned eps (ref), max |dr| in AU per
+    """The method's own truncation error on the sample: the oracle with the
+    step control at eps / 100 and the corrector threshold at eps_pc / 100
+    against the oracle at the tuned controls (ref), max |dr| in AU per
     population, over the bodies both runs finish."""
-    tight, _, st, _ = orc.propagate_many(orc.force_model(eps=1e-11), w.states[:, sub],
-                                         w.epochs[sub], t_end)
+    tight, _, st, _ = orc.propagate_many(orc.force_model(eps=1e-11, eps_pc=1e-12),
+                                         w.states[:, sub], w.epochs[sub], t_end)
     ok = (st == 0) & (np.asarray(ref_status) == 0)
     d = np.linalg.norm(tight[:3] - ref[:3], axis=0)
     out = {}
@@ -461,6 +516,32 @@ def ragged_leg(args, K, dev, flush, stream):
         res[name] = (box["st"].cpu().numpy(), status.cpu().numpy())
         out[name] = {"value": n * 365.0 / (ms / 1e3), "unit": "body-days/s", "ms": ms,
                      "prop_ms": stt["prop_ms"], "steps": stt["steps"], "deferred": stt["deferred"]}
+    # the autotuner's pick per precision (kete_autotune on a body sample over
+    # the same year), timed on the whole population beside the hand variants
+    for name, prec in (("fp64_autotuned", kete.FP64), ("mixed_autotuned", kete.MIXED)):
+        fm = kete.force_model(precision=prec)
+        e0 = torch.full((n,), W.T0, dtype=torch.float64, device=dev)
+        pick = K.autotune(st0, e0, np.array([t_end]), fm=fm, max_sample=args.tune_sample)
+        box = {}
+
+        def call():
+            s = st0.clone(); e = torch.full((n,), W.T0, dtype=torch.float64, device=dev)
+            box["st"] = s
+            return K.propagate(s, e, t_end, fm=fm)
+        call()
+        ms, status = _timed(stream, call, flush, 2)
+        stt = K.get_stats()
+        out[name] = {"value": n * 365.0 / (ms / 1e3), "unit": "body-days/s", "ms": ms,
+                     "prop_ms": stt["prop_ms"], "steps": stt["steps"], "deferred": stt["deferred"],
+                     "variant": dict(zip(("kind", "block", "split_lanes", "defer_steps",
+                                          "cost_order"), pick))}
+    hand = {k: out[k]["ms"] for k in ("fp64", "fp64_static", "fp64_split8")}
+    out["autotune"] = {"fp64_pick_ms": out["fp64_autotuned"]["ms"],
+                       "fp64_best_hand_ms": min(hand.values()),
+                       "mixed_pick_ms": out["mixed_autotuned"]["ms"],
+                       "mixed_best_hand_ms": min(out["mixed"]["ms"], out["mixed_split8"]["ms"]),
+                       "sample": f"{min(n, args.tune_sample)} of {n} bodies on grids scaled by "
+                                 f"{min(n, args.tune_sample) / n:.3f}"}
     K.set_propagation(kete.FP64, kete.PROP_WORK_STEALING, 128)
     K.set_propagation(kete.MIXED, kete.PROP_WORK_STEALING, 128)
     out["mixed_speedup_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
@@ -574,6 +655,8 @@ def run_leg(args):
         out = adjoint_leg(args, K, dev, flush, stream, peak)
     elif args.leg == "longspan":
         out = longspan_leg(args, K, dev, flush, stream)
+    elif args.leg == "ztf":
+        out = ztf_leg(args, K, dev, flush, stream, peak, measured_hbm_gbs())
     else:
         out = ragged_leg(args, K, dev, flush, stream)
     print(json.dumps({"leg": args.leg, **out}))
@@ -752,7 +835,9 @@ def run_gb300(args):
                    "n_hits": int(nhg), "finite": int(np.isfinite(mags).sum()),
                    "median_mag": float(np.nanmedian(mags)) if np.isfinite(mags).any() else None,
                    "hit_list_unchanged": same}
-    adjoint = ragged = longspan = None
+    adjoint = ragged = longspan = ztf = None
+    if rank == 0 and world == 1 and not args.no_ztf:
+        ztf = ztf_leg(args, K, dev, flush, stream, peak_nominal, measured_hbm_gbs())
     if rank == 0 and world == 1 and args.longspan:
         longspan = longspan_leg(args, K, dev, flush, stream)
     if rank == 0 and world == 1 and not args.no_adjoint:
@@ -768,7 +853,6 @@ def run_gb300(args):
                    "batches": s0["n_batches"], "precision": args.precision,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "fov_checks_per_s": checks,
-        "fov_stage": fov_stage_roofline(stats, n, peak_nominal, measured_hbm_gbs()),
         "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": achieved,
                      "peak": peak_nominal, "unit": "TFLOP/s", "frac": achieved / peak_nominal,
                      "traffic": traffic, "peak_probe_measured": (peak_probe or 0) / 1e12,
@@ -778,11 +862,6 @@ def run_gb300(args):
                      "fp64_warp_inst_per_s": lane_probe},
         "cpu_baseline": cpu,
         "accuracy": accuracy,
-        "mixed_precision": mixed_leg,
-        "magnitudes": mag_leg,
-        "adjoint": adjoint,
-        "ragged": ragged,
-        "longspan": longspan,
         "e2e": e2e,
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "clocks": clocks,
@@ -791,6 +870,14 @@ def run_gb300(args):
                                         "n_candidates", "n_hits")},
         "phases_ms": {k: s0[k] for k in ("prop_ms", "prep_ms", "cand_ms", "exact_ms", "order_ms")},
         "wall_s_timed": t_wall,
+        "magnitudes": mag_leg,
+        "longspan": longspan,
+        "adjoint": adjoint,
+        "ragged": ragged,
+        # the survey comparisons last: mixed precision on both survey years
+        "ztf1y": ztf,
+        "mixed_precision": mixed_leg,
+        "fov_stage": fov_stage_roofline(stats, n, peak_nominal, measured_hbm_gbs()),
     }
     if rank == 0:
         print(json.dumps(out))
@@ -819,10 +906,15 @@ def main():
                     help="add the long-span leg (decades back; ~3 min) to the benchmark line")
     ap.add_argument("--back-bodies", type=int, default=20_000)
     ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--no-ztf", action="store_true", help="skip the ZTF-like survey year leg")
+    ap.add_argument("--ztf-sample", type=int, default=256)
+    ap.add_argument("--ztf-bodies", type=int, default=0, help="smaller ZTF-like case (profiling)")
+    ap.add_argument("--ztf-exposures", type=int, default=0)
     ap.add_argument("--adj-bodies", type=int, default=100_000)
     ap.add_argument("--adj-sample", type=int, default=512)
     ap.add_argument("--ragged-bodies", type=int, default=500_000)
-    ap.add_argument("--leg", default="all", choices=["all", "adjoint", "ragged", "longspan"],
+    ap.add_argument("--tune-sample", type=int, default=131072)
+    ap.add_argument("--leg", default="all", choices=["all", "adjoint", "ragged", "longspan", "ztf"],
                     help="run one leg alone (profiling); the default prints the benchmark line")
     args = ap.parse_args()
     if args.impl == "reference":

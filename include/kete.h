@@ -373,8 +373,10 @@ int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block, int 
 /* Autotuner: time every launch variant (static 128, work stealing 64 and 128,
  * each in index and in cost order; work stealing 128 in cost order with long
  * bodies set aside after 64 attempts per stop for 8 or 4 lanes each, or after
- * 24 for 8 lanes) on an evenly strided sample of up to `max_sample` of the n
- * bodies (device states [6][n] / epochs [n], not modified) propagated along
+ * 24 for 8 lanes) on an evenly spread sample of min(max_sample, n) of the n
+ * bodies (device states [6][n] / epochs [n], not modified), run on persistent
+ * grids scaled down by sample / n so that each lane works through as many
+ * bodies as in the whole run, propagated along
  * the chain of stops (host, ascending) with force model fm, keep the fastest
  * for fm's precision, and report it in *kind, *block, *split_lanes,
  * *defer_steps, *cost_order (host, each may be NULL).
@@ -422,6 +424,27 @@ int kete_adjoint(kete_ctx *ctx, const double *states, const double *epochs, int6
                  const kete_obs *obs, int32_t m, const kete_force_model *fm,
                  const kete_survey_opts *opt, double ckpt_days, double *loss, double *grad,
                  double *pred, int32_t *status);
+
+/* Per-observation sky partials of an orbit fit: the rows of its Jacobian,
+ * d(RA_j, Dec_j)/d(x0, v0) for every observation j of every body, whose
+ * J^T J (weighted by the observation errors) gives the covariance of the
+ * fitted initial state (the differentiation of the path of Sec. 2 / App. A,
+ * for orbit fitting and uncertainty).  The forward model, arguments, batching,
+ * checkpoint grid, FP64 and the status codes are kete_adjoint's; the observed
+ * ra/dec of obs are not used.  jac (device, [n][m][2][6]): jac[i][j][0][c] =
+ * d RA_ij / d y0_c and jac[i][j][1][c] = d Dec_ij / d y0_c, y0 = (x0, v0) of
+ * body i (rad per AU, rad per AU/day); rows of unused observation slots and
+ * of failed bodies (status not KETE_BODY_OK) are NaN.  Each row is the state-
+ * transition matrix at the observation's batch midpoint -- the variational
+ * equations dx'' = (da/dx) dx (Newtonian da/dx, as kete_adjoint) integrated
+ * forward over every stored step -- multiplied by the partials of the
+ * two-body, light-time and RA/Dec map there.  pred (device, [n][m][2], may be
+ * NULL): predicted RA, Dec.  Scratch: about 100 KB + 290 m bytes per body, in
+ * chunks within opt->mem_budget_gb.  Errors: as kete_adjoint. */
+int kete_sky_jacobian(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                      const kete_obs *obs, int32_t m, const kete_force_model *fm,
+                      const kete_survey_opts *opt, double ckpt_days, double *jac, double *pred,
+                      int32_t *status);
 
 /* Largest n kete_propagate_noalloc accepts. */
 #define KETE_NOALLOC_MAX_BODIES 65536

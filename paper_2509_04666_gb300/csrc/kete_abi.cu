@@ -33,7 +33,7 @@ enum Slot {
     S_KSTOP, S_DEFER_LIST, S_DEFER_CNT, S_ORDER, S_ORDER_KEY, S_ORDER_HIST, S_ORDER_OFF,
     S_ORDER_SCAN, S_ORDER_N, S_ADJ_TEND, S_LEG_OUT,
     S_EXT_START, S_EXT_EX, S_EXT_TMP, S_EXT_FIRST, S_EXT_SUB, S_EXT_PARENT, S_EXT_CNT,
-    S_EXT_OFF, S_EXT_CUR, S_EXT_GROUP, S_EXT_KEEP, S_EXT_KCNT, S_EXT_KOFF,
+    S_EXT_OFF, S_EXT_CUR, S_EXT_GROUP, S_EXT_KEEP, S_EXT_KCNT, S_EXT_KOFF, S_ADJ_PHI,
     S_NSLOTS
 };
 
@@ -462,9 +462,10 @@ static int cost_order(kete_ctx *ctx, const double *states, int64_t stride, const
 }
 
 // Launch the propagation kernel with the context's variant for F's precision.
+// out_aos: stop k of body i at out[(k stride + i) * 6 + c] (see k_propagate)
 static int propagate(kete_ctx *ctx, const ForceDev &F, ChainState cs, const double *stops_dev,
                      int n_stops, double *out, int64_t stride, bool keep_on_fail,
-                     const NodeTable *nt, int leg0)
+                     const NodeTable *nt, int leg0, bool out_aos = false)
 {
     PropVariant var = ctx->var[F.precision == KETE_MIXED ? 1 : 0];
     unsigned long long *next = nullptr;
@@ -491,7 +492,8 @@ static int propagate(kete_ctx *ctx, const ForceDev &F, ChainState cs, const doub
     ctx->stats.prop_budget = var.budget;
     ctx->stats.prop_order = var.order;
     CUDA_TRY(launch_propagate(ctx->E, F, cs, stops_dev, n_stops, out, stride, keep_on_fail,
-                              ctx->d_ctr, ctx->stream, nt, leg0, var, next, dp, order, order_n));
+                              ctx->d_ctr, ctx->stream, nt, leg0, var, next, dp, order, order_n,
+                              out_aos));
     if (dp) ctx->extra_launches += 1;   // the second phase
     return KETE_OK;
 }
@@ -918,7 +920,7 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
         const int32_t nek = e1 - e0;
         // propagation to the batch midpoints of this chunk
         prop_event(ctx, true);
-        r = propagate(ctx, F, cs, B.t_ref + k0, nk, stop_states, n, false, &nt, k0);
+        r = propagate(ctx, F, cs, B.t_ref + k0, nk, stop_states, n, false, &nt, k0, true);
         if (r != KETE_OK) return r;
         prop_event(ctx, false);
         launches++;
@@ -977,7 +979,8 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
             ExactArgs xa;
             xa.E = ctx->E; xa.X = X; xa.B = B; xa.frames = frames; xa.faux = faux;
             xa.stop_states = stop_states; xa.n = n; xa.k0 = k0; xa.e_begin = e0; xa.e_end = e1;
-            xa.exp_off = exp_off; xa.cand_body = cand_body; xa.exp_first = exp_first;
+            xa.exp_off = exp_off; xa.n_cand = (int64_t)ncand; xa.cand_body = cand_body;
+            xa.exp_first = exp_first;
             xa.hits = hit_tmp; xa.cap = hit_cap; xa.frame_cnt = frame_cnt; xa.status = cs.status;
             xa.ctr = ctx->d_ctr;
             xa.mag = mag;
@@ -1167,15 +1170,19 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
     F.nongrav = nullptr;   // the sample is gathered: body indices differ from the caller's
     CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
+    // The sample (spread evenly over the bodies) runs on persistent grids scaled
+    // down by m / n, so that each lane works through as many bodies as in the
+    // whole run: on the full grid a sample would leave a lane a few bodies and
+    // be dominated by its longest-lived ones, which favours the split variants.
     const int64_t m = std::min(n, max_sample);
-    const int64_t stride = n / m;
+    const double scale = (double)m / (double)n;
     double *sst, *sep, *out, *d_stops;
     GET(S_TUNE_ST, 6 * m, sst);
     GET(S_TUNE_EP, m, sep);
     GET(S_TUNE_OUT, (size_t)n_stops * 6 * m, out);
     GET(S_STOPS, n_stops, d_stops);
     CUDA_TRY(cudaMemcpyAsync(d_stops, stops, n_stops * sizeof(double), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(launch_gather_bodies(states, epochs, n, stride, m, sst, sep, st));
+    CUDA_TRY(launch_gather_bodies(states, epochs, n, m, sst, sep, st));
     // schedules x cost order, then the split variants (with cost order)
     PropVariant cands[9];
     const int kinds[3][2] = {{PROP_STATIC, 128}, {PROP_WORK_STEALING, 64}, {PROP_WORK_STEALING, 128}};
@@ -1196,10 +1203,11 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
     float best_ms = 1e30f;
     PropVariant best = saved;
     cudaEvent_t e0 = event_at(ctx, 0), e1 = event_at(ctx, 1);
+    for (int c = 0; c < n_cands; c++) cands[c].grid_scale = scale;
     for (int c = 0; c < n_cands; c++) {
         ctx->var[F.precision == KETE_MIXED ? 1 : 0] = cands[c];
-        float ms = 0.0f;
-        for (int rep = 0; rep < 2; rep++) {   // the first run warms up
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {   // the first run warms up; the best of the others
             ChainState cs;
             r = run_chain(ctx, F, sst, sep, m, cs);
             if (r != KETE_OK) return r;
@@ -1212,13 +1220,16 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
             if (r != KETE_OK) return r;
             CUDA_TRY(cudaEventRecord(e1, st));
             CUDA_TRY(cudaEventSynchronize(e1));
-            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            float t = 0.0f;
+            CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0) ms = std::min(ms, t);
         }
         if (ms < best_ms) {
             best_ms = ms;
             best = cands[c];
         }
     }
+    best.grid_scale = 1.0;
     ctx->var[F.precision == KETE_MIXED ? 1 : 0] = best;
     if (kind) *kind = best.kind;
     if (block) *block = best.block;
@@ -1228,15 +1239,19 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
     return KETE_OK;
 }
 
-extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
-                            const kete_obs *obs, int32_t m, const kete_force_model *fm,
-                            const kete_survey_opts *opt_in, double ckpt_days, double *loss,
-                            double *grad, double *pred, int32_t *status)
+// The orbit-fit path of kete_adjoint and kete_sky_jacobian: forward pass with
+// step records, then (jac) the state-transition matrix at every batch
+// midpoint, the observations (loss, predictions, partials), then (grad) the
+// backward pass.
+static int adjoint_impl(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                        const kete_obs *obs, int32_t m, const kete_force_model *fm,
+                        const kete_survey_opts *opt_in, double ckpt_days, double *loss,
+                        double *grad, double *pred, double *jac, int32_t *status)
 {
     if (!ctx) return KETE_ERR_BAD_ARG;
     if (!ctx->have_ephem) return fail(ctx, KETE_ERR_NO_EPHEM, "no ephemeris loaded");
     if (n < 0 || n > INT32_MAX || m < 1 || m > KETE_ADJ_MAX_OBS ||
-        (n > 0 && (!states || !epochs || !obs || !loss)) ||
+        (n > 0 && (!states || !epochs || !obs || (!loss && !jac))) ||
         !(ckpt_days == 0.0 || ckpt_days >= 1e-3) || !std::isfinite(ckpt_days))
         return fail(ctx, KETE_ERR_BAD_ARG,
                     "bad arguments (m must lie in 1..%d, ckpt_days 0 or >= 1e-3)", KETE_ADJ_MAX_OBS);
@@ -1272,12 +1287,14 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
         P.loss = loss;
         P.grad = grad;
         P.pred = pred;
+        P.jac = jac;
         P.status = status;
         P.ctr = ctx->d_ctr;
         // scratch per chunk of bodies within the memory budget
         const int cap = KETE_ADJ_MAX_STEPS;
         const size_t per_body = (size_t)cap * kAdjRec * sizeof(double) +
                                 (size_t)m * (sizeof(int32_t) + 12 * sizeof(double)) +
+                                (jac ? (size_t)m * 36 * sizeof(double) : 0) +
                                 3 * sizeof(int32_t);
         const double budget = (opt.mem_budget_gb > 0 ? opt.mem_budget_gb : 8.0) * 1073741824.0;
         int64_t chunk = (int64_t)(budget / (double)per_body);
@@ -1293,6 +1310,8 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
         GET(S_ADJ_YREF, (size_t)chunk * m * 6, B.yref);
         GET(S_ADJ_GJUMP, (size_t)chunk * m * 6, B.gjump);
         GET(S_ADJ_STATUS, chunk, B.status);
+        B.phi = nullptr;
+        if (jac) GET(S_ADJ_PHI, (size_t)chunk * m * 36, B.phi);
         unsigned long long *next = nullptr;
         GET(S_NEXTBODY, 1, next);
         int launches = 0;
@@ -1313,6 +1332,10 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
             }
             CUDA_TRY(launch_adjoint_forward(ctx->E, F, B, P, i0, nc, next, ctx->stream, order));
             prop_event(ctx, false);
+            if (jac) {
+                CUDA_TRY(launch_adjoint_stm(B, P, i0, nc, ctx->stream));
+                launches++;
+            }
             CUDA_TRY(launch_adjoint_observe(ctx->E, B, P, i0, nc, ctx->stream));
             launches += 2;
             if (grad) {
@@ -1328,4 +1351,24 @@ extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *e
     if (ctx->h_ctr->error_flags & (1 << 6))
         return fail(ctx, KETE_ERR_BAD_ARG, "observations of a body are not sorted by epoch");
     return KETE_OK;
+}
+
+extern "C" int kete_adjoint(kete_ctx *ctx, const double *states, const double *epochs, int64_t n,
+                            const kete_obs *obs, int32_t m, const kete_force_model *fm,
+                            const kete_survey_opts *opt, double ckpt_days, double *loss,
+                            double *grad, double *pred, int32_t *status)
+{
+    if (ctx && n > 0 && !loss) return fail(ctx, KETE_ERR_BAD_ARG, "loss is required");
+    return adjoint_impl(ctx, states, epochs, n, obs, m, fm, opt, ckpt_days, loss, grad, pred,
+                        nullptr, status);
+}
+
+extern "C" int kete_sky_jacobian(kete_ctx *ctx, const double *states, const double *epochs,
+                                 int64_t n, const kete_obs *obs, int32_t m,
+                                 const kete_force_model *fm, const kete_survey_opts *opt,
+                                 double ckpt_days, double *jac, double *pred, int32_t *status)
+{
+    if (ctx && n > 0 && !jac) return fail(ctx, KETE_ERR_BAD_ARG, "jac is required");
+    return adjoint_impl(ctx, states, epochs, n, obs, m, fm, opt, ckpt_days, nullptr, nullptr,
+                        pred, jac, status);
 }

@@ -23,8 +23,14 @@
 //                   step by collocation on the step's 9 sample epochs (its 8
 //                   nodes and its end); dL/dy(t_ref) is added at each batch
 //                   midpoint.  dL/dx0 = -mu'(t0), dL/dv0 = mu(t0).
-// The backward pass evaluates no force and reads no ephemeris: every Jacobian
-// it needs was recorded by the forward pass.
+//   k_adj_stm       (per-observation sky partials) one lane per body: the six
+//                   columns of the state-transition matrix obey dx'' = J(t) dx,
+//                   integrated forward over the recorded steps by the same
+//                   collocation; the matrix is kept at every batch midpoint and
+//                   k_adj_observe multiplies each observation's RA and Dec
+//                   partials by it.
+// The backward and state-transition passes evaluate no force and read no
+// ephemeris: every Jacobian they need was recorded by the forward pass.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -44,22 +50,23 @@ namespace kete {
 //   mu(sig_n)  = mu_0 + sig_n mu'_0 + sum_k W2[n][k] F_k
 //   mu'(sig_n) = mu'_0 + sum_k W1[n][k] F_k
 // where W1[n][k] = int_0^sig_n l_k(s) ds, W2[n][k] = int_0^sig_n (sig_n - s) l_k(s) ds.
+// The forward pass of the state-transition matrix uses the same weights for
+// the forward variable s = (t - t_start) / h on the samples (node 0, ..., node
+// 7, step end): W1f, W2f.
 struct AdjTables {
     double sig[9];
     double W1[9][9];
     double W2[9][9];
+    double sigf[9];
+    double W1f[9][9];
+    double W2f[9][9];
 };
 static __constant__ AdjTables g_adj;
 
-static void fill_adj_tables(AdjTables &T)
+// Lagrange-basis integrals on 9 sample points sg (see AdjTables)
+static void fill_colloc(const long double sg[9], double sig[9], double W1[9][9], double W2[9][9])
 {
-    RadauTables rt;
-    fill_radau_tables(rt);
-    long double sg[9];
-    sg[0] = 0.0L;
-    for (int n = 1; n <= 7; n++) sg[n] = 1.0L - (long double)rt.h[8 - n];
-    sg[8] = 1.0L;
-    for (int n = 0; n < 9; n++) T.sig[n] = (double)sg[n];
+    for (int n = 0; n < 9; n++) sig[n] = (double)sg[n];
     for (int k = 0; k < 9; k++) {
         // l_k(s) = prod_{j != k} (s - sg_j) / (sg_k - sg_j), power basis
         long double c[9] = {1.0L, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -79,10 +86,24 @@ static void fill_adj_tables(AdjTables &T)
                 w2 += c[p] * sp * sg[n] / ((p + 1) * (p + 2));
                 sp *= sg[n];
             }
-            T.W1[n][k] = (double)(w1 / den);
-            T.W2[n][k] = (double)(w2 / den);
+            W1[n][k] = (double)(w1 / den);
+            W2[n][k] = (double)(w2 / den);
         }
     }
+}
+
+static void fill_adj_tables(AdjTables &T)
+{
+    RadauTables rt;
+    fill_radau_tables(rt);
+    long double sg[9];
+    sg[0] = 0.0L;
+    for (int n = 1; n <= 7; n++) sg[n] = 1.0L - (long double)rt.h[8 - n];
+    sg[8] = 1.0L;
+    fill_colloc(sg, T.sig, T.W1, T.W2);
+    for (int n = 0; n <= 7; n++) sg[n] = (long double)rt.h[n];
+    sg[8] = 1.0L;
+    fill_colloc(sg, T.sigf, T.W1f, T.W2f);
 }
 
 cudaError_t upload_adjoint_tables(cudaStream_t st)
@@ -504,7 +525,7 @@ k_adj_observe(EphemDev E, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
     }
     double Lj = 0.0, gj[6] = {0, 0, 0, 0, 0, 0};
     double ra = __longlong_as_double(0x7ff8000000000000ll), dec = ra;
-    bool bad = false;
+    bool bad = false, jac_done = false;
     const bool mine = (lane < mi) && (st == KETE_BODY_OK || st == KETE_BODY_ADJ_CAP);
     if (mine) {
         const double *y = B.yref + ((size_t)i * P.m + kb) * 6;
@@ -547,30 +568,59 @@ k_adj_observe(EphemDev E, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
             const double cd = cos(ob.dec);
             const double r0 = wrap_pi(ra - ob.ra) * cd, r1 = dec - ob.dec;
             Lj = r0 * r0 + r1 * r1;
-            // dL_j/du: RA/Dec partials in the equatorial frame, rotated back
+            // partials of RA and Dec with respect to u: in the equatorial frame,
+            // dRA = (-Y, X, 0) / rxy^2, dDec = (-X Z, -Y Z, rxy^2) / (|u|^2 rxy),
+            // rotated back to the ecliptic
             const double X = u[0];
             const double Y = P.cos_eps * u[1] - P.sin_eps * u[2];
             const double Z = P.sin_eps * u[1] + P.cos_eps * u[2];
             const double rxy2 = X * X + Y * Y, rxy = sqrt(rxy2), uu = rxy2 + Z * Z;
-            const double ka = 2.0 * r0 * cd / rxy2;
-            const double kd = 2.0 * r1 / (uu * rxy);
-            const double gX = -ka * Y - kd * X * Z;
-            const double gY = ka * X - kd * Y * Z;
-            const double gZ = kd * rxy2;
-            double wv[3] = {gX, P.cos_eps * gY + P.sin_eps * gZ, -P.sin_eps * gY + P.cos_eps * gZ};
+            const double ia = 1.0 / rxy2, id = 1.0 / (uu * rxy);
+            const double aY = X * ia;
+            const double dY = -Y * Z * id, dZ = rxy2 * id;
+            double wa[3] = {-Y * ia, P.cos_eps * aY, -P.sin_eps * aY};
+            double wd[3] = {-X * Z * id, P.cos_eps * dY + P.sin_eps * dZ,
+                            -P.sin_eps * dY + P.cos_eps * dZ};
             // light time: u = P(t_obs - tau) - obs with tau = |u| / c, so
             // du = P_y dy - Pdot dtau, dtau = rho.P_y dy / (c + rho.Pdot)
             const double un = sqrt(uu);
             const double rh[3] = {u[0] / un, u[1] / un, u[2] / un};
             const double pd[3] = {vh[0] + svel[0], vh[1] + svel[1], vh[2] + svel[2]};
-            const double wp = wv[0] * pd[0] + wv[1] * pd[1] + wv[2] * pd[2];
             const double den = kC + (rh[0] * pd[0] + rh[1] * pd[1] + rh[2] * pd[2]);
+            const double pa = (wa[0] * pd[0] + wa[1] * pd[1] + wa[2] * pd[2]) / den;
+            const double pdd = (wd[0] * pd[0] + wd[1] * pd[1] + wd[2] * pd[2]) / den;
 #pragma unroll
-            for (int c = 0; c < 3; c++) wv[c] -= (wp / den) * rh[c];
+            for (int c = 0; c < 3; c++) {
+                wa[c] -= pa * rh[c];
+                wd[c] -= pdd * rh[c];
+            }
             double Jr[3][6];
             kepler_jacobian(mu, sqmu, hr, hv, dfin, chi, Jr);
+            double ga[6], gd[6];   // d RA / d y(t_ref), d Dec / d y(t_ref)
 #pragma unroll
-            for (int c = 0; c < 6; c++) gj[c] = wv[0] * Jr[0][c] + wv[1] * Jr[1][c] + wv[2] * Jr[2][c];
+            for (int c = 0; c < 6; c++) {
+                ga[c] = wa[0] * Jr[0][c] + wa[1] * Jr[1][c] + wa[2] * Jr[2][c];
+                gd[c] = wd[0] * Jr[0][c] + wd[1] * Jr[1][c] + wd[2] * Jr[2][c];
+                gj[c] = fma(2.0 * r0 * cd, ga[c], 2.0 * r1 * gd[c]);
+            }
+            if (P.jac && st == KETE_BODY_OK) {
+                // rows of the orbit-fit Jacobian: d(RA, Dec)/d y(t_ref) Phi
+                const double *phi = B.phi + ((size_t)i * P.m + kb) * 36;
+                double *jr = P.jac + (gi * P.m + lane) * 12;
+#pragma unroll
+                for (int c0 = 0; c0 < 6; c0++) {
+                    double sa = 0.0, sd = 0.0;
+#pragma unroll
+                    for (int c = 0; c < 6; c++) {
+                        const double p = phi[c * 6 + c0];
+                        sa = fma(ga[c], p, sa);
+                        sd = fma(gd[c], p, sd);
+                    }
+                    jr[c0] = sa;
+                    jr[6 + c0] = sd;
+                }
+                jac_done = true;
+            }
         }
         if (P.pred) {
             P.pred[(gi * P.m + lane) * 2] = ra;
@@ -580,7 +630,15 @@ k_adj_observe(EphemDev E, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
         P.pred[(gi * P.m + lane) * 2] = ra;
         P.pred[(gi * P.m + lane) * 2 + 1] = dec;
     }
+    if (P.jac && lane < P.m && !jac_done) {   // unused slot or failed body: NaN rows
+        double *jr = P.jac + (gi * P.m + lane) * 12;
+        for (int q = 0; q < 12; q++) jr[q] = __longlong_as_double(0x7ff8000000000000ll);
+    }
     const bool any_bad = __any_sync(0xffffffffu, bad);
+    if (P.jac && any_bad && lane < P.m) {   // a failed body has no Jacobian
+        double *jr = P.jac + (gi * P.m + lane) * 12;
+        for (int q = 0; q < 12; q++) jr[q] = __longlong_as_double(0x7ff8000000000000ll);
+    }
     sh[w][lane][0] = Lj;
 #pragma unroll
     for (int c = 0; c < 6; c++) sh[w][lane][1 + c] = gj[c];
@@ -591,7 +649,7 @@ k_adj_observe(EphemDev E, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
         for (int j = 0; j < mi; j++) L += sh[w][j][0];
         const bool ok = (st == KETE_BODY_OK || st == KETE_BODY_ADJ_CAP) && !any_bad;
         if (any_bad && st == KETE_BODY_OK) st = KETE_BODY_KEPLER_CAP;
-        P.loss[gi] = ok ? L : __longlong_as_double(0x7ff8000000000000ll);
+        if (P.loss) P.loss[gi] = ok ? L : __longlong_as_double(0x7ff8000000000000ll);
         B.status[i] = st;
         if (P.status) P.status[gi] = st;
     }
@@ -723,6 +781,101 @@ k_adj_backward(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
 }
 
 // ---------------------------------------------------------------------------
+// state-transition matrix at the batch midpoints
+// ---------------------------------------------------------------------------
+// sample k of a step in the forward order: J at node k (k <= 7), at the step
+// end (k = 8: the next record's node 0)
+__device__ __forceinline__ const double *jac_sample_fwd(const double *r, const double *r_next, int k)
+{
+    return k == 8 ? r_next + 2 : r + 2 + 6 * k;
+}
+
+// One lane per body: the six columns (dx, dv) of Phi obey dx'' = J(t) dx.  Over
+// a recorded step of size h, with s = (t - t_start) / h and F_k = h^2 J_k dx_k
+// at the samples s_k (node 0..7, end):
+//   dx(s_n) = dx_0 + s_n h dv_0 + sum_k W2f[n][k] F_k,
+//   dv(1)   = dv_0 + (1/h) sum_k W1f[8][k] F_k,
+// solved by Picard iteration (contraction ~ h^2 |J|, at most 12 sweeps).
+// Phi is stored at each batch midpoint when the chain reaches it.
+__global__ void __launch_bounds__(128)
+k_adj_stm(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const int st = B.status[i];
+    if (st != KETE_BODY_OK) return;   // the observation kernel writes NaN rows
+    const int count = B.n_rec[i];
+    const int nb = B.nbat[i];
+    const double *rec = B.rec + (size_t)i * B.cap * kAdjRec;
+    const int32_t *bidx = B.bidx + (size_t)i * P.m;
+    double *phi_out = B.phi + (size_t)i * P.m * 36;
+    for (int c0 = 0; c0 < 6; c0++) {
+        double dx[3] = {0, 0, 0}, dv[3] = {0, 0, 0};
+        if (c0 < 3) dx[c0] = 1.0;
+        else dv[c0 - 3] = 1.0;
+        int kb = 0;
+        for (int s = 0; s <= count - 1; s++) {
+            // batches whose midpoint the chain reached after s steps
+            while (kb < nb && bidx[kb] == s) {
+                double *ph = phi_out + (size_t)kb * 36;
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    ph[r * 6 + c0] = dx[r];
+                    ph[(3 + r) * 6 + c0] = dv[r];
+                }
+                kb++;
+            }
+            if (s == count - 1) break;
+            const double *r = rec + (size_t)s * kAdjRec;
+            const double *rn = r + kAdjRec;
+            const double h = __ldg(r + 1) - __ldg(r);
+            const double h2 = h * h;
+            double xk[9][3], Fk[9][3];
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) xk[k][c] = fma(g_adj.sigf[k] * h, dv[c], dx[c]);
+                jmul(jac_sample_fwd(r, rn, k), xk[k], Fk[k]);
+#pragma unroll
+                for (int c = 0; c < 3; c++) Fk[k][c] *= h2;
+            }
+            for (int it = 0; it < 12; it++) {
+                double delta = 0.0, size = 0.0;
+#pragma unroll
+                for (int k = 1; k < 9; k++) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        double acc = fma(g_adj.sigf[k] * h, dv[c], dx[c]);
+#pragma unroll
+                        for (int j = 0; j < 9; j++) acc = fma(g_adj.W2f[k][j], Fk[j][c], acc);
+                        if (k == 8) {
+                            delta = fmax(delta, fabs(acc - xk[8][c]));
+                            size = fmax(size, fabs(acc));
+                        }
+                        xk[k][c] = acc;
+                    }
+                }
+#pragma unroll
+                for (int k = 1; k < 9; k++) {
+                    jmul(jac_sample_fwd(r, rn, k), xk[k], Fk[k]);
+#pragma unroll
+                    for (int c = 0; c < 3; c++) Fk[k][c] *= h2;
+                }
+                if (delta <= 1e-16 * size) break;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < 9; j++) acc = fma(g_adj.W1f[8][j], Fk[j][c], acc);
+                dv[c] += acc / h;
+                dx[c] = xk[8][c];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
@@ -771,6 +924,13 @@ cudaError_t launch_adjoint_observe(const EphemDev &E, const AdjBuffers &B, const
                                    int64_t i0, int64_t nc, cudaStream_t st)
 {
     if (nc > 0) k_adj_observe<<<blocks_for(nc, 4), 128, 0, st>>>(E, B, P, i0, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_stm(const AdjBuffers &B, const AdjProblem &P, int64_t i0, int64_t nc,
+                               cudaStream_t st)
+{
+    if (nc > 0) k_adj_stm<<<blocks_for(nc, 128), 128, 0, st>>>(B, P, i0, nc);
     return cudaGetLastError();
 }
 

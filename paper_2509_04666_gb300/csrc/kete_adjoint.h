@@ -24,6 +24,7 @@ struct AdjProblem {
     double span, ckpt;
     double cos_eps, sin_eps;
     double *loss, *grad, *pred;
+    double *jac;       // [n][m][2][6] d(RA, Dec)/d(x0, v0) per observation, or null
     int32_t *status;
     DevCounters *ctr;
 };
@@ -37,6 +38,8 @@ struct AdjBuffers {
     int32_t *bidx;     // [nc][m] steps taken when batch k's midpoint was reached
     double *yref;      // [nc][m][6] state at batch k's midpoint
     double *gjump;     // [nc][m][6] dL/dy(t_ref) of batch k
+    double *phi;       // [nc][m][36] state-transition matrix at batch k's midpoint
+                       // (row-major, d y_r(t_ref) / d y0_c; only with P.jac)
     int32_t *status;   // [nc]
 };
 
@@ -54,5 +57,9 @@ cudaError_t launch_adjoint_observe(const EphemDev &E, const AdjBuffers &B, const
                                    int64_t i0, int64_t nc, cudaStream_t st);
 cudaError_t launch_adjoint_backward(const AdjBuffers &B, const AdjProblem &P, int64_t i0,
                                     int64_t nc, cudaStream_t st);
+// the state-transition matrix at every batch midpoint (B.phi), integrated
+// forward over the recorded steps
+cudaError_t launch_adjoint_stm(const AdjBuffers &B, const AdjProblem &P, int64_t i0, int64_t nc,
+                               cudaStream_t st);
 
 }  // namespace kete

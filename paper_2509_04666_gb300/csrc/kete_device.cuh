@@ -449,12 +449,25 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
     }
     double best = kEncounterAu * kEncounterAu;
     if (!row64 && !ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
-    double sun[6];
+    // the Sun: position in FP64 (the monopole); its velocity enters only the
+    // FP32 GR term, so per thread it comes from the FP32 series
+    double sun[3];
+    float sunv[3] = {0.f, 0.f, 0.f};
+    const bool sun_gr = F.gr_mask & 1u;
     if (row64) {
 #pragma unroll
-        for (int q = 0; q < 6; q++) sun[q] = __ldg(row64 + q);
+        for (int q = 0; q < 3; q++) sun[q] = __ldg(row64 + q);
+        if (sun_gr) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) sunv[q] = (float)__ldg(row64 + 3 + q);
+        }
     } else {
-        cheb_state64(E, 0, g.s, g.tau, sun);
+        cheb_state64(E, 0, g.s, g.tau, sun, false);
+        if (sun_gr) {
+            float s6[6];
+            cheb_state32(E, 0, g.s, (float)g.tau, s6, true);
+            sunv[0] = s6[3]; sunv[1] = s6[4]; sunv[2] = s6[5];
+        }
     }
     const double d[3] = {x[0] - sun[0], x[1] - sun[1], x[2] - sun[2]};
     const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
@@ -470,10 +483,10 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
         as[1] = f * d[1];
         as[2] = f * d[2];
         // the Sun's GR and J2 corrections, FP32 (relative size 1e-8, 1e-13)
-        const bool gr = F.gr_mask & 1u, j2 = F.j2_mask & 1u;
-        if (gr || j2) {
-            float w[3] = {vf[0] - (float)sun[3], vf[1] - (float)sun[4], vf[2] - (float)sun[5]};
-            mass_terms<float>(F.gm32[0], F.j2k32[0], F.pole32[0], false, gr, j2, df, w, af);
+        const bool j2 = F.j2_mask & 1u;
+        if (sun_gr || j2) {
+            float w[3] = {vf[0] - sunv[0], vf[1] - sunv[1], vf[2] - sunv[2]};
+            mass_terms<float>(F.gm32[0], F.j2k32[0], F.pole32[0], false, sun_gr, j2, df, w, af);
         }
     }
     const float sunf[3] = {(float)sun[0], (float)sun[1], (float)sun[2]};
@@ -616,6 +629,11 @@ __device__ __forceinline__ void stumpff(double z, double &C, double &S)
 
 // Heliocentric state (r0, v0) advanced by dt under mu.  chi is the universal
 // anomaly: in = initial guess (0 = none), out = solution (warm start).
+// Without a guess, chi starts from its Taylor series in dt (dchi/dt =
+// sqrt(mu)/|r|): sqrt(mu) [dt/r0 - rdot dt^2/(2 r0^2) + (2 rdot^2 - r0 rddot)
+// dt^3/(6 r0^3)], rdot = r0.v0/r0, rddot = (v0^2 - rdot^2)/r0 - mu/r0^2, while
+// sqrt(mu/r0^3) |dt| < 0.2 (a few ulps off for the FoV stage's day-long
+// intervals: Newton then needs two iterations); beyond that from dt/r0.
 // Newton's iteration on F(chi) = A chi^2 C + B chi^3 S + r0 chi - sqrt(mu) dt
 // has converged when its step falls below 1e-15 |chi| or below the rounding
 // of F itself (4 ulps of the sum of its terms' magnitudes, divided by F'):
@@ -633,7 +651,16 @@ __device__ __forceinline__ bool kepler_uv(double mu, double sqmu, const double r
     double A = rv / sqmu;
     double B = 1.0 - alpha * rn0;
     double target = sqmu * dt;
-    if (chi == 0.0) chi = target / rn0;
+    if (chi == 0.0) {
+        chi = target / rn0;
+        const double ri = 1.0 / rn0;
+        if (fabs(dt) * sqmu * ri * sqrt(ri) < 0.2) {
+            const double rd = rv * ri;
+            const double rdd = (vv - rd * rd) * ri - mu * ri * ri;
+            const double u = dt * ri;
+            chi *= fma(fma(2.0 * rd * rd - rn0 * rdd, u * (1.0 / 6.0), -0.5 * rd), u, 1.0);
+        }
+    }
     double C = 0.5, S = 1.0 / 6.0, z = 0.0;
     bool ok = false;
     for (int it = 0; it < 64; it++) {

@@ -360,7 +360,7 @@ struct CandCtx {
     ExpArrays X;
     BatchArrays B;
     CellGrid G;
-    const double *stop_states;   // [C][6][n]
+    const double *stop_states;   // [C][n][6]: body i's state at batch k0 + kl
     int64_t n;
     int32_t k0, nk;              // chunk batches [k0, k0+nk)
     const int64_t *cell_start;   // [nk * n_cells + 1]
@@ -409,10 +409,10 @@ __global__ void __launch_bounds__(256) k_candidates(CandCtx C)
     const int32_t kl = (int32_t)(idx / C.n);
     const int32_t i = (int32_t)(idx - (int64_t)kl * C.n);
     const int32_t k = C.k0 + kl;
-    const double *st = C.stop_states + (int64_t)kl * 6 * C.n;
-    const double p[3] = {st[i], st[C.n + i], st[2 * C.n + i]};
+    const double *st = C.stop_states + ((int64_t)kl * C.n + i) * 6;
+    const double p[3] = {st[0], st[1], st[2]};
     if (!isfinite(p[0])) return;
-    const double v[3] = {st[3 * C.n + i], st[4 * C.n + i], st[5 * C.n + i]};
+    const double v[3] = {st[3], st[4], st[5]};
     const double *O = C.B.O + 3 * k;
     const double *sun = C.B.sun + 6 * k;
     const float robs = (float)C.B.robs[k];
@@ -488,7 +488,7 @@ __global__ void k_cand_scatter(const uint2 *__restrict__ cand, unsigned long lon
 }
 
 // ---------------------------------------------------------------------------
-// exact test: one warp per exposure, lanes over its candidate bodies
+// exact test: one thread per candidate (exposure, body) pair
 // ---------------------------------------------------------------------------
 struct ExactCtx {
     EphemDev E;
@@ -500,6 +500,7 @@ struct ExactCtx {
     int64_t n;
     int32_t k0, e_begin, e_end;
     const int64_t *exp_off;      // chunk-relative
+    int64_t n_cand;              // candidates of the chunk (exp_off[e_end - e_begin])
     const int32_t *cand_body;
     const int32_t *exp_first;
     kete_hit *hits;
@@ -599,15 +600,24 @@ __device__ __forceinline__ void twobody_pos(const TwoBodyLT &T, const double *su
     }
 }
 
+// Candidates are grouped by exposure (CSR exp_off), so neighbouring threads
+// mostly share an exposure and its data; every lane has a candidate of its
+// own whatever the exposures' candidate counts.
 __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
 {
-    const int lane = threadIdx.x & 31;
     const int32_t nexp = C.e_end - C.e_begin;
-    const int32_t warp = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int32_t nwarps = (int32_t)(((int64_t)gridDim.x * blockDim.x) >> 5);
     const double mu = C.E.gm[0];
     const double sqmu = sqrt(mu);
-    for (int32_t el = warp; el < nexp; el += nwarps) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < C.n_cand; q += stride) {
+        // the exposure of candidate q: the last el with exp_off[el] <= q
+        int32_t lo = 0, hi = nexp - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(C.exp_off + mid) <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        const int32_t el = lo;
         const int32_t e = C.e_begin + el;
         const int32_t k = C.X.batch[e];
         const int32_t kl = k - C.k0;
@@ -618,14 +628,13 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
         const double sun_obs[6] = {C.X.sun[6 * e], C.X.sun[6 * e + 1], C.X.sun[6 * e + 2],
                                    C.X.sun[6 * e + 3], C.X.sun[6 * e + 4], C.X.sun[6 * e + 5]};
         const int32_t f0 = C.exp_first[e], f1 = C.exp_first[e + 1];
-        const int64_t c0 = C.exp_off[el], c1 = C.exp_off[el + 1];
-        const double *st = C.stop_states + (int64_t)kl * 6 * C.n;
-        for (int64_t q = c0 + lane; q < c1; q += 32) {
+        {
             const int32_t i = C.cand_body[q];
+            const double *st = C.stop_states + ((int64_t)kl * C.n + i) * 6;
             double hr[3], hv[3];
             for (int c = 0; c < 3; c++) {
-                hr[c] = st[c * C.n + i] - sun[c];
-                hv[c] = st[(3 + c) * C.n + i] - sun[3 + c];
+                hr[c] = st[c] - sun[c];
+                hv[c] = st[3 + c] - sun[3 + c];
             }
             // light delay (Sec. 2): tau0 = |r(t)-o|/c, three fixed iterations
             double chi = 0.0, pos[3];
@@ -650,51 +659,64 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
             }
             if (!ok) {
                 if (C.status) atomicCAS(&C.status[i], KETE_BODY_OK, KETE_BODY_KEPLER_CAP);
-                continue;
+                continue;   // next candidate of this thread
             }
             const double un = sqrt(dot3(u, u));
             const float uf[3] = {(float)(u[0] / un), (float)(u[1] / un), (float)(u[2] / un)};
             bool have_radec = false;
             double ra = 0.0, dec = 0.0;
-            for (int32_t f = f0; f < f1; f++) {
-                const float4 a = C.faux[f];
-                if (a.x * uf[0] + a.y * uf[1] + a.z * uf[2] < a.w) continue;
-                const kete_frame &fr = C.frames[f];
-                bool inside = true;
-                if (fr.n_edges == KETE_FRAME_CONE) {
-                    // angle(u, centre) < r  <=>  c.u > |c| |u| cos r
-                    const double *cv = fr.normals[0];
-                    const double cn = sqrt(dot3(cv, cv));
-                    inside = fma(cv[0], u[0], fma(cv[1], u[1], cv[2] * u[2])) >
-                             cos(fr.normals[1][0]) * cn * un;
+            // Sub-fields 64 at a time: first the FP32 cap tests of all of them
+            // into a mask, then the exact tests of this lane's passing ones
+            // only -- each pass of the second loop gives every lane a
+            // sub-field of its own, where a loop over the sub-fields would run
+            // the FP64 test whenever any lane of the warp passed a cap.
+            for (int32_t fb = f0; fb < f1; fb += 64) {
+                const int32_t nfb = min(64, f1 - fb);
+                unsigned long long pass = 0ull;
+                for (int32_t j = 0; j < nfb; j++) {
+                    const float4 a = __ldg(C.faux + fb + j);
+                    if (a.x * uf[0] + a.y * uf[1] + a.z * uf[2] >= a.w) pass |= 1ull << j;
                 }
-                for (int kq = 0; kq < fr.n_edges; kq++) {
-                    const double *nv = fr.normals[kq];
-                    if (!(fma(nv[0], u[0], fma(nv[1], u[1], nv[2] * u[2])) > 0.0)) inside = false;
-                }
-                if (!inside) continue;
-                if (!have_radec) {
-                    radec(u, C.cos_eps, C.sin_eps, ra, dec);
-                    have_radec = true;
-                }
-                unsigned long long slot = agg_append(&C.ctr->hits);
-                if (slot < C.cap) {
-                    kete_hit hh;
-                    hh.frame = f;
-                    hh.body = i;
-                    hh.mag = __int_as_float(0x7fc00000);
-                    if (C.mag) {
-                        // heliocentric position at emission: pos minus the Sun there
-                        const double ph[3] = {pos[0] - fma(-tau, sun_obs[3], sun_obs[0]),
-                                              pos[1] - fma(-tau, sun_obs[4], sun_obs[1]),
-                                              pos[2] - fma(-tau, sun_obs[5], sun_obs[2])};
-                        hh.mag = apparent_mag(C.mag[i], ph, u, un);
+                while (pass) {
+                    const int32_t f = fb + __ffsll((long long)pass) - 1;
+                    pass &= pass - 1ull;
+                    const kete_frame &fr = C.frames[f];
+                    bool inside = true;
+                    if (fr.n_edges == KETE_FRAME_CONE) {
+                        // angle(u, centre) < r  <=>  c.u > |c| |u| cos r
+                        const double *cv = fr.normals[0];
+                        const double cn = sqrt(dot3(cv, cv));
+                        inside = fma(cv[0], u[0], fma(cv[1], u[1], cv[2] * u[2])) >
+                                 cos(fr.normals[1][0]) * cn * un;
                     }
-                    hh.ra = ra;
-                    hh.dec = dec;
-                    C.hits[slot] = hh;
+                    for (int kq = 0; kq < fr.n_edges; kq++) {
+                        const double *nv = fr.normals[kq];
+                        if (!(fma(nv[0], u[0], fma(nv[1], u[1], nv[2] * u[2])) > 0.0)) inside = false;
+                    }
+                    if (!inside) continue;
+                    if (!have_radec) {
+                        radec(u, C.cos_eps, C.sin_eps, ra, dec);
+                        have_radec = true;
+                    }
+                    unsigned long long slot = agg_append(&C.ctr->hits);
+                    if (slot < C.cap) {
+                        kete_hit hh;
+                        hh.frame = f;
+                        hh.body = i;
+                        hh.mag = __int_as_float(0x7fc00000);
+                        if (C.mag) {
+                            // heliocentric position at emission: pos minus the Sun there
+                            const double ph[3] = {pos[0] - fma(-tau, sun_obs[3], sun_obs[0]),
+                                                  pos[1] - fma(-tau, sun_obs[4], sun_obs[1]),
+                                                  pos[2] - fma(-tau, sun_obs[5], sun_obs[2])};
+                            hh.mag = apparent_mag(C.mag[i], ph, u, un);
+                        }
+                        hh.ra = ra;
+                        hh.dec = dec;
+                        C.hits[slot] = hh;
+                    }
+                    atomicAdd(&C.frame_cnt[f], 1);
                 }
-                atomicAdd(&C.frame_cnt[f], 1);
             }
         }
     }
@@ -947,15 +969,15 @@ cudaError_t fov_exact(const ExactArgs &a, int n_sm, cudaStream_t st)
     ExactCtx C;
     C.E = a.E; C.X = a.X; C.B = a.B; C.frames = a.frames; C.faux = a.faux;
     C.stop_states = a.stop_states; C.n = a.n; C.k0 = a.k0; C.e_begin = a.e_begin;
-    C.e_end = a.e_end; C.exp_off = a.exp_off; C.cand_body = a.cand_body;
+    C.e_end = a.e_end; C.exp_off = a.exp_off; C.n_cand = a.n_cand; C.cand_body = a.cand_body;
     C.exp_first = a.exp_first; C.hits = a.hits; C.cap = a.cap; C.frame_cnt = a.frame_cnt;
     C.status = a.status; C.ctr = a.ctr; C.mag = a.mag;
     const double eps = 84381.448 / 3600.0 * (kPi / 180.0);
     C.cos_eps = cos(eps);
     C.sin_eps = sin(eps);
     int64_t nexp = a.e_end - a.e_begin;
-    if (nexp <= 0) return cudaSuccess;
-    int64_t blocks = (nexp * 32 + 127) / 128;
+    if (nexp <= 0 || a.n_cand <= 0) return cudaSuccess;
+    int64_t blocks = (a.n_cand + 127) / 128;
     int64_t cap_blocks = (int64_t)n_sm * 16;
     if (blocks > cap_blocks) blocks = cap_blocks;
     KLAUNCH(k_exact<<<(unsigned)blocks, 128, 0, st>>>(C));

@@ -43,7 +43,7 @@ struct CandArgs {
     ExpArrays X;
     BatchArrays B;
     CellGrid G;
-    const double *stop_states;
+    const double *stop_states;   // [nk][n][6] per-body records of the chunk's batches
     int64_t n;
     int32_t k0, nk;
     const int64_t *cell_start;
@@ -61,10 +61,11 @@ struct ExactArgs {
     BatchArrays B;
     const kete_frame *frames;
     const float4 *faux;
-    const double *stop_states;
+    const double *stop_states;   // [nk][n][6] per-body records of the chunk's batches
     int64_t n;
     int32_t k0, e_begin, e_end;
     const int64_t *exp_off;
+    int64_t n_cand;            // candidates of the chunk
     const int32_t *cand_body;
     const int32_t *exp_first;
     kete_hit *hits;

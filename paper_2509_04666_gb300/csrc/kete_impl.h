@@ -100,6 +100,8 @@ struct PropVariant {
     int split = 0;    // lanes per body for long bodies (4, 8, 16; 0 or 1: none)
     int budget = 0;   // step attempts per stop after which a body is set aside
     int order = 0;    // take bodies most expensive first (kete_order.cu)
+    double grid_scale = 1.0;   // persistent grids scaled by this (<= 1: a sample of the
+                               // bodies run with as many bodies per lane as the whole)
 };
 cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
                              const double *stops_dev, int n_stops, double *out,
@@ -108,10 +110,10 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
                              PropVariant var = PropVariant{PROP_STATIC, 128},
                              unsigned long long *next_body = nullptr,
                              PropDefer *defer = nullptr, const int32_t *order = nullptr,
-                             const unsigned long long *order_n = nullptr);
+                             const unsigned long long *order_n = nullptr, bool out_aos = false);
 int propagate_ws_blocks(int block, int mode);
-cudaError_t launch_gather_bodies(const double *st, const double *ep, int64_t n, int64_t stride,
-                                 int64_t m, double *dst, double *dep, cudaStream_t s);
+cudaError_t launch_gather_bodies(const double *st, const double *ep, int64_t n, int64_t m,
+                                 double *dst, double *dep, cudaStream_t s);
 cudaError_t launch_chain_finish(ChainState cs, double *states, double *epochs,
                                 int32_t *status, cudaStream_t st);
 // kete_noalloc.cu: propagation with the chain scratch in a fixed device array

@@ -11,6 +11,7 @@
 // max_steps step attempts per leg, after which the body gets a status code.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -25,15 +26,24 @@ void upload_radau_tables(cudaStream_t st) { upload_step_tables(st); }
 #endif
 
 // The propagation kernel.  Each group of G lanes (G = 1: one lane) owns one
-// body at a time and advances it one step attempt per loop iteration along its
-// chain of stops, writing the state at every stop to out[k][c][i] (stride
-// out_stride between rows) and the chain state back when it is done.  Stop k
-// of this launch is leg leg0 + k of the node table (if any).
+// body at a time and advances it along its chain of stops, writing the state
+// at every stop to out[k][c][i] (stride out_stride between rows; out_aos: to
+// out[k][i][c] with out_stride bodies per stop, one contiguous 48-byte record
+// per body and stop) and the chain state back when it is done.  Stop k of this launch is leg leg0 + k of the
+// node table (if any).
+// One pass of the loop is one corrector sweep (7 force evaluations) for every
+// group inside a step attempt; a group at a step boundary first evaluates the
+// acceleration there and starts its attempt, in the same pass.  A group whose
+// corrector converges after fewer sweeps than its warp-mates' does not wait
+// for them: it ends its step and joins the next pass with its next attempt.
+// (An FP64 warp-instruction costs the same whatever its active lanes, so
+// lanes idling through other lanes' extra sweeps are lost throughput.)
 //   refill = 0 (static): group j of the grid takes body j and then idles;
 //   refill = 1 (work stealing, persistent grid): a group whose body is done
 //   takes the next one from an atomic counter (warp-aggregated), so a body
 //   needing hundreds of steps no longer idles the rest of its warp.
-// Both schedules run the same instructions per body: results are identical.
+// Every body sees the same arithmetic in the same order whatever the
+// schedule and whatever its warp-mates do: results are identical.
 // Queue q: the bodies come from q.list (q.list_n of them, device) instead of
 // 0..n-1, resuming at their saved stops cs.kstop[i] if q.resume; with q.defer set, a
 // body that has made more than q.budget step attempts per stop reached is
@@ -44,8 +54,8 @@ void upload_radau_tables(cudaStream_t st) { upload_step_tables(st); }
 template <int MODE, int G, bool NG>
 __global__ void __launch_bounds__(128, KETE_PROP_MIN_BLOCKS)
 k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ stops,
-            int n_stops, double *__restrict__ out, int64_t out_stride, int keep_on_fail,
-            DevCounters *ctr, NodeTable nt, int use_nt, int leg0,
+            int n_stops, double *__restrict__ out, int64_t out_stride, int out_aos,
+            int keep_on_fail, DevCounters *ctr, NodeTable nt, int use_nt, int leg0,
             unsigned long long *__restrict__ next_body, int refill, PropQueue q)
 {
     const int64_t n = cs.n;
@@ -64,6 +74,8 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
     S.have_a0 = false;
     S.ng = nullptr;
     LegView L = leg_view(nullptr, 0);
+    Attempt A;
+    bool in_attempt = false;  // A holds a step attempt with sweeps to go
     bool first = true;
     for (;;) {
         // groups without a body take the next ones
@@ -99,6 +111,7 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
                     S.have_a0 = false;
                     S.ng = (NG && F.nongrav) ? F.nongrav + i : nullptr;
                     L = leg_view(use_nt ? &nt : nullptr, leg0 + k);
+                    in_attempt = false;
                     if (status == KETE_BODY_OK && k < n_stops) aim_step(F, t, stops[k], dt);
                 } else {
                     i = n;   // drained
@@ -109,7 +122,8 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
         const bool active = (i >= 0 && i < n);
         if (!__any_sync(FULL, active)) break;
         if (!active) continue;
-        if (k < n_stops && status == KETE_BODY_OK && t != stops[k]) {
+        // a group at a step boundary: set aside, or start its next attempt
+        if (!in_attempt && k < n_stops && status == KETE_BODY_OK && t != stops[k]) {
             if (q.defer && !S.have_a0 && body_attempts >= (long long)q.budget * (k + 1)) {
                 // set the body aside at this step boundary
                 if (writer) {
@@ -130,23 +144,38 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
             }
             body_attempts++;
             if (++attempts > F.max_steps) status = KETE_BODY_STEP_CAP;
-            else status = step_once<MODE, false, G>(E, F, L, x, v, t, dt, stops[k], S, cnt);
-            if (status == KETE_BODY_OK && t != stops[k]) continue;
+            else status = step_begin<MODE, false, G>(E, F, L, x, v, t, dt, stops[k], S, A, cnt);
+            in_attempt = (status == KETE_BODY_OK);
+        }
+        // one corrector sweep for every group inside an attempt
+        if (in_attempt) {
+            bool done = false;
+            status = attempt_sweep<MODE, false, G>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, A,
+                                                   done, cnt, nullptr, S.ng);
+            if (status != KETE_BODY_OK) {
+                in_attempt = false;
+            } else if (done) {
+                in_attempt = false;
+                status = step_end<MODE>(F, A, x, v, t, dt, S, cnt);
+            }
+            if (in_attempt || (status == KETE_BODY_OK && t != stops[k])) continue;
         }
         // the body is at stop k (or failed): record it and move on
         while (k < n_stops && (status != KETE_BODY_OK || t == stops[k])) {
-            double *o = out + (int64_t)k * 6 * out_stride;
+            // component c of this stop's record at o[c * cs_]
+            double *o = out_aos ? out + ((int64_t)k * out_stride + i) * 6
+                                : out + (int64_t)k * 6 * out_stride + i;
+            const int64_t cs_ = out_aos ? 1 : out_stride;
             if (writer) {
                 if (status == KETE_BODY_OK) {
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
-                        o[c * out_stride + i] = x[c];
-                        o[(3 + c) * out_stride + i] = v[c];
+                        o[c * cs_] = x[c];
+                        o[(3 + c) * cs_] = v[c];
                     }
                 } else if (!keep_on_fail) {
 #pragma unroll
-                    for (int c = 0; c < 6; c++)
-                        o[c * out_stride + i] = __longlong_as_double(0x7ff8000000000000ll);
+                    for (int c = 0; c < 6; c++) o[c * cs_] = __longlong_as_double(0x7ff8000000000000ll);
                 }
             }
             k++;
@@ -264,14 +293,15 @@ __global__ void k_ephem_eval(EphemDev E, const double *__restrict__ t, int64_t n
     }
 }
 
-// strided sample of bodies: dst[c][j] = src[c][j * stride] (autotuner)
+// evenly spread sample of m of the n bodies: dst[c][j] = src[c][floor(j n / m)]
+// (autotuner)
 __global__ void k_gather_bodies(const double *__restrict__ st, const double *__restrict__ ep,
-                                int64_t n, int64_t stride, int64_t m, double *__restrict__ dst,
+                                int64_t n, int64_t m, double *__restrict__ dst,
                                 double *__restrict__ dep)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
-    const int64_t i = j * stride;
+    const int64_t i = (j * n) / m;
     for (int c = 0; c < 6; c++) dst[c * m + j] = st[c * n + i];
     dep[j] = ep[i];
 }
@@ -319,29 +349,29 @@ int propagate_ws_blocks(int block, int mode)
 template <int MODE, int G>
 static void launch_k(int64_t grid, int block, cudaStream_t st, const EphemDev &E,
                      const ForceDev &F, ChainState cs, const double *stops, int n_stops,
-                     double *out, int64_t stride, int kof, DevCounters *ctr, NodeTable t, int unt,
-                     int leg0, unsigned long long *next, int refill, PropQueue q)
+                     double *out, int64_t stride, int aos, int kof, DevCounters *ctr, NodeTable t,
+                     int unt, int leg0, unsigned long long *next, int refill, PropQueue q)
 {
     if (F.nongrav)
         k_propagate<MODE, G, true><<<(unsigned)grid, block, 0, st>>>(
-            E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, refill, q);
+            E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
     else
         k_propagate<MODE, G, false><<<(unsigned)grid, block, 0, st>>>(
-            E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, refill, q);
+            E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
 }
 
 template <int MODE>
 static void launch_split(int G, int64_t grid, int block, cudaStream_t st, const EphemDev &E,
                          const ForceDev &F, ChainState cs, const double *stops, int n_stops,
-                         double *out, int64_t stride, int kof, DevCounters *ctr, NodeTable t,
-                         int unt, int leg0, unsigned long long *next, PropQueue q)
+                         double *out, int64_t stride, int aos, int kof, DevCounters *ctr,
+                         NodeTable t, int unt, int leg0, unsigned long long *next, PropQueue q)
 {
     if (G == 4)
-        launch_k<MODE, 4>(grid, block, st, E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, 1, q);
+        launch_k<MODE, 4>(grid, block, st, E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, 1, q);
     else if (G == 16)
-        launch_k<MODE, 16>(grid, block, st, E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, 1, q);
+        launch_k<MODE, 16>(grid, block, st, E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, 1, q);
     else
-        launch_k<MODE, 8>(grid, block, st, E, F, cs, stops, n_stops, out, stride, kof, ctr, t, unt, leg0, next, 1, q);
+        launch_k<MODE, 8>(grid, block, st, E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, 1, q);
 }
 
 cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs,
@@ -349,8 +379,10 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
                              int64_t out_stride, bool keep_on_fail, DevCounters *ctr,
                              cudaStream_t st, const NodeTable *nt, int leg0, PropVariant var,
                              unsigned long long *next_body, PropDefer *defer,
-                             const int32_t *order, const unsigned long long *order_n)
+                             const int32_t *order, const unsigned long long *order_n,
+                             bool out_aos)
 {
+    const int aos = out_aos ? 1 : 0;
     if (cs.n <= 0 || n_stops <= 0) return cudaGetLastError();
     NodeTable t{};
     if (nt) t = *nt;
@@ -364,6 +396,8 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
         if (e != cudaSuccess) return e;
         refill = 1;
         int64_t persistent = propagate_ws_blocks(block, F.precision);
+        if (var.grid_scale < 1.0)
+            persistent = std::max<int64_t>(1, (int64_t)(persistent * var.grid_scale + 0.5));
         if (grid > persistent) grid = persistent;
     }
     // phase 1: one lane per body; with a split variant, long bodies are set aside
@@ -381,9 +415,9 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
         q.budget = var.budget;
     }
     if (mixed)
-        launch_k<KETE_MIXED, 1>(grid, block, st, E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, next_body, refill, q);
+        launch_k<KETE_MIXED, 1>(grid, block, st, E, F, cs, stops_dev, n_stops, out, out_stride, aos, kof, ctr, t, unt, leg0, next_body, refill, q);
     else
-        launch_k<KETE_FP64, 1>(grid, block, st, E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, next_body, refill, q);
+        launch_k<KETE_FP64, 1>(grid, block, st, E, F, cs, stops_dev, n_stops, out, out_stride, aos, kof, ctr, t, unt, leg0, next_body, refill, q);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !split) return e;
     // phase 2: the set-aside bodies, var.split lanes each, persistent grid
@@ -396,18 +430,20 @@ cudaError_t launch_propagate(const EphemDev &E, const ForceDev &F, ChainState cs
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t grid2 = (int64_t)(sms > 0 ? sms : 152) * 2;
+    int64_t grid2 = (int64_t)(sms > 0 ? sms : 152) * 2;
+    if (var.grid_scale < 1.0)
+        grid2 = std::max<int64_t>(1, (int64_t)(grid2 * var.grid_scale + 0.5));
     if (mixed)
-        launch_split<KETE_MIXED>(var.split, grid2, 128, st, E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, defer->next, q2);
+        launch_split<KETE_MIXED>(var.split, grid2, 128, st, E, F, cs, stops_dev, n_stops, out, out_stride, aos, kof, ctr, t, unt, leg0, defer->next, q2);
     else
-        launch_split<KETE_FP64>(var.split, grid2, 128, st, E, F, cs, stops_dev, n_stops, out, out_stride, kof, ctr, t, unt, leg0, defer->next, q2);
+        launch_split<KETE_FP64>(var.split, grid2, 128, st, E, F, cs, stops_dev, n_stops, out, out_stride, aos, kof, ctr, t, unt, leg0, defer->next, q2);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_bodies(const double *st, const double *ep, int64_t n, int64_t stride,
-                                 int64_t m, double *dst, double *dep, cudaStream_t s)
+cudaError_t launch_gather_bodies(const double *st, const double *ep, int64_t n, int64_t m,
+                                 double *dst, double *dep, cudaStream_t s)
 {
-    if (m > 0) k_gather_bodies<<<grid_for(m, 256), 256, 0, s>>>(st, ep, n, stride, m, dst, dep);
+    if (m > 0) k_gather_bodies<<<grid_for(m, 256), 256, 0, s>>>(st, ep, n, m, dst, dep);
     return cudaGetLastError();
 }
 

@@ -111,113 +111,162 @@ __device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, doubl
     return st;
 }
 
-// One Gauss-Radau attempt of size h from (t, x0, v0) with a0 = a(t, x0, v0)
-// (as0: its FP64 part).  rows != null: the step spans the whole leg and the
-// planets come from the node rows (node n at rows.r64 + n * stride).
-// JAC: every node evaluation also stores da/dx at node n to jrec[6n..6n+5];
-// the last corrector iteration's values remain.
-template <int MODE, bool JAC = false, int G = 1>
-__device__ __forceinline__ int radau_attempt(const EphemDev &E, const ForceDev &F, double t,
-                                             const double x0[3], const double v0[3],
-                                             const double a0[3], const double as0[3],
-                                             uint32_t close, Encounter enc, double h,
-                                             LegRows rows, double x1[3], double v1[3],
-                                             double &err, Cnt &cnt, double *jrec = nullptr,
-                                             const kete_nongrav *ng = nullptr)
-{
+// Corrector state of one Gauss-Radau step attempt of size h (from t to
+// t_new) between corrector sweeps; one sweep is one corrector iteration over
+// the 7 substep nodes.  rows.r64 != null: the step spans the whole leg and
+// the planets come from the node rows (node n at rows.r64 + n * stride).
+struct Attempt {
     double b[7][3], g[7][3];
+    double gs7[3];          // mixed precision: b6 of the FP64 part, last sweep
+    double amax, pc_prev;   // max|a| at the last node and the last convergence measure
+    double h, t_new;
+    LegRows rows;
+    int it;                 // sweeps done
+};
+
+__device__ __forceinline__ void attempt_begin(Attempt &A, double h, double t_new, LegRows rows)
+{
 #pragma unroll
     for (int m = 0; m < 7; m++)
 #pragma unroll
-        for (int i = 0; i < 3; i++) b[m][i] = g[m][i] = 0.0;
-    double amax = 0.0, pc_prev = 0.0;
-    double gs7[3] = {0.0, 0.0, 0.0};   // b6 of the FP64 part (mixed precision)
-    for (int it = 1; it <= F.max_iter; it++) {
-        double b6o[3] = {b[6][0], b[6][1], b[6][2]};
-        double F7[3];
-        if (MODE == KETE_MIXED) {
-#pragma unroll
-            for (int i = 0; i < 3; i++) gs7[i] = g_rt.w7[0] * as0[i];
-        }
-#pragma unroll
-        for (int n = 1; n <= 7; n++) {
-            const double s = g_rt.h[n];
-            const double sh = s * h;
-            double xn[3], vn[3], dxn[3];
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                // x(s) = x0 + s h v0 + (s h)^2 [a0/2 + sum_k b_k s^(k+1) / ((k+2)(k+3))]
-                // v(s) = v0 + s h [a0 + sum_k b_k s^(k+1) / (k+2)]
-                // with the node's weights from the table (smallest terms first)
-                double px = b[6][i] * g_rt.wx[n][6];
-                double pv = b[6][i] * g_rt.wv[n][6];
-#pragma unroll
-                for (int k = 5; k >= 0; k--) {
-                    px = fma(b[k][i], g_rt.wx[n][k], px);
-                    pv = fma(b[k][i], g_rt.wv[n][k], pv);
-                }
-                px = fma(a0[i], 0.5, px);
-                pv = pv + a0[i];
-                dxn[i] = fma(sh * sh, px, sh * v0[i]);   // displacement since the step start
-                xn[i] = x0[i] + dxn[i];
-                vn[i] = fma(sh, pv, v0[i]);
-            }
-            double Fn[3], Fs[3];
-            const double *r64 = rows.r64 ? rows.r64 + n * rows.stride64 : nullptr;
-            const float *r32 = rows.r32 ? rows.r32 + n * rows.stride64 : nullptr;
-            int st = accel<MODE, JAC, G>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs, enc, dxn,
-                                         false, JAC ? jrec + 6 * n : nullptr, ng);
-            cnt.evals++;
-            if (r64) cnt.node_evals++;
-            if (st != KETE_BODY_OK) return st;
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                double gn = (Fn[i] - a0[i]) * g_rt.rinv[n][0];
-#pragma unroll
-                for (int k = 1; k < n; k++) gn = (gn - g[k - 1][i]) * g_rt.rinv[n][k];
-                double dg = gn - g[n - 1][i];
-                g[n - 1][i] = gn;
-#pragma unroll
-                for (int m = 0; m < n; m++) b[m][i] = fma(g_rt.c[n][m], dg, b[m][i]);
-                if (n == 7) F7[i] = Fn[i];
-                if (MODE == KETE_MIXED) gs7[i] = fma(g_rt.w7[n], Fs[i], gs7[i]);
-            }
-        }
-        cnt.iters++;
-        double db = 0.0;
-        amax = 0.0;
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            db = fmax(db, fabs(b[6][i] - b6o[i]));
-            amax = fmax(amax, fabs(F7[i]));
-        }
-        double pc = db / amax;
-        if (!isfinite(pc)) return KETE_BODY_NONFINITE;
-        if (pc < F.eps_pc) break;
-        if (it >= 3 && pc >= pc_prev) break;
-        pc_prev = pc;
-    }
-    // step-size error estimate: max|b6| / max|a|; in mixed precision b6 of the
-    // smooth FP64 part (FP32 rounding is not smooth and b6 would amplify it)
-    double bmax = (MODE == KETE_MIXED)
-                      ? fmax(fabs(gs7[0]), fmax(fabs(gs7[1]), fabs(gs7[2])))
-                      : fmax(fabs(b[6][0]), fmax(fabs(b[6][1]), fabs(b[6][2])));
-    err = bmax / amax;
+        for (int i = 0; i < 3; i++) A.b[m][i] = A.g[m][i] = 0.0;
+    A.gs7[0] = A.gs7[1] = A.gs7[2] = 0.0;
+    A.amax = 0.0;
+    A.pc_prev = 0.0;
+    A.h = h;
+    A.t_new = t_new;
+    A.rows = rows;
+    A.it = 0;
+}
+
+// The corrector update at node N (compile-time): Newton divided difference
+// g_{N-1} from the node's force and the earlier g, then the power-basis
+// coefficients b.
+template <int MODE, int N>
+__device__ __forceinline__ void node_update(Attempt &A, const double Fn[3], const double Fs[3],
+                                            const double a0[3], double F7[3])
+{
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        double px = fma(b[6][i], 1.0 / 72.0, b[5][i] * (1.0 / 56.0));
-        px = fma(b[4][i], 1.0 / 42.0, px);
-        px = fma(b[3][i], 1.0 / 30.0, px);
-        px = fma(b[2][i], 1.0 / 20.0, px);
-        px = fma(b[1][i], 1.0 / 12.0, px);
-        px = fma(b[0][i], 1.0 / 6.0, px);
+        double gn = (Fn[i] - a0[i]) * g_rt.rinv[N][0];
+#pragma unroll
+        for (int k = 1; k < N; k++) gn = (gn - A.g[k - 1][i]) * g_rt.rinv[N][k];
+        double dg = gn - A.g[N - 1][i];
+        A.g[N - 1][i] = gn;
+#pragma unroll
+        for (int m = 0; m < N; m++) A.b[m][i] = fma(g_rt.c[N][m], dg, A.b[m][i]);
+        if (N == 7) F7[i] = Fn[i];
+        if (MODE == KETE_MIXED) A.gs7[i] = fma(g_rt.w7[N], Fs[i], A.gs7[i]);
+    }
+}
+
+// One corrector sweep of the attempt from (t, x0, v0) with a0 = a(t, x0, v0)
+// (as0: its FP64 part).  Sets done when the corrector has converged
+// (max|db6|/max|a| < eps_pc), stopped improving (from the third sweep) or
+// reached max_iter sweeps.  JAC: every node evaluation also stores da/dx at
+// node n to jrec[6n..6n+5]; the last sweep's values remain.
+template <int MODE, bool JAC = false, int G = 1>
+__device__ __forceinline__ int attempt_sweep(const EphemDev &E, const ForceDev &F, double t,
+                                             const double x0[3], const double v0[3],
+                                             const double a0[3], const double as0[3],
+                                             uint32_t close, Encounter enc, Attempt &A, bool &done,
+                                             Cnt &cnt, double *jrec = nullptr,
+                                             const kete_nongrav *ng = nullptr)
+{
+    const double h = A.h;
+    double b6o[3] = {A.b[6][0], A.b[6][1], A.b[6][2]};
+    double F7[3];
+    if (MODE == KETE_MIXED) {
+#pragma unroll
+        for (int i = 0; i < 3; i++) A.gs7[i] = g_rt.w7[0] * as0[i];
+    }
+    // one copy of the force evaluation: the node index is the same for every
+    // lane of the sweep (uniform table reads, uniform guards below)
+#pragma unroll 1
+    for (int n = 1; n <= 7; n++) {
+        const double s = g_rt.h[n];
+        const double sh = s * h;
+        double xn[3], vn[3], dxn[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            // x(s) = x0 + s h v0 + (s h)^2 [a0/2 + sum_k b_k s^(k+1) / ((k+2)(k+3))]
+            // v(s) = v0 + s h [a0 + sum_k b_k s^(k+1) / (k+2)]
+            // with the node's weights from the table (smallest terms first)
+            double px = A.b[6][i] * g_rt.wx[n][6];
+            double pv = A.b[6][i] * g_rt.wv[n][6];
+#pragma unroll
+            for (int k = 5; k >= 0; k--) {
+                px = fma(A.b[k][i], g_rt.wx[n][k], px);
+                pv = fma(A.b[k][i], g_rt.wv[n][k], pv);
+            }
+            px = fma(a0[i], 0.5, px);
+            pv = pv + a0[i];
+            dxn[i] = fma(sh * sh, px, sh * v0[i]);   // displacement since the step start
+            xn[i] = x0[i] + dxn[i];
+            vn[i] = fma(sh, pv, v0[i]);
+        }
+        double Fn[3], Fs[3];
+        const double *r64 = A.rows.r64 ? A.rows.r64 + n * A.rows.stride64 : nullptr;
+        const float *r32 = A.rows.r32 ? A.rows.r32 + n * A.rows.stride64 : nullptr;
+        int st = accel<MODE, JAC, G>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs, enc, dxn,
+                                     false, JAC ? jrec + 6 * n : nullptr, ng);
+        cnt.evals++;
+        if (r64) cnt.node_evals++;
+        if (st != KETE_BODY_OK) return st;
+        switch (n) {
+        case 1: node_update<MODE, 1>(A, Fn, Fs, a0, F7); break;
+        case 2: node_update<MODE, 2>(A, Fn, Fs, a0, F7); break;
+        case 3: node_update<MODE, 3>(A, Fn, Fs, a0, F7); break;
+        case 4: node_update<MODE, 4>(A, Fn, Fs, a0, F7); break;
+        case 5: node_update<MODE, 5>(A, Fn, Fs, a0, F7); break;
+        case 6: node_update<MODE, 6>(A, Fn, Fs, a0, F7); break;
+        default: node_update<MODE, 7>(A, Fn, Fs, a0, F7); break;
+        }
+    }
+    cnt.iters++;
+    A.it++;
+    double db = 0.0, amax = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        db = fmax(db, fabs(A.b[6][i] - b6o[i]));
+        amax = fmax(amax, fabs(F7[i]));
+    }
+    A.amax = amax;
+    const double pc = db / amax;
+    if (!isfinite(pc)) return KETE_BODY_NONFINITE;
+    done = (pc < F.eps_pc) || (A.it >= 3 && pc >= A.pc_prev) || (A.it >= F.max_iter);
+    A.pc_prev = pc;
+    return KETE_BODY_OK;
+}
+
+// The attempt's end state and its IAS15 error estimate max|b6| / max|a| (in
+// mixed precision b6 of the smooth FP64 part: FP32 rounding is not smooth and
+// b6 would amplify it).
+template <int MODE>
+__device__ __forceinline__ int attempt_end(const Attempt &A, const double x0[3], const double v0[3],
+                                           const double a0[3], double x1[3], double v1[3],
+                                           double &err)
+{
+    const double h = A.h;
+    double bmax = (MODE == KETE_MIXED)
+                      ? fmax(fabs(A.gs7[0]), fmax(fabs(A.gs7[1]), fabs(A.gs7[2])))
+                      : fmax(fabs(A.b[6][0]), fmax(fabs(A.b[6][1]), fabs(A.b[6][2])));
+    err = bmax / A.amax;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        double px = fma(A.b[6][i], 1.0 / 72.0, A.b[5][i] * (1.0 / 56.0));
+        px = fma(A.b[4][i], 1.0 / 42.0, px);
+        px = fma(A.b[3][i], 1.0 / 30.0, px);
+        px = fma(A.b[2][i], 1.0 / 20.0, px);
+        px = fma(A.b[1][i], 1.0 / 12.0, px);
+        px = fma(A.b[0][i], 1.0 / 6.0, px);
         px = fma(a0[i], 0.5, px);
-        double pv = fma(b[6][i], 0.125, b[5][i] * (1.0 / 7.0));
-        pv = fma(b[4][i], 1.0 / 6.0, pv);
-        pv = fma(b[3][i], 0.2, pv);
-        pv = fma(b[2][i], 0.25, pv);
-        pv = fma(b[1][i], 1.0 / 3.0, pv);
-        pv = fma(b[0][i], 0.5, pv);
+        double pv = fma(A.b[6][i], 0.125, A.b[5][i] * (1.0 / 7.0));
+        pv = fma(A.b[4][i], 1.0 / 6.0, pv);
+        pv = fma(A.b[3][i], 0.2, pv);
+        pv = fma(A.b[2][i], 0.25, pv);
+        pv = fma(A.b[1][i], 1.0 / 3.0, pv);
+        pv = fma(A.b[0][i], 0.5, pv);
         pv = pv + a0[i];
         x1[i] = fma(h * h, px, fma(h, v0[i], x0[i]));
         v1[i] = fma(h, pv, v0[i]);
@@ -265,16 +314,15 @@ __device__ __forceinline__ LegView leg_view(const NodeTable *nt, int kg)
     return L;
 }
 
-// One step attempt of (x, v, t) toward `target` (t != target).  Accepted: the
-// state advances and dt holds the next proposal.  Rejected: dt shrinks and a0
-// is kept.  Returns a KETE_BODY_* status.
-// JAC: da/dx at the 8 nodes of the attempt go to jrec[6n..6n+5] (see
-// radau_attempt); after an accepted step they describe that step.
+// Start a step attempt of (x, v, t) toward `target` (t != target): the
+// acceleration at the step start if it is not known yet (kept across a
+// rejection), the step size and its node rows, the corrector state A.
+// Returns a KETE_BODY_* status.  JAC: as attempt_sweep (jrec[0..5] at t).
 template <int MODE, bool JAC = false, int G = 1>
-__device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, const LegView &L,
-                                         double x[3], double v[3], double &t, double &dt,
-                                         double target, StepState &S, Cnt &cnt,
-                                         double *jrec = nullptr)
+__device__ __forceinline__ int step_begin(const EphemDev &E, const ForceDev &F, const LegView &L,
+                                          const double x[3], const double v[3], double t,
+                                          double dt, double target, StepState &S, Attempt &A,
+                                          Cnt &cnt, double *jrec = nullptr)
 {
     // rows of node 0 serve a0 whenever the step starts at the leg start
     const bool at_start = L.r64 && (t == L.t0) && isfinite(L.h);
@@ -307,10 +355,21 @@ __device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, c
         rows.r64 = L.r64;
         rows.r32 = L.r32;
     }
+    attempt_begin(A, h, t_new, rows);
+    return KETE_BODY_OK;
+}
+
+// End a step attempt whose corrector is done: IAS15 step control.  Accepted:
+// the state advances and dt holds the next proposal.  Rejected: dt shrinks and
+// a0 is kept.  Returns a KETE_BODY_* status.
+template <int MODE>
+__device__ __forceinline__ int step_end(const ForceDev &F, const Attempt &A, double x[3],
+                                        double v[3], double &t, double &dt, StepState &S, Cnt &cnt)
+{
     double x1[3], v1[3], err;
-    int st = radau_attempt<MODE, JAC, G>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, h, rows,
-                                         x1, v1, err, cnt, jrec, S.ng);
+    int st = attempt_end<MODE>(A, x, v, S.a0, x1, v1, err);
     if (st != KETE_BODY_OK) return st;
+    const double h = A.h;
     double dt_new;
     if (isfinite(err) && err >= 2.2250738585072014e-308)
         dt_new = pow(F.eps / err, 1.0 / 7.0) * h;
@@ -328,10 +387,33 @@ __device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, c
         x[i] = x1[i];
         v[i] = v1[i];
     }
-    t = t_new;
+    t = A.t_new;
     S.have_a0 = false;
     cnt.steps++;
     return KETE_BODY_OK;
+}
+
+// One whole step attempt of (x, v, t) toward `target` (t != target):
+// step_begin, corrector sweeps until done, step_end.
+// JAC: da/dx at the 8 nodes of the attempt go to jrec[6n..6n+5]; after an
+// accepted step they describe that step.
+template <int MODE, bool JAC = false, int G = 1>
+__device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, const LegView &L,
+                                         double x[3], double v[3], double &t, double &dt,
+                                         double target, StepState &S, Cnt &cnt,
+                                         double *jrec = nullptr)
+{
+    Attempt A;
+    int st = step_begin<MODE, JAC, G>(E, F, L, x, v, t, dt, target, S, A, cnt, jrec);
+    if (st != KETE_BODY_OK) return st;
+    for (;;) {
+        bool done = false;
+        st = attempt_sweep<MODE, JAC, G>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, A, done, cnt,
+                                         jrec, S.ng);
+        if (st != KETE_BODY_OK) return st;
+        if (done) break;
+    }
+    return step_end<MODE>(F, A, x, v, t, dt, S, cnt);
 }
 
 // orient the carried step toward the next stop (|dt| kept; dt_init to start)

@@ -30,7 +30,7 @@ EXPORTS = ["kete_create", "kete_destroy", "kete_set_stream", "kete_last_error",
            "kete_ephem_eval", "kete_propagate", "kete_propagate_stops", "kete_fov_check",
            "kete_get_stats", "kete_propagate_noalloc", "kete_set_propagation", "kete_autotune",
            "kete_adjoint", "kete_fov_check_mag", "kete_propagate_legs",
-           "kete_fov_check_extended"]
+           "kete_fov_check_extended", "kete_sky_jacobian"]
 EXT_MAX_SUB = 64
 MAG_NONE, MAG_HG, MAG_COMET_TOTAL, MAG_COMET_NUCLEUS = 0, 1, 2, 3
 
@@ -113,6 +113,8 @@ def lib():
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.kete_adjoint.argtypes = [vp, vp, vp, i64, vp, C.c_int32, C.POINTER(ForceModel),
                                    C.POINTER(SurveyOpts), dbl, vp, vp, vp, vp]
+        L.kete_sky_jacobian.argtypes = [vp, vp, vp, i64, vp, C.c_int32, C.POINTER(ForceModel),
+                                        C.POINTER(SurveyOpts), dbl, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -467,6 +469,32 @@ class Kete:
                                        pr.data_ptr() if pr is not None else None,
                                        status.data_ptr()))
         return loss, g, pr, status
+
+    def sky_jacobian(self, states, epochs, obs, fm=None, opts=None, ckpt_days=8.0, pred=False):
+        """Per-observation sky partials (kete_sky_jacobian): jac [n, m, 2, 6] =
+        d(RA, Dec)/d(x0, v0) of every observation, obs as for adjoint (its
+        observed RA/Dec are not used).  Returns (jac, pred [n, m, 2] or None,
+        status [n])."""
+        n = epochs.numel()
+        _dev_f64(states, "states", (6, n)); _dev_f64(epochs, "epochs", (n,))
+        if obs.dim() != 3 or obs.shape[0] != n or obs.shape[2] != 6:
+            raise ValueError("obs must have shape [n, m, 6]")
+        m = obs.shape[1]
+        _dev_f64(obs, "obs")
+        dev = states.device
+        jac = torch.empty((n, m, 2, 6), dtype=torch.float64, device=dev)
+        pr = torch.empty((n, m, 2), dtype=torch.float64, device=dev) if pred else None
+        status = torch.zeros(n, dtype=torch.int32, device=dev)
+        fm = fm or force_model()
+        _check_nongrav(fm, n)
+        opts = opts or survey_opts()
+        self._sync_stream()
+        self._check(lib().kete_sky_jacobian(self._h, states.data_ptr(), epochs.data_ptr(), n,
+                                            obs.data_ptr(), m, C.byref(fm), C.byref(opts),
+                                            float(ckpt_days), jac.data_ptr(),
+                                            pr.data_ptr() if pr is not None else None,
+                                            status.data_ptr()))
+        return jac, pr, status
 
     def set_propagation(self, precision: int, kind: int, block: int = 128, split: int = 0,
                         defer_steps: int = 0, cost_order: bool = True):
