@@ -43,12 +43,24 @@ MAS = math.radians(1.0 / 3.6e6)
 PROFILED_TRAFFIC = {"src_sha": "cfb11c9322fcded9", "bytes_per_body_stop": 183.2}
 
 
-def kernel_source_sha():
+# FP64 work of the exact FoV test per candidate as ncu counts it (2 x DFMA +
+# DMUL + DADD thread instructions over the timed launch of the same small case,
+# divided by its candidates); valid only while the FoV kernels' source is
+# unchanged.  The modelled count below leaves out the divisions, square roots
+# and convergence tests that the executed count includes.
+PROFILED_EXACT = {"src_sha": None, "fp64_flops_per_candidate": None}
+
+
+def kernel_source_sha(files=("kete_prop.cu", "kete_device.cuh", "kete_step.cuh", "kete_order.cu")):
     h = hashlib.sha256()
-    for f in ("kete_prop.cu", "kete_device.cuh", "kete_step.cuh", "kete_order.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2509_04666_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def fov_source_sha():
+    return kernel_source_sha(("kete_fov.cu", "kete_device.cuh"))
 
 
 def _bits(m):
@@ -204,19 +216,24 @@ EXACT_FLOPS_PER_CANDIDATE = 25 + 4 * 55 + 70 + 30 + 5 * 33 + 20
 
 def fov_stage_roofline(stats, n_bodies, peak_fp64_tflops, hbm_gbs):
     """Rooflines of the FoV stage's two kernels from the call's counters:
-    k_exact against the FP64 peak (EXACT_FLOPS_PER_CANDIDATE per candidate),
-    the candidate search against HBM (per body and batch the 48-B stop state
-    read, per candidate 8 B written and read back)."""
+    k_exact against the FP64 peak (its FP64 work per candidate as ncu counts
+    it while the kernel source matches the profile, else the model
+    EXACT_FLOPS_PER_CANDIDATE), the candidate search against HBM (per body
+    and batch the 48-B stop state read, per candidate 8 B written and read
+    back)."""
     cand = statistics.mean(s["n_candidates"] for s in stats)
     batches = stats[-1]["n_batches"]
     exact_ms = statistics.mean(s["exact_ms"] for s in stats)
     cand_ms = statistics.mean(s["cand_ms"] for s in stats)
-    ex = EXACT_FLOPS_PER_CANDIDATE * cand / (exact_ms / 1e3) / 1e12
+    per, basis = EXACT_FLOPS_PER_CANDIDATE, "model"
+    if PROFILED_EXACT["src_sha"] == fov_source_sha() and PROFILED_EXACT["fp64_flops_per_candidate"]:
+        per, basis = PROFILED_EXACT["fp64_flops_per_candidate"], "ncu-counted"
+    ex = per * cand / (exact_ms / 1e3) / 1e12
     cbytes = n_bodies * batches * 48.0 + cand * 16.0
     cgbs = cbytes / (cand_ms / 1e3) / 1e9
     return {"exact": {"bound": "alu", "achieved": ex, "peak": peak_fp64_tflops, "unit": "TFLOP/s",
                       "frac": ex / peak_fp64_tflops, "candidates": cand, "ms": exact_ms,
-                      "flops_per_candidate": EXACT_FLOPS_PER_CANDIDATE},
+                      "flops_per_candidate": per, "flops_basis": basis},
             "candidates": {"bound": "hbm", "achieved": cgbs, "peak": hbm_gbs, "unit": "GB/s",
                            "frac": cgbs / hbm_gbs if hbm_gbs else None,
                            "bytes": cbytes, "ms": cand_ms}}

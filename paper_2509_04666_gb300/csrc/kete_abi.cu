@@ -24,7 +24,7 @@ namespace {
 
 enum Slot {
     S_CHAIN, S_STATUS, S_STOPS, S_STOPSTATES, S_ISSTART, S_EX, S_SCANTMP, S_FCEN, S_FAUX,
-    S_EXPFIRST, S_XEPOCH, S_XOBS, S_XCEN, S_XRAD, S_XCS, S_XBATCH, S_NEXT, S_BFIRST, S_BTREF,
+    S_EXPFIRST, S_XEPOCH, S_XOBS, S_XCEN, S_XCENF, S_XRAD, S_XCS, S_XBATCH, S_NEXT, S_BFIRST, S_BTREF,
     S_BO, S_BROBS, S_BTSPAN, S_BRMAX, S_BSUN, S_NBATCH, S_BANDS, S_CELLKEY, S_CELLCNT,
     S_CELLSTART, S_CELLCUR, S_CELLEXP, S_CAND, S_EXPCNT, S_EXPOFF, S_EXPCUR, S_CANDBODY,
     S_HITTMP, S_FRAMECNT, S_FRAMEOFF, S_FRAMECUR, S_HITGROUP, S_MAXRAD, S_NT_T0, S_NT_H,
@@ -839,6 +839,7 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
     GET(S_XCEN, 3 * ne, X.cen);
     GET(S_XRAD, ne, X.rad);
     GET(S_XCS, ne, X.cs);
+    GET(S_XCENF, ne, X.cenf);
     GET(S_XBATCH, ne, X.batch);
     GET(S_XSUN, 6 * ne, X.sun);
     GET(S_XOBSREL, ne, X.obs_rel);

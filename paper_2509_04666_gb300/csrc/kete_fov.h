@@ -15,6 +15,7 @@ struct ExpArrays {
     double *cen;       // [E][3] unit centre of the covering cap
     double *rad;       // [E] cap radius, rad (pi = covers everything)
     float2 *cs;        // [E] (cos r, sin r) of the cap, cos = -2 when r = pi
+    float4 *cenf;      // [E] the centre in FP32 for the candidate search (w unused)
     int32_t *batch;    // [E]
     double *sun;       // [E][6] Sun position and velocity at the exposure epoch
     float4 *obs_rel;   // [E] observer minus its batch's mean observer (FP32), w unused
