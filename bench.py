@@ -510,13 +510,16 @@ def ragged_leg(args, K, dev, flush, stream):
     res = {}
     ng = W.nongrav_params(w.labels)
     ng_dev = kete.nongrav_to_device(ng, dev)
-    for name, prec, kind, split, with_ng in (
-            ("fp64", kete.FP64, kete.PROP_WORK_STEALING, 0, False),
-            ("mixed", kete.MIXED, kete.PROP_WORK_STEALING, 0, False),
-            ("fp64_static", kete.FP64, kete.PROP_STATIC, 0, False),
-            ("fp64_split8", kete.FP64, kete.PROP_WORK_STEALING, 8, False),
-            ("mixed_split8", kete.MIXED, kete.PROP_WORK_STEALING, 8, False),
-            ("fp64_nongrav", kete.FP64, kete.PROP_WORK_STEALING, 0, True)):
+    variants = (("fp64", kete.FP64, kete.PROP_WORK_STEALING, 0, False),
+                ("mixed", kete.MIXED, kete.PROP_WORK_STEALING, 0, False),
+                ("fp64_static", kete.FP64, kete.PROP_STATIC, 0, False),
+                ("fp64_split8", kete.FP64, kete.PROP_WORK_STEALING, 8, False),
+                ("mixed_split8", kete.MIXED, kete.PROP_WORK_STEALING, 8, False),
+                ("fp64_nongrav", kete.FP64, kete.PROP_WORK_STEALING, 0, True))
+    if args.ragged_variants:   # a subset alone (profiling): no comparisons, no oracle
+        keep = args.ragged_variants.split(",")
+        variants = tuple(v for v in variants if v[0] in keep)
+    for name, prec, kind, split, with_ng in variants:
         K.set_propagation(prec, kind, 128, split, 64 if split else 0)
         fm = kete.force_model(precision=prec)
         if with_ng:
@@ -533,6 +536,8 @@ def ragged_leg(args, K, dev, flush, stream):
         res[name] = (box["st"].cpu().numpy(), status.cpu().numpy())
         out[name] = {"value": n * 365.0 / (ms / 1e3), "unit": "body-days/s", "ms": ms,
                      "prop_ms": stt["prop_ms"], "steps": stt["steps"], "deferred": stt["deferred"]}
+    if args.ragged_variants:
+        return out
     # the autotuner's pick per precision (kete_autotune on a body sample over
     # the same year), timed on the whole population beside the hand variants
     for name, prec in (("fp64_autotuned", kete.FP64), ("mixed_autotuned", kete.MIXED)):
@@ -931,6 +936,8 @@ def main():
     ap.add_argument("--adj-sample", type=int, default=512)
     ap.add_argument("--ragged-bodies", type=int, default=500_000)
     ap.add_argument("--tune-sample", type=int, default=131072)
+    ap.add_argument("--ragged-variants", default="",
+                    help="comma list of ragged-leg variants to run alone (profiling)")
     ap.add_argument("--leg", default="all", choices=["all", "adjoint", "ragged", "longspan", "ztf"],
                     help="run one leg alone (profiling); the default prints the benchmark line")
     args = ap.parse_args()
