@@ -115,8 +115,8 @@ typedef struct kete_force_model {
     /* Per-body non-gravitational terms: device array of one kete_nongrav per
      * body of the call, indexed like its states (8-byte aligned), or NULL
      * (default).  Read by kete_propagate, kete_propagate_stops,
-     * kete_propagate_noalloc and kete_fov_check(_mag); kete_adjoint refuses
-     * it (KETE_ERR_BAD_ARG: its gradient covers gravity only) and
+     * kete_propagate_noalloc, kete_fov_check(_mag), kete_adjoint and
+     * kete_sky_jacobian (whose derivatives then take the terms' partials);
      * kete_autotune times its sample without it. */
     const kete_nongrav *nongrav;
 } kete_force_model;
@@ -407,9 +407,14 @@ typedef struct kete_obs {
  *   loss[i] = sum_j (wrap(RA_j - RA_obs_j) cos Dec_obs_j)^2 + (Dec_j - Dec_obs_j)^2
  * (device, [n]); grad (device, [6][n], may be NULL) = d loss[i] / d(x0, v0)
  * from the adjoint equations integrated backward over every stored forward
- * step (Newtonian Jacobians; the GR and J2 contributions to da/dx, below
- * 1e-8 relative, and da/dv are omitted), plus the partials of the two-body,
- * light-time and RA/Dec map by forward-mode differentiation; pred (device,
+ * step, plus the partials of the two-body, light-time and RA/Dec map by
+ * forward-mode differentiation.  fm->nongrav NULL: the Newtonian da/dx alone
+ * (the GR and J2 parts of da/dx and GR's da/dv, below 1e-8 relative, are
+ * omitted).  fm->nongrav set (per-body terms, as kete_propagate): the forward
+ * model includes them and the adjoint takes the full model's da/dx and da/dv
+ * -- Newtonian, GR, J2 and the body's non-gravitational terms with their
+ * thermal lag -- by forward-mode dual numbers at every node of every step
+ * (about 300 KB more scratch per body, and a slower forward pass); pred (device,
  * [n][m][2], may be NULL) = predicted RA, Dec.  FP64 only (fm->precision is
  * ignored).  status (device, [n], may be NULL).
  * ckpt_days: 0 (no grid) or >= 1e-3; a body whose grid would exceed 65536
@@ -436,8 +441,8 @@ int kete_adjoint(kete_ctx *ctx, const double *states, const double *epochs, int6
  * body i (rad per AU, rad per AU/day); rows of unused observation slots and
  * of failed bodies (status not KETE_BODY_OK) are NaN.  Each row is the state-
  * transition matrix at the observation's batch midpoint -- the variational
- * equations dx'' = (da/dx) dx (Newtonian da/dx, as kete_adjoint) integrated
- * forward over every stored step -- multiplied by the partials of the
+ * equations dx'' = (da/dx) dx + (da/dv) dx' (the Jacobians of kete_adjoint)
+ * integrated forward over every stored step -- multiplied by the partials of the
  * two-body, light-time and RA/Dec map there.  pred (device, [n][m][2], may be
  * NULL): predicted RA, Dec.  Scratch: about 100 KB + 290 m bytes per body, in
  * chunks within opt->mem_budget_gb.  Errors: as kete_adjoint. */

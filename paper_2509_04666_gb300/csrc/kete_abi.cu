@@ -33,7 +33,7 @@ enum Slot {
     S_KSTOP, S_DEFER_LIST, S_DEFER_CNT, S_ORDER, S_ORDER_KEY, S_ORDER_HIST, S_ORDER_OFF,
     S_ORDER_SCAN, S_ORDER_N, S_ADJ_TEND, S_LEG_OUT,
     S_EXT_START, S_EXT_EX, S_EXT_TMP, S_EXT_FIRST, S_EXT_SUB, S_EXT_PARENT, S_EXT_CNT,
-    S_EXT_OFF, S_EXT_CUR, S_EXT_GROUP, S_EXT_KEEP, S_EXT_KCNT, S_EXT_KOFF, S_ADJ_PHI,
+    S_EXT_OFF, S_EXT_CUR, S_EXT_GROUP, S_EXT_KEEP, S_EXT_KCNT, S_EXT_KOFF, S_ADJ_PHI, S_ADJ_RECX,
     S_NSLOTS
 };
 
@@ -1265,9 +1265,6 @@ static int adjoint_impl(kete_ctx *ctx, const double *states, const double *epoch
     if (fm) fm64 = *fm;
     else kete_force_model_default(&fm64);
     fm64.precision = KETE_FP64;
-    if (fm64.nongrav)
-        return fail(ctx, KETE_ERR_BAD_ARG,
-                    "kete_adjoint differentiates gravity only: nongrav must be NULL");
     ForceDev F;
     int r = make_force(ctx, &fm64, F);
     if (r != KETE_OK) return r;
@@ -1293,7 +1290,9 @@ static int adjoint_impl(kete_ctx *ctx, const double *states, const double *epoch
         P.ctr = ctx->d_ctr;
         // scratch per chunk of bodies within the memory budget
         const int cap = KETE_ADJ_MAX_STEPS;
-        const size_t per_body = (size_t)cap * kAdjRec * sizeof(double) +
+        // with non-gravitational terms the records carry the full model's Jacobian
+        const bool full = fm64.nongrav != nullptr;
+        const size_t per_body = (size_t)cap * (kAdjRec + (full ? kAdjRecX : 0)) * sizeof(double) +
                                 (size_t)m * (sizeof(int32_t) + 12 * sizeof(double)) +
                                 (jac ? (size_t)m * 36 * sizeof(double) : 0) +
                                 3 * sizeof(int32_t);
@@ -1313,6 +1312,8 @@ static int adjoint_impl(kete_ctx *ctx, const double *states, const double *epoch
         GET(S_ADJ_STATUS, chunk, B.status);
         B.phi = nullptr;
         if (jac) GET(S_ADJ_PHI, (size_t)chunk * m * 36, B.phi);
+        B.recx = nullptr;
+        if (full) GET(S_ADJ_RECX, (size_t)chunk * cap * kAdjRecX, B.recx);
         unsigned long long *next = nullptr;
         GET(S_NEXTBODY, 1, next);
         int launches = 0;

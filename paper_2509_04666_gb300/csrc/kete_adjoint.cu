@@ -146,188 +146,7 @@ __device__ __forceinline__ int obs_count(const kete_obs *o, int m)
 }
 
 // ---------------------------------------------------------------------------
-// forward pass
-// ---------------------------------------------------------------------------
-// Per-lane walk over one body's stops: the batch midpoints and the checkpoint
-// grid epoch0 + k ckpt (before the last midpoint), merged in ascending order.
-struct StopWalk {
-    int mi, nb;          // observations in use, batches
-    int kb, j1;          // next batch, end of its observations
-    double tref;         // its midpoint
-    int kc;              // next checkpoint index
-    double tc, t_last;   // its epoch, the last midpoint
-    bool ckpt_ok;        // tc is a stop
-};
-
-// the next stop of the walk (call only while w.kb < w.nb); mid: a midpoint
-__device__ __forceinline__ double walk_target(const StopWalk &w, bool &mid)
-{
-    mid = !(w.ckpt_ok && w.tc < w.tref);
-    return mid ? w.tref : w.tc;
-}
-
-__device__ __forceinline__ void walk_next_ckpt(StopWalk &w, double epoch0, double ckpt)
-{
-    w.kc++;
-    w.tc = epoch0 + (double)w.kc * ckpt;
-    w.ckpt_ok = w.tc < w.t_last;
-}
-
-// One lane per body at a time, one step attempt per loop iteration (lanes of a
-// warp stay in step while their bodies sit at different stops).  refill = 1:
-// persistent grid, a lane whose body is done takes the next one from *next.
-__global__ void __launch_bounds__(128)
-k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc,
-              unsigned long long *__restrict__ next, int refill, const int32_t *__restrict__ order)
-{
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    Cnt cnt = {0, 0, 0, 0, 0};
-    int64_t i = -1;   // current body (chunk index); -1: none; nc: no work left
-    double x[3], v[3], t = 0.0, dt = 0.0, epoch0 = 0.0, ts = 0.0;
-    bool mid = false, capped = false;
-    int status = KETE_BODY_OK, count = 0;
-    long long attempts = 0;
-    const kete_obs *o = nullptr;
-    StopWalk W;
-    StepState S;
-    S.have_a0 = false;
-    S.ng = nullptr;   // the adjoint differentiates gravity only
-    const LegView L = leg_view(nullptr, 0);
-    double *rec = nullptr;
-    bool first = true;
-    for (;;) {
-        const bool need = (i < 0);
-        const unsigned m = __ballot_sync(FULL, need);
-        if (m) {
-            unsigned long long base = 0;
-            const int leader = __ffs(m) - 1;
-            if (refill) {
-                if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(m));
-                base = __shfl_sync(FULL, base, leader);
-            }
-            if (need) {
-                unsigned long long mine = base + __popc(m & ((1u << lane) - 1u));
-                if (!refill)
-                    mine = first ? (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x
-                                 : (unsigned long long)nc;
-                if (mine < (unsigned long long)nc) {
-                    i = order ? (int64_t)order[mine] : (int64_t)mine;
-                    const int64_t gi = i0 + i;
-                    o = P.obs + gi * P.m;
-                    bool fin = true;
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        x[c] = P.states[c * P.n + gi];
-                        v[c] = P.states[(3 + c) * P.n + gi];
-                        fin = fin && isfinite(x[c]) && isfinite(v[c]);
-                    }
-                    epoch0 = P.epochs[gi];
-                    t = epoch0;
-                    dt = 0.0;
-                    status = (fin && isfinite(epoch0)) ? KETE_BODY_OK : KETE_BODY_NONFINITE;
-                    W.mi = obs_count(o, P.m);
-                    for (int j = 1; j < W.mi; j++)
-                        if (o[j].epoch < o[j - 1].epoch) {
-                            atomicOr(&P.ctr->error_flags, 1 << 6);
-                            status = KETE_BODY_NONFINITE;
-                        }
-                    // batches and the last midpoint (the checkpoint grid ends there)
-                    W.nb = 0;
-                    W.t_last = epoch0;
-                    for (int j0 = 0; j0 < W.mi; W.nb++) j0 = next_batch(o, W.mi, j0, P.span, W.t_last);
-                    W.kb = 0;
-                    W.j1 = (W.mi > 0) ? next_batch(o, W.mi, 0, P.span, W.tref) : 0;
-                    W.kc = 1;
-                    W.tc = epoch0 + P.ckpt;
-                    W.ckpt_ok = P.ckpt > 0.0 && W.tc < W.t_last;
-                    rec = B.rec + (size_t)i * B.cap * kAdjRec;
-                    count = 0;
-                    capped = false;
-                    attempts = 0;
-                    S.have_a0 = false;
-                    if (W.kb < W.nb) {
-                        ts = walk_target(W, mid);
-                        aim_step(F, t, ts, dt);
-                    }
-                } else {
-                    i = nc;
-                }
-            }
-        }
-        first = false;
-        const bool active = (i >= 0 && i < nc);
-        if (!__any_sync(FULL, active)) break;
-        if (!active) continue;
-        if (status == KETE_BODY_OK && W.kb < W.nb && t != ts) {
-            if (++attempts > F.max_steps) {
-                status = KETE_BODY_STEP_CAP;
-            } else {
-                const int slot = count < B.cap - 1 ? count : B.cap - 2;
-                double *r = rec + (size_t)slot * kAdjRec;
-                const double t_prev = t;
-                status = step_once<KETE_FP64, true>(E, F, L, x, v, t, dt, ts, S, cnt, r + 2);
-                if (status == KETE_BODY_OK && t != t_prev) {
-                    r[0] = t_prev;
-                    r[1] = t;
-                    if (count < B.cap - 1) count++;
-                    else capped = true;
-                }
-            }
-            if (status == KETE_BODY_OK && t != ts) continue;
-        }
-        // at the stop ts (or failed): bookkeeping, then the next stop
-        if (status == KETE_BODY_OK && W.kb < W.nb) {
-            if (mid) {
-                double *y = B.yref + ((size_t)i * P.m + W.kb) * 6;
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    y[c] = x[c];
-                    y[3 + c] = v[c];
-                }
-                B.bidx[(size_t)i * P.m + W.kb] = count;
-                if (W.ckpt_ok && W.tc == W.tref) walk_next_ckpt(W, epoch0, P.ckpt);   // one stop
-                W.kb++;
-                if (W.kb < W.nb) W.j1 = next_batch(o, W.mi, W.j1, P.span, W.tref);
-            } else if (W.kc >= kAdjMaxCkpt) {   // bounded work per body
-                status = KETE_BODY_STEP_CAP;
-            } else {
-                walk_next_ckpt(W, epoch0, P.ckpt);
-            }
-            if (status == KETE_BODY_OK && W.kb < W.nb) {
-                ts = walk_target(W, mid);
-                aim_step(F, t, ts, dt);
-                S.have_a0 = false;
-                attempts = 0;
-                continue;
-            }
-        }
-        // the body is done
-        if (status == KETE_BODY_OK && !capped) {
-            // terminal record: da/dx at the final state closes the last step
-            double *r = rec + (size_t)count * kAdjRec;
-            double a[3], J[6];
-            Encounter enc;
-            const double zero[3] = {0.0, 0.0, 0.0};
-            status = accel_fp64<true>(E, F, t, 0.0, nullptr, x, v, a, enc, zero, true, J);
-            cnt.evals++;
-            r[0] = t;
-            r[1] = t;
-#pragma unroll
-            for (int q = 0; q < 6; q++) r[2 + q] = J[q];
-            count++;
-        }
-        if (status == KETE_BODY_OK && capped) status = KETE_BODY_ADJ_CAP;
-        B.n_rec[i] = (status == KETE_BODY_OK) ? count : 0;
-        B.nbat[i] = W.nb;
-        B.status[i] = status;
-        i = -1;
-    }
-    flush_counters(cnt, P.ctr);
-}
-
-// ---------------------------------------------------------------------------
-// observation operator and its partials
+// forward-mode dual numbers
 // ---------------------------------------------------------------------------
 // forward-mode dual number with 6 tangents (d/d r0, d/d v0)
 struct D6 {
@@ -477,6 +296,426 @@ __device__ void kepler_jacobian(double mu, double sqmu, const double r0[3], cons
     }
 }
 
+__device__ __forceinline__ D6 operator*(const D6 &a, double s) { return s * a; }
+__device__ __forceinline__ D6 ddot(const D6 a[3], const D6 b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+// a^p, d(a^p) = p a^(p-1) da
+__device__ __forceinline__ D6 dpow(const D6 &a, double p)
+{
+    D6 r;
+    r.v = pow(a.v, p);
+    const double k = p * r.v / a.v;
+#pragma unroll
+    for (int q = 0; q < 6; q++) r.d[q] = k * a.d[q];
+    return r;
+}
+__device__ __forceinline__ void dcross(const D6 a[3], const D6 b[3], D6 c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// The universal-variable two-body map of a state (R0, V0) in dual numbers
+// (any tangents) over a fixed dt: chi from the plain solve, its tangent from one
+// Newton step of Kepler's equation at the converged root (see
+// kepler_jacobian), then r = f R0 + g V0, v = fdot R0 + gdot V0.
+__device__ bool kepler_dual(double mu, double sqmu, const D6 R0[3], const D6 V0[3], double dt,
+                            D6 R[3], D6 V[3])
+{
+    const double r0v[3] = {R0[0].v, R0[1].v, R0[2].v}, v0v[3] = {V0[0].v, V0[1].v, V0[2].v};
+    double chi = 0.0, rr[3], vr[3];
+    const bool ok = kepler_uv(mu, sqmu, r0v, v0v, dt, chi, rr, vr);
+    const D6 rn0 = dsqrt(ddot(R0, R0));
+    const D6 vv = ddot(V0, V0);
+    const D6 rv = ddot(R0, V0);
+    const D6 alpha = 2.0 * dinv(rn0) - (1.0 / mu) * vv;
+    const D6 A = (1.0 / sqmu) * rv;
+    const D6 B = 1.0 + (-1.0) * (alpha * rn0);
+    const double x2 = chi * chi;
+    D6 C, S;
+    stumpff_dual(x2 * alpha, C, S);
+    const D6 Fk = (-sqmu * dt) + (x2 * (A * C) + (x2 * chi) * (B * S) + chi * rn0);
+    const double z = x2 * alpha.v;
+    const double dF = A.v * chi * (1.0 - z * S.v) + B.v * x2 * C.v + rn0.v;
+    D6 X = (-1.0 / dF) * Fk;
+    X.v = chi;
+    const D6 X2 = X * X;
+    const D6 Z = X2 * alpha;
+    D6 C2, S2;
+    stumpff_dual(Z, C2, S2);
+    const D6 f = 1.0 + (-1.0) * (X2 * C2 * dinv(rn0));
+    const D6 g = dt + (-1.0 / sqmu) * (X2 * X * S2);
+#pragma unroll
+    for (int i = 0; i < 3; i++) R[i] = f * R0[i] + g * V0[i];
+    const D6 rn = dsqrt(ddot(R, R));
+    const D6 fd = sqmu * (dinv(rn * rn0) * (((-1.0) + Z * S2) * X));
+    const D6 gd = 1.0 + (-1.0) * (X2 * C2 * dinv(rn));
+#pragma unroll
+    for (int i = 0; i < 3; i++) V[i] = fd * R0[i] + gd * V0[i];
+    return ok;
+}
+
+// da/dx and da/dv (row-major 3x3, a_i by x_c) of the force terms beyond the
+// Newtonian point masses at (t0 + off, x, v): the GR term (Eq. A.3) and the J2
+// term (Eq. A.4) of every mass that carries them, and the body's
+// non-gravitational terms (App. A.4-A.5: radiation pressure with drag, the JPL
+// comet model with its thermal lag through the two-body map), by forward-mode
+// dual numbers with the six tangents of (x, v).  The Newtonian da/dx
+// (newton_jacobian, symmetric) is added by the caller.
+__device__ int extra_jacobian(const EphemDev &E, const ForceDev &F, double t0, double off,
+                              const double x[3], const double v[3], const kete_nongrav *ng,
+                              double Ax[9], double Av[9])
+{
+    Seg g;
+    if (!ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
+    D6 X[3], V[3], a[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        X[c] = dconst(x[c]);
+        X[c].d[c] = 1.0;
+        V[c] = dconst(v[c]);
+        V[c].d[3 + c] = 1.0;
+        a[c] = dconst(0.0);
+    }
+    for (int m = 0; m < E.n_bodies; m++) {
+        if (!((F.active_mask >> m) & 1u)) continue;
+        const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
+        if (!gr && !j2) continue;
+        double st[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        cheb_state64(E, m, g.s, g.tau, st, gr);
+        D6 r[3], w[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            r[c] = (-st[c]) + X[c];
+            w[c] = (-st[3 + c]) + V[c];
+        }
+        const double mu = E.gm[m];
+        const D6 ri = dinv(dsqrt(ddot(r, r)));
+        const D6 ri2 = ri * ri, ri3 = ri2 * ri;
+        if (gr) {   // mu / (c^2 r^3) [(4 mu / r - w^2) r + 4 (r.w) w]
+            const D6 k = (mu * kInvC2) * ri3;
+            const D6 f = k * ((4.0 * mu) * ri + (-1.0) * ddot(w, w));
+            const D6 fw = 4.0 * (k * ddot(r, w));
+#pragma unroll
+            for (int c = 0; c < 3; c++) a[c] = a[c] + f * r[c] + fw * w[c];
+        }
+        if (j2) {   // -psi [(1 - 5 z^2 / r^2) r + 2 z p], psi = 1.5 J2 mu R^2 / r^5
+            const double *P = F.pole[m];
+            const D6 z = P[0] * r[0] + P[1] * r[1] + P[2] * r[2];
+            const D6 psi = F.j2k[m] * (ri3 * ri2);
+            const D6 q = 5.0 * (z * z * ri2);
+            const D6 f = (-1.0) * (psi * (1.0 + (-1.0) * q));
+            const D6 fp = -2.0 * (psi * z);
+#pragma unroll
+            for (int c = 0; c < 3; c++) a[c] = a[c] + f * r[c] + fp * P[c];
+        }
+    }
+    if (ng) {
+        const kete_nongrav p = *ng;
+        const double mu = E.gm[0];
+        double sun[6];
+        cheb_state64(E, 0, g.s, g.tau, sun, true);
+        D6 r[3], w[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            r[c] = (-sun[c]) + X[c];
+            w[c] = (-sun[3 + c]) + V[c];
+        }
+        if (p.beta != 0.0) {   // beta mu / r^2 [(1 - rdot / c) rhat - w / c]
+            const D6 rr = ddot(r, r);
+            const D6 rin = dinv(dsqrt(rr));
+            const D6 rdot = ddot(r, w) * rin;
+            const D6 f = (p.beta * mu) * dinv(rr);
+            const D6 kr = f * (1.0 + (-kInvC) * rdot) * rin;
+            const D6 kw = kInvC * f;
+#pragma unroll
+            for (int c = 0; c < 3; c++) a[c] = a[c] + kr * r[c] + (-1.0) * (kw * w[c]);
+        }
+        if (p.a1 != 0.0 || p.a2 != 0.0 || p.a3 != 0.0) {
+            D6 rl[3], wl[3];
+            if (p.dt != 0.0) {
+                if (!kepler_dual(mu, sqrt(mu), r, w, -p.dt, rl, wl)) return KETE_BODY_KEPLER_CAP;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; c++) { rl[c] = r[c]; wl[c] = w[c]; }
+            }
+            const D6 rn = dsqrt(ddot(rl, rl));
+            const D6 q = (1.0 / p.r0) * rn;
+            D6 gq = p.alpha * dpow(q, -p.m);
+            if (p.k != 0.0) gq = gq * dpow(1.0 + dpow(q, p.n), -p.k);
+            const D6 irn = dinv(rn);
+            D6 rh[3], h[3], nh[3], th[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) rh[c] = rl[c] * irn;
+            dcross(rl, wl, h);
+            const D6 ihn = dinv(dsqrt(ddot(h, h)));
+#pragma unroll
+            for (int c = 0; c < 3; c++) nh[c] = h[c] * ihn;
+            dcross(nh, rh, th);
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                a[c] = a[c] + gq * (p.a1 * rh[c] + p.a2 * th[c] + p.a3 * nh[c]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            Ax[3 * i + c] = a[i].d[c];
+            Av[3 * i + c] = a[i].d[3 + c];
+        }
+    return KETE_BODY_OK;
+}
+
+// The full model's Jacobian at the 8 nodes of an accepted step (t0, x0, v0,
+// a0, the attempt's final corrector coefficients A.b and size A.h): node n at
+// x(s) = x0 + s h v0 + (s h)^2 [a0/2 + sum_k b_k s^(k+1) / ((k+2)(k+3))],
+// v(s) = v0 + s h [a0 + sum_k b_k s^(k+1) / (k+2)], da/dx beyond the Newtonian
+// part and da/dv from extra_jacobian, to out[18 n .. 18 n + 17].
+__device__ __noinline__ int record_extra(const EphemDev &E, const ForceDev &F, double t0,
+                                         const double x0[3], const double v0[3],
+                                         const double a0[3], const Attempt &A,
+                                         const kete_nongrav *ng, double *out)
+{
+    for (int n = 0; n < 8; n++) {
+        const double sh = g_rt.h[n] * A.h;
+        double xn[3], vn[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            double px = A.b[6][i] * g_rt.wx[n][6];
+            double pv = A.b[6][i] * g_rt.wv[n][6];
+#pragma unroll
+            for (int k = 5; k >= 0; k--) {
+                px = fma(A.b[k][i], g_rt.wx[n][k], px);
+                pv = fma(A.b[k][i], g_rt.wv[n][k], pv);
+            }
+            px = fma(a0[i], 0.5, px);
+            pv = pv + a0[i];
+            xn[i] = x0[i] + fma(sh * sh, px, sh * v0[i]);
+            vn[i] = fma(sh, pv, v0[i]);
+        }
+        const int st = extra_jacobian(E, F, t0, sh, xn, vn, ng, out + 18 * n, out + 18 * n + 9);
+        if (st != KETE_BODY_OK) return st;
+    }
+    return KETE_BODY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// forward pass
+// ---------------------------------------------------------------------------
+// Per-lane walk over one body's stops: the batch midpoints and the checkpoint
+// grid epoch0 + k ckpt (before the last midpoint), merged in ascending order.
+struct StopWalk {
+    int mi, nb;          // observations in use, batches
+    int kb, j1;          // next batch, end of its observations
+    double tref;         // its midpoint
+    int kc;              // next checkpoint index
+    double tc, t_last;   // its epoch, the last midpoint
+    bool ckpt_ok;        // tc is a stop
+};
+
+// the next stop of the walk (call only while w.kb < w.nb); mid: a midpoint
+__device__ __forceinline__ double walk_target(const StopWalk &w, bool &mid)
+{
+    mid = !(w.ckpt_ok && w.tc < w.tref);
+    return mid ? w.tref : w.tc;
+}
+
+__device__ __forceinline__ void walk_next_ckpt(StopWalk &w, double epoch0, double ckpt)
+{
+    w.kc++;
+    w.tc = epoch0 + (double)w.kc * ckpt;
+    w.ckpt_ok = w.tc < w.t_last;
+}
+
+// One lane per body at a time, one step attempt per loop iteration (lanes of a
+// warp stay in step while their bodies sit at different stops).  refill = 1:
+// persistent grid, a lane whose body is done takes the next one from *next.
+// RICH: the body's non-gravitational terms enter the force, and every record
+// gets the full model's Jacobian (B.recx) besides the Newtonian da/dx.
+template <bool RICH>
+__global__ void __launch_bounds__(128)
+k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc,
+              unsigned long long *__restrict__ next, int refill, const int32_t *__restrict__ order)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    Cnt cnt = {0, 0, 0, 0, 0};
+    int64_t i = -1;   // current body (chunk index); -1: none; nc: no work left
+    double x[3], v[3], t = 0.0, dt = 0.0, epoch0 = 0.0, ts = 0.0;
+    bool mid = false, capped = false;
+    int status = KETE_BODY_OK, count = 0;
+    long long attempts = 0;
+    const kete_obs *o = nullptr;
+    StopWalk W;
+    StepState S;
+    S.have_a0 = false;
+    S.ng = nullptr;   // set per body on the full-model path
+    const LegView L = leg_view(nullptr, 0);
+    double *rec = nullptr, *recx = nullptr;
+    bool first = true;
+    for (;;) {
+        const bool need = (i < 0);
+        const unsigned m = __ballot_sync(FULL, need);
+        if (m) {
+            unsigned long long base = 0;
+            const int leader = __ffs(m) - 1;
+            if (refill) {
+                if (lane == leader) base = atomicAdd(next, (unsigned long long)__popc(m));
+                base = __shfl_sync(FULL, base, leader);
+            }
+            if (need) {
+                unsigned long long mine = base + __popc(m & ((1u << lane) - 1u));
+                if (!refill)
+                    mine = first ? (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x
+                                 : (unsigned long long)nc;
+                if (mine < (unsigned long long)nc) {
+                    i = order ? (int64_t)order[mine] : (int64_t)mine;
+                    const int64_t gi = i0 + i;
+                    o = P.obs + gi * P.m;
+                    bool fin = true;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        x[c] = P.states[c * P.n + gi];
+                        v[c] = P.states[(3 + c) * P.n + gi];
+                        fin = fin && isfinite(x[c]) && isfinite(v[c]);
+                    }
+                    epoch0 = P.epochs[gi];
+                    t = epoch0;
+                    dt = 0.0;
+                    status = (fin && isfinite(epoch0)) ? KETE_BODY_OK : KETE_BODY_NONFINITE;
+                    W.mi = obs_count(o, P.m);
+                    for (int j = 1; j < W.mi; j++)
+                        if (o[j].epoch < o[j - 1].epoch) {
+                            atomicOr(&P.ctr->error_flags, 1 << 6);
+                            status = KETE_BODY_NONFINITE;
+                        }
+                    // batches and the last midpoint (the checkpoint grid ends there)
+                    W.nb = 0;
+                    W.t_last = epoch0;
+                    for (int j0 = 0; j0 < W.mi; W.nb++) j0 = next_batch(o, W.mi, j0, P.span, W.t_last);
+                    W.kb = 0;
+                    W.j1 = (W.mi > 0) ? next_batch(o, W.mi, 0, P.span, W.tref) : 0;
+                    W.kc = 1;
+                    W.tc = epoch0 + P.ckpt;
+                    W.ckpt_ok = P.ckpt > 0.0 && W.tc < W.t_last;
+                    rec = B.rec + (size_t)i * B.cap * kAdjRec;
+                    if (RICH) {
+                        recx = B.recx + (size_t)i * B.cap * kAdjRecX;
+                        S.ng = F.nongrav ? F.nongrav + gi : nullptr;
+                    }
+                    count = 0;
+                    capped = false;
+                    attempts = 0;
+                    S.have_a0 = false;
+                    if (W.kb < W.nb) {
+                        ts = walk_target(W, mid);
+                        aim_step(F, t, ts, dt);
+                    }
+                } else {
+                    i = nc;
+                }
+            }
+        }
+        first = false;
+        const bool active = (i >= 0 && i < nc);
+        if (!__any_sync(FULL, active)) break;
+        if (!active) continue;
+        if (status == KETE_BODY_OK && W.kb < W.nb && t != ts) {
+            if (++attempts > F.max_steps) {
+                status = KETE_BODY_STEP_CAP;
+            } else {
+                const int slot = count < B.cap - 1 ? count : B.cap - 2;
+                double *r = rec + (size_t)slot * kAdjRec;
+                const double t_prev = t;
+                if (RICH) {   // the accepted attempt's coefficients give the node states
+                    const double x0[3] = {x[0], x[1], x[2]}, v0[3] = {v[0], v[1], v[2]};
+                    Attempt A;
+                    status = step_begin<KETE_FP64, true>(E, F, L, x, v, t, dt, ts, S, A, cnt, r + 2);
+                    while (status == KETE_BODY_OK) {
+                        bool done = false;
+                        status = attempt_sweep<KETE_FP64, true>(E, F, t, x, v, S.a0, S.as0,
+                                                                S.close, S.enc, A, done, cnt,
+                                                                r + 2, S.ng);
+                        if (done) break;
+                    }
+                    if (status == KETE_BODY_OK)
+                        status = step_end<KETE_FP64>(F, A, x, v, t, dt, S, cnt);
+                    if (status == KETE_BODY_OK && t != t_prev)
+                        status = record_extra(E, F, t_prev, x0, v0, S.a0, A, S.ng,
+                                              recx + (size_t)slot * kAdjRecX);
+                } else {
+                    status = step_once<KETE_FP64, true>(E, F, L, x, v, t, dt, ts, S, cnt, r + 2);
+                }
+                if (status == KETE_BODY_OK && t != t_prev) {
+                    r[0] = t_prev;
+                    r[1] = t;
+                    if (count < B.cap - 1) count++;
+                    else capped = true;
+                }
+            }
+            if (status == KETE_BODY_OK && t != ts) continue;
+        }
+        // at the stop ts (or failed): bookkeeping, then the next stop
+        if (status == KETE_BODY_OK && W.kb < W.nb) {
+            if (mid) {
+                double *y = B.yref + ((size_t)i * P.m + W.kb) * 6;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    y[c] = x[c];
+                    y[3 + c] = v[c];
+                }
+                B.bidx[(size_t)i * P.m + W.kb] = count;
+                if (W.ckpt_ok && W.tc == W.tref) walk_next_ckpt(W, epoch0, P.ckpt);   // one stop
+                W.kb++;
+                if (W.kb < W.nb) W.j1 = next_batch(o, W.mi, W.j1, P.span, W.tref);
+            } else if (W.kc >= kAdjMaxCkpt) {   // bounded work per body
+                status = KETE_BODY_STEP_CAP;
+            } else {
+                walk_next_ckpt(W, epoch0, P.ckpt);
+            }
+            if (status == KETE_BODY_OK && W.kb < W.nb) {
+                ts = walk_target(W, mid);
+                aim_step(F, t, ts, dt);
+                S.have_a0 = false;
+                attempts = 0;
+                continue;
+            }
+        }
+        // the body is done
+        if (status == KETE_BODY_OK && !capped) {
+            // terminal record: da/dx at the final state closes the last step
+            double *r = rec + (size_t)count * kAdjRec;
+            double a[3], J[6];
+            Encounter enc;
+            const double zero[3] = {0.0, 0.0, 0.0};
+            status = accel_fp64<true>(E, F, t, 0.0, nullptr, x, v, a, enc, zero, true, J, S.ng);
+            cnt.evals++;
+            r[0] = t;
+            r[1] = t;
+#pragma unroll
+            for (int q = 0; q < 6; q++) r[2 + q] = J[q];
+            if (RICH && status == KETE_BODY_OK) {
+                double *rx = recx + (size_t)count * kAdjRecX;
+                status = extra_jacobian(E, F, t, 0.0, x, v, S.ng, rx, rx + 9);
+            }
+            count++;
+        }
+        if (status == KETE_BODY_OK && capped) status = KETE_BODY_ADJ_CAP;
+        B.n_rec[i] = (status == KETE_BODY_OK) ? count : 0;
+        B.nbat[i] = W.nb;
+        B.status[i] = status;
+        i = -1;
+    }
+    flush_counters(cnt, P.ctr);
+}
+
+// ---------------------------------------------------------------------------
+// observation operator and its partials
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ bool sun_at(const EphemDev &E, double t0, double off, double p[3],
                                        double v[3])
 {
@@ -876,6 +1115,248 @@ k_adj_stm(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
 }
 
 // ---------------------------------------------------------------------------
+// the full force model: da/dx beyond the Newtonian part and da/dv
+// ---------------------------------------------------------------------------
+// extension (Ex, Av) of backward sample k (see jac_sample)
+__device__ __forceinline__ const double *jacx_sample(const double *rx, const double *rx_next, int k)
+{
+    return k == 0 ? rx_next : rx + 18 * (8 - k);
+}
+
+// extension of forward sample k (see jac_sample_fwd)
+__device__ __forceinline__ const double *jacx_sample_fwd(const double *rx, const double *rx_next,
+                                                         int k)
+{
+    return k == 8 ? rx_next : rx + 18 * k;
+}
+
+// adjoint right-hand sides: G = h^2 (J + Ex)^T m, H = h Av^T m (J symmetric,
+// Ex and Av row-major a_i by x_c)
+__device__ __forceinline__ void adj_rhs_full(const double *J, const double *X, double h,
+                                             const double m[3], double G[3], double H[3])
+{
+    double jm[3];
+    jmul(J, m, jm);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const double ex = fma(__ldg(X + c), m[0], fma(__ldg(X + 3 + c), m[1], __ldg(X + 6 + c) * m[2]));
+        const double av =
+            fma(__ldg(X + 9 + c), m[0], fma(__ldg(X + 12 + c), m[1], __ldg(X + 15 + c) * m[2]));
+        G[c] = h * h * (jm[c] + ex);
+        H[c] = h * av;
+    }
+}
+
+// variational right-hand side: F = h^2 ((J + Ex) dx + Av dv)
+__device__ __forceinline__ void var_rhs_full(const double *J, const double *X, double h,
+                                             const double dx[3], const double dv[3], double F[3])
+{
+    double jx[3];
+    jmul(J, dx, jx);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const double *e = X + 3 * c, *a = X + 9 + 3 * c;
+        const double ex = fma(__ldg(e), dx[0], fma(__ldg(e + 1), dx[1], __ldg(e + 2) * dx[2]));
+        const double av = fma(__ldg(a), dv[0], fma(__ldg(a + 1), dv[1], __ldg(a + 2) * dv[2]));
+        F[c] = h * h * (jx[c] + ex + av);
+    }
+}
+
+// Backward pass of the full model.  The adjoints (lx, mu) = (lambda_x,
+// lambda_v) obey lx' = -Ax^T mu, mu' = -lx - Av^T mu.  In the backward variable
+// s = (t_end - t) / h of a recorded step, with G_k = h^2 Ax^T mu_k and
+// H_k = h Av^T mu_k at the samples sig_k:
+//   mu(sig_n) = mu_0 + sig_n h lx_0 + sum_k (W2[n][k] G_k + W1[n][k] H_k),
+//   lx(1)     = lx_0 + (1/h) sum_k W1[8][k] G_k,
+// solved by Gauss-Seidel sweeps over the samples (contraction ~ h^2 |Ax| +
+// h |Av|, at most 16 sweeps).  Without the extension this is k_adj_backward.
+__global__ void __launch_bounds__(128)
+k_adj_backward_full(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const int64_t gi = i0 + i;
+    if (B.status[i] != KETE_BODY_OK) {
+        for (int c = 0; c < 6; c++) P.grad[c * P.n + gi] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    const int count = B.n_rec[i];
+    int kb = B.nbat[i] - 1;
+    const double *rec = B.rec + (size_t)i * B.cap * kAdjRec;
+    const double *recx = B.recx + (size_t)i * B.cap * kAdjRecX;
+    const int32_t *bidx = B.bidx + (size_t)i * P.m;
+    const double *gjump = B.gjump + (size_t)i * P.m * 6;
+    double mu[3] = {0, 0, 0}, lx[3] = {0, 0, 0};
+    for (int s = count - 2; s >= -1; s--) {
+        while (kb >= 0 && bidx[kb] == s + 1) {
+            const double *g = gjump + kb * 6;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                lx[c] += g[c];
+                mu[c] += g[3 + c];
+            }
+            kb--;
+        }
+        if (s < 0) break;
+        if (mu[0] == 0.0 && mu[1] == 0.0 && mu[2] == 0.0 && lx[0] == 0.0 && lx[1] == 0.0 &&
+            lx[2] == 0.0)
+            continue;
+        const double *r = rec + (size_t)s * kAdjRec;
+        const double *rn = r + kAdjRec;
+        const double *rx = recx + (size_t)s * kAdjRecX;
+        const double *rxn = rx + kAdjRecX;
+        const double h = __ldg(r + 1) - __ldg(r);
+        const double q0[3] = {h * lx[0], h * lx[1], h * lx[2]};
+        double G[9][3], H[9][3], m8[3];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            double m[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) m[c] = fma(g_adj.sig[k], q0[c], mu[c]);
+            adj_rhs_full(jac_sample(r, rn, k), jacx_sample(rx, rxn, k), h, m, G[k], H[k]);
+            if (k == 8)
+#pragma unroll
+                for (int c = 0; c < 3; c++) m8[c] = m[c];
+        }
+        for (int it = 0; it < 16; it++) {
+            double delta = 0.0, size = 0.0;
+#pragma unroll
+            for (int n = 1; n < 9; n++) {
+                double m[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    double acc = fma(g_adj.sig[n], q0[c], mu[c]);
+#pragma unroll
+                    for (int j = 0; j < 9; j++)
+                        acc = fma(g_adj.W2[n][j], G[j][c], fma(g_adj.W1[n][j], H[j][c], acc));
+                    m[c] = acc;
+                }
+                if (n == 8) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        delta = fmax(delta, fabs(m[c] - m8[c]));
+                        size = fmax(size, fabs(m[c]));
+                        m8[c] = m[c];
+                    }
+                }
+                adj_rhs_full(jac_sample(r, rn, n), jacx_sample(rx, rxn, n), h, m, G[n], H[n]);
+            }
+            if (delta <= 1e-16 * size) break;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j < 9; j++) acc = fma(g_adj.W1[8][j], G[j][c], acc);
+            lx[c] += acc / h;
+            mu[c] = m8[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        P.grad[c * P.n + gi] = lx[c];
+        P.grad[(3 + c) * P.n + gi] = mu[c];
+    }
+}
+
+// State-transition matrix of the full model: the columns (dx, dv) obey
+// dx' = dv, dv' = Ax dx + Av dv.  In the forward variable of a recorded step,
+// with F_k = h^2 (Ax dx_k + Av dv_k) at the samples (node 0..7, step end):
+//   dx(s_n) = dx_0 + s_n h dv_0 + sum_k W2f[n][k] F_k,
+//   dv(s_n) = dv_0 + (1/h) sum_k W1f[n][k] F_k,
+// Gauss-Seidel sweeps as in k_adj_backward_full.
+__global__ void __launch_bounds__(128)
+k_adj_stm_full(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    if (B.status[i] != KETE_BODY_OK) return;   // the observation kernel writes NaN rows
+    const int count = B.n_rec[i];
+    const int nb = B.nbat[i];
+    const double *rec = B.rec + (size_t)i * B.cap * kAdjRec;
+    const double *recx = B.recx + (size_t)i * B.cap * kAdjRecX;
+    const int32_t *bidx = B.bidx + (size_t)i * P.m;
+    double *phi_out = B.phi + (size_t)i * P.m * 36;
+    for (int c0 = 0; c0 < 6; c0++) {
+        double dx[3] = {0, 0, 0}, dv[3] = {0, 0, 0};
+        if (c0 < 3) dx[c0] = 1.0;
+        else dv[c0 - 3] = 1.0;
+        int kb = 0;
+        for (int s = 0; s <= count - 1; s++) {
+            while (kb < nb && bidx[kb] == s) {
+                double *ph = phi_out + (size_t)kb * 36;
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    ph[q * 6 + c0] = dx[q];
+                    ph[(3 + q) * 6 + c0] = dv[q];
+                }
+                kb++;
+            }
+            if (s == count - 1) break;
+            const double *r = rec + (size_t)s * kAdjRec;
+            const double *rn = r + kAdjRec;
+            const double *rx = recx + (size_t)s * kAdjRecX;
+            const double *rxn = rx + kAdjRecX;
+            const double h = __ldg(r + 1) - __ldg(r);
+            const double ih = 1.0 / h;
+            double F[9][3], x8[3], v8[3];
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                double xk[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) xk[c] = fma(g_adj.sigf[k] * h, dv[c], dx[c]);
+                var_rhs_full(jac_sample_fwd(r, rn, k), jacx_sample_fwd(rx, rxn, k), h, xk, dv,
+                             F[k]);
+                if (k == 8)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        x8[c] = xk[c];
+                        v8[c] = dv[c];
+                    }
+            }
+            for (int it = 0; it < 16; it++) {
+                double delta = 0.0, size = 0.0;
+#pragma unroll
+                for (int n = 1; n < 9; n++) {
+                    double xn[3], vn[3];
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        double ax = fma(g_adj.sigf[n] * h, dv[c], dx[c]), av = 0.0;
+#pragma unroll
+                        for (int j = 0; j < 9; j++) {
+                            ax = fma(g_adj.W2f[n][j], F[j][c], ax);
+                            av = fma(g_adj.W1f[n][j], F[j][c], av);
+                        }
+                        xn[c] = ax;
+                        vn[c] = fma(av, ih, dv[c]);
+                    }
+                    if (n == 8) {
+#pragma unroll
+                        for (int c = 0; c < 3; c++) {
+                            delta = fmax(delta, fmax(fabs(xn[c] - x8[c]), fabs(h * (vn[c] - v8[c]))));
+                            size = fmax(size, fmax(fabs(xn[c]), fabs(h * vn[c])));
+                            x8[c] = xn[c];
+                            v8[c] = vn[c];
+                        }
+                    }
+                    var_rhs_full(jac_sample_fwd(r, rn, n), jacx_sample_fwd(rx, rxn, n), h, xn, vn,
+                                 F[n]);
+                }
+                if (delta <= 1e-16 * size) break;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < 9; j++) acc = fma(g_adj.W1f[8][j], F[j][c], acc);
+                dv[c] = fma(acc, ih, dv[c]);
+                dx[c] = x8[c];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
@@ -911,12 +1392,14 @@ cudaError_t launch_adjoint_forward(const EphemDev &E, const ForceDev &F, const A
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_forward, 128, 0);
+        if (B.recx) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_forward<true>, 128, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_forward<false>, 128, 0);
         const int64_t persistent = (int64_t)(sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
         if (grid > persistent) grid = persistent;
         refill = 1;
     }
-    k_adj_forward<<<(unsigned)grid, 128, 0, st>>>(E, F, B, P, i0, nc, next, refill, order);
+    if (B.recx) k_adj_forward<true><<<(unsigned)grid, 128, 0, st>>>(E, F, B, P, i0, nc, next, refill, order);
+    else k_adj_forward<false><<<(unsigned)grid, 128, 0, st>>>(E, F, B, P, i0, nc, next, refill, order);
     return cudaGetLastError();
 }
 
@@ -930,14 +1413,18 @@ cudaError_t launch_adjoint_observe(const EphemDev &E, const AdjBuffers &B, const
 cudaError_t launch_adjoint_stm(const AdjBuffers &B, const AdjProblem &P, int64_t i0, int64_t nc,
                                cudaStream_t st)
 {
-    if (nc > 0) k_adj_stm<<<blocks_for(nc, 128), 128, 0, st>>>(B, P, i0, nc);
+    if (nc <= 0) return cudaGetLastError();
+    if (B.recx) k_adj_stm_full<<<blocks_for(nc, 128), 128, 0, st>>>(B, P, i0, nc);
+    else k_adj_stm<<<blocks_for(nc, 128), 128, 0, st>>>(B, P, i0, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_backward(const AdjBuffers &B, const AdjProblem &P, int64_t i0,
                                     int64_t nc, cudaStream_t st)
 {
-    if (nc > 0) k_adj_backward<<<blocks_for(nc, 128), 128, 0, st>>>(B, P, i0, nc);
+    if (nc <= 0) return cudaGetLastError();
+    if (B.recx) k_adj_backward_full<<<blocks_for(nc, 128), 128, 0, st>>>(B, P, i0, nc);
+    else k_adj_backward<<<blocks_for(nc, 128), 128, 0, st>>>(B, P, i0, nc);
     return cudaGetLastError();
 }
 

@@ -12,6 +12,8 @@ namespace kete {
 // da/dx (xx, xy, xz, yy, yz, zz) at the step's 8 Gauss-Radau nodes; a final
 // record (t_end = t_start) holds da/dx at the last state in node 0's place
 constexpr int kAdjRec = 2 + 8 * 6;
+// the full-model extension of a record: 8 nodes x (da/dx beyond Newton, da/dv)
+constexpr int kAdjRecX = 8 * 18;
 // checkpoint stops per body before the chain gives up (KETE_BODY_STEP_CAP)
 constexpr int kAdjMaxCkpt = 1 << 16;
 
@@ -40,6 +42,10 @@ struct AdjBuffers {
     double *gjump;     // [nc][m][6] dL/dy(t_ref) of batch k
     double *phi;       // [nc][m][36] state-transition matrix at batch k's midpoint
                        // (row-major, d y_r(t_ref) / d y0_c; only with P.jac)
+    double *recx;      // [nc][cap][8][18] per record and node: da/dx beyond the Newtonian
+                       // part (9, row-major) and da/dv (9) -- the full force model's
+                       // Jacobian (calls with non-gravitational terms); null: the
+                       // Newtonian da/dx of rec alone
     int32_t *status;   // [nc]
 };
 

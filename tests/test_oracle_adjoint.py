@@ -168,3 +168,35 @@ def test_sky_jacobian_gives_the_loss_gradient(adj_small):
     dra = (pred[:, 0] - obs["ra"] + math.pi) % (2 * math.pi) - math.pi
     g2 = (2 * (dra * cd2)[:, None] * jac[:, 0, :] + 2 * (pred[:, 1] - obs["dec"])[:, None] * jac[:, 1, :]).sum(0)
     assert np.abs(g2 - g).max() < 1e-9 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("kind", ["dust", "lagged", "comet"])
+def test_variational_gradient_with_nongrav_matches_finite_differences(adj_small, kind):
+    """With non-gravitational terms the variational equations take the full
+    model's da/dx and da/dv (radiation pressure with drag; the comet model,
+    its thermal lag through the two-body map): the gradient still equals
+    central differences of the loss."""
+    w = adj_small
+    orc = O.Oracle(w.ephem.to_bytes())
+    ng = {"dust": O.dust_ng(0.03),
+          "lagged": O.asteroid_ng(2e-8, -1e-8, 5e-9, dt=20.0),
+          "comet": O.comet_ng(5e-8, 1e-8, -2e-9, dt=15.0)}[kind]
+    fm = orc.force_model(ng=ng)
+    i = {"dust": 3, "lagged": 11, "comet": 27}[kind]
+    obs = _observations(orc, fm, w, i)
+    y = w.states[:, i] + w.meta["offsets"][:, i]
+    rc, loss, _, g = orc.body_loss(fm, y, W.T0, obs)
+    assert rc == 0 and loss > 0
+    fd = np.zeros(6)
+    for c in range(6):
+        h = 1e-7 if c < 3 else 1e-9
+        yp, ym = y.copy(), y.copy()
+        yp[c] += h; ym[c] -= h
+        _, lp, _, _ = orc.body_loss(fm, yp, W.T0, obs, grad=False)
+        _, lm, _, _ = orc.body_loss(fm, ym, W.T0, obs, grad=False)
+        fd[c] = (lp - lm) / (2 * h)
+    assert np.abs(g[:3] - fd[:3]).max() < 1e-6 * np.abs(g[:3]).max(), (g, fd)
+    assert np.abs(g[3:] - fd[3:]).max() < 1e-6 * np.abs(g[3:]).max(), (g, fd)
+    # the terms change the gradient by far more than that
+    rc, _, _, g0 = orc.body_loss(orc.force_model(), y, W.T0, obs)
+    assert np.abs(g0 - g).max() > 1e-4 * np.abs(g).max()
