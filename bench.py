@@ -40,7 +40,7 @@ MAS = math.radians(1.0 / 3.6e6)
 # of the same workload (100k bodies x 21 stops), per body-stop, scaled to the
 # full launch by its body-stops; valid only while the kernel source is
 # unchanged (the source hash below).
-PROFILED_TRAFFIC = {"src_sha": "cfb11c9322fcded9", "bytes_per_body_stop": 183.2}
+PROFILED_TRAFFIC = {"src_sha": "e33cb9938323ed22", "bytes_per_body_stop": 65.6}
 
 
 # FP64 work of the exact FoV test per candidate as ncu counts it (2 x DFMA +
@@ -48,7 +48,14 @@ PROFILED_TRAFFIC = {"src_sha": "cfb11c9322fcded9", "bytes_per_body_stop": 183.2}
 # divided by its candidates); valid only while the FoV kernels' source is
 # unchanged.  The modelled count below leaves out the divisions, square roots
 # and convergence tests that the executed count includes.
-PROFILED_EXACT = {"src_sha": None, "fp64_flops_per_candidate": None}
+PROFILED_EXACT = {"src_sha": "eaaf2a2532119499", "fp64_flops_per_candidate": 894.0}
+
+# FP64 arithmetic thread instructions (DFMA + DMUL + DADD) the FP64 survey's
+# propagation kernel executes per accepted step, from the same ncu capture as
+# the traffic (100k bodies x 21 stops: 16.92 G over 2,119,119 steps); with the
+# step count of a run it gives the FP64 pipe's issue rate, which the FLOP
+# roofline understates (a DMUL or DADD takes an FMA's issue slot).
+PROFILED_ISSUE = {"src_sha": "e33cb9938323ed22", "fp64_inst_per_step": 7984.0}
 
 
 def kernel_source_sha(files=("kete_prop.cu", "kete_device.cuh", "kete_step.cuh", "kete_order.cu")):
@@ -604,7 +611,7 @@ def longspan_leg(args, K, dev, flush, stream):
     """Backward propagation over decades and centuries: 20,000 bodies of the
     survey population carried back 50 years, and 1,000 clones of a
     Jupiter-family comet (JPL comet model) carried back 170 years, one lane
-    per body against lane groups of 8."""
+    per body against lane groups of 8 and 16."""
     import torch
     import oracle as O
     from paper_2509_04666_gb300 import kete, workloads as W
@@ -613,7 +620,8 @@ def longspan_leg(args, K, dev, flush, stream):
              (("fp64", kete.FP64, 0), ("mixed", kete.MIXED, 0))),
             ("clones", W.clones(n_clones=1000, years=170.0), "nongrav",
              (("fp64", kete.FP64, 0), ("fp64_split8", kete.FP64, 8),
-              ("mixed_split8", kete.MIXED, 8))))
+              ("fp64_split16", kete.FP64, 16), ("mixed_split8", kete.MIXED, 8),
+              ("mixed_split16", kete.MIXED, 16))))
     for leg, w, ngkey, variants in legs:
         n = w.n_bodies
         days = abs(w.t_end - W.T0)
@@ -772,6 +780,14 @@ def run_gb300(args):
     traffic = None
     if PROFILED_TRAFFIC["src_sha"] == src_sha and PROFILED_TRAFFIC["bytes_per_body_stop"]:
         traffic = PROFILED_TRAFFIC["bytes_per_body_stop"] * n * s0["n_batches"] / max(1, s0["prop_launches"])
+    issue = None
+    if PROFILED_ISSUE["src_sha"] == src_sha and not mixed:
+        per = PROFILED_ISSUE["fp64_inst_per_step"]
+        rate = per * s0["steps"] / (prop_ms / 1e3)
+        issue = {"fp64_thread_inst_per_step": per, "thread_inst_per_s": rate,
+                 "frac_nominal": rate / (peak_nominal * 1e12 / 2),
+                 "frac_probe": rate / (peak_probe / 2) if peak_probe else None,
+                 "basis": "ncu-counted DFMA+DMUL+DADD per accepted step (100k-body case)"}
     # ---- e2e: the public call with host buffers ----------------------------------
     e2e = None
     if not args.no_e2e:
@@ -881,7 +897,7 @@ def run_gb300(args):
                      "flops_per_launch": flops / max(1, s0["prop_launches"]),
                      "fp32_tflops_alongside": flops32 / (prop_ms / 1e3) / 1e12,
                      "prop_ms_per_step": prop_ms, "peak_basis": "152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
-                     "fp64_warp_inst_per_s": lane_probe},
+                     "fp64_warp_inst_per_s": lane_probe, "fp64_issue": issue},
         "cpu_baseline": cpu,
         "accuracy": accuracy,
         "e2e": e2e,

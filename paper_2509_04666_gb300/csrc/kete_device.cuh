@@ -361,6 +361,27 @@ static __device__ __noinline__ NgOut nongrav_terms(const EphemDev &E, const doub
                                                    const kete_nongrav *P, double x0, double x1,
                                                    double x2, double v0, double v1, double v2);
 
+// Lane groups (G > 1): the body's non-gravitational terms (ng may be null)
+// computed by the group's last lane -- the one that holds the fewest masses
+// -- and added to its partial sum acc before the group sum; every lane of
+// the group returns the same status.
+template <int G>
+__device__ __forceinline__ int group_nongrav(const EphemDev &E, const double *row64, Seg g,
+                                             const kete_nongrav *ng, const double x[3],
+                                             const double v[3], double acc[3])
+{
+    if (!ng) return KETE_BODY_OK;
+    int st = KETE_BODY_OK;
+    if (LaneGroup<G>::rank() == G - 1) {
+        const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2]);
+        st = o.status;
+        acc[0] += o.a[0];
+        acc[1] += o.a[1];
+        acc[2] += o.a[2];
+    }
+    return __shfl_sync(LaneGroup<G>::mask(), st, G - 1, G);
+}
+
 // Full-FP64 acceleration.
 // detect (step start, off = 0): also record in enc the nearest planet within
 // kEncounterAu and its relative position; otherwise enc is read.
@@ -426,6 +447,10 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
         if (JAC) newton_jacobian(E.gm[m], r, J);
     }
     if (G > 1) {
+        // the body's own terms go to the group's last lane, which holds the
+        // fewest masses, and join the group sum (a lagged comet term costs a
+        // two-body solve: done once per group, beside the others' masses)
+        const int ng_status = group_nongrav<G>(E, row64, g, ng, x, v, a);
 #pragma unroll
         for (int c = 0; c < 3; c++) a[c] = LaneGroup<G>::sum(a[c]);
         if (JAC) {
@@ -433,6 +458,7 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
             for (int q = 0; q < 6; q++) J[q] = LaneGroup<G>::sum(J[q]);
         }
         if (detect) encounter_reduce<G>(best, enc);
+        return ng_status;
     }
     if (ng) {
         const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2]);
@@ -566,7 +592,9 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
         float w[3] = {vf[0] - st[3], vf[1] - st[4], vf[2] - st[5]};
         mass_terms<float>(F.gm32[m], F.j2k32[m], F.pole32[m], true, gr, j2, r, w, af);
     }
+    int ng_status = KETE_BODY_OK;
     if (G > 1) {
+        ng_status = group_nongrav<G>(E, row64, g, ng, x, v, as);   // FP64, smooth part
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             as[c] = LaneGroup<G>::sum(as[c]);
@@ -576,8 +604,8 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
             close = LaneGroup<G>::bit_or(close);
             encounter_reduce<G>(best, enc);
         }
-    }
-    if (ng) {   // FP64, part of the smooth FP64 sum that controls the step
+        if (ng_status != KETE_BODY_OK) return ng_status;
+    } else if (ng) {   // FP64, part of the smooth FP64 sum that controls the step
         const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2]);
         if (o.status != KETE_BODY_OK) return o.status;
         as[0] += o.a[0];

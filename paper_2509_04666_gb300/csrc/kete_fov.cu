@@ -355,7 +355,8 @@ __global__ void k_cell_scatter(int32_t e_begin, int32_t e_end, const int32_t *__
 }
 
 // ---------------------------------------------------------------------------
-// candidates: thread per (body, batch of the chunk)
+// candidates: an item is one (body, batch of the chunk); a warp shares the
+// tests of its 32 items
 // ---------------------------------------------------------------------------
 struct CandCtx {
     ExpArrays X;
@@ -403,76 +404,160 @@ __device__ __forceinline__ void test_exposure(const CandCtx &C, int32_t e, const
     }
 }
 
+// The runs of one item: contiguous ranges of exposure indices to test, either
+// the whole batch (direct) or, band by band, the cells within R of the body's
+// direction (indices into cell_exp).  A lane steps through its item's runs
+// one at a time.
+struct CandRuns {
+    int mode;            // 0: none left, 1: direct range, 2: cell ranges
+    int64_t a, b;        // current run [a, b)
+    int j, jhi, r, nr;   // band, last band, piece of the band, pieces
+    int rl0, rh0, rl1, rh1;   // cell index ranges of the band's pieces
+    float lon, dlon;
+    int64_t base;        // first cell key of the item's batch
+};
+
+// next non-empty run (or mode 0)
+__device__ __forceinline__ void cand_next_run(const CandCtx &C, CandRuns &u)
+{
+    const CellGrid &G = C.G;
+    while (u.mode == 2 && u.a >= u.b) {
+        if (u.r >= u.nr) {
+            if (++u.j > u.jhi) {
+                u.mode = 0;
+                break;
+            }
+            const int nj = G.band_n[u.j];
+            const float w = (float)kTwoPi / nj;
+            const int ilo = (int)floorf((u.lon - u.dlon) / w), ihi = (int)floorf((u.lon + u.dlon) / w);
+            if (u.dlon >= (float)kPi || ihi - ilo + 1 >= nj) {
+                u.rl0 = 0; u.rh0 = nj - 1; u.nr = 1;
+            } else if (ilo < 0) {
+                u.rl0 = 0; u.rh0 = ihi; u.rl1 = ilo + nj; u.rh1 = nj - 1; u.nr = 2;
+            } else if (ihi >= nj) {
+                u.rl0 = ilo; u.rh0 = nj - 1; u.rl1 = 0; u.rh1 = ihi - nj; u.nr = 2;
+            } else {
+                u.rl0 = ilo; u.rh0 = ihi; u.nr = 1;
+            }
+            u.r = 0;
+        }
+        const int64_t k0 = u.base + G.band_off[u.j];
+        const int lo = u.r == 0 ? u.rl0 : u.rl1, hi = u.r == 0 ? u.rh0 : u.rh1;
+        u.a = C.cell_start[k0 + lo];
+        u.b = C.cell_start[k0 + hi + 1];
+        u.r++;
+    }
+    if (u.mode == 1 && u.a >= u.b) u.mode = 0;
+}
+
+// Each lane sets up its item (the body's batch state, the conservative
+// search radius, its runs); then the warp takes the tests of all 32 items 32
+// at a time: slot q of a round goes to the lane whose pending tests cover it
+// (a prefix sum over the lanes' counts and a 5-step search), so the lanes stay
+// busy whatever the spread of the items' test counts -- a body near the
+// observer that tests every exposure of its batch is shared by the warp.
+// Every (item, exposure) pair is tested once, with its own item's geometry:
+// the candidates are those of a thread-per-item scan.
 __global__ void __launch_bounds__(256) k_candidates(CandCtx C)
 {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= C.n * C.nk) return;
-    const int32_t kl = (int32_t)(idx / C.n);
-    const int32_t i = (int32_t)(idx - (int64_t)kl * C.n);
-    const int32_t k = C.k0 + kl;
-    const double *st = C.stop_states + ((int64_t)kl * C.n + i) * 6;
-    const double p[3] = {st[0], st[1], st[2]};
-    if (!isfinite(p[0])) return;
-    const double v[3] = {st[3], st[4], st[5]};
-    const double *O = C.B.O + 3 * k;
-    const double *sun = C.B.sun + 6 * k;
-    const float robs = (float)C.B.robs[k];
-    // FP32 from here on: a conservative prefilter, padded for its rounding
-    const float d[3] = {(float)(p[0] - O[0]), (float)(p[1] - O[1]), (float)(p[2] - O[2])};
-    const float D = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    const float h[3] = {(float)(p[0] - sun[0]), (float)(p[1] - sun[1]), (float)(p[2] - sun[2])};
-    const float vh[3] = {(float)(v[0] - sun[3]), (float)(v[1] - sun[4]), (float)(v[2] - sun[5])};
-    const float rh = sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
-    const float vn = sqrtf(vh[0] * vh[0] + vh[1] * vh[1] + vh[2] * vh[2]);
-    // time offsets from t_ref: frame epochs within tspan, light time below tau_max
-    const float T = (float)C.B.tspan[k] + (D + robs + 1.0f) * (float)kInvC;
-    // heliocentric displacement bound, valid while the body stays beyond rh/2
-    const float disp = vn * T + 2.0f * (float)C.mu_sun * T * T / (rh * rh);
-    const float s = (disp + (float)kSunSpeedMax * T) * 1.0001f + 1e-6f;
-    const bool all = (disp > 0.5f * rh) || (s + robs >= 0.99f * D) || (D < 0.05f);
-    const float rho = all ? (float)kPi : asinf((s + robs) / D);
-    const float R = rho + (float)C.B.rmax[k] + 4.0f * kPadF;
-    const int32_t e0 = C.B.first[k], e1 = C.B.first[k + 1];
-    const float pb[3] = {d[0], d[1], d[2]};
-    if (all || R >= 1.2f) {
-        for (int32_t e = e0; e < e1; e++) test_exposure(C, e, pb, all ? 1e30f : s, i);
-        return;
+    const int64_t n_items = C.n * C.nk;
+    if (idx - lane >= n_items) return;   // whole warps past the end
+    CandRuns u;
+    u.mode = 0;
+    u.a = u.b = 0;
+    float pb[3] = {0.0f, 0.0f, 0.0f}, s_eff = 0.0f;
+    int32_t body = 0;
+    if (idx < n_items) {
+        const int32_t kl = (int32_t)(idx / C.n);
+        const int32_t i = (int32_t)(idx - (int64_t)kl * C.n);
+        const int32_t k = C.k0 + kl;
+        body = i;
+        const double *st = C.stop_states + ((int64_t)kl * C.n + i) * 6;
+        const double p[3] = {st[0], st[1], st[2]};
+        if (isfinite(p[0])) {
+            const double v[3] = {st[3], st[4], st[5]};
+            const double *O = C.B.O + 3 * k;
+            const double *sun = C.B.sun + 6 * k;
+            const float robs = (float)C.B.robs[k];
+            // FP32 from here on: a conservative prefilter, padded for its rounding
+            const float d[3] = {(float)(p[0] - O[0]), (float)(p[1] - O[1]), (float)(p[2] - O[2])};
+            const float D = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const float h[3] = {(float)(p[0] - sun[0]), (float)(p[1] - sun[1]), (float)(p[2] - sun[2])};
+            const float vh[3] = {(float)(v[0] - sun[3]), (float)(v[1] - sun[4]), (float)(v[2] - sun[5])};
+            const float rh = sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+            const float vn = sqrtf(vh[0] * vh[0] + vh[1] * vh[1] + vh[2] * vh[2]);
+            // time offsets from t_ref: frame epochs within tspan, light time below tau_max
+            const float T = (float)C.B.tspan[k] + (D + robs + 1.0f) * (float)kInvC;
+            // heliocentric displacement bound, valid while the body stays beyond rh/2
+            const float disp = vn * T + 2.0f * (float)C.mu_sun * T * T / (rh * rh);
+            const float s = (disp + (float)kSunSpeedMax * T) * 1.0001f + 1e-6f;
+            const bool all = (disp > 0.5f * rh) || (s + robs >= 0.99f * D) || (D < 0.05f);
+            const float rho = all ? (float)kPi : asinf((s + robs) / D);
+            const float R = rho + (float)C.B.rmax[k] + 4.0f * kPadF;
+            pb[0] = d[0]; pb[1] = d[1]; pb[2] = d[2];
+            s_eff = all ? 1e30f : s;
+            if (all || R >= 1.2f) {   // every exposure of the batch
+                u.mode = 1;
+                u.a = C.B.first[k];
+                u.b = C.B.first[k + 1];
+            } else {   // the cells within R of the body's direction from the mean observer
+                const CellGrid &G = C.G;
+                const float lat = asinf(fminf(1.0f, fmaxf(-1.0f, d[2] / D)));
+                float lon = atan2f(d[1], d[0]);
+                if (lon < 0.0f) lon += (float)kTwoPi;
+                const float hb = (float)G.hb;
+                int jlo = (int)floorf((lat - R + 0.5f * (float)kPi) / hb);
+                int jhi = (int)floorf((lat + R + 0.5f * (float)kPi) / hb);
+                jlo = jlo < 0 ? 0 : jlo;
+                jhi = jhi >= G.n_bands ? G.n_bands - 1 : jhi;
+                u.lon = lon;
+                if (fabsf(lat) + R >= 0.5f * (float)kPi - 1e-4f) u.dlon = (float)kPi;
+                else u.dlon = asinf(fminf(1.0f, sinf(R) / cosf(lat))) + 4.0f * kPadF;
+                u.mode = 2;
+                u.j = jlo - 1;
+                u.jhi = jhi;
+                u.r = u.nr = 0;
+                u.base = (int64_t)kl * G.n_cells;
+            }
+        }
     }
-    // enumerate the cells within R of the body's direction from the mean observer
-    const float lat = asinf(fminf(1.0f, fmaxf(-1.0f, d[2] / D)));
-    float lon = atan2f(d[1], d[0]);
-    if (lon < 0.0f) lon += (float)kTwoPi;
-    const CellGrid &G = C.G;
-    const float hb = (float)G.hb;
-    int jlo = (int)floorf((lat - R + 0.5f * (float)kPi) / hb);
-    int jhi = (int)floorf((lat + R + 0.5f * (float)kPi) / hb);
-    jlo = jlo < 0 ? 0 : jlo;
-    jhi = jhi >= G.n_bands ? G.n_bands - 1 : jhi;
-    float dlon;
-    if (fabsf(lat) + R >= 0.5f * (float)kPi - 1e-4f) dlon = (float)kPi;
-    else dlon = asinf(fminf(1.0f, sinf(R) / cosf(lat))) + 4.0f * kPadF;
-    const int64_t base = (int64_t)kl * G.n_cells;
-    for (int j = jlo; j <= jhi; j++) {
-        const int nj = G.band_n[j];
-        const float w = (float)kTwoPi / nj;
-        int ilo = (int)floorf((lon - dlon) / w), ihi = (int)floorf((lon + dlon) / w);
-        int nr = 0;
-        int64_t rl[2], rh2[2];
-        if (dlon >= (float)kPi || ihi - ilo + 1 >= nj) {
-            rl[0] = 0; rh2[0] = nj - 1; nr = 1;
-        } else if (ilo < 0) {
-            rl[0] = 0; rh2[0] = ihi; rl[1] = ilo + nj; rh2[1] = nj - 1; nr = 2;
-        } else if (ihi >= nj) {
-            rl[0] = ilo; rh2[0] = nj - 1; rl[1] = 0; rh2[1] = ihi - nj; nr = 2;
-        } else {
-            rl[0] = ilo; rh2[0] = ihi; nr = 1;
+    for (;;) {
+        cand_next_run(C, u);
+        const int cnt = u.mode ? (int)min(u.b - u.a, (int64_t)32) : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
         }
-        for (int r = 0; r < nr; r++) {
-            const int64_t lo_key = base + G.band_off[j] + rl[r];
-            const int64_t hi_key = base + G.band_off[j] + rh2[r];
-            const int64_t a = C.cell_start[lo_key], b = C.cell_start[hi_key + 1];
-            for (int64_t q = a; q < b; q++) test_exposure(C, C.cell_exp[q], pb, s, i);
+        const int total = __shfl_sync(FULL, incl, 31);
+        if (total == 0) break;
+        const int excl = incl - cnt;
+        // owner of slot `lane`: the first lane whose inclusive count exceeds it
+        int own = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int v = __shfl_sync(FULL, incl, own + step - 1);
+            if (v <= lane) own += step;
         }
+        own = own > 31 ? 31 : own;
+        const int off = lane - __shfl_sync(FULL, excl, own);
+        const int64_t a_o = __shfl_sync(FULL, u.a, own);
+        const int mode_o = __shfl_sync(FULL, u.mode, own);
+        const float q[3] = {__shfl_sync(FULL, pb[0], own), __shfl_sync(FULL, pb[1], own),
+                            __shfl_sync(FULL, pb[2], own)};
+        const float s_o = __shfl_sync(FULL, s_eff, own);
+        const int32_t body_o = __shfl_sync(FULL, body, own);
+        if (lane < total) {
+            const int32_t e = mode_o == 1 ? (int32_t)(a_o + off) : C.cell_exp[a_o + off];
+            test_exposure(C, e, q, s_o, body_o);
+        }
+        // each lane's tests taken this round
+        const int taken = min(max(32 - excl, 0), cnt);
+        u.a += taken;
     }
 }
 

@@ -180,18 +180,3 @@ def test_fov_check_with_nongrav_matches_oracle(K, mb1k_dense):
                            * math.cos(r[k]["dec"]), r[k]["dec"] - p[k]["dec"])
                 for k in set(r) & set(p))
     assert shift > 100 * MAS
-
-
-def test_adjoint_refuses_nongrav(K, pop):
-    from paper_2509_04666_gb300 import kete
-    w, ng = pop
-    K.load_ephem(w.ephem.to_bytes())
-    keep = kete.nongrav_to_device(ng[:4], "cuda")
-    fm = kete.force_model()
-    fm.nongrav = keep.data_ptr()
-    obs = np.zeros((4, 3), W.OBS_DTYPE)
-    obs["epoch"] = W.T0 + np.arange(1.0, 4.0)
-    obs_dev = _dev(np.ascontiguousarray(obs).view(np.float64).reshape(4, 3, 6))
-    with pytest.raises(kete.KeteError) as e:
-        K.adjoint(_dev(w.states[:, :4]), _dev(np.full(4, W.T0)), obs_dev, fm=fm)
-    assert e.value.code == kete.ERR_BAD_ARG
