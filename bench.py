@@ -611,7 +611,7 @@ def longspan_leg(args, K, dev, flush, stream):
     """Backward propagation over decades and centuries: 20,000 bodies of the
     survey population carried back 50 years, and 1,000 clones of a
     Jupiter-family comet (JPL comet model) carried back 170 years, one lane
-    per body against lane groups of 8 and 16."""
+    per body against lane groups of 4, 8 and 16."""
     import torch
     import oracle as O
     from paper_2509_04666_gb300 import kete, workloads as W
@@ -619,9 +619,10 @@ def longspan_leg(args, K, dev, flush, stream):
     legs = (("catalogue", W.backward_catalogue(n_bodies=args.back_bodies, years=50.0), None,
              (("fp64", kete.FP64, 0), ("mixed", kete.MIXED, 0))),
             ("clones", W.clones(n_clones=1000, years=170.0), "nongrav",
-             (("fp64", kete.FP64, 0), ("fp64_split8", kete.FP64, 8),
-              ("fp64_split16", kete.FP64, 16), ("mixed_split8", kete.MIXED, 8),
-              ("mixed_split16", kete.MIXED, 16))))
+             (("fp64", kete.FP64, 0), ("fp64_split4", kete.FP64, 4),
+              ("fp64_split8", kete.FP64, 8), ("fp64_split16", kete.FP64, 16),
+              ("mixed", kete.MIXED, 0), ("mixed_split4", kete.MIXED, 4),
+              ("mixed_split8", kete.MIXED, 8))))
     for leg, w, ngkey, variants in legs:
         n = w.n_bodies
         days = abs(w.t_end - W.T0)
