@@ -36,7 +36,14 @@ def test_fov_stage_roofline():
     stats = [{"n_candidates": 1000, "n_batches": 10, "exact_ms": 2.0, "cand_ms": 1.0}] * 3
     r = bench.fov_stage_roofline(stats, 500, 1.0, 5000.0)
     ex = r["exact"]
-    assert math.isclose(ex["achieved"], bench.EXACT_FLOPS_PER_CANDIDATE * 1000 / 2e-3 / 1e12)
+    # the ncu-counted work per candidate while the FoV sources are the profiled
+    # ones, the model otherwise
+    if bench.PROFILED_EXACT["src_sha"] == bench.fov_source_sha():
+        per, basis = bench.PROFILED_EXACT["fp64_flops_per_candidate"], "ncu-counted"
+    else:
+        per, basis = bench.EXACT_FLOPS_PER_CANDIDATE, "model"
+    assert ex["flops_per_candidate"] == per and ex["flops_basis"] == basis
+    assert math.isclose(ex["achieved"], per * 1000 / 2e-3 / 1e12)
     assert ex["frac"] == ex["achieved"] and ex["unit"] == "TFLOP/s"
     c = r["candidates"]
     assert c["bytes"] == 500 * 10 * 48 + 1000 * 16
