@@ -34,6 +34,7 @@ enum Slot {
     S_ORDER_SCAN, S_ORDER_N, S_ADJ_TEND, S_LEG_OUT,
     S_EXT_START, S_EXT_EX, S_EXT_TMP, S_EXT_FIRST, S_EXT_SUB, S_EXT_PARENT, S_EXT_CNT,
     S_EXT_OFF, S_EXT_CUR, S_EXT_GROUP, S_EXT_KEEP, S_EXT_KCNT, S_EXT_KOFF, S_ADJ_PHI, S_ADJ_RECX,
+    S_PRE_KEEP, S_PRE_N,
     S_NSLOTS
 };
 
@@ -974,7 +975,11 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
         CUDA_TRY(fov_cand_scatter((const uint2 *)ctx->slot[S_CAND].p, ncand, exp_off, e0, exp_cur, cand_body, st));
         phase_mark(ctx, PH_CAND, false);
         launches += 3;
-        // exact two-body + light time + polygon test
+        // exact two-body + light time + polygon test, after the FP32 prefilter
+        uint32_t *pre_keep;
+        unsigned long long *pre_n;
+        GET(S_PRE_KEEP, ncand, pre_keep);
+        GET(S_PRE_N, 1, pre_n);
         for (int attempt = 0; attempt < 3; attempt++) {
             CUDA_TRY(cudaMemcpyAsync(&ctx->d_ctr->hits, &hits_total, sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
             ExactArgs xa;
@@ -985,10 +990,12 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
             xa.hits = hit_tmp; xa.cap = hit_cap; xa.frame_cnt = frame_cnt; xa.status = cs.status;
             xa.ctr = ctx->d_ctr;
             xa.mag = mag;
+            xa.keep = pre_keep;
+            xa.n_keep = pre_n;
             phase_mark(ctx, PH_EXACT, true);
             CUDA_TRY(fov_exact(xa, ctx->n_sm, st));
             phase_mark(ctx, PH_EXACT, false);
-            launches++;
+            if (ncand > 0 && nek > 0) launches += ncand <= 0xffffffffull ? 2 : 1;
             unsigned long long nh = 0;
             CUDA_TRY(cudaMemcpyAsync(&nh, &ctx->d_ctr->hits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));

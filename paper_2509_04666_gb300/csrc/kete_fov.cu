@@ -596,7 +596,47 @@ struct ExactCtx {
     DevCounters *ctr;
     double cos_eps, sin_eps;
     const kete_mag_params *mag;
+    uint32_t *keep;                     // candidates kept by the prefilter (null: all)
+    unsigned long long *n_keep;
 };
+
+// The exposure, batch and body of candidate q and the body's heliocentric
+// batch state (shared by the prefilter and the exact test).
+struct CandSetup {
+    int32_t e, k, kl, f0, f1, i;
+    double dt_obs, o[3], sun_obs[6], hr[3], hv[3];
+};
+
+__device__ __forceinline__ void cand_setup(const ExactCtx &C, int64_t q, CandSetup &S)
+{
+    const int32_t nexp = C.e_end - C.e_begin;
+    // the exposure of candidate q: the last el with exp_off[el] <= q
+    int32_t lo = 0, hi = nexp - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(C.exp_off + mid) <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    const int32_t e = C.e_begin + lo;
+    S.e = e;
+    S.k = C.X.batch[e];
+    S.kl = S.k - C.k0;
+    S.dt_obs = C.X.epoch[e] - C.B.t_ref[S.k];
+#pragma unroll
+    for (int c = 0; c < 3; c++) S.o[c] = C.X.obs[3 * e + c];
+#pragma unroll
+    for (int c = 0; c < 6; c++) S.sun_obs[c] = C.X.sun[6 * e + c];
+    S.f0 = C.exp_first[e];
+    S.f1 = C.exp_first[e + 1];
+    S.i = C.cand_body[q];
+    const double *st = C.stop_states + ((int64_t)S.kl * C.n + S.i) * 6;
+    const double *sun = C.B.sun + 6 * S.k;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        S.hr[c] = st[c] - sun[c];
+        S.hv[c] = st[3 + c] - sun[3 + c];
+    }
+}
 
 // Apparent magnitude (Sec. 3.3; comet appendix) from the heliocentric
 // position p of the body at emission and the apparent vector u (|u| = dl):
@@ -689,39 +729,112 @@ __device__ __forceinline__ void twobody_pos(const TwoBodyLT &T, const double *su
 // Candidates are grouped by exposure (CSR exp_off), so neighbouring threads
 // mostly share an exposure and its data; every lane has a candidate of its
 // own whatever the exposures' candidate counts.
+// FP32 prefilter of a candidate before its two-body solve.  From the
+// body's heliocentric batch state (hr, hv) a second-order Taylor step gives
+// its position at the exposure epoch, retarded by the light time as the exact
+// path does (p(t - tau) ~ p(t) - tau v(t), the Sun moved by -tau v_sun).  The
+// distance E to the exact position is bounded by
+//   J s^3 / 6 + a_max tau^2 / 2           (Taylor remainder, s = |dt| + tau;
+//                                          J = 4 mu v_max / r_min^3 bounds
+//                                          |da/dt| of two-body motion)
+// + FP32 rounding (and the light time's own error, a relative 1e-3 of it),
+// valid while the body stays beyond r_min = r/2 (displacement within the
+// interval below r/2; otherwise no cheap bound and the candidate goes on).
+// The predicted direction is then within theta = E / (|u| - E) of the exact
+// one, so a candidate whose predicted direction misses every sub-field's
+// FP32 cap by more than theta (plus the FP32 dot products' rounding) fails
+// the exact path's cap test too, and is not a hit.
+__device__ __forceinline__ bool exact_prefilter(const ExactCtx &C, const double hr[3],
+                                                const double hv[3], double dt,
+                                                const double sun_obs[6], const double o[3],
+                                                int32_t f0, int32_t f1, double mu)
+{
+    const float muf = (float)mu;
+    const float r[3] = {(float)hr[0], (float)hr[1], (float)hr[2]};
+    const float v[3] = {(float)hv[0], (float)hv[1], (float)hv[2]};
+    const float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    const float rn = sqrtf(rr);
+    const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const float adt = fabsf((float)dt);
+    const float so[3] = {(float)(sun_obs[0] - o[0]), (float)(sun_obs[1] - o[1]),
+                         (float)(sun_obs[2] - o[2])};
+    const float son = sqrtf(so[0] * so[0] + so[1] * so[1] + so[2] * so[2]);
+    // light time bound: the body is within rn + son + motion of the observer
+    const float tmax = (rn + son + vn * adt + 1.0f) * (float)kInvC * 1.01f;
+    const float s = adt + tmax;
+    const float rmin = 0.5f * rn;
+    const float amax = muf / (rmin * rmin);
+    if (!(vn * s + 0.5f * amax * s * s <= rmin)) return true;   // no cheap bound
+    const float vmax = vn + amax * s;
+    const float J = 4.0f * muf * vmax / (rmin * rmin * rmin);
+    // position at the exposure epoch (heliocentric, FP32)
+    const float dtf = (float)dt;
+    const float k = -muf / (rr * rn);                  // a = k r
+    const float h2 = 0.5f * dtf * dtf * k;
+    float p[3], vt[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        p[c] = fmaf(v[c], dtf, fmaf(h2, r[c], r[c]));
+        vt[c] = fmaf(k * dtf, r[c], v[c]) + (float)sun_obs[3 + c];   // body + Sun velocity
+    }
+    float u[3] = {so[0] + p[0], so[1] + p[1], so[2] + p[2]};
+    float tau = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * (float)kInvC;
+#pragma unroll
+    for (int it = 0; it < 2; it++) {
+        float w[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) w[c] = fmaf(-tau, vt[c], u[c]);
+        tau = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]) * (float)kInvC;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) u[c] = fmaf(-tau, vt[c], u[c]);
+    const float un = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    // bound on the distance to the exact retarded position; the light time's
+    // own error (that distance over c) moves the position by at most
+    // |v| / c < 1e-3 of it, hence the factor
+    const float E = 1.001f * (J * s * s * s * (1.0f / 6.0f) + 0.5f * amax * tmax * tmax +
+                              2e-6f * (rn + son + un + vn * adt)) + 1e-9f;
+    if (!(E < 0.5f * un)) return true;
+    const float theta = E / (un - E) + 2e-6f;
+    const float iu = 1.0f / un;
+    const float uh[3] = {u[0] * iu, u[1] * iu, u[2] * iu};
+    for (int32_t f = f0; f < f1; f++) {
+        const float4 a = __ldg(C.faux + f);
+        if (a.x * uh[0] + a.y * uh[1] + a.z * uh[2] >= a.w - theta) return true;
+    }
+    return false;
+}
+
+// The prefilter pass: thread per candidate; the candidates it keeps are
+// appended to C.keep (warp-aggregated), so that the exact pass runs them with
+// full lanes (an FP64 warp instruction costs the same whatever its active
+// lanes: a rejection inside the exact pass would save nothing).
+__global__ void __launch_bounds__(128) k_exact_prefilter(ExactCtx C)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= C.n_cand) return;
+    CandSetup S;
+    cand_setup(C, q, S);
+    if (exact_prefilter(C, S.hr, S.hv, S.dt_obs, S.sun_obs, S.o, S.f0, S.f1, C.E.gm[0])) {
+        const unsigned long long slot = agg_append(C.n_keep);
+        C.keep[slot] = (uint32_t)q;
+    }
+}
+
 __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
 {
-    const int32_t nexp = C.e_end - C.e_begin;
     const double mu = C.E.gm[0];
     const double sqmu = sqrt(mu);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < C.n_cand; q += stride) {
-        // the exposure of candidate q: the last el with exp_off[el] <= q
-        int32_t lo = 0, hi = nexp - 1;
-        while (lo < hi) {
-            const int32_t mid = (lo + hi + 1) >> 1;
-            if (__ldg(C.exp_off + mid) <= q) lo = mid;
-            else hi = mid - 1;
-        }
-        const int32_t el = lo;
-        const int32_t e = C.e_begin + el;
-        const int32_t k = C.X.batch[e];
-        const int32_t kl = k - C.k0;
-        const double t_ref = C.B.t_ref[k];
-        const double dt_obs = C.X.epoch[e] - t_ref;
-        const double o[3] = {C.X.obs[3 * e], C.X.obs[3 * e + 1], C.X.obs[3 * e + 2]};
-        const double *sun = C.B.sun + 6 * k;
-        const double sun_obs[6] = {C.X.sun[6 * e], C.X.sun[6 * e + 1], C.X.sun[6 * e + 2],
-                                   C.X.sun[6 * e + 3], C.X.sun[6 * e + 4], C.X.sun[6 * e + 5]};
-        const int32_t f0 = C.exp_first[e], f1 = C.exp_first[e + 1];
+    const int64_t n_work = C.keep ? (int64_t)*C.n_keep : C.n_cand;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_work; j += stride) {
+        const int64_t q = C.keep ? (int64_t)C.keep[j] : j;
+        CandSetup S;
+        cand_setup(C, q, S);
+        const int32_t f0 = S.f0, f1 = S.f1, i = S.i;
+        const double dt_obs = S.dt_obs;
+        const double *o = S.o, *sun_obs = S.sun_obs, *hr = S.hr, *hv = S.hv;
         {
-            const int32_t i = C.cand_body[q];
-            const double *st = C.stop_states + ((int64_t)kl * C.n + i) * 6;
-            double hr[3], hv[3];
-            for (int c = 0; c < 3; c++) {
-                hr[c] = st[c] - sun[c];
-                hv[c] = st[3 + c] - sun[3 + c];
-            }
             // light delay (Sec. 2): tau0 = |r(t)-o|/c, three fixed iterations
             double chi = 0.0, pos[3];
             TwoBodyLT T;
@@ -1059,11 +1172,20 @@ cudaError_t fov_exact(const ExactArgs &a, int n_sm, cudaStream_t st)
     C.e_end = a.e_end; C.exp_off = a.exp_off; C.n_cand = a.n_cand; C.cand_body = a.cand_body;
     C.exp_first = a.exp_first; C.hits = a.hits; C.cap = a.cap; C.frame_cnt = a.frame_cnt;
     C.status = a.status; C.ctr = a.ctr; C.mag = a.mag;
+    // the prefilter stores 32-bit candidate indices
+    const bool pre = a.keep && a.n_keep && a.n_cand <= (int64_t)UINT32_MAX;
+    C.keep = pre ? a.keep : nullptr;
+    C.n_keep = pre ? a.n_keep : nullptr;
     const double eps = 84381.448 / 3600.0 * (kPi / 180.0);
     C.cos_eps = cos(eps);
     C.sin_eps = sin(eps);
     int64_t nexp = a.e_end - a.e_begin;
     if (nexp <= 0 || a.n_cand <= 0) return cudaSuccess;
+    if (pre) {
+        const cudaError_t e = cudaMemsetAsync(a.n_keep, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+        KLAUNCH(k_exact_prefilter<<<(unsigned)((a.n_cand + 127) / 128), 128, 0, st>>>(C));
+    }
     int64_t blocks = (a.n_cand + 127) / 128;
     int64_t cap_blocks = (int64_t)n_sm * 16;
     if (blocks > cap_blocks) blocks = cap_blocks;

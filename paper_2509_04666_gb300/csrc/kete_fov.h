@@ -75,6 +75,10 @@ struct ExactArgs {
     int32_t *status;
     DevCounters *ctr;
     const kete_mag_params *mag = nullptr;   // [n] magnitude models, or null
+    // scratch of the prefilter pass (null: no prefilter): the indices of the
+    // candidates it keeps ([n_cand]) and their count
+    uint32_t *keep = nullptr;
+    unsigned long long *n_keep = nullptr;
 };
 
 cudaError_t fov_frame_prep(const kete_frame *frames, int64_t nf, int64_t n_obs, int32_t *is_start,
