@@ -43,10 +43,10 @@ MAS = math.radians(1.0 / 3.6e6)
 PROFILED_TRAFFIC = {"src_sha": "5daa2e5f92c9841a", "bytes_per_body_stop": 66.1}
 
 
-# FP64 work of the exact FoV test per candidate as ncu counts it (2 x DFMA +
-# DMUL + DADD thread instructions over the timed launch of the same small case,
-# divided by its candidates); valid only while the FoV kernels' source is
-# unchanged.  The modelled count below leaves out the divisions, square roots
+# FP64 work of the exact FoV test per candidate it solves as ncu counts it (2 x
+# DFMA + DMUL + DADD thread instructions of the timed k_exact launch of the
+# same small case, divided by the candidates the prefilter passed to it); valid
+# only while the FoV kernels' source is unchanged.  The modelled count below leaves out the divisions, square roots
 # and convergence tests that the executed count includes.
 PROFILED_EXACT = {"src_sha": "144d5cc6c7577198", "fp64_flops_per_candidate": 894.2}
 
@@ -223,23 +223,26 @@ EXACT_FLOPS_PER_CANDIDATE = 25 + 4 * 55 + 70 + 30 + 5 * 33 + 20
 
 def fov_stage_roofline(stats, n_bodies, peak_fp64_tflops, hbm_gbs):
     """Rooflines of the FoV stage's two kernels from the call's counters:
-    k_exact against the FP64 peak (its FP64 work per candidate as ncu counts
-    it while the kernel source matches the profile, else the model
-    EXACT_FLOPS_PER_CANDIDATE), the candidate search against HBM (per body
-    and batch the 48-B stop state read, per candidate 8 B written and read
-    back)."""
+    the exact test against the FP64 peak (its FP64 work per candidate that
+    the FP32 prefilter passed on to the two-body solve, as ncu counts it while
+    the kernel source matches the profile, else the model
+    EXACT_FLOPS_PER_CANDIDATE; the prefilter's FP32 work is left out), the
+    candidate search against HBM (per body and batch the 48-B stop state
+    read, per candidate 8 B written and read back)."""
     cand = statistics.mean(s["n_candidates"] for s in stats)
+    tested = statistics.mean(s.get("n_exact", s["n_candidates"]) for s in stats)
     batches = stats[-1]["n_batches"]
     exact_ms = statistics.mean(s["exact_ms"] for s in stats)
     cand_ms = statistics.mean(s["cand_ms"] for s in stats)
     per, basis = EXACT_FLOPS_PER_CANDIDATE, "model"
     if PROFILED_EXACT["src_sha"] == fov_source_sha() and PROFILED_EXACT["fp64_flops_per_candidate"]:
         per, basis = PROFILED_EXACT["fp64_flops_per_candidate"], "ncu-counted"
-    ex = per * cand / (exact_ms / 1e3) / 1e12
+    ex = per * tested / (exact_ms / 1e3) / 1e12
     cbytes = n_bodies * batches * 48.0 + cand * 16.0
     cgbs = cbytes / (cand_ms / 1e3) / 1e9
     return {"exact": {"bound": "alu", "achieved": ex, "peak": peak_fp64_tflops, "unit": "TFLOP/s",
-                      "frac": ex / peak_fp64_tflops, "candidates": cand, "ms": exact_ms,
+                      "frac": ex / peak_fp64_tflops, "candidates": cand,
+                      "past_prefilter": tested, "ms": exact_ms,
                       "flops_per_candidate": per, "flops_basis": basis},
             "candidates": {"bound": "hbm", "achieved": cgbs, "peak": hbm_gbs, "unit": "GB/s",
                            "frac": cgbs / hbm_gbs if hbm_gbs else None,

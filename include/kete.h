@@ -187,6 +187,8 @@ typedef struct kete_stats {
     int64_t prop_budget;         /* step attempts per stop before a body is set aside */
     int64_t deferred;            /* bodies set aside and finished by the split phase */
     int64_t prop_order;          /* 1: bodies were taken most expensive first */
+    int64_t n_exact;             /* candidates the FP32 prefilter passed on to the FP64
+                                    two-body solve (the rest cannot be hits) */
 } kete_stats;
 
 /* propagation launch variants (kete_set_propagation, kete_autotune) */

@@ -915,7 +915,7 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
     r = node_table(ctx, B.t_ref, nb, epochs, nt);
     if (r != KETE_OK) return r;
     launches++;
-    unsigned long long hits_total = 0, cands_total = 0;
+    unsigned long long hits_total = 0, cands_total = 0, exact_total = 0;
     for (int32_t k0 = 0; k0 < nb; k0 += C) {
         const int32_t k1 = std::min(nb, k0 + C), nk = k1 - k0;
         const int32_t e0 = h_first[k0], e1 = h_first[k1];
@@ -996,11 +996,14 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
             CUDA_TRY(fov_exact(xa, ctx->n_sm, st));
             phase_mark(ctx, PH_EXACT, false);
             if (ncand > 0 && nek > 0) launches += ncand <= 0xffffffffull ? 2 : 1;
-            unsigned long long nh = 0;
+            unsigned long long nh = 0, nkept = ncand;
             CUDA_TRY(cudaMemcpyAsync(&nh, &ctx->d_ctr->hits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            if (ncand > 0 && nek > 0 && ncand <= 0xffffffffull)
+                CUDA_TRY(cudaMemcpyAsync(&nkept, pre_n, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));
             if (nh <= hit_cap) {
                 hits_total = nh;
+                exact_total += nkept;
                 break;
             }
             // grow the hit buffer, keep earlier chunks' hits, redo this chunk
@@ -1026,6 +1029,7 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
     ctx->stats.n_batches = nb;
     ctx->stats.n_exposures = ne;
     ctx->stats.n_candidates = (int64_t)cands_total;
+    ctx->stats.n_exact = (int64_t)exact_total;
     ctx->stats.n_hits = (int64_t)hits_total;
     *n_hits = (int64_t)hits_total;
     CUDA_TRY(launch_chain_finish(cs, nullptr, nullptr, status, st));
@@ -1046,6 +1050,7 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
         ctx->stats.n_batches = nb;
         ctx->stats.n_exposures = ne;
         ctx->stats.n_candidates = (int64_t)cands_total;
+    ctx->stats.n_exact = (int64_t)exact_total;
         ctx->stats.n_hits = *n_hits;
         ctx->stats.launches = launches + ctx->extra_launches;
         return KETE_OK;
@@ -1075,6 +1080,7 @@ static int fov_check_impl(kete_ctx *ctx, const double *states, const double *epo
     ctx->stats.n_batches = nb;
     ctx->stats.n_exposures = ne;
     ctx->stats.n_candidates = (int64_t)cands_total;
+    ctx->stats.n_exact = (int64_t)exact_total;
     ctx->stats.n_hits = (int64_t)hits_total;
     ctx->stats.launches = launches + ctx->extra_launches;
     return KETE_OK;

@@ -63,7 +63,8 @@ class Stats(C.Structure):
                 ("launches", C.c_int64), ("prep_ms", C.c_double), ("cand_ms", C.c_double),
                 ("exact_ms", C.c_double), ("order_ms", C.c_double), ("node_evals", C.c_int64),
                 ("prop_kind", C.c_int64), ("prop_block", C.c_int64), ("prop_split", C.c_int64),
-                ("prop_budget", C.c_int64), ("deferred", C.c_int64), ("prop_order", C.c_int64)]
+                ("prop_budget", C.c_int64), ("deferred", C.c_int64), ("prop_order", C.c_int64),
+                ("n_exact", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
