@@ -744,7 +744,13 @@ __device__ __forceinline__ void twobody_pos(const TwoBodyLT &T, const double *su
 // one, so a candidate whose predicted direction misses every sub-field's
 // FP32 cap by more than theta (plus the FP32 dot products' rounding) fails
 // the exact path's cap test too, and is not a hit.
-__device__ __forceinline__ bool exact_prefilter(const ExactCtx &C, const double hr[3],
+// An exposure of several sub-fields is tested first against its covering cap
+// (radius rad >= angle(centre, c_k) + r_k for every sub-field k): a direction
+// that passes sub-field k's FP32 test is within r_k + kPadF + 3e-3 of c_k
+// (the test's 2e-6 cosine slack plus FP32 rounding widen the angle by at most
+// sqrt(2 x 2.4e-6) < 3e-3), hence within rad + kPadF + 3e-3 of the centre, and
+// the predicted direction within theta more.
+__device__ __forceinline__ bool exact_prefilter(const ExactCtx &C, int32_t e, const double hr[3],
                                                 const double hv[3], double dt,
                                                 const double sun_obs[6], const double o[3],
                                                 int32_t f0, int32_t f1, double mu)
@@ -798,6 +804,15 @@ __device__ __forceinline__ bool exact_prefilter(const ExactCtx &C, const double 
     const float theta = E / (un - E) + 2e-6f;
     const float iu = 1.0f / un;
     const float uh[3] = {u[0] * iu, u[1] * iu, u[2] * iu};
+    if (f1 - f0 > 1) {
+        const float2 cs = C.X.cs[e];
+        if (cs.x > -1.5f) {
+            const float phi = kPadF + 3e-3f + theta;
+            const float lim = cs.x * cosf(phi) - cs.y * sinf(phi) - 2e-6f;   // cos(rad + phi)
+            const float4 c = C.X.cenf[e];
+            if (c.x * uh[0] + c.y * uh[1] + c.z * uh[2] < lim) return false;
+        }
+    }
     for (int32_t f = f0; f < f1; f++) {
         const float4 a = __ldg(C.faux + f);
         if (a.x * uh[0] + a.y * uh[1] + a.z * uh[2] >= a.w - theta) return true;
@@ -815,7 +830,7 @@ __global__ void __launch_bounds__(128) k_exact_prefilter(ExactCtx C)
     if (q >= C.n_cand) return;
     CandSetup S;
     cand_setup(C, q, S);
-    if (exact_prefilter(C, S.hr, S.hv, S.dt_obs, S.sun_obs, S.o, S.f0, S.f1, C.E.gm[0])) {
+    if (exact_prefilter(C, S.e, S.hr, S.hv, S.dt_obs, S.sun_obs, S.o, S.f0, S.f1, C.E.gm[0])) {
         const unsigned long long slot = agg_append(C.n_keep);
         C.keep[slot] = (uint32_t)q;
     }
