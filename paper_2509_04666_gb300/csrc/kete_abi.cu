@@ -1214,7 +1214,7 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
         cands[n_cands++].order = 1;
     }
     const PropVariant saved = ctx->var[F.precision == KETE_MIXED ? 1 : 0];
-    float best_ms = 1e30f;
+    float best_ms = 1e30f, saved_ms = -1.0f;
     PropVariant best = saved;
     cudaEvent_t e0 = event_at(ctx, 0), e1 = event_at(ctx, 1);
     for (int c = 0; c < n_cands; c++) cands[c].grid_scale = scale;
@@ -1242,7 +1242,14 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
             best_ms = ms;
             best = cands[c];
         }
+        if (cands[c].kind == saved.kind && cands[c].block == saved.block &&
+            cands[c].split == saved.split && cands[c].budget == saved.budget &&
+            cands[c].order == saved.order)
+            saved_ms = ms;
     }
+    // the sample's timings differ by a few per cent from run to run: the
+    // variant in use stays unless another beats it by more than 3 %
+    if (saved_ms > 0.0f && best_ms > 0.97f * saved_ms) best = saved;
     best.grid_scale = 1.0;
     ctx->var[F.precision == KETE_MIXED ? 1 : 0] = best;
     if (kind) *kind = best.kind;
