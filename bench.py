@@ -48,7 +48,7 @@ PROFILED_TRAFFIC = {"src_sha": "5daa2e5f92c9841a", "bytes_per_body_stop": 66.1}
 # same small case, divided by the candidates the prefilter passed to it); valid
 # only while the FoV kernels' source is unchanged.  The modelled count below leaves out the divisions, square roots
 # and convergence tests that the executed count includes.
-PROFILED_EXACT = {"src_sha": "144d5cc6c7577198", "fp64_flops_per_candidate": 894.2}
+PROFILED_EXACT = {"src_sha": "0e2f887dfeee92fc", "fp64_flops_per_candidate": 924.9}
 
 # FP64 arithmetic thread instructions (DFMA + DMUL + DADD) the FP64 survey's
 # propagation kernel executes per accepted step, from the same ncu capture as
