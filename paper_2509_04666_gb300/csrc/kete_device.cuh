@@ -32,6 +32,9 @@ struct RadauTables {
     double w7[8];        // 1 / prod_{k != n} (h_n - h_k): b6 = g7 = sum_n w7[n] F_n
     double wx[8][7];     // h_n^(k+1) / ((k+2)(k+3)): weight of b_k in x at node n
     double wv[8][7];     // h_n^(k+1) / (k+2): weight of b_k in v at node n
+    // FP32 copies for the mixed-precision node velocity (it feeds only FP32
+    // terms there; an FP64 -> FP32 conversion costs an FP64 issue slot)
+    float cf[8][7], wvf[8][7];
 };
 
 // ---------------------------------------------------------------------------
@@ -491,7 +494,8 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
                                            const float *__restrict__ row32, uint32_t &close,
                                            const double x[3], const double v[3], double a[3],
                                            double as[3], Encounter &enc, const double dx[3],
-                                           bool detect, const kete_nongrav *ng = nullptr)
+                                           bool detect, const kete_nongrav *ng = nullptr,
+                                           const float *vf_in = nullptr)
 {
     Seg g = {0, 0.0};
     as[0] = as[1] = as[2] = 0.0;
@@ -510,9 +514,9 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
     if (row64) {
 #pragma unroll
         for (int q = 0; q < 3; q++) sun[q] = __ldg(row64 + q);
-        if (sun_gr) {
+        if (sun_gr) {   // the FP32 row holds the same velocity, already rounded
 #pragma unroll
-            for (int q = 0; q < 3; q++) sunv[q] = (float)__ldg(row64 + 3 + q);
+            for (int q = 0; q < 3; q++) sunv[q] = row32 ? __ldg(row32 + 3 + q) : (float)__ldg(row64 + 3 + q);
         }
     } else {
         cheb_state64(E, 0, g.s, g.tau, sun, false);
@@ -524,7 +528,11 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
     }
     const double d[3] = {x[0] - sun[0], x[1] - sun[1], x[2] - sun[2]};
     const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
-    const float vf[3] = {(float)v[0], (float)v[1], (float)v[2]};
+    // the body's velocity enters only FP32 terms: taken in FP32 when the
+    // caller has it (vf_in), else rounded here
+    float vf[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) vf[c] = vf_in ? vf_in[c] : (float)v[c];
     float af[3] = {0.f, 0.f, 0.f};
     const int rk = LaneGroup<G>::rank();
     if (rk == 0 && (F.active_mask & 1u)) {
@@ -542,7 +550,13 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
             mass_terms<float>(F.gm32[0], F.j2k32[0], F.pole32[0], false, sun_gr, j2, df, w, af);
         }
     }
-    const float sunf[3] = {(float)sun[0], (float)sun[1], (float)sun[2]};
+    // the Sun in FP32 only for the per-thread planet series (node rows are
+    // already Sun-relative)
+    float sunf[3] = {0.f, 0.f, 0.f};
+    if (!row32) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) sunf[q] = (float)sun[q];
+    }
     const float tau32 = row64 ? 0.f : (float)g.tau;
     for (int m = (rk == 0 ? G : rk); m < E.n_bodies; m += G) {
         if (!((F.active_mask >> m) & 1u)) continue;
@@ -585,7 +599,11 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
                 r64[1] = enc.d0[1] + (dx[1] - dp[1]);
                 r64[2] = enc.d0[2] + (dx[2] - dp[2]);
             }
-            double w[3] = {v[0] - s64[3], v[1] - s64[4], v[2] - s64[5]};
+            // (the body's velocity as the FP32 terms see it when it came in FP32:
+            // it enters only the GR term, 1e-8 of the planet's pull)
+            double w[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) w[c] = (vf_in ? (double)vf[c] : v[c]) - s64[3 + c];
             mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r64, w, as);
             continue;
         }

@@ -51,7 +51,7 @@ void upload_radau_tables(cudaStream_t st) { upload_step_tables(st); }
 // to q.defer) for a second launch with more lanes per body.
 // NG: bodies may carry non-gravitational terms (F.nongrav); the instantiation
 // without them has those branches compiled out.
-template <int MODE, int G, bool NG>
+template <int MODE, int G, bool NG, bool V32 = false>
 __global__ void __launch_bounds__(128, KETE_PROP_MIN_BLOCKS)
 k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ stops,
             int n_stops, double *__restrict__ out, int64_t out_stride, int out_aos,
@@ -150,7 +150,7 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
         // one corrector sweep for every group inside an attempt
         if (in_attempt) {
             bool done = false;
-            status = attempt_sweep<MODE, false, G>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, A,
+            status = attempt_sweep<MODE, false, G, V32>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, A,
                                                    done, cnt, nullptr, S.ng);
             if (status != KETE_BODY_OK) {
                 in_attempt = false;
@@ -352,8 +352,12 @@ static void launch_k(int64_t grid, int block, cudaStream_t st, const EphemDev &E
                      double *out, int64_t stride, int aos, int kof, DevCounters *ctr, NodeTable t,
                      int unt, int leg0, unsigned long long *next, int refill, PropQueue q)
 {
+    // mixed precision with node rows: the node velocity in FP32 (V32)
     if (F.nongrav)
         k_propagate<MODE, G, true><<<(unsigned)grid, block, 0, st>>>(
+            E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
+    else if (MODE == KETE_MIXED && G == 1 && unt)
+        k_propagate<MODE, G, false, true><<<(unsigned)grid, block, 0, st>>>(
             E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
     else
         k_propagate<MODE, G, false><<<(unsigned)grid, block, 0, st>>>(

@@ -46,7 +46,10 @@ static inline void fill_radau_tables(RadauTables &t)
             }
             std::memcpy(poly, nxt, sizeof(poly));
         }
-        for (int m = 0; m < 7; m++) t.c[n][m] = (m < n) ? poly[m] : 0.0;
+        for (int m = 0; m < 7; m++) {
+            t.c[n][m] = (m < n) ? poly[m] : 0.0;
+            t.cf[n][m] = (float)t.c[n][m];
+        }
     }
     // predictor weights of the power-basis coefficients at each node
     for (int n = 0; n < 8; n++) {
@@ -54,6 +57,7 @@ static inline void fill_radau_tables(RadauTables &t)
         for (int k = 0; k < 7; k++) {
             t.wx[n][k] = sp / ((k + 2.0) * (k + 3.0));
             t.wv[n][k] = sp / (k + 2.0);
+            t.wvf[n][k] = (float)t.wv[n][k];
             sp *= kRadauH[n];
         }
     }
@@ -96,11 +100,13 @@ __device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, doubl
                                      const double *row64, const float *row32, uint32_t &close,
                                      const double x[3], const double v[3], double a[3],
                                      double as[3], Encounter &enc, const double dx[3], bool detect,
-                                     double *jout = nullptr, const kete_nongrav *ng = nullptr)
+                                     double *jout = nullptr, const kete_nongrav *ng = nullptr,
+                                     const float *vf = nullptr)
 {
     static_assert(!(JAC && MODE == KETE_MIXED), "Jacobian capture is FP64 only");
     if (MODE == KETE_MIXED)
-        return accel_mixed<G>(E, F, t0, off, row64, row32, close, x, v, a, as, enc, dx, detect, ng);
+        return accel_mixed<G>(E, F, t0, off, row64, row32, close, x, v, a, as, enc, dx, detect, ng,
+                              vf);
     double J[6];
     int st = accel_fp64<JAC, G>(E, F, t0, off, row64, x, v, a, enc, dx, detect, J, ng);
     as[0] = a[0]; as[1] = a[1]; as[2] = a[2];
@@ -117,6 +123,7 @@ __device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, doubl
 // the planets come from the node rows (node n at rows.r64 + n * stride).
 struct Attempt {
     double b[7][3], g[7][3];
+    float bf[7][3];         // mixed precision: b in FP32, for the node velocity
     double gs7[3];          // mixed precision: b6 of the FP64 part, last sweep
     double amax, pc_prev;   // max|a| at the last node and the last convergence measure
     double h, t_new;
@@ -129,7 +136,10 @@ __device__ __forceinline__ void attempt_begin(Attempt &A, double h, double t_new
 #pragma unroll
     for (int m = 0; m < 7; m++)
 #pragma unroll
-        for (int i = 0; i < 3; i++) A.b[m][i] = A.g[m][i] = 0.0;
+        for (int i = 0; i < 3; i++) {
+            A.b[m][i] = A.g[m][i] = 0.0;
+            A.bf[m][i] = 0.0f;
+        }
     A.gs7[0] = A.gs7[1] = A.gs7[2] = 0.0;
     A.amax = 0.0;
     A.pc_prev = 0.0;
@@ -142,7 +152,7 @@ __device__ __forceinline__ void attempt_begin(Attempt &A, double h, double t_new
 // The corrector update at node N (compile-time): Newton divided difference
 // g_{N-1} from the node's force and the earlier g, then the power-basis
 // coefficients b.
-template <int MODE, int N>
+template <int MODE, int N, bool V32 = false>
 __device__ __forceinline__ void node_update(Attempt &A, const double Fn[3], const double Fs[3],
                                             const double a0[3], double F7[3])
 {
@@ -155,17 +165,22 @@ __device__ __forceinline__ void node_update(Attempt &A, const double Fn[3], cons
         A.g[N - 1][i] = gn;
 #pragma unroll
         for (int m = 0; m < N; m++) A.b[m][i] = fma(g_rt.c[N][m], dg, A.b[m][i]);
+        if (MODE == KETE_MIXED && V32) {
+            const float dgf = (float)dg;
+#pragma unroll
+            for (int m = 0; m < N; m++) A.bf[m][i] = fmaf(g_rt.cf[N][m], dgf, A.bf[m][i]);
+        }
         if (N == 7) F7[i] = Fn[i];
         if (MODE == KETE_MIXED) A.gs7[i] = fma(g_rt.w7[N], Fs[i], A.gs7[i]);
     }
 }
 
 // One corrector sweep of the attempt from (t, x0, v0) with a0 = a(t, x0, v0)
-// (as0: its FP64 part).  Sets done when the corrector has converged
+// (as0: its FP64 part).  V32: see vel32 below.  Sets done when the corrector has converged
 // (max|db6|/max|a| < eps_pc), stopped improving (from the third sweep) or
 // reached max_iter sweeps.  JAC: every node evaluation also stores da/dx at
 // node n to jrec[6n..6n+5]; the last sweep's values remain.
-template <int MODE, bool JAC = false, int G = 1>
+template <int MODE, bool JAC = false, int G = 1, bool V32 = false>
 __device__ __forceinline__ int attempt_sweep(const EphemDev &E, const ForceDev &F, double t,
                                              const double x0[3], const double v0[3],
                                              const double a0[3], const double as0[3],
@@ -176,9 +191,22 @@ __device__ __forceinline__ int attempt_sweep(const EphemDev &E, const ForceDev &
     const double h = A.h;
     double b6o[3] = {A.b[6][0], A.b[6][1], A.b[6][2]};
     double F7[3];
+    // V32 (mixed precision, launches with node rows): without non-gravitational
+    // terms the node velocity feeds only FP32 terms, so it is predicted in FP32
+    // from A.bf (kept only in these launches: the extra registers cost the
+    // per-thread-ephemeris launches more than the FP64 work they save)
+    const bool vel32 = (MODE == KETE_MIXED) && V32 && !ng;
+    float v0f[3], a0f[3];
     if (MODE == KETE_MIXED) {
 #pragma unroll
         for (int i = 0; i < 3; i++) A.gs7[i] = g_rt.w7[0] * as0[i];
+        if (vel32) {
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                v0f[i] = (float)v0[i];
+                a0f[i] = (float)a0[i];
+            }
+        }
     }
     // one copy of the force evaluation: the node index is the same for every
     // lane of the sweep (uniform table reads, uniform guards below)
@@ -187,40 +215,49 @@ __device__ __forceinline__ int attempt_sweep(const EphemDev &E, const ForceDev &
         const double s = g_rt.h[n];
         const double sh = s * h;
         double xn[3], vn[3], dxn[3];
+        float vnf[3];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             // x(s) = x0 + s h v0 + (s h)^2 [a0/2 + sum_k b_k s^(k+1) / ((k+2)(k+3))]
             // v(s) = v0 + s h [a0 + sum_k b_k s^(k+1) / (k+2)]
             // with the node's weights from the table (smallest terms first)
             double px = A.b[6][i] * g_rt.wx[n][6];
-            double pv = A.b[6][i] * g_rt.wv[n][6];
 #pragma unroll
-            for (int k = 5; k >= 0; k--) {
-                px = fma(A.b[k][i], g_rt.wx[n][k], px);
-                pv = fma(A.b[k][i], g_rt.wv[n][k], pv);
-            }
+            for (int k = 5; k >= 0; k--) px = fma(A.b[k][i], g_rt.wx[n][k], px);
             px = fma(a0[i], 0.5, px);
-            pv = pv + a0[i];
             dxn[i] = fma(sh * sh, px, sh * v0[i]);   // displacement since the step start
             xn[i] = x0[i] + dxn[i];
-            vn[i] = fma(sh, pv, v0[i]);
+            if (vel32) {
+                float pv = A.bf[6][i] * g_rt.wvf[n][6];
+#pragma unroll
+                for (int k = 5; k >= 0; k--) pv = fmaf(A.bf[k][i], g_rt.wvf[n][k], pv);
+                vnf[i] = fmaf((float)sh, pv + a0f[i], v0f[i]);
+                vn[i] = 0.0;
+            } else {
+                double pv = A.b[6][i] * g_rt.wv[n][6];
+#pragma unroll
+                for (int k = 5; k >= 0; k--) pv = fma(A.b[k][i], g_rt.wv[n][k], pv);
+                pv = pv + a0[i];
+                vn[i] = fma(sh, pv, v0[i]);
+            }
         }
         double Fn[3], Fs[3];
         const double *r64 = A.rows.r64 ? A.rows.r64 + n * A.rows.stride64 : nullptr;
         const float *r32 = A.rows.r32 ? A.rows.r32 + n * A.rows.stride64 : nullptr;
         int st = accel<MODE, JAC, G>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs, enc, dxn,
-                                     false, JAC ? jrec + 6 * n : nullptr, ng);
+                                     false, JAC ? jrec + 6 * n : nullptr, ng,
+                                     vel32 ? vnf : nullptr);
         cnt.evals++;
         if (r64) cnt.node_evals++;
         if (st != KETE_BODY_OK) return st;
         switch (n) {
-        case 1: node_update<MODE, 1>(A, Fn, Fs, a0, F7); break;
-        case 2: node_update<MODE, 2>(A, Fn, Fs, a0, F7); break;
-        case 3: node_update<MODE, 3>(A, Fn, Fs, a0, F7); break;
-        case 4: node_update<MODE, 4>(A, Fn, Fs, a0, F7); break;
-        case 5: node_update<MODE, 5>(A, Fn, Fs, a0, F7); break;
-        case 6: node_update<MODE, 6>(A, Fn, Fs, a0, F7); break;
-        default: node_update<MODE, 7>(A, Fn, Fs, a0, F7); break;
+        case 1: node_update<MODE, 1, V32>(A, Fn, Fs, a0, F7); break;
+        case 2: node_update<MODE, 2, V32>(A, Fn, Fs, a0, F7); break;
+        case 3: node_update<MODE, 3, V32>(A, Fn, Fs, a0, F7); break;
+        case 4: node_update<MODE, 4, V32>(A, Fn, Fs, a0, F7); break;
+        case 5: node_update<MODE, 5, V32>(A, Fn, Fs, a0, F7); break;
+        case 6: node_update<MODE, 6, V32>(A, Fn, Fs, a0, F7); break;
+        default: node_update<MODE, 7, V32>(A, Fn, Fs, a0, F7); break;
         }
     }
     cnt.iters++;
