@@ -352,11 +352,12 @@ static void launch_k(int64_t grid, int block, cudaStream_t st, const EphemDev &E
                      double *out, int64_t stride, int aos, int kof, DevCounters *ctr, NodeTable t,
                      int unt, int leg0, unsigned long long *next, int refill, PropQueue q)
 {
-    // mixed precision with node rows: the node velocity in FP32 (V32)
+    // mixed precision along a chain of stops served by node rows: the node
+    // velocity in FP32 (V32); a single leg (one stop) rarely uses its rows
     if (F.nongrav)
         k_propagate<MODE, G, true><<<(unsigned)grid, block, 0, st>>>(
             E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
-    else if (MODE == KETE_MIXED && G == 1 && unt)
+    else if (MODE == KETE_MIXED && G == 1 && unt && n_stops > 1)
         k_propagate<MODE, G, false, true><<<(unsigned)grid, block, 0, st>>>(
             E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
     else
