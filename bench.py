@@ -48,7 +48,7 @@ PROFILED_TRAFFIC = {"src_sha": "2ed433c60b2bc931", "bytes_per_body_stop": 66.1}
 # same small case, divided by the candidates the prefilter passed to it); valid
 # only while the FoV kernels' source is unchanged.  The modelled count below leaves out the divisions, square roots
 # and convergence tests that the executed count includes.
-PROFILED_EXACT = {"src_sha": "0e2f887dfeee92fc", "fp64_flops_per_candidate": 924.9}
+PROFILED_EXACT = {"src_sha": "778547018286519d", "fp64_flops_per_candidate": 924.9}
 
 # FP64 arithmetic thread instructions (DFMA + DMUL + DADD) the FP64 survey's
 # propagation kernel executes per accepted step, from the same ncu capture as
@@ -380,6 +380,20 @@ def adjoint_leg(args, K, dev, flush, stream, peak):
     flops = adj_flops(st, fm, w.ephem.n_coef)
     fwd_tf = flops / (st["prop_ms"] / 1e3) / 1e12
     ok = int((status == 0).sum().item())
+    # the same fit with non-gravitational terms: every body on the full-model
+    # path (da/dx and da/dv of GR, J2 and the terms at every node)
+    ng = W.nongrav_params(w.labels, dust_frac=0.05)
+    ng_dev = kete.nongrav_to_device(ng, dev)
+    fm_ng = kete.force_model(nongrav=ng_dev)
+    opts_ng = kete.survey_opts(mem_budget_gb=48.0)  # ~400 KB of records a body
+    call_ng = lambda: K.adjoint(y, ep, ob, fm=fm_ng, opts=opts_ng, ckpt_days=8.0)
+    call_ng()
+    ms_ng, (_, _, _, status_ng) = _timed(stream, call_ng, flush, 2)
+    st_ng = K.get_stats()
+    nongrav = {"ms_per_step": ms_ng, "forward_ms": st_ng["prop_ms"],
+               "cost_vs_gravity": ms_ng / ms, "bodies_ok": int((status_ng == 0).sum().item()),
+               "terms": "every 10th body a transverse 1/r^2 drift, 5 % of the rest radiation "
+                        "pressure with beta logU[1e-3, 0.1]; all bodies on the full-model path"}
     # sampled parity: observations and reference gradient from the oracle alone
     orc = O.Oracle(w.ephem.to_bytes())
     fmo = orc.force_model()
@@ -418,6 +432,7 @@ def adjoint_leg(args, K, dev, flush, stream, peak):
         "bodies_ok": ok, "steps": st["steps"], "force_evals": st["force_evals"],
         "roofline": {"bound": "alu", "kernel": "k_adj_forward", "achieved": fwd_tf, "peak": peak,
                      "unit": "TFLOP/s", "frac": fwd_tf / peak, "traffic": None},
+        "nongrav": nongrav,
         "parity": {"sampled_bodies": len(sub), "max_rel_grad_x": float(rel_x.max()),
                    "max_rel_grad_v": float(rel_v.max()),
                    "max_rel_loss": float((np.abs(ls - loss_r) / loss_r).max()),
