@@ -233,6 +233,79 @@ __device__ __forceinline__ void cheb_state64(const EphemDev &E, int m, int s, do
     }
 }
 
+// The Chebyshev basis at tau, shared by every body of one evaluation: T_k(tau)
+// and k U_{k-1}(tau) (T_k' = k U_{k-1}), from the recurrences of cheb_pos /
+// cheb_pos_vel in the same order, so that cheb_state64b's sums are bit for bit
+// theirs.  The per-body recurrence steps (1 FP64 FMA per coefficient for the
+// position, 3 for the velocity) are done once instead of for every body; the
+// basis is read back from the stack (load slots, not FP64 ones).
+constexpr int kBasisMax = 16;
+struct ChebBasis {
+    double T[kBasisMax], dT[kBasisMax];
+};
+
+__device__ __forceinline__ void cheb_basis(int nc, double tau, bool vel, ChebBasis &B)
+{
+    const double t2 = 2.0 * tau;
+    double Tm1 = 1.0, T = tau;   // T_0, T_1
+    double Um1 = 1.0, U = t2;    // U_0, U_1
+    B.T[0] = 1.0;
+    B.T[1] = tau;
+    B.dT[1] = 1.0;
+    for (int k = 2; k < nc; k++) {
+        const double Tn = fma(t2, T, -Tm1);
+        Tm1 = T;
+        T = Tn;
+        B.T[k] = T;
+        if (vel) {
+            B.dT[k] = (double)k * U;
+            const double Un = fma(t2, U, -Um1);
+            Um1 = U;
+            U = Un;
+        }
+    }
+}
+
+// Planet state of body m from a shared basis (see cheb_basis): the sums of
+// cheb_pos / cheb_pos_vel with the basis read instead of recomputed.
+static __device__ __noinline__ PlanetState cheb_state64b(const EphemDev &E, int m, int s,
+                                                         const ChebBasis &B, bool vel)
+{
+    const double *__restrict__ c = ephem_coef(E, m, s);
+    const int nc = E.n_coef;
+    double p[3], v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double c1 = __ldg(c + d * nc + 1);
+        p[d] = fma(c1, B.T[1], __ldg(c + d * nc));
+        v[d] = c1;
+    }
+    if (vel) {
+        for (int k = 2; k < nc; k++) {
+            const double Tk = B.T[k], dk = B.dT[k];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const double ck = __ldg(c + d * nc + k);
+                p[d] = fma(ck, Tk, p[d]);
+                v[d] = fma(ck, dk, v[d]);
+            }
+        }
+        const double dtau_dt = 2.0 * E.inv_seg;
+#pragma unroll
+        for (int d = 0; d < 3; d++) v[d] *= dtau_dt;
+    } else {
+        for (int k = 2; k < nc; k++) {
+            const double Tk = B.T[k];
+#pragma unroll
+            for (int d = 0; d < 3; d++) p[d] = fma(__ldg(c + d * nc + k), Tk, p[d]);
+        }
+    }
+    PlanetState o;
+    o.x = p[0]; o.y = p[1]; o.z = p[2];
+    o.vx = v[0]; o.vy = v[1]; o.vz = v[2];
+    return o;
+}
+
 // FP32 Clenshaw of body m (mixed precision, planets only), the recurrences
 // interleaved; vel as in cheb_state64
 __device__ __forceinline__ void cheb_state32(const EphemDev &E, int m, int s, float tau,
@@ -410,6 +483,10 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
     }
     double best = kEncounterAu * kEncounterAu;
     if (!row64 && !ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
+    // per-thread ephemeris: one Chebyshev basis for all the bodies
+    ChebBasis basis;
+    const bool use_basis = !row64 && E.n_coef <= kBasisMax;
+    if (use_basis) cheb_basis(E.n_coef, g.tau, (F.gr_mask & F.active_mask) != 0u, basis);
     for (int m = LaneGroup<G>::rank(); m < E.n_bodies; m += G) {
         if (!((F.active_mask >> m) & 1u)) continue;
         const bool gr = (F.gr_mask >> m) & 1u, j2 = (F.j2_mask >> m) & 1u;
@@ -422,6 +499,10 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
 #pragma unroll
                 for (int q = 3; q < 6; q++) st[q] = __ldg(row64 + 6 * m + q);
             }
+        } else if (use_basis) {
+            const PlanetState o = cheb_state64b(E, m, g.s, basis, gr);
+            st[0] = o.x; st[1] = o.y; st[2] = o.z;
+            st[3] = o.vx; st[4] = o.vy; st[5] = o.vz;
         } else {
             cheb_state64(E, m, g.s, g.tau, st, gr);
         }

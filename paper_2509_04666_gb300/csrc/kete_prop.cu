@@ -354,15 +354,20 @@ static void launch_k(int64_t grid, int block, cudaStream_t st, const EphemDev &E
 {
     // mixed precision along a chain of stops served by node rows: the node
     // velocity in FP32 (V32); a single leg (one stop) rarely uses its rows
-    if (F.nongrav)
+    if (F.nongrav) {
         k_propagate<MODE, G, true><<<(unsigned)grid, block, 0, st>>>(
             E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
-    else if (MODE == KETE_MIXED && G == 1 && unt && n_stops > 1)
-        k_propagate<MODE, G, false, true><<<(unsigned)grid, block, 0, st>>>(
-            E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
-    else
-        k_propagate<MODE, G, false><<<(unsigned)grid, block, 0, st>>>(
-            E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
+        return;
+    }
+    if constexpr (MODE == KETE_MIXED && G == 1) {
+        if (unt && n_stops > 1) {
+            k_propagate<MODE, G, false, true><<<(unsigned)grid, block, 0, st>>>(
+                E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
+            return;
+        }
+    }
+    k_propagate<MODE, G, false><<<(unsigned)grid, block, 0, st>>>(
+        E, F, cs, stops, n_stops, out, stride, aos, kof, ctr, t, unt, leg0, next, refill, q);
 }
 
 template <int MODE>
