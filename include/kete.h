@@ -415,10 +415,13 @@ typedef struct kete_obs {
  * forward-mode differentiation.  fm->nongrav NULL: the Newtonian da/dx alone
  * (the GR and J2 parts of da/dx and GR's da/dv, below 1e-8 relative, are
  * omitted).  fm->nongrav set (per-body terms, as kete_propagate): the forward
- * model includes them and the adjoint takes the full model's da/dx and da/dv
- * -- Newtonian, GR, J2 and the body's non-gravitational terms with their
- * thermal lag -- by forward-mode dual numbers at every node of every step
- * (about 300 KB more scratch per body, and a slower forward pass); pred (device,
+ * model includes them and, for every body whose terms are not all zero, the
+ * adjoint takes the full model's da/dx and da/dv -- Newtonian, GR, J2 and
+ * the body's non-gravitational terms with their thermal lag -- by
+ * forward-mode dual numbers at every node of every step (about 300 KB more
+ * scratch per body, and a slower forward pass for those bodies; bodies with
+ * and without terms are scheduled apart); a body whose terms are all zero is
+ * differentiated as without fm->nongrav; pred (device,
  * [n][m][2], may be NULL) = predicted RA, Dec.  FP64 only (fm->precision is
  * ignored).  status (device, [n], may be NULL).
  * ckpt_days: 0 (no grid) or >= 1e-3; a body whose grid would exceed 65536

@@ -34,7 +34,7 @@ enum Slot {
     S_ORDER_SCAN, S_ORDER_N, S_ADJ_TEND, S_LEG_OUT,
     S_EXT_START, S_EXT_EX, S_EXT_TMP, S_EXT_FIRST, S_EXT_SUB, S_EXT_PARENT, S_EXT_CNT,
     S_EXT_OFF, S_EXT_CUR, S_EXT_GROUP, S_EXT_KEEP, S_EXT_KCNT, S_EXT_KOFF, S_ADJ_PHI, S_ADJ_RECX,
-    S_PRE_KEEP, S_PRE_N,
+    S_PRE_KEEP, S_PRE_N, S_ADJ_RICH,
     S_NSLOTS
 };
 
@@ -1333,7 +1333,11 @@ static int adjoint_impl(kete_ctx *ctx, const double *states, const double *epoch
         B.phi = nullptr;
         if (jac) GET(S_ADJ_PHI, (size_t)chunk * m * 36, B.phi);
         B.recx = nullptr;
-        if (full) GET(S_ADJ_RECX, (size_t)chunk * cap * kAdjRecX, B.recx);
+        B.rich = nullptr;
+        if (full) {
+            GET(S_ADJ_RECX, (size_t)chunk * cap * kAdjRecX, B.recx);
+            GET(S_ADJ_RICH, chunk, B.rich);
+        }
         unsigned long long *next = nullptr;
         GET(S_NEXTBODY, 1, next);
         int launches = 0;
@@ -1347,8 +1351,10 @@ static int adjoint_impl(kete_ctx *ctx, const double *states, const double *epoch
             if (order_on) {   // most expensive bodies first (schedule only)
                 unsigned long long *order_n;
                 CUDA_TRY(launch_adjoint_last_epoch(P, i0, nc, t_end, ctx->stream));
+                // bodies with and without non-gravitational terms in separate
+                // ranges, so that the full-model records rarely share a warp
                 int r2 = cost_order(ctx, states + i0, n, epochs + i0, nc, nullptr, 0, t_end,
-                                    nullptr, &order, &order_n);
+                                    F.nongrav ? F.nongrav + i0 : nullptr, &order, &order_n);
                 if (r2 != KETE_OK) return r2;
                 launches += 1;
             }

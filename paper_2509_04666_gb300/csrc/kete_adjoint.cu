@@ -534,8 +534,10 @@ __device__ __forceinline__ void walk_next_ckpt(StopWalk &w, double epoch0, doubl
 // One lane per body at a time, one step attempt per loop iteration (lanes of a
 // warp stay in step while their bodies sit at different stops).  refill = 1:
 // persistent grid, a lane whose body is done takes the next one from *next.
-// RICH: the body's non-gravitational terms enter the force, and every record
-// gets the full model's Jacobian (B.recx) besides the Newtonian da/dx.
+// RICH: a body with non-gravitational terms has them in its force, and each
+// of its records gets the full model's Jacobian (B.recx) besides the
+// Newtonian da/dx; a body whose terms are all zero keeps the Newtonian
+// records (B.rich[i] tells which).
 template <bool RICH>
 __global__ void __launch_bounds__(128)
 k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc,
@@ -554,8 +556,9 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
     StepState S;
     S.have_a0 = false;
     S.ng = nullptr;   // set per body on the full-model path
+    S.ng_chi = 0.0;
     const LegView L = leg_view(nullptr, 0);
-    double *rec = nullptr, *recx = nullptr;
+    double *rec = nullptr, *recx = nullptr;   // recx: null for a body without terms
     bool first = true;
     for (;;) {
         const bool need = (i < 0);
@@ -604,8 +607,12 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
                     W.ckpt_ok = P.ckpt > 0.0 && W.tc < W.t_last;
                     rec = B.rec + (size_t)i * B.cap * kAdjRec;
                     if (RICH) {
-                        recx = B.recx + (size_t)i * B.cap * kAdjRecX;
-                        S.ng = F.nongrav ? F.nongrav + gi : nullptr;
+                        const kete_nongrav *p = F.nongrav ? F.nongrav + gi : nullptr;
+                        const bool terms = p && (p->a1 != 0.0 || p->a2 != 0.0 ||
+                                                 p->a3 != 0.0 || p->beta != 0.0);
+                        recx = terms ? B.recx + (size_t)i * B.cap * kAdjRecX : nullptr;
+                        S.ng = terms ? p : nullptr;
+                        S.ng_chi = 0.0;
                     }
                     count = 0;
                     capped = false;
@@ -631,7 +638,7 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
                 const int slot = count < B.cap - 1 ? count : B.cap - 2;
                 double *r = rec + (size_t)slot * kAdjRec;
                 const double t_prev = t;
-                if (RICH) {   // the accepted attempt's coefficients give the node states
+                if (RICH && recx) {   // the accepted attempt's coefficients give the node states
                     const double x0[3] = {x[0], x[1], x[2]}, v0[3] = {v[0], v[1], v[2]};
                     Attempt A;
                     status = step_begin<KETE_FP64, true>(E, F, L, x, v, t, dt, ts, S, A, cnt, r + 2);
@@ -639,7 +646,7 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
                         bool done = false;
                         status = attempt_sweep<KETE_FP64, true>(E, F, t, x, v, S.a0, S.as0,
                                                                 S.close, S.enc, A, done, cnt,
-                                                                r + 2, S.ng);
+                                                                r + 2, S.ng, &S.ng_chi);
                         if (done) break;
                     }
                     if (status == KETE_BODY_OK)
@@ -692,13 +699,14 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
             double a[3], J[6];
             Encounter enc;
             const double zero[3] = {0.0, 0.0, 0.0};
-            status = accel_fp64<true>(E, F, t, 0.0, nullptr, x, v, a, enc, zero, true, J, S.ng);
+            status = accel_fp64<true>(E, F, t, 0.0, nullptr, x, v, a, enc, zero, true, J, S.ng,
+                                      &S.ng_chi);
             cnt.evals++;
             r[0] = t;
             r[1] = t;
 #pragma unroll
             for (int q = 0; q < 6; q++) r[2 + q] = J[q];
-            if (RICH && status == KETE_BODY_OK) {
+            if (RICH && recx && status == KETE_BODY_OK) {
                 double *rx = recx + (size_t)count * kAdjRecX;
                 status = extra_jacobian(E, F, t, 0.0, x, v, S.ng, rx, rx + 9);
             }
@@ -708,6 +716,7 @@ k_adj_forward(EphemDev E, ForceDev F, AdjBuffers B, AdjProblem P, int64_t i0, in
         B.n_rec[i] = (status == KETE_BODY_OK) ? count : 0;
         B.nbat[i] = W.nb;
         B.status[i] = status;
+        if (RICH) B.rich[i] = recx ? 1 : 0;
         i = -1;
     }
     flush_counters(cnt, P.ctr);
@@ -1120,6 +1129,7 @@ k_adj_stm(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
 // extension (Ex, Av) of backward sample k (see jac_sample)
 __device__ __forceinline__ const double *jacx_sample(const double *rx, const double *rx_next, int k)
 {
+    if (!rx) return nullptr;   // a body without terms
     return k == 0 ? rx_next : rx + 18 * (8 - k);
 }
 
@@ -1127,11 +1137,12 @@ __device__ __forceinline__ const double *jacx_sample(const double *rx, const dou
 __device__ __forceinline__ const double *jacx_sample_fwd(const double *rx, const double *rx_next,
                                                          int k)
 {
+    if (!rx) return nullptr;   // a body without terms
     return k == 8 ? rx_next : rx + 18 * k;
 }
 
 // adjoint right-hand sides: G = h^2 (J + Ex)^T m, H = h Av^T m (J symmetric,
-// Ex and Av row-major a_i by x_c)
+// Ex and Av row-major a_i by x_c; X null: a body without terms, Ex = Av = 0)
 __device__ __forceinline__ void adj_rhs_full(const double *J, const double *X, double h,
                                              const double m[3], double G[3], double H[3])
 {
@@ -1139,15 +1150,17 @@ __device__ __forceinline__ void adj_rhs_full(const double *J, const double *X, d
     jmul(J, m, jm);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const double ex = fma(__ldg(X + c), m[0], fma(__ldg(X + 3 + c), m[1], __ldg(X + 6 + c) * m[2]));
-        const double av =
-            fma(__ldg(X + 9 + c), m[0], fma(__ldg(X + 12 + c), m[1], __ldg(X + 15 + c) * m[2]));
+        double ex = 0.0, av = 0.0;
+        if (X) {
+            ex = fma(__ldg(X + c), m[0], fma(__ldg(X + 3 + c), m[1], __ldg(X + 6 + c) * m[2]));
+            av = fma(__ldg(X + 9 + c), m[0], fma(__ldg(X + 12 + c), m[1], __ldg(X + 15 + c) * m[2]));
+        }
         G[c] = h * h * (jm[c] + ex);
         H[c] = h * av;
     }
 }
 
-// variational right-hand side: F = h^2 ((J + Ex) dx + Av dv)
+// variational right-hand side: F = h^2 ((J + Ex) dx + Av dv) (X null: Ex = Av = 0)
 __device__ __forceinline__ void var_rhs_full(const double *J, const double *X, double h,
                                              const double dx[3], const double dv[3], double F[3])
 {
@@ -1155,9 +1168,12 @@ __device__ __forceinline__ void var_rhs_full(const double *J, const double *X, d
     jmul(J, dx, jx);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const double *e = X + 3 * c, *a = X + 9 + 3 * c;
-        const double ex = fma(__ldg(e), dx[0], fma(__ldg(e + 1), dx[1], __ldg(e + 2) * dx[2]));
-        const double av = fma(__ldg(a), dv[0], fma(__ldg(a + 1), dv[1], __ldg(a + 2) * dv[2]));
+        double ex = 0.0, av = 0.0;
+        if (X) {
+            const double *e = X + 3 * c, *a = X + 9 + 3 * c;
+            ex = fma(__ldg(e), dx[0], fma(__ldg(e + 1), dx[1], __ldg(e + 2) * dx[2]));
+            av = fma(__ldg(a), dv[0], fma(__ldg(a + 1), dv[1], __ldg(a + 2) * dv[2]));
+        }
         F[c] = h * h * (jx[c] + ex + av);
     }
 }
@@ -1183,7 +1199,7 @@ k_adj_backward_full(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
     const int count = B.n_rec[i];
     int kb = B.nbat[i] - 1;
     const double *rec = B.rec + (size_t)i * B.cap * kAdjRec;
-    const double *recx = B.recx + (size_t)i * B.cap * kAdjRecX;
+    const double *recx = B.rich[i] ? B.recx + (size_t)i * B.cap * kAdjRecX : nullptr;
     const int32_t *bidx = B.bidx + (size_t)i * P.m;
     const double *gjump = B.gjump + (size_t)i * P.m * 6;
     double mu[3] = {0, 0, 0}, lx[3] = {0, 0, 0};
@@ -1203,8 +1219,8 @@ k_adj_backward_full(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
             continue;
         const double *r = rec + (size_t)s * kAdjRec;
         const double *rn = r + kAdjRec;
-        const double *rx = recx + (size_t)s * kAdjRecX;
-        const double *rxn = rx + kAdjRecX;
+        const double *rx = recx ? recx + (size_t)s * kAdjRecX : nullptr;
+        const double *rxn = recx ? rx + kAdjRecX : nullptr;
         const double h = __ldg(r + 1) - __ldg(r);
         const double q0[3] = {h * lx[0], h * lx[1], h * lx[2]};
         double G[9][3], H[9][3], m8[3];
@@ -1274,7 +1290,7 @@ k_adj_stm_full(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
     const int count = B.n_rec[i];
     const int nb = B.nbat[i];
     const double *rec = B.rec + (size_t)i * B.cap * kAdjRec;
-    const double *recx = B.recx + (size_t)i * B.cap * kAdjRecX;
+    const double *recx = B.rich[i] ? B.recx + (size_t)i * B.cap * kAdjRecX : nullptr;
     const int32_t *bidx = B.bidx + (size_t)i * P.m;
     double *phi_out = B.phi + (size_t)i * P.m * 36;
     for (int c0 = 0; c0 < 6; c0++) {
@@ -1295,8 +1311,8 @@ k_adj_stm_full(AdjBuffers B, AdjProblem P, int64_t i0, int64_t nc)
             if (s == count - 1) break;
             const double *r = rec + (size_t)s * kAdjRec;
             const double *rn = r + kAdjRec;
-            const double *rx = recx + (size_t)s * kAdjRecX;
-            const double *rxn = rx + kAdjRecX;
+            const double *rx = recx ? recx + (size_t)s * kAdjRecX : nullptr;
+            const double *rxn = recx ? rx + kAdjRecX : nullptr;
             const double h = __ldg(r + 1) - __ldg(r);
             const double ih = 1.0 / h;
             double F[9][3], x8[3], v8[3];

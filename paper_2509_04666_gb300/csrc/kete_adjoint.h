@@ -46,6 +46,9 @@ struct AdjBuffers {
                        // part (9, row-major) and da/dv (9) -- the full force model's
                        // Jacobian (calls with non-gravitational terms); null: the
                        // Newtonian da/dx of rec alone
+    int32_t *rich;     // [nc] (with recx) 1: the body has non-gravitational terms and
+                       // its records carry recx; 0: a body without terms, Newtonian
+                       // records only
     int32_t *status;   // [nc]
 };
 

@@ -432,10 +432,12 @@ __device__ __forceinline__ void newton_jacobian(double mu, const double r[3], do
 struct NgOut {
     double a[3];
     int status;
+    double chi;   // the thermal lag's two-body solution (universal anomaly), for the next call
 };
 static __device__ __noinline__ NgOut nongrav_terms(const EphemDev &E, const double *row64, Seg g,
                                                    const kete_nongrav *P, double x0, double x1,
-                                                   double x2, double v0, double v1, double v2);
+                                                   double x2, double v0, double v1, double v2,
+                                                   double chi0);
 
 // Lane groups (G > 1): the body's non-gravitational terms (ng may be null)
 // computed by the group's last lane -- the one that holds the fewest masses
@@ -444,12 +446,14 @@ static __device__ __noinline__ NgOut nongrav_terms(const EphemDev &E, const doub
 template <int G>
 __device__ __forceinline__ int group_nongrav(const EphemDev &E, const double *row64, Seg g,
                                              const kete_nongrav *ng, const double x[3],
-                                             const double v[3], double acc[3])
+                                             const double v[3], double acc[3], double *ng_chi)
 {
     if (!ng) return KETE_BODY_OK;
     int st = KETE_BODY_OK;
     if (LaneGroup<G>::rank() == G - 1) {
-        const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2]);
+        const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2],
+                                      ng_chi ? *ng_chi : 0.0);
+        if (ng_chi) *ng_chi = o.chi;
         st = o.status;
         acc[0] += o.a[0];
         acc[1] += o.a[1];
@@ -469,7 +473,8 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
                                           double off, const double *__restrict__ row64,
                                           const double x[3], const double v[3], double a[3],
                                           Encounter &enc, const double dx[3], bool detect,
-                                          double *J = nullptr, const kete_nongrav *ng = nullptr)
+                                          double *J = nullptr, const kete_nongrav *ng = nullptr,
+                                          double *ng_chi = nullptr)
 {
     Seg g = {0, 0.0};
     a[0] = a[1] = a[2] = 0.0;
@@ -534,7 +539,7 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
         // the body's own terms go to the group's last lane, which holds the
         // fewest masses, and join the group sum (a lagged comet term costs a
         // two-body solve: done once per group, beside the others' masses)
-        const int ng_status = group_nongrav<G>(E, row64, g, ng, x, v, a);
+        const int ng_status = group_nongrav<G>(E, row64, g, ng, x, v, a, ng_chi);
 #pragma unroll
         for (int c = 0; c < 3; c++) a[c] = LaneGroup<G>::sum(a[c]);
         if (JAC) {
@@ -545,7 +550,9 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
         return ng_status;
     }
     if (ng) {
-        const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2]);
+        const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2],
+                                      ng_chi ? *ng_chi : 0.0);
+        if (ng_chi) *ng_chi = o.chi;
         if (o.status != KETE_BODY_OK) return o.status;
         a[0] += o.a[0];
         a[1] += o.a[1];
@@ -576,7 +583,7 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
                                            const double x[3], const double v[3], double a[3],
                                            double as[3], Encounter &enc, const double dx[3],
                                            bool detect, const kete_nongrav *ng = nullptr,
-                                           const float *vf_in = nullptr)
+                                           const float *vf_in = nullptr, double *ng_chi = nullptr)
 {
     Seg g = {0, 0.0};
     as[0] = as[1] = as[2] = 0.0;
@@ -693,7 +700,7 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
     }
     int ng_status = KETE_BODY_OK;
     if (G > 1) {
-        ng_status = group_nongrav<G>(E, row64, g, ng, x, v, as);   // FP64, smooth part
+        ng_status = group_nongrav<G>(E, row64, g, ng, x, v, as, ng_chi);   // FP64, smooth part
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             as[c] = LaneGroup<G>::sum(as[c]);
@@ -705,7 +712,9 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
         }
         if (ng_status != KETE_BODY_OK) return ng_status;
     } else if (ng) {   // FP64, part of the smooth FP64 sum that controls the step
-        const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2]);
+        const NgOut o = nongrav_terms(E, row64, g, ng, x[0], x[1], x[2], v[0], v[1], v[2],
+                                      ng_chi ? *ng_chi : 0.0);
+        if (ng_chi) *ng_chi = o.chi;
         if (o.status != KETE_BODY_OK) return o.status;
         as[0] += o.a[0];
         as[1] += o.a[1];
@@ -860,9 +869,10 @@ __device__ __forceinline__ bool kepler_uv(double mu, double sqmu, const double r
 // and the JPL comet model (Eq. A.7) from the two-body state dt days earlier.
 static __device__ __noinline__ NgOut nongrav_terms(const EphemDev &E, const double *row64, Seg g,
                                                    const kete_nongrav *P, double x0, double x1,
-                                                   double x2, double v0, double v1, double v2)
+                                                   double x2, double v0, double v1, double v2,
+                                                   double chi0)
 {
-    NgOut o = {{0.0, 0.0, 0.0}, KETE_BODY_OK};
+    NgOut o = {{0.0, 0.0, 0.0}, KETE_BODY_OK, chi0};
     double sun[6];
     if (row64) {
 #pragma unroll
@@ -886,19 +896,28 @@ static __device__ __noinline__ NgOut nongrav_terms(const EphemDev &E, const doub
     if (p.a1 != 0.0 || p.a2 != 0.0 || p.a3 != 0.0) {
         double rl[3] = {r[0], r[1], r[2]}, wl[3] = {w[0], w[1], w[2]};
         if (p.dt != 0.0) {
-            double chi = 0.0;
+            // Newton starts from the previous evaluation's solution (0: the
+            // series start): the lagged state moves little between the nodes
+            double chi = chi0;
             if (!kepler_uv(mu, sqrt(mu), r, w, -p.dt, chi, rl, wl)) {
                 o.status = KETE_BODY_KEPLER_CAP;
                 return o;
             }
+            o.chi = chi;
         }
         const double rn = sqrt(rl[0] * rl[0] + rl[1] * rl[1] + rl[2] * rl[2]);
         const double q = rn / p.r0;
-        // g(r); the asteroid form (m = 2, k = 0: alpha / q^2) without pow
+        // g(r) = alpha q^-m (1 + q^n)^-k: the asteroid form (m = 2, k = 0) as
+        // alpha / q^2, else from one logarithm of q, q^x = exp(x ln q) (a
+        // relative error of a few 1e-16 |x ln q| in a term of ~1e-8 of |a|)
         double gq = p.alpha;
-        if (p.m == 2.0) gq /= q * q;
-        else gq *= pow(q, -p.m);
-        if (p.k != 0.0) gq *= pow(1.0 + pow(q, p.n), -p.k);
+        if (p.m == 2.0 && p.k == 0.0) {
+            gq /= q * q;
+        } else {
+            const double lq = log(q);
+            gq *= exp(-p.m * lq);
+            if (p.k != 0.0) gq *= exp(-p.k * log1p(exp(p.n * lq)));
+        }
         const double rh[3] = {rl[0] / rn, rl[1] / rn, rl[2] / rn};
         double h[3] = {rl[1] * wl[2] - rl[2] * wl[1], rl[2] * wl[0] - rl[0] * wl[2],
                        rl[0] * wl[1] - rl[1] * wl[0]};

@@ -73,6 +73,7 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
     StepState S;
     S.have_a0 = false;
     S.ng = nullptr;
+    S.ng_chi = 0.0;
     LegView L = leg_view(nullptr, 0);
     Attempt A;
     bool in_attempt = false;  // A holds a step attempt with sweeps to go
@@ -110,6 +111,7 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
                     body_attempts = 0;
                     S.have_a0 = false;
                     S.ng = (NG && F.nongrav) ? F.nongrav + i : nullptr;
+                    S.ng_chi = 0.0;
                     L = leg_view(use_nt ? &nt : nullptr, leg0 + k);
                     in_attempt = false;
                     if (status == KETE_BODY_OK && k < n_stops) aim_step(F, t, stops[k], dt);
@@ -151,7 +153,7 @@ k_propagate(EphemDev E, ForceDev F, ChainState cs, const double *__restrict__ st
         if (in_attempt) {
             bool done = false;
             status = attempt_sweep<MODE, false, G, V32>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, A,
-                                                   done, cnt, nullptr, S.ng);
+                                                   done, cnt, nullptr, S.ng, &S.ng_chi);
             if (status != KETE_BODY_OK) {
                 in_attempt = false;
             } else if (done) {

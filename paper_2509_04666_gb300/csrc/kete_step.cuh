@@ -101,14 +101,14 @@ __device__ __forceinline__ int accel(const EphemDev &E, const ForceDev &F, doubl
                                      const double x[3], const double v[3], double a[3],
                                      double as[3], Encounter &enc, const double dx[3], bool detect,
                                      double *jout = nullptr, const kete_nongrav *ng = nullptr,
-                                     const float *vf = nullptr)
+                                     const float *vf = nullptr, double *ng_chi = nullptr)
 {
     static_assert(!(JAC && MODE == KETE_MIXED), "Jacobian capture is FP64 only");
     if (MODE == KETE_MIXED)
         return accel_mixed<G>(E, F, t0, off, row64, row32, close, x, v, a, as, enc, dx, detect, ng,
-                              vf);
+                              vf, ng_chi);
     double J[6];
-    int st = accel_fp64<JAC, G>(E, F, t0, off, row64, x, v, a, enc, dx, detect, J, ng);
+    int st = accel_fp64<JAC, G>(E, F, t0, off, row64, x, v, a, enc, dx, detect, J, ng, ng_chi);
     as[0] = a[0]; as[1] = a[1]; as[2] = a[2];
     if (JAC) {
 #pragma unroll
@@ -186,7 +186,8 @@ __device__ __forceinline__ int attempt_sweep(const EphemDev &E, const ForceDev &
                                              const double a0[3], const double as0[3],
                                              uint32_t close, Encounter enc, Attempt &A, bool &done,
                                              Cnt &cnt, double *jrec = nullptr,
-                                             const kete_nongrav *ng = nullptr)
+                                             const kete_nongrav *ng = nullptr,
+                                             double *ng_chi = nullptr)
 {
     const double h = A.h;
     double b6o[3] = {A.b[6][0], A.b[6][1], A.b[6][2]};
@@ -246,7 +247,7 @@ __device__ __forceinline__ int attempt_sweep(const EphemDev &E, const ForceDev &
         const float *r32 = A.rows.r32 ? A.rows.r32 + n * A.rows.stride64 : nullptr;
         int st = accel<MODE, JAC, G>(E, F, t, sh, r64, r32, close, xn, vn, Fn, Fs, enc, dxn,
                                      false, JAC ? jrec + 6 * n : nullptr, ng,
-                                     vel32 ? vnf : nullptr);
+                                     vel32 ? vnf : nullptr, ng_chi);
         cnt.evals++;
         if (r64) cnt.node_evals++;
         if (st != KETE_BODY_OK) return st;
@@ -323,6 +324,7 @@ struct StepState {
                             // segment boundary during an encounter
     bool have_a0;           // a0 valid for (x, v, t): kept across a rejection
     const kete_nongrav *ng; // the body's non-gravitational terms (null: none)
+    double ng_chi;          // the thermal lag's last two-body solution (0: none yet)
 };
 
 // Node-table view of leg kg (null pointers: no rows).
@@ -367,7 +369,7 @@ __device__ __forceinline__ int step_begin(const EphemDev &E, const ForceDev &F, 
         const double zero[3] = {0.0, 0.0, 0.0};
         int st = accel<MODE, JAC, G>(E, F, t, 0.0, at_start ? L.r64 : nullptr,
                                      at_start ? L.r32 : nullptr, S.close, x, v, S.a0, S.as0,
-                                     S.enc, zero, true, jrec, S.ng);
+                                     S.enc, zero, true, jrec, S.ng, nullptr, &S.ng_chi);
         cnt.evals++;
         if (at_start) cnt.node_evals++;
         if (st != KETE_BODY_OK) return st;
@@ -446,7 +448,7 @@ __device__ __forceinline__ int step_once(const EphemDev &E, const ForceDev &F, c
     for (;;) {
         bool done = false;
         st = attempt_sweep<MODE, JAC, G>(E, F, t, x, v, S.a0, S.as0, S.close, S.enc, A, done, cnt,
-                                         jrec, S.ng);
+                                         jrec, S.ng, &S.ng_chi);
         if (st != KETE_BODY_OK) return st;
         if (done) break;
     }
