@@ -380,8 +380,8 @@ def adjoint_leg(args, K, dev, flush, stream, peak):
     flops = adj_flops(st, fm, w.ephem.n_coef)
     fwd_tf = flops / (st["prop_ms"] / 1e3) / 1e12
     ok = int((status == 0).sum().item())
-    # the same fit with non-gravitational terms: every body on the full-model
-    # path (da/dx and da/dv of GR, J2 and the terms at every node)
+    # the same fit with non-gravitational terms: the bodies with terms on the
+    # full-model path (da/dx and da/dv of GR, J2 and the terms at every node)
     ng = W.nongrav_params(w.labels, dust_frac=0.05)
     ng_dev = kete.nongrav_to_device(ng, dev)
     fm_ng = kete.force_model(nongrav=ng_dev)
@@ -393,7 +393,7 @@ def adjoint_leg(args, K, dev, flush, stream, peak):
     nongrav = {"ms_per_step": ms_ng, "forward_ms": st_ng["prop_ms"],
                "cost_vs_gravity": ms_ng / ms, "bodies_ok": int((status_ng == 0).sum().item()),
                "terms": "every 10th body a transverse 1/r^2 drift, 5 % of the rest radiation "
-                        "pressure with beta logU[1e-3, 0.1]; all bodies on the full-model path"}
+                        "pressure with beta logU[1e-3, 0.1]; those bodies on the full-model path"}
     # sampled parity: observations and reference gradient from the oracle alone
     orc = O.Oracle(w.ephem.to_bytes())
     fmo = orc.force_model()
