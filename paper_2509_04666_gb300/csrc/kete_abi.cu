@@ -1213,31 +1213,41 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
         cands[n_cands].budget = splits[q][1];
         cands[n_cands++].order = 1;
     }
-    const PropVariant saved = ctx->var[F.precision == KETE_MIXED ? 1 : 0];
+    const int slot = F.precision == KETE_MIXED ? 1 : 0;
+    const PropVariant saved = ctx->var[slot];
     float best_ms = 1e30f, saved_ms = -1.0f;
     PropVariant best = saved;
     cudaEvent_t e0 = event_at(ctx, 0), e1 = event_at(ctx, 1);
-    for (int c = 0; c < n_cands; c++) cands[c].grid_scale = scale;
-    for (int c = 0; c < n_cands; c++) {
-        ctx->var[F.precision == KETE_MIXED ? 1 : 0] = cands[c];
-        float ms = 1e30f;
-        for (int rep = 0; rep < 3; rep++) {   // the first run warms up; the best of the others
+    // time variant v on cnt bodies (states st, epochs ep; output rows out),
+    // the best of reps runs after one that warms up
+    auto time_variant = [&](const PropVariant &v, const double *st_, const double *ep_,
+                            int64_t cnt, double *out_, int reps, float &ms) -> int {
+        ctx->var[slot] = v;
+        ms = 1e30f;
+        for (int rep = 0; rep <= reps; rep++) {
             ChainState cs;
-            r = run_chain(ctx, F, sst, sep, m, cs);
-            if (r != KETE_OK) return r;
+            int r2 = run_chain(ctx, F, st_, ep_, cnt, cs);
+            if (r2 != KETE_OK) return r2;
             NodeTable nt;
-            r = node_table(ctx, d_stops, (int)n_stops, sep, nt);
-            if (r != KETE_OK) return r;
+            r2 = node_table(ctx, d_stops, (int)n_stops, ep_, nt);
+            if (r2 != KETE_OK) return r2;
             CUDA_TRY(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
             CUDA_TRY(cudaEventRecord(e0, st));
-            r = propagate(ctx, F, cs, d_stops, (int)n_stops, out, m, false, &nt, 0);
-            if (r != KETE_OK) return r;
+            r2 = propagate(ctx, F, cs, d_stops, (int)n_stops, out_, cnt, false, &nt, 0);
+            if (r2 != KETE_OK) return r2;
             CUDA_TRY(cudaEventRecord(e1, st));
             CUDA_TRY(cudaEventSynchronize(e1));
             float t = 0.0f;
             CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
             if (rep > 0) ms = std::min(ms, t);
         }
+        return KETE_OK;
+    };
+    for (int c = 0; c < n_cands; c++) cands[c].grid_scale = scale;
+    for (int c = 0; c < n_cands; c++) {
+        float ms;
+        r = time_variant(cands[c], sst, sep, m, out, 2, ms);
+        if (r != KETE_OK) return r;
         if (ms < best_ms) {
             best_ms = ms;
             best = cands[c];
@@ -1247,11 +1257,27 @@ extern "C" int kete_autotune(kete_ctx *ctx, const double *states, const double *
             cands[c].order == saved.order)
             saved_ms = ms;
     }
-    // a sample ranks variants that differ by a few per cent unreliably (on the
-    // ragged year in mixed precision it preferred index order by 3-5 % where
-    // the whole population ran 3-4 % slower with it): the variant in use
-    // stays unless another beats it by more than 5 %
+    // a sample ranks variants that differ by a few per cent unreliably (its
+    // scaled-down grid holds fewer warps per SM than the real launch): the
+    // variant in use stays unless another beats it by more than 5 %, and a
+    // pick that does is checked against it on all the bodies when their
+    // output rows fit in 2 GB
     if (saved_ms > 0.0f && best_ms > 0.95f * saved_ms) best = saved;
+    const bool same = best.kind == saved.kind && best.block == saved.block &&
+                      best.split == saved.split && best.budget == saved.budget &&
+                      best.order == saved.order;
+    if (!same && m < n && saved_ms > 0.0f && (double)n_stops * 48.0 * (double)n <= 2e9) {
+        double *full_out;
+        GET(S_TUNE_OUT, (size_t)n_stops * 6 * n, full_out);
+        PropVariant pick = best, cur = saved;
+        pick.grid_scale = cur.grid_scale = 1.0;
+        float ms_pick, ms_cur;
+        r = time_variant(pick, states, epochs, n, full_out, 1, ms_pick);
+        if (r != KETE_OK) return r;
+        r = time_variant(cur, states, epochs, n, full_out, 1, ms_cur);
+        if (r != KETE_OK) return r;
+        if (!(ms_pick < ms_cur)) best = saved;
+    }
     best.grid_scale = 1.0;
     ctx->var[F.precision == KETE_MIXED ? 1 : 0] = best;
     if (kind) *kind = best.kind;
