@@ -381,9 +381,9 @@ int kete_set_propagation(kete_ctx *ctx, int precision, int kind, int block, int 
  * bodies as in the whole run, propagated along
  * the chain of stops (host, ascending) with force model fm, keep the fastest
  * for fm's precision -- the variant already set stays unless another beats it
- * by more than 5 % on the sample, and such a pick is then timed against it on
- * all n bodies (when n_stops x n x 48 bytes of output fit in 2 GB; a sample
- * ranks close variants unreliably) -- and report it in *kind, *block,
+ * by more than 5 % on the sample and then by more than 2 % on all n bodies
+ * (checked when n_stops x n x 48 bytes of output fit in 2 GB; a sample ranks
+ * close variants unreliably) -- and report it in *kind, *block,
  * *split_lanes, *defer_steps,
  * *cost_order (host, each may be NULL).
  * Errors: BAD_ARG, NO_EPHEM, NOMEM, CUDA. */
