@@ -564,7 +564,11 @@ def ragged_leg(args, K, dev, flush, stream):
     if args.ragged_variants:
         return out
     # the autotuner's pick per precision (kete_autotune on a body sample over
-    # the same year), timed on the whole population beside the hand variants
+    # the same year), timed on the whole population beside the hand variants;
+    # the autotuner starts from the default variant (the loop above left the
+    # last hand variant set)
+    K.set_propagation(kete.FP64, kete.PROP_WORK_STEALING, 128)
+    K.set_propagation(kete.MIXED, kete.PROP_WORK_STEALING, 128)
     for name, prec in (("fp64_autotuned", kete.FP64), ("mixed_autotuned", kete.MIXED)):
         fm = kete.force_model(precision=prec)
         e0 = torch.full((n,), W.T0, dtype=torch.float64, device=dev)
