@@ -368,24 +368,6 @@ int kete_load_ephem(kete_ctx *ctx, const void *buf, size_t nbytes)
     E.n_coef = nc;
     E.n_bodies = nb;
     std::memcpy(E.gm, p + 48, sizeof(double) * KETE_MAX_BODIES);
-    // the Sun's tail: from the first index k >= 2 whose coefficients (largest
-    // over segments and coordinates) sum to <= 1e-10 AU, its terms carry at
-    // most ~1e-17 AU of FP32 rounding
-    {
-        std::vector<double> mx(nc, 0.0);
-        for (int s = 0; s < ns; s++)
-            for (int d = 0; d < 3; d++)
-                for (int k = 0; k < nc; k++)
-                    mx[k] = std::max(mx[k], std::fabs(f64[((size_t)s * 3 + d) * nc + k]));
-        int K = nc;
-        double tail = 0.0;
-        for (int k = nc - 1; k >= 2; k--) {
-            tail += mx[k];
-            if (!(tail <= 1e-10)) break;
-            K = k;
-        }
-        E.sun_k32 = K;
-    }
     ctx->E = E;
     ctx->have_ephem = true;
     return KETE_OK;

@@ -306,47 +306,6 @@ static __device__ __noinline__ PlanetState cheb_state64b(const EphemDev &E, int 
     return o;
 }
 
-// The Sun's position for the mixed-precision monopole: the terms k < sun_k32
-// summed in FP64 as cheb_pos does, the rest -- whose coefficients sum to at
-// most 1e-10 AU -- in FP32 from the FP32 table (rounding ~1e-17 AU).
-static __device__ __noinline__ PlanetState sun_pos_mixed(const EphemDev &E, int s, double tau)
-{
-    const int nc = E.n_coef, K = E.sun_k32 < nc ? E.sun_k32 : nc;
-    const double *__restrict__ c = ephem_coef(E, 0, s);
-    const double t2 = 2.0 * tau;
-    double p[3];
-    double Tm1 = 1.0, T = tau;   // T_0, T_1
-#pragma unroll
-    for (int d = 0; d < 3; d++) p[d] = fma(__ldg(c + d * nc + 1), tau, __ldg(c + d * nc));
-    for (int k = 2; k < K; k++) {
-        const double Tn = fma(t2, T, -Tm1);
-        Tm1 = T;
-        T = Tn;
-#pragma unroll
-        for (int d = 0; d < 3; d++) p[d] = fma(__ldg(c + d * nc + k), T, p[d]);
-    }
-    if (K < nc) {
-        const float *__restrict__ cf = E.coef32 + (size_t)s * 3 * nc;
-        const float tf = (float)tau, t2f = 2.0f * tf;
-        float Um1 = 1.0f, U = tf, q[3] = {0.0f, 0.0f, 0.0f};   // T_0, T_1 in FP32
-        for (int k = 2; k < nc; k++) {
-            const float Un = fmaf(t2f, U, -Um1);
-            Um1 = U;
-            U = Un;
-            if (k >= K) {
-#pragma unroll
-                for (int d = 0; d < 3; d++) q[d] = fmaf(__ldg(cf + d * nc + k), U, q[d]);
-            }
-        }
-#pragma unroll
-        for (int d = 0; d < 3; d++) p[d] += (double)q[d];
-    }
-    PlanetState o;
-    o.x = p[0]; o.y = p[1]; o.z = p[2];
-    o.vx = o.vy = o.vz = 0.0;
-    return o;
-}
-
 // FP32 Clenshaw of body m (mixed precision, planets only), the recurrences
 // interleaved; vel as in cheb_state64
 __device__ __forceinline__ void cheb_state32(const EphemDev &E, int m, int s, float tau,
@@ -648,8 +607,7 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
             for (int q = 0; q < 3; q++) sunv[q] = row32 ? __ldg(row32 + 3 + q) : (float)__ldg(row64 + 3 + q);
         }
     } else {
-        const PlanetState so = sun_pos_mixed(E, g.s, g.tau);
-        sun[0] = so.x; sun[1] = so.y; sun[2] = so.z;
+        cheb_state64(E, 0, g.s, g.tau, sun, false);
         if (sun_gr) {
             float s6[6];
             cheb_state32(E, 0, g.s, (float)g.tau, s6, true);

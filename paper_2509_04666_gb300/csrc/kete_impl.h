@@ -17,8 +17,6 @@ struct EphemDev {
     double t_start, t_end, seg_len, inv_seg;
     int n_seg, n_coef, n_bodies, pad;
     double gm[KETE_MAX_BODIES];
-    int sun_k32;             // mixed precision: the Sun's coefficients from this index on sum
-                             // to <= 1e-10 AU, so their terms are summed in FP32 (n_coef: none)
 };
 
 // device view of a force model (derived quantities precomputed on the host)
