@@ -238,27 +238,29 @@ __device__ __forceinline__ void cheb_state64(const EphemDev &E, int m, int s, do
 // cheb_pos_vel in the same order, so that cheb_state64b's sums are bit for bit
 // theirs.  The per-body recurrence steps (1 FP64 FMA per coefficient for the
 // position, 3 for the velocity) are done once instead of for every body; the
-// basis is read back from the stack (load slots, not FP64 ones).
-constexpr int kBasisMax = 16;
+// basis is read back from shared memory (load slots, not FP64 ones; no DRAM),
+// one column per thread: element k of a thread's basis at T[k * kBasisLanes].
+constexpr int kBasisMax = 16;     // coefficients a table may have for the shared basis
+constexpr int kBasisLanes = 128;  // threads per block it serves
 struct ChebBasis {
-    double T[kBasisMax], dT[kBasisMax];
+    double *T, *dT;   // this thread's columns
 };
 
-__device__ __forceinline__ void cheb_basis(int nc, double tau, bool vel, ChebBasis &B)
+__device__ __forceinline__ void cheb_basis(int nc, double tau, bool vel, ChebBasis B)
 {
     const double t2 = 2.0 * tau;
     double Tm1 = 1.0, T = tau;   // T_0, T_1
     double Um1 = 1.0, U = t2;    // U_0, U_1
     B.T[0] = 1.0;
-    B.T[1] = tau;
-    B.dT[1] = 1.0;
+    B.T[kBasisLanes] = tau;
+    B.dT[kBasisLanes] = 1.0;
     for (int k = 2; k < nc; k++) {
         const double Tn = fma(t2, T, -Tm1);
         Tm1 = T;
         T = Tn;
-        B.T[k] = T;
+        B.T[k * kBasisLanes] = T;
         if (vel) {
-            B.dT[k] = (double)k * U;
+            B.dT[k * kBasisLanes] = (double)k * U;
             const double Un = fma(t2, U, -Um1);
             Um1 = U;
             U = Un;
@@ -269,7 +271,7 @@ __device__ __forceinline__ void cheb_basis(int nc, double tau, bool vel, ChebBas
 // Planet state of body m from a shared basis (see cheb_basis): the sums of
 // cheb_pos / cheb_pos_vel with the basis read instead of recomputed.
 static __device__ __noinline__ PlanetState cheb_state64b(const EphemDev &E, int m, int s,
-                                                         const ChebBasis &B, bool vel)
+                                                         ChebBasis B, bool vel)
 {
     const double *__restrict__ c = ephem_coef(E, m, s);
     const int nc = E.n_coef;
@@ -277,12 +279,12 @@ static __device__ __noinline__ PlanetState cheb_state64b(const EphemDev &E, int 
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const double c1 = __ldg(c + d * nc + 1);
-        p[d] = fma(c1, B.T[1], __ldg(c + d * nc));
+        p[d] = fma(c1, B.T[kBasisLanes], __ldg(c + d * nc));
         v[d] = c1;
     }
     if (vel) {
         for (int k = 2; k < nc; k++) {
-            const double Tk = B.T[k], dk = B.dT[k];
+            const double Tk = B.T[k * kBasisLanes], dk = B.dT[k * kBasisLanes];
 #pragma unroll
             for (int d = 0; d < 3; d++) {
                 const double ck = __ldg(c + d * nc + k);
@@ -295,7 +297,7 @@ static __device__ __noinline__ PlanetState cheb_state64b(const EphemDev &E, int 
         for (int d = 0; d < 3; d++) v[d] *= dtau_dt;
     } else {
         for (int k = 2; k < nc; k++) {
-            const double Tk = B.T[k];
+            const double Tk = B.T[k * kBasisLanes];
 #pragma unroll
             for (int d = 0; d < 3; d++) p[d] = fma(__ldg(c + d * nc + k), Tk, p[d]);
         }
@@ -488,9 +490,14 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
     }
     double best = kEncounterAu * kEncounterAu;
     if (!row64 && !ephem_seg(E, t0, off, g)) return KETE_BODY_OUT_OF_SPAN;
-    // per-thread ephemeris: one Chebyshev basis for all the bodies
+    // per-thread ephemeris: one Chebyshev basis for all the bodies, in shared
+    // memory (a column per thread)
+    __shared__ double s_basis[2 * kBasisMax * kBasisLanes];
     ChebBasis basis;
-    const bool use_basis = !row64 && E.n_coef <= kBasisMax;
+    basis.T = s_basis + threadIdx.x;
+    basis.dT = s_basis + kBasisMax * kBasisLanes + threadIdx.x;
+    const bool use_basis = !row64 && E.n_coef <= kBasisMax && threadIdx.x < kBasisLanes &&
+                           blockDim.x <= kBasisLanes;
     if (use_basis) cheb_basis(E.n_coef, g.tau, (F.gr_mask & F.active_mask) != 0u, basis);
     for (int m = LaneGroup<G>::rank(); m < E.n_bodies; m += G) {
         if (!((F.active_mask >> m) & 1u)) continue;
