@@ -40,7 +40,7 @@ MAS = math.radians(1.0 / 3.6e6)
 # of the same workload (100k bodies x 21 stops), per body-stop, scaled to the
 # full launch by its body-stops; valid only while the kernel source is
 # unchanged (the source hash below).
-PROFILED_TRAFFIC = {"src_sha": "0ea0dad59eb90c94", "bytes_per_body_stop": 65.6}
+PROFILED_TRAFFIC = {"src_sha": "d141a72662bbbcba", "bytes_per_body_stop": 65.9}
 
 
 # FP64 work of the exact FoV test per candidate it solves as ncu counts it (2 x
@@ -48,14 +48,14 @@ PROFILED_TRAFFIC = {"src_sha": "0ea0dad59eb90c94", "bytes_per_body_stop": 65.6}
 # same small case, divided by the candidates the prefilter passed to it); valid
 # only while the FoV kernels' source is unchanged.  The modelled count below leaves out the divisions, square roots
 # and convergence tests that the executed count includes.
-PROFILED_EXACT = {"src_sha": "f6551ffe1487b19a", "fp64_flops_per_candidate": 924.9}
+PROFILED_EXACT = {"src_sha": "4342528b4c0eb507", "fp64_flops_per_candidate": 834.6}
 
 # FP64 arithmetic thread instructions (DFMA + DMUL + DADD) the FP64 survey's
 # propagation kernel executes per accepted step, from the same ncu capture as
 # the traffic (100k bodies x 21 stops: 16.83 G over 2,119,119 steps); with the
 # step count of a run it gives the FP64 pipe's issue rate, which the FLOP
 # roofline understates (a DMUL or DADD takes an FMA's issue slot).
-PROFILED_ISSUE = {"src_sha": "0ea0dad59eb90c94", "fp64_inst_per_step": 7942.0}
+PROFILED_ISSUE = {"src_sha": "d141a72662bbbcba", "fp64_inst_per_step": 7942.3}
 
 
 def kernel_source_sha(files=("kete_prop.cu", "kete_device.cuh", "kete_step.cuh", "kete_order.cu")):

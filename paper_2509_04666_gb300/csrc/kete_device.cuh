@@ -736,55 +736,54 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
 // ---------------------------------------------------------------------------
 // universal-variable two-body propagation
 // ---------------------------------------------------------------------------
-// Stumpff C(z), S(z): nested (Horner) form of the power series for |z| < 1
-// (six terms when |z| < 1e-3, eleven otherwise), closed trigonometric /
-// hyperbolic forms beyond.
+// Stumpff C(z), S(z): the power series C = sum_k (-z)^k / (2k+2)!,
+// S = sum_k (-z)^k / (2k+3)! by Horner's rule in z (one FMA per term, the
+// coefficients folded at compile time) for |z| < 1 (seven terms when
+// |z| < 1e-3: the first omitted one is below 1e-34; twelve otherwise: below
+// 3e-27), closed trigonometric / hyperbolic forms beyond.
+__host__ __device__ constexpr double stumpff_c_coef(int k)
+{
+    double a = 0.5;   // 1 / 2!
+    for (int j = 1; j <= k; j++) a = -a / ((2.0 * j + 1.0) * (2.0 * j + 2.0));
+    return a;
+}
+__host__ __device__ constexpr double stumpff_s_coef(int k)
+{
+    double a = 1.0 / 6.0;   // 1 / 3!
+    for (int j = 1; j <= k; j++) a = -a / ((2.0 * j + 2.0) * (2.0 * j + 3.0));
+    return a;
+}
+// c <- c z + a_K, ..., down to a_0
+template <int K>
+struct StumpffHorner {
+    static __device__ __forceinline__ void run(double z, double &c, double &s)
+    {
+        constexpr double ck = stumpff_c_coef(K), sk = stumpff_s_coef(K);
+        c = fma(c, z, ck);
+        s = fma(s, z, sk);
+        StumpffHorner<K - 1>::run(z, c, s);
+    }
+};
+template <>
+struct StumpffHorner<-1> {
+    static __device__ __forceinline__ void run(double, double &, double &) {}
+};
+// terms k = 0 .. K-1
+template <int K>
+__device__ __forceinline__ void stumpff_series(double z, double &C, double &S)
+{
+    constexpr double c_top = stumpff_c_coef(K - 1), s_top = stumpff_s_coef(K - 1);
+    double c = c_top, s = s_top;
+    StumpffHorner<K - 2>::run(z, c, s);
+    C = c;
+    S = s;
+}
 __device__ __forceinline__ void stumpff(double z, double &C, double &S)
 {
     if (fabs(z) < 1e-3) {
-        // six terms of each series: the first omitted term is below 2e-20
-        double c = fma(-z * (1.0 / (13.0 * 14.0)), 1.0, 1.0);
-        c = fma(-z * (1.0 / (11.0 * 12.0)), c, 1.0);
-        c = fma(-z * (1.0 / (9.0 * 10.0)), c, 1.0);
-        c = fma(-z * (1.0 / (7.0 * 8.0)), c, 1.0);
-        c = fma(-z * (1.0 / (5.0 * 6.0)), c, 1.0);
-        c = fma(-z * (1.0 / (3.0 * 4.0)), c, 1.0);
-        C = 0.5 * c;
-        double s = fma(-z * (1.0 / (14.0 * 15.0)), 1.0, 1.0);
-        s = fma(-z * (1.0 / (12.0 * 13.0)), s, 1.0);
-        s = fma(-z * (1.0 / (10.0 * 11.0)), s, 1.0);
-        s = fma(-z * (1.0 / (8.0 * 9.0)), s, 1.0);
-        s = fma(-z * (1.0 / (6.0 * 7.0)), s, 1.0);
-        s = fma(-z * (1.0 / (4.0 * 5.0)), s, 1.0);
-        S = s * (1.0 / 6.0);
+        stumpff_series<7>(z, C, S);
     } else if (fabs(z) < 1.0) {
-        // C = 1/2 (1 - z/(3.4) (1 - z/(5.6) (1 - ...)))
-        double c = 1.0, s = 1.0;
-        c = fma(-z * (1.0 / (23.0 * 24.0)), c, 1.0);
-        c = fma(-z * (1.0 / (21.0 * 22.0)), c, 1.0);
-        c = fma(-z * (1.0 / (19.0 * 20.0)), c, 1.0);
-        c = fma(-z * (1.0 / (17.0 * 18.0)), c, 1.0);
-        c = fma(-z * (1.0 / (15.0 * 16.0)), c, 1.0);
-        c = fma(-z * (1.0 / (13.0 * 14.0)), c, 1.0);
-        c = fma(-z * (1.0 / (11.0 * 12.0)), c, 1.0);
-        c = fma(-z * (1.0 / (9.0 * 10.0)), c, 1.0);
-        c = fma(-z * (1.0 / (7.0 * 8.0)), c, 1.0);
-        c = fma(-z * (1.0 / (5.0 * 6.0)), c, 1.0);
-        c = fma(-z * (1.0 / (3.0 * 4.0)), c, 1.0);
-        C = 0.5 * c;
-        // S = 1/6 (1 - z/(4.5) (1 - z/(6.7) (1 - ...)))
-        s = fma(-z * (1.0 / (24.0 * 25.0)), s, 1.0);
-        s = fma(-z * (1.0 / (22.0 * 23.0)), s, 1.0);
-        s = fma(-z * (1.0 / (20.0 * 21.0)), s, 1.0);
-        s = fma(-z * (1.0 / (18.0 * 19.0)), s, 1.0);
-        s = fma(-z * (1.0 / (16.0 * 17.0)), s, 1.0);
-        s = fma(-z * (1.0 / (14.0 * 15.0)), s, 1.0);
-        s = fma(-z * (1.0 / (12.0 * 13.0)), s, 1.0);
-        s = fma(-z * (1.0 / (10.0 * 11.0)), s, 1.0);
-        s = fma(-z * (1.0 / (8.0 * 9.0)), s, 1.0);
-        s = fma(-z * (1.0 / (6.0 * 7.0)), s, 1.0);
-        s = fma(-z * (1.0 / (4.0 * 5.0)), s, 1.0);
-        S = s * (1.0 / 6.0);
+        stumpff_series<12>(z, C, S);
     } else if (z > 0.0) {
         double q = sqrt(z), sn, cs;
         sincos(q, &sn, &cs);
@@ -814,9 +813,11 @@ __device__ __forceinline__ bool kepler_uv(double mu, double sqmu, const double r
                                           const double v0[3], double dt, double &chi,
                                           double r[3], double v[3])
 {
-    // reciprocals taken once: FP64 division is a multi-instruction sequence
-    double rn0 = sqrt(fma(r0[0], r0[0], fma(r0[1], r0[1], r0[2] * r0[2])));
-    const double ri = 1.0 / rn0, isqmu = 1.0 / sqmu;
+    // reciprocals taken once: FP64 division and square root are
+    // multi-instruction sequences (|r0| from its reciprocal square root)
+    const double rr0 = fma(r0[0], r0[0], fma(r0[1], r0[1], r0[2] * r0[2]));
+    const double ri = rsqrt(rr0), isqmu = 1.0 / sqmu;
+    const double rn0 = rr0 * ri;
     double vv = fma(v0[0], v0[0], fma(v0[1], v0[1], v0[2] * v0[2]));
     double rv = fma(r0[0], v0[0], fma(r0[1], v0[1], r0[2] * v0[2]));
     double alpha = fma(-vv * isqmu, isqmu, 2.0 * ri);

@@ -677,24 +677,27 @@ __device__ __forceinline__ float apparent_mag(const kete_mag_params &P, const do
 // differentiating a twice more with |r.v| <= |r||v| and d(r.v)/dt = v^2 -
 // mu/|r| bounds the fourth derivative by |r4| <= 4 mu (mu/|r| + 6 v^2) / |r|^4.
 // With twice that bound (the expansion point moves by v tau) the term is
-// below lt_taylor_bound(); main-belt bodies give ~1e-17 AU, bodies at 0.2 AU
-// from the Sun ~1e-13 AU, a sungrazer at 0.01 AU ~1e-7 AU.  Where the bound
-// exceeds kTaylorMaxAu, k_exact solves the two-body problem at every
-// light-time iterate instead, as the definition does.  The Sun at t_obs -
+// below tau^4 mu (mu / |r| + 6 v^2) / (3 |r|^4); main-belt bodies give ~1e-17
+// AU, bodies at 0.2 AU from the Sun ~1e-13 AU, a sungrazer at 0.01 AU ~1e-7
+// AU.  Where the bound exceeds kTaylorMaxAu (lt_taylor_poor), k_exact solves
+// the two-body problem at every light-time iterate instead, as the definition
+// does.  The Sun at t_obs -
 // tau comes from its state at the exposure epoch, S - V tau (the neglected
 // term, a_sun tau^2 / 2 with |a_sun| ~ 1e-8 AU/day^2, stays below 2e-11 AU
 // for tau < 0.06 day).
 constexpr double kTaylorMaxAu = 1e-13;
 struct TwoBodyLT {
     double r[3], mv[3], a2[3], mj6[3];   // r, -v, a/2, -j/6 at dt_obs
+    double ri;                           // 1 / |r|
 };
 
-__device__ __forceinline__ double lt_taylor_bound(double mu, const TwoBodyLT &T, double tau)
+// the bound above exceeds kTaylorMaxAu (compared without the division)
+__device__ __forceinline__ bool lt_taylor_poor(double mu, const TwoBodyLT &T, double tau)
 {
     const double rr = dot3(T.r, T.r);
     const double vv = dot3(T.mv, T.mv);
     const double t2 = tau * tau;
-    return t2 * t2 * mu * (mu * rsqrt(rr) + 6.0 * vv) / (3.0 * rr * rr);
+    return t2 * t2 * mu * fma(mu, T.ri, 6.0 * vv) > (3.0 * kTaylorMaxAu) * (rr * rr);
 }
 
 __device__ __forceinline__ bool twobody_at(double mu, double sqmu, const double hr[3],
@@ -705,6 +708,7 @@ __device__ __forceinline__ bool twobody_at(double mu, double sqmu, const double 
     const bool ok = kepler_uv(mu, sqmu, hr, hv, dt_obs, chi, T.r, v);
     const double rr = dot3(T.r, T.r);
     const double ri = rsqrt(rr), ri2 = ri * ri;
+    T.ri = ri;
     const double k = -mu * ri2 * ri;
     const double q = 3.0 * dot3(T.r, v) * ri2;
 #pragma unroll
@@ -854,11 +858,13 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
             double chi = 0.0, pos[3];
             TwoBodyLT T;
             bool ok = twobody_at(mu, sqmu, hr, hv, dt_obs, chi, T);
-            twobody_pos(T, sun_obs, 0.0, pos);
+            // twobody_pos at tau = 0
+#pragma unroll
+            for (int c = 0; c < 3; c++) pos[c] = sun_obs[c] + T.r[c];
             double u[3] = {pos[0] - o[0], pos[1] - o[1], pos[2] - o[2]};
             double tau = sqrt(dot3(u, u)) * kInvC;
             // near the Sun the cubic is not good enough: solve at every iterate
-            const bool exact_lt = lt_taylor_bound(mu, T, 1.01 * tau) > kTaylorMaxAu;
+            const bool exact_lt = lt_taylor_poor(mu, T, 1.01 * tau);
             for (int it = 0; it < 4; it++) {
                 if (exact_lt) {
                     double rk[3], vk[3];
@@ -875,8 +881,9 @@ __global__ void __launch_bounds__(128) k_exact(ExactCtx C)
                 if (C.status) atomicCAS(&C.status[i], KETE_BODY_OK, KETE_BODY_KEPLER_CAP);
                 continue;   // next candidate of this thread
             }
-            const double un = sqrt(dot3(u, u));
-            const double iun = 1.0 / un;
+            const double uu = dot3(u, u);
+            const double un = sqrt(uu);
+            const double iun = rsqrt(uu);   // for the FP32 direction only
             const float uf[3] = {(float)(u[0] * iun), (float)(u[1] * iun), (float)(u[2] * iun)};
             bool have_radec = false;
             double ra = 0.0, dec = 0.0;
