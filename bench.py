@@ -40,7 +40,7 @@ MAS = math.radians(1.0 / 3.6e6)
 # of the same workload (100k bodies x 21 stops), per body-stop, scaled to the
 # full launch by its body-stops; valid only while the kernel source is
 # unchanged (the source hash below).
-PROFILED_TRAFFIC = {"src_sha": "d141a72662bbbcba", "bytes_per_body_stop": 65.9}
+PROFILED_TRAFFIC = {"src_sha": "6c043addf4c24b22", "bytes_per_body_stop": 65.7}
 
 
 # FP64 work of the exact FoV test per candidate it solves as ncu counts it (2 x
@@ -48,14 +48,14 @@ PROFILED_TRAFFIC = {"src_sha": "d141a72662bbbcba", "bytes_per_body_stop": 65.9}
 # same small case, divided by the candidates the prefilter passed to it); valid
 # only while the FoV kernels' source is unchanged.  The modelled count below leaves out the divisions, square roots
 # and convergence tests that the executed count includes.
-PROFILED_EXACT = {"src_sha": "4342528b4c0eb507", "fp64_flops_per_candidate": 834.6}
+PROFILED_EXACT = {"src_sha": "e94eae79f1bc68a2", "fp64_flops_per_candidate": 834.6}
 
 # FP64 arithmetic thread instructions (DFMA + DMUL + DADD) the FP64 survey's
 # propagation kernel executes per accepted step, from the same ncu capture as
-# the traffic (100k bodies x 21 stops: 16.83 G over 2,119,119 steps); with the
+# the traffic (100k bodies x 21 stops: 16.46 G over 2,119,119 steps); with the
 # step count of a run it gives the FP64 pipe's issue rate, which the FLOP
 # roofline understates (a DMUL or DADD takes an FMA's issue slot).
-PROFILED_ISSUE = {"src_sha": "d141a72662bbbcba", "fp64_inst_per_step": 7942.3}
+PROFILED_ISSUE = {"src_sha": "6c043addf4c24b22", "fp64_inst_per_step": 7765.8}
 
 
 def kernel_source_sha(files=("kete_prop.cu", "kete_device.cuh", "kete_step.cuh", "kete_order.cu")):
@@ -74,40 +74,61 @@ def _bits(m):
     return bin(m & 0x1FF).count("1")
 
 
+# coefficients a table may have for the per-thread path's shared Chebyshev
+# basis (longer tables take the series with the basis made on the fly)
+BASIS_MAX = 16
+# FLOPs of the force terms per mass: Newton (with the relative position and
+# velocity), GR (Eq. A.3) and J2 (Eq. A.4) with their per-mass factors formed
+# on the host
+NEWTON_FLOPS, GR_FLOPS, J2_FLOPS = 25, 23, 20
+
+
+def series64_flops(n_coef, act, gr):
+    """FP64 FLOPs of one per-thread evaluation's planet series: the segment
+    lookup (10), then either the shared basis (T_k: 1 + 2 (n_coef - 2); with
+    a GR mass also k U_(k-1): 3 (n_coef - 2)) and per mass 6 + 6 (n_coef - 2)
+    for the position, 10 + 12 (n_coef - 2) for a GR mass's position and
+    velocity; or, beyond BASIS_MAX, the basis made on the fly per mass:
+    6 + 8 (n_coef - 2), + 9 (n_coef - 2) + 3 for a velocity."""
+    k = n_coef - 2
+    if n_coef <= BASIS_MAX:
+        basis = 1 + 2 * k + (3 * k if gr else 0)
+        return 10 + basis + (act - gr) * (6 + 6 * k) + gr * (10 + 12 * k)
+    return 10 + act * (6 + 8 * k) + gr * (9 * k + 3)
+
+
 def prop_flops(st, fm, n_coef, mixed):
     """Algorithmic FLOPs of k_propagate from its counters (FMA = 2), as the
     kernel computes them for the force model fm:
-      per force evaluation from node rows: per active mass 25 (Newton incl.
-        relative position and velocity), +25 per GR mass (Eq. A.3), +21 per J2
-        mass (Eq. A.4);
-      per-thread evaluation (step not spanning a whole leg): + 10 for the
-        segment lookup, + per mass the position series and per GR mass the
-        velocity series.  FP64 series are summed upward with the basis made on
-        the fly (three coordinates): position 6 + 8 (n_coef - 2), velocity
-        9 (n_coef - 2) + 3.  FP32 series (mixed precision) by Clenshaw:
+      per force evaluation from node rows: per active mass NEWTON_FLOPS, per
+        GR mass + GR_FLOPS, per J2 mass + J2_FLOPS;
+      per-thread evaluation (step not spanning a whole leg): + the planet
+        series (series64_flops).  FP32 series (mixed precision) by Clenshaw:
         position 3 (3 (n_coef - 1) + 3), velocity 3 (4 (n_coef - 1) + 1);
       per corrector iteration: 7 substep predictors (x, v) and the g/b
         updates, 1440 (+48 for the FP64-part b6 in mixed precision);
       per step attempt: final x, v and step control, 121.
     In mixed precision the FP64 work of an evaluation is the Sun's monopole
-    (19) plus, per-thread, the Sun's position and velocity series; the
-    planetary terms are FP32.  Returns (fp64_flops, fp32_flops)."""
+    (19) plus, per-thread, the segment lookup and the Sun's position series
+    (on the fly); the planetary terms, the Sun's velocity series (with a
+    GR term) and the close-planet test at each step start (5 per planet) are
+    FP32.  Returns (fp64_flops, fp32_flops)."""
     act, gr, j2 = _bits(fm.body_mask), _bits(fm.gr_mask), _bits(fm.j2_mask)
-    pos64, vel64 = 6 + 8 * (n_coef - 2), 9 * (n_coef - 2) + 3
     pos32, vel32 = 3 * (3 * (n_coef - 1) + 3), 3 * (4 * (n_coef - 1) + 1)
     evals, node = st["force_evals"], st["node_evals"]
     attempts = st["steps"] + st["rejected"]
     if not mixed:
-        per = 25 * act + 25 * gr + 21 * j2
-        f64 = evals * per + (evals - node) * (act * pos64 + gr * vel64 + 10)
+        per = NEWTON_FLOPS * act + GR_FLOPS * gr + J2_FLOPS * j2
+        f64 = evals * per + (evals - node) * series64_flops(n_coef, act, gr)
         f64 += st["iterations"] * 1440 + attempts * 121
         return f64, 0
-    f64 = evals * 19 + (evals - node) * (pos64 + vel64 + 10) + st["iterations"] * 1488 \
-        + attempts * 121
-    f64 += st["steps"] * 8 * (act - 1)          # close-planet check at each step start
+    pos64 = 6 + 8 * (n_coef - 2)
+    f64 = evals * 19 + (evals - node) * (pos64 + 10) + st["iterations"] * 1488 + attempts * 121
     sun_gr, sun_j2 = fm.gr_mask & 1, fm.j2_mask & 1
-    per32 = 25 * (act - 1) + 25 * (gr - sun_gr) + 21 * (j2 - sun_j2) + 25 * sun_gr + 21 * sun_j2
-    f32 = evals * per32 + (evals - node) * ((act - 1) * pos32 + (gr - sun_gr) * vel32)
+    per32 = NEWTON_FLOPS * (act - 1) + GR_FLOPS * gr + J2_FLOPS * j2
+    f32 = evals * per32 + (evals - node) * ((act - 1) * pos32 + (gr - sun_gr) * vel32
+                                            + sun_gr * (pos32 + vel32))
+    f32 += st["steps"] * 5 * (act - 1)          # close-planet test at each step start
     return f64, f32
 
 

@@ -404,9 +404,18 @@ static int make_force(kete_ctx *ctx, const kete_force_model *fm_in, ForceDev &F)
         F.pole[m][2] = -se * ey + ce * ez;
     }
     for (int m = 0; m < KETE_MAX_BODIES; m++) {
-        F.gm32[m] = (float)ctx->E.gm[m];
+        const double gm = ctx->E.gm[m];
+        F.gm4[m] = 4.0 * gm;
+        F.grk[m] = gm * kInvC2;
+        F.gr4k[m] = 4.0 * F.grk[m];
+        for (int c = 0; c < 3; c++) F.pole_m2[m][c] = -2.0 * F.pole[m][c];
+        F.gm32[m] = (float)gm;
         F.j2k32[m] = (float)F.j2k[m];
         for (int c = 0; c < 3; c++) F.pole32[m][c] = (float)F.pole[m][c];
+        F.gm4_32[m] = (float)F.gm4[m];
+        F.grk32[m] = (float)F.grk[m];
+        F.gr4k32[m] = (float)F.gr4k[m];
+        for (int c = 0; c < 3; c++) F.pole_m2_32[m][c] = (float)F.pole_m2[m][c];
     }
     F.eps = fm.eps;
     F.eps_pc = fm.eps_pc;

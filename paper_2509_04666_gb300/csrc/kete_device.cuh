@@ -15,12 +15,8 @@
 namespace kete {
 
 // ---------------------------------------------------------------------------
-// physical constants (App. A.1 units: AU, TDB days)
+// constants (the physical ones, App. A.1 units, in kete_impl.h)
 // ---------------------------------------------------------------------------
-constexpr double kKmPerAu = 149597870.7;
-constexpr double kC = 299792.458 * 86400.0 / kKmPerAu;   // speed of light, AU/day
-constexpr double kInvC2 = 1.0 / (kC * kC);
-constexpr double kInvC = 1.0 / kC;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.28318530717958647692;
 
@@ -167,35 +163,52 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 template <>
 __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 
+// The constants of one mass (mu = GM; the GR and J2 factors from ForceDev).
+template <typename T>
+struct MassK {
+    T mu, mu4, grk, gr4k, j2k;   // mu, 4 mu, mu / c^2, 4 mu / c^2, 1.5 J2 mu R^2
+    const T *P, *Pm2;            // unit pole, -2 x the pole
+};
+__device__ __forceinline__ MassK<double> mass_k64(const EphemDev &E, const ForceDev &F, int m)
+{
+    return MassK<double>{E.gm[m], F.gm4[m], F.grk[m], F.gr4k[m], F.j2k[m], F.pole[m], F.pole_m2[m]};
+}
+__device__ __forceinline__ MassK<float> mass_k32(const ForceDev &F, int m)
+{
+    return MassK<float>{F.gm32[m], F.gm4_32[m], F.grk32[m], F.gr4k32[m], F.j2k32[m], F.pole32[m],
+                        F.pole_m2_32[m]};
+}
+
 // the three terms of one mass, accumulated into a[]; w = relative velocity
 template <typename T>
-__device__ __forceinline__ void mass_terms(T mu, T j2k, const T *P, bool newton, bool gr, bool j2,
+__device__ __forceinline__ void mass_terms(const MassK<T> &K, bool newton, bool gr, bool j2,
                                            const T r[3], const T w[3], T a[3])
 {
     T rr = fma(r[0], r[0], fma(r[1], r[1], r[2] * r[2]));
     T ri = rsqrt_t<T>(rr);
     T ri2 = ri * ri;
     T ri3 = ri2 * ri;
-    T f = newton ? -mu * ri3 : (T)0;
+    T f = newton ? -K.mu * ri3 : (T)0;
     if (gr) {
         T ww = fma(w[0], w[0], fma(w[1], w[1], w[2] * w[2]));
         T rw = fma(r[0], w[0], fma(r[1], w[1], r[2] * w[2]));
-        T k = mu * ri3 * (T)kInvC2;
-        f = fma(k, fma((T)4 * mu, ri, -ww), f);
-        T fw = (T)4 * k * rw;
+        T k = K.grk * ri3;                     // mu / (c^2 r^3)
+        f = fma(k, fma(K.mu4, ri, -ww), f);
+        T fw = (K.gr4k * ri3) * rw;            // 4 k (r.v)
         a[0] = fma(fw, w[0], a[0]);
         a[1] = fma(fw, w[1], a[1]);
         a[2] = fma(fw, w[2], a[2]);
     }
     if (j2) {
+        const T *P = K.P;
         T z = fma(r[0], P[0], fma(r[1], P[1], r[2] * P[2]));
-        T psi = j2k * ri3 * ri2;   // 1.5 J2 mu R^2 / r^5
-        T q = (T)5 * z * z * ri2;
-        f = fma(-psi, (T)1 - q, f);
-        T fp = (T)-2 * psi * z;
-        a[0] = fma(fp, P[0], a[0]);
-        a[1] = fma(fp, P[1], a[1]);
-        a[2] = fma(fp, P[2], a[2]);
+        T psi = K.j2k * ri3 * ri2;   // 1.5 J2 mu R^2 / r^5
+        T q = z * z * ri2;           // (z / r)^2
+        f = fma(-psi, fma((T)-5, q, (T)1), f);
+        T fp = psi * z;              // along -2 P
+        a[0] = fma(fp, K.Pm2[0], a[0]);
+        a[1] = fma(fp, K.Pm2[1], a[1]);
+        a[2] = fma(fp, K.Pm2[2], a[2]);
     }
     a[0] = fma(f, r[0], a[0]);
     a[1] = fma(f, r[1], a[1]);
@@ -539,7 +552,7 @@ __device__ __forceinline__ int accel_fp64(const EphemDev &E, const ForceDev &F, 
             w[1] = v[1] - st[4];
             w[2] = v[2] - st[5];
         }
-        mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r, w, a);
+        mass_terms<double>(mass_k64(E, F, m), true, gr, j2, r, w, a);
         if (JAC) newton_jacobian(E.gm[m], r, J);
     }
     if (G > 1) {
@@ -642,7 +655,7 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
         const bool j2 = F.j2_mask & 1u;
         if (sun_gr || j2) {
             float w[3] = {vf[0] - sunv[0], vf[1] - sunv[1], vf[2] - sunv[2]};
-            mass_terms<float>(F.gm32[0], F.j2k32[0], F.pole32[0], false, sun_gr, j2, df, w, af);
+            mass_terms<float>(mass_k32(F, 0), false, sun_gr, j2, df, w, af);
         }
     }
     // the Sun in FP32 only for the per-thread planet series (node rows are
@@ -699,11 +712,11 @@ __device__ __forceinline__ int accel_mixed(const EphemDev &E, const ForceDev &F,
             double w[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) w[c] = (vf_in ? (double)vf[c] : v[c]) - s64[3 + c];
-            mass_terms<double>(E.gm[m], F.j2k[m], F.pole[m], true, gr, j2, r64, w, as);
+            mass_terms<double>(mass_k64(E, F, m), true, gr, j2, r64, w, as);
             continue;
         }
         float w[3] = {vf[0] - st[3], vf[1] - st[4], vf[2] - st[5]};
-        mass_terms<float>(F.gm32[m], F.j2k32[m], F.pole32[m], true, gr, j2, r, w, af);
+        mass_terms<float>(mass_k32(F, m), true, gr, j2, r, w, af);
     }
     int ng_status = KETE_BODY_OK;
     if (G > 1) {

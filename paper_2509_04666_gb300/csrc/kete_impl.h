@@ -10,6 +10,12 @@
 
 namespace kete {
 
+// physical constants (App. A.1 units: AU, TDB days)
+constexpr double kKmPerAu = 149597870.7;
+constexpr double kC = 299792.458 * 86400.0 / kKmPerAu;   // speed of light, AU/day
+constexpr double kInvC2 = 1.0 / (kC * kC);
+constexpr double kInvC = 1.0 / kC;
+
 // device view of the loaded Chebyshev table
 struct EphemDev {
     const double *coef;      // [body][seg][3][n_coef]
@@ -26,6 +32,11 @@ struct ForceDev {
     int32_t precision;
     double j2k[KETE_MAX_BODIES];        // 1.5 * J2 * mu * R^2
     double pole[KETE_MAX_BODIES][3];    // unit pole, ecliptic J2000
+    // per-mass factors of the GR and J2 terms, formed once here (each saves
+    // an FP64 multiply per mass and force evaluation): 4 mu, mu / c^2,
+    // 4 mu / c^2 and -2 x the pole
+    double gm4[KETE_MAX_BODIES], grk[KETE_MAX_BODIES], gr4k[KETE_MAX_BODIES];
+    double pole_m2[KETE_MAX_BODIES][3];
     double eps, eps_pc, safety, dt_init;
     int32_t max_iter, pad;
     int64_t max_steps;
@@ -33,6 +44,8 @@ struct ForceDev {
     float gm32[KETE_MAX_BODIES];
     float j2k32[KETE_MAX_BODIES];
     float pole32[KETE_MAX_BODIES][3];
+    float gm4_32[KETE_MAX_BODIES], grk32[KETE_MAX_BODIES], gr4k32[KETE_MAX_BODIES];
+    float pole_m2_32[KETE_MAX_BODIES][3];
     const kete_nongrav *nongrav;        // per-body non-gravitational terms or null
 };
 

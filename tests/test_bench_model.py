@@ -14,12 +14,18 @@ class _FM:
 def test_prop_flops_node_rows_and_per_thread():
     st = {"force_evals": 10, "node_evals": 10, "steps": 0, "rejected": 0, "iterations": 0}
     f64, f32 = bench.prop_flops(st, _FM, 12, False)
-    assert f64 == 10 * (25 * 9 + 25 * 3 + 21 * 2) and f32 == 0
+    assert f64 == 10 * (25 * 9 + 23 * 3 + 20 * 2) and f32 == 0
     st["node_evals"] = 0
     f64b, _ = bench.prop_flops(st, _FM, 12, False)
-    # per-thread: segment lookup + a position series per mass + a velocity
-    # series per GR mass, summed upward (8 and 9 operations per coefficient)
-    assert f64b - f64 == 10 * (10 + 9 * (6 + 8 * 10) + 3 * (9 * 10 + 3))
+    # per-thread: segment lookup, the shared basis (T_k and, with GR masses,
+    # k U_(k-1)), then 3 FMAs per coefficient for a position and 6 for a
+    # position with its velocity (+ 1 + 3 to scale the velocity)
+    assert f64b - f64 == 10 * (10 + (1 + 2 * 10 + 3 * 10) + 6 * (6 + 6 * 10) + 3 * (10 + 12 * 10))
+    # a table beyond the shared basis: the basis made on the fly per mass
+    f64c, _ = bench.prop_flops(st, _FM, 20, False)
+    st["node_evals"] = 10
+    f64d, _ = bench.prop_flops(st, _FM, 20, False)
+    assert f64c - f64d == 10 * (10 + 9 * (6 + 8 * 18) + 3 * (9 * 18 + 3))
     st = {"force_evals": 0, "node_evals": 0, "steps": 2, "rejected": 1, "iterations": 5}
     assert bench.prop_flops(st, _FM, 12, False)[0] == 5 * 1440 + 3 * 121
 
@@ -27,9 +33,13 @@ def test_prop_flops_node_rows_and_per_thread():
 def test_prop_flops_mixed_split():
     st = {"force_evals": 4, "node_evals": 0, "steps": 1, "rejected": 0, "iterations": 1}
     f64, f32 = bench.prop_flops(st, _FM, 12, True)
-    assert f64 == 4 * 19 + 4 * ((6 + 80) + (90 + 3) + 10) + 1488 + 121 + 8 * 8
-    per32 = 25 * 8 + 25 * 2 + 21 * 1 + 25 + 21
-    assert f32 == 4 * per32 + 4 * (8 * 3 * (3 * 11 + 3) + 2 * 3 * (4 * 11 + 1))
+    # FP64: the Sun's monopole, and per-thread its position series
+    assert f64 == 4 * 19 + 4 * ((6 + 80) + 10) + 1488 + 121
+    # FP32: the planets' terms and the Sun's GR and J2, the planets' series,
+    # the Sun's position and velocity series, the close-planet test
+    per32 = 25 * 8 + 23 * 3 + 20 * 2
+    pos32, vel32 = 3 * (3 * 11 + 3), 3 * (4 * 11 + 1)
+    assert f32 == 4 * per32 + 4 * (8 * pos32 + 2 * vel32 + (pos32 + vel32)) + 5 * 8
 
 
 def test_fov_stage_roofline():
