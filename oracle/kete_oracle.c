@@ -94,7 +94,10 @@ int ko_ephem_load(ko_ephem *e, const void *buf, size_t n)
     if (n < 256 || memcmp(p, "KETECHB1", 8) != 0) return -1;
     memcpy(hdr, p + 8, sizeof(hdr));
     memcpy(td, p + 24, sizeof(td));
-    if (hdr[0] != 1 || hdr[1] < 1 || hdr[1] > KO_MAX_BODIES || hdr[2] < 1 || hdr[3] < 1)
+    /* at most 64 coefficients: the recurrences below keep T_k, U_k, D_k in
+     * arrays of 64 */
+    if (hdr[0] != 1 || hdr[1] < 1 || hdr[1] > KO_MAX_BODIES || hdr[2] < 1 || hdr[2] > 64 ||
+        hdr[3] < 1)
         return -1;
     e->n_bodies = hdr[1];
     e->n_coef = hdr[2];
