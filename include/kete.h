@@ -222,7 +222,10 @@ void kete_survey_opts_default(kete_survey_opts *opt);
  * n_bodies; int32 n_coef; int32 n_seg; double t_start; double seg_len;
  * double gm[16] at byte 48}, then double coef[n_bodies][n_seg][3][n_coef]
  * (ecliptic x, y, z of each body, AU; segment s covers [t_start + s L,
- * t_start + (s+1) L) with tau = 2 (t - t_mid)/L).  Replaces any earlier table.
+ * t_start + (s+1) L) with tau = 2 (t - t_mid)/L).  2 <= n_coef <= 64; tables of
+ * at most 16 coefficients per segment are evaluated per thread from one
+ * shared Chebyshev basis per force evaluation, longer ones with the basis
+ * made per body (the same sums, more FP64 work).  Replaces any earlier table.
  * Errors: KETE_ERR_BAD_ARG (malformed header/size), KETE_ERR_CUDA. */
 int kete_load_ephem(kete_ctx *ctx, const void *buf, size_t nbytes);
 
