@@ -94,3 +94,20 @@ def test_truncation_by_population_on_the_ragged_sample():
     assert tr["bodies"] >= len(sub) - 2
     assert tr["main_belt"] < 5e-14 and tr["trojan"] < 5e-14
     assert max(tr["neo"], tr["comet"]) < 3e-13 and tr["encounter"] < 1e-12
+
+
+def test_prop_flops_model_matches_the_profiled_launch():
+    """The FLOP model against the FP64 arithmetic ncu counted in the profiled
+    launch of the survey kernel (100,000 bodies x 21 stops: DFMA 8.784 G,
+    DMUL 4.488 G, DADD 3.185 G thread instructions; the run's counters
+    below), while the kernel sources are the profiled ones."""
+    if bench.PROFILED_ISSUE["src_sha"] != bench.kernel_source_sha():
+        import pytest
+        pytest.skip("kernel sources changed since the profile")
+    st = {"steps": 2119119, "rejected": 0, "force_evals": 46747675, "node_evals": 46141130,
+          "iterations": 6375508}
+    counted = 2 * 8783880360 + 4487792905 + 3184988488
+    model, _ = bench.prop_flops(st, _FM, 12, False)
+    assert abs(model / counted - 1.0) < 0.03, model / counted
+    inst = (8783880360 + 4487792905 + 3184988488) / st["steps"]
+    assert abs(inst - bench.PROFILED_ISSUE["fp64_inst_per_step"]) < 0.5
