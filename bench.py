@@ -48,7 +48,7 @@ PROFILED_TRAFFIC = {"src_sha": "6c043addf4c24b22", "bytes_per_body_stop": 65.7}
 # same small case, divided by the candidates the prefilter passed to it); valid
 # only while the FoV kernels' source is unchanged.  The modelled count below leaves out the divisions, square roots
 # and convergence tests that the executed count includes.
-PROFILED_EXACT = {"src_sha": "e94eae79f1bc68a2", "fp64_flops_per_candidate": 834.6}
+PROFILED_EXACT = {"src_sha": "78dc3d3396ef0f3c", "fp64_flops_per_candidate": 834.6}
 
 # FP64 arithmetic thread instructions (DFMA + DMUL + DADD) the FP64 survey's
 # propagation kernel executes per accepted step, from the same ncu capture as

@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(256) k_candidates(CandCtx C)
             const int32_t e = mode_o == 1 ? (int32_t)(a_o + off) : C.cell_exp[a_o + off];
             test_exposure(C, e, q, s_o, body_o);
         }
-        // each lane's tests taken this round
+        // each lane's tests taken in this pass of the loop
         const int taken = min(max(32 - excl, 0), cnt);
         u.a += taken;
     }
